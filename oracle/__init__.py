@@ -1,0 +1,248 @@
+"""CPU oracle of the VRM diffusion operator (arXiv 1508.06379).
+
+TEST INFRASTRUCTURE ONLY: a plain FP64 C restatement of the method
+(``vrm_oracle.c``) with a ctypes wrapper.  Only the tests, the smoke check
+and bench.py's CPU-baseline leg import this package; the CUDA library and
+its Python binding never do.  ``build()`` compiles the shared object with gcc
+(OpenMP, no floating-point contraction).
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vrm_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force=False):
+    """Compile liboracle.so next to the source (gcc, -ffp-contract=off)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_long), ("n_out", ctypes.c_long), ("n_diffused", ctypes.c_long),
+                ("n_inserted", ctypes.c_long), ("open_segments", ctypes.c_long),
+                ("small_ok", ctypes.c_long), ("full_ok", ctypes.c_long), ("no_stencil", ctypes.c_long),
+                ("max_pivots", ctypes.c_long), ("rounds", ctypes.c_int), ("max_dt_ratio", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        L.orc_reduce.restype = ctypes.c_long
+        L.orc_reduce.argtypes = [P, ctypes.c_long, ctypes.c_double, P]
+        L.orc_segment.restype = ctypes.c_int
+        L.orc_segment.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.orc_neighbours.restype = ctypes.c_long
+        L.orc_neighbours.argtypes = [P, P, ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int, P, P, ctypes.c_int, P, P]
+        L.orc_insertion_offsets.restype = None
+        L.orc_insertion_offsets.argtypes = [ctypes.c_double, P, P]
+        L.orc_insert.restype = ctypes.c_long
+        L.orc_insert.argtypes = [P, P, ctypes.c_long, ctypes.c_long, P, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P]
+        L.orc_rows.restype = ctypes.c_int
+        L.orc_rows.argtypes = [ctypes.c_int]
+        L.orc_vandermonde_column.restype = None
+        L.orc_vandermonde_column.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, P]
+        L.orc_phase1.restype = ctypes.c_int
+        L.orc_phase1.argtypes = [ctypes.c_int, ctypes.c_int, P, P, P, P, P]
+        L.orc_solve_weights.restype = None
+        L.orc_solve_weights.argtypes = [P, P, ctypes.c_long, P, P, P, ctypes.c_int, P, ctypes.c_double,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
+        L.orc_apply.restype = None
+        L.orc_apply.argtypes = [ctypes.c_long, ctypes.c_long, P, P, P, P, P, ctypes.c_int, ctypes.c_double, P]
+        L.orc_euler.restype = None
+        L.orc_euler.argtypes = [ctypes.c_long, ctypes.c_long, P, P, ctypes.c_double, P]
+        L.orc_step.restype = ctypes.c_long
+        L.orc_step.argtypes = [P, P, ctypes.c_long, ctypes.c_long, P, P, ctypes.c_double, ctypes.c_double,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+        L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.restype = None
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads():
+    return lib().orc_num_threads()
+
+
+def set_num_threads(t):
+    lib().orc_set_num_threads(int(t))
+
+
+# Derived constants, computed exactly as the oracle's step does.
+def constants(h, r=0.5, R=2.0, nu=1.0, c_diff=1.0, order=1):
+    rh, Rh = r * h, R * h
+    hp = h * h * h
+    if order == 2:
+        hp = hp * h
+    return dict(lo2=rh * rh, hi2=Rh * Rh, Rh=Rh, c_bound=c_diff * hp, nu_over_h2=nu / (h * h))
+
+
+def reduce(gamma, c_bound):
+    """Diffused flags (Sec. 3.5, Eq. reduced_bound): returns uint8[n]."""
+    g = _f64(gamma)
+    out = np.zeros(len(g), dtype=np.uint8)
+    lib().orc_reduce(_p(g), len(g), float(c_bound), _p(out))
+    return out
+
+
+def segment(dx, dy):
+    return lib().orc_segment(float(dx), float(dy))
+
+
+def neighbours(x, y, h, r=0.5, R=2.0, k_cap=32, fp32=False):
+    """Annulus neighbourhoods (Eq. neighbourhood), segment masks, small nbhd."""
+    x, y = _f64(x), _f64(y)
+    n = len(x)
+    c = constants(h, r, R)
+    count = np.zeros(n, dtype=np.int32)
+    idx = np.full((max(n, 1), k_cap), -1, dtype=np.int32)
+    mask = np.zeros(n, dtype=np.uint8)
+    small = np.full((max(n, 1), 8), -1, dtype=np.int32)
+    mx = lib().orc_neighbours(_p(x), _p(y), n, c["lo2"], c["hi2"], c["Rh"], int(bool(fp32)), _p(count), _p(idx),
+                              k_cap, _p(mask), _p(small))
+    return dict(count=count, idx=idx[:n], mask=mask, small=small[:n], max_count=int(mx))
+
+
+def insertion_offsets(h):
+    ox = np.zeros(8)
+    oy = np.zeros(8)
+    lib().orc_insertion_offsets(float(h), _p(ox), _p(oy))
+    return ox, oy
+
+
+def insert(x, y, diffused, h, r=0.5, R=2.0, max_rounds=8, capacity=None):
+    """Insertion rounds (Sec. 4.2).  Returns (x', y', rounds, open_segments)."""
+    n = len(x)
+    cap = capacity if capacity is not None else n + 8 * int(np.sum(diffused)) * (max_rounds + 1) + 16
+    xb = np.zeros(cap)
+    yb = np.zeros(cap)
+    xb[:n] = x
+    yb[:n] = y
+    d = np.ascontiguousarray(diffused, dtype=np.uint8)
+    c = constants(h, r, R)
+    rounds = ctypes.c_int(0)
+    open_ = ctypes.c_long(0)
+    n2 = lib().orc_insert(_p(xb), _p(yb), n, cap, _p(d), float(h), c["lo2"], c["hi2"], c["Rh"], int(max_rounds),
+                          ctypes.byref(rounds), ctypes.byref(open_))
+    if n2 < 0:
+        raise ValueError("capacity too small: need %d" % (-n2))
+    return xb[:n2].copy(), yb[:n2].copy(), rounds.value, open_.value
+
+
+def vandermonde(order, xi, eta):
+    m = lib().orc_rows(order)
+    K = len(xi)
+    V = np.zeros((m, K))
+    col = np.zeros(9)
+    for j in range(K):
+        lib().orc_vandermonde_column(order, float(xi[j]), float(eta[j]), _p(col))
+        V[:, j] = col[:m]
+    return V
+
+
+def phase1(V, b):
+    """Phase-I simplex on V f = b, f >= 0 (Sec. 4.1).  Returns (status, f, pivots, residual)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    b = _f64(b)
+    m, K = V.shape
+    f = np.zeros(max(K, 1))
+    npiv = ctypes.c_int(0)
+    res = ctypes.c_double(0)
+    st = lib().orc_phase1(m, K, _p(V), _p(b), _p(f), ctypes.byref(npiv), ctypes.byref(res))
+    return st, f[:K], npiv.value, res.value
+
+
+def solve_weights(x, y, diffused, nb, h, order=1, fallback=True, W=8):
+    x, y = _f64(x), _f64(y)
+    n = len(x)
+    k_cap = nb["idx"].shape[1]
+    cols = np.full((max(n, 1), W), -1, dtype=np.int32)
+    f = np.zeros((max(n, 1), W))
+    fii = np.zeros(max(n, 1))
+    status = np.zeros(max(n, 1), dtype=np.uint8)
+    npiv = np.zeros(max(n, 1), dtype=np.int32)
+    d = np.ascontiguousarray(diffused, dtype=np.uint8)
+    cnt = np.ascontiguousarray(nb["count"], dtype=np.int32)
+    idx = np.ascontiguousarray(nb["idx"], dtype=np.int32)
+    small = np.ascontiguousarray(nb["small"], dtype=np.int32)
+    lib().orc_solve_weights(_p(x), _p(y), n, _p(d), _p(cnt), _p(idx), k_cap, _p(small), float(h), int(order),
+                            int(bool(fallback)), W, _p(cols), _p(f), _p(fii), _p(status), _p(npiv))
+    return dict(cols=cols[:n], f=f[:n], fii=fii[:n], status=status[:n], npiv=npiv[:n])
+
+
+def apply(n_total, gamma, diffused, w, nu_over_h2):
+    g = _f64(gamma)
+    d = np.zeros(max(n_total, 1), dtype=np.uint8)
+    d[:len(diffused)] = diffused
+    out = np.zeros(max(n_total, 1))
+    cols = np.ascontiguousarray(w["cols"], dtype=np.int32)
+    f = _f64(w["f"])
+    fii = _f64(w["fii"])
+    W = cols.shape[1] if cols.ndim == 2 else 8
+    lib().orc_apply(n_total, len(g), _p(g), _p(d), _p(cols), _p(f), _p(fii), W, float(nu_over_h2), _p(out))
+    return out[:n_total]
+
+
+def step(x, y, gamma, h, nu, dt, r=0.5, R=2.0, c_diff=1.0, order=1, k_cap=32, max_rounds=8, fallback=True,
+         fp32_search=False, capacity=None):
+    """One VRM step.  Returns (x', y', gamma', stats dict)."""
+    n = len(x)
+    cap = capacity if capacity is not None else 2 * n + 1024
+    xb = np.zeros(cap)
+    yb = np.zeros(cap)
+    xb[:n] = x
+    yb[:n] = y
+    g = _f64(gamma)
+    go = np.zeros(cap)
+    st = Stats()
+    n2 = lib().orc_step(_p(xb), _p(yb), n, cap, _p(g), _p(go), float(h), float(r), float(R), float(nu),
+                        float(c_diff), int(order), float(dt), int(k_cap), int(max_rounds), int(bool(fallback)),
+                        int(bool(fp32_search)), ctypes.byref(st))
+    if n2 < 0:
+        raise ValueError("capacity too small: need %d" % (-n2))
+    return xb[:n2].copy(), yb[:n2].copy(), go[:n2].copy(), st.as_dict()
+
+
+def pipeline(x, y, gamma, h, nu, r=0.5, R=2.0, c_diff=1.0, order=1, k_cap=32, max_rounds=8, fallback=True,
+             fp32_search=False):
+    """Stage-by-stage run of one operator evaluation (the same steps as
+    ``step``), returning every intermediate for per-stage comparisons."""
+    c = constants(h, r, R, nu, c_diff, order)
+    diffused = reduce(gamma, c["c_bound"])
+    x2, y2, rounds, open_ = insert(x, y, diffused, h, r, R, max_rounds)
+    n2 = len(x2)
+    d2 = np.zeros(n2, dtype=np.uint8)
+    d2[:len(x)] = diffused
+    nb = neighbours(x2, y2, h, r, R, k_cap, fp32_search)
+    w = solve_weights(x2, y2, d2, nb, h, order, fallback)
+    dg = apply(n2, gamma, d2, w, c["nu_over_h2"])
+    return dict(diffused=d2, x=x2, y=y2, rounds=rounds, open=open_, nb=nb, w=w, dgamma=dg, const=c)
