@@ -1,0 +1,390 @@
+#!/usr/bin/env python3
+"""Throughput of one VRM diffusion step (vrm_step) on one GB300.
+
+Workload (default): the 1,002,001-particle lattice of spacing h = 2e-3 on
+[-1, 1]^2, jittered by U(-0.3h, 0.3h) per coordinate (seed 1508002), carrying
+a mixture of 8 Gaussian vortices; nu = 1e-3, growth control (C_diff = 1) and
+insertion on, Euler step dt = (1/8)(r h)^2/(4 nu).  A step is the whole
+operator: growth control, insertion rounds, neighbourhoods, LP weights,
+application and Euler update.  Metric: particles per second, counted after
+insertion (n'), whole job.
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the launching stream with an L2 flush (a 512 MB write) between steps,
+outside the events.  Every step takes the same input (the step is
+idempotent: it reads gamma_in and writes gamma_out and the appended
+positions), so every step does the same work.
+
+--impl reference times the CPU oracle (oracle/, FP64 C with OpenMP) on a
+bounded sample of the same workload with the same metric.
+Under torchrun (N > 1) every rank runs its own replica (replicas only: the
+operator is evaluated on one GPU per cloud, with no collective on the data
+path); the value is the sum of particles over ranks / the slowest rank's time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particles/s per VRM diffusion step on 1 GB300"
+UNIT = "particles/s"
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz (x1000 -> GFLOP/s)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mixture_1m", choices=["mixture_1m", "lamb_oseen_h002"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name, rank=0):
+    import vrm_inputs
+    if name == "mixture_1m":
+        h, nu = 2e-3, 1e-3
+        x, y, g = vrm_inputs.gaussian_mixture_cloud(h=h, jitter=0.3, seed=vrm_inputs.SEED_BASE + 2 + 1000 * rank)
+        desc = {"workload": "jittered lattice 1001x1001, h=2e-3, jitter 0.3h, 8-Gaussian mixture, nu=1e-3, "
+                            "C_diff=1, insertion on, FP64", "n": int(len(x)), "h": h, "nu": nu}
+    else:
+        h, nu = 0.02, 1e-3
+        x, y, g = vrm_inputs.lamb_oseen_lattice(h, 1.0, nu, 1.0, eps=1e-10)
+        desc = {"workload": "Lamb-Oseen lattice h=0.02, Gamma=1, nu=1e-3, t0=1, |omega|>1e-10", "n": int(len(x)),
+                "h": h, "nu": nu}
+    dt = (0.5 * h) ** 2 / (4 * nu) / 8
+    desc["dt"] = dt
+    return x, y, g, h, nu, dt, desc
+
+
+def sample_window(x, y, g, frac):
+    """Centred square window holding about `frac` of the cloud."""
+    import numpy as np
+    lo_x, hi_x = x.min(), x.max()
+    lo_y, hi_y = y.min(), y.max()
+    a = 0.5 * math.sqrt(frac)
+    cx, cy = 0.5 * (lo_x + hi_x), 0.5 * (lo_y + hi_y)
+    keep = (np.abs(x - cx) <= a * (hi_x - lo_x)) & (np.abs(y - cy) <= a * (hi_y - lo_y))
+    return x[keep].copy(), y[keep].copy(), g[keep].copy()
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, bus_id=None):
+        self.proc = None
+        self.lines = []
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if bus_id:
+            cmd += ["-i", bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for t, line in self.lines:
+            if t < t0 or t > t1:
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def lp_small_flops(n_lp, pivots):
+    """Algorithmic FP64 flops of the small-neighbourhood LPs (m = 5 rows,
+    K = 8 columns): per LP 120 for the Vandermonde columns and phase-I cost
+    row (8 x [2 offsets + 3 distance + 2 scalings + 3 products + 5 sums]) and
+    93 for the final residual (40 multiply-adds, 5 differences) and f~_ii
+    (8 sums); per pivot 122: 5 ratio divisions, 9 pivot-row scalings and the
+    (m+1)(K+1) = 54 multiply-adds of the tableau update."""
+    return n_lp * (120 + 93) + pivots * 122
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1508_06379_gb300 as vrm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    vrm.build()
+    x, y, g, h, nu, dt, desc = workload(args.workload, rank)
+    n = len(x)
+    cap = int(n * 1.6) + 4096
+    dev = torch.device("cuda", local)
+    xb = torch.zeros(cap, dtype=torch.float64, device=dev)
+    yb = torch.zeros(cap, dtype=torch.float64, device=dev)
+    xb[:n] = torch.from_numpy(x).to(dev)
+    yb[:n] = torch.from_numpy(y).to(dev)
+    gi = torch.from_numpy(g).to(dev)
+    go = torch.zeros(cap, dtype=torch.float64, device=dev)
+    ctx = vrm.VRM(h=h, nu=nu)
+    ctx.set_timing(True)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        flush.zero_()
+        ctx.step(xb, yb, n, gi, go, dt)
+    torch.cuda.synchronize()
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        bus = None
+    clocks = Clocks(bus if isinstance(bus, str) else None)
+    time.sleep(0.5)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = vrm.launch_count()
+    t_wall0 = time.time()
+    total_ms = 0.0
+    parts = 0
+    stage_ms = {k: [] for k in vrm.STAGES}
+    stats = None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n2, stats = ctx.step(xb, yb, n, gi, go, dt)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        parts += n2
+        for k, v in ctx.stage_times().items():
+            stage_ms[k].append(v)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    launches = vrm.launch_count() - launches0
+    ck = clocks.stop(t_wall0, t_wall1)
+    if dist:
+        t = torch.tensor([total_ms, float(parts)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_ms_max, parts_all = tmax[0].item(), t[1].item()
+    else:
+        total_ms_max, parts_all = total_ms, float(parts)
+    value = parts_all / (total_ms_max * 1e-3)
+
+    # end to end through the C ABI with host buffers: h2d of the inputs and d2h
+    # of the result (gamma_out and appended positions) inside the timed region
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.from_numpy(y).pin_memory()
+    gh = torch.from_numpy(g).pin_memory()
+    go_h = torch.empty(cap, dtype=torch.float64).pin_memory()
+    xo_h = torch.empty(cap, dtype=torch.float64).pin_memory()
+    yo_h = torch.empty(cap, dtype=torch.float64).pin_memory()
+    e2e_ms, e2e_parts, h2d, d2h = 0.0, 0, 0, 0
+    e2e_steps = max(1, min(args.steps, 10))
+    for _ in range(e2e_steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xb[:n].copy_(xh, non_blocking=True)
+        yb[:n].copy_(yh, non_blocking=True)
+        gi.copy_(gh, non_blocking=True)
+        n2, _ = ctx.step(xb, yb, n, gi, go, dt, stats=False)
+        go_h[:n2].copy_(go[:n2], non_blocking=True)
+        xo_h[n:n2].copy_(xb[n:n2], non_blocking=True)
+        yo_h[n:n2].copy_(yb[n:n2], non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        e2e_parts += n2
+        h2d = 24 * n
+        d2h = 8 * n2 + 16 * (n2 - n)
+    e2e_value = e2e_parts / (e2e_ms * 1e-3)
+    if dist:
+        t = torch.tensor([e2e_ms, float(e2e_parts)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        e2e_value = t[1].item() / (tmax[0].item() * 1e-3)
+
+    mean_stage = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage_ms.items()}
+    dom = max(mean_stage, key=mean_stage.get)
+    roofline = roofline_for(dom, mean_stage[dom], stats, n)
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(args.workload)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(desc, n_out=int(stats["n_out"]), n_diffused=int(stats["n_diffused"]),
+                       n_inserted=int(stats["n_inserted"]), insertion_rounds=int(stats["rounds"]),
+                       l2="flushed between steps (512 MB write)", parallelism="replicas" if world > 1 else "1 GPU"),
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "roofline": roofline,
+        "stage_ms": {k: round(v, 4) for k, v in mean_stage.items()},
+        "lp": {"small_solved": int(stats["lp_small_solved"]), "small_pivots": int(stats["lp_small_pivots"]),
+               "full_solved": int(stats["lp_full_solved"]), "max_pivots": int(stats["max_pivots"])},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current source of that kernel (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        data = json.load(open(p))
+        ent = data[kernel]
+        src = open(os.path.join(ROOT, "paper_1508_06379_gb300", "csrc", ent["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != ent["source_sha256"]:
+            return None
+        return ent["bytes_per_launch"]
+    except Exception:
+        return None
+
+
+def roofline_for(stage, ms, stats, n):
+    if stage == "lp_small":
+        flops = lp_small_flops(stats["lp_small_solved"], stats["lp_small_pivots"])
+        ach = flops / (ms * 1e-3) / 1e12
+        peak = FP64_PEAK_GFLOPS / 1000.0
+        return {"kernel": "k_lp_small", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": traffic_for("k_lp_small"),
+                "peak_source": "FP64: 152 SMs x 2 FMA lanes/clk x 2 flop x 2.07 GHz (derived; measured FMA loop "
+                               "1.198 TFLOP/s)"}
+    hbm = None
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
+        src = "of measured"
+    except Exception:
+        hbm, src = 6800.0, "of fallback"
+    n_out = stats["n_out"]
+    if stage == "search":
+        nbytes = n_out * 100.0
+        kern = "k_search_all"
+    elif stage == "apply":
+        nbytes = n_out * 69.0 + stats["n_diffused"] * 49.0
+        kern = "k_apply"
+    else:
+        nbytes = n_out * 24.0
+        kern = stage
+    ach = nbytes / (ms * 1e-3) / 1e9
+    return {"kernel": kern, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": traffic_for(kern), "peak_source": src}
+
+
+def cpu_baseline(name, frac=0.3):
+    """The oracle as it stands on a bounded sample (centred window) of the
+    workload, all host cores."""
+    import oracle
+    oracle.build()
+    x, y, g, h, nu, dt, _ = workload(name)
+    if name == "mixture_1m":
+        x, y, g = sample_window(x, y, g, frac)
+    t0 = time.time()
+    x2, y2, g2, st = oracle.step(x, y, g, h, nu, dt)
+    t = time.time() - t0
+    return {"value": len(x2) / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "one oracle step on the centred window holding %.0f%% of the workload (%d particles in, %d "
+                      "after insertion), %.1f s" % (100 * frac, len(x), len(x2), t)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    x, y, g, h, nu, dt, desc = workload(args.workload)
+    frac = 0.06 if args.workload == "mixture_1m" else 1.0
+    if frac < 1.0:
+        x, y, g = sample_window(x, y, g, frac)
+    for _ in range(args.warmup):
+        oracle.step(x, y, g, h, nu, dt)
+    t0 = time.time()
+    parts = 0
+    for _ in range(args.steps):
+        x2, y2, g2, st = oracle.step(x, y, g, h, nu, dt)
+        parts += len(x2)
+    t = time.time() - t0
+    value = parts / t
+    sample = "each step: one oracle step on the centred window holding %.0f%% of the workload (%d particles in)" % (
+        100 * frac, len(x))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": desc,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,247 @@
+/*
+ * vrm.h: C ABI of the GB300 (sm_103a) implementation of the diffusion
+ * operator of the splitting-free vorticity redistribution method (VRM),
+ * M. Kirchhart and S. Obi, arXiv 1508.06379.
+ *
+ * A 2-D vortex-particle cloud carries circulations Gamma_i at positions x_i
+ * (Sec. 1, Eq. vfield).  The operator approximates nu * Laplacian of the
+ * vorticity by redistribution weights f_ij (Sec. 2):
+ *     dGamma_j/dt = nu sum_i f_ij Gamma_i                  (Eq. nsode)
+ * with f_ij >= 0 for j != i, f_ii = -sum_{j != i} f_ij (Eq. fii), chosen per
+ * particle so that the moment conditions V_i f_i = b hold (Eq. momcondmv).
+ *
+ * Conventions shared by every entry point
+ *   - All array arguments are DEVICE pointers owned by the caller, unless a
+ *     comment says "host".  The library never frees or keeps them.
+ *   - Positions are FP64, structure of arrays: x[i], y[i].
+ *   - Indices are int32 (particle counts below 2^31).
+ *   - Neighbour rows are "ELL" rows of width k_cap: row i occupies
+ *     nbr_idx[i*k_cap .. i*k_cap + min(nbr_count[i], k_cap)), ascending
+ *     global indices; entries past the count are not written.
+ *   - Stencils have width VRM_STENCIL_W: stencil i occupies
+ *     cols[i*W .. i*W+W), f[i*W .. i*W+W): the nonzero h-scaled weights
+ *     f~_ij = h^2 f_ij in the LP's column order, padded with -1 / 0.0;
+ *     fii[i] = f~_ii.
+ *   - small (n*8 int32) and cols (n*VRM_STENCIL_W int32) must start on a
+ *     16-byte boundary (their rows are read as 16-byte vectors); a
+ *     misaligned pointer gives VRM_ERR_ARG.
+ *   - Every call is asynchronous on the given stream, except that a call
+ *     which returns a size or statistics to a host pointer synchronises the
+ *     stream before it returns.
+ *   - Every call returns a vrm_status; no call aborts or throws.  On
+ *     VRM_ERR_CUDA the stream's work may be incomplete; on any error the
+ *     output arrays are unspecified.
+ *   - Derived constants are computed once in vrm_create, in FP64, as
+ *       lo2 = (r h)^2, hi2 = (R h)^2         annulus bounds (Eq. neighbourhood)
+ *       c_bound = C_diff * ((h*h)*h)         growth-control bound (Eq. reduced_bound, n = 1)
+ *       nu_over_h2 = nu / (h*h)
+ *       inv_h = 1 / h
+ *     so that a caller can reproduce every decision bit for bit.
+ */
+#ifndef VRM_H
+#define VRM_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+typedef int vrm_status;
+#define VRM_OK 0
+#define VRM_ERR_ARG 1        /* bad parameter, null pointer, NaN/Inf input */
+#define VRM_ERR_CAPACITY 2   /* an output or scratch capacity is too small */
+#define VRM_ERR_CUDA 3       /* a CUDA runtime call failed */
+#define VRM_ERR_UNSUPPORTED 4 /* a parameter value this build does not support */
+
+/* Stencil width: columns kept per particle (small neighbourhood = 8). */
+#define VRM_STENCIL_W 8
+/* Largest neighbour-row width (k_cap) the library accepts. */
+#define VRM_KCAP_MAX 32
+
+/* Per-particle LP outcome codes (status arrays). */
+#define VRM_LP_NOT_DIFFUSED 0
+#define VRM_LP_SMALL 1   /* solved on the small neighbourhood (Sec. 4.3) */
+#define VRM_LP_FULL 2    /* solved on the full neighbourhood after a retry */
+#define VRM_LP_NONE 3    /* no non-negative stencil found: zero stencil */
+
+/* Precision of the neighbour search (Sec. 2, Eq. neighbourhood). */
+#define VRM_PREC_FP64 0  /* FP64 distances (bit-identical to the FP64 oracle) */
+#define VRM_PREC_MIXED 1 /* FP32 distances on FP32-rounded positions; the LP
+                            and the application stay FP64 */
+
+/* ---- parameters ---------------------------------------------------------- */
+typedef struct vrm_params {
+  double h;          /* mean particle spacing (length units) */
+  double r;          /* inner annulus radius in units of h (paper: 1/2) */
+  double R;          /* outer annulus radius in units of h (paper: 2) */
+  double nu;         /* kinematic viscosity */
+  double c_diff;     /* growth-control constant C_diff (Eq. reduced_bound) */
+  int32_t order;     /* consistency order n; this build supports n = 1 (m = 5 rows) */
+  int32_t k_cap;     /* neighbour-row width, 8 <= k_cap <= VRM_KCAP_MAX */
+  int32_t max_rounds;/* insertion rounds per step (Sec. 4.2), >= 0 */
+  int32_t fallback;  /* 1: retry failed small neighbourhoods on the full one (Sec. 4.3) */
+  int32_t precision; /* VRM_PREC_FP64 or VRM_PREC_MIXED */
+  int32_t reserved;
+} vrm_params;
+
+/* Counters of one call.  Filled only when a stats pointer is given (host). */
+typedef struct vrm_stats {
+  int64_t n_in;          /* particles given */
+  int64_t n_out;         /* particles after insertion */
+  int64_t n_diffused;    /* |D|: particles that diffuse (Sec. 3.5) */
+  int64_t n_inserted;    /* zero-strength particles appended (Sec. 4.2) */
+  int64_t open_segments; /* empty segments of diffused particles left after max_rounds */
+  int64_t small_ok;      /* stencils from the small neighbourhood */
+  int64_t full_ok;       /* stencils from the full-neighbourhood retry */
+  int64_t no_stencil;    /* diffused particles left with a zero stencil */
+  int32_t rounds;        /* insertion rounds that appended particles */
+  int32_t max_pivots;    /* largest pivot count of one LP */
+  int32_t max_count;     /* largest neighbour count (> k_cap means rows were cut) */
+  int32_t reserved;
+  double max_dt_ratio;   /* max over diffused i of nu*dt*(-f~_ii)/h^2; > 1 breaks
+                            the a-posteriori stability bound (Thm. stability) */
+  int64_t lp_small_solved; /* LPs run on small neighbourhoods (= |D|) */
+  int64_t lp_small_pivots; /* pivots summed over those LPs */
+  int64_t lp_full_solved;  /* LPs run on full neighbourhoods */
+  int64_t lp_full_pivots;  /* pivots summed over those LPs */
+} vrm_stats;
+
+/* Stages of vrm_step, for vrm_stage_times. */
+#define VRM_STAGE_REDUCE 0   /* growth control, diffused list */
+#define VRM_STAGE_GRID 1     /* cell grid of the given cloud, segment masks */
+#define VRM_STAGE_INSERT 2   /* insertion rounds */
+#define VRM_STAGE_SEARCH 3   /* cell grid of the final cloud, neighbourhoods */
+#define VRM_STAGE_LP_SMALL 4 /* LP on small neighbourhoods */
+#define VRM_STAGE_LP_FULL 5  /* LP retry on full neighbourhoods */
+#define VRM_STAGE_APPLY 6    /* application and Euler update */
+#define VRM_STAGE_COUNT 7
+
+typedef struct vrm_ctx vrm_ctx;
+
+/* Paper defaults: r = 1/2, R = 2, n = 1, C_diff = 1 (Sec. 4.2, 6), k_cap = 32,
+   8 insertion rounds, fallback on, FP64; h and nu set to 1. */
+void vrm_default_params(vrm_params* p);
+
+/* Text of a status code (static storage). */
+const char* vrm_status_string(vrm_status s);
+
+/* Create a context on the current CUDA device.  Checks the parameters
+   (VRM_ERR_ARG / VRM_ERR_UNSUPPORTED) and computes the derived constants.
+   The context owns its scratch memory, grown on demand by the calls below;
+   one context must not be used by two streams at once. */
+vrm_status vrm_create(const vrm_params* p, vrm_ctx** out);
+void vrm_destroy(vrm_ctx* ctx);
+
+/*
+ * Growth control and insertion (Sec. 3.5 and Sec. 4.2).
+ *   1. D = the particles that diffuse: the complement of the longest prefix I
+ *      of the particles sorted by (|Gamma_i|, i) with
+ *      sum_I |Gamma_i| <= C_diff h^{n+2} ||Gamma||_1 (Eq. reduced_bound),
+ *      the sums taken exactly on |Gamma_i| 2^(96-E) truncated to integers.
+ *   2. Insertion rounds: every i in D whose annulus r h <= |x_j - x_i| <= R h
+ *      leaves a 45-degree segment s empty proposes x_i + 1.5 h (cos, sin)
+ *      ((s + 1/2) pi/4); a proposal is dropped if a proposal of smaller key
+ *      (i, s) lies closer than r h; the rest are appended in key order.
+ *      Rounds repeat until none is proposed, at most max_rounds times.
+ * x, y:      capacity entries; [0, n) given, appended points written at [n, n').
+ * gamma:     n circulations (read only).
+ * diffused:  capacity bytes out: 1 for i in D, 0 otherwise (also 0 on [n, n')).
+ * n_out:     host; receives n'.  Synchronises the stream.
+ * Errors: VRM_ERR_ARG on null pointers, n < 0, n > capacity or non-finite
+ * input; VRM_ERR_CAPACITY when n' would exceed capacity (stats->n_out, if
+ * given, then holds the count needed).
+ */
+vrm_status vrm_insert_reduce(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capacity, const double* gamma,
+                             uint8_t* diffused, int32_t* n_out, vrm_stats* stats, cudaStream_t stream);
+
+/*
+ * Neighbourhoods (Eq. neighbourhood), segment masks and small neighbourhoods
+ * (Sec. 4.2, 4.3) of n particles, by a cell-list search.
+ * nbr_count: n out, |N_i \ {i}| (the true count, also above k_cap).
+ * nbr_idx:   n*k_cap out, ELL rows (see top); rows above k_cap keep their
+ *            k_cap smallest indices.
+ * seg_mask:  n out, bit s set iff segment s of the annulus holds a particle;
+ *            segment s is the half-open angle [s pi/4, (s+1) pi/4) of r_ij.
+ * small:     n*8 out, small[i*8+s] = the particle of segment s with the
+ *            smallest distance (ties: smaller index), -1 if empty.
+ * max_count: host, optional (may be NULL); receives max_i nbr_count[i] and
+ *            synchronises.  Without it the call is fully asynchronous.
+ * Errors: VRM_ERR_ARG; VRM_ERR_CAPACITY if max_count is requested and some
+ * row exceeds k_cap (the outputs are still written, cut as described).
+ */
+vrm_status vrm_build_neighbourhoods(vrm_ctx* ctx, const double* x, const double* y, int32_t n, int32_t* nbr_count,
+                                    int32_t* nbr_idx, uint8_t* seg_mask, int32_t* small, int32_t* max_count,
+                                    cudaStream_t stream);
+
+/*
+ * Redistribution weights (Sec. 2 Eq. momcondmv, Sec. 4.1, 4.3) of every
+ * particle with diffused[i] = 1: the phase-I simplex on the small
+ * neighbourhood (columns ordered by (|r_ij|^2, j)), rows
+ * (1,0) (0,1) (2,0) (1,1) (0,2) in xi = r_ij / h with b = (0,0,2,0,2);
+ * artificials start the basis; entering column = lowest index with reduced
+ * cost < -1e-12; leaving row = minimum ratio over pivots > 1e-12, ties within
+ * 1e-12 max(1, ratio) to the lowest basic variable (artificials first); at
+ * most 64 pivots; feasible iff phase-I objective <= 1e-10 and
+ * max |V f~ - b| <= 1e-10; basic values <= 1e-11 are zeros.  If infeasible
+ * and fallback is on, the same LP on the full row (its k_cap first entries,
+ * ordered by (|r_ij|^2, j)); if that fails too the stencil is zero.
+ * f~_ii = -sum_j f~_ij in column order.
+ * Inputs are the outputs of vrm_build_neighbourhoods on the same x, y, n.
+ * cols, f:  n*VRM_STENCIL_W out; fii: n out; status: n out (VRM_LP_*).
+ * stats:    host, optional; fills small_ok, full_ok, no_stencil, max_pivots,
+ *           n_diffused and synchronises.
+ */
+vrm_status vrm_solve_weights(vrm_ctx* ctx, const double* x, const double* y, int32_t n, const uint8_t* diffused,
+                             const int32_t* nbr_count, const int32_t* nbr_idx, const int32_t* small, int32_t* cols,
+                             double* f, double* fii, uint8_t* status, vrm_stats* stats, cudaStream_t stream);
+
+/*
+ * Operator application (Eq. nsode, reduced form Eq. reducedop):
+ *   dgamma[j] = (nu/h^2) * sum_{i in D} f~_ij Gamma_i
+ * for j in [0, n), as a gather over the neighbour rows (the annulus relation
+ * is symmetric, so every i with j in its stencil is in row j): terms in
+ * ascending i with the self term f~_jj Gamma_j at i = j, products and sums
+ * rounded separately, no atomics.  Particles i >= n_gamma carry Gamma = 0.
+ * gamma: n_gamma values; diffused, nbr_*, cols, f, fii as produced above.
+ */
+vrm_status vrm_apply(vrm_ctx* ctx, int32_t n, int32_t n_gamma, const double* gamma, const uint8_t* diffused,
+                     const int32_t* nbr_count, const int32_t* nbr_idx, const int32_t* cols, const double* f,
+                     const double* fii, double* dgamma, cudaStream_t stream);
+
+/*
+ * One forward-Euler step of the heat equation with the VRM operator
+ * (Sec. 3.3): growth control, insertion, neighbourhoods, weights, then
+ *   gamma_out[j] = fma(dt, dgamma[j], gamma_in[j])   (gamma_in = 0 for j >= n)
+ * for j in [0, n').  Scratch lives in the context.
+ * x, y:      capacity entries; inserted points appended at [n, n').
+ * gamma_in:  n values (read only); gamma_out: capacity entries, must not
+ *            overlap gamma_in.  Repeating a call with the same n and
+ *            gamma_in gives the same result (x, y beyond n are overwritten
+ *            with the same points).
+ * n_out:     host; receives n'.  Synchronises the stream.
+ * stats:     host, optional.
+ * Errors: as vrm_insert_reduce and vrm_build_neighbourhoods; a row above
+ * k_cap gives VRM_ERR_CAPACITY (stats->max_count holds the width needed).
+ */
+vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capacity, const double* gamma_in,
+                    double* gamma_out, double dt, int32_t* n_out, vrm_stats* stats, cudaStream_t stream);
+
+/* Per-stage timing of vrm_step with CUDA events recorded on the call's
+   stream between the stages.  Off by default; enable != 0 turns it on. */
+vrm_status vrm_set_timing(vrm_ctx* ctx, int32_t enable);
+/* ms[VRM_STAGE_COUNT] (host) receives the stage durations in milliseconds of
+   the last vrm_step made with timing on (0 for stages it skipped).  Waits for
+   that step's events. */
+vrm_status vrm_stage_times(vrm_ctx* ctx, float* ms);
+
+/* Kernels launched by this library in this process so far (all contexts). */
+int64_t vrm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VRM_H */

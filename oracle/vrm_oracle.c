@@ -110,7 +110,8 @@ long orc_reduce(const double* gamma, long n, double c_bound, unsigned char* diff
     double a = fabs(gamma[i]);
     if (a > amax) amax = a;
   }
-  if (amax == 0.0) {
+  if (amax == 0.0 || !(c_bound < 1.0)) {
+    /* no circulation, or a bound of at least ||Gamma||_1: nothing diffuses */
     memset(diffused, 0, (size_t)n);
     return 0;
   }

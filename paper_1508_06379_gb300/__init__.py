@@ -1,0 +1,16 @@
+"""GB300 (sm_103a) implementation of the diffusion operator of the
+splitting-free vorticity redistribution method (Kirchhart & Obi,
+arXiv 1508.06379).
+
+The compute path is the CUDA library libvrm.so (C ABI in include/vrm.h);
+this package holds its build and a thin ctypes binding with the same names
+as the C entry points.
+"""
+from .binding import (KCAP_MAX, LP_FULL, LP_NONE, LP_NOT_DIFFUSED, LP_SMALL, STENCIL_W, VRM, VRM_ERR_ARG,
+                      VRM_ERR_CAPACITY, VRM_ERR_CUDA, VRM_ERR_UNSUPPORTED, VRM_OK, Params, Stats, VRMError,
+                      library_path, load_library, launch_count, STAGES)
+from .builder import build
+
+__all__ = ["VRM", "VRMError", "Params", "Stats", "build", "load_library", "library_path", "launch_count", "STAGES", "STENCIL_W", "KCAP_MAX",
+           "LP_NOT_DIFFUSED", "LP_SMALL", "LP_FULL", "LP_NONE", "VRM_OK", "VRM_ERR_ARG", "VRM_ERR_CAPACITY",
+           "VRM_ERR_CUDA", "VRM_ERR_UNSUPPORTED"]

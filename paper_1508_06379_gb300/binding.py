@@ -1,0 +1,239 @@
+"""ctypes binding of libvrm.so (the C ABI of include/vrm.h).
+
+Argument marshalling only: every stage runs in the CUDA library.  Tensors
+must be contiguous CUDA tensors of the documented dtypes; the calls are
+issued on torch's current CUDA stream.  If the library is missing this module
+raises; there is no fallback.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import builder as _build
+
+VRM_OK = 0
+VRM_ERR_ARG = 1
+VRM_ERR_CAPACITY = 2
+VRM_ERR_CUDA = 3
+VRM_ERR_UNSUPPORTED = 4
+STENCIL_W = 8
+KCAP_MAX = 32
+PREC_FP64 = 0
+PREC_MIXED = 1
+LP_NOT_DIFFUSED, LP_SMALL, LP_FULL, LP_NONE = 0, 1, 2, 3
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("r", ctypes.c_double), ("R", ctypes.c_double), ("nu", ctypes.c_double),
+                ("c_diff", ctypes.c_double), ("order", ctypes.c_int32), ("k_cap", ctypes.c_int32),
+                ("max_rounds", ctypes.c_int32), ("fallback", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_in", ctypes.c_int64), ("n_out", ctypes.c_int64), ("n_diffused", ctypes.c_int64),
+                ("n_inserted", ctypes.c_int64), ("open_segments", ctypes.c_int64), ("small_ok", ctypes.c_int64),
+                ("full_ok", ctypes.c_int64), ("no_stencil", ctypes.c_int64), ("rounds", ctypes.c_int32),
+                ("max_pivots", ctypes.c_int32), ("max_count", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_dt_ratio", ctypes.c_double), ("lp_small_solved", ctypes.c_int64),
+                ("lp_small_pivots", ctypes.c_int64), ("lp_full_solved", ctypes.c_int64),
+                ("lp_full_pivots", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class VRMError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, _lib_handle().vrm_status_string(status).decode(), status))
+
+
+# Exported symbols and their signatures (mirrors include/vrm.h).
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+SIGNATURES = {
+    "vrm_default_params": (None, [P]),
+    "vrm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "vrm_create": (ctypes.c_int, [P, P]),
+    "vrm_destroy": (None, [P]),
+    "vrm_insert_reduce": (ctypes.c_int, [P, P, P, I32, I32, P, P, P, P, P]),
+    "vrm_build_neighbourhoods": (ctypes.c_int, [P, P, P, I32, P, P, P, P, P, P]),
+    "vrm_solve_weights": (ctypes.c_int, [P, P, P, I32, P, P, P, P, P, P, P, P, P, P]),
+    "vrm_apply": (ctypes.c_int, [P, I32, I32, P, P, P, P, P, P, P, P, P]),
+    "vrm_step": (ctypes.c_int, [P, P, P, I32, I32, P, P, ctypes.c_double, P, P, P]),
+    "vrm_set_timing": (ctypes.c_int, [P, I32]),
+    "vrm_stage_times": (ctypes.c_int, [P, P]),
+    "vrm_launch_count": (ctypes.c_int64, []),
+}
+STAGES = ("reduce", "grid", "insert", "search", "lp_small", "lp_full", "apply")
+
+_LIB = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def _lib_handle():
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError("libvrm.so is not built (%s); run __graft_entry__.build() or "
+                               "python -m paper_1508_06379_gb300.builder" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def launch_count():
+    """Kernels the library has launched in this process."""
+    return int(_lib_handle().vrm_launch_count())
+
+
+def load_library(build_if_missing=False):
+    if build_if_missing:
+        _build.build()
+    return _lib_handle()
+
+
+def _ptr(t, dtype, what, min_numel=0):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % what)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (what, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    if t.numel() < min_numel:
+        raise ValueError("%s holds %d elements, needs %d" % (what, t.numel(), min_numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class VRM:
+    """One context of the VRM library (parameters + scratch)."""
+
+    def __init__(self, h, nu, r=0.5, R=2.0, c_diff=1.0, order=1, k_cap=32, max_rounds=8, fallback=True,
+                 precision="fp64"):
+        self.lib = _lib_handle()
+        p = Params()
+        self.lib.vrm_default_params(ctypes.byref(p))
+        p.h, p.nu, p.r, p.R, p.c_diff = float(h), float(nu), float(r), float(R), float(c_diff)
+        p.order, p.k_cap, p.max_rounds, p.fallback = int(order), int(k_cap), int(max_rounds), int(bool(fallback))
+        p.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
+        self.params = p
+        self.k_cap = int(k_cap)
+        h_ = ctypes.c_void_p()
+        st = self.lib.vrm_create(ctypes.byref(p), ctypes.byref(h_))
+        if st != VRM_OK:
+            raise VRMError(st, "vrm_create")
+        self.ctx = h_
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.vrm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != VRM_OK:
+            raise VRMError(st, what)
+
+    # -- stages -------------------------------------------------------------------
+    def insert_reduce(self, x, y, n, gamma, diffused=None, stats=True):
+        cap = x.numel()
+        if diffused is None:
+            diffused = torch.empty(cap, dtype=torch.uint8, device=x.device)
+        n_out = ctypes.c_int32(0)
+        s = Stats()
+        st = self.lib.vrm_insert_reduce(self.ctx, _ptr(x, torch.float64, "x", n), _ptr(y, torch.float64, "y", cap),
+                                        int(n), int(cap), _ptr(gamma, torch.float64, "gamma", n),
+                                        _ptr(diffused, torch.uint8, "diffused", cap), ctypes.byref(n_out),
+                                        ctypes.byref(s) if stats else None, _stream())
+        self._check(st, "vrm_insert_reduce")
+        return n_out.value, diffused, s.as_dict()
+
+    def build_neighbourhoods(self, x, y, n, out=None, max_count=True):
+        dev = x.device
+        o = out or {}
+        cnt = o.get("count", torch.empty(n, dtype=torch.int32, device=dev))
+        idx = o.get("idx", torch.empty(max(n, 1) * self.k_cap, dtype=torch.int32, device=dev))
+        mask = o.get("mask", torch.empty(n, dtype=torch.uint8, device=dev))
+        small = o.get("small", torch.empty(max(n, 1) * 8, dtype=torch.int32, device=dev))
+        mc = ctypes.c_int32(0)
+        st = self.lib.vrm_build_neighbourhoods(
+            self.ctx, _ptr(x, torch.float64, "x", n), _ptr(y, torch.float64, "y", n), int(n),
+            _ptr(cnt, torch.int32, "nbr_count", n), _ptr(idx, torch.int32, "nbr_idx", n * self.k_cap),
+            _ptr(mask, torch.uint8, "seg_mask", n), _ptr(small, torch.int32, "small", 8 * n),
+            ctypes.byref(mc) if max_count else None, _stream())
+        self._check(st, "vrm_build_neighbourhoods")
+        return dict(count=cnt, idx=idx, mask=mask, small=small, max_count=mc.value if max_count else None)
+
+    def solve_weights(self, x, y, n, diffused, nb, out=None, stats=True):
+        dev = x.device
+        o = out or {}
+        W = STENCIL_W
+        cols = o.get("cols", torch.empty(max(n, 1) * W, dtype=torch.int32, device=dev))
+        f = o.get("f", torch.empty(max(n, 1) * W, dtype=torch.float64, device=dev))
+        fii = o.get("fii", torch.empty(max(n, 1), dtype=torch.float64, device=dev))
+        status = o.get("status", torch.empty(max(n, 1), dtype=torch.uint8, device=dev))
+        s = Stats()
+        st = self.lib.vrm_solve_weights(
+            self.ctx, _ptr(x, torch.float64, "x", n), _ptr(y, torch.float64, "y", n), int(n),
+            _ptr(diffused, torch.uint8, "diffused", n), _ptr(nb["count"], torch.int32, "nbr_count", n),
+            _ptr(nb["idx"], torch.int32, "nbr_idx", n * self.k_cap), _ptr(nb["small"], torch.int32, "small", 8 * n),
+            _ptr(cols, torch.int32, "cols", n * W), _ptr(f, torch.float64, "f", n * W),
+            _ptr(fii, torch.float64, "fii", n), _ptr(status, torch.uint8, "status", n),
+            ctypes.byref(s) if stats else None, _stream())
+        self._check(st, "vrm_solve_weights")
+        return dict(cols=cols, f=f, fii=fii, status=status, stats=s.as_dict())
+
+    def apply(self, n, n_gamma, gamma, diffused, nb, w, dgamma=None):
+        if dgamma is None:
+            dgamma = torch.empty(max(n, 1), dtype=torch.float64, device=gamma.device)
+        W = STENCIL_W
+        st = self.lib.vrm_apply(
+            self.ctx, int(n), int(n_gamma), _ptr(gamma, torch.float64, "gamma", n_gamma),
+            _ptr(diffused, torch.uint8, "diffused", n), _ptr(nb["count"], torch.int32, "nbr_count", n),
+            _ptr(nb["idx"], torch.int32, "nbr_idx", n * self.k_cap), _ptr(w["cols"], torch.int32, "cols", n * W),
+            _ptr(w["f"], torch.float64, "f", n * W), _ptr(w["fii"], torch.float64, "fii", n),
+            _ptr(dgamma, torch.float64, "dgamma", n), _stream())
+        self._check(st, "vrm_apply")
+        return dgamma
+
+    def set_timing(self, enable=True):
+        self._check(self.lib.vrm_set_timing(self.ctx, int(bool(enable))), "vrm_set_timing")
+
+    def stage_times(self):
+        """Stage durations (ms) of the last step made with timing on."""
+        buf = (ctypes.c_float * len(STAGES))()
+        self._check(self.lib.vrm_stage_times(self.ctx, buf), "vrm_stage_times")
+        return dict(zip(STAGES, list(buf)))
+
+    def step(self, x, y, n, gamma_in, gamma_out, dt, stats=True):
+        """One Euler step; x, y, gamma_out hold `capacity` = x.numel() entries."""
+        cap = x.numel()
+        n_out = ctypes.c_int32(0)
+        s = Stats()
+        st = self.lib.vrm_step(self.ctx, _ptr(x, torch.float64, "x", n), _ptr(y, torch.float64, "y", cap), int(n),
+                               int(cap), _ptr(gamma_in, torch.float64, "gamma_in", n),
+                               _ptr(gamma_out, torch.float64, "gamma_out", cap), float(dt), ctypes.byref(n_out),
+                               ctypes.byref(s) if stats else None, _stream())
+        self._check(st, "vrm_step")
+        return n_out.value, s.as_dict()

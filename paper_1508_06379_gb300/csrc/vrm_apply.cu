@@ -1,0 +1,72 @@
+// Operator application (Eq. nsode, reduced operator Eq. reducedop) and the
+// forward-Euler update (Sec. 3.3).
+//
+//   dGamma_j/dt = (nu/h^2) sum_{i in D} f~_ij Gamma_i
+//
+// computed as a gather, one thread per target j and no floating-point
+// atomics: the annulus relation is symmetric (dx and dy only change sign when
+// i and j swap, so d2 is bit-identical), hence every source i whose stencil
+// contains j is in j's neighbour row, and the row is sorted by index.  The
+// terms are added in ascending i with the self term f~_jj Gamma_j at i = j,
+// each product and sum rounded separately, which fixes the result bit for
+// bit given the weights.  Targets are visited in cell order so that the
+// stencils of the neighbours of a warp's targets share cache lines.
+#include "vrm_internal.cuh"
+
+namespace vrm {
+
+__global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, int n_gamma, const double* __restrict__ gamma,
+                                                  const uint8_t* __restrict__ diffused,
+                                                  const int* __restrict__ nbr_count, const int* __restrict__ nbr_idx,
+                                                  const int* __restrict__ cols, const double* __restrict__ f,
+                                                  const double* __restrict__ fii, const int* __restrict__ order,
+                                                  double* __restrict__ dgamma, double* __restrict__ gamma_out,
+                                                  double dt) {
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
+    const int j = order ? order[p] : (int)p;
+    const int cnt0 = nbr_count[j];
+    const int cnt = cnt0 < c.k_cap ? cnt0 : c.k_cap;
+    const int* row = nbr_idx + (size_t)j * c.k_cap;
+    const bool self_src = j < n_gamma && diffused[j];
+    const double gj = j < n_gamma ? gamma[j] : 0.0;
+    const double selfv = self_src ? __dmul_rn(fii[j], gj) : 0.0;
+    bool self_done = !self_src;
+    double acc = 0.0;
+    for (int t = 0; t < cnt; ++t) {
+      const int i = row[t];
+      if (!self_done && i > j) {
+        acc = __dadd_rn(acc, selfv);
+        self_done = true;
+      }
+      if (i >= n_gamma || !diffused[i]) continue;
+      const int4* cr = reinterpret_cast<const int4*>(cols + (size_t)i * VRM_STENCIL_W);
+      const int4 a = cr[0], b = cr[1];
+      int slot = -1;
+      slot = (a.x == j) ? 0 : slot;
+      slot = (a.y == j) ? 1 : slot;
+      slot = (a.z == j) ? 2 : slot;
+      slot = (a.w == j) ? 3 : slot;
+      slot = (b.x == j) ? 4 : slot;
+      slot = (b.y == j) ? 5 : slot;
+      slot = (b.z == j) ? 6 : slot;
+      slot = (b.w == j) ? 7 : slot;
+      if (slot >= 0) acc = __dadd_rn(acc, __dmul_rn(f[(size_t)i * VRM_STENCIL_W + slot], gamma[i]));
+    }
+    if (!self_done) acc = __dadd_rn(acc, selfv);
+    const double dg = __dmul_rn(c.nu_over_h2, acc);
+    if (dgamma) dgamma[j] = dg;
+    if (gamma_out) gamma_out[j] = __fma_rn(dt, dg, gj);
+  }
+}
+
+cudaError_t apply_gather(const Consts& c, int n, int n_gamma, const double* gamma, const uint8_t* diffused,
+                         const int* nbr_count, const int* nbr_idx, const int* cols, const double* f, const double* fii,
+                         const int* order, double* dgamma, double* gamma_out, double dt, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (n + kBlock - 1) / kBlock;
+  k_apply<<<blocks, kBlock, 0, s>>>(c, n, n_gamma, gamma, diffused, nbr_count, nbr_idx, cols, f, fii, order, dgamma,
+                                    gamma_out, dt); note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace vrm

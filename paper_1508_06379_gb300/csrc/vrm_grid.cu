@@ -1,0 +1,276 @@
+// Cell grid, scans and compaction for the VRM library.
+//
+// The neighbour search (Sec. 2, Eq. neighbourhood) runs on a uniform cell
+// grid whose cell side is at least R h, so that the annulus of a particle lies
+// in the 3 x 3 cells around it.  Particles are binned by a counting sort:
+// an atomic count per cell gives every particle its rank inside its cell, an
+// exclusive scan gives the cell starts, and a scatter writes positions and
+// indices in cell order (row-major cells, so the three cells of one grid row
+// are contiguous in memory).  The order inside a cell is not deterministic;
+// no result depends on it (neighbour rows are sorted by index afterwards).
+#include <atomic>
+
+#include "vrm_internal.cuh"
+
+namespace vrm {
+
+static int g_sm_count = 0;
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+int sm_count() {
+  if (g_sm_count == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sm_count <= 0) g_sm_count = 1;
+  }
+  return g_sm_count;
+}
+
+int persistent_blocks(int block_threads, int per_sm) {
+  (void)block_threads;
+  return sm_count() * per_sm;
+}
+
+// ---- scans -------------------------------------------------------------------
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+size_t scan_tmp_ints(int n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 2; }
+
+template <typename T>
+__device__ __forceinline__ int load_count(const T* in, long i, int n) {
+  return i < n ? (int)in[i] : 0;
+}
+
+// Block-wide exclusive scan of one int per thread; returns the block total.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
+  __shared__ int warp_sums[kScanThreads / 32];
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) warp_sums[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < kScanThreads / 32) warp_sums[lane] = wi - w;
+    if (lane == kScanThreads / 32 - 1) *total = wi;
+  }
+  __syncthreads();
+  int r = incl - v + warp_sums[warp];
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+__global__ void k_tile_sums(const T* __restrict__ in, int n, int* __restrict__ tile_sums) {
+  long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * kScanItems;
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) s += load_count(in, base + k, n);
+  __shared__ int total;
+  block_exclusive_scan(s, &total);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// Single block: exclusive scan of the tile sums in place; tile_sums[ntiles]
+// receives the grand total.
+__global__ void k_scan_tile_sums(int* __restrict__ tile_sums, int ntiles) {
+  __shared__ int total;
+  int carry = 0;
+  for (int base = 0; base < ntiles; base += kScanThreads) {
+    int i = base + threadIdx.x;
+    int v = i < ntiles ? tile_sums[i] : 0;
+    int ex = block_exclusive_scan(v, &total);
+    if (i < ntiles) tile_sums[i] = ex + carry;
+    carry += total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tile_sums[ntiles] = carry;
+}
+
+template <typename T>
+__global__ void k_tile_scan(const T* __restrict__ in, int n, const int* __restrict__ tile_sums, int ntiles,
+                            int* __restrict__ out) {
+  long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * kScanItems;
+  int v[kScanItems];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = load_count(in, base + k, n);
+    s += v[k];
+  }
+  __shared__ int total;
+  int ex = block_exclusive_scan(s, &total) + tile_sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < n) out[base + k] = ex;
+    ex += v[k];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_sums[ntiles];
+}
+
+template <typename T>
+static cudaError_t scan_impl(const T* in, int* out, int n, int* tmp, cudaStream_t s) {
+  if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int), s);
+  int ntiles = (n + kScanTile - 1) / kScanTile;
+  k_tile_sums<T><<<ntiles, kScanThreads, 0, s>>>(in, n, tmp); note_launch();
+  k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(tmp, ntiles); note_launch();
+  k_tile_scan<T><<<ntiles, kScanThreads, 0, s>>>(in, n, tmp, ntiles, out); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t scan_exclusive_i32(const int* in, int* out, int n, int* tmp, cudaStream_t s) {
+  return scan_impl<int>(in, out, n, tmp, s);
+}
+cudaError_t scan_exclusive_u8(const uint8_t* in, int* out, int n, int* tmp, cudaStream_t s) {
+  return scan_impl<uint8_t>(in, out, n, tmp, s);
+}
+
+__global__ void k_compact(const uint8_t* __restrict__ flags, int n, const int* __restrict__ pos,
+                          int* __restrict__ list, int* __restrict__ count) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    if (flags[i]) list[pos[i]] = (int)i;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count = pos[n];
+}
+
+cudaError_t compact_flags(const uint8_t* flags, int n, int* list, int* count, int* pos, int* tmp, cudaStream_t s) {
+  cudaError_t e = scan_exclusive_u8(flags, pos, n, tmp, s);
+  if (e != cudaSuccess) return e;
+  int blocks = n > 0 ? (n + kBlock - 1) / kBlock : 1;
+  if (blocks > 8 * sm_count()) blocks = 8 * sm_count();
+  k_compact<<<blocks, kBlock, 0, s>>>(flags, n, pos, list, count); note_launch();
+  return cudaGetLastError();
+}
+
+// ---- grid ----------------------------------------------------------------------
+
+__global__ void k_bbox_init(unsigned long long* bb) {
+  bb[0] = ~0ull;  // min x (ordered)
+  bb[1] = 0ull;   // max x
+  bb[2] = ~0ull;  // min y
+  bb[3] = 0ull;   // max y
+  bb[4] = 0ull;   // non-finite flag
+}
+
+__global__ void k_bbox(const double* __restrict__ x, const double* __restrict__ y, int n,
+                       unsigned long long* __restrict__ bb) {
+  unsigned long long mnx = ~0ull, mxx = 0, mny = ~0ull, mxy = 0;
+  int bad = 0;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    double a = x[i], b = y[i];
+    if (!isfinite(a) || !isfinite(b)) {
+      bad = 1;
+      continue;
+    }
+    unsigned long long oa = ordered_bits(a), ob = ordered_bits(b);
+    mnx = oa < mnx ? oa : mnx;
+    mxx = oa > mxx ? oa : mxx;
+    mny = ob < mny ? ob : mny;
+    mxy = ob > mxy ? ob : mxy;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long t;
+    t = __shfl_xor_sync(0xffffffffu, mnx, o);
+    mnx = t < mnx ? t : mnx;
+    t = __shfl_xor_sync(0xffffffffu, mxx, o);
+    mxx = t > mxx ? t : mxx;
+    t = __shfl_xor_sync(0xffffffffu, mny, o);
+    mny = t < mny ? t : mny;
+    t = __shfl_xor_sync(0xffffffffu, mxy, o);
+    mxy = t > mxy ? t : mxy;
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&bb[0], mnx);
+    atomicMax(&bb[1], mxx);
+    atomicMin(&bb[2], mny);
+    atomicMax(&bb[3], mxy);
+    if (bad) atomicOr(&bb[4], 1ull);
+  }
+}
+
+__global__ void k_grid_finalize(const unsigned long long* __restrict__ bb, int n, double Rh, int ncell_cap,
+                                Grid* __restrict__ g) {
+  Grid G;
+  G.nonfinite = (int)bb[4];
+  double x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+  if (n > 0 && bb[0] != ~0ull) {
+    x0 = from_ordered_bits(bb[0]);
+    x1 = from_ordered_bits(bb[1]);
+    y0 = from_ordered_bits(bb[2]);
+    y1 = from_ordered_bits(bb[3]);
+  }
+  double cs = Rh * (1.0 + 1e-6);
+  double w = x1 - x0, hgt = y1 - y0;
+  // keep nx * ny within the cell capacity for very sparse clouds
+  while ((floor(w / cs) + 1.0) * (floor(hgt / cs) + 1.0) > (double)ncell_cap) cs *= 2.0;
+  G.x0 = x0;
+  G.y0 = y0;
+  G.inv_cs = 1.0 / cs;
+  G.nx = (int)floor(w * G.inv_cs) + 1;
+  G.ny = (int)floor(hgt * G.inv_cs) + 1;
+  if ((long)G.nx * G.ny > ncell_cap) {  // rounding at the limit: enlarge once more
+    G.inv_cs *= 0.5;
+    G.nx = (int)floor(w * G.inv_cs) + 1;
+    G.ny = (int)floor(hgt * G.inv_cs) + 1;
+  }
+  G.ncell = G.nx * G.ny;
+  *g = G;
+}
+
+__global__ void k_bin(const double* __restrict__ x, const double* __restrict__ y, int n, const Grid* __restrict__ gp,
+                      int* __restrict__ cell_key, int* __restrict__ cell_rank, int* __restrict__ cell_count) {
+  const Grid g = *gp;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    int key = grid_cell_y(g, y[i]) * g.nx + grid_cell_x(g, x[i]);
+    cell_key[i] = key;
+    cell_rank[i] = atomicAdd(&cell_count[key], 1);
+  }
+}
+
+__global__ void k_scatter(const double* __restrict__ x, const double* __restrict__ y, int n,
+                          const int* __restrict__ cell_key, const int* __restrict__ cell_rank,
+                          const int* __restrict__ cell_start, double2* __restrict__ sorted_xy,
+                          int* __restrict__ sorted_idx) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    int p = cell_start[cell_key[i]] + cell_rank[i];
+    sorted_xy[p] = make_double2(x[i], y[i]);
+    sorted_idx[p] = (int)i;
+  }
+}
+
+cudaError_t grid_build(const double* x, const double* y, int n, double Rh, int ncell_cap, Grid* g, int* cell_key,
+                       int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy, int* sorted_idx,
+                       unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s) {
+  int blocks = n > 0 ? (n + kBlock - 1) / kBlock : 1;
+  int pblocks = blocks < 4 * sm_count() ? blocks : 4 * sm_count();
+  k_bbox_init<<<1, 1, 0, s>>>(bbox_tmp); note_launch();
+  k_bbox<<<pblocks, kBlock, 0, s>>>(x, y, n, bbox_tmp); note_launch();
+  k_grid_finalize<<<1, 1, 0, s>>>(bbox_tmp, n, Rh, ncell_cap, g); note_launch();
+  cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int) * (size_t)ncell_cap, s);
+  if (e != cudaSuccess) return e;
+  k_bin<<<blocks, kBlock, 0, s>>>(x, y, n, g, cell_key, cell_rank, cell_count); note_launch();
+  e = scan_exclusive_i32(cell_count, cell_start, ncell_cap, scan_tmp, s);
+  if (e != cudaSuccess) return e;
+  k_scatter<<<blocks, kBlock, 0, s>>>(x, y, n, cell_key, cell_rank, cell_start, sorted_xy, sorted_idx); note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace vrm

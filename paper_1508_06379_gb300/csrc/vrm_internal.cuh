@@ -1,0 +1,185 @@
+// Internal declarations of the VRM CUDA library (not part of the C ABI).
+//
+// Layout of the work (one context, one stream):
+//   vrm_grid.cu    bounding box, cell binning, scans and compaction
+//   vrm_reduce.cu  growth control (Sec. 3.5): exact radix select on |Gamma|
+//   vrm_search.cu  annulus neighbourhoods, segment masks, small neighbourhoods
+//   vrm_insert.cu  insertion rounds (Sec. 4.2)
+//   vrm_lp.cu      phase-I simplex per particle (Sec. 4.1, 4.3)
+//   vrm_apply.cu   gather-form operator application and Euler update
+//   vrm_api.cu     the C ABI: argument checks, scratch, orchestration
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vrm.h"
+
+namespace vrm {
+
+typedef unsigned __int128 u128;
+
+// Threads per block for the streaming kernels, and the persistent grid size
+// (a multiple of the SM count) used for grid-stride loops.
+constexpr int kBlock = 256;
+
+// Constants every kernel may need, passed by value.
+struct Consts {
+  double h, inv_h, lo2, hi2, Rh, c_bound, nu_over_h2;
+  float lo2f, hi2f;
+  double ins_dx[8], ins_dy[8];  // insertion offsets 1.5h (cos, sin)((s+1/2) pi/4)
+  int k_cap;
+  int max_rounds;
+  int fallback;
+  int precision;
+};
+
+// Uniform cell grid, device resident (written by grid_build).
+struct Grid {
+  double x0, y0, inv_cs;
+  int nx, ny, ncell;
+  int nonfinite;  // set if a position was NaN/Inf
+};
+
+// Device-side counters of one step.
+struct DevStats {
+  int n_diffused;
+  int n_open;          // open particles of the current insertion round
+  int n_accepted;      // points accepted in the current round
+  int small_ok, full_ok, no_stencil;
+  int max_pivots;
+  int max_count;
+  int n_fail;          // particles queued for the full-neighbourhood LP
+  int nonfinite;       // set if a circulation was NaN/Inf
+  unsigned long long max_dt_ratio_bits;  // positive double, as bits
+  unsigned long long lp_small_pivots, lp_full_pivots;
+  int lp_small_solved, lp_full_solved;
+};
+
+// Growth-control selection state (device resident).
+struct ReduceState {
+  unsigned long long amax_bits;  // max |Gamma| as bits
+  int E;                         // max |Gamma| < 2^E
+  int done;                      // 1: no particle diffuses / selection finished early
+  unsigned long long prefix;     // high key bits matched so far
+  unsigned long long tau_lo, tau_hi;  // remaining budget (u128)
+  unsigned long long T;          // threshold key (bits of |Gamma|)
+  int k_tie;                     // particles with key == T that stay out (lowest indices)
+  int all_out;                   // 1: every particle stays out (sum within bound)
+  unsigned long long hist[256][4];  // per digit: limb sums (3 x 32-bit limbs) and count
+};
+
+struct Scratch;  // defined in vrm_api.cu
+
+// ---- device helpers --------------------------------------------------------
+
+// Segment k covers [k pi/4, (k+1) pi/4) counter-clockwise from +x, decided by
+// comparisons only (seg(-r) = seg(r) + 4 mod 8 exactly).
+template <typename T>
+__device__ __forceinline__ int segment_of(T dx, T dy) {
+  int s;
+  if (dx > T(0) && dy >= T(0)) s = dy < dx ? 0 : 1;
+  else if (dx <= T(0) && dy > T(0)) s = dy > -dx ? 2 : 3;
+  else if (dx < T(0) && dy <= T(0)) s = dy > dx ? 4 : 5;
+  else s = -dy > dx ? 6 : 7;
+  return s;
+}
+
+// Squared distance with separate roundings (no contraction).
+__device__ __forceinline__ double dist2(double dx, double dy) {
+  return __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+}
+__device__ __forceinline__ float dist2f(float dx, float dy) {
+  return __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+}
+
+// Order-preserving map of doubles to u64 (for atomic min/max).
+__device__ __forceinline__ unsigned long long ordered_bits(double d) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double from_ordered_bits(unsigned long long b) {
+  b = (b >> 63) ? (b & 0x7FFFFFFFFFFFFFFFull) : ~b;
+  return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ int grid_cell_x(const Grid& g, double x) {
+  int c = (int)floor(__dmul_rn(__dsub_rn(x, g.x0), g.inv_cs));
+  return c < 0 ? 0 : (c >= g.nx ? g.nx - 1 : c);
+}
+__device__ __forceinline__ int grid_cell_y(const Grid& g, double y) {
+  int c = (int)floor(__dmul_rn(__dsub_rn(y, g.y0), g.inv_cs));
+  return c < 0 ? 0 : (c >= g.ny ? g.ny - 1 : c);
+}
+
+// ---- launch helpers (host) -----------------------------------------------
+
+int persistent_blocks(int block_threads, int per_sm);
+int sm_count();
+// Counts kernel launches of the library (vrm_launch_count).
+void note_launch();
+long long launch_count();
+
+// vrm_grid.cu
+// Builds the cell grid over n particles: bbox, cell size (>= Rh (1+1e-6),
+// doubled while the cell count exceeds ncell_cap), keys, exclusive scan of
+// the cell counts (cell_start, ncell_cap + 1 entries), sorted positions and
+// indices.  Grid g is written on the device.
+cudaError_t grid_build(const double* x, const double* y, int n, double Rh, int ncell_cap, Grid* g, int* cell_key,
+                       int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy, int* sorted_idx,
+                       unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s);
+// Exclusive scan of n ints into out[0..n] (out[n] = total).
+cudaError_t scan_exclusive_i32(const int* in, int* out, int n, int* tmp, cudaStream_t s);
+// Exclusive scan of n bytes (0/1) into out[0..n].
+cudaError_t scan_exclusive_u8(const uint8_t* in, int* out, int n, int* tmp, cudaStream_t s);
+// list[k] = the k-th index with flag set (ascending); count written to *count
+// (device).  pos is scratch of n+1 ints.
+cudaError_t compact_flags(const uint8_t* flags, int n, int* list, int* count, int* pos, int* tmp, cudaStream_t s);
+size_t scan_tmp_ints(int n);
+
+// vrm_reduce.cu
+cudaError_t reduce_select(const double* gamma, int n, double c_bound, uint8_t* diffused, ReduceState* st,
+                          uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds, cudaStream_t s);
+
+// vrm_search.cu
+cudaError_t search_all(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
+                       const int* sorted_idx, int n, int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small,
+                       DevStats* ds, cudaStream_t s);
+cudaError_t search_masks(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
+                         const int* sorted_idx, const double* x, const double* y, const int* list,
+                         const int* list_count, int cap, uint8_t* mask, cudaStream_t s);
+
+// vrm_insert.cu
+// Open list of round 1: the diffused particles (dlist, ascending) whose
+// segment mask is not full; open[] ascending, *n_open on the device.
+cudaError_t open_list(const int* dlist, const int* dcount, int cap, const uint8_t* mask, uint8_t* flag, int* pos,
+                      int* open, int* n_open, int* scan_tmp, cudaStream_t s);
+// First half of an insertion round: proposals and the conflict rule.
+// acc_pos[n_open] receives the number of accepted points.
+cudaError_t insert_round_accept(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
+                                const int* sorted_idx, const double* x, const double* y, const int* open,
+                                int n_open, const uint8_t* mask, uint8_t* cand, uint8_t* acc, int* acc_count,
+                                int* acc_pos, int* scan_tmp, cudaStream_t s);
+// Second half: append at x[n_cur..], update masks, next open list.
+cudaError_t insert_round_commit(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
+                                const int* sorted_idx, double* x, double* y, int n_cur, const int* open, int n_open,
+                                uint8_t* mask, uint8_t* cand, uint8_t* acc, const int* acc_pos, int* open_next,
+                                uint8_t* keep_flag, int* keep_pos, int* n_next, int* scan_tmp, cudaStream_t s);
+cudaError_t count_open_segments(const int* open, int n_open, const uint8_t* mask, int* out, cudaStream_t s);
+
+// vrm_lp.cu
+cudaError_t lp_small(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
+                     int cap, const int* small, int* cols, double* f, double* fii, uint8_t* status, int* fail_list,
+                     DevStats* ds, double dt, cudaStream_t s);
+cudaError_t lp_full(const Consts& c, const double* x, const double* y, const int* fail_list, const int* fail_count,
+                    int cap, const int* nbr_count, const int* nbr_idx, int* cols, double* f, double* fii,
+                    uint8_t* status, DevStats* ds, double dt, cudaStream_t s);
+cudaError_t lp_clear(int n, const uint8_t* diffused, int* cols, double* f, double* fii, uint8_t* status,
+                     cudaStream_t s);
+
+// vrm_apply.cu
+cudaError_t apply_gather(const Consts& c, int n, int n_gamma, const double* gamma, const uint8_t* diffused,
+                         const int* nbr_count, const int* nbr_idx, const int* cols, const double* f, const double* fii,
+                         const int* order, double* dgamma, double* gamma_out, double dt, cudaStream_t s);
+
+}  // namespace vrm

@@ -1,0 +1,549 @@
+// Redistribution weights: phase-I simplex per diffused particle (Sec. 2 Eq.
+// momcondmv, Sec. 4.1, small neighbourhoods Sec. 4.3).
+//
+// The LP  V f = b, f >= 0  has m = 5 rows (1,0) (0,1) (2,0) (1,1) (0,2) in
+// xi = r_ij / h and b = (0,0,2,0,2).  Phase I minimises the sum of m
+// artificials; they start the basis and, once they leave, never re-enter.
+// Rules (identical to the FP64 oracle, which solves the basis systems by LU
+// every iteration while this code updates a tableau):
+//   entering: lowest column with reduced cost < -1e-12 (Bland);
+//   leaving:  minimum ratio over pivot elements > 1e-12; ratios within
+//             1e-12 max(1, min) tie, the tie goes to the basic variable of
+//             lowest index (artificials 0..4 before structurals 5..);
+//   at most 64 pivots; feasible iff the phase-I objective <= 1e-10 and
+//   max |V f - b| <= 1e-10; basic values <= 1e-11 are zeros.
+//
+// GB300 has about 1/60 of its FP32 rate in FP64, and every FP64 instruction
+// of a warp costs the same whether its lanes are busy or not.  The small
+// neighbourhood LP therefore runs one particle per thread with the 5 x 8
+// tableau in registers: every FP64 lane-operation does useful work, and
+// pivot row/column selections are register selects on the integer pipes.
+// The rare full-neighbourhood retry runs one particle per warp, one tableau
+// column per lane (K <= 32), with the pivot column broadcast by shuffles.
+#include <climits>
+
+#include "vrm_internal.cuh"
+
+namespace vrm {
+
+constexpr double kTolPrice = 1e-12;
+constexpr double kTolPivot = 1e-12;
+constexpr double kTolTie = 1e-12;
+constexpr double kTolPhase1 = 1e-10;
+constexpr double kTolSnap = 1e-11;
+constexpr double kTolResid = 1e-10;
+constexpr int kPivotCap = 64;
+constexpr int kM = 5;
+
+__device__ __forceinline__ void cswap(double* d2, int* j, double* a, double* b, int p, int q) {
+  bool sw = (d2[q] < d2[p]) || (d2[q] == d2[p] && j[q] < j[p]);
+  double t0 = sw ? d2[q] : d2[p], t1 = sw ? d2[p] : d2[q];
+  d2[p] = t0;
+  d2[q] = t1;
+  int u0 = sw ? j[q] : j[p], u1 = sw ? j[p] : j[q];
+  j[p] = u0;
+  j[q] = u1;
+  double v0 = sw ? a[q] : a[p], v1 = sw ? a[p] : a[q];
+  a[p] = v0;
+  a[q] = v1;
+  double w0 = sw ? b[q] : b[p], w1 = sw ? b[p] : b[q];
+  b[p] = w0;
+  b[q] = w1;
+}
+
+// Batcher odd-even merge sort of 8 (d2, j) keys with two payloads.
+__device__ __forceinline__ void sort8(double* d2, int* j, double* a, double* b) {
+  cswap(d2, j, a, b, 0, 1); cswap(d2, j, a, b, 2, 3); cswap(d2, j, a, b, 4, 5); cswap(d2, j, a, b, 6, 7);
+  cswap(d2, j, a, b, 0, 2); cswap(d2, j, a, b, 1, 3); cswap(d2, j, a, b, 4, 6); cswap(d2, j, a, b, 5, 7);
+  cswap(d2, j, a, b, 1, 2); cswap(d2, j, a, b, 5, 6);
+  cswap(d2, j, a, b, 0, 4); cswap(d2, j, a, b, 1, 5); cswap(d2, j, a, b, 2, 6); cswap(d2, j, a, b, 3, 7);
+  cswap(d2, j, a, b, 2, 4); cswap(d2, j, a, b, 3, 5);
+  cswap(d2, j, a, b, 1, 2); cswap(d2, j, a, b, 3, 4); cswap(d2, j, a, b, 5, 6);
+}
+
+__device__ __forceinline__ void vcol(double xi, double eta, double* v) {
+  v[0] = xi;
+  v[1] = eta;
+  v[2] = __dmul_rn(xi, xi);
+  v[3] = __dmul_rn(xi, eta);
+  v[4] = __dmul_rn(eta, eta);
+}
+
+__device__ __forceinline__ double b_of(int r) { return (r == 2 || r == 4) ? 2.0 : 0.0; }
+
+struct WarpStats {
+  int ok, none, maxpiv;
+  double maxratio;
+};
+
+__device__ __forceinline__ void flush_stats(DevStats* ds, int ok, int none, int maxpiv, double maxratio, bool full,
+                                            int solved, int pivots) {
+  solved = __reduce_add_sync(0xffffffffu, solved);
+  pivots = __reduce_add_sync(0xffffffffu, pivots);
+  ok = __reduce_add_sync(0xffffffffu, ok);
+  none = __reduce_add_sync(0xffffffffu, none);
+  maxpiv = __reduce_max_sync(0xffffffffu, maxpiv);
+  unsigned long long rb = (unsigned long long)__double_as_longlong(maxratio);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long t = __shfl_xor_sync(0xffffffffu, rb, o);
+    rb = t > rb ? t : rb;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (ok) atomicAdd(full ? &ds->full_ok : &ds->small_ok, ok);
+    if (none) atomicAdd(&ds->no_stencil, none);
+    if (maxpiv) atomicMax(&ds->max_pivots, maxpiv);
+    if (rb) atomicMax(&ds->max_dt_ratio_bits, rb);
+    if (solved) atomicAdd(full ? &ds->lp_full_solved : &ds->lp_small_solved, solved);
+    if (pivots) atomicAdd(full ? &ds->lp_full_pivots : &ds->lp_small_pivots, (unsigned long long)pivots);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __restrict__ x,
+                                                  const double* __restrict__ y, const int* __restrict__ list,
+                                                  const int* __restrict__ list_count, const int* __restrict__ small,
+                                                  int* __restrict__ cols, double* __restrict__ f,
+                                                  double* __restrict__ fii, uint8_t* __restrict__ status,
+                                                  int* __restrict__ fail_list, DevStats* __restrict__ ds,
+                                                  double nu_dt) {
+  const int m = *list_count;
+  const double inv_h2 = 1.0 / (c.h * c.h);
+  int st_ok = 0, st_none = 0, st_maxpiv = 0, st_solved = 0, st_pivots = 0;
+  double st_ratio = 0.0;
+  // grid-stride over whole warps so that the warp-level statistics below run converged
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long base = (long)blockIdx.x * blockDim.x; base < m; base += stride) {
+    const long t = base + threadIdx.x;
+    if (t < m) {
+      const int i = list[t];
+      const double xi0 = x[i], yi0 = y[i];
+      const int4 s0 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[0];
+      const int4 s1 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[1];
+      int cj[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+      double cd2[8], cxi[8], ceta[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (cj[k] >= 0) {
+          const double dx = __dsub_rn(x[cj[k]], xi0), dy = __dsub_rn(y[cj[k]], yi0);
+          cd2[k] = dist2(dx, dy);
+          cxi[k] = dx;
+          ceta[k] = dy;
+        } else {
+          cd2[k] = 1e300;
+          cj[k] = INT_MAX;
+          cxi[k] = 0.0;
+          ceta[k] = 0.0;
+        }
+      }
+      sort8(cd2, cj, cxi, ceta);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        cxi[k] = __dmul_rn(cxi[k], c.inv_h);
+        ceta[k] = __dmul_rn(ceta[k], c.inv_h);
+      }
+      // tableau: T[r][k] = (B^-1 V)_rk, rhs = B^-1 b, d = reduced costs, w = objective
+      double T[kM][8], rhs[kM], d[8], w = 4.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        double v[kM];
+        vcol(cxi[k], ceta[k], v);
+        double s = 0.0;
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          T[r][k] = v[r];
+          s = __dadd_rn(s, v[r]);
+        }
+        d[k] = 0.0 - s;
+      }
+#pragma unroll
+      for (int r = 0; r < kM; ++r) rhs[r] = b_of(r);
+      int basis[kM] = {0, 1, 2, 3, 4};
+      unsigned basic = 0;
+      int it = 0, code = 0;
+      for (;;) {
+        int q = -1;
+#pragma unroll
+        for (int k = 7; k >= 0; --k)
+          if (!((basic >> k) & 1u) && d[k] < -kTolPrice) q = k;
+        if (q < 0) break;
+        if (it == kPivotCap) {
+          code = 2;
+          break;
+        }
+        double a[kM];
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          double v = T[r][0];
+#pragma unroll
+          for (int k = 1; k < 8; ++k) v = (q == k) ? T[r][k] : v;
+          a[r] = v;
+        }
+        double ratio[kM], theta = 1e308;
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          ratio[r] = a[r] > kTolPivot ? __ddiv_rn(rhs[r], a[r]) : 1e308;
+          if (a[r] > kTolPivot) {
+            any = true;
+            theta = ratio[r] < theta ? ratio[r] : theta;
+          }
+        }
+        if (!any) {
+          code = 2;
+          break;
+        }
+        const double lim = theta + kTolTie * (theta > 1.0 ? theta : 1.0);
+        int leave = -1, lbas = INT_MAX;
+#pragma unroll
+        for (int r = 0; r < kM; ++r)
+          if (a[r] > kTolPivot && ratio[r] <= lim && basis[r] < lbas) {
+            leave = r;
+            lbas = basis[r];
+          }
+        double piv = a[0], prhs_raw = rhs[0];
+#pragma unroll
+        for (int r = 1; r < kM; ++r) {
+          piv = (leave == r) ? a[r] : piv;
+          prhs_raw = (leave == r) ? rhs[r] : prhs_raw;
+        }
+        const double rcp = __drcp_rn(piv);
+        double prow[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          double v = T[0][k];
+#pragma unroll
+          for (int r = 1; r < kM; ++r) v = (leave == r) ? T[r][k] : v;
+          prow[k] = (k == q) ? 1.0 : __dmul_rn(v, rcp);
+        }
+        const double prhs = __dmul_rn(prhs_raw, rcp);
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          const bool lr = (leave == r);
+          const double ar = lr ? 0.0 : a[r];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const double u = __fma_rn(-ar, prow[k], T[r][k]);
+            T[r][k] = lr ? prow[k] : ((k == q) ? 0.0 : u);
+          }
+          const double ur = __fma_rn(-ar, prhs, rhs[r]);
+          rhs[r] = lr ? prhs : ur;
+        }
+        double dq = d[0];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) dq = (q == k) ? d[k] : dq;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) d[k] = (k == q) ? 0.0 : __fma_rn(-dq, prow[k], d[k]);
+        w = __fma_rn(-dq, prhs, w);
+        if (lbas >= kM) basic &= ~(1u << (lbas - kM));
+        basic |= 1u << q;
+#pragma unroll
+        for (int r = 0; r < kM; ++r) basis[r] = (leave == r) ? kM + q : basis[r];
+        ++it;
+      }
+      // basic solution, snapped, and its residual
+      double fv[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) fv[k] = 0.0;
+      double wsum = 0.0;
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        if (basis[r] < kM) {
+          wsum = __dadd_rn(wsum, rhs[r]);
+        } else {
+          const double v = rhs[r] > kTolSnap ? rhs[r] : 0.0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == kM + k) ? v : fv[k];
+        }
+      }
+      double rmax = 0.0;
+      {
+        double acc[kM] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          double v[kM];
+          vcol(cxi[k], ceta[k], v);
+#pragma unroll
+          for (int r = 0; r < kM; ++r) acc[r] = __dadd_rn(acc[r], __dmul_rn(v[r], fv[k]));
+        }
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          const double e = fabs(__dsub_rn(acc[r], b_of(r)));
+          rmax = e > rmax ? e : rmax;
+        }
+      }
+      const bool feasible = code == 0 && wsum <= kTolPhase1 && rmax <= kTolResid;
+      st_maxpiv = it > st_maxpiv ? it : st_maxpiv;
+      ++st_solved;
+      st_pivots += it;
+      int* crow = cols + (size_t)i * VRM_STENCIL_W;
+      double* frow = f + (size_t)i * VRM_STENCIL_W;
+      if (feasible) {
+        int slot = 0;
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (fv[k] != 0.0) {
+            crow[slot] = cj[k];
+            frow[slot] = fv[k];
+            ++slot;
+            s = __dadd_rn(s, fv[k]);
+          }
+        for (int k = slot; k < VRM_STENCIL_W; ++k) {
+          crow[k] = -1;
+          frow[k] = 0.0;
+        }
+        fii[i] = -s;
+        status[i] = VRM_LP_SMALL;
+        ++st_ok;
+        const double q = __dmul_rn(__dmul_rn(nu_dt, s), inv_h2);
+        st_ratio = q > st_ratio ? q : st_ratio;
+      } else if (c.fallback) {
+        fail_list[atomicAdd(&ds->n_fail, 1)] = i;
+      } else {
+        for (int k = 0; k < VRM_STENCIL_W; ++k) {
+          crow[k] = -1;
+          frow[k] = 0.0;
+        }
+        fii[i] = 0.0;
+        status[i] = VRM_LP_NONE;
+        ++st_none;
+      }
+    }
+  }
+  flush_stats(ds, st_ok, st_none, st_maxpiv, st_ratio, false, st_solved, st_pivots);
+}
+
+// Full-neighbourhood retry: one warp per particle, lane l holds column l.
+__global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restrict__ x,
+                                                 const double* __restrict__ y, const int* __restrict__ fail_list,
+                                                 const int* __restrict__ fail_count,
+                                                 const int* __restrict__ nbr_count, const int* __restrict__ nbr_idx,
+                                                 int* __restrict__ cols, double* __restrict__ f,
+                                                 double* __restrict__ fii, uint8_t* __restrict__ status,
+                                                 DevStats* __restrict__ ds, double nu_dt) {
+  const int lane = threadIdx.x & 31;
+  const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
+  const int m = *fail_count;
+  const double inv_h2 = 1.0 / (c.h * c.h);
+  int st_ok = 0, st_none = 0, st_maxpiv = 0, st_solved = 0, st_pivots = 0;
+  double st_ratio = 0.0;
+  for (long t = warp; t < m; t += nwarps) {
+    const int i = fail_list[t];
+    const int cnt = nbr_count[i];
+    const int K = cnt < c.k_cap ? cnt : c.k_cap;
+    const double xi0 = x[i], yi0 = y[i];
+    double d2 = 1e300, dx = 0.0, dy = 0.0;
+    int j = INT_MAX;
+    if (lane < K) {
+      j = nbr_idx[(size_t)i * c.k_cap + lane];
+      dx = __dsub_rn(x[j], xi0);
+      dy = __dsub_rn(y[j], yi0);
+      d2 = dist2(dx, dy);
+    }
+    // bitonic sort of (d2, j) across the warp, ascending
+    for (int size = 2; size <= 32; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        const double od2 = __shfl_xor_sync(0xffffffffu, d2, stride);
+        const int oj = __shfl_xor_sync(0xffffffffu, j, stride);
+        const double odx = __shfl_xor_sync(0xffffffffu, dx, stride);
+        const double ody = __shfl_xor_sync(0xffffffffu, dy, stride);
+        const bool up = ((lane & size) == 0);
+        const bool lower = ((lane & stride) == 0);
+        const bool other_less = (od2 < d2) || (od2 == d2 && oj < j);
+        const bool take = (lower == up) ? other_less : !other_less && !(od2 == d2 && oj == j);
+        if (take) {
+          d2 = od2;
+          j = oj;
+          dx = odx;
+          dy = ody;
+        }
+      }
+    }
+    const double cxi = __dmul_rn(dx, c.inv_h), ceta = __dmul_rn(dy, c.inv_h);
+    double T[kM], v[kM];
+    vcol(cxi, ceta, v);
+    double s = 0.0;
+#pragma unroll
+    for (int r = 0; r < kM; ++r) {
+      T[r] = v[r];
+      s = __dadd_rn(s, v[r]);
+    }
+    double d = 0.0 - s;
+    double rhs[kM], w = 4.0;
+#pragma unroll
+    for (int r = 0; r < kM; ++r) rhs[r] = b_of(r);
+    int basis[kM] = {0, 1, 2, 3, 4};
+    bool isb = false;
+    int it = 0, code = 0;
+    for (;;) {
+      const unsigned cand = __ballot_sync(0xffffffffu, lane < K && !isb && d < -kTolPrice);
+      if (!cand) break;
+      if (it == kPivotCap) {
+        code = 2;
+        break;
+      }
+      const int q = __ffs(cand) - 1;
+      double a[kM];
+#pragma unroll
+      for (int r = 0; r < kM; ++r) a[r] = __shfl_sync(0xffffffffu, T[r], q);
+      double ratio[kM], theta = 1e308;
+      bool any = false;
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        ratio[r] = a[r] > kTolPivot ? __ddiv_rn(rhs[r], a[r]) : 1e308;
+        if (a[r] > kTolPivot) {
+          any = true;
+          theta = ratio[r] < theta ? ratio[r] : theta;
+        }
+      }
+      if (!any) {
+        code = 2;
+        break;
+      }
+      const double lim = theta + kTolTie * (theta > 1.0 ? theta : 1.0);
+      int leave = -1, lbas = INT_MAX;
+#pragma unroll
+      for (int r = 0; r < kM; ++r)
+        if (a[r] > kTolPivot && ratio[r] <= lim && basis[r] < lbas) {
+          leave = r;
+          lbas = basis[r];
+        }
+      double piv = a[0], prhs_raw = rhs[0], prow_raw = T[0];
+#pragma unroll
+      for (int r = 1; r < kM; ++r) {
+        piv = (leave == r) ? a[r] : piv;
+        prhs_raw = (leave == r) ? rhs[r] : prhs_raw;
+        prow_raw = (leave == r) ? T[r] : prow_raw;
+      }
+      const double rcp = __drcp_rn(piv);
+      const double prow = (lane == q) ? 1.0 : __dmul_rn(prow_raw, rcp);
+      const double prhs = __dmul_rn(prhs_raw, rcp);
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        const bool lr = (leave == r);
+        const double ar = lr ? 0.0 : a[r];
+        const double u = __fma_rn(-ar, prow, T[r]);
+        T[r] = lr ? prow : ((lane == q) ? 0.0 : u);
+        const double ur = __fma_rn(-ar, prhs, rhs[r]);
+        rhs[r] = lr ? prhs : ur;
+      }
+      const double dq = __shfl_sync(0xffffffffu, d, q);
+      d = (lane == q) ? 0.0 : __fma_rn(-dq, prow, d);
+      w = __fma_rn(-dq, prhs, w);
+      if (lbas >= kM && lane == lbas - kM) isb = false;
+      if (lane == q) isb = true;
+#pragma unroll
+      for (int r = 0; r < kM; ++r) basis[r] = (leave == r) ? kM + q : basis[r];
+      ++it;
+    }
+    double fv = 0.0, wsum = 0.0;
+#pragma unroll
+    for (int r = 0; r < kM; ++r) {
+      if (basis[r] < kM) wsum = __dadd_rn(wsum, rhs[r]);
+      else if (basis[r] == kM + lane) fv = rhs[r] > kTolSnap ? rhs[r] : 0.0;
+    }
+    double rmax = 0.0;
+#pragma unroll
+    for (int r = 0; r < kM; ++r) {
+      double p = __dmul_rn(v[r], fv);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) p = __dadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
+      const double e = fabs(__dsub_rn(p, b_of(r)));
+      rmax = e > rmax ? e : rmax;
+    }
+    const bool feasible = code == 0 && wsum <= kTolPhase1 && rmax <= kTolResid;
+    int* crow = cols + (size_t)i * VRM_STENCIL_W;
+    double* frow = f + (size_t)i * VRM_STENCIL_W;
+    const unsigned nz = __ballot_sync(0xffffffffu, feasible && fv != 0.0);
+    if (feasible) {
+      const int slot = __popc(nz & ((1u << lane) - 1u));
+      if (fv != 0.0 && slot < VRM_STENCIL_W) {
+        crow[slot] = j;
+        frow[slot] = fv;
+      }
+      const int used = __popc(nz);
+      if (lane >= used && lane < VRM_STENCIL_W) {
+        crow[lane] = -1;
+        frow[lane] = 0.0;
+      }
+      // f~_ii = -sum of the nonzero weights in column order
+      double sacc = 0.0;
+      unsigned rest = nz;
+      while (rest) {
+        const int l = __ffs(rest) - 1;
+        rest &= rest - 1;
+        sacc = __dadd_rn(sacc, __shfl_sync(0xffffffffu, fv, l));
+      }
+      if (lane == 0) {
+        fii[i] = -sacc;
+        status[i] = VRM_LP_FULL;
+        ++st_ok;
+        const double q = __dmul_rn(__dmul_rn(nu_dt, sacc), inv_h2);
+        st_ratio = q > st_ratio ? q : st_ratio;
+      }
+    } else {
+      if (lane < VRM_STENCIL_W) {
+        crow[lane] = -1;
+        frow[lane] = 0.0;
+      }
+      if (lane == 0) {
+        fii[i] = 0.0;
+        status[i] = VRM_LP_NONE;
+        ++st_none;
+      }
+    }
+    st_maxpiv = it > st_maxpiv ? it : st_maxpiv;
+    if (lane == 0) {
+      ++st_solved;
+      st_pivots += it;
+    }
+  }
+  flush_stats(ds, st_ok, st_none, st_maxpiv, st_ratio, true, st_solved, st_pivots);
+}
+
+__global__ void k_lp_clear(int n, const uint8_t* __restrict__ diffused, int* __restrict__ cols,
+                           double* __restrict__ f, double* __restrict__ fii, uint8_t* __restrict__ status) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    if (diffused[i]) continue;
+    for (int k = 0; k < VRM_STENCIL_W; ++k) {
+      cols[i * VRM_STENCIL_W + k] = -1;
+      f[i * VRM_STENCIL_W + k] = 0.0;
+    }
+    fii[i] = 0.0;
+    status[i] = VRM_LP_NOT_DIFFUSED;
+  }
+}
+
+cudaError_t lp_small(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
+                     int cap, const int* small, int* cols, double* f, double* fii, uint8_t* status, int* fail_list,
+                     DevStats* ds, double nu_dt, cudaStream_t s) {
+  if (cap <= 0) return cudaSuccess;
+  int blocks = (cap + 127) / 128;
+  if (blocks > 16 * sm_count()) blocks = 16 * sm_count();
+  k_lp_small<<<blocks, 128, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list, ds, nu_dt); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t lp_full(const Consts& c, const double* x, const double* y, const int* fail_list, const int* fail_count,
+                    int cap, const int* nbr_count, const int* nbr_idx, int* cols, double* f, double* fii,
+                    uint8_t* status, DevStats* ds, double nu_dt, cudaStream_t s) {
+  if (cap <= 0) return cudaSuccess;
+  long warps = cap;
+  long blocks = (warps * 32 + 127) / 128;
+  if (blocks > 4 * sm_count()) blocks = 4 * sm_count();
+  k_lp_full<<<(int)blocks, 128, 0, s>>>(c, x, y, fail_list, fail_count, nbr_count, nbr_idx, cols, f, fii, status, ds,
+                                        nu_dt); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t lp_clear(int n, const uint8_t* diffused, int* cols, double* f, double* fii, uint8_t* status,
+                     cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  int blocks = (n + kBlock - 1) / kBlock;
+  if (blocks > 8 * sm_count()) blocks = 8 * sm_count();
+  k_lp_clear<<<blocks, kBlock, 0, s>>>(n, diffused, cols, f, fii, status); note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace vrm

@@ -1,0 +1,316 @@
+"""GPU parity: every stage of the CUDA library against the FP64 oracle on the
+same seeded inputs, called through the C ABI (ctypes binding).
+
+Bars: neighbour rows, masks, small neighbourhoods, the diffused set and the
+inserted positions bit-exact; LP outcome and stencil columns identical;
+weights within 1e-12 (relative to max(1, |f~|)); dGamma within
+1e-12 * (nu/h^2) sum_i |f~_ij Gamma_i| per element (the scale of the terms
+summed), and bit-exact when both sides use the same weights.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import vrm_inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+W = 8
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1508_06379_gb300 as v
+    v.build()
+    return v
+
+
+def cu(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def clouds():
+    out = []
+    x, y, g = vrm_inputs.random_cloud(900, h=0.05, jitter=0.35, seed=0)
+    out.append(("jitter900", x, y, g, 0.05))
+    x, y, g = vrm_inputs.random_cloud(20000, h=0.01, jitter=0.3, seed=1)
+    out.append(("jitter20k", x, y, g, 0.01))
+    x, y, g = vrm_inputs.uniform_scatter(3000, half_width=1.0, seed=2)
+    out.append(("scatter3k", x, y, g, 0.04))
+    x, y, g = vrm_inputs.lamb_oseen_lattice(0.02, 1.0, 1e-3, 1.0, eps=1e-10)
+    out.append(("lamb_oseen_h002", x, y, g, 0.02))
+    x, y, g = vrm_inputs.lamb_oseen_lattice(1 / 64, 1.0, 1e-3, 1.0, eps=1e-10)
+    out.append(("lamb_oseen_exact", x, y, g, 1 / 64))
+    return out
+
+
+CLOUDS = clouds()
+IDS = [c[0] for c in CLOUDS]
+
+
+def rows_equal(cnt_g, idx_g, nb, k_cap):
+    cnt_o = nb["count"]
+    assert np.array_equal(cnt_g, cnt_o)
+    for i in range(len(cnt_o)):
+        m = min(cnt_o[i], k_cap)
+        if not np.array_equal(idx_g[i, :m], nb["idx"][i, :m]):
+            raise AssertionError("row %d differs: %s vs %s" % (i, idx_g[i, :m], nb["idx"][i, :m]))
+
+
+@pytest.mark.parametrize("case", CLOUDS, ids=IDS)
+def test_neighbourhoods_bit_exact(lib, orc, case):
+    name, x, y, g, h = case
+    n = len(x)
+    ctx = lib.VRM(h=h, nu=1e-3)
+    nb_g = ctx.build_neighbourhoods(cu(x), cu(y), n)
+    nb_o = orc.neighbours(x, y, h, k_cap=32)
+    assert nb_g["max_count"] == nb_o["max_count"]
+    rows_equal(nb_g["count"].cpu().numpy(), nb_g["idx"].cpu().numpy()[: n * 32].reshape(n, 32), nb_o, 32)
+    assert np.array_equal(nb_g["mask"].cpu().numpy(), nb_o["mask"])
+    assert np.array_equal(nb_g["small"].cpu().numpy()[: n * 8].reshape(n, 8), nb_o["small"])
+
+
+def gamma_variants(n, seed):
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal(n) * np.exp(rng.uniform(-25, 0, n))
+    g[::13] = 0.0
+    g[7::29] = -g[3::29][: len(g[7::29])]  # exact ties in |Gamma|
+    return g
+
+
+@pytest.mark.parametrize("c_diff", [1e-3, 1.0, 1e3])
+@pytest.mark.parametrize("case", CLOUDS[:3], ids=IDS[:3])
+def test_growth_control_bit_exact(lib, orc, case, c_diff):
+    name, x, y, g, h = case
+    n = len(x)
+    for gg in (g, gamma_variants(n, 5), np.full(n, 0.25)):
+        ctx = lib.VRM(h=h, nu=1e-3, c_diff=c_diff, max_rounds=0)
+        xb = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
+        yb = torch.zeros(n + 16, dtype=torch.float64, device="cuda")
+        xb[:n] = cu(x)
+        yb[:n] = cu(y)
+        n2, diff, st = ctx.insert_reduce(xb, yb, n, cu(gg))
+        c = orc.constants(h, c_diff=c_diff)
+        d_o = orc.reduce(gg, c["c_bound"])
+        assert np.array_equal(diff.cpu().numpy()[:n], d_o)
+        assert st["n_diffused"] == int(d_o.sum())
+
+
+@pytest.mark.parametrize("case", CLOUDS, ids=IDS)
+def test_insertion_bit_exact(lib, orc, case):
+    name, x, y, g, h = case
+    n = len(x)
+    c = orc.constants(h)
+    d_o = orc.reduce(g, c["c_bound"])
+    x2, y2, rounds, open_ = orc.insert(x, y, d_o, h)
+    cap = len(x2) + 64
+    ctx = lib.VRM(h=h, nu=1e-3)
+    xb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    yb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    xb[:n] = cu(x)
+    yb[:n] = cu(y)
+    n2, diff, st = ctx.insert_reduce(xb, yb, n, cu(g))
+    assert n2 == len(x2)
+    assert st["rounds"] == rounds and st["open_segments"] == open_
+    assert np.array_equal(xb.cpu().numpy()[:n2], x2)
+    assert np.array_equal(yb.cpu().numpy()[:n2], y2)
+    assert not diff.cpu().numpy()[n:n2].any()
+
+
+def test_insertion_single_particle_and_rounds(lib, orc):
+    h = 0.1
+    ctx = lib.VRM(h=h, nu=1e-2)
+    xb = torch.zeros(64, dtype=torch.float64, device="cuda")
+    yb = torch.zeros(64, dtype=torch.float64, device="cuda")
+    xb[0], yb[0] = 0.3, -0.2
+    n2, diff, st = ctx.insert_reduce(xb, yb, 1, cu(np.array([1.0])))
+    x2, y2, rounds, _ = orc.insert(np.array([0.3]), np.array([-0.2]), np.array([1], np.uint8), h)
+    assert n2 == 9 and np.array_equal(xb.cpu().numpy()[:9], x2) and np.array_equal(yb.cpu().numpy()[:9], y2)
+    # scattered cloud: several rounds
+    x, y, g = vrm_inputs.uniform_scatter(400, half_width=0.4, seed=11)
+    c = orc.constants(0.05)
+    d_o = orc.reduce(g, c["c_bound"])
+    for mr in (1, 2, 16):
+        x2, y2, rounds, open_ = orc.insert(x, y, d_o, 0.05, max_rounds=mr)
+        ctx = lib.VRM(h=0.05, nu=1e-2, max_rounds=mr)
+        cap = len(x2) + 8
+        xb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        yb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        xb[:400] = cu(x)
+        yb[:400] = cu(y)
+        n2, diff, st = ctx.insert_reduce(xb, yb, 400, cu(g))
+        assert n2 == len(x2) and st["open_segments"] == open_ and st["rounds"] == rounds
+        assert np.array_equal(xb.cpu().numpy()[:n2], x2)
+
+
+def weights_equal(w_g, w_o, n, rel=1e-12):
+    st_g = w_g["status"].cpu().numpy()[:n]
+    assert np.array_equal(st_g, w_o["status"]), np.nonzero(st_g != w_o["status"])[0][:10]
+    cols_g = w_g["cols"].cpu().numpy()[: n * W].reshape(n, W)
+    assert np.array_equal(cols_g, w_o["cols"]), np.nonzero((cols_g != w_o["cols"]).any(1))[0][:10]
+    f_g = w_g["f"].cpu().numpy()[: n * W].reshape(n, W)
+    assert np.all(np.abs(f_g - w_o["f"]) <= rel * np.maximum(1.0, np.abs(w_o["f"])))
+    fii_g = w_g["fii"].cpu().numpy()[:n]
+    assert np.all(np.abs(fii_g - w_o["fii"]) <= rel * np.maximum(1.0, np.abs(w_o["fii"])))
+
+
+@pytest.mark.parametrize("case", CLOUDS, ids=IDS)
+def test_weights_match_oracle(lib, orc, case):
+    name, x, y, g, h = case
+    p = orc.pipeline(x, y, g, h, 1e-3)
+    X, Y, D, nb = p["x"], p["y"], p["diffused"], p["nb"]
+    n = len(X)
+    ctx = lib.VRM(h=h, nu=1e-3)
+    nbt = dict(count=cu(nb["count"]), idx=cu(nb["idx"].reshape(-1)), small=cu(nb["small"].reshape(-1)))
+    w_g = ctx.solve_weights(cu(X), cu(Y), n, cu(D), nbt)
+    weights_equal(w_g, p["w"], n)
+    st = w_g["stats"]
+    assert st["small_ok"] == int(np.sum(p["w"]["status"] == 1))
+    assert st["full_ok"] == int(np.sum(p["w"]["status"] == 2))
+
+
+def dgamma_scale(n, gamma, diffused, w, nu_over_h2):
+    s = np.zeros(n)
+    ng = len(gamma)
+    for i in range(ng):
+        if not diffused[i]:
+            continue
+        for t in range(W):
+            j = w["cols"][i, t]
+            if j >= 0:
+                s[j] += abs(w["f"][i, t] * gamma[i])
+        s[i] += abs(w["fii"][i] * gamma[i])
+    return nu_over_h2 * s
+
+
+@pytest.mark.parametrize("case", CLOUDS, ids=IDS)
+def test_apply_bit_exact_given_weights(lib, orc, case):
+    name, x, y, g, h = case
+    nu = 1e-3
+    p = orc.pipeline(x, y, g, h, nu)
+    X, D, nb, w = p["x"], p["diffused"], p["nb"], p["w"]
+    n = len(X)
+    ctx = lib.VRM(h=h, nu=nu)
+    nbt = dict(count=cu(nb["count"]), idx=cu(nb["idx"].reshape(-1)))
+    wt = dict(cols=cu(w["cols"].reshape(-1)), f=cu(w["f"].reshape(-1)), fii=cu(w["fii"]))
+    dg = ctx.apply(n, len(g), cu(g), cu(D), nbt, wt).cpu().numpy()[:n]
+    assert np.array_equal(dg, p["dgamma"])
+
+
+@pytest.mark.parametrize("case", CLOUDS, ids=IDS)
+def test_step_matches_oracle(lib, orc, case):
+    name, x, y, g, h = case
+    nu = 1e-3
+    dt = 0.25 * h * h / nu
+    x2, y2, g2, st_o = orc.step(x, y, g, h, nu, dt)
+    n = len(x)
+    cap = len(x2) + 128
+    ctx = lib.VRM(h=h, nu=nu)
+    xb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    yb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    xb[:n] = cu(x)
+    yb[:n] = cu(y)
+    go = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    gi = cu(g)
+    n2, st = ctx.step(xb, yb, n, gi, go, dt)
+    assert n2 == len(x2)
+    assert np.array_equal(xb.cpu().numpy()[:n2], x2) and np.array_equal(yb.cpu().numpy()[:n2], y2)
+    for k in ("n_diffused", "n_inserted", "small_ok", "full_ok", "no_stencil", "rounds", "open_segments"):
+        assert st[k] == st_o[k], (k, st[k], st_o[k])
+    p = orc.pipeline(x, y, g, h, nu)
+    scale = dgamma_scale(n2, g, p["diffused"], p["w"], p["const"]["nu_over_h2"]) * dt
+    got = go.cpu().numpy()[:n2]
+    err = np.abs(got - g2)
+    tol = 1e-12 * scale + 4 * np.spacing(np.abs(g2))
+    assert np.all(err <= tol), (np.max(err / np.maximum(tol, 1e-300)))
+    # repeating the call with the same inputs gives the same outputs
+    go2 = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    n3, _ = ctx.step(xb, yb, n, gi, go2, dt)
+    assert n3 == n2 and torch.equal(go, go2)
+
+
+def test_lamb_oseen_ten_euler_steps(lib, orc):
+    # one operator evaluation plus 10 Euler steps with dt = 0.25 h^2/nu on the
+    # h = 0.02 Lamb-Oseen lattice (Gamma = 1, nu = 1e-3, t0 = 1): each GPU step
+    # is checked against the oracle step from the same state
+    h, nu = 0.02, 1e-3
+    x, y, g = vrm_inputs.lamb_oseen_lattice(h, 1.0, nu, 1.0, eps=1e-10)
+    dt = 0.25 * h * h / nu
+    ctx = lib.VRM(h=h, nu=nu)
+    cap = 4 * len(x) + 1024
+    for it in range(11):
+        x2, y2, g2, st_o = orc.step(x, y, g, h, nu, dt if it else 0.0)
+        n = len(x)
+        xb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        yb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        xb[:n] = cu(x)
+        yb[:n] = cu(y)
+        go = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        n2, st = ctx.step(xb, yb, n, cu(g), go, dt if it else 0.0)
+        assert n2 == len(x2)
+        assert np.array_equal(xb.cpu().numpy()[:n2], x2)
+        got = go.cpu().numpy()[:n2]
+        assert np.max(np.abs(got - g2)) <= 1e-12 * np.abs(g).sum() + 1e-300
+        x, y, g = x2, y2, g2
+    # circulation conserved through the run
+    assert abs(g.sum() - vrm_inputs.lamb_oseen_lattice(h, 1.0, nu, 1.0, eps=1e-10)[2].sum()) < 1e-12
+
+
+def test_edge_cases(lib, orc):
+    v = lib
+    ctx = v.VRM(h=0.1, nu=1e-2)
+    e = torch.zeros(16, dtype=torch.float64, device="cuda")
+    # empty cloud
+    n2, st = ctx.step(e.clone(), e.clone(), 0, e[:0], torch.zeros(16, dtype=torch.float64, device="cuda"), 0.1)
+    assert n2 == 0
+    # all-zero circulation: nothing diffuses, nothing is inserted, Gamma stays 0
+    x, y, _ = vrm_inputs.random_cloud(100, h=0.1, seed=3)
+    cap = 256
+    xb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    yb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    xb[:100] = cu(x)
+    yb[:100] = cu(y)
+    go = torch.ones(cap, dtype=torch.float64, device="cuda")
+    n2, st = ctx.step(xb, yb, 100, torch.zeros(100, dtype=torch.float64, device="cuda"), go, 0.1)
+    assert n2 == 100 and st["n_diffused"] == 0 and torch.count_nonzero(go[:100]) == 0
+    # NaN input is an argument error, not a fault
+    g = torch.ones(100, dtype=torch.float64, device="cuda")
+    g[5] = float("nan")
+    with pytest.raises(v.VRMError) as ei:
+        ctx.step(xb, yb, 100, g, go, 0.1)
+    assert ei.value.status == v.VRM_ERR_ARG
+    xn = xb.clone()
+    xn[3] = float("inf")
+    with pytest.raises(v.VRMError) as ei:
+        ctx.step(xn, yb, 100, torch.ones(100, dtype=torch.float64, device="cuda"), go, 0.1)
+    assert ei.value.status == v.VRM_ERR_ARG
+    # capacity too small for the inserted particles
+    small_cap = torch.zeros(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(v.VRMError) as ei:
+        ctx.step(small_cap.clone(), small_cap.clone(), 1, torch.ones(1, dtype=torch.float64, device="cuda"),
+                 torch.zeros(3, dtype=torch.float64, device="cuda"), 0.1)
+    assert ei.value.status == v.VRM_ERR_CAPACITY
+    # the context stays usable after errors
+    go = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    n2, st = ctx.step(xb, yb, 100, torch.ones(100, dtype=torch.float64, device="cuda") * 1e-3, go, 0.0)
+    assert n2 >= 100
+    # a dense cluster overflows k_cap rows: capacity error with the width needed
+    rng = np.random.default_rng(0)
+    xc = rng.uniform(0, 0.15, 60)
+    yc = rng.uniform(0, 0.15, 60)
+    ctx2 = v.VRM(h=0.1, nu=1e-2, k_cap=8)
+    with pytest.raises(v.VRMError) as ei:
+        ctx2.build_neighbourhoods(cu(xc), cu(yc), 60)
+    assert ei.value.status == v.VRM_ERR_CAPACITY
+    # bad parameters
+    with pytest.raises(v.VRMError):
+        v.VRM(h=-1.0, nu=1.0)
+    with pytest.raises(v.VRMError):
+        v.VRM(h=0.1, nu=1.0, k_cap=64)
