@@ -86,12 +86,12 @@ class Clocks:
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
              "clocks_event_reasons.sw_power_cap"
 
-    def __init__(self, bus_id=None):
+    def __init__(self, gpu_id=None):
         self.proc = None
         self.lines = []
         cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
-        if bus_id:
-            cmd += ["-i", bus_id]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
         try:
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
@@ -176,12 +176,12 @@ def run_ours(args):
         flush.zero_()
         ctx.step(xb, yb, n, gi, go, dt)
     torch.cuda.synchronize()
-    bus = None
+    gpu_id = None
     try:
-        bus = torch.cuda.get_device_properties(local).pci_bus_id
+        gpu_id = "GPU-%s" % torch.cuda.get_device_properties(local).uuid
     except Exception:
-        bus = None
-    clocks = Clocks(bus if isinstance(bus, str) else None)
+        gpu_id = None
+    clocks = Clocks(gpu_id)
     time.sleep(0.5)
     if dist:
         dist.barrier()
@@ -227,7 +227,7 @@ def run_ours(args):
     xo_h = torch.empty(cap, dtype=torch.float64).pin_memory()
     yo_h = torch.empty(cap, dtype=torch.float64).pin_memory()
     e2e_ms, e2e_parts, h2d, d2h = 0.0, 0, 0, 0
-    e2e_steps = max(1, min(args.steps, 10))
+    e2e_steps = max(1, min(args.steps, 5))
     for _ in range(e2e_steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)

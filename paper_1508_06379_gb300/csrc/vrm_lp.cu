@@ -160,7 +160,12 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
       int basis[kM] = {0, 1, 2, 3, 4};
       unsigned basic = 0;
       int it = 0, code = 0;
+      int n_art = kM;  // artificials in the basis
       for (;;) {
+        // with no artificial left the phase-I costs of the basis are zero, so
+        // every reduced cost is exactly zero: phase I is over (the updated
+        // cost row only holds rounding noise then)
+        if (n_art == 0) break;
         int q = -1;
 #pragma unroll
         for (int k = 7; k >= 0; --k)
@@ -235,6 +240,7 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         for (int k = 0; k < 8; ++k) d[k] = (k == q) ? 0.0 : __fma_rn(-dq, prow[k], d[k]);
         w = __fma_rn(-dq, prhs, w);
         if (lbas >= kM) basic &= ~(1u << (lbas - kM));
+        else --n_art;
         basic |= 1u << q;
 #pragma unroll
         for (int r = 0; r < kM; ++r) basis[r] = (leave == r) ? kM + q : basis[r];
@@ -376,7 +382,9 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
     int basis[kM] = {0, 1, 2, 3, 4};
     bool isb = false;
     int it = 0, code = 0;
+    int n_art = kM;
     for (;;) {
+      if (n_art == 0) break;  // phase I over: every reduced cost is zero
       const unsigned cand = __ballot_sync(0xffffffffu, lane < K && !isb && d < -kTolPrice);
       if (!cand) break;
       if (it == kPivotCap) {
@@ -432,6 +440,7 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
       d = (lane == q) ? 0.0 : __fma_rn(-dq, prow, d);
       w = __fma_rn(-dq, prhs, w);
       if (lbas >= kM && lane == lbas - kM) isb = false;
+      if (lbas < kM) --n_art;
       if (lane == q) isb = true;
 #pragma unroll
       for (int r = 0; r < kM; ++r) basis[r] = (leave == r) ? kM + q : basis[r];
