@@ -504,8 +504,10 @@ void orc_rhs(int order, double* b) {
 }
 
 /* LU factorisation with partial pivoting of the m x m matrix A (row-major),
-   in place; piv[k] = row swapped with k.  Returns 0 if singular. */
-static int lu_factor(int m, double* A, int* piv) {
+   in place; piv[k] = row swapped with k (first row of largest |A[r][k]|),
+   rcp[k] = 1 / U[k][k].  The multipliers are A[r][k] * rcp[k].
+   Returns 0 if singular. */
+static int lu_factor(int m, double* A, int* piv, double* rcp) {
   for (int k = 0; k < m; ++k) {
     int p = k;
     double best = fabs(A[k * m + k]);
@@ -522,17 +524,18 @@ static int lu_factor(int m, double* A, int* piv) {
         A[k * m + c] = A[p * m + c];
         A[p * m + c] = t;
       }
+    rcp[k] = 1.0 / A[k * m + k];
     for (int r = k + 1; r < m; ++r) {
-      double l = A[r * m + k] / A[k * m + k];
+      double l = A[r * m + k] * rcp[k];
       A[r * m + k] = l;
-      for (int c = k + 1; c < m; ++c) A[r * m + c] -= l * A[k * m + c];
+      for (int c = k + 1; c < m; ++c) A[r * m + c] = A[r * m + c] - l * A[k * m + c];
     }
   }
   return 1;
 }
 
 /* Solve A z = rhs with the factors of lu_factor (z overwrites rhs). */
-static void lu_solve(int m, const double* LU, const int* piv, double* z) {
+static void lu_solve(int m, const double* LU, const int* piv, const double* rcp, double* z) {
   for (int k = 0; k < m; ++k)
     if (piv[k] != k) {
       double t = z[k];
@@ -540,22 +543,22 @@ static void lu_solve(int m, const double* LU, const int* piv, double* z) {
       z[piv[k]] = t;
     }
   for (int r = 1; r < m; ++r)
-    for (int c = 0; c < r; ++c) z[r] -= LU[r * m + c] * z[c];
+    for (int c = 0; c < r; ++c) z[r] = z[r] - LU[r * m + c] * z[c];
   for (int r = m - 1; r >= 0; --r) {
-    for (int c = r + 1; c < m; ++c) z[r] -= LU[r * m + c] * z[c];
-    z[r] /= LU[r * m + r];
+    for (int c = r + 1; c < m; ++c) z[r] = z[r] - LU[r * m + c] * z[c];
+    z[r] = z[r] * rcp[r];
   }
 }
 
 /* Solve A^T z = rhs with the factors of lu_factor (P A = L U, so
    A^T = U^T L^T P). */
-static void lu_solve_transposed(int m, const double* LU, const int* piv, double* z) {
+static void lu_solve_transposed(int m, const double* LU, const int* piv, const double* rcp, double* z) {
   for (int r = 0; r < m; ++r) {
-    for (int c = 0; c < r; ++c) z[r] -= LU[c * m + r] * z[c];
-    z[r] /= LU[r * m + r];
+    for (int c = 0; c < r; ++c) z[r] = z[r] - LU[c * m + r] * z[c];
+    z[r] = z[r] * rcp[r];
   }
   for (int r = m - 1; r >= 0; --r)
-    for (int c = r + 1; c < m; ++c) z[r] -= LU[c * m + r] * z[c];
+    for (int c = r + 1; c < m; ++c) z[r] = z[r] - LU[c * m + r] * z[c];
   for (int k = m - 1; k >= 0; --k)
     if (piv[k] != k) {
       double t = z[k];
@@ -585,7 +588,7 @@ static void lu_solve_transposed(int m, const double* LU, const int* piv, double*
  */
 int orc_phase1(int m, int K, const double* V, const double* b, double* f, int* npiv, double* resid) {
   int basis[9];
-  double B[81], xB[9], y[9], d[9];
+  double B[81], xB[9], y[9], d[9], rcp[9];
   int piv[9];
   for (int k = 0; k < m; ++k) basis[k] = k;
   int it = 0, status = 0;
@@ -596,14 +599,14 @@ int orc_phase1(int m, int K, const double* V, const double* b, double* f, int* n
         int v = basis[k];
         B[r * m + k] = v < m ? (r == v ? 1.0 : 0.0) : V[r * K + (v - m)];
       }
-    if (!lu_factor(m, B, piv)) {
+    if (!lu_factor(m, B, piv, rcp)) {
       status = 2;
       break;
     }
     for (int r = 0; r < m; ++r) xB[r] = b[r];
-    lu_solve(m, B, piv, xB);
+    lu_solve(m, B, piv, rcp, xB);
     for (int k = 0; k < m; ++k) y[k] = basis[k] < m ? 1.0 : 0.0;
-    lu_solve_transposed(m, B, piv, y);
+    lu_solve_transposed(m, B, piv, rcp, y);
     /* pricing (Bland): lowest structural index with reduced cost < -tol */
     int q = -1;
     for (int j = 0; j < K && q < 0; ++j) {
@@ -622,7 +625,7 @@ int orc_phase1(int m, int K, const double* V, const double* b, double* f, int* n
       break;
     }
     for (int r = 0; r < m; ++r) d[r] = V[r * K + q];
-    lu_solve(m, B, piv, d);
+    lu_solve(m, B, piv, rcp, d);
     /* ratio test */
     double theta = INFINITY;
     for (int k = 0; k < m; ++k)
@@ -652,9 +655,9 @@ int orc_phase1(int m, int K, const double* V, const double* b, double* f, int* n
       int v = basis[k];
       B[r * m + k] = v < m ? (r == v ? 1.0 : 0.0) : V[r * K + (v - m)];
     }
-  if (!lu_factor(m, B, piv)) return 2;
+  if (!lu_factor(m, B, piv, rcp)) return 2;
   for (int r = 0; r < m; ++r) xB[r] = b[r];
-  lu_solve(m, B, piv, xB);
+  lu_solve(m, B, piv, rcp, xB);
   double w = 0.0;
   for (int k = 0; k < m; ++k)
     if (basis[k] < m) w += xB[k];

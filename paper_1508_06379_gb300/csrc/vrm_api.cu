@@ -25,6 +25,7 @@ struct vrm::Scratch {
   Grid* grid = nullptr;
   int *cell_key = nullptr, *cell_rank = nullptr, *cell_count = nullptr, *cell_start = nullptr;
   double2* sorted_xy = nullptr;
+  float2* sorted_loc = nullptr;
   int* sorted_idx = nullptr;
   unsigned long long* bbox = nullptr;
   int *scan_tmp = nullptr, *pos = nullptr;
@@ -35,8 +36,14 @@ struct vrm::Scratch {
   uint8_t* diffused = nullptr;
   int* dlist = nullptr;
   // insertion
-  uint8_t *mask = nullptr, *cand = nullptr, *acc = nullptr, *keep_flag = nullptr;
-  int *open_a = nullptr, *open_b = nullptr, *acc_count = nullptr, *acc_pos = nullptr, *keep_pos = nullptr;
+  uint8_t *mask = nullptr, *keep_flag = nullptr;
+  int *open_a = nullptr, *open_b = nullptr, *keep_pos = nullptr, *ccnt = nullptr, *ccpos = nullptr;
+  // proposals of one insertion round (grown on demand)
+  int cand_cap = 0, cand_ncell_cap = 0;
+  double *cx = nullptr, *cy = nullptr;
+  uint8_t* ckeep = nullptr;
+  int *capos = nullptr, *cscan_tmp = nullptr;
+  CandGrid cg = {};
   // neighbourhoods and weights of vrm_step
   int *nbr_count = nullptr, *nbr_idx = nullptr, *small = nullptr, *cols = nullptr, *fail_list = nullptr;
   uint8_t *seg_mask = nullptr, *status = nullptr;
@@ -68,11 +75,25 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
 }
 
+void free_cand(Scratch& s) {
+  void* ptrs[] = {s.cx, s.cy, s.ckeep, s.capos, s.cscan_tmp, s.cg.grid, s.cg.cell_key, s.cg.cell_rank,
+                  s.cg.cell_count, s.cg.cell_start, s.cg.sorted_idx, s.cg.sorted_xy, s.cg.sorted_loc, s.cg.bbox};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  s.cx = s.cy = nullptr;
+  s.ckeep = nullptr;
+  s.capos = s.cscan_tmp = nullptr;
+  s.cg = CandGrid{};
+  s.cand_cap = s.cand_ncell_cap = 0;
+}
+
 void free_scratch(Scratch& s) {
-  void* ptrs[] = {s.grid, s.cell_key, s.cell_rank, s.cell_count, s.cell_start, s.sorted_xy, s.sorted_idx, s.bbox,
-                  s.scan_tmp, s.pos, s.rstate, s.tie_flag, s.tie_rank, s.diffused, s.dlist, s.mask, s.cand, s.acc,
-                  s.keep_flag, s.open_a, s.open_b, s.acc_count, s.acc_pos, s.keep_pos, s.nbr_count, s.nbr_idx,
-                  s.small, s.cols, s.fail_list, s.seg_mask, s.status, s.f, s.fii, s.ds, s.counters};
+  free_cand(s);
+  void* ptrs[] = {s.grid, s.cell_key, s.cell_rank, s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc,
+                  s.sorted_idx, s.bbox,
+                  s.scan_tmp, s.pos, s.rstate, s.tie_flag, s.tie_rank, s.diffused, s.dlist, s.mask, s.keep_flag,
+                  s.open_a, s.open_b, s.keep_pos, s.ccnt, s.ccpos, s.nbr_count, s.nbr_idx, s.small, s.cols,
+                  s.fail_list, s.seg_mask, s.status, s.f, s.fii, s.ds, s.counters};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s.h_ds) cudaFreeHost(s.h_ds);
@@ -106,6 +127,7 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.cell_count, ncell);
   VRM_ALLOC(s.cell_start, ncell + 1);
   VRM_ALLOC(s.sorted_xy, n);
+  VRM_ALLOC(s.sorted_loc, n);
   VRM_ALLOC(s.sorted_idx, n);
   VRM_ALLOC(s.bbox, 8);
   VRM_ALLOC(s.scan_tmp, scan_tmp_ints((int)(ncell > n ? ncell : n)) + 16);
@@ -116,14 +138,12 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.diffused, n);
   VRM_ALLOC(s.dlist, n);
   VRM_ALLOC(s.mask, n);
-  VRM_ALLOC(s.cand, n);
-  VRM_ALLOC(s.acc, n);
   VRM_ALLOC(s.keep_flag, n);
   VRM_ALLOC(s.open_a, n);
   VRM_ALLOC(s.open_b, n);
-  VRM_ALLOC(s.acc_count, n);
-  VRM_ALLOC(s.acc_pos, (long)n + 1);
   VRM_ALLOC(s.keep_pos, (long)n + 1);
+  VRM_ALLOC(s.ccnt, n);
+  VRM_ALLOC(s.ccpos, (long)n + 1);
   VRM_ALLOC(s.nbr_count, n);
   VRM_ALLOC(s.nbr_idx, (long)n * k);
   VRM_ALLOC(s.small, (long)n * 8);
@@ -139,13 +159,46 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_ds, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_counters, sizeof(int) * 8);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_grid, sizeof(Grid));
-  if (e == cudaSuccess) e = cudaMemsetAsync(s.cand, 0, (size_t)n, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s.acc, 0, (size_t)n, st);
   if (e != cudaSuccess) {
     free_scratch(s);
     cudaGetLastError();
   }
   return e;
+}
+
+// Proposal buffers for n_cand proposals (grown by 50% steps, never shrunk).
+cudaError_t ensure_cand(Scratch& s, int n_cand, cudaStream_t st) {
+  if (n_cand <= s.cand_cap && s.cx) return cudaSuccess;
+  cudaStreamSynchronize(st);
+  long want = n_cand;
+  if (want < (long)s.cand_cap + s.cand_cap / 2) want = (long)s.cand_cap + s.cand_cap / 2;
+  if (want < 4096) want = 4096;
+  if (want > 0x7FFFFFF0L) want = 0x7FFFFFF0L;
+  free_cand(s);
+  const long ncell = 2 * want + 1024;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = dalloc(&s.cx, want);
+  if (e == cudaSuccess) e = dalloc(&s.cy, want);
+  if (e == cudaSuccess) e = dalloc(&s.ckeep, want);
+  if (e == cudaSuccess) e = dalloc(&s.capos, want + 1);
+  if (e == cudaSuccess) e = dalloc(&s.cscan_tmp, scan_tmp_ints((int)ncell) + 16);
+  if (e == cudaSuccess) e = dalloc(&s.cg.grid, 1);
+  if (e == cudaSuccess) e = dalloc(&s.cg.cell_key, want);
+  if (e == cudaSuccess) e = dalloc(&s.cg.cell_rank, want);
+  if (e == cudaSuccess) e = dalloc(&s.cg.cell_count, ncell);
+  if (e == cudaSuccess) e = dalloc(&s.cg.cell_start, ncell + 1);
+  if (e == cudaSuccess) e = dalloc(&s.cg.sorted_idx, want);
+  if (e == cudaSuccess) e = dalloc(&s.cg.sorted_xy, want);
+  if (e == cudaSuccess) e = dalloc(&s.cg.sorted_loc, want);
+  if (e == cudaSuccess) e = dalloc(&s.cg.bbox, 8);
+  if (e != cudaSuccess) {
+    free_cand(s);
+    cudaGetLastError();
+    return e;
+  }
+  s.cand_cap = (int)want;
+  s.cand_ncell_cap = (int)ncell;
+  return cudaSuccess;
 }
 
 #define VRM_CUDA(call)                       \
@@ -228,10 +281,9 @@ vrm_status stage_insert_reduce(vrm_ctx* ctx, double* x, double* y, int n, int ca
   if (capacity > n) VRM_CUDA(cudaMemsetAsync(diffused + n, 0, (size_t)(capacity - n), st));
   VRM_CUDA(compact_flags(diffused, n, s.dlist, s.counters + 0, s.pos, s.scan_tmp, st));
   VRM_CUDA(mark(ctx, VRM_STAGE_GRID, st));
-  VRM_CUDA(grid_build(x, y, n, c.Rh, s.ncell_cap, s.grid, s.cell_key, s.cell_rank, s.cell_count, s.cell_start,
-                      s.sorted_xy, s.sorted_idx, s.bbox, s.scan_tmp, st));
-  VRM_CUDA(search_masks(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_idx, x, y, s.dlist, s.counters + 0, n,
-                        s.mask, st));
+  VRM_CUDA(grid_build(x, y, n, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank, s.cell_count,
+                      s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp, st));
+  VRM_CUDA(search_masks(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, n, diffused, s.mask, st));
   VRM_CUDA(open_list(s.dlist, s.counters + 0, n, s.mask, s.keep_flag, s.pos, s.open_a, s.counters + 1, s.scan_tmp,
                      st));
   VRM_CUDA(mark(ctx, VRM_STAGE_INSERT, st));
@@ -248,22 +300,22 @@ vrm_status stage_insert_reduce(vrm_ctx* ctx, double* x, double* y, int n, int ca
       open_segments = s.h_counters[3];
       break;
     }
-    VRM_CUDA(insert_round_accept(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_idx, x, y, s.open_a, n_open, s.mask,
-                                 s.cand, s.acc, s.acc_count, s.acc_pos, s.scan_tmp, st));
-    int accepted = 0;
-    VRM_CUDA(cudaMemcpyAsync(s.h_counters + 4, s.acc_pos + n_open, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VRM_CUDA(insert_count(s.open_a, n_open, s.mask, s.ccnt, s.ccpos, s.scan_tmp, st));
+    VRM_CUDA(cudaMemcpyAsync(s.h_counters + 4, s.ccpos + n_open, sizeof(int), cudaMemcpyDeviceToHost, st));
     VRM_CUDA(cudaStreamSynchronize(st));
-    accepted = s.h_counters[4];
+    const int n_cand = s.h_counters[4];
+    VRM_CUDA(ensure_cand(s, n_cand, st));
+    VRM_CUDA(insert_propose(c, s.open_a, n_open, s.mask, s.ccpos, x, y, s.cx, s.cy, n_cand, s.cand_ncell_cap, s.cg,
+                            s.ckeep, s.capos, s.cscan_tmp, st));
+    VRM_CUDA(cudaMemcpyAsync(s.h_counters + 5, s.capos + n_cand, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VRM_CUDA(cudaStreamSynchronize(st));
+    const int accepted = s.h_counters[5];
     if ((long)n_cur + accepted > capacity) {
       if (acc_stats) acc_stats->n_out = (long)n_cur + accepted;
-      // leave the context clean for the next call
-      VRM_CUDA(cudaMemsetAsync(s.cand, 0, (size_t)s.cap, st));
-      VRM_CUDA(cudaMemsetAsync(s.acc, 0, (size_t)s.cap, st));
       return VRM_ERR_CAPACITY;
     }
-    VRM_CUDA(insert_round_commit(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_idx, x, y, n_cur, s.open_a, n_open,
-                                 s.mask, s.cand, s.acc, s.acc_pos, s.open_b, s.keep_flag, s.keep_pos, s.counters + 2,
-                                 s.scan_tmp, st));
+    VRM_CUDA(insert_commit(c, s.open_a, n_open, s.cx, s.cy, n_cand, s.cg, s.ckeep, s.capos, n_cur, x, y, s.mask,
+                           s.keep_flag, s.keep_pos, s.open_b, s.counters + 2, s.scan_tmp, st));
     VRM_CUDA(cudaMemcpyAsync(s.h_counters + 2, s.counters + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
     VRM_CUDA(cudaStreamSynchronize(st));
     n_cur += accepted;
@@ -411,10 +463,10 @@ vrm_status vrm_build_neighbourhoods(vrm_ctx* ctx, const double* x, const double*
   Scratch& s = ctx->s;
   VRM_CUDA(ensure_scratch(ctx, n, stream));
   VRM_CUDA(cudaMemsetAsync(s.ds, 0, sizeof(DevStats), stream));
-  VRM_CUDA(grid_build(x, y, n, ctx->c.Rh, s.ncell_cap, s.grid, s.cell_key, s.cell_rank, s.cell_count, s.cell_start,
-                      s.sorted_xy, s.sorted_idx, s.bbox, s.scan_tmp, stream));
-  VRM_CUDA(search_all(ctx->c, s.grid, s.cell_start, s.sorted_xy, s.sorted_idx, n, nbr_count, nbr_idx, seg_mask,
-                      small, s.ds, stream));
+  VRM_CUDA(grid_build(x, y, n, ctx->c.Rh, ctx->c.lo2, ctx->c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank,
+                      s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp, stream));
+  VRM_CUDA(search_all(ctx->c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, n, nbr_count, nbr_idx,
+                      seg_mask, small, s.ds, stream));
   if (max_count) {
     VRM_CUDA(read_back(ctx, stream));
     if (s.h_grid->nonfinite) return VRM_ERR_ARG;
@@ -496,10 +548,10 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
   if (r != VRM_OK) return r;
   VRM_CUDA(mark(ctx, VRM_STAGE_SEARCH, stream));
   if (n2 > n)
-    VRM_CUDA(grid_build(x, y, n2, c.Rh, s.ncell_cap, s.grid, s.cell_key, s.cell_rank, s.cell_count, s.cell_start,
-                        s.sorted_xy, s.sorted_idx, s.bbox, s.scan_tmp, stream));
-  VRM_CUDA(search_all(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_idx, n2, s.nbr_count, s.nbr_idx, s.seg_mask,
-                      s.small, s.ds, stream));
+    VRM_CUDA(grid_build(x, y, n2, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank, s.cell_count,
+                        s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp, stream));
+  VRM_CUDA(search_all(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, n2, s.nbr_count, s.nbr_idx,
+                      s.seg_mask, s.small, s.ds, stream));
   const double nu_dt = ctx->p.nu * dt;
   VRM_CUDA(mark(ctx, VRM_STAGE_LP_SMALL, stream));
   VRM_CUDA(lp_small(c, x, y, s.dlist, s.counters + 0, n, s.small, s.cols, s.f, s.fii, s.status, s.fail_list, s.ds,

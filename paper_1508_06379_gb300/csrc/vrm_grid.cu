@@ -206,8 +206,8 @@ __global__ void k_bbox(const double* __restrict__ x, const double* __restrict__ 
   }
 }
 
-__global__ void k_grid_finalize(const unsigned long long* __restrict__ bb, int n, double Rh, int ncell_cap,
-                                Grid* __restrict__ g) {
+__global__ void k_grid_finalize(const unsigned long long* __restrict__ bb, int n, double Rh, double lo2, double hi2,
+                                int ncell_cap, Grid* __restrict__ g) {
   Grid G;
   G.nonfinite = (int)bb[4];
   double x0 = 0, x1 = 0, y0 = 0, y1 = 0;
@@ -232,6 +232,13 @@ __global__ void k_grid_finalize(const unsigned long long* __restrict__ bb, int n
     G.ny = (int)floor(hgt * G.inv_cs) + 1;
   }
   G.ncell = G.nx * G.ny;
+  const double s2 = G.inv_cs * G.inv_cs;
+  const float lo2c = (float)(lo2 * s2), hi2c = (float)(hi2 * s2);
+  G.lo_out = lo2c - kBand;
+  G.lo_in = lo2c + kBand;
+  G.hi_in = hi2c - kBand;
+  G.hi_out = hi2c + kBand;
+  G.seg_eps = kSegEps;
   *g = G;
 }
 
@@ -245,31 +252,37 @@ __global__ void k_bin(const double* __restrict__ x, const double* __restrict__ y
   }
 }
 
-__global__ void k_scatter(const double* __restrict__ x, const double* __restrict__ y, int n,
+__global__ void k_scatter(const double* __restrict__ x, const double* __restrict__ y, int n, const Grid* __restrict__ gp,
                           const int* __restrict__ cell_key, const int* __restrict__ cell_rank,
                           const int* __restrict__ cell_start, double2* __restrict__ sorted_xy,
-                          int* __restrict__ sorted_idx) {
+                          float2* __restrict__ sorted_loc, int* __restrict__ sorted_idx) {
+  const Grid g = *gp;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    int p = cell_start[cell_key[i]] + cell_rank[i];
-    sorted_xy[p] = make_double2(x[i], y[i]);
+    const int key = cell_key[i];
+    const int p = cell_start[key] + cell_rank[i];
+    const double xi = x[i], yi = y[i];
+    sorted_xy[p] = make_double2(xi, yi);
+    sorted_loc[p] = make_float2(grid_local_x(g, xi, key % g.nx), grid_local_y(g, yi, key / g.nx));
     sorted_idx[p] = (int)i;
   }
 }
 
-cudaError_t grid_build(const double* x, const double* y, int n, double Rh, int ncell_cap, Grid* g, int* cell_key,
-                       int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy, int* sorted_idx,
-                       unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s) {
+cudaError_t grid_build(const double* x, const double* y, int n, double Rh, double lo2, double hi2, int ncell_cap,
+                       Grid* g, int* cell_key, int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy,
+                       float2* sorted_loc, int* sorted_idx, unsigned long long* bbox_tmp, int* scan_tmp,
+                       cudaStream_t s) {
   int blocks = n > 0 ? (n + kBlock - 1) / kBlock : 1;
   int pblocks = blocks < 4 * sm_count() ? blocks : 4 * sm_count();
   k_bbox_init<<<1, 1, 0, s>>>(bbox_tmp); note_launch();
   k_bbox<<<pblocks, kBlock, 0, s>>>(x, y, n, bbox_tmp); note_launch();
-  k_grid_finalize<<<1, 1, 0, s>>>(bbox_tmp, n, Rh, ncell_cap, g); note_launch();
+  k_grid_finalize<<<1, 1, 0, s>>>(bbox_tmp, n, Rh, lo2, hi2, ncell_cap, g); note_launch();
   cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int) * (size_t)ncell_cap, s);
   if (e != cudaSuccess) return e;
   k_bin<<<blocks, kBlock, 0, s>>>(x, y, n, g, cell_key, cell_rank, cell_count); note_launch();
   e = scan_exclusive_i32(cell_count, cell_start, ncell_cap, scan_tmp, s);
   if (e != cudaSuccess) return e;
-  k_scatter<<<blocks, kBlock, 0, s>>>(x, y, n, cell_key, cell_rank, cell_start, sorted_xy, sorted_idx); note_launch();
+  k_scatter<<<blocks, kBlock, 0, s>>>(x, y, n, g, cell_key, cell_rank, cell_start, sorted_xy, sorted_loc,
+                                      sorted_idx); note_launch();
   return cudaGetLastError();
 }
 

@@ -35,11 +35,22 @@ struct Consts {
 };
 
 // Uniform cell grid, device resident (written by grid_build).
+// Besides FP64 positions, the sorted arrays hold FP32 cell-local coordinates
+// u - floor(u) with u = (x - x0)/cs.  In cell units the offset of two
+// particles is (cell difference) + (local difference), within 5e-7 of the
+// exact value (|offset| < 2 cells), so an FP32 squared distance is within
+// 1e-5 of the exact one: pairs further than `band` from an annulus bound are
+// decided in FP32, the rest by the FP64 definition.
 struct Grid {
   double x0, y0, inv_cs;
   int nx, ny, ncell;
-  int nonfinite;  // set if a position was NaN/Inf
+  int nonfinite;          // set if a position was NaN/Inf
+  float lo_out, lo_in;    // (r h / cs)^2 -/+ band
+  float hi_in, hi_out;    // (R h / cs)^2 -/+ band
+  float seg_eps;          // FP32 segment decisions need this margin (cell units)
 };
+constexpr float kBand = 2e-5f;
+constexpr float kSegEps = 4e-6f;
 
 // Device-side counters of one step.
 struct DevStats {
@@ -111,6 +122,19 @@ __device__ __forceinline__ int grid_cell_y(const Grid& g, double y) {
   int c = (int)floor(__dmul_rn(__dsub_rn(y, g.y0), g.inv_cs));
   return c < 0 ? 0 : (c >= g.ny ? g.ny - 1 : c);
 }
+// Cell-local FP32 coordinate of x in a cell of index cx.
+__device__ __forceinline__ float grid_local_x(const Grid& g, double x, int cx) {
+  return __double2float_rn(__dsub_rn(__dmul_rn(__dsub_rn(x, g.x0), g.inv_cs), (double)cx));
+}
+__device__ __forceinline__ float grid_local_y(const Grid& g, double y, int cy) {
+  return __double2float_rn(__dsub_rn(__dmul_rn(__dsub_rn(y, g.y0), g.inv_cs), (double)cy));
+}
+// Segment of an FP32 cell-unit offset, or -1 when it lies within seg_eps of a
+// decision line (then the FP64 classifier decides).
+__device__ __forceinline__ int segment_or_ambiguous(float du, float dv, float eps) {
+  if (fabsf(du) <= eps || fabsf(dv) <= eps || fabsf(dv - du) <= 2.f * eps || fabsf(dv + du) <= 2.f * eps) return -1;
+  return segment_of(du, dv);
+}
 
 // ---- launch helpers (host) -----------------------------------------------
 
@@ -125,9 +149,10 @@ long long launch_count();
 // doubled while the cell count exceeds ncell_cap), keys, exclusive scan of
 // the cell counts (cell_start, ncell_cap + 1 entries), sorted positions and
 // indices.  Grid g is written on the device.
-cudaError_t grid_build(const double* x, const double* y, int n, double Rh, int ncell_cap, Grid* g, int* cell_key,
-                       int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy, int* sorted_idx,
-                       unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s);
+cudaError_t grid_build(const double* x, const double* y, int n, double Rh, double lo2, double hi2, int ncell_cap,
+                       Grid* g, int* cell_key, int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy,
+                       float2* sorted_loc, int* sorted_idx, unsigned long long* bbox_tmp, int* scan_tmp,
+                       cudaStream_t s);
 // Exclusive scan of n ints into out[0..n] (out[n] = total).
 cudaError_t scan_exclusive_i32(const int* in, int* out, int n, int* tmp, cudaStream_t s);
 // Exclusive scan of n bytes (0/1) into out[0..n].
@@ -143,28 +168,40 @@ cudaError_t reduce_select(const double* gamma, int n, double c_bound, uint8_t* d
 
 // vrm_search.cu
 cudaError_t search_all(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
-                       const int* sorted_idx, int n, int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small,
-                       DevStats* ds, cudaStream_t s);
+                       const float2* sorted_loc, const int* sorted_idx, int n, int* nbr_count, int* nbr_idx,
+                       uint8_t* seg_mask, int* small, DevStats* ds, cudaStream_t s);
+// Segment masks of the particles flagged in `flag` (n entries), in cell order.
 cudaError_t search_masks(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
-                         const int* sorted_idx, const double* x, const double* y, const int* list,
-                         const int* list_count, int cap, uint8_t* mask, cudaStream_t s);
+                         const float2* sorted_loc, const int* sorted_idx, int n, const uint8_t* flag, uint8_t* mask,
+                         cudaStream_t s);
 
 // vrm_insert.cu
+// Cell grid of the insertion proposals of one round.
+struct CandGrid {
+  Grid* grid;
+  int *cell_key, *cell_rank, *cell_count, *cell_start, *sorted_idx;
+  double2* sorted_xy;
+  float2* sorted_loc;
+  unsigned long long* bbox;
+};
 // Open list of round 1: the diffused particles (dlist, ascending) whose
 // segment mask is not full; open[] ascending, *n_open on the device.
 cudaError_t open_list(const int* dlist, const int* dcount, int cap, const uint8_t* mask, uint8_t* flag, int* pos,
                       int* open, int* n_open, int* scan_tmp, cudaStream_t s);
-// First half of an insertion round: proposals and the conflict rule.
-// acc_pos[n_open] receives the number of accepted points.
-cudaError_t insert_round_accept(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
-                                const int* sorted_idx, const double* x, const double* y, const int* open,
-                                int n_open, const uint8_t* mask, uint8_t* cand, uint8_t* acc, int* acc_count,
-                                int* acc_pos, int* scan_tmp, cudaStream_t s);
-// Second half: append at x[n_cur..], update masks, next open list.
-cudaError_t insert_round_commit(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
-                                const int* sorted_idx, double* x, double* y, int n_cur, const int* open, int n_open,
-                                uint8_t* mask, uint8_t* cand, uint8_t* acc, const int* acc_pos, int* open_next,
-                                uint8_t* keep_flag, int* keep_pos, int* n_next, int* scan_tmp, cudaStream_t s);
+// Proposal counts of the open particles; cpos[n_open] = number of proposals.
+cudaError_t insert_count(const int* open, int n_open, const uint8_t* mask, int* cnt, int* cpos, int* scan_tmp,
+                         cudaStream_t s);
+// Writes the proposals in key order, bins them, runs the conflict rule;
+// apos[n_cand] = number accepted.
+cudaError_t insert_propose(const Consts& c, const int* open, int n_open, const uint8_t* mask, const int* cpos,
+                           const double* x, const double* y, double* cx, double* cy, int n_cand, int ncell_cap,
+                           const CandGrid& cg, uint8_t* keep, int* apos, int* scan_tmp, cudaStream_t s);
+// Appends the accepted proposals at x[n_cur..], updates the masks, writes the
+// next open list (count in *n_next).
+cudaError_t insert_commit(const Consts& c, const int* open, int n_open, const double* cx, const double* cy,
+                          int n_cand, const CandGrid& cg, const uint8_t* keep, const int* apos, int n_cur, double* x,
+                          double* y, uint8_t* mask, uint8_t* keep_flag, int* keep_pos, int* open_next, int* n_next,
+                          int* scan_tmp, cudaStream_t s);
 cudaError_t count_open_segments(const int* open, int n_open, const uint8_t* mask, int* out, cudaStream_t s);
 
 // vrm_lp.cu

@@ -71,6 +71,76 @@ __device__ __forceinline__ void vcol(double xi, double eta, double* v) {
 
 __device__ __forceinline__ double b_of(int r) { return (r == 2 || r == 4) ? 2.0 : 0.0; }
 
+
+// Basic solution of the final basis, by the same LU sequence as the oracle's
+// basis solves (partial pivoting on the first largest |pivot|, full row
+// swaps, multipliers A[r][k] * (1/A[k][k]), products and differences rounded
+// separately), so that equal bases give bit-identical weights.  Column k of
+// B is the unit vector e_v for an artificial v = basis[k] < 5, else the
+// Vandermonde column of (bxi[k], beta[k]).  Returns false if B is singular.
+__device__ __forceinline__ bool basis_solve(const int* basis, const double* bxi, const double* beta, double* z) {
+  double A[kM][kM];
+#pragma unroll
+  for (int k = 0; k < kM; ++k) {
+    double v[kM];
+    vcol(bxi[k], beta[k], v);
+#pragma unroll
+    for (int r = 0; r < kM; ++r) A[r][k] = basis[k] < kM ? (basis[k] == r ? 1.0 : 0.0) : v[r];
+  }
+  int piv[kM];
+  double rcp[kM];
+#pragma unroll
+  for (int k = 0; k < kM; ++k) {
+    int p = k;
+    double best = fabs(A[k][k]);
+#pragma unroll
+    for (int r = k + 1; r < kM; ++r)
+      if (fabs(A[r][k]) > best) {
+        best = fabs(A[r][k]);
+        p = r;
+      }
+    piv[k] = p;
+    if (best == 0.0) return false;
+#pragma unroll
+    for (int r = k + 1; r < kM; ++r)
+#pragma unroll
+      for (int c = 0; c < kM; ++c) {
+        const double a = A[k][c], b = A[r][c];
+        A[k][c] = (p == r) ? b : a;
+        A[r][c] = (p == r) ? a : b;
+      }
+    rcp[k] = __drcp_rn(A[k][k]);
+#pragma unroll
+    for (int r = k + 1; r < kM; ++r) {
+      const double l = __dmul_rn(A[r][k], rcp[k]);
+      A[r][k] = l;
+#pragma unroll
+      for (int c = k + 1; c < kM; ++c) A[r][c] = __dsub_rn(A[r][c], __dmul_rn(l, A[k][c]));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kM; ++r) z[r] = b_of(r);
+#pragma unroll
+  for (int k = 0; k < kM; ++k)
+#pragma unroll
+    for (int r = k + 1; r < kM; ++r) {
+      const double a = z[k], b = z[r];
+      z[k] = (piv[k] == r) ? b : a;
+      z[r] = (piv[k] == r) ? a : b;
+    }
+#pragma unroll
+  for (int r = 1; r < kM; ++r)
+#pragma unroll
+    for (int c = 0; c < r; ++c) z[r] = __dsub_rn(z[r], __dmul_rn(A[r][c], z[c]));
+#pragma unroll
+  for (int r = kM - 1; r >= 0; --r) {
+#pragma unroll
+    for (int c = r + 1; c < kM; ++c) z[r] = __dsub_rn(z[r], __dmul_rn(A[r][c], z[c]));
+    z[r] = __dmul_rn(z[r], rcp[r]);
+  }
+  return true;
+}
+
 struct WarpStats {
   int ok, none, maxpiv;
   double maxratio;
@@ -246,19 +316,35 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         for (int r = 0; r < kM; ++r) basis[r] = (leave == r) ? kM + q : basis[r];
         ++it;
       }
-      // basic solution, snapped, and its residual
+      // basic solution of the final basis (fresh LU solve), snapped, and
+      // its residual
       double fv[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) fv[k] = 0.0;
       double wsum = 0.0;
+      if (code == 0) {
+        double bxi[kM], beta[kM], xB[kM];
 #pragma unroll
-      for (int r = 0; r < kM; ++r) {
-        if (basis[r] < kM) {
-          wsum = __dadd_rn(wsum, rhs[r]);
-        } else {
-          const double v = rhs[r] > kTolSnap ? rhs[r] : 0.0;
+        for (int r = 0; r < kM; ++r) {
+          double a = 0.0, e = 0.0;
 #pragma unroll
-          for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == kM + k) ? v : fv[k];
+          for (int k = 0; k < 8; ++k) {
+            a = (basis[r] == kM + k) ? cxi[k] : a;
+            e = (basis[r] == kM + k) ? ceta[k] : e;
+          }
+          bxi[r] = a;
+          beta[r] = e;
+        }
+        if (!basis_solve(basis, bxi, beta, xB)) code = 2;
+#pragma unroll
+        for (int r = 0; r < kM; ++r) {
+          if (basis[r] < kM) {
+            wsum = __dadd_rn(wsum, xB[r]);
+          } else {
+            const double v = xB[r] > kTolSnap ? xB[r] : 0.0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == kM + k) ? v : fv[k];
+          }
         }
       }
       double rmax = 0.0;
@@ -446,11 +532,23 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
       for (int r = 0; r < kM; ++r) basis[r] = (leave == r) ? kM + q : basis[r];
       ++it;
     }
+    // basic solution of the final basis by the oracle's LU sequence; every
+    // lane solves the same system from the broadcast basic columns
     double fv = 0.0, wsum = 0.0;
+    if (code == 0) {
+      double bxi[kM], beta[kM], xB[kM];
 #pragma unroll
-    for (int r = 0; r < kM; ++r) {
-      if (basis[r] < kM) wsum = __dadd_rn(wsum, rhs[r]);
-      else if (basis[r] == kM + lane) fv = rhs[r] > kTolSnap ? rhs[r] : 0.0;
+      for (int r = 0; r < kM; ++r) {
+        const int src = basis[r] >= kM ? basis[r] - kM : 0;
+        bxi[r] = __shfl_sync(0xffffffffu, cxi, src);
+        beta[r] = __shfl_sync(0xffffffffu, ceta, src);
+      }
+      if (!basis_solve(basis, bxi, beta, xB)) code = 2;
+#pragma unroll
+      for (int r = 0; r < kM; ++r) {
+        if (basis[r] < kM) wsum = __dadd_rn(wsum, xB[r]);
+        else if (basis[r] == kM + lane) fv = xB[r] > kTolSnap ? xB[r] : 0.0;
+      }
     }
     double rmax = 0.0;
 #pragma unroll

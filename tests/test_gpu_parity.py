@@ -150,15 +150,20 @@ def test_insertion_single_particle_and_rounds(lib, orc):
         assert np.array_equal(xb.cpu().numpy()[:n2], x2)
 
 
-def weights_equal(w_g, w_o, n, rel=1e-12):
+def weights_equal(w_g, w_o, n):
+    """Same LP outcome, same stencil columns, and bit-identical weights: the
+    GPU solves the final basis by the same LU sequence as the oracle."""
     st_g = w_g["status"].cpu().numpy()[:n]
-    assert np.array_equal(st_g, w_o["status"]), np.nonzero(st_g != w_o["status"])[0][:10]
+    bad = np.nonzero(st_g != w_o["status"])[0]
+    assert len(bad) == 0, ("status differs", bad[:10], st_g[bad[:10]], w_o["status"][bad[:10]])
     cols_g = w_g["cols"].cpu().numpy()[: n * W].reshape(n, W)
-    assert np.array_equal(cols_g, w_o["cols"]), np.nonzero((cols_g != w_o["cols"]).any(1))[0][:10]
+    bad = np.nonzero((cols_g != w_o["cols"]).any(1))[0]
+    assert len(bad) == 0, ("columns differ", bad[:10])
     f_g = w_g["f"].cpu().numpy()[: n * W].reshape(n, W)
-    assert np.all(np.abs(f_g - w_o["f"]) <= rel * np.maximum(1.0, np.abs(w_o["f"])))
+    bad = np.nonzero((f_g != w_o["f"]).any(1))[0]
+    assert len(bad) == 0, ("weights differ", bad[:5], f_g[bad[:5]], w_o["f"][bad[:5]])
     fii_g = w_g["fii"].cpu().numpy()[:n]
-    assert np.all(np.abs(fii_g - w_o["fii"]) <= rel * np.maximum(1.0, np.abs(w_o["fii"])))
+    assert np.array_equal(fii_g, w_o["fii"])
 
 
 @pytest.mark.parametrize("case", CLOUDS, ids=IDS)
@@ -229,7 +234,10 @@ def test_step_matches_oracle(lib, orc, case):
     got = go.cpu().numpy()[:n2]
     err = np.abs(got - g2)
     tol = 1e-12 * scale + 4 * np.spacing(np.abs(g2))
-    assert np.all(err <= tol), (np.max(err / np.maximum(tol, 1e-300)))
+    worst = int(np.argmax(err - tol))
+    assert np.all(err <= tol), ("dGamma off", worst, got[worst], g2[worst], tol[worst])
+    # with identical stencils the step is bit-identical
+    assert np.array_equal(got, g2)
     # repeating the call with the same inputs gives the same outputs
     go2 = torch.zeros(cap, dtype=torch.float64, device="cuda")
     n3, _ = ctx.step(xb, yb, n, gi, go2, dt)
