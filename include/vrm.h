@@ -182,8 +182,9 @@ vrm_status vrm_build_neighbourhoods(vrm_ctx* ctx, const double* x, const double*
  * neighbourhood (columns ordered by (|r_ij|^2, j)), rows
  * (1,0) (0,1) (2,0) (1,1) (0,2) in xi = r_ij / h with b = (0,0,2,0,2);
  * artificials start the basis; entering column = lowest index with reduced
- * cost < -1e-12; leaving row = minimum ratio over pivots > 1e-12, ties within
- * 1e-12 max(1, ratio) to the lowest basic variable (artificials first); at
+ * cost < -1e-9; leaving row = minimum ratio over pivots > 1e-9 (basic values
+ * <= 1e-11 count as zero), ties within 1e-12 max(1, ratio) to the lowest
+ * basic variable (artificials first); at
  * most 64 pivots; feasible iff phase-I objective <= 1e-10 and
  * max |V f~ - b| <= 1e-10; basic values <= 1e-11 are zeros.  If infeasible
  * and fallback is on, the same LP on the full row (its k_cap first entries,

@@ -32,8 +32,8 @@
 typedef unsigned __int128 u128;
 
 #define ORC_PIVOT_CAP 64
-#define ORC_TOL_PRICE 1e-12   /* entering: reduced cost < -tol */
-#define ORC_TOL_PIVOT 1e-12   /* ratio test: pivot element > tol */
+#define ORC_TOL_PRICE 1e-9    /* entering: reduced cost < -tol */
+#define ORC_TOL_PIVOT 1e-9    /* ratio test: pivot element > tol */
 #define ORC_TOL_TIE 1e-12     /* ratio ties: within tol * max(1, min ratio) */
 #define ORC_TOL_PHASE1 1e-10  /* feasible iff phase-I objective <= tol */
 #define ORC_TOL_SNAP 1e-11    /* basic values <= tol are degenerate zeros */
@@ -574,10 +574,11 @@ static void lu_solve_transposed(int m, const double* LU, const int* piv, const d
  * basis from scratch by LU (Sec. 4.1), as the paper does.
  * Variables: artificial a_k has index k (0..m-1), structural f_j has index
  * m + j.  Start basis: the artificials.  Entering: the structural column of
- * lowest index with reduced cost < -1e-12 (Bland); artificials that left are
- * never re-entered.  Leaving: minimum ratio over pivot elements > 1e-12;
- * ratios within 1e-12 max(1, min) are tied and the tie goes to the basic
- * variable of lowest index (Bland).  At most 64 pivots.
+ * lowest index with reduced cost < -1e-9 (Bland); artificials that left are
+ * never re-entered.  Leaving: minimum ratio over pivot elements > 1e-9, the
+ * basic values at or below 1e-11 taken as the zeros they are; ratios within
+ * 1e-12 max(1, min) are tied and the tie goes to the basic variable of lowest
+ * index (Bland).  At most 64 pivots.
  *
  * V: m x K row-major.  f: K outputs: basic values above 1e-11, others 0
  * (degenerate basics come out at rounding level, of either sign; they are
@@ -627,10 +628,13 @@ int orc_phase1(int m, int K, const double* V, const double* b, double* f, int* n
     for (int r = 0; r < m; ++r) d[r] = V[r * K + q];
     lu_solve(m, B, piv, rcp, d);
     /* ratio test */
+    /* basic values at or below the snap tolerance are degenerate zeros */
+    double xr[9];
+    for (int k = 0; k < m; ++k) xr[k] = xB[k] > ORC_TOL_SNAP ? xB[k] : 0.0;
     double theta = INFINITY;
     for (int k = 0; k < m; ++k)
       if (d[k] > ORC_TOL_PIVOT) {
-        double ratio = xB[k] / d[k];
+        double ratio = xr[k] / d[k];
         if (ratio < theta) theta = ratio;
       }
     if (theta == INFINITY) {
@@ -640,7 +644,7 @@ int orc_phase1(int m, int K, const double* V, const double* b, double* f, int* n
     double lim = theta + ORC_TOL_TIE * (theta > 1.0 ? theta : 1.0);
     int leave = -1;
     for (int k = 0; k < m; ++k)
-      if (d[k] > ORC_TOL_PIVOT && xB[k] / d[k] <= lim)
+      if (d[k] > ORC_TOL_PIVOT && xr[k] / d[k] <= lim)
         if (leave < 0 || basis[k] < basis[leave]) leave = k;
     basis[leave] = m + q;
     ++it;

@@ -6,10 +6,11 @@
 // artificials; they start the basis and, once they leave, never re-enter.
 // Rules (identical to the FP64 oracle, which solves the basis systems by LU
 // every iteration while this code updates a tableau):
-//   entering: lowest column with reduced cost < -1e-12 (Bland);
-//   leaving:  minimum ratio over pivot elements > 1e-12; ratios within
-//             1e-12 max(1, min) tie, the tie goes to the basic variable of
-//             lowest index (artificials 0..4 before structurals 5..);
+//   entering: lowest column with reduced cost < -1e-9 (Bland);
+//   leaving:  minimum ratio over pivot elements > 1e-9, basic values at or
+//             below 1e-11 taken as zero; ratios within 1e-12 max(1, min)
+//             tie, the tie goes to the basic variable of lowest index
+//             (artificials 0..4 before structurals 5..);
 //   at most 64 pivots; feasible iff the phase-I objective <= 1e-10 and
 //   max |V f - b| <= 1e-10; basic values <= 1e-11 are zeros.
 //
@@ -26,8 +27,8 @@
 
 namespace vrm {
 
-constexpr double kTolPrice = 1e-12;
-constexpr double kTolPivot = 1e-12;
+constexpr double kTolPrice = 1e-9;
+constexpr double kTolPivot = 1e-9;
 constexpr double kTolTie = 1e-12;
 constexpr double kTolPhase1 = 1e-10;
 constexpr double kTolSnap = 1e-11;
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         bool any = false;
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
-          ratio[r] = a[r] > kTolPivot ? __ddiv_rn(rhs[r], a[r]) : 1e308;
+          ratio[r] = a[r] > kTolPivot ? __ddiv_rn(rhs[r] > kTolSnap ? rhs[r] : 0.0, a[r]) : 1e308;
           if (a[r] > kTolPivot) {
             any = true;
             theta = ratio[r] < theta ? ratio[r] : theta;
@@ -485,7 +486,7 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
       bool any = false;
 #pragma unroll
       for (int r = 0; r < kM; ++r) {
-        ratio[r] = a[r] > kTolPivot ? __ddiv_rn(rhs[r], a[r]) : 1e308;
+        ratio[r] = a[r] > kTolPivot ? __ddiv_rn(rhs[r] > kTolSnap ? rhs[r] : 0.0, a[r]) : 1e308;
         if (a[r] > kTolPivot) {
           any = true;
           theta = ratio[r] < theta ? ratio[r] : theta;

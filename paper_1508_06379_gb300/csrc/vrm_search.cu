@@ -70,12 +70,21 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
           int s = segment_or_ambiguous(du, dv, g.seg_eps);
           if (s < 0) s = segment_of(dx, dy);
           mask |= 1u << s;
+          // current best of segment s by register selects, one FP64 compare
+          double cb = bd[0];
+          int cjb = bj[0];
 #pragma unroll
-          for (int t = 0; t < 8; ++t)
-            if (t == s && (d2 < bd[t] || (d2 == bd[t] && j < bj[t]))) {
-              bd[t] = d2;
-              bj[t] = j;
+          for (int t = 1; t < 8; ++t) {
+            cb = (s == t) ? bd[t] : cb;
+            cjb = (s == t) ? bj[t] : cjb;
+          }
+          if (d2 < cb || (d2 == cb && j < cjb)) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              bd[t] = (s == t) ? d2 : bd[t];
+              bj[t] = (s == t) ? j : bj[t];
             }
+          }
           if (cnt < k_cap || j < list[k_cap - 1]) {
             int pos = cnt < k_cap ? cnt : k_cap - 1;
             while (pos > 0 && list[pos - 1] > j) {
