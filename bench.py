@@ -80,37 +80,37 @@ def sample_window(x, y, g, frac):
 
 
 class Clocks:
-    """nvidia-smi samples (200 ms) while the timed region runs."""
+    """nvidia-smi samples (one query every ~200 ms from a thread) while the
+    timed region runs."""
 
     FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
              "clocks_event_reasons.sw_power_cap"
 
     def __init__(self, gpu_id=None):
-        self.proc = None
-        self.lines = []
-        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        self.cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits"]
         if gpu_id:
-            cmd += ["-i", gpu_id]
-        try:
-            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
-        except Exception:
-            self.proc = None
+            self.cmd += ["-i", gpu_id]
+        self.lines = []
+        self.stop_flag = False
+        self.thread = threading.Thread(target=self._poll, daemon=True)
+        self.thread.start()
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append((time.time(), line.strip()))
+    def _poll(self):
+        while not self.stop_flag:
+            t = time.time()
+            try:
+                out = subprocess.run(self.cmd, capture_output=True, text=True, timeout=5).stdout
+                for line in out.splitlines():
+                    if line.strip():
+                        self.lines.append((t, line.strip()))
+            except Exception:
+                pass
+            time.sleep(max(0.0, 0.2 - (time.time() - t)))
 
     def stop(self, t0, t1):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
+        self.stop_flag = True
+        self.thread.join(timeout=10)
         sm, smax, reasons, power = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for t, line in self.lines:
@@ -128,9 +128,10 @@ class Clocks:
             for k, name in enumerate(names):
                 if parts[5 + k].lower() == "active":
                     reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm),
-                "power_w_max": max(power) if power else None}
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
 def lp_small_flops(n_lp, pivots):

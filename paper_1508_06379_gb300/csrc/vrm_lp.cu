@@ -36,8 +36,51 @@ constexpr double kTolResid = 1e-10;
 constexpr int kPivotCap = 64;
 constexpr int kM = 5;
 
+// FP64 comparisons on the integer pipes: for non-NaN doubles the signed
+// 64-bit pattern orders the non-negative values, so these tests spend no
+// FP64 instruction (GB300's FP64 pipe is the bottleneck of this kernel).
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// x > t, for t > 0
+__device__ __forceinline__ bool gt_pos(double x, double t) { return dbits(x) > dbits(t); }
+// x < -t, for t > 0
+__device__ __forceinline__ bool lt_neg(double x, double t) {
+  const long long b = dbits(x);
+  return b < 0 && (b & 0x7FFFFFFFFFFFFFFFLL) > dbits(t);
+}
+// a < b, for a, b in [+0, inf]
+__device__ __forceinline__ bool lt_nonneg(double a, double b) {
+  return (unsigned long long)dbits(a) < (unsigned long long)dbits(b);
+}
+// |a| > |b|
+__device__ __forceinline__ bool abs_gt(double a, double b) {
+  return (dbits(a) & 0x7FFFFFFFFFFFFFFFLL) > (dbits(b) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ double dneg(double x) { return __longlong_as_double(dbits(x) ^ (long long)0x8000000000000000ULL); }
+
+// Reciprocal of a > 0 (a in the binary32 normal range) for the tableau: a
+// binary32 seed made from the bit pattern (rounded mantissa, integer ops),
+// a binary32 reciprocal, widened by integer ops, then Newton steps
+// r <- r + r (1 - a r) in FP64; one step gives about 2^-45 relative error,
+// two give full FP64 accuracy.  Only the pivot decisions use these values;
+// the weights come from the exact basis solve below.
+template <int STEPS>
+__device__ __forceinline__ double rcp_newton(double a) {
+  const unsigned long long b = (unsigned long long)dbits(a);
+  const unsigned long long mr = (b + 0x10000000ULL) >> 29;  // round the mantissa to 23 bits
+  const int e32 = (int)((mr >> 23) & 0x7FF) - 1023 + 127;
+  const float af = __int_as_float((e32 << 23) | (int)(mr & 0x7FFFFF));
+  const unsigned rb = __float_as_uint(__frcp_rn(af));
+  const unsigned long long db =
+      ((unsigned long long)((int)((rb >> 23) & 0xFF) - 127 + 1023) << 52) | ((unsigned long long)(rb & 0x7FFFFF) << 29);
+  double r = __longlong_as_double((long long)db);
+#pragma unroll
+  for (int k = 0; k < STEPS; ++k) r = __fma_rn(r, __fma_rn(-a, r, 1.0), r);
+  return r;
+}
+
 __device__ __forceinline__ void cswap(double* d2, int* j, double* a, double* b, int p, int q) {
-  bool sw = (d2[q] < d2[p]) || (d2[q] == d2[p] && j[q] < j[p]);
+  const unsigned long long bq = (unsigned long long)dbits(d2[q]), bp = (unsigned long long)dbits(d2[p]);
+  bool sw = (bq < bp) || (bq == bp && j[q] < j[p]);
   double t0 = sw ? d2[q] : d2[p], t1 = sw ? d2[p] : d2[q];
   d2[p] = t0;
   d2[q] = t1;
@@ -93,15 +136,15 @@ __device__ __forceinline__ bool basis_solve(const int* basis, const double* bxi,
 #pragma unroll
   for (int k = 0; k < kM; ++k) {
     int p = k;
-    double best = fabs(A[k][k]);
+    double best = A[k][k];
 #pragma unroll
     for (int r = k + 1; r < kM; ++r)
-      if (fabs(A[r][k]) > best) {
-        best = fabs(A[r][k]);
+      if (abs_gt(A[r][k], best)) {
+        best = A[r][k];
         p = r;
       }
     piv[k] = p;
-    if (best == 0.0) return false;
+    if ((dbits(best) & 0x7FFFFFFFFFFFFFFFLL) == 0) return false;
 #pragma unroll
     for (int r = k + 1; r < kM; ++r)
 #pragma unroll
@@ -212,8 +255,8 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         cxi[k] = __dmul_rn(cxi[k], c.inv_h);
         ceta[k] = __dmul_rn(ceta[k], c.inv_h);
       }
-      // tableau: T[r][k] = (B^-1 V)_rk, rhs = B^-1 b, d = reduced costs, w = objective
-      double T[kM][8], rhs[kM], d[8], w = 4.0;
+      // tableau: T[r][k] = (B^-1 V)_rk, rhs = B^-1 b, d = phase-I reduced costs
+      double T[kM][8], rhs[kM], d[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         double v[kM];
@@ -224,7 +267,7 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
           T[r][k] = v[r];
           s = __dadd_rn(s, v[r]);
         }
-        d[k] = 0.0 - s;
+        d[k] = dneg(s);
       }
 #pragma unroll
       for (int r = 0; r < kM; ++r) rhs[r] = b_of(r);
@@ -240,7 +283,7 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         int q = -1;
 #pragma unroll
         for (int k = 7; k >= 0; --k)
-          if (!((basic >> k) & 1u) && d[k] < -kTolPrice) q = k;
+          if (!((basic >> k) & 1u) && lt_neg(d[k], kTolPrice)) q = k;
         if (q < 0) break;
         if (it == kPivotCap) {
           code = 2;
@@ -254,25 +297,29 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
           for (int k = 1; k < 8; ++k) v = (q == k) ? T[r][k] : v;
           a[r] = v;
         }
+        // ratio test: basic values <= kTolSnap are zeros; ratios by a
+        // Newton reciprocal (relative error ~2^-45, far inside the tie window)
         double ratio[kM], theta = 1e308;
-        bool any = false;
+        bool elig[kM], any = false;
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
-          ratio[r] = a[r] > kTolPivot ? __ddiv_rn(rhs[r] > kTolSnap ? rhs[r] : 0.0, a[r]) : 1e308;
-          if (a[r] > kTolPivot) {
+          elig[r] = gt_pos(a[r], kTolPivot);
+          const double num = gt_pos(rhs[r], kTolSnap) ? rhs[r] : 0.0;
+          ratio[r] = elig[r] ? __dmul_rn(num, rcp_newton<1>(a[r])) : 1e308;
+          if (elig[r]) {
             any = true;
-            theta = ratio[r] < theta ? ratio[r] : theta;
+            theta = lt_nonneg(ratio[r], theta) ? ratio[r] : theta;
           }
         }
         if (!any) {
           code = 2;
           break;
         }
-        const double lim = theta + kTolTie * (theta > 1.0 ? theta : 1.0);
+        const double lim = __fma_rn(kTolTie, gt_pos(theta, 1.0) ? theta : 1.0, theta);
         int leave = -1, lbas = INT_MAX;
 #pragma unroll
         for (int r = 0; r < kM; ++r)
-          if (a[r] > kTolPivot && ratio[r] <= lim && basis[r] < lbas) {
+          if (elig[r] && !lt_nonneg(lim, ratio[r]) && basis[r] < lbas) {
             leave = r;
             lbas = basis[r];
           }
@@ -282,7 +329,7 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
           piv = (leave == r) ? a[r] : piv;
           prhs_raw = (leave == r) ? rhs[r] : prhs_raw;
         }
-        const double rcp = __drcp_rn(piv);
+        const double rcp = rcp_newton<2>(piv);
         double prow[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -292,24 +339,22 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
           prow[k] = (k == q) ? 1.0 : __dmul_rn(v, rcp);
         }
         const double prhs = __dmul_rn(prhs_raw, rcp);
+        // row r <- row r - a_r prow; the leaving row becomes prow itself
+        // (zeroed, multiplier -1), and column q becomes exactly e_leave
+        // because prow[q] = 1 and T[r][q] = a_r
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
           const bool lr = (leave == r);
-          const double ar = lr ? 0.0 : a[r];
+          const double ar = lr ? -1.0 : a[r];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            const double u = __fma_rn(-ar, prow[k], T[r][k]);
-            T[r][k] = lr ? prow[k] : ((k == q) ? 0.0 : u);
-          }
-          const double ur = __fma_rn(-ar, prhs, rhs[r]);
-          rhs[r] = lr ? prhs : ur;
+          for (int k = 0; k < 8; ++k) T[r][k] = __fma_rn(-ar, prow[k], lr ? 0.0 : T[r][k]);
+          rhs[r] = __fma_rn(-ar, prhs, lr ? 0.0 : rhs[r]);
         }
         double dq = d[0];
 #pragma unroll
         for (int k = 1; k < 8; ++k) dq = (q == k) ? d[k] : dq;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) d[k] = (k == q) ? 0.0 : __fma_rn(-dq, prow[k], d[k]);
-        w = __fma_rn(-dq, prhs, w);
+        for (int k = 0; k < 8; ++k) d[k] = __fma_rn(-dq, prow[k], d[k]);
         if (lbas >= kM) basic &= ~(1u << (lbas - kM));
         else --n_art;
         basic |= 1u << q;
@@ -317,12 +362,12 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         for (int r = 0; r < kM; ++r) basis[r] = (leave == r) ? kM + q : basis[r];
         ++it;
       }
-      // basic solution of the final basis (fresh LU solve), snapped, and
-      // its residual
+      // basic solution of the final basis (fresh LU solve, bit-identical to
+      // the oracle's), snapped, and its residual over the basic columns
       double fv[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) fv[k] = 0.0;
-      double wsum = 0.0;
+      double wsum = 0.0, rmax = 0.0;
       if (code == 0) {
         double bxi[kM], beta[kM], xB[kM];
 #pragma unroll
@@ -337,34 +382,27 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
           beta[r] = e;
         }
         if (!basis_solve(basis, bxi, beta, xB)) code = 2;
+        double acc[kM];
+#pragma unroll
+        for (int r = 0; r < kM; ++r) acc[r] = dneg(b_of(r));
 #pragma unroll
         for (int r = 0; r < kM; ++r) {
           if (basis[r] < kM) {
             wsum = __dadd_rn(wsum, xB[r]);
           } else {
-            const double v = xB[r] > kTolSnap ? xB[r] : 0.0;
+            const double v = gt_pos(xB[r], kTolSnap) ? xB[r] : 0.0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == kM + k) ? v : fv[k];
+            double col[kM];
+            vcol(bxi[r], beta[r], col);
+#pragma unroll
+            for (int q = 0; q < kM; ++q) acc[q] = __fma_rn(col[q], v, acc[q]);
           }
         }
+#pragma unroll
+        for (int r = 0; r < kM; ++r) rmax = abs_gt(acc[r], rmax) ? fabs(acc[r]) : rmax;
       }
-      double rmax = 0.0;
-      {
-        double acc[kM] = {0.0, 0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          double v[kM];
-          vcol(cxi[k], ceta[k], v);
-#pragma unroll
-          for (int r = 0; r < kM; ++r) acc[r] = __dadd_rn(acc[r], __dmul_rn(v[r], fv[k]));
-        }
-#pragma unroll
-        for (int r = 0; r < kM; ++r) {
-          const double e = fabs(__dsub_rn(acc[r], b_of(r)));
-          rmax = e > rmax ? e : rmax;
-        }
-      }
-      const bool feasible = code == 0 && wsum <= kTolPhase1 && rmax <= kTolResid;
+      const bool feasible = code == 0 && !gt_pos(wsum, kTolPhase1) && !gt_pos(rmax, kTolResid);
       st_maxpiv = it > st_maxpiv ? it : st_maxpiv;
       ++st_solved;
       st_pivots += it;
@@ -375,7 +413,7 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k < 8; ++k)
-          if (fv[k] != 0.0) {
+          if (dbits(fv[k]) != 0) {
             crow[slot] = cj[k];
             frow[slot] = fv[k];
             ++slot;

@@ -6,13 +6,13 @@
 // The annulus test of the method is the FP64 definition
 //   lo2 <= dx*dx + dy*dy <= hi2,  dx = x_j - x_i,  dy = y_j - y_i,
 // every operation rounded separately.  GB300 runs FP64 at 1/60 of its FP32
-// rate, so each pair is first measured in FP32 on cell-local coordinates
-// (error below 1e-5 cell^2): a pair outside the bounds by more than the band
-// is skipped, a pair inside by more than the band is a member without an FP64
-// bound test, and only the hits (which need their FP64 squared distance for
-// the small neighbourhood's order) and the pairs in the band take FP64 work.
-// Segments are decided in FP32 unless the offset is within seg_eps of a
-// decision line.  The result is bit-identical to the FP64 definition.
+// rate, so each pair is measured in FP32 on cell-local coordinates (error
+// below 1e-5 cell^2): a pair further than the band from both bounds is
+// decided in FP32; segments are decided in FP32 unless the offset lies within
+// seg_eps of a decision line; the closest member of a segment is chosen in
+// FP32 unless another member lies within two bands of it.  Only the
+// undecided cases (rare on jittered clouds, frequent on exact lattices) take
+// the FP64 definition, so the result is bit-identical to it.
 //
 // The row is kept sorted by index in a per-thread buffer (the k_cap smallest
 // indices survive); the closest particle of every segment is tracked in
@@ -21,6 +21,22 @@
 
 namespace vrm {
 
+// Exact member test and segment of one candidate pair, for the rare pairs
+// the FP32 measure cannot decide.  Returns the segment, or -1 if j is not in
+// the annulus of i.
+__device__ __forceinline__ int exact_member(const Consts& c, const double2& pi, const double2& pj, bool certain_in,
+                                            double* d2_out) {
+  const double dx = __dsub_rn(pj.x, pi.x), dy = __dsub_rn(pj.y, pi.y);
+  const double d2 = dist2(dx, dy);
+  *d2_out = d2;
+  if (!certain_in && (d2 < c.lo2 || d2 > c.hi2)) return -1;
+  return segment_of(dx, dy);
+}
+
+// Small neighbourhood bookkeeping: per segment the smallest FP32 squared
+// distance and its particle, and a flag `amb` set when another member of
+// the segment lies within 2 bands of it (then the FP32 order may differ from
+// the FP64 order, and a second pass decides that segment exactly).
 template <int KCAP>
 __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __restrict__ gp,
                                                        const int* __restrict__ cell_start,
@@ -32,6 +48,7 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
                                                        DevStats* __restrict__ ds) {
   const Grid g = *gp;
   const int k_cap = c.k_cap;
+  const float tie = 2.f * kBand;
   int local_max = 0;
   for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
     const int i = sidx[p];
@@ -40,14 +57,14 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
     const int cx = grid_cell_x(g, pi.x), cy = grid_cell_y(g, pi.y);
     int list[KCAP];
     int cnt = 0;
-    double bd[8];
+    float bf[8];
     int bj[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-      bd[t] = 1e300;
+      bf[t] = 3e38f;
       bj[t] = -1;
     }
-    unsigned mask = 0;
+    unsigned mask = 0, amb = 0;
     for (int by = cy - 1; by <= cy + 1; ++by) {
       if (by < 0 || by >= g.ny) continue;
       const float dvb = (float)(by - cy) - li.y;
@@ -63,25 +80,29 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
           if (d2f < g.lo_out || d2f > g.hi_out) continue;
           const int j = sidx[q];
           if (j == i) continue;
-          const double2 pj = sxy[q];
-          const double dx = __dsub_rn(pj.x, pi.x), dy = __dsub_rn(pj.y, pi.y);
-          const double d2 = dist2(dx, dy);
-          if (!(d2f > g.lo_in && d2f < g.hi_in) && (d2 < c.lo2 || d2 > c.hi2)) continue;
-          int s = segment_or_ambiguous(du, dv, g.seg_eps);
-          if (s < 0) s = segment_of(dx, dy);
+          const bool certain_in = d2f > g.lo_in && d2f < g.hi_in;
+          int s = certain_in ? segment_or_ambiguous(du, dv, g.seg_eps) : -1;
+          if (s < 0) {
+            double d2;
+            s = exact_member(c, pi, sxy[q], certain_in, &d2);
+            if (s < 0) continue;
+          }
           mask |= 1u << s;
-          // current best of segment s by register selects, one FP64 compare
-          double cb = bd[0];
+          float cb = bf[0];
           int cjb = bj[0];
 #pragma unroll
           for (int t = 1; t < 8; ++t) {
-            cb = (s == t) ? bd[t] : cb;
+            cb = (s == t) ? bf[t] : cb;
             cjb = (s == t) ? bj[t] : cjb;
           }
-          if (d2 < cb || (d2 == cb && j < cjb)) {
+          const bool take = cjb < 0 || d2f < cb || (d2f == cb && j < cjb);
+          // conservative: the displaced or the new member is close to the best
+          const bool close = cjb >= 0 && fabsf(d2f - cb) <= tie;
+          if (close) amb |= 1u << s;
+          if (take) {
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-              bd[t] = (s == t) ? d2 : bd[t];
+              bf[t] = (s == t) ? d2f : bf[t];
               bj[t] = (s == t) ? j : bj[t];
             }
           }
@@ -94,6 +115,51 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
             list[pos] = j;
           }
           ++cnt;
+        }
+      }
+    }
+    if (amb) {
+      // exact FP64 order (ties to the smaller index) for the flagged segments
+      double bd[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        bd[t] = 1e300;
+        if ((amb >> t) & 1u) bj[t] = -1;
+      }
+      for (int by = cy - 1; by <= cy + 1; ++by) {
+        if (by < 0 || by >= g.ny) continue;
+        const float dvb = (float)(by - cy) - li.y;
+        for (int bx = cx - 1; bx <= cx + 1; ++bx) {
+          if (bx < 0 || bx >= g.nx) continue;
+          const float dub = (float)(bx - cx) - li.x;
+          const int cell = by * g.nx + bx;
+          const int q0 = cell_start[cell], q1 = cell_start[cell + 1];
+          for (int q = q0; q < q1; ++q) {
+            const float2 lj = sloc[q];
+            const float du = dub + lj.x, dv = dvb + lj.y;
+            const float d2f = __fmaf_rn(du, du, dv * dv);
+            if (d2f < g.lo_out || d2f > g.hi_out) continue;
+            const int j = sidx[q];
+            if (j == i) continue;
+            const bool certain_in = d2f > g.lo_in && d2f < g.hi_in;
+            double d2;
+            const int s = exact_member(c, pi, sxy[q], certain_in, &d2);
+            if (s < 0 || !((amb >> s) & 1u)) continue;
+            double cb = bd[0];
+            int cjb = bj[0];
+#pragma unroll
+            for (int t = 1; t < 8; ++t) {
+              cb = (s == t) ? bd[t] : cb;
+              cjb = (s == t) ? bj[t] : cjb;
+            }
+            if (cjb < 0 || d2 < cb || (d2 == cb && j < cjb)) {
+#pragma unroll
+              for (int t = 0; t < 8; ++t) {
+                bd[t] = (s == t) ? d2 : bd[t];
+                bj[t] = (s == t) ? j : bj[t];
+              }
+            }
+          }
         }
       }
     }
