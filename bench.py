@@ -80,30 +80,70 @@ def sample_window(x, y, g, frac):
 
 
 class Clocks:
-    """nvidia-smi samples (one query every ~200 ms from a thread) while the
-    timed region runs."""
+    """SM clock, power and clock-event reasons sampled while the timed region
+    runs: read-only NVML queries (libnvidia-ml through ctypes) every 5 ms from
+    a thread, else nvidia-smi queries every 200 ms."""
 
-    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
-             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
-             "clocks_event_reasons.sw_power_cap"
+    # clock event reason bits (nvml.h): hw slowdown, sw thermal, hw thermal, sw power cap
+    REASONS = {0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown", 0x4: "sw_power_cap"}
 
-    def __init__(self, gpu_id=None):
-        self.cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits"]
-        if gpu_id:
-            self.cmd += ["-i", gpu_id]
-        self.lines = []
+    def __init__(self, gpu_uuid=None):
+        self.samples = []  # (t, sm_mhz, max_mhz, power_w, reasons bitmask or names)
         self.stop_flag = False
+        self.nvml = None
+        self.handle = None
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() == 0:
+                h = ctypes.c_void_p()
+                ok = -1
+                if gpu_uuid:
+                    ok = lib.nvmlDeviceGetHandleByUUID(gpu_uuid.encode(), ctypes.byref(h))
+                if ok != 0:
+                    ok = lib.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h))
+                if ok == 0:
+                    self.nvml, self.handle, self.ct = lib, h, ctypes
+                    self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                        getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+        except Exception:
+            self.nvml = None
+        self.cmd = ["nvidia-smi", "--query-gpu=clocks.sm,clocks.max.sm,power.draw,"
+                    "clocks_event_reasons.hw_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                    "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                    "--format=csv,noheader,nounits"]
+        if gpu_uuid:
+            self.cmd += ["-i", gpu_uuid]
         self.thread = threading.Thread(target=self._poll, daemon=True)
         self.thread.start()
+
+    def _nvml_sample(self):
+        ct, lib, h = self.ct, self.nvml, self.handle
+        clk, mx, pw, rs = ct.c_uint(), ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        lib.nvmlDeviceGetClockInfo(h, 1, ct.byref(clk))  # NVML_CLOCK_SM
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, ct.byref(mx))
+        lib.nvmlDeviceGetPowerUsage(h, ct.byref(pw))
+        names = []
+        if self.reasons_fn is not None and self.reasons_fn(h, ct.byref(rs)) == 0:
+            names = [n for bit, n in self.REASONS.items() if rs.value & bit]
+        return (time.time(), float(clk.value), float(mx.value), pw.value / 1000.0, names)
 
     def _poll(self):
         while not self.stop_flag:
             t = time.time()
             try:
+                if self.nvml is not None:
+                    self.samples.append(self._nvml_sample())
+                    time.sleep(0.005)
+                    continue
                 out = subprocess.run(self.cmd, capture_output=True, text=True, timeout=5).stdout
                 for line in out.splitlines():
-                    if line.strip():
-                        self.lines.append((t, line.strip()))
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 7:
+                        continue
+                    names = [n for n, v in zip(["hw_slowdown", "sw_thermal_slowdown", "hw_thermal_slowdown",
+                                                "sw_power_cap"], parts[3:7]) if v.lower() == "active"]
+                    self.samples.append((t, float(parts[0]), float(parts[1]), float(parts[2]), names))
             except Exception:
                 pass
             time.sleep(max(0.0, 0.2 - (time.time() - t)))
@@ -111,27 +151,13 @@ class Clocks:
     def stop(self, t0, t1):
         self.stop_flag = True
         self.thread.join(timeout=10)
-        sm, smax, reasons, power = [], [], set(), []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for t, line in self.lines:
-            if t < t0 or t > t1:
-                continue
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-                power.append(float(parts[3]))
-            except ValueError:
-                continue
-            for k, name in enumerate(names):
-                if parts[5 + k].lower() == "active":
-                    reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm), "power_w_max": max(power) if power else None}
+        sel = [s for s in self.samples if t0 <= s[0] <= t1]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock samples"], "samples": 0}
+        reasons = sorted({n for s in sel for n in s[4]})
+        return {"sm_mhz": statistics.median(s[1] for s in sel), "sm_max_mhz": max(s[2] for s in sel),
+                "reasons": reasons, "samples": len(sel), "power_w_max": max(s[3] for s in sel),
+                "source": "nvml" if self.nvml is not None else "nvidia-smi"}
 
 
 def lp_small_flops(n_lp, pivots):
@@ -179,7 +205,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     gpu_id = None
     try:
-        gpu_id = "GPU-%s" % torch.cuda.get_device_properties(local).uuid
+        gpu_id = str(torch.cuda.get_device_properties(local).uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
     except Exception:
         gpu_id = None
     clocks = Clocks(gpu_id)
