@@ -360,20 +360,20 @@ def roofline_for(stage, ms, stats, n):
             "traffic": traffic_for(kern), "peak_source": src}
 
 
-def cpu_baseline(name, frac=0.3):
+def cpu_baseline(name, frac=1.0):
     """The oracle as it stands on a bounded sample (centred window) of the
     workload, all host cores."""
     import oracle
     oracle.build()
     x, y, g, h, nu, dt, _ = workload(name)
-    if name == "mixture_1m":
+    if name == "mixture_1m" and frac < 1.0:
         x, y, g = sample_window(x, y, g, frac)
     t0 = time.time()
     x2, y2, g2, st = oracle.step(x, y, g, h, nu, dt)
     t = time.time() - t0
     return {"value": len(x2) / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "one oracle step on the centred window holding %.0f%% of the workload (%d particles in, %d "
-                      "after insertion), %.1f s" % (100 * frac, len(x), len(x2), t)}
+            "sample": "one oracle step on %s of the workload (%d particles in, %d after insertion), %.1f s" % (
+                "all" if frac >= 1.0 else "a centred window holding %.0f%%" % (100 * frac), len(x), len(x2), t)}
 
 
 def run_reference(args):
