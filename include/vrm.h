@@ -241,6 +241,35 @@ vrm_status vrm_stage_times(vrm_ctx* ctx, float* ms);
 /* Kernels launched by this library in this process so far (all contexts). */
 int64_t vrm_launch_count(void);
 
+/* Largest cloud vrm_build_neighbourhoods_noalloc accepts. */
+#define VRM_NOALLOC_MAX_N 65536
+
+/*
+ * The neighbourhood search of vrm_build_neighbourhoods (same outputs, bit for
+ * bit) for callers that cannot allocate memory when they need it: code that
+ * runs while a stream is being captured into a CUDA graph (an allocation
+ * there breaks or serialises the capture), real-time loops with no room for
+ * allocator latency, and applications whose memory is all handed to their
+ * own pool beforehand.  The paper has no counterpart; it is a service of this
+ * library.
+ *
+ * It takes the parameters instead of a context and calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Its scratch is one fixed device
+ * array of about 3.4 MB inside this library, which every GPU that loads the
+ * library holds until the process exits; it serves clouds of at most
+ * VRM_NOALLOC_MAX_N particles and returns VRM_ERR_CAPACITY above that.
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress, once per device, with that device current); make
+ * that first call before any stream capture.  Every call shares the array
+ * and overwrites what the previous call left there, so calls whose work
+ * overlaps on the GPU (two streams, or two host threads) race: serialise
+ * them.  Arguments, outputs, errors and the optional max_count are as for
+ * vrm_build_neighbourhoods; only r, R, h and k_cap of *p are used.
+ */
+vrm_status vrm_build_neighbourhoods_noalloc(const vrm_params* p, const double* x, const double* y, int32_t n,
+                                            int32_t* nbr_count, int32_t* nbr_idx, uint8_t* seg_mask, int32_t* small,
+                                            int32_t* max_count, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,7 +66,9 @@ SIGNATURES = {
     "vrm_set_timing": (ctypes.c_int, [P, I32]),
     "vrm_stage_times": (ctypes.c_int, [P, P]),
     "vrm_launch_count": (ctypes.c_int64, []),
+    "vrm_build_neighbourhoods_noalloc": (ctypes.c_int, [P, P, P, I32, P, P, P, P, P, P]),
 }
+NOALLOC_MAX_N = 65536
 STAGES = ("reduce", "grid", "insert", "search", "lp_small", "lp_full", "apply")
 
 _LIB = None
@@ -95,6 +97,31 @@ def _lib_handle():
 def launch_count():
     """Kernels the library has launched in this process."""
     return int(_lib_handle().vrm_launch_count())
+
+
+def build_neighbourhoods_noalloc(x, y, n, h, r=0.5, R=2.0, k_cap=32, out=None, max_count=True):
+    """vrm_build_neighbourhoods_noalloc: neighbourhoods without a context and
+    without any allocation inside the library (scratch in a fixed device
+    array; n <= NOALLOC_MAX_N).  Output tensors may be passed in `out`."""
+    lib = _lib_handle()
+    p = Params()
+    lib.vrm_default_params(ctypes.byref(p))
+    p.h, p.r, p.R, p.k_cap = float(h), float(r), float(R), int(k_cap)
+    dev = x.device
+    o = out or {}
+    cnt = o.get("count", torch.empty(max(n, 1), dtype=torch.int32, device=dev))
+    idx = o.get("idx", torch.empty(max(n, 1) * k_cap, dtype=torch.int32, device=dev))
+    mask = o.get("mask", torch.empty(max(n, 1), dtype=torch.uint8, device=dev))
+    small = o.get("small", torch.empty(max(n, 1) * 8, dtype=torch.int32, device=dev))
+    mc = ctypes.c_int32(0)
+    st = lib.vrm_build_neighbourhoods_noalloc(
+        ctypes.byref(p), _ptr(x, torch.float64, "x", n), _ptr(y, torch.float64, "y", n), int(n),
+        _ptr(cnt, torch.int32, "nbr_count", n), _ptr(idx, torch.int32, "nbr_idx", n * k_cap),
+        _ptr(mask, torch.uint8, "seg_mask", n), _ptr(small, torch.int32, "small", 8 * n),
+        ctypes.byref(mc) if max_count else None, _stream())
+    if st != VRM_OK:
+        raise VRMError(st, "vrm_build_neighbourhoods_noalloc")
+    return dict(count=cnt, idx=idx, mask=mask, small=small, max_count=mc.value if max_count else None)
 
 
 def load_library(build_if_missing=False):
