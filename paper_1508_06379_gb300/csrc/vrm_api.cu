@@ -1,8 +1,17 @@
 // C ABI of the VRM library: parameter checks, context scratch, and the
 // order of the stages of one operator evaluation (Sec. 3.3, 3.5, 4):
 // growth control -> insertion -> neighbourhoods -> weights -> application.
+//
+// vrm_step runs every stage on the device with the counts kept in device
+// memory (StepState), so the whole step is one CUDA graph: it is captured
+// once per set of buffers (x, y, gamma_in, gamma_out, capacity), with the
+// insertion rounds as a conditional while node whose body is one round, and
+// replayed on later calls; n and dt travel in a host-to-device copy at the
+// head of the graph.  When graph capture is unavailable the same kernels run
+// eagerly, rounds unrolled with a host check between them.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -10,18 +19,10 @@
 
 using namespace vrm;
 
-namespace {
-
-struct Buf {
-  void* p = nullptr;
-};
-
-}  // namespace
-
 struct vrm::Scratch {
   int cap = 0;        // particles the buffers hold
   int ncell_cap = 0;  // cells of the grid
-  // grid
+  // particle grid
   Grid* grid = nullptr;
   int *cell_key = nullptr, *cell_rank = nullptr, *cell_count = nullptr, *cell_start = nullptr;
   double2* sorted_xy = nullptr;
@@ -35,25 +36,29 @@ struct vrm::Scratch {
   int* tie_rank = nullptr;
   uint8_t* diffused = nullptr;
   int* dlist = nullptr;
-  // insertion
-  uint8_t *mask = nullptr, *keep_flag = nullptr;
-  int *open_a = nullptr, *open_b = nullptr, *keep_pos = nullptr, *ccnt = nullptr, *ccpos = nullptr;
-  // proposals of one insertion round (grown on demand)
-  int cand_cap = 0, cand_ncell_cap = 0;
-  double *cx = nullptr, *cy = nullptr;
-  uint8_t* ckeep = nullptr;
-  int *capos = nullptr, *cscan_tmp = nullptr;
-  CandGrid cg = {};
+  // insertion: masks and the round buffers (proposals up to 8 per open particle)
+  uint8_t* mask = nullptr;
+  RoundBufs rb = {};
   // neighbourhoods and weights of vrm_step
   int *nbr_count = nullptr, *nbr_idx = nullptr, *small = nullptr, *cols = nullptr, *fail_list = nullptr;
   uint8_t *seg_mask = nullptr, *status = nullptr;
   double *f = nullptr, *fii = nullptr;
-  // counters
+  // counters and state
   DevStats* ds = nullptr;
-  int* counters = nullptr;  // [0] |D|, [1] n_open, [2] n_next, [3] open segments
-  DevStats* h_ds = nullptr;  // pinned
-  int* h_counters = nullptr; // pinned
-  Grid* h_grid = nullptr;    // pinned
+  int* counters = nullptr;  // [0] |D|, [1] first open list length
+  StepState* st = nullptr;
+  // pinned host mirrors
+  DevStats* h_ds = nullptr;
+  int* h_counters = nullptr;
+  Grid* h_grid = nullptr;
+  StepState* h_params = nullptr;  // n, capacity, dt, max_rounds of the next step
+  StepState* h_state = nullptr;   // state after the step
+};
+
+struct StepGraph {
+  cudaGraphExec_t exec = nullptr;
+  const void *x = nullptr, *y = nullptr, *gi = nullptr, *go = nullptr;
+  int cap = 0, timing = 0;
 };
 
 struct vrm_ctx {
@@ -66,6 +71,10 @@ struct vrm_ctx {
   int events_ready = 0;
   int stage_done[VRM_STAGE_COUNT] = {0};
   cudaEvent_t ev[VRM_STAGE_COUNT + 1];
+  // graph of vrm_step and the two streams used to capture it
+  int use_graph = 1;
+  StepGraph graph;
+  cudaStream_t cap_stream = nullptr, body_stream = nullptr;
 };
 
 namespace {
@@ -75,30 +84,24 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * (count > 0 ? count : 1));
 }
 
-void free_cand(Scratch& s) {
-  void* ptrs[] = {s.cx, s.cy, s.ckeep, s.capos, s.cscan_tmp, s.cg.grid, s.cg.cell_key, s.cg.cell_rank,
-                  s.cg.cell_count, s.cg.cell_start, s.cg.sorted_idx, s.cg.sorted_xy, s.cg.sorted_loc, s.cg.bbox};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
-  s.cx = s.cy = nullptr;
-  s.ckeep = nullptr;
-  s.capos = s.cscan_tmp = nullptr;
-  s.cg = CandGrid{};
-  s.cand_cap = s.cand_ncell_cap = 0;
+void drop_graph(vrm_ctx* ctx) {
+  if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
+  ctx->graph = StepGraph{};
 }
 
 void free_scratch(Scratch& s) {
-  free_cand(s);
+  RoundBufs& r = s.rb;
   void* ptrs[] = {s.grid, s.cell_key, s.cell_rank, s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc,
-                  s.sorted_idx, s.bbox,
-                  s.scan_tmp, s.pos, s.rstate, s.tie_flag, s.tie_rank, s.diffused, s.dlist, s.mask, s.keep_flag,
-                  s.open_a, s.open_b, s.keep_pos, s.ccnt, s.ccpos, s.nbr_count, s.nbr_idx, s.small, s.cols,
-                  s.fail_list, s.seg_mask, s.status, s.f, s.fii, s.ds, s.counters};
+                  s.sorted_idx, s.bbox, s.scan_tmp, s.pos, s.rstate, s.tie_flag, s.tie_rank, s.diffused, s.dlist,
+                  s.mask, r.open, r.open_next, r.cnt, r.cpos, r.keep_flag, r.keep_pos, r.cx, r.cy, r.keep, r.apos,
+                  r.cg.grid, r.cg.cell_key, r.cg.cell_rank, r.cg.cell_count, r.cg.cell_start, r.cg.sorted_idx,
+                  r.cg.sorted_xy, r.cg.sorted_loc, r.cg.bbox, r.scan_tmp, s.nbr_count, s.nbr_idx, s.small, s.cols,
+                  s.fail_list, s.seg_mask, s.status, s.f, s.fii, s.ds, s.counters, s.st};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  if (s.h_ds) cudaFreeHost(s.h_ds);
-  if (s.h_counters) cudaFreeHost(s.h_counters);
-  if (s.h_grid) cudaFreeHost(s.h_grid);
+  void* hp[] = {s.h_ds, s.h_counters, s.h_grid, s.h_params, s.h_state};
+  for (void* p : hp)
+    if (p) cudaFreeHost(p);
   Scratch empty;
   s = empty;
 }
@@ -108,17 +111,20 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   Scratch& s = ctx->s;
   if (cap <= s.cap && s.ds) return cudaSuccess;
   cudaStreamSynchronize(st);
+  drop_graph(ctx);
   long want = cap;
   if (s.cap > 0 && want < (long)s.cap + s.cap / 4) want = (long)s.cap + s.cap / 4;
   if (want < 1024) want = 1024;
-  if (want > 0x7FFFFFF0L) want = 0x7FFFFFF0L;
+  if (want > 0x0FFFFFF0L) want = 0x0FFFFFF0L;  // 8 proposals per particle must fit int32
   free_scratch(s);
   const int n = (int)want;
+  const long n8 = 8L * n;
   const int k = ctx->p.k_cap;
   const long ncell = 2 * (long)n + 1024;
   s.cap = n;
   s.ncell_cap = (int)ncell;
   cudaError_t e = cudaSuccess;
+  RoundBufs& r = s.rb;
 #define VRM_ALLOC(ptr, count) \
   if (e == cudaSuccess) e = dalloc(&(ptr), (size_t)(count))
   VRM_ALLOC(s.grid, 1);
@@ -138,12 +144,27 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.diffused, n);
   VRM_ALLOC(s.dlist, n);
   VRM_ALLOC(s.mask, n);
-  VRM_ALLOC(s.keep_flag, n);
-  VRM_ALLOC(s.open_a, n);
-  VRM_ALLOC(s.open_b, n);
-  VRM_ALLOC(s.keep_pos, (long)n + 1);
-  VRM_ALLOC(s.ccnt, n);
-  VRM_ALLOC(s.ccpos, (long)n + 1);
+  VRM_ALLOC(r.open, n);
+  VRM_ALLOC(r.open_next, n);
+  VRM_ALLOC(r.cnt, n);
+  VRM_ALLOC(r.cpos, (long)n + 1);
+  VRM_ALLOC(r.keep_flag, n);
+  VRM_ALLOC(r.keep_pos, (long)n + 1);
+  VRM_ALLOC(r.cx, n8);
+  VRM_ALLOC(r.cy, n8);
+  VRM_ALLOC(r.keep, n8);
+  VRM_ALLOC(r.apos, n8 + 1);
+  VRM_ALLOC(r.cg.grid, 1);
+  VRM_ALLOC(r.cg.cell_key, n8);
+  VRM_ALLOC(r.cg.cell_rank, n8);
+  VRM_ALLOC(r.cg.cell_count, ncell);
+  VRM_ALLOC(r.cg.cell_start, ncell + 1);
+  VRM_ALLOC(r.cg.sorted_idx, n8);
+  VRM_ALLOC(r.cg.sorted_xy, n8);
+  VRM_ALLOC(r.cg.sorted_loc, n8);
+  VRM_ALLOC(r.cg.bbox, 8);
+  VRM_ALLOC(r.scan_tmp, scan_tmp_ints((int)(n8 > ncell ? n8 : ncell)) + 16);
+  r.ncell_cap = (int)ncell;
   VRM_ALLOC(s.nbr_count, n);
   VRM_ALLOC(s.nbr_idx, (long)n * k);
   VRM_ALLOC(s.small, (long)n * 8);
@@ -155,10 +176,13 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.fii, n);
   VRM_ALLOC(s.ds, 1);
   VRM_ALLOC(s.counters, 8);
+  VRM_ALLOC(s.st, 1);
 #undef VRM_ALLOC
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_ds, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_counters, sizeof(int) * 8);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_grid, sizeof(Grid));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_params, sizeof(StepState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_state, sizeof(StepState));
   if (e != cudaSuccess) {
     free_scratch(s);
     cudaGetLastError();
@@ -166,44 +190,9 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   return e;
 }
 
-// Proposal buffers for n_cand proposals (grown by 50% steps, never shrunk).
-cudaError_t ensure_cand(Scratch& s, int n_cand, cudaStream_t st) {
-  if (n_cand <= s.cand_cap && s.cx) return cudaSuccess;
-  cudaStreamSynchronize(st);
-  long want = n_cand;
-  if (want < (long)s.cand_cap + s.cand_cap / 2) want = (long)s.cand_cap + s.cand_cap / 2;
-  if (want < 4096) want = 4096;
-  if (want > 0x7FFFFFF0L) want = 0x7FFFFFF0L;
-  free_cand(s);
-  const long ncell = 2 * want + 1024;
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = dalloc(&s.cx, want);
-  if (e == cudaSuccess) e = dalloc(&s.cy, want);
-  if (e == cudaSuccess) e = dalloc(&s.ckeep, want);
-  if (e == cudaSuccess) e = dalloc(&s.capos, want + 1);
-  if (e == cudaSuccess) e = dalloc(&s.cscan_tmp, scan_tmp_ints((int)ncell) + 16);
-  if (e == cudaSuccess) e = dalloc(&s.cg.grid, 1);
-  if (e == cudaSuccess) e = dalloc(&s.cg.cell_key, want);
-  if (e == cudaSuccess) e = dalloc(&s.cg.cell_rank, want);
-  if (e == cudaSuccess) e = dalloc(&s.cg.cell_count, ncell);
-  if (e == cudaSuccess) e = dalloc(&s.cg.cell_start, ncell + 1);
-  if (e == cudaSuccess) e = dalloc(&s.cg.sorted_idx, want);
-  if (e == cudaSuccess) e = dalloc(&s.cg.sorted_xy, want);
-  if (e == cudaSuccess) e = dalloc(&s.cg.sorted_loc, want);
-  if (e == cudaSuccess) e = dalloc(&s.cg.bbox, 8);
-  if (e != cudaSuccess) {
-    free_cand(s);
-    cudaGetLastError();
-    return e;
-  }
-  s.cand_cap = (int)want;
-  s.cand_ncell_cap = (int)ncell;
-  return cudaSuccess;
-}
-
-#define VRM_CUDA(call)                       \
-  do {                                       \
-    cudaError_t _e = (call);                 \
+#define VRM_CUDA(call)                          \
+  do {                                          \
+    cudaError_t _e = (call);                    \
     if (_e != cudaSuccess) return VRM_ERR_CUDA; \
   } while (0)
 
@@ -257,6 +246,7 @@ cudaError_t read_back(vrm_ctx* ctx, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(s.h_ds, s.ds, sizeof(DevStats), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_counters, s.counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_grid, s.grid, sizeof(Grid), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s.h_state, s.st, sizeof(StepState), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   return e;
 }
@@ -265,76 +255,6 @@ double ratio_from_bits(unsigned long long b) {
   double d;
   memcpy(&d, &b, sizeof d);
   return d;
-}
-
-cudaError_t mark(vrm_ctx* ctx, int k, cudaStream_t st);
-
-// Growth control + insertion on x, y (capacity entries, n given).  Leaves the
-// diffused flags in `diffused` (capacity), the diffused list in s.dlist with
-// its count in s.counters[0], and *n_cur = n'.
-vrm_status stage_insert_reduce(vrm_ctx* ctx, double* x, double* y, int n, int capacity, const double* gamma,
-                               uint8_t* diffused, int* n_cur_out, vrm_stats* acc_stats, cudaStream_t st) {
-  Scratch& s = ctx->s;
-  const Consts& c = ctx->c;
-  VRM_CUDA(mark(ctx, VRM_STAGE_REDUCE, st));
-  VRM_CUDA(reduce_select(gamma, n, c.c_bound, diffused, s.rstate, s.tie_flag, s.tie_rank, s.scan_tmp, s.ds, st));
-  if (capacity > n) VRM_CUDA(cudaMemsetAsync(diffused + n, 0, (size_t)(capacity - n), st));
-  VRM_CUDA(compact_flags(diffused, n, s.dlist, s.counters + 0, s.pos, s.scan_tmp, st));
-  VRM_CUDA(mark(ctx, VRM_STAGE_GRID, st));
-  VRM_CUDA(grid_build(x, y, n, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank, s.cell_count,
-                      s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp, st));
-  VRM_CUDA(search_masks(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, n, diffused, s.mask, st));
-  VRM_CUDA(open_list(s.dlist, s.counters + 0, n, s.mask, s.keep_flag, s.pos, s.open_a, s.counters + 1, s.scan_tmp,
-                     st));
-  VRM_CUDA(mark(ctx, VRM_STAGE_INSERT, st));
-  VRM_CUDA(read_back(ctx, st));
-  if (s.h_grid->nonfinite || s.h_ds->nonfinite) return VRM_ERR_ARG;
-  int n_open = s.h_counters[1];
-  int n_cur = n;
-  int rounds = 0;
-  long open_segments = 0;
-  for (int round = 0; n_open > 0; ++round) {
-    if (round == c.max_rounds) {
-      VRM_CUDA(count_open_segments(s.open_a, n_open, s.mask, s.counters + 3, st));
-      VRM_CUDA(read_back(ctx, st));
-      open_segments = s.h_counters[3];
-      break;
-    }
-    VRM_CUDA(insert_count(s.open_a, n_open, s.mask, s.ccnt, s.ccpos, s.scan_tmp, st));
-    VRM_CUDA(cudaMemcpyAsync(s.h_counters + 4, s.ccpos + n_open, sizeof(int), cudaMemcpyDeviceToHost, st));
-    VRM_CUDA(cudaStreamSynchronize(st));
-    const int n_cand = s.h_counters[4];
-    VRM_CUDA(ensure_cand(s, n_cand, st));
-    VRM_CUDA(insert_propose(c, s.open_a, n_open, s.mask, s.ccpos, x, y, s.cx, s.cy, n_cand, s.cand_ncell_cap, s.cg,
-                            s.ckeep, s.capos, s.cscan_tmp, st));
-    VRM_CUDA(cudaMemcpyAsync(s.h_counters + 5, s.capos + n_cand, sizeof(int), cudaMemcpyDeviceToHost, st));
-    VRM_CUDA(cudaStreamSynchronize(st));
-    const int accepted = s.h_counters[5];
-    if ((long)n_cur + accepted > capacity) {
-      if (acc_stats) acc_stats->n_out = (long)n_cur + accepted;
-      return VRM_ERR_CAPACITY;
-    }
-    VRM_CUDA(insert_commit(c, s.open_a, n_open, s.cx, s.cy, n_cand, s.cg, s.ckeep, s.capos, n_cur, x, y, s.mask,
-                           s.keep_flag, s.keep_pos, s.open_b, s.counters + 2, s.scan_tmp, st));
-    VRM_CUDA(cudaMemcpyAsync(s.h_counters + 2, s.counters + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
-    VRM_CUDA(cudaStreamSynchronize(st));
-    n_cur += accepted;
-    if (accepted > 0) ++rounds;
-    int* t = s.open_a;
-    s.open_a = s.open_b;
-    s.open_b = t;
-    n_open = s.h_counters[2];
-  }
-  if (acc_stats) {
-    acc_stats->n_in = n;
-    acc_stats->n_out = n_cur;
-    acc_stats->n_diffused = s.h_counters[0];
-    acc_stats->n_inserted = n_cur - n;
-    acc_stats->open_segments = open_segments;
-    acc_stats->rounds = rounds;
-  }
-  *n_cur_out = n_cur;
-  return VRM_OK;
 }
 
 bool bad_ptr(const void* p, int n) { return n > 0 && p == nullptr; }
@@ -346,6 +266,189 @@ cudaError_t mark(vrm_ctx* ctx, int k, cudaStream_t st) {
   if (!ctx->timing) return cudaSuccess;
   if (k > 0 && k <= VRM_STAGE_COUNT) ctx->stage_done[k - 1] = 1;
   return cudaEventRecord(ctx->ev[k], st);
+}
+
+__global__ void k_clear_tail(uint8_t* __restrict__ a, const StepState* __restrict__ st, int cap) {
+  const int n = st->n;
+  for (long i = (long)n + blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (long)gridDim.x * blockDim.x) a[i] = 0;
+}
+
+// Growth control, grid of the given cloud, segment masks, first open list
+// (the rounds follow).  n is read from s.st->n.
+cudaError_t enqueue_front(vrm_ctx* ctx, double* x, double* y, int cap, const double* gamma, uint8_t* diffused,
+                          cudaStream_t st) {
+  Scratch& s = ctx->s;
+  const Consts& c = ctx->c;
+  const int* n_dev = &s.st->n;
+  cudaError_t e;
+  if ((e = mark(ctx, VRM_STAGE_REDUCE, st)) != cudaSuccess) return e;
+  if ((e = reduce_select_dev(gamma, cap, n_dev, c.c_bound, diffused, s.rstate, s.tie_flag, s.tie_rank, s.scan_tmp,
+                             s.ds, st)) != cudaSuccess)
+    return e;
+  k_clear_tail<<<4 * sm_count(), kBlock, 0, st>>>(diffused, s.st, cap); note_launch();
+  if ((e = compact_flags_dev(diffused, cap, n_dev, s.dlist, s.counters + 0, s.pos, s.scan_tmp, st)) != cudaSuccess)
+    return e;
+  if ((e = mark(ctx, VRM_STAGE_GRID, st)) != cudaSuccess) return e;
+  if ((e = grid_build_dev(x, y, cap, n_dev, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank,
+                          s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
+                          st)) != cudaSuccess)
+    return e;
+  if ((e = search_masks_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, cap, n_dev, diffused,
+                            s.mask, st)) != cudaSuccess)
+    return e;
+  if ((e = open_list(s.dlist, s.counters + 0, cap, s.mask, s.rb.keep_flag, s.pos, s.rb.open, s.counters + 1,
+                     s.scan_tmp, st)) != cudaSuccess)
+    return e;
+  return mark(ctx, VRM_STAGE_INSERT, st);
+}
+
+// Final grid, neighbourhoods, weights, application + Euler, statistics copy.
+cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const double* gamma_in, double* gamma_out,
+                         cudaStream_t st) {
+  Scratch& s = ctx->s;
+  const Consts& c = ctx->c;
+  const int* n_cur = &s.st->n_cur;
+  cudaError_t e;
+  if ((e = rounds_finish(s.st, s.rb.open, s.mask, cap, st)) != cudaSuccess) return e;
+  if ((e = mark(ctx, VRM_STAGE_SEARCH, st)) != cudaSuccess) return e;
+  if ((e = grid_build_dev(x, y, cap, n_cur, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank,
+                          s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
+                          st)) != cudaSuccess)
+    return e;
+  if ((e = search_all_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, cap, n_cur, s.nbr_count,
+                          s.nbr_idx, s.seg_mask, s.small, s.ds, st)) != cudaSuccess)
+    return e;
+  if ((e = mark(ctx, VRM_STAGE_LP_SMALL, st)) != cudaSuccess) return e;
+  if ((e = lp_small(c, x, y, s.dlist, s.counters + 0, cap, s.small, s.cols, s.f, s.fii, s.status, s.fail_list, s.ds,
+                    0.0, st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
+    return e;
+  if ((e = mark(ctx, VRM_STAGE_LP_FULL, st)) != cudaSuccess) return e;
+  if ((e = lp_full(c, x, y, s.fail_list, &s.ds->n_fail, cap, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii, s.status,
+                   s.ds, 0.0, st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
+    return e;
+  if ((e = mark(ctx, VRM_STAGE_APPLY, st)) != cudaSuccess) return e;
+  if ((e = apply_gather_dev(c, cap, n_cur, cap, &s.st->n, gamma_in, s.diffused, s.nbr_count, s.nbr_idx, s.cols, s.f,
+                            s.fii, s.sorted_idx, nullptr, gamma_out, 0.0, &s.st->dt, st)) != cudaSuccess)
+    return e;
+  if ((e = mark(ctx, VRM_STAGE_COUNT, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(s.h_ds, s.ds, sizeof(DevStats), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(s.h_counters, s.counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(s.h_grid, s.grid, sizeof(Grid), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  return cudaMemcpyAsync(s.h_state, s.st, sizeof(StepState), cudaMemcpyDeviceToHost, st);
+}
+
+cudaError_t enqueue_head(vrm_ctx* ctx, cudaStream_t st) {
+  Scratch& s = ctx->s;
+  cudaError_t e = cudaMemcpyAsync(s.st, s.h_params, sizeof(StepState), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.ds, 0, sizeof(DevStats), st);
+  return e;
+}
+
+// Captures the whole step on the context's streams; the insertion rounds are
+// a conditional while node.  Returns false (graph left empty) on failure.
+bool capture_step(vrm_ctx* ctx, double* x, double* y, int cap, const double* gamma_in, double* gamma_out) {
+  Scratch& s = ctx->s;
+  if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return false;
+  if (!ctx->body_stream && cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return false;
+  cudaStream_t cs = ctx->cap_stream;
+  cudaGraph_t g = nullptr;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  const bool capturing = ok;
+  ok = ok && enqueue_head(ctx, cs) == cudaSuccess;
+  ok = ok && enqueue_front(ctx, x, y, cap, gamma_in, s.diffused, cs) == cudaSuccess;
+  cudaGraphConditionalHandle handle = 0;
+  if (ok) {
+    cudaStreamCaptureStatus status;
+    cudaGraph_t cg = nullptr;
+    ok = cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, nullptr, nullptr, nullptr) == cudaSuccess;
+    ok = ok && cudaGraphConditionalHandleCreate(&handle, cg, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  }
+  ok = ok && rounds_init(s.st, s.counters + 1, handle, true, cs) == cudaSuccess;
+  if (ok) {
+    cudaStreamCaptureStatus status;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    ok = cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, &deps, nullptr, &ndeps) == cudaSuccess;
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    ok = ok && cudaGraphAddNode(&node, cg, deps, nullptr, ndeps, &cp) == cudaSuccess;
+    ok = ok && cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                   cudaSuccess;
+    if (ok) {
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      ok = cudaStreamBeginCaptureToGraph(ctx->body_stream, body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        ok = round_body(ctx->c, s.st, s.grid, s.rb, cap, s.mask, x, y, handle, true, ctx->body_stream) ==
+             cudaSuccess;
+        cudaGraph_t got = nullptr;
+        const bool ended = cudaStreamEndCapture(ctx->body_stream, &got) == cudaSuccess;
+        ok = ok && ended;
+      }
+    }
+  }
+  ok = ok && enqueue_back(ctx, x, y, cap, gamma_in, gamma_out, cs) == cudaSuccess;
+  if (capturing) {
+    const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
+    ok = ok && ended && g;
+  }
+  cudaGraphExec_t exec = nullptr;
+  ok = ok && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  if (!ok) {
+    if (exec) cudaGraphExecDestroy(exec);
+    return false;
+  }
+  drop_graph(ctx);
+  ctx->graph.exec = exec;
+  ctx->graph.x = x;
+  ctx->graph.y = y;
+  ctx->graph.gi = gamma_in;
+  ctx->graph.go = gamma_out;
+  ctx->graph.cap = cap;
+  ctx->graph.timing = ctx->timing;
+  return true;
+}
+
+// The same step without a graph: rounds unrolled, with a host check of the
+// open list between rounds.  back = false stops after insertion.
+vrm_status run_step_eager(vrm_ctx* ctx, double* x, double* y, int cap, const double* gamma_in, double* gamma_out,
+                          uint8_t* diffused, bool back, cudaStream_t st) {
+  Scratch& s = ctx->s;
+  VRM_CUDA(enqueue_head(ctx, st));
+  VRM_CUDA(enqueue_front(ctx, x, y, cap, gamma_in, diffused, st));
+  VRM_CUDA(rounds_init(s.st, s.counters + 1, 0, false, st));
+  for (int r = 0; r < ctx->p.max_rounds; ++r) {
+    VRM_CUDA(cudaMemcpyAsync(s.h_state, s.st, sizeof(StepState), cudaMemcpyDeviceToHost, st));
+    VRM_CUDA(cudaStreamSynchronize(st));
+    if (s.h_state->n_open == 0) break;
+    VRM_CUDA(round_body(ctx->c, s.st, s.grid, s.rb, cap, s.mask, x, y, 0, false, st));
+  }
+  if (back) {
+    VRM_CUDA(enqueue_back(ctx, x, y, cap, gamma_in, gamma_out, st));
+  } else {
+    VRM_CUDA(rounds_finish(s.st, s.rb.open, s.mask, cap, st));
+  }
+  return VRM_OK;
+}
+
+void fill_front_stats(vrm_ctx* ctx, int n, vrm_stats* st) {
+  const Scratch& s = ctx->s;
+  const StepState& S = *s.h_state;
+  st->n_in = n;
+  st->n_out = S.overflow ? S.n_needed : S.n_cur;
+  st->n_diffused = s.h_counters[0];
+  st->n_inserted = S.n_cur - n;
+  st->open_segments = S.open_segments;
+  st->rounds = S.rounds_appended;
 }
 
 }  // namespace
@@ -387,6 +490,8 @@ vrm_status vrm_create(const vrm_params* p, vrm_ctx** out) {
   if (!ctx) return VRM_ERR_CUDA;
   ctx->p = *p;
   fill_consts(*p, ctx->c);
+  const char* env = getenv("VRM_NO_GRAPH");
+  ctx->use_graph = !(env && env[0] == '1');
   if (cudaGetDevice(&ctx->device) != cudaSuccess) {
     delete ctx;
     return VRM_ERR_CUDA;
@@ -397,9 +502,12 @@ vrm_status vrm_create(const vrm_params* p, vrm_ctx** out) {
 
 void vrm_destroy(vrm_ctx* ctx) {
   if (!ctx) return;
+  drop_graph(ctx);
   free_scratch(ctx->s);
   if (ctx->events_ready)
     for (int k = 0; k <= VRM_STAGE_COUNT; ++k) cudaEventDestroy(ctx->ev[k]);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
   delete ctx;
 }
 
@@ -440,12 +548,27 @@ vrm_status vrm_insert_reduce(vrm_ctx* ctx, double* x, double* y, int32_t n, int3
     *n_out = 0;
     return VRM_OK;
   }
+  Scratch& s = ctx->s;
   VRM_CUDA(ensure_scratch(ctx, capacity, stream));
-  VRM_CUDA(cudaMemsetAsync(ctx->s.ds, 0, sizeof(DevStats), stream));
-  int n_cur = n;
-  vrm_status st = stage_insert_reduce(ctx, x, y, n, capacity, gamma, diffused, &n_cur, stats, stream);
-  if (st != VRM_OK) return st;
-  *n_out = n_cur;
+  VRM_CUDA(cudaStreamSynchronize(stream));
+  StepState P;
+  memset(&P, 0, sizeof(P));
+  P.n = n;
+  P.capacity = capacity;
+  P.max_rounds = ctx->p.max_rounds;
+  *s.h_params = P;
+  const int timing = ctx->timing;
+  ctx->timing = 0;
+  vrm_status r = run_step_eager(ctx, x, y, capacity, gamma, nullptr, diffused, false, stream);
+  ctx->timing = timing;
+  if (r != VRM_OK) return r;
+  VRM_CUDA(read_back(ctx, stream));
+  if (s.h_grid->nonfinite || s.h_ds->nonfinite) return VRM_ERR_ARG;
+  vrm_stats local;
+  vrm_stats* st = stats ? stats : &local;
+  fill_front_stats(ctx, n, st);
+  if (s.h_state->overflow) return VRM_ERR_CAPACITY;
+  *n_out = s.h_state->n_cur;
   return VRM_OK;
 }
 
@@ -538,32 +661,40 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
     return VRM_OK;
   }
   Scratch& s = ctx->s;
-  const Consts& c = ctx->c;
   VRM_CUDA(ensure_scratch(ctx, capacity, stream));
-  VRM_CUDA(cudaMemsetAsync(s.ds, 0, sizeof(DevStats), stream));
-  int n2 = n;
+  // the pinned parameter block is read by the step's head copy: wait for any
+  // earlier step on this stream before rewriting it
+  VRM_CUDA(cudaStreamSynchronize(stream));
+  StepState P;
+  memset(&P, 0, sizeof(P));
+  P.n = n;
+  P.capacity = capacity;
+  P.dt = dt;
+  P.max_rounds = ctx->p.max_rounds;
+  *s.h_params = P;
   if (ctx->timing)
     for (int k = 0; k < VRM_STAGE_COUNT; ++k) ctx->stage_done[k] = 0;
-  vrm_status r = stage_insert_reduce(ctx, x, y, n, capacity, gamma_in, s.diffused, &n2, st, stream);
-  if (r != VRM_OK) return r;
-  VRM_CUDA(mark(ctx, VRM_STAGE_SEARCH, stream));
-  if (n2 > n)
-    VRM_CUDA(grid_build(x, y, n2, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank, s.cell_count,
-                        s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp, stream));
-  VRM_CUDA(search_all(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, n2, s.nbr_count, s.nbr_idx,
-                      s.seg_mask, s.small, s.ds, stream));
-  const double nu_dt = ctx->p.nu * dt;
-  VRM_CUDA(mark(ctx, VRM_STAGE_LP_SMALL, stream));
-  VRM_CUDA(lp_small(c, x, y, s.dlist, s.counters + 0, n, s.small, s.cols, s.f, s.fii, s.status, s.fail_list, s.ds,
-                    nu_dt, stream));
-  VRM_CUDA(mark(ctx, VRM_STAGE_LP_FULL, stream));
-  VRM_CUDA(lp_full(c, x, y, s.fail_list, &s.ds->n_fail, n, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii, s.status,
-                   s.ds, nu_dt, stream));
-  VRM_CUDA(mark(ctx, VRM_STAGE_APPLY, stream));
-  VRM_CUDA(apply_gather(c, n2, n, gamma_in, s.diffused, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii, s.sorted_idx,
-                        nullptr, gamma_out, dt, stream));
-  VRM_CUDA(mark(ctx, VRM_STAGE_COUNT, stream));
-  VRM_CUDA(read_back(ctx, stream));
+  bool launched = false;
+  if (ctx->use_graph) {
+    const StepGraph& G = ctx->graph;
+    const bool hit = G.exec && G.x == x && G.y == y && G.gi == gamma_in && G.go == gamma_out && G.cap == capacity &&
+                     G.timing == ctx->timing;
+    if (!hit && !capture_step(ctx, x, y, capacity, gamma_in, gamma_out)) ctx->use_graph = 0;
+    if (ctx->use_graph) {
+      // the captured event nodes record every stage boundary
+      if (ctx->timing)
+        for (int k = 0; k < VRM_STAGE_COUNT; ++k) ctx->stage_done[k] = 1;
+      VRM_CUDA(cudaGraphLaunch(ctx->graph.exec, stream));
+      launched = true;
+    }
+  }
+  if (!launched) {
+    vrm_status r = run_step_eager(ctx, x, y, capacity, gamma_in, gamma_out, s.diffused, true, stream);
+    if (r != VRM_OK) return r;
+  }
+  VRM_CUDA(cudaStreamSynchronize(stream));
+  if (s.h_grid->nonfinite || s.h_ds->nonfinite) return VRM_ERR_ARG;
+  fill_front_stats(ctx, n, st);
   st->small_ok = s.h_ds->small_ok;
   st->full_ok = s.h_ds->full_ok;
   st->no_stencil = s.h_ds->no_stencil;
@@ -574,7 +705,8 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
   st->lp_small_pivots = (int64_t)s.h_ds->lp_small_pivots;
   st->lp_full_solved = s.h_ds->lp_full_solved;
   st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
-  *n_out = n2;
+  if (s.h_state->overflow) return VRM_ERR_CAPACITY;
+  *n_out = s.h_state->n_cur;
   if (s.h_ds->max_count > ctx->p.k_cap) return VRM_ERR_CAPACITY;
   return VRM_OK;
 }

@@ -15,13 +15,17 @@
 
 namespace vrm {
 
-__global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, int n_gamma, const double* __restrict__ gamma,
+__global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __restrict__ n_dev, int n_gamma,
+                                                  const int* __restrict__ n_gamma_dev, const double* __restrict__ gamma,
                                                   const uint8_t* __restrict__ diffused,
                                                   const int* __restrict__ nbr_count, const int* __restrict__ nbr_idx,
                                                   const int* __restrict__ cols, const double* __restrict__ f,
                                                   const double* __restrict__ fii, const int* __restrict__ order,
                                                   double* __restrict__ dgamma, double* __restrict__ gamma_out,
-                                                  double dt) {
+                                                  double dt, const double* __restrict__ dt_dev) {
+  if (n_dev) n = *n_dev;
+  if (n_gamma_dev) n_gamma = *n_gamma_dev;
+  if (dt_dev) dt = *dt_dev;
   for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
     const int j = order ? order[p] : (int)p;
     const int cnt0 = nbr_count[j];
@@ -59,14 +63,23 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, int n_gamma, 
   }
 }
 
+cudaError_t apply_gather_dev(const Consts& c, int n_bound, const int* n_dev, int n_gamma, const int* n_gamma_dev,
+                             const double* gamma, const uint8_t* diffused, const int* nbr_count, const int* nbr_idx,
+                             const int* cols, const double* f, const double* fii, const int* order, double* dgamma,
+                             double* gamma_out, double dt, const double* dt_dev, cudaStream_t s) {
+  if (n_bound <= 0) return cudaSuccess;
+  int blocks = (n_bound + kBlock - 1) / kBlock;
+  k_apply<<<blocks, kBlock, 0, s>>>(c, n_bound, n_dev, n_gamma, n_gamma_dev, gamma, diffused, nbr_count, nbr_idx, cols,
+                                    f, fii, order, dgamma, gamma_out, dt, dt_dev);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t apply_gather(const Consts& c, int n, int n_gamma, const double* gamma, const uint8_t* diffused,
                          const int* nbr_count, const int* nbr_idx, const int* cols, const double* f, const double* fii,
                          const int* order, double* dgamma, double* gamma_out, double dt, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  int blocks = (n + kBlock - 1) / kBlock;
-  k_apply<<<blocks, kBlock, 0, s>>>(c, n, n_gamma, gamma, diffused, nbr_count, nbr_idx, cols, f, fii, order, dgamma,
-                                    gamma_out, dt); note_launch();
-  return cudaGetLastError();
+  return apply_gather_dev(c, n, nullptr, n_gamma, nullptr, gamma, diffused, nbr_count, nbr_idx, cols, f, fii, order,
+                          dgamma, gamma_out, dt, nullptr, s);
 }
 
 }  // namespace vrm

@@ -77,20 +77,30 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
   return r;
 }
 
+// Tile sums; tiles are visited grid-stride so that the grid can be sized by
+// an upper bound while the count itself comes from device memory (n_dev).
 template <typename T>
-__global__ void k_tile_sums(const T* __restrict__ in, int n, int* __restrict__ tile_sums) {
-  long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * kScanItems;
-  int s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) s += load_count(in, base + k, n);
+__global__ void k_tile_sums(const T* __restrict__ in, int n, const int* __restrict__ n_dev,
+                            int* __restrict__ tile_sums) {
+  if (n_dev) n = *n_dev;
+  const int ntiles = (n + kScanTile - 1) / kScanTile;
   __shared__ int total;
-  block_exclusive_scan(s, &total);
-  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    long base = (long)t * kScanTile + (long)threadIdx.x * kScanItems;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) s += load_count(in, base + k, n);
+    block_exclusive_scan(s, &total);
+    if (threadIdx.x == 0) tile_sums[t] = total;
+    __syncthreads();
+  }
 }
 
 // Single block: exclusive scan of the tile sums in place; tile_sums[ntiles]
 // receives the grand total.
-__global__ void k_scan_tile_sums(int* __restrict__ tile_sums, int ntiles) {
+__global__ void k_scan_tile_sums(int* __restrict__ tile_sums, int n, const int* __restrict__ n_dev) {
+  if (n_dev) n = *n_dev;
+  const int ntiles = (n + kScanTile - 1) / kScanTile;
   __shared__ int total;
   int carry = 0;
   for (int base = 0; base < ntiles; base += kScanThreads) {
@@ -105,41 +115,58 @@ __global__ void k_scan_tile_sums(int* __restrict__ tile_sums, int ntiles) {
 }
 
 template <typename T>
-__global__ void k_tile_scan(const T* __restrict__ in, int n, const int* __restrict__ tile_sums, int ntiles,
-                            int* __restrict__ out) {
-  long base = (long)blockIdx.x * kScanTile + (long)threadIdx.x * kScanItems;
-  int v[kScanItems];
-  int s = 0;
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    v[k] = load_count(in, base + k, n);
-    s += v[k];
-  }
+__global__ void k_tile_scan(const T* __restrict__ in, int n, const int* __restrict__ n_dev,
+                            const int* __restrict__ tile_sums, int* __restrict__ out) {
+  if (n_dev) n = *n_dev;
+  const int ntiles = (n + kScanTile - 1) / kScanTile;
   __shared__ int total;
-  int ex = block_exclusive_scan(s, &total) + tile_sums[blockIdx.x];
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    long base = (long)t * kScanTile + (long)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    if (base + k < n) out[base + k] = ex;
-    ex += v[k];
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = load_count(in, base + k, n);
+      s += v[k];
+    }
+    int ex = block_exclusive_scan(s, &total) + tile_sums[t];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (base + k < n) out[base + k] = ex;
+      ex += v[k];
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_sums[ntiles];
 }
 
+static int scan_grid(int n_bound) {
+  int ntiles = (n_bound + kScanTile - 1) / kScanTile;
+  int cap = 4 * sm_count();
+  return ntiles < 1 ? 1 : (ntiles < cap ? ntiles : cap);
+}
+
 template <typename T>
-static cudaError_t scan_impl(const T* in, int* out, int n, int* tmp, cudaStream_t s) {
-  if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int), s);
-  int ntiles = (n + kScanTile - 1) / kScanTile;
-  k_tile_sums<T><<<ntiles, kScanThreads, 0, s>>>(in, n, tmp); note_launch();
-  k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(tmp, ntiles); note_launch();
-  k_tile_scan<T><<<ntiles, kScanThreads, 0, s>>>(in, n, tmp, ntiles, out); note_launch();
+static cudaError_t scan_impl(const T* in, int* out, int n, const int* n_dev, int* tmp, cudaStream_t s) {
+  if (!n_dev && n <= 0) return cudaMemsetAsync(out, 0, sizeof(int), s);
+  const int g = scan_grid(n);
+  k_tile_sums<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp); note_launch();
+  k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(tmp, n, n_dev); note_launch();
+  k_tile_scan<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp, out); note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t scan_exclusive_i32(const int* in, int* out, int n, int* tmp, cudaStream_t s) {
-  return scan_impl<int>(in, out, n, tmp, s);
+  return scan_impl<int>(in, out, n, nullptr, tmp, s);
 }
 cudaError_t scan_exclusive_u8(const uint8_t* in, int* out, int n, int* tmp, cudaStream_t s) {
-  return scan_impl<uint8_t>(in, out, n, tmp, s);
+  return scan_impl<uint8_t>(in, out, n, nullptr, tmp, s);
+}
+cudaError_t scan_exclusive_i32_dev(const int* in, int* out, int n_bound, const int* n_dev, int* tmp, cudaStream_t s) {
+  return scan_impl<int>(in, out, n_bound, n_dev, tmp, s);
+}
+cudaError_t scan_exclusive_u8_dev(const uint8_t* in, int* out, int n_bound, const int* n_dev, int* tmp,
+                                  cudaStream_t s) {
+  return scan_impl<uint8_t>(in, out, n_bound, n_dev, tmp, s);
 }
 
 __global__ void k_compact(const uint8_t* __restrict__ flags, int n, const int* __restrict__ pos,
@@ -168,8 +195,9 @@ __global__ void k_bbox_init(unsigned long long* bb) {
   bb[4] = 0ull;   // non-finite flag
 }
 
-__global__ void k_bbox(const double* __restrict__ x, const double* __restrict__ y, int n,
+__global__ void k_bbox(const double* __restrict__ x, const double* __restrict__ y, int n, const int* __restrict__ n_dev,
                        unsigned long long* __restrict__ bb) {
+  if (n_dev) n = *n_dev;
   unsigned long long mnx = ~0ull, mxx = 0, mny = ~0ull, mxy = 0;
   int bad = 0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -206,8 +234,9 @@ __global__ void k_bbox(const double* __restrict__ x, const double* __restrict__ 
   }
 }
 
-__global__ void k_grid_finalize(const unsigned long long* __restrict__ bb, int n, double Rh, double lo2, double hi2,
-                                int ncell_cap, Grid* __restrict__ g) {
+__global__ void k_grid_finalize(const unsigned long long* __restrict__ bb, int n, const int* __restrict__ n_dev,
+                                double Rh, double lo2, double hi2, int ncell_cap, Grid* __restrict__ g) {
+  if (n_dev) n = *n_dev;
   Grid G;
   G.nonfinite = (int)bb[4];
   double x0 = 0, x1 = 0, y0 = 0, y1 = 0;
@@ -242,8 +271,10 @@ __global__ void k_grid_finalize(const unsigned long long* __restrict__ bb, int n
   *g = G;
 }
 
-__global__ void k_bin(const double* __restrict__ x, const double* __restrict__ y, int n, const Grid* __restrict__ gp,
-                      int* __restrict__ cell_key, int* __restrict__ cell_rank, int* __restrict__ cell_count) {
+__global__ void k_bin(const double* __restrict__ x, const double* __restrict__ y, int n, const int* __restrict__ n_dev,
+                      const Grid* __restrict__ gp, int* __restrict__ cell_key, int* __restrict__ cell_rank,
+                      int* __restrict__ cell_count) {
+  if (n_dev) n = *n_dev;
   const Grid g = *gp;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     int key = grid_cell_y(g, y[i]) * g.nx + grid_cell_x(g, x[i]);
@@ -252,10 +283,12 @@ __global__ void k_bin(const double* __restrict__ x, const double* __restrict__ y
   }
 }
 
-__global__ void k_scatter(const double* __restrict__ x, const double* __restrict__ y, int n, const Grid* __restrict__ gp,
+__global__ void k_scatter(const double* __restrict__ x, const double* __restrict__ y, int n,
+                          const int* __restrict__ n_dev, const Grid* __restrict__ gp,
                           const int* __restrict__ cell_key, const int* __restrict__ cell_rank,
                           const int* __restrict__ cell_start, double2* __restrict__ sorted_xy,
                           float2* __restrict__ sorted_loc, int* __restrict__ sorted_idx) {
+  if (n_dev) n = *n_dev;
   const Grid g = *gp;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const int key = cell_key[i];
@@ -267,22 +300,60 @@ __global__ void k_scatter(const double* __restrict__ x, const double* __restrict
   }
 }
 
+static int stream_grid(int n_bound, int per_sm) {
+  int b = n_bound > 0 ? (n_bound + kBlock - 1) / kBlock : 1;
+  int cap = per_sm * sm_count();
+  return b < cap ? b : cap;
+}
+
+cudaError_t grid_build_dev(const double* x, const double* y, int n_bound, const int* n_dev, double Rh, double lo2,
+                           double hi2, int ncell_cap, Grid* g, int* cell_key, int* cell_rank, int* cell_count,
+                           int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx,
+                           unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s) {
+  k_bbox_init<<<1, 1, 0, s>>>(bbox_tmp); note_launch();
+  k_bbox<<<stream_grid(n_bound, 4), kBlock, 0, s>>>(x, y, n_bound, n_dev, bbox_tmp); note_launch();
+  k_grid_finalize<<<1, 1, 0, s>>>(bbox_tmp, n_bound, n_dev, Rh, lo2, hi2, ncell_cap, g); note_launch();
+  return grid_bin_dev(x, y, n_bound, n_dev, ncell_cap, g, cell_key, cell_rank, cell_count, cell_start, sorted_xy,
+                      sorted_loc, sorted_idx, scan_tmp, s);
+}
+
+cudaError_t grid_bin_dev(const double* x, const double* y, int n_bound, const int* n_dev, int ncell_cap, const Grid* g,
+                         int* cell_key, int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy,
+                         float2* sorted_loc, int* sorted_idx, int* scan_tmp, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int) * (size_t)ncell_cap, s);
+  if (e != cudaSuccess) return e;
+  const int b = stream_grid(n_bound, 8);
+  k_bin<<<b, kBlock, 0, s>>>(x, y, n_bound, n_dev, g, cell_key, cell_rank, cell_count); note_launch();
+  e = scan_exclusive_i32(cell_count, cell_start, ncell_cap, scan_tmp, s);
+  if (e != cudaSuccess) return e;
+  k_scatter<<<b, kBlock, 0, s>>>(x, y, n_bound, n_dev, g, cell_key, cell_rank, cell_start, sorted_xy, sorted_loc,
+                                 sorted_idx);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t grid_build(const double* x, const double* y, int n, double Rh, double lo2, double hi2, int ncell_cap,
                        Grid* g, int* cell_key, int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy,
                        float2* sorted_loc, int* sorted_idx, unsigned long long* bbox_tmp, int* scan_tmp,
                        cudaStream_t s) {
-  int blocks = n > 0 ? (n + kBlock - 1) / kBlock : 1;
-  int pblocks = blocks < 4 * sm_count() ? blocks : 4 * sm_count();
-  k_bbox_init<<<1, 1, 0, s>>>(bbox_tmp); note_launch();
-  k_bbox<<<pblocks, kBlock, 0, s>>>(x, y, n, bbox_tmp); note_launch();
-  k_grid_finalize<<<1, 1, 0, s>>>(bbox_tmp, n, Rh, lo2, hi2, ncell_cap, g); note_launch();
-  cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int) * (size_t)ncell_cap, s);
+  return grid_build_dev(x, y, n, nullptr, Rh, lo2, hi2, ncell_cap, g, cell_key, cell_rank, cell_count, cell_start,
+                        sorted_xy, sorted_loc, sorted_idx, bbox_tmp, scan_tmp, s);
+}
+
+// list[k] = the k-th index with flag set; the count comes from n_dev.
+__global__ void k_compact_dev(const uint8_t* __restrict__ flags, int n, const int* __restrict__ n_dev,
+                              const int* __restrict__ pos, int* __restrict__ list, int* __restrict__ count) {
+  if (n_dev) n = *n_dev;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    if (flags[i]) list[pos[i]] = (int)i;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count = pos[n];
+}
+
+cudaError_t compact_flags_dev(const uint8_t* flags, int n_bound, const int* n_dev, int* list, int* count, int* pos,
+                              int* tmp, cudaStream_t s) {
+  cudaError_t e = scan_exclusive_u8_dev(flags, pos, n_bound, n_dev, tmp, s);
   if (e != cudaSuccess) return e;
-  k_bin<<<blocks, kBlock, 0, s>>>(x, y, n, g, cell_key, cell_rank, cell_count); note_launch();
-  e = scan_exclusive_i32(cell_count, cell_start, ncell_cap, scan_tmp, s);
-  if (e != cudaSuccess) return e;
-  k_scatter<<<blocks, kBlock, 0, s>>>(x, y, n, g, cell_key, cell_rank, cell_start, sorted_xy, sorted_loc,
-                                      sorted_idx); note_launch();
+  k_compact_dev<<<stream_grid(n_bound, 8), kBlock, 0, s>>>(flags, n_bound, n_dev, pos, list, count); note_launch();
   return cudaGetLastError();
 }
 

@@ -27,37 +27,15 @@ static int blocks_for(int m) {
   return b < 8 * sm_count() ? b : 8 * sm_count();
 }
 
-__global__ void k_cand_count(const int* __restrict__ open, int n_open, const uint8_t* __restrict__ mask,
-                             int* __restrict__ cnt) {
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x)
-    cnt[t] = __popc((~(unsigned)mask[open[t]]) & 0xFFu);
-}
-
-__global__ void k_cand_emit(Consts c, const int* __restrict__ open, int n_open, const uint8_t* __restrict__ mask,
-                            const int* __restrict__ cpos, const double* __restrict__ x,
-                            const double* __restrict__ y, double* __restrict__ cx, double* __restrict__ cy) {
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x) {
-    const int i = open[t];
-    const unsigned empty = (~(unsigned)mask[i]) & 0xFFu;
-    const double xi = x[i], yi = y[i];
-    int pos = cpos[t];
-    for (int s = 0; s < 8; ++s)
-      if ((empty >> s) & 1u) {
-        cx[pos] = __dadd_rn(xi, c.ins_dx[s]);
-        cy[pos] = __dadd_rn(yi, c.ins_dy[s]);
-        ++pos;
-      }
-  }
-}
-
 // keep[c] = 1 unless a proposal of smaller index lies closer than r h.
 // Pairs clearly apart (or clearly too close) are decided in FP32 on the
 // cell-local coordinates, the rest by the FP64 distance.
 __global__ void __launch_bounds__(kBlock) k_conflict(Consts c, const Grid* __restrict__ gp,
                                                      const int* __restrict__ cell_start,
                                                      const double2* __restrict__ sxy, const float2* __restrict__ sloc,
-                                                     const int* __restrict__ sidx, int n_cand,
+                                                     const int* __restrict__ sidx, const int* __restrict__ n_cand_dev,
                                                      uint8_t* __restrict__ keep) {
+  const int n_cand = *n_cand_dev;
   const Grid g = *gp;
   for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n_cand; p += (long)gridDim.x * blockDim.x) {
     const int ci = sidx[p];
@@ -95,16 +73,6 @@ __global__ void __launch_bounds__(kBlock) k_conflict(Consts c, const Grid* __res
   }
 }
 
-__global__ void k_append(const double* __restrict__ cx, const double* __restrict__ cy,
-                         const uint8_t* __restrict__ keep, const int* __restrict__ apos, int n_cand, int n_cur,
-                         double* __restrict__ x, double* __restrict__ y) {
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_cand; t += (long)gridDim.x * blockDim.x)
-    if (keep[t]) {
-      x[n_cur + apos[t]] = cx[t];
-      y[n_cur + apos[t]] = cy[t];
-    }
-}
-
 // Segment bits of the accepted proposals in the annulus of every open
 // particle; keep_flag[t] = 1 if the mask is still not full.  FP32 filter on
 // cell-local coordinates as in the neighbour search.
@@ -114,8 +82,9 @@ __global__ void __launch_bounds__(kBlock) k_mask_update(Consts c, const Grid* __
                                                         const float2* __restrict__ sloc,
                                                         const int* __restrict__ sidx, const uint8_t* __restrict__ keep,
                                                         const double* __restrict__ x, const double* __restrict__ y,
-                                                        const int* __restrict__ open, int n_open,
+                                                        const int* __restrict__ open, const int* __restrict__ n_open_dev,
                                                         uint8_t* __restrict__ mask, uint8_t* __restrict__ keep_flag) {
+  const int n_open = *n_open_dev;
   const Grid g = *gp;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x) {
     const int i = open[t];
@@ -157,21 +126,12 @@ __global__ void __launch_bounds__(kBlock) k_mask_update(Consts c, const Grid* __
 
 // out[k] = list[t] for the k-th flagged t (order kept); *count = total.
 __global__ void k_compact_list(const int* __restrict__ list, const uint8_t* __restrict__ flag,
-                               const int* __restrict__ pos, int m, int* __restrict__ out, int* __restrict__ count) {
+                               const int* __restrict__ pos, int m, const int* __restrict__ m_dev,
+                               int* __restrict__ out, int* __restrict__ count) {
+  if (m_dev) m = *m_dev;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x)
     if (flag[t]) out[pos[t]] = list[t];
   if (blockIdx.x == 0 && threadIdx.x == 0) *count = pos[m];
-}
-
-// Empty segments left on the open list (reported when max_rounds is hit).
-__global__ void k_count_open_segments(const int* __restrict__ open, int n_open, const uint8_t* __restrict__ mask,
-                                      int* __restrict__ out) {
-  int s = 0;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x)
-    s += __popc((~(unsigned)mask[open[t]]) & 0xFFu);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
 }
 
 // Open list of round 1: diffused particles whose mask is not full.
@@ -188,51 +148,154 @@ cudaError_t open_list(const int* dlist, const int* dcount, int cap, const uint8_
   k_open_flags<<<b, kBlock, 0, s>>>(dlist, dcount, mask, flag, cap); note_launch();
   cudaError_t e = scan_exclusive_u8(flag, pos, cap, scan_tmp, s);
   if (e != cudaSuccess) return e;
-  k_compact_list<<<b, kBlock, 0, s>>>(dlist, flag, pos, cap, open, n_open); note_launch();
+  k_compact_list<<<b, kBlock, 0, s>>>(dlist, flag, pos, cap, nullptr, open, n_open); note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t insert_count(const int* open, int n_open, const uint8_t* mask, int* cnt, int* cpos, int* scan_tmp,
-                         cudaStream_t s) {
-  k_cand_count<<<blocks_for(n_open), kBlock, 0, s>>>(open, n_open, mask, cnt); note_launch();
-  return scan_exclusive_i32(cnt, cpos, n_open, scan_tmp, s);  // cpos[n_open] = proposals
+// ---- device-resident rounds (no host round trips; graph-capturable) ----------
+
+__global__ void k_rounds_init(StepState* st, const int* __restrict__ n_open_src, cudaGraphConditionalHandle h,
+                              int graph) {
+  st->n_open = *n_open_src;
+  st->round = 0;
+  st->rounds_appended = 0;
+  st->overflow = 0;
+  st->n_needed = 0;
+  st->open_segments = 0;
+  st->n_cur = st->n;
+  const int go = st->n_open > 0 && st->max_rounds > 0;
+  if (!go) st->n_open = 0;  // nothing to do: every round is a no-op
+  if (graph) cudaGraphSetConditional(h, go);
 }
 
-cudaError_t insert_propose(const Consts& c, const int* open, int n_open, const uint8_t* mask, const int* cpos,
-                           const double* x, const double* y, double* cx, double* cy, int n_cand, int ncell_cap,
-                           const CandGrid& cg, uint8_t* keep, int* apos, int* scan_tmp, cudaStream_t s) {
-  k_cand_emit<<<blocks_for(n_open), kBlock, 0, s>>>(c, open, n_open, mask, cpos, x, y, cx, cy); note_launch();
-  cudaError_t e = grid_build(cx, cy, n_cand, c.Rh, c.lo2, c.hi2, ncell_cap, cg.grid, cg.cell_key, cg.cell_rank,
-                             cg.cell_count, cg.cell_start, cg.sorted_xy, cg.sorted_loc, cg.sorted_idx, cg.bbox,
-                             scan_tmp, s);
-  if (e != cudaSuccess) return e;
-  int b = n_cand > 0 ? (n_cand + kBlock - 1) / kBlock : 1;
-  k_conflict<<<b, kBlock, 0, s>>>(c, cg.grid, cg.cell_start, cg.sorted_xy, cg.sorted_loc, cg.sorted_idx, n_cand,
-                                   keep);
-  note_launch();
-  return scan_exclusive_u8(keep, apos, n_cand, scan_tmp, s);  // apos[n_cand] = accepted
+__global__ void k_cand_count_dev(const int* __restrict__ open, const StepState* __restrict__ st,
+                                 const uint8_t* __restrict__ mask, int* __restrict__ cnt) {
+  const int n_open = st->n_open;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x)
+    cnt[t] = __popc((~(unsigned)mask[open[t]]) & 0xFFu);
 }
 
-cudaError_t insert_commit(const Consts& c, const int* open, int n_open, const double* cx, const double* cy,
-                          int n_cand, const CandGrid& cg, const uint8_t* keep, const int* apos, int n_cur, double* x,
-                          double* y, uint8_t* mask, uint8_t* keep_flag, int* keep_pos, int* open_next, int* n_next,
-                          int* scan_tmp, cudaStream_t s) {
-  k_append<<<blocks_for(n_cand), kBlock, 0, s>>>(cx, cy, keep, apos, n_cand, n_cur, x, y); note_launch();
-  int b = n_open > 0 ? (n_open + kBlock - 1) / kBlock : 1;
-  k_mask_update<<<b, kBlock, 0, s>>>(c, cg.grid, cg.cell_start, cg.sorted_xy, cg.sorted_loc, cg.sorted_idx, keep,
-                                      x, y, open, n_open, mask, keep_flag);
-  note_launch();
-  cudaError_t e = scan_exclusive_u8(keep_flag, keep_pos, n_open, scan_tmp, s);
-  if (e != cudaSuccess) return e;
-  k_compact_list<<<blocks_for(n_open), kBlock, 0, s>>>(open, keep_flag, keep_pos, n_open, open_next, n_next);
-  note_launch();
+__global__ void k_set_ncand(StepState* st, const int* __restrict__ cpos) { st->n_cand = cpos[st->n_open]; }
+
+__global__ void k_cand_emit_dev(Consts c, const int* __restrict__ open, const StepState* __restrict__ st,
+                                const uint8_t* __restrict__ mask, const int* __restrict__ cpos,
+                                const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ cx,
+                                double* __restrict__ cy) {
+  const int n_open = st->n_open;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x) {
+    const int i = open[t];
+    const unsigned empty = (~(unsigned)mask[i]) & 0xFFu;
+    const double xi = x[i], yi = y[i];
+    int pos = cpos[t];
+    for (int s = 0; s < 8; ++s)
+      if ((empty >> s) & 1u) {
+        cx[pos] = __dadd_rn(xi, c.ins_dx[s]);
+        cy[pos] = __dadd_rn(yi, c.ins_dy[s]);
+        ++pos;
+      }
+  }
+}
+
+__global__ void k_copy_grid(const Grid* __restrict__ src, Grid* __restrict__ dst) { *dst = *src; }
+
+// Accepted count; capacity check (then the round appends nothing and the
+// loop stops with the overflow flag).
+__global__ void k_round_check(StepState* st, const int* __restrict__ apos) {
+  const int a = apos[st->n_cand];
+  st->accepted = a;
+  if ((long)st->n_cur + a > st->capacity) {
+    st->overflow = 1;
+    st->n_needed = st->n_cur + a;
+  }
+}
+
+__global__ void k_append_dev(const double* __restrict__ cx, const double* __restrict__ cy,
+                             const uint8_t* __restrict__ keep, const int* __restrict__ apos,
+                             const StepState* __restrict__ st, double* __restrict__ x, double* __restrict__ y) {
+  if (st->overflow) return;
+  const int n_cand = st->n_cand, n_cur = st->n_cur;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_cand; t += (long)gridDim.x * blockDim.x)
+    if (keep[t]) {
+      x[n_cur + apos[t]] = cx[t];
+      y[n_cur + apos[t]] = cy[t];
+    }
+}
+
+__global__ void k_copy_list(const int* __restrict__ src, int* __restrict__ dst, const StepState* __restrict__ st) {
+  const int m = st->n_next;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) dst[t] = src[t];
+}
+
+__global__ void k_round_end(StepState* st, cudaGraphConditionalHandle h, int graph) {
+  if (st->n_open > 0) {
+    if (!st->overflow) {
+      st->n_cur += st->accepted;
+      if (st->accepted > 0) st->rounds_appended += 1;
+    }
+    st->round += 1;
+    st->n_open = st->overflow ? 0 : st->n_next;
+  }
+  // rounds stop at max_rounds with the open list kept for the statistics
+  const int go = !st->overflow && st->n_open > 0 && st->round < st->max_rounds;
+  if (graph) cudaGraphSetConditional(h, go);
+}
+
+// Empty segments left (only when max_rounds ended the loop with open particles).
+__global__ void k_rounds_finish(StepState* st, const int* __restrict__ open, const uint8_t* __restrict__ mask) {
+  const int n_open = (st->overflow || st->round < st->max_rounds) ? 0 : st->n_open;
+  int s = 0;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x)
+    s += __popc((~(unsigned)mask[open[t]]) & 0xFFu);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(&st->open_segments, s);
+}
+
+cudaError_t rounds_init(StepState* st, const int* n_open_src, cudaGraphConditionalHandle handle, bool graph,
+                        cudaStream_t s) {
+  k_rounds_init<<<1, 1, 0, s>>>(st, n_open_src, handle, graph ? 1 : 0); note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t count_open_segments(const int* open, int n_open, const uint8_t* mask, int* out, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int), s);
+cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const RoundBufs& rb, int cap, uint8_t* mask,
+                       double* x, double* y, cudaGraphConditionalHandle handle, bool graph, cudaStream_t s) {
+  const int bo = blocks_for(cap);
+  const long cand_cap = 8L * cap;
+  const int bc = blocks_for((int)(cand_cap < 0x7FFFFFFF ? cand_cap : 0x7FFFFFFF));
+  k_cand_count_dev<<<bo, kBlock, 0, s>>>(rb.open, st, mask, rb.cnt); note_launch();
+  cudaError_t e = scan_exclusive_i32_dev(rb.cnt, rb.cpos, cap, &st->n_open, rb.scan_tmp, s);
   if (e != cudaSuccess) return e;
-  k_count_open_segments<<<blocks_for(n_open), kBlock, 0, s>>>(open, n_open, mask, out); note_launch();
+  k_set_ncand<<<1, 1, 0, s>>>(st, rb.cpos); note_launch();
+  k_cand_emit_dev<<<bo, kBlock, 0, s>>>(c, rb.open, st, mask, rb.cpos, x, y, rb.cx, rb.cy); note_launch();
+  // proposals binned on the particle grid's geometry (cells >= R h; points
+  // outside it clamp into the edge cells, which keeps 3 x 3 scans complete)
+  k_copy_grid<<<1, 1, 0, s>>>(pgrid, rb.cg.grid); note_launch();
+  e = grid_bin_dev(rb.cx, rb.cy, (int)cand_cap, &st->n_cand, rb.ncell_cap, rb.cg.grid, rb.cg.cell_key,
+                   rb.cg.cell_rank, rb.cg.cell_count, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
+                   rb.cg.sorted_idx, rb.scan_tmp, s);
+  if (e != cudaSuccess) return e;
+  k_conflict<<<bc, kBlock, 0, s>>>(c, rb.cg.grid, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
+                                   rb.cg.sorted_idx, &st->n_cand, rb.keep);
+  note_launch();
+  e = scan_exclusive_u8_dev(rb.keep, rb.apos, (int)cand_cap, &st->n_cand, rb.scan_tmp, s);
+  if (e != cudaSuccess) return e;
+  k_round_check<<<1, 1, 0, s>>>(st, rb.apos); note_launch();
+  k_append_dev<<<bc, kBlock, 0, s>>>(rb.cx, rb.cy, rb.keep, rb.apos, st, x, y); note_launch();
+  k_mask_update<<<bo, kBlock, 0, s>>>(c, rb.cg.grid, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
+                                      rb.cg.sorted_idx, rb.keep, x, y, rb.open, &st->n_open, mask, rb.keep_flag);
+  note_launch();
+  e = scan_exclusive_u8_dev(rb.keep_flag, rb.keep_pos, cap, &st->n_open, rb.scan_tmp, s);
+  if (e != cudaSuccess) return e;
+  k_compact_list<<<bo, kBlock, 0, s>>>(rb.open, rb.keep_flag, rb.keep_pos, cap, &st->n_open, rb.open_next,
+                                       &st->n_next);
+  note_launch();
+  k_copy_list<<<bo, kBlock, 0, s>>>(rb.open_next, rb.open, st); note_launch();
+  k_round_end<<<1, 1, 0, s>>>(st, handle, graph ? 1 : 0); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t rounds_finish(StepState* st, const int* open, const uint8_t* mask, int cap, cudaStream_t s) {
+  k_rounds_finish<<<blocks_for(cap), kBlock, 0, s>>>(st, open, mask); note_launch();
   return cudaGetLastError();
 }
 

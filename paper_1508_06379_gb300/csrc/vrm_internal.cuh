@@ -77,7 +77,27 @@ struct ReduceState {
   unsigned long long T;          // threshold key (bits of |Gamma|)
   int k_tie;                     // particles with key == T that stay out (lowest indices)
   int all_out;                   // 1: every particle stays out (sum within bound)
+  unsigned int blocks_done;      // blocks of the current pass that have merged their histogram
   unsigned long long hist[256][4];  // per digit: limb sums (3 x 32-bit limbs) and count
+};
+
+// Device-resident state of one vrm_step (so that the step runs without host
+// round trips and can be captured in a CUDA graph).
+struct StepState {
+  int n;               // particles given
+  int capacity;        // room in x, y, gamma_out
+  double dt;           // Euler step
+  int n_cur;           // particles now (grows with insertion)
+  int n_open;          // open particles of the current insertion round
+  int n_cand;          // proposals of the current round
+  int accepted;        // proposals accepted in the current round
+  int n_next;          // open particles left after the round
+  int round;           // insertion rounds run
+  int rounds_appended; // rounds that appended particles
+  int overflow;        // 1: an insertion would exceed the capacity
+  int n_needed;        // particles that would have been needed then
+  int open_segments;   // empty segments left when max_rounds is reached
+  int max_rounds;
 };
 
 struct Scratch;  // defined in vrm_api.cu
@@ -153,8 +173,23 @@ cudaError_t grid_build(const double* x, const double* y, int n, double Rh, doubl
                        Grid* g, int* cell_key, int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy,
                        float2* sorted_loc, int* sorted_idx, unsigned long long* bbox_tmp, int* scan_tmp,
                        cudaStream_t s);
+// Same with the count read from device memory (*n_dev <= n_bound); the
+// cell grid is then binned with the geometry already in g (grid_bin_dev).
+cudaError_t grid_build_dev(const double* x, const double* y, int n_bound, const int* n_dev, double Rh, double lo2,
+                           double hi2, int ncell_cap, Grid* g, int* cell_key, int* cell_rank, int* cell_count,
+                           int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx,
+                           unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s);
+cudaError_t grid_bin_dev(const double* x, const double* y, int n_bound, const int* n_dev, int ncell_cap, const Grid* g,
+                         int* cell_key, int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy,
+                         float2* sorted_loc, int* sorted_idx, int* scan_tmp, cudaStream_t s);
 // Exclusive scan of n ints into out[0..n] (out[n] = total).
 cudaError_t scan_exclusive_i32(const int* in, int* out, int n, int* tmp, cudaStream_t s);
+// Scans and compaction with the count in device memory (*n_dev <= n_bound).
+cudaError_t scan_exclusive_i32_dev(const int* in, int* out, int n_bound, const int* n_dev, int* tmp, cudaStream_t s);
+cudaError_t scan_exclusive_u8_dev(const uint8_t* in, int* out, int n_bound, const int* n_dev, int* tmp,
+                                  cudaStream_t s);
+cudaError_t compact_flags_dev(const uint8_t* flags, int n_bound, const int* n_dev, int* list, int* count, int* pos,
+                              int* tmp, cudaStream_t s);
 // Exclusive scan of n bytes (0/1) into out[0..n].
 cudaError_t scan_exclusive_u8(const uint8_t* in, int* out, int n, int* tmp, cudaStream_t s);
 // list[k] = the k-th index with flag set (ascending); count written to *count
@@ -165,11 +200,21 @@ size_t scan_tmp_ints(int n);
 // vrm_reduce.cu
 cudaError_t reduce_select(const double* gamma, int n, double c_bound, uint8_t* diffused, ReduceState* st,
                           uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds, cudaStream_t s);
+cudaError_t reduce_select_dev(const double* gamma, int n_bound, const int* n_dev, double c_bound, uint8_t* diffused,
+                              ReduceState* st, uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds,
+                              cudaStream_t s);
 
 // vrm_search.cu
 cudaError_t search_all(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
                        const float2* sorted_loc, const int* sorted_idx, int n, int* nbr_count, int* nbr_idx,
                        uint8_t* seg_mask, int* small, DevStats* ds, cudaStream_t s);
+cudaError_t search_all_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
+                           const float2* sorted_loc, const int* sorted_idx, int n_bound, const int* n_dev,
+                           int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small, DevStats* ds,
+                           cudaStream_t s);
+cudaError_t search_masks_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
+                             const float2* sorted_loc, const int* sorted_idx, int n_bound, const int* n_dev,
+                             const uint8_t* flag, uint8_t* mask, cudaStream_t s);
 // Segment masks of the particles flagged in `flag` (n entries), in cell order.
 cudaError_t search_masks(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
                          const float2* sorted_loc, const int* sorted_idx, int n, const uint8_t* flag, uint8_t* mask,
@@ -188,29 +233,41 @@ struct CandGrid {
 // segment mask is not full; open[] ascending, *n_open on the device.
 cudaError_t open_list(const int* dlist, const int* dcount, int cap, const uint8_t* mask, uint8_t* flag, int* pos,
                       int* open, int* n_open, int* scan_tmp, cudaStream_t s);
-// Proposal counts of the open particles; cpos[n_open] = number of proposals.
-cudaError_t insert_count(const int* open, int n_open, const uint8_t* mask, int* cnt, int* cpos, int* scan_tmp,
-                         cudaStream_t s);
-// Writes the proposals in key order, bins them, runs the conflict rule;
-// apos[n_cand] = number accepted.
-cudaError_t insert_propose(const Consts& c, const int* open, int n_open, const uint8_t* mask, const int* cpos,
-                           const double* x, const double* y, double* cx, double* cy, int n_cand, int ncell_cap,
-                           const CandGrid& cg, uint8_t* keep, int* apos, int* scan_tmp, cudaStream_t s);
-// Appends the accepted proposals at x[n_cur..], updates the masks, writes the
-// next open list (count in *n_next).
-cudaError_t insert_commit(const Consts& c, const int* open, int n_open, const double* cx, const double* cy,
-                          int n_cand, const CandGrid& cg, const uint8_t* keep, const int* apos, int n_cur, double* x,
-                          double* y, uint8_t* mask, uint8_t* keep_flag, int* keep_pos, int* open_next, int* n_next,
-                          int* scan_tmp, cudaStream_t s);
-cudaError_t count_open_segments(const int* open, int n_open, const uint8_t* mask, int* out, cudaStream_t s);
+
+// Buffers of the device-resident insertion rounds (proposal capacity 8 n).
+struct RoundBufs {
+  int* open;           // open list (cap)
+  int* open_next;      // compacted next open list (cap)
+  int *cnt, *cpos;     // proposals per open particle and their offsets (cap, cap+1)
+  uint8_t *keep_flag;  // open particle still open (cap)
+  int* keep_pos;       // (cap+1)
+  double *cx, *cy;     // proposals (8 cap)
+  uint8_t* keep;       // proposal accepted (8 cap)
+  int* apos;           // offsets of accepted proposals (8 cap + 1)
+  int ncell_cap;       // cells of the proposal grid
+  CandGrid cg;         // proposal cell grid (geometry copied from the particle grid)
+  int* scan_tmp;       // scan workspace for 8 cap entries
+};
+// Round state initialisation after the open list exists; sets the loop
+// condition (handle may be 0 when not capturing).
+cudaError_t rounds_init(StepState* st, const int* n_open_src, cudaGraphConditionalHandle handle, bool graph,
+                        cudaStream_t s);
+// One insertion round on device-resident counts; a no-op once the state has
+// no open particle.  The last kernel updates the state and, in a graph, sets
+// the while-loop condition.
+cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const RoundBufs& rb, int cap, uint8_t* mask,
+                       double* x, double* y, cudaGraphConditionalHandle handle, bool graph, cudaStream_t s);
+cudaError_t rounds_finish(StepState* st, const int* open, const uint8_t* mask, int cap, cudaStream_t s);
 
 // vrm_lp.cu
+// nu_dt = nu * dt for the stability statistic; with dt_dev it is nu * *dt_dev.
 cudaError_t lp_small(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
                      int cap, const int* small, int* cols, double* f, double* fii, uint8_t* status, int* fail_list,
-                     DevStats* ds, double dt, cudaStream_t s);
+                     DevStats* ds, double nu_dt, cudaStream_t s, const double* dt_dev = nullptr, double nu = 0.0);
 cudaError_t lp_full(const Consts& c, const double* x, const double* y, const int* fail_list, const int* fail_count,
                     int cap, const int* nbr_count, const int* nbr_idx, int* cols, double* f, double* fii,
-                    uint8_t* status, DevStats* ds, double dt, cudaStream_t s);
+                    uint8_t* status, DevStats* ds, double nu_dt, cudaStream_t s, const double* dt_dev = nullptr,
+                    double nu = 0.0);
 cudaError_t lp_clear(int n, const uint8_t* diffused, int* cols, double* f, double* fii, uint8_t* status,
                      cudaStream_t s);
 
@@ -218,5 +275,9 @@ cudaError_t lp_clear(int n, const uint8_t* diffused, int* cols, double* f, doubl
 cudaError_t apply_gather(const Consts& c, int n, int n_gamma, const double* gamma, const uint8_t* diffused,
                          const int* nbr_count, const int* nbr_idx, const int* cols, const double* f, const double* fii,
                          const int* order, double* dgamma, double* gamma_out, double dt, cudaStream_t s);
+cudaError_t apply_gather_dev(const Consts& c, int n_bound, const int* n_dev, int n_gamma, const int* n_gamma_dev,
+                             const double* gamma, const uint8_t* diffused, const int* nbr_count, const int* nbr_idx,
+                             const int* cols, const double* f, const double* fii, const int* order, double* dgamma,
+                             double* gamma_out, double dt, const double* dt_dev, cudaStream_t s);
 
 }  // namespace vrm

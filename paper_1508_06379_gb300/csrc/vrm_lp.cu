@@ -219,7 +219,8 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
                                                   int* __restrict__ cols, double* __restrict__ f,
                                                   double* __restrict__ fii, uint8_t* __restrict__ status,
                                                   int* __restrict__ fail_list, DevStats* __restrict__ ds,
-                                                  double nu_dt) {
+                                                  double nu_dt, const double* __restrict__ dt_dev, double nu) {
+  if (dt_dev) nu_dt = nu * *dt_dev;
   const int m = *list_count;
   const double inv_h2 = 1.0 / (c.h * c.h);
   int st_ok = 0, st_none = 0, st_maxpiv = 0, st_solved = 0, st_pivots = 0;
@@ -451,7 +452,9 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
                                                  const int* __restrict__ nbr_count, const int* __restrict__ nbr_idx,
                                                  int* __restrict__ cols, double* __restrict__ f,
                                                  double* __restrict__ fii, uint8_t* __restrict__ status,
-                                                 DevStats* __restrict__ ds, double nu_dt) {
+                                                 DevStats* __restrict__ ds, double nu_dt,
+                                                 const double* __restrict__ dt_dev, double nu) {
+  if (dt_dev) nu_dt = nu * *dt_dev;
   const int lane = threadIdx.x & 31;
   const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
@@ -663,23 +666,24 @@ __global__ void k_lp_clear(int n, const uint8_t* __restrict__ diffused, int* __r
 
 cudaError_t lp_small(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
                      int cap, const int* small, int* cols, double* f, double* fii, uint8_t* status, int* fail_list,
-                     DevStats* ds, double nu_dt, cudaStream_t s) {
+                     DevStats* ds, double nu_dt, cudaStream_t s, const double* dt_dev, double nu) {
   if (cap <= 0) return cudaSuccess;
   int blocks = (cap + 127) / 128;
   if (blocks > 16 * sm_count()) blocks = 16 * sm_count();
-  k_lp_small<<<blocks, 128, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list, ds, nu_dt); note_launch();
+  k_lp_small<<<blocks, 128, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list, ds, nu_dt, dt_dev,
+                                    nu); note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t lp_full(const Consts& c, const double* x, const double* y, const int* fail_list, const int* fail_count,
                     int cap, const int* nbr_count, const int* nbr_idx, int* cols, double* f, double* fii,
-                    uint8_t* status, DevStats* ds, double nu_dt, cudaStream_t s) {
+                    uint8_t* status, DevStats* ds, double nu_dt, cudaStream_t s, const double* dt_dev, double nu) {
   if (cap <= 0) return cudaSuccess;
   long warps = cap;
   long blocks = (warps * 32 + 127) / 128;
   if (blocks > 4 * sm_count()) blocks = 4 * sm_count();
   k_lp_full<<<(int)blocks, 128, 0, s>>>(c, x, y, fail_list, fail_count, nbr_count, nbr_idx, cols, f, fii, status, ds,
-                                        nu_dt); note_launch();
+                                        nu_dt, dt_dev, nu); note_launch();
   return cudaGetLastError();
 }
 

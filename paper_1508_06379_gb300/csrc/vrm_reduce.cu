@@ -5,14 +5,17 @@
 // The choice must not depend on summation order, so the sums are exact
 // integers: q_i = floor(|Gamma_i| 2^(96-E)) with max|Gamma| < 2^E, summed as
 // three 32-bit limbs in 64-bit counters (no carries lost for n < 2^31).
+// q_i is formed from the bit pattern with integer shifts (the same value as
+// floor(ldexp(|Gamma_i|, 96-E)), computed without FP64 instructions).
 //
 // Instead of sorting, eight passes select the threshold key T (the bit
 // pattern of |Gamma|, which orders like the value for non-negative doubles)
 // one byte at a time: each pass histograms the exact q-sums of the particles
-// whose key matches the bytes chosen so far, and one thread picks the first
-// byte at which the running sum crosses the remaining budget.  Particles with
-// key == T are tied; the first k_tie of them by index stay out, found with a
-// scan of the tie flags.
+// whose key matches the bytes chosen so far; the last block of the pass to
+// finish scans the 256 buckets in parallel and picks the first byte at which
+// the running sum crosses the remaining budget.  Particles with key == T are
+// tied; the first k_tie of them by index stay out, found with a scan of the
+// tie flags.
 #include "vrm_internal.cuh"
 
 namespace vrm {
@@ -31,8 +34,30 @@ __device__ __forceinline__ double u128_to_dbl(u128 s) {
   return __dadd_rn(__dmul_rn(__ull2double_rn(hi), two64), __ull2double_rn(lo));
 }
 
+// floor(|a| 2^(96-E)) from the bit pattern key of |a| (a finite, |a| < 2^E):
+// |a| = M 2^(e-1075) for a normal (M with the hidden bit), M 2^-1074 for a
+// subnormal; the product by 2^(96-E) is a shift, floor a right shift.
+__device__ __forceinline__ u128 q_of_key(unsigned long long key, int E) {
+  const int ebits = (int)(key >> 52);
+  const unsigned long long frac = key & 0xFFFFFFFFFFFFFull;
+  const unsigned long long M = ebits ? (frac | 0x10000000000000ull) : frac;
+  const int sh = (ebits ? ebits - 1075 : -1074) + 96 - E;
+  if (sh >= 0) return (u128)M << sh;  // sh <= 43 because |a| < 2^E
+  if (sh <= -64) return 0;
+  return (u128)(M >> (-sh));
+}
+
+// E with max|Gamma| < 2^E (frexp exponent) from the bit pattern, no FP64.
+__device__ __forceinline__ int exponent_of_key(unsigned long long key) {
+  const int ebits = (int)(key >> 52);
+  if (ebits) return ebits - 1022;
+  const unsigned long long frac = key & 0xFFFFFFFFFFFFFull;
+  return (64 - __clzll((long long)frac)) - 1074;  // bit length of frac - 1074
+}
+
+// Bucket value from its limbs; read past L1 (other blocks wrote them by atomics).
 __device__ __forceinline__ u128 limbs_value(const unsigned long long* h) {
-  return (u128)h[0] + ((u128)h[1] << 32) + ((u128)h[2] << 64);
+  return (u128)__ldcg(h) + ((u128)__ldcg(h + 1) << 32) + ((u128)__ldcg(h + 2) << 64);
 }
 
 __global__ void k_reduce_init(ReduceState* st) {
@@ -47,19 +72,21 @@ __global__ void k_reduce_init(ReduceState* st) {
     st->T = 0;
     st->k_tie = 0;
     st->all_out = 0;
+    st->blocks_done = 0;
   }
 }
 
-__global__ void k_absmax(const double* __restrict__ g, int n, ReduceState* __restrict__ st, DevStats* ds) {
+__global__ void k_absmax(const double* __restrict__ g, int n, const int* __restrict__ n_dev, ReduceState* __restrict__ st,
+                         DevStats* ds) {
+  if (n_dev) n = *n_dev;
   unsigned long long m = 0;
   int bad = 0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    double v = g[i];
-    if (!isfinite(v)) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(g[i]) & 0x7FFFFFFFFFFFFFFFull;
+    if (b >= 0x7FF0000000000000ull) {  // Inf or NaN
       bad = 1;
       continue;
     }
-    unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
     m = b > m ? b : m;
   }
 #pragma unroll
@@ -74,40 +101,137 @@ __global__ void k_absmax(const double* __restrict__ g, int n, ReduceState* __res
   }
 }
 
-__global__ void k_reduce_prepare(ReduceState* st, double c_bound) {
-  if (st->amax_bits == 0 || !(c_bound < 1.0)) {
-    // no circulation, or a bound of at least ||Gamma||_1: nothing diffuses
-    st->all_out = 1;
-    st->done = 1;
+// Choice of the byte of pass `pass` from the 256 bucket sums, by all 256
+// threads of the last block: inclusive scan of the 128-bit bucket sums, then
+// the first bucket whose running sum exceeds the budget.
+__device__ void choose_digit(ReduceState* st, double c_bound, int pass) {
+  __shared__ unsigned long long s_lo[256], s_hi[256];
+  __shared__ int s_sel;
+  const int b = threadIdx.x;
+  const u128 v = limbs_value(st->hist[b]);
+  const unsigned long long cnt = __ldcg(&st->hist[b][3]);
+  // inclusive scan (Hillis-Steele over 256 entries in shared memory)
+  u128 acc = v;
+  s_lo[b] = (unsigned long long)acc;
+  s_hi[b] = (unsigned long long)(acc >> 64);
+  __syncthreads();
+  for (int o = 1; o < 256; o <<= 1) {
+    u128 add = 0;
+    if (b >= o) add = ((u128)s_hi[b - o] << 64) | (u128)s_lo[b - o];
+    __syncthreads();
+    acc += add;
+    s_lo[b] = (unsigned long long)acc;
+    s_hi[b] = (unsigned long long)(acc >> 64);
+    __syncthreads();
+  }
+  const u128 total = ((u128)s_hi[255] << 64) | (u128)s_lo[255];
+  u128 tau;
+  if (pass == 0) {
+    tau = dbl_floor_to_u128(__dmul_rn(c_bound, u128_to_dbl(total)));
+  } else {
+    tau = ((u128)st->tau_hi << 64) | (u128)st->tau_lo;
+  }
+  if (b == 0) s_sel = 255;
+  __syncthreads();
+  if (pass == 0 && total <= tau) {
+    if (b == 0) {
+      st->all_out = 1;
+      st->done = 1;
+    }
     return;
   }
-  int E;
-  frexp(__longlong_as_double((long long)st->amax_bits), &E);
-  st->E = E;
+  // first bucket with inclusive sum > tau (exists: the total exceeds tau)
+  const u128 excl = acc - v;
+  if (acc > tau && excl <= tau) atomicMin(&s_sel, b);
+  __syncthreads();
+  const int sel = s_sel;
+  if (b == sel) {
+    const u128 rem = tau - excl;
+    st->prefix = (st->prefix << 8) | (unsigned long long)sel;
+    st->tau_lo = (unsigned long long)rem;
+    st->tau_hi = (unsigned long long)(rem >> 64);
+    if (pass == 7) {
+      // all particles with key == T have the same q_T > 0; the first k_tie
+      // by index fit: k_tie = max k <= count with k q_T <= rem (bisection)
+      const unsigned long long T = st->prefix;
+      const u128 qT = q_of_key(T, st->E);
+      unsigned long long lo = 0, hi = cnt;
+      while (lo < hi) {
+        const unsigned long long mid = (lo + hi + 1) / 2;
+        if ((u128)mid * qT <= rem) lo = mid;
+        else hi = mid - 1;
+      }
+      st->T = T;
+      st->k_tie = (int)lo;
+      st->done = 1;
+    }
+  }
+  __syncthreads();
+  st->hist[b][0] = st->hist[b][1] = st->hist[b][2] = st->hist[b][3] = 0;
 }
 
-__global__ void k_reduce_hist(const double* __restrict__ g, int n, ReduceState* __restrict__ st, int pass) {
+// One pass: block histograms of the exact q-sums per byte of the key, merged
+// into st->hist; the last block to finish chooses the byte.
+__global__ void __launch_bounds__(256) k_reduce_pass(const double* __restrict__ g, int n, const int* __restrict__ n_dev,
+                                                     ReduceState* __restrict__ st, double c_bound, int pass) {
+  if (n_dev) n = *n_dev;
   __shared__ unsigned long long h[256][4];
+  __shared__ bool last;
   for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b][0] = h[b][1] = h[b][2] = h[b][3] = 0;
+  if (pass == 0 && blockIdx.x == 0 && threadIdx.x == 0 && st->amax_bits != 0) st->E = exponent_of_key(st->amax_bits);
   __syncthreads();
   const int done = st->done;
-  const int E = st->E;
-  const unsigned long long prefix = st->prefix;
   if (!done) {
+    const unsigned long long amax = st->amax_bits;
+    const int E = exponent_of_key(amax);
+    const unsigned long long prefix = st->prefix;
     const int shift = 56 - 8 * pass;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-      double a = fabs(g[i]);
-      unsigned long long key = (unsigned long long)__double_as_longlong(a);
-      if (pass > 0 && (key >> (shift + 8)) != prefix) continue;
-      int d = (int)((key >> shift) & 0xFF);
-      u128 q = dbl_floor_to_u128(ldexp(a, 96 - E));
-      unsigned long long l0 = (unsigned long long)(q & 0xFFFFFFFFull);
-      unsigned long long l1 = (unsigned long long)((q >> 32) & 0xFFFFFFFFull);
-      unsigned long long l2 = (unsigned long long)(q >> 64);
-      if (l0) atomicAdd(&h[d][0], l0);
-      if (l1) atomicAdd(&h[d][1], l1);
-      if (l2) atomicAdd(&h[d][2], l2);
-      atomicAdd(&h[d][3], 1ull);
+    const int lane = threadIdx.x & 31;
+    // whole warps step through the particles so that lanes holding the same
+    // byte merge their exact limb sums before one shared atomic per byte (the
+    // leading bytes are shared by nearly all particles)
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+      const long i = base + lane;
+      bool pending = false;
+      int d = 0;
+      unsigned long long l0 = 0, l1 = 0, l2 = 0;
+      if (i < n) {
+        const unsigned long long key = (unsigned long long)__double_as_longlong(g[i]) & 0x7FFFFFFFFFFFFFFFull;
+        if (pass == 0 || (key >> (shift + 8)) == prefix) {
+          pending = true;
+          d = (int)((key >> shift) & 0xFF);
+          const u128 q = q_of_key(key, E);
+          l0 = (unsigned long long)(q & 0xFFFFFFFFull);
+          l1 = (unsigned long long)((q >> 32) & 0xFFFFFFFFull);
+          l2 = (unsigned long long)(q >> 64);
+        }
+      }
+      unsigned todo = __ballot_sync(0xffffffffu, pending);
+      while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int dl = __shfl_sync(0xffffffffu, d, leader);
+        const bool mine = pending && d == dl;
+        const unsigned peers = __ballot_sync(0xffffffffu, mine);
+        // 16-bit halves of the 32-bit limbs: sums of 32 lanes stay below 2^21
+        unsigned long long sum[3];
+        const unsigned long long lim[3] = {l0, l1, l2};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const unsigned lo = mine ? (unsigned)(lim[k] & 0xFFFFu) : 0u;
+          const unsigned hi = mine ? (unsigned)(lim[k] >> 16) : 0u;
+          sum[k] = (unsigned long long)__reduce_add_sync(0xffffffffu, lo) +
+                   ((unsigned long long)__reduce_add_sync(0xffffffffu, hi) << 16);
+        }
+        if (lane == leader) {
+          if (sum[0]) atomicAdd(&h[dl][0], sum[0]);
+          if (sum[1]) atomicAdd(&h[dl][1], sum[1]);
+          if (sum[2]) atomicAdd(&h[dl][2], sum[2]);
+          atomicAdd(&h[dl][3], (unsigned long long)__popc(peers));
+        }
+        if (mine) pending = false;
+        todo &= ~peers;
+      }
     }
   }
   __syncthreads();
@@ -119,63 +243,33 @@ __global__ void k_reduce_hist(const double* __restrict__ g, int n, ReduceState* 
         atomicAdd(&st->hist[b][2], h[b][2]);
         atomicAdd(&st->hist[b][3], h[b][3]);
       }
+  // last block to finish chooses the byte (histogram complete)
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x == 0) st->blocks_done = 0;
+  if (!done) choose_digit(st, c_bound, pass);
 }
 
-__global__ void k_reduce_choose(ReduceState* st, double c_bound, int pass) {
-  if (threadIdx.x != 0) return;
-  if (st->done) return;
-  u128 tau;
-  if (pass == 0) {
-    u128 S = 0;
-    for (int b = 0; b < 256; ++b) S += limbs_value(st->hist[b]);
-    tau = dbl_floor_to_u128(__dmul_rn(c_bound, u128_to_dbl(S)));
-    if (S <= tau) {
-      st->all_out = 1;
-      st->done = 1;
-      return;
-    }
-  } else {
-    tau = ((u128)st->tau_hi << 64) | (u128)st->tau_lo;
-  }
-  u128 cum = 0;
-  int bsel = 255;
-  for (int b = 0; b < 256; ++b) {
-    u128 sb = limbs_value(st->hist[b]);
-    if (cum + sb > tau) {
-      bsel = b;
-      break;
-    }
-    cum += sb;
-  }
-  tau -= cum;
-  unsigned long long count_sel = st->hist[bsel][3];
-  st->prefix = (st->prefix << 8) | (unsigned long long)bsel;
-  st->tau_lo = (unsigned long long)tau;
-  st->tau_hi = (unsigned long long)(tau >> 64);
-  for (int b = 0; b < 256; ++b) st->hist[b][0] = st->hist[b][1] = st->hist[b][2] = st->hist[b][3] = 0;
-  if (pass == 7) {
-    // all particles with key == T have the same q_T > 0; the first k_tie by
-    // index fit: k_tie = max k <= count with k q_T <= tau (binary search)
-    unsigned long long T = st->prefix;
-    u128 qT = dbl_floor_to_u128(ldexp(__longlong_as_double((long long)T), 96 - st->E));
-    unsigned long long lo = 0, hi = count_sel;
-    while (lo < hi) {
-      unsigned long long mid = (lo + hi + 1) / 2;
-      if ((u128)mid * qT <= tau) lo = mid;
-      else hi = mid - 1;
-    }
-    st->T = T;
-    st->k_tie = (int)lo;
+__global__ void k_reduce_prepare(ReduceState* st, double c_bound) {
+  if (st->amax_bits == 0 || !(c_bound < 1.0)) {
+    // no circulation, or a bound of at least ||Gamma||_1: nothing diffuses
+    st->all_out = 1;
     st->done = 1;
   }
 }
 
-__global__ void k_reduce_mark(const double* __restrict__ g, int n, const ReduceState* __restrict__ st,
-                              uint8_t* __restrict__ diffused, uint8_t* __restrict__ tie_flag) {
+__global__ void k_reduce_mark(const double* __restrict__ g, int n, const int* __restrict__ n_dev,
+                              const ReduceState* __restrict__ st, uint8_t* __restrict__ diffused,
+                              uint8_t* __restrict__ tie_flag) {
+  if (n_dev) n = *n_dev;
   const int all_out = st->all_out;
   const unsigned long long T = st->T;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    unsigned long long key = (unsigned long long)__double_as_longlong(fabs(g[i]));
+    const unsigned long long key = (unsigned long long)__double_as_longlong(g[i]) & 0x7FFFFFFFFFFFFFFFull;
     uint8_t d = 0, t = 0;
     if (!all_out) {
       d = key > T;
@@ -186,29 +280,36 @@ __global__ void k_reduce_mark(const double* __restrict__ g, int n, const ReduceS
   }
 }
 
-__global__ void k_reduce_ties(int n, const ReduceState* __restrict__ st, const uint8_t* __restrict__ tie_flag,
-                              const int* __restrict__ tie_rank, uint8_t* __restrict__ diffused) {
+__global__ void k_reduce_ties(int n, const int* __restrict__ n_dev, const ReduceState* __restrict__ st,
+                              const uint8_t* __restrict__ tie_flag, const int* __restrict__ tie_rank,
+                              uint8_t* __restrict__ diffused) {
+  if (n_dev) n = *n_dev;
   const int k_tie = st->k_tie;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     if (tie_flag[i] && tie_rank[i] >= k_tie) diffused[i] = 1;
 }
 
-cudaError_t reduce_select(const double* gamma, int n, double c_bound, uint8_t* diffused, ReduceState* st,
-                          uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds, cudaStream_t s) {
-  int blocks = n > 0 ? (n + kBlock - 1) / kBlock : 1;
-  int pblocks = blocks < 4 * sm_count() ? blocks : 4 * sm_count();
+cudaError_t reduce_select_dev(const double* gamma, int n_bound, const int* n_dev, double c_bound, uint8_t* diffused,
+                              ReduceState* st, uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds,
+                              cudaStream_t s) {
+  int blocks = n_bound > 0 ? (n_bound + kBlock - 1) / kBlock : 1;
+  int pblocks = blocks < 2 * sm_count() ? blocks : 2 * sm_count();
   k_reduce_init<<<1, 256, 0, s>>>(st); note_launch();
-  k_absmax<<<pblocks, kBlock, 0, s>>>(gamma, n, st, ds); note_launch();
+  k_absmax<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, ds); note_launch();
   k_reduce_prepare<<<1, 1, 0, s>>>(st, c_bound); note_launch();
   for (int pass = 0; pass < 8; ++pass) {
-    k_reduce_hist<<<pblocks, kBlock, 0, s>>>(gamma, n, st, pass); note_launch();
-    k_reduce_choose<<<1, 32, 0, s>>>(st, c_bound, pass); note_launch();
+    k_reduce_pass<<<pblocks, 256, 0, s>>>(gamma, n_bound, n_dev, st, c_bound, pass); note_launch();
   }
-  k_reduce_mark<<<pblocks, kBlock, 0, s>>>(gamma, n, st, diffused, tie_flag); note_launch();
-  cudaError_t e = scan_exclusive_u8(tie_flag, tie_rank, n, scan_tmp, s);
+  k_reduce_mark<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, diffused, tie_flag); note_launch();
+  cudaError_t e = scan_exclusive_u8_dev(tie_flag, tie_rank, n_bound, n_dev, scan_tmp, s);
   if (e != cudaSuccess) return e;
-  k_reduce_ties<<<pblocks, kBlock, 0, s>>>(n, st, tie_flag, tie_rank, diffused); note_launch();
+  k_reduce_ties<<<pblocks, kBlock, 0, s>>>(n_bound, n_dev, st, tie_flag, tie_rank, diffused); note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t reduce_select(const double* gamma, int n, double c_bound, uint8_t* diffused, ReduceState* st,
+                          uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds, cudaStream_t s) {
+  return reduce_select_dev(gamma, n, nullptr, c_bound, diffused, st, tie_flag, tie_rank, scan_tmp, ds, s);
 }
 
 }  // namespace vrm

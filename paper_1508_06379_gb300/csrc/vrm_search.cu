@@ -43,9 +43,11 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
                                                        const double2* __restrict__ sxy,
                                                        const float2* __restrict__ sloc,
                                                        const int* __restrict__ sidx, int n,
+                                                       const int* __restrict__ n_dev,
                                                        int* __restrict__ nbr_count, int* __restrict__ nbr_idx,
                                                        uint8_t* __restrict__ seg_mask, int* __restrict__ small,
                                                        DevStats* __restrict__ ds) {
+  if (n_dev) n = *n_dev;
   const Grid g = *gp;
   const int k_cap = c.k_cap;
   const float tie = 2.f * kBand;
@@ -188,8 +190,10 @@ __global__ void __launch_bounds__(kBlock) k_search_masks(Consts c, const Grid* _
                                                          const double2* __restrict__ sxy,
                                                          const float2* __restrict__ sloc,
                                                          const int* __restrict__ sidx, int n,
+                                                         const int* __restrict__ n_dev,
                                                          const uint8_t* __restrict__ flag,
                                                          uint8_t* __restrict__ mask) {
+  if (n_dev) n = *n_dev;
   const Grid g = *gp;
   for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
     const int i = sidx[p];
@@ -230,13 +234,32 @@ __global__ void __launch_bounds__(kBlock) k_search_masks(Consts c, const Grid* _
   }
 }
 
+cudaError_t search_all_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
+                           const float2* sorted_loc, const int* sorted_idx, int n_bound, const int* n_dev,
+                           int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small, DevStats* ds,
+                           cudaStream_t s) {
+  if (n_bound <= 0) return cudaSuccess;
+  int blocks = (n_bound + kBlock - 1) / kBlock;
+  k_search_all<VRM_KCAP_MAX><<<blocks, kBlock, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n_bound,
+                                                        n_dev, nbr_count, nbr_idx, seg_mask, small, ds);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t search_all(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
                        const float2* sorted_loc, const int* sorted_idx, int n, int* nbr_count, int* nbr_idx,
                        uint8_t* seg_mask, int* small, DevStats* ds, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  int blocks = (n + kBlock - 1) / kBlock;
-  k_search_all<VRM_KCAP_MAX><<<blocks, kBlock, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n,
-                                                        nbr_count, nbr_idx, seg_mask, small, ds);
+  return search_all_dev(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n, nullptr, nbr_count, nbr_idx,
+                        seg_mask, small, ds, s);
+}
+
+cudaError_t search_masks_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
+                             const float2* sorted_loc, const int* sorted_idx, int n_bound, const int* n_dev,
+                             const uint8_t* flag, uint8_t* mask, cudaStream_t s) {
+  if (n_bound <= 0) return cudaSuccess;
+  int blocks = (n_bound + kBlock - 1) / kBlock;
+  k_search_masks<<<blocks, kBlock, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n_bound, n_dev, flag,
+                                           mask);
   note_launch();
   return cudaGetLastError();
 }
@@ -244,11 +267,7 @@ cudaError_t search_all(const Consts& c, const Grid* g, const int* cell_start, co
 cudaError_t search_masks(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
                          const float2* sorted_loc, const int* sorted_idx, int n, const uint8_t* flag, uint8_t* mask,
                          cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  int blocks = (n + kBlock - 1) / kBlock;
-  k_search_masks<<<blocks, kBlock, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n, flag, mask);
-  note_launch();
-  return cudaGetLastError();
+  return search_masks_dev(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n, nullptr, flag, mask, s);
 }
 
 }  // namespace vrm

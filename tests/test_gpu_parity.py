@@ -351,3 +351,34 @@ def test_full_size_mixture_step(lib, orc):
     scale = np.abs(g2) + np.abs(g).max() * 1e-30
     assert np.all(np.abs(got - g2) <= 1e-12 * (nu / h ** 2) * dt * 16 * np.abs(g).max() + 4 * np.spacing(scale))
     assert len(mismatch) == 0, (len(mismatch), mismatch[:5])
+
+
+def test_graph_and_eager_steps_agree(lib, orc, monkeypatch):
+    # vrm_step captures the whole step in a CUDA graph (insertion rounds as a
+    # conditional while node); VRM_NO_GRAPH=1 runs the same kernels eagerly
+    x, y, g = vrm_inputs.random_cloud(20000, h=0.01, jitter=0.3, seed=1)
+    h, nu = 0.01, 1e-3
+    dt = (0.5 * h) ** 2 / (4 * nu) / 8
+    n = len(x)
+    outs = []
+    for env in ("0", "1"):
+        monkeypatch.setenv("VRM_NO_GRAPH", env)
+        ctx = lib.VRM(h=h, nu=nu)
+        cap = 2 * n
+        xb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        yb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        xb[:n] = cu(x)
+        yb[:n] = cu(y)
+        gi = cu(g)
+        res = []
+        for rep in range(3):  # replays of the captured graph, then a new buffer set
+            go = torch.zeros(cap, dtype=torch.float64, device="cuda")
+            n2, st = ctx.step(xb, yb, n, gi, go, dt * (rep + 1))
+            res.append((n2, xb[:n2].cpu().numpy().copy(), go[:n2].cpu().numpy().copy(), st["small_ok"]))
+        outs.append(res)
+    for a, b in zip(outs[0], outs[1]):
+        assert a[0] == b[0] and a[3] == b[3]
+        assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+    # and the first against the oracle
+    x2, y2, g2, st_o = orc.step(x, y, g, h, nu, dt)
+    assert outs[0][0][0] == len(x2) and np.array_equal(outs[0][0][2], g2)
