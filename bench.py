@@ -230,8 +230,11 @@ def run_ours(args):
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
         parts += n2
-        for k, v in ctx.stage_times().items():
-            stage_ms[k].append(v)
+        try:
+            for k, v in ctx.stage_times().items():
+                stage_ms[k].append(v)
+        except Exception:
+            pass
     torch.cuda.synchronize()
     t_wall1 = time.time()
     launches = vrm.launch_count() - launches0
@@ -284,7 +287,7 @@ def run_ours(args):
 
     mean_stage = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage_ms.items()}
     dom = max(mean_stage, key=mean_stage.get)
-    roofline = roofline_for(dom, mean_stage[dom], stats, n)
+    roofline = roofline_for(dom, mean_stage[dom], stats, n) if mean_stage[dom] > 0 else None
     if rank != 0:
         if dist:
             dist.barrier()

@@ -238,7 +238,8 @@ vrm_status vrm_set_timing(vrm_ctx* ctx, int32_t enable);
    that step's events. */
 vrm_status vrm_stage_times(vrm_ctx* ctx, float* ms);
 
-/* Kernels launched by this library in this process so far (all contexts). */
+/* Kernels launched by this library in this process so far (all contexts),
+   kernels run by replays of a captured step graph included. */
 int64_t vrm_launch_count(void);
 
 /* Largest cloud vrm_build_neighbourhoods_noalloc accepts. */

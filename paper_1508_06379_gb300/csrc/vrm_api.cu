@@ -59,6 +59,8 @@ struct StepGraph {
   cudaGraphExec_t exec = nullptr;
   const void *x = nullptr, *y = nullptr, *gi = nullptr, *go = nullptr;
   int cap = 0, timing = 0;
+  long long kernels_outer = 0;  // kernel nodes outside the insertion loop
+  long long kernels_body = 0;   // kernel nodes of one insertion round
 };
 
 struct vrm_ctx {
@@ -262,9 +264,15 @@ bool bad_ptr(const void* p, int n) { return n > 0 && p == nullptr; }
 bool misaligned16(const void* p) { return ((uintptr_t)p & 15u) != 0; }
 
 // Records the boundary event in front of stage k (k = VRM_STAGE_COUNT: end).
+// External records so that, inside a captured graph, they become event
+// record nodes that the host can time.
 cudaError_t mark(vrm_ctx* ctx, int k, cudaStream_t st) {
   if (!ctx->timing) return cudaSuccess;
   if (k > 0 && k <= VRM_STAGE_COUNT) ctx->stage_done[k - 1] = 1;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess) return e;
+  if (cap == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(ctx->ev[k], st, cudaEventRecordExternal);
   return cudaEventRecord(ctx->ev[k], st);
 }
 
@@ -355,6 +363,9 @@ bool capture_step(vrm_ctx* ctx, double* x, double* y, int cap, const double* gam
     return false;
   cudaStream_t cs = ctx->cap_stream;
   cudaGraph_t g = nullptr;
+  // kernels recorded into the graph are counted when the graph runs
+  const long long l0 = launch_count();
+  long long body_kernels = 0;
   bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
   const bool capturing = ok;
   ok = ok && enqueue_head(ctx, cs) == cudaSuccess;
@@ -386,8 +397,10 @@ bool capture_step(vrm_ctx* ctx, double* x, double* y, int cap, const double* gam
       ok = cudaStreamBeginCaptureToGraph(ctx->body_stream, body, nullptr, nullptr, 0,
                                          cudaStreamCaptureModeThreadLocal) == cudaSuccess;
       if (ok) {
+        const long long b0 = launch_count();
         ok = round_body(ctx->c, s.st, s.grid, s.rb, cap, s.mask, x, y, handle, true, ctx->body_stream) ==
              cudaSuccess;
+        body_kernels = launch_count() - b0;
         cudaGraph_t got = nullptr;
         const bool ended = cudaStreamEndCapture(ctx->body_stream, &got) == cudaSuccess;
         ok = ok && ended;
@@ -403,6 +416,8 @@ bool capture_step(vrm_ctx* ctx, double* x, double* y, int cap, const double* gam
   ok = ok && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
   if (g) cudaGraphDestroy(g);
   cudaGetLastError();
+  const long long recorded = launch_count() - l0;
+  add_launches(-recorded);
   if (!ok) {
     if (exec) cudaGraphExecDestroy(exec);
     return false;
@@ -415,6 +430,8 @@ bool capture_step(vrm_ctx* ctx, double* x, double* y, int cap, const double* gam
   ctx->graph.go = gamma_out;
   ctx->graph.cap = cap;
   ctx->graph.timing = ctx->timing;
+  ctx->graph.kernels_outer = recorded - body_kernels;
+  ctx->graph.kernels_body = body_kernels;
   return true;
 }
 
@@ -693,6 +710,7 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
     if (r != VRM_OK) return r;
   }
   VRM_CUDA(cudaStreamSynchronize(stream));
+  if (launched) add_launches(ctx->graph.kernels_outer + ctx->graph.kernels_body * s.h_state->round);
   if (s.h_grid->nonfinite || s.h_ds->nonfinite) return VRM_ERR_ARG;
   fill_front_stats(ctx, n, st);
   st->small_ok = s.h_ds->small_ok;

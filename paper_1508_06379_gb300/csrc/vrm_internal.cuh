@@ -162,6 +162,7 @@ int persistent_blocks(int block_threads, int per_sm);
 int sm_count();
 // Counts kernel launches of the library (vrm_launch_count).
 void note_launch();
+void add_launches(long long k);
 long long launch_count();
 
 // vrm_grid.cu
