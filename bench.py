@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mixture_1m", choices=["mixture_1m", "lamb_oseen_h002"])
+    ap.add_argument("--workload", default="mixture_1m", choices=["mixture_1m", "lamb_oseen_h002", "batched_64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -409,10 +409,178 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+BATCH_DESC = ("64 independent jittered mixture clouds, log-uniform 1e4..5e5 particles, h ~ U[1e-3, 4e-3], "
+              "jitter 0.3h, nu=1e-3, C_diff=1, insertion on, FP64, one vrm_step_batched call per step")
+
+
+def batched_workload():
+    import vrm_inputs
+    clouds = vrm_inputs.batched_clouds()
+    nu = 1e-3
+    return clouds, nu, [(0.5 * h) ** 2 / (4 * nu) / 8 for (_, _, _, h) in clouds]
+
+
+def run_batched(args):
+    """The 64-cloud workload: one vrm_step_batched call per step (one graph
+    with a branch per cloud) against the same clouds stepped one after the
+    other through vrm_step (each cloud its own captured graph)."""
+    import torch
+
+    import paper_1508_06379_gb300 as vrm
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    vrm.build()
+    clouds, nu, dts = batched_workload()
+    dev = torch.device("cuda", local)
+    devs = []
+    for (x, y, g, h), dt in zip(clouds, dts):
+        n = len(x)
+        cap = int(n * 1.6) + 4096
+        xb = torch.zeros(cap, dtype=torch.float64, device=dev)
+        yb = torch.zeros(cap, dtype=torch.float64, device=dev)
+        xb[:n] = torch.from_numpy(x).to(dev)
+        yb[:n] = torch.from_numpy(y).to(dev)
+        devs.append(dict(x=xb, y=yb, gamma_in=torch.from_numpy(g).to(dev),
+                         gamma_out=torch.zeros(cap, dtype=torch.float64, device=dev), n=n, h=h, dt=dt))
+    batch = vrm.VRMBatch(max_clouds=len(devs), nu=nu)
+    singles = [vrm.VRM(h=d["h"], nu=nu) for d in devs]
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def one_batched():
+        res, st = batch.step(devs)
+        return sum(r[0] for r in res), st
+
+    def one_sequential():
+        parts = 0
+        for d, c in zip(devs, singles):
+            n2, _ = c.step(d["x"], d["y"], d["n"], d["gamma_in"], d["gamma_out"], d["dt"], stats=False)
+            parts += n2
+        return parts, None
+
+    def timed(fn, steps):
+        ms, parts, st = 0.0, 0, None
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            p, s_ = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            parts += p
+            st = s_ or st
+        return ms, parts, st
+
+    for _ in range(args.warmup):
+        one_batched()
+        one_sequential()
+    torch.cuda.synchronize()
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(local).uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    clocks = Clocks(gpu_id)
+    time.sleep(0.5)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = vrm.launch_count()
+    t_wall0 = time.time()
+    ms, parts, stats = timed(one_batched, args.steps)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    launches = vrm.launch_count() - launches0
+    ck = clocks.stop(t_wall0, t_wall1)
+    seq_ms, seq_parts, _ = timed(one_sequential, args.steps)
+    if dist:
+        t = torch.tensor([ms, float(parts), seq_ms, float(seq_parts)], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        ms_max, parts_all, seq_max, seq_all = tmax[0].item(), t[1].item(), tmax[2].item(), t[3].item()
+    else:
+        ms_max, parts_all, seq_max, seq_all = ms, float(parts), seq_ms, float(seq_parts)
+    value = parts_all / (ms_max * 1e-3)
+    seq_value = seq_all / (seq_max * 1e-3)
+
+    # end to end: host buffers in, dGamma and inserted positions out, per step
+    hosts = [(torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory(), torch.from_numpy(g).pin_memory(),
+              torch.empty(d["x"].numel(), dtype=torch.float64).pin_memory(),
+              torch.empty(d["x"].numel(), dtype=torch.float64).pin_memory(),
+              torch.empty(d["x"].numel(), dtype=torch.float64).pin_memory()) for (x, y, g, _), d in zip(clouds, devs)]
+    e2e_ms, e2e_parts, h2d, d2h = 0.0, 0, 0, 0
+    for _ in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for d, (xh, yh, gh, _, _, _) in zip(devs, hosts):
+            n = d["n"]
+            d["x"][:n].copy_(xh, non_blocking=True)
+            d["y"][:n].copy_(yh, non_blocking=True)
+            d["gamma_in"].copy_(gh, non_blocking=True)
+        res, _ = batch.step(devs, stats=False)
+        h2d = d2h = 0
+        for d, (n2, _), (_, _, _, go_h, xo_h, yo_h) in zip(devs, res, hosts):
+            n = d["n"]
+            go_h[:n2].copy_(d["gamma_out"][:n2], non_blocking=True)
+            xo_h[n:n2].copy_(d["x"][n:n2], non_blocking=True)
+            yo_h[n:n2].copy_(d["y"][n:n2], non_blocking=True)
+            h2d += 24 * n
+            d2h += 8 * n2 + 16 * (n2 - n)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+        e2e_parts += sum(r[0] for r in res)
+    e2e_value = e2e_parts / (e2e_ms * 1e-3)
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    ns = [d["n"] for d in devs]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": BATCH_DESC, "clouds": len(devs), "n_total": int(sum(ns)), "n_min": int(min(ns)),
+                   "n_max": int(max(ns)), "nu": nu, "n_out": int(stats["n_out"]),
+                   "n_diffused": int(stats["n_diffused"]), "n_inserted": int(stats["n_inserted"]),
+                   "l2": "flushed between steps (512 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "sequential": {"value": seq_value, "unit": UNIT, "ms_per_step": seq_max / args.steps,
+                       "what": "the same clouds through vrm_step one after the other, each its own captured graph"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "roofline": None,
+        "lp": {"small_solved": int(stats["lp_small_solved"]), "small_pivots": int(stats["lp_small_pivots"]),
+               "full_solved": int(stats["lp_full_solved"]), "max_pivots": int(stats["max_pivots"])},
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched_64":
+        run_batched(args)
     else:
         run_ours(args)
 

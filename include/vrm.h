@@ -152,7 +152,8 @@ void vrm_destroy(vrm_ctx* ctx);
  * n_out:     host; receives n'.  Synchronises the stream.
  * Errors: VRM_ERR_ARG on null pointers, n < 0, n > capacity or non-finite
  * input; VRM_ERR_CAPACITY when n' would exceed capacity (stats->n_out, if
- * given, then holds the count needed).
+ * given, then holds the count after the first round that did not fit: a
+ * lower bound of the capacity needed, since later rounds were not run).
  */
 vrm_status vrm_insert_reduce(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capacity, const double* gamma,
                              uint8_t* diffused, int32_t* n_out, vrm_stats* stats, cudaStream_t stream);
@@ -229,6 +230,39 @@ vrm_status vrm_apply(vrm_ctx* ctx, int32_t n, int32_t n_gamma, const double* gam
  */
 vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capacity, const double* gamma_in,
                     double* gamma_out, double dt, int32_t* n_out, vrm_stats* stats, cudaStream_t stream);
+
+/*
+ * Batched steps: many independent clouds (each with its own spacing h and
+ * step dt) advanced by one call.  The clouds' steps are captured once as
+ * parallel branches of one CUDA graph (per-cloud insertion loops included)
+ * and replayed while the clouds' buffers, capacities and spacings stay the
+ * same, so uneven clouds share the GPU.  Every cloud gets exactly the result
+ * of vrm_step on it with the batch's parameters and its own h.
+ */
+typedef struct vrm_cloud {
+  double* x;              /* device, capacity entries; inserted points appended */
+  double* y;
+  const double* gamma_in; /* device, n entries (read only) */
+  double* gamma_out;      /* device, capacity entries, not overlapping gamma_in */
+  int32_t n;              /* particles given */
+  int32_t capacity;
+  double h;               /* particle spacing of this cloud */
+  double dt;              /* Euler step of this cloud */
+  int32_t n_out;          /* out: particles after insertion (on VRM_ERR_CAPACITY: the count after the
+                             first round that did not fit, a lower bound of the capacity needed) */
+  int32_t status;         /* out: VRM_OK, VRM_ERR_ARG or VRM_ERR_CAPACITY for this cloud */
+} vrm_cloud;
+
+typedef struct vrm_batch vrm_batch;
+
+/* A batch for up to max_clouds clouds; p gives every parameter but h. */
+vrm_status vrm_batch_create(const vrm_params* p, int32_t max_clouds, vrm_batch** out);
+void vrm_batch_destroy(vrm_batch* b);
+/* One step of every cloud.  Synchronises the stream.  Returns VRM_OK when
+   every cloud succeeded, else the first failing cloud's status (each cloud's
+   own status is in clouds[c].status).  stats (host, optional) receives the
+   sums over the clouds (maxima for the max_* fields). */
+vrm_status vrm_step_batched(vrm_batch* b, vrm_cloud* clouds, int32_t n_clouds, vrm_stats* stats, cudaStream_t stream);
 
 /* Per-stage timing of vrm_step with CUDA events recorded on the call's
    stream between the stages.  Off by default; enable != 0 turns it on. */

@@ -44,6 +44,13 @@ class Stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class Cloud(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("gamma_in", ctypes.c_void_p),
+                ("gamma_out", ctypes.c_void_p), ("n", ctypes.c_int32), ("capacity", ctypes.c_int32),
+                ("h", ctypes.c_double), ("dt", ctypes.c_double), ("n_out", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
 class VRMError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -67,6 +74,9 @@ SIGNATURES = {
     "vrm_stage_times": (ctypes.c_int, [P, P]),
     "vrm_launch_count": (ctypes.c_int64, []),
     "vrm_build_neighbourhoods_noalloc": (ctypes.c_int, [P, P, P, I32, P, P, P, P, P, P]),
+    "vrm_batch_create": (ctypes.c_int, [P, I32, P]),
+    "vrm_batch_destroy": (None, [P]),
+    "vrm_step_batched": (ctypes.c_int, [P, P, I32, P, P]),
 }
 NOALLOC_MAX_N = 65536
 STAGES = ("reduce", "grid", "insert", "search", "lp_small", "lp_full", "apply")
@@ -264,3 +274,54 @@ class VRM:
                                ctypes.byref(s) if stats else None, _stream())
         self._check(st, "vrm_step")
         return n_out.value, s.as_dict()
+
+
+class VRMBatch:
+    """Many independent clouds advanced by one call (vrm_step_batched); every
+    parameter but the spacing h is shared."""
+
+    def __init__(self, max_clouds, nu, r=0.5, R=2.0, c_diff=1.0, order=1, k_cap=32, max_rounds=8, fallback=True):
+        self.lib = _lib_handle()
+        p = Params()
+        self.lib.vrm_default_params(ctypes.byref(p))
+        p.h, p.nu, p.r, p.R, p.c_diff = 1.0, float(nu), float(r), float(R), float(c_diff)
+        p.order, p.k_cap, p.max_rounds, p.fallback = int(order), int(k_cap), int(max_rounds), int(bool(fallback))
+        self.params = p
+        self.max_clouds = int(max_clouds)
+        h_ = ctypes.c_void_p()
+        st = self.lib.vrm_batch_create(ctypes.byref(p), self.max_clouds, ctypes.byref(h_))
+        if st != VRM_OK:
+            raise VRMError(st, "vrm_batch_create")
+        self.b = h_
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.vrm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, clouds, stats=True, raise_on_error=True):
+        """clouds: sequence of dicts with x, y, gamma_in, gamma_out (CUDA float64
+        tensors, capacity = x.numel()), n, h, dt.  Returns (per-cloud list of
+        (n_out, status), summed stats)."""
+        arr = (Cloud * max(len(clouds), 1))()
+        for k, c in enumerate(clouds):
+            cap = c["x"].numel()
+            n = int(c["n"])
+            arr[k].x = _ptr(c["x"], torch.float64, "x", n)
+            arr[k].y = _ptr(c["y"], torch.float64, "y", cap)
+            arr[k].gamma_in = _ptr(c["gamma_in"], torch.float64, "gamma_in", n)
+            arr[k].gamma_out = _ptr(c["gamma_out"], torch.float64, "gamma_out", cap)
+            arr[k].n, arr[k].capacity = n, cap
+            arr[k].h, arr[k].dt = float(c["h"]), float(c["dt"])
+        s = Stats()
+        st = self.lib.vrm_step_batched(self.b, arr, len(clouds), ctypes.byref(s) if stats else None, _stream())
+        out = [(arr[k].n_out, arr[k].status) for k in range(len(clouds))]
+        if st != VRM_OK and raise_on_error:
+            raise VRMError(st, "vrm_step_batched")
+        return out, s.as_dict()

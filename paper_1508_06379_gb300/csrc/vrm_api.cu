@@ -68,6 +68,7 @@ struct vrm_ctx {
   Consts c;
   int device = 0;
   Scratch s;
+  long long scratch_gen = 0;  // bumped whenever the scratch is reallocated
   // per-stage timing: ev[k] is recorded where stage k starts, ev[k+1] where it ends
   int timing = 0;
   int events_ready = 0;
@@ -77,6 +78,30 @@ struct vrm_ctx {
   int use_graph = 1;
   StepGraph graph;
   cudaStream_t cap_stream = nullptr, body_stream = nullptr;
+};
+
+// What a batch graph was captured for: per cloud the buffers, capacity and
+// spacing (n and dt travel in the per-cloud parameter copies).
+struct BatchKey {
+  const void *x = nullptr, *y = nullptr, *gi = nullptr, *go = nullptr;
+  int cap = 0;
+  double h = 0.0;
+  long long scratch_gen = -1;  // the sub-context's scratch generation
+};
+
+struct vrm_batch {
+  vrm_params base;
+  int max_clouds = 0;
+  int use_graph = 1;
+  vrm_ctx** sub = nullptr;           // one context per cloud slot
+  cudaStream_t* branch = nullptr;    // capture streams, one per cloud slot
+  cudaEvent_t* join = nullptr;
+  cudaStream_t cap_stream = nullptr, body_stream = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  BatchKey* key = nullptr;           // per slot; cap 0 = slot not in the graph
+  long long* kernels_outer = nullptr;
+  long long* kernels_body = nullptr;
 };
 
 namespace {
@@ -114,6 +139,7 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   if (cap <= s.cap && s.ds) return cudaSuccess;
   cudaStreamSynchronize(st);
   drop_graph(ctx);
+  ++ctx->scratch_gen;
   long want = cap;
   if (s.cap > 0 && want < (long)s.cap + s.cap / 4) want = (long)s.cap + s.cap / 4;
   if (want < 1024) want = 1024;
@@ -353,22 +379,16 @@ cudaError_t enqueue_head(vrm_ctx* ctx, cudaStream_t st) {
   return e;
 }
 
-// Captures the whole step on the context's streams; the insertion rounds are
-// a conditional while node.  Returns false (graph left empty) on failure.
-bool capture_step(vrm_ctx* ctx, double* x, double* y, int cap, const double* gamma_in, double* gamma_out) {
+// Records one context's whole step into the graph being captured on cs: the
+// insertion rounds become a conditional while node whose body is captured on
+// body_stream.  Kernel counts of the outer part and of one round are
+// returned for the launch accounting.
+bool record_step(vrm_ctx* ctx, cudaStream_t cs, cudaStream_t body_stream, double* x, double* y, int cap,
+                 const double* gamma_in, double* gamma_out, long long* outer_kernels, long long* body_kernels) {
   Scratch& s = ctx->s;
-  if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-    return false;
-  if (!ctx->body_stream && cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking) != cudaSuccess)
-    return false;
-  cudaStream_t cs = ctx->cap_stream;
-  cudaGraph_t g = nullptr;
-  // kernels recorded into the graph are counted when the graph runs
   const long long l0 = launch_count();
-  long long body_kernels = 0;
-  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-  const bool capturing = ok;
-  ok = ok && enqueue_head(ctx, cs) == cudaSuccess;
+  long long bk = 0;
+  bool ok = enqueue_head(ctx, cs) == cudaSuccess;
   ok = ok && enqueue_front(ctx, x, y, cap, gamma_in, s.diffused, cs) == cudaSuccess;
   cudaGraphConditionalHandle handle = 0;
   if (ok) {
@@ -394,20 +414,40 @@ bool capture_step(vrm_ctx* ctx, double* x, double* y, int cap, const double* gam
                    cudaSuccess;
     if (ok) {
       cudaGraph_t body = cp.conditional.phGraph_out[0];
-      ok = cudaStreamBeginCaptureToGraph(ctx->body_stream, body, nullptr, nullptr, 0,
-                                         cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      ok = cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+           cudaSuccess;
       if (ok) {
         const long long b0 = launch_count();
-        ok = round_body(ctx->c, s.st, s.grid, s.rb, cap, s.mask, x, y, handle, true, ctx->body_stream) ==
-             cudaSuccess;
-        body_kernels = launch_count() - b0;
+        ok = round_body(ctx->c, s.st, s.grid, s.rb, cap, s.mask, x, y, handle, true, body_stream) == cudaSuccess;
+        bk = launch_count() - b0;
         cudaGraph_t got = nullptr;
-        const bool ended = cudaStreamEndCapture(ctx->body_stream, &got) == cudaSuccess;
+        const bool ended = cudaStreamEndCapture(body_stream, &got) == cudaSuccess;
         ok = ok && ended;
       }
     }
   }
   ok = ok && enqueue_back(ctx, x, y, cap, gamma_in, gamma_out, cs) == cudaSuccess;
+  const long long recorded = launch_count() - l0;
+  add_launches(-recorded);  // counted when the graph runs
+  *outer_kernels = recorded - bk;
+  *body_kernels = bk;
+  return ok;
+}
+
+// Captures the whole step on the context's streams; the insertion rounds are
+// a conditional while node.  Returns false (graph left empty) on failure.
+bool capture_step(vrm_ctx* ctx, double* x, double* y, int cap, const double* gamma_in, double* gamma_out) {
+  Scratch& s = ctx->s;
+  if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return false;
+  if (!ctx->body_stream && cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return false;
+  cudaStream_t cs = ctx->cap_stream;
+  cudaGraph_t g = nullptr;
+  long long outer = 0, body = 0;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  const bool capturing = ok;
+  ok = ok && record_step(ctx, cs, ctx->body_stream, x, y, cap, gamma_in, gamma_out, &outer, &body);
   if (capturing) {
     const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
     ok = ok && ended && g;
@@ -416,8 +456,6 @@ bool capture_step(vrm_ctx* ctx, double* x, double* y, int cap, const double* gam
   ok = ok && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
   if (g) cudaGraphDestroy(g);
   cudaGetLastError();
-  const long long recorded = launch_count() - l0;
-  add_launches(-recorded);
   if (!ok) {
     if (exec) cudaGraphExecDestroy(exec);
     return false;
@@ -430,8 +468,8 @@ bool capture_step(vrm_ctx* ctx, double* x, double* y, int cap, const double* gam
   ctx->graph.go = gamma_out;
   ctx->graph.cap = cap;
   ctx->graph.timing = ctx->timing;
-  ctx->graph.kernels_outer = recorded - body_kernels;
-  ctx->graph.kernels_body = body_kernels;
+  ctx->graph.kernels_outer = outer;
+  ctx->graph.kernels_body = body;
   return true;
 }
 
@@ -729,4 +767,246 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
   return VRM_OK;
 }
 
+vrm_status vrm_batch_create(const vrm_params* p, int32_t max_clouds, vrm_batch** out) {
+  if (!out) return VRM_ERR_ARG;
+  *out = nullptr;
+  if (max_clouds < 1 || max_clouds > 4096) return VRM_ERR_ARG;
+  vrm_status st = check_params(p);
+  if (st != VRM_OK) return st;
+  vrm_batch* b = new (std::nothrow) vrm_batch();
+  if (!b) return VRM_ERR_CUDA;
+  b->base = *p;
+  b->max_clouds = max_clouds;
+  const char* env = getenv("VRM_NO_GRAPH");
+  b->use_graph = !(env && env[0] == '1');
+  b->sub = new (std::nothrow) vrm_ctx*[max_clouds]();
+  b->branch = new (std::nothrow) cudaStream_t[max_clouds]();
+  b->join = new (std::nothrow) cudaEvent_t[max_clouds]();
+  b->key = new (std::nothrow) BatchKey[max_clouds]();
+  b->kernels_outer = new (std::nothrow) long long[max_clouds]();
+  b->kernels_body = new (std::nothrow) long long[max_clouds]();
+  if (!b->sub || !b->branch || !b->join || !b->key || !b->kernels_outer || !b->kernels_body) {
+    vrm_batch_destroy(b);
+    return VRM_ERR_CUDA;
+  }
+  *out = b;
+  return VRM_OK;
+}
+
+void vrm_batch_destroy(vrm_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (int c = 0; c < b->max_clouds; ++c) {
+    if (b->sub && b->sub[c]) vrm_destroy(b->sub[c]);
+    if (b->branch && b->branch[c]) cudaStreamDestroy(b->branch[c]);
+    if (b->join && b->join[c]) cudaEventDestroy(b->join[c]);
+  }
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->body_stream) cudaStreamDestroy(b->body_stream);
+  delete[] b->sub;
+  delete[] b->branch;
+  delete[] b->join;
+  delete[] b->key;
+  delete[] b->kernels_outer;
+  delete[] b->kernels_body;
+  delete b;
+}
+
 }  // extern "C"
+
+namespace {
+
+// Captures every active cloud's step as one branch of one graph: a fork
+// event on the capture stream, each cloud's whole step (with its own
+// insertion while node) on its own branch stream, and joins back.
+bool capture_batch(vrm_batch* b, const vrm_cloud* clouds, int n_clouds, const bool* active) {
+  if (!b->cap_stream && cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return false;
+  if (!b->body_stream && cudaStreamCreateWithFlags(&b->body_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return false;
+  if (!b->fork && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return false;
+  for (int c = 0; c < n_clouds; ++c) {
+    if (!active[c]) continue;
+    if (!b->branch[c] && cudaStreamCreateWithFlags(&b->branch[c], cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (!b->join[c] && cudaEventCreateWithFlags(&b->join[c], cudaEventDisableTiming) != cudaSuccess) return false;
+  }
+  cudaStream_t cs = b->cap_stream;
+  cudaGraph_t g = nullptr;
+  bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  const bool capturing = ok;
+  ok = ok && cudaEventRecord(b->fork, cs) == cudaSuccess;
+  for (int c = 0; c < n_clouds && ok; ++c) {
+    if (!active[c]) continue;
+    const vrm_cloud& C = clouds[c];
+    ok = cudaStreamWaitEvent(b->branch[c], b->fork, 0) == cudaSuccess;
+    ok = ok && record_step(b->sub[c], b->branch[c], b->body_stream, C.x, C.y, C.capacity, C.gamma_in, C.gamma_out,
+                           &b->kernels_outer[c], &b->kernels_body[c]);
+    ok = ok && cudaEventRecord(b->join[c], b->branch[c]) == cudaSuccess;
+    ok = ok && cudaStreamWaitEvent(cs, b->join[c], 0) == cudaSuccess;
+  }
+  if (capturing) {
+    const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
+    ok = ok && ended && g;
+  }
+  cudaGraphExec_t exec = nullptr;
+  ok = ok && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  for (int c = 0; c < b->max_clouds; ++c) b->key[c] = BatchKey{};
+  if (!ok) {
+    if (exec) cudaGraphExecDestroy(exec);
+    return false;
+  }
+  b->exec = exec;
+  for (int c = 0; c < n_clouds; ++c) {
+    if (!active[c]) continue;
+    const vrm_cloud& C = clouds[c];
+    b->key[c] = BatchKey{C.x, C.y, C.gamma_in, C.gamma_out, C.capacity, C.h, b->sub[c]->scratch_gen};
+  }
+  return true;
+}
+
+// Outcome of one cloud's step from its pinned mirrors (as in vrm_step).
+vrm_status finish_cloud(vrm_ctx* ctx, vrm_cloud& C, vrm_stats* st) {
+  Scratch& s = ctx->s;
+  memset(st, 0, sizeof(*st));
+  if (s.h_grid->nonfinite || s.h_ds->nonfinite) return VRM_ERR_ARG;
+  fill_front_stats(ctx, C.n, st);
+  st->small_ok = s.h_ds->small_ok;
+  st->full_ok = s.h_ds->full_ok;
+  st->no_stencil = s.h_ds->no_stencil;
+  st->max_pivots = s.h_ds->max_pivots;
+  st->max_count = s.h_ds->max_count;
+  st->max_dt_ratio = ratio_from_bits(s.h_ds->max_dt_ratio_bits);
+  st->lp_small_solved = s.h_ds->lp_small_solved;
+  st->lp_small_pivots = (int64_t)s.h_ds->lp_small_pivots;
+  st->lp_full_solved = s.h_ds->lp_full_solved;
+  st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
+  C.n_out = st->n_out;
+  if (s.h_state->overflow) return VRM_ERR_CAPACITY;
+  if (s.h_ds->max_count > ctx->p.k_cap) return VRM_ERR_CAPACITY;
+  return VRM_OK;
+}
+
+void add_stats(vrm_stats* t, const vrm_stats& a) {
+  t->n_in += a.n_in;
+  t->n_out += a.n_out;
+  t->n_diffused += a.n_diffused;
+  t->n_inserted += a.n_inserted;
+  t->open_segments += a.open_segments;
+  t->small_ok += a.small_ok;
+  t->full_ok += a.full_ok;
+  t->no_stencil += a.no_stencil;
+  if (a.rounds > t->rounds) t->rounds = a.rounds;
+  if (a.max_pivots > t->max_pivots) t->max_pivots = a.max_pivots;
+  if (a.max_count > t->max_count) t->max_count = a.max_count;
+  if (a.max_dt_ratio > t->max_dt_ratio) t->max_dt_ratio = a.max_dt_ratio;
+  t->lp_small_solved += a.lp_small_solved;
+  t->lp_small_pivots += a.lp_small_pivots;
+  t->lp_full_solved += a.lp_full_solved;
+  t->lp_full_pivots += a.lp_full_pivots;
+}
+
+}  // namespace
+
+extern "C" vrm_status vrm_step_batched(vrm_batch* b, vrm_cloud* clouds, int32_t n_clouds, vrm_stats* stats,
+                                       cudaStream_t stream) {
+  if (!b || n_clouds < 0 || n_clouds > b->max_clouds || (n_clouds > 0 && !clouds)) return VRM_ERR_ARG;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  // argument checks of every cloud before any work
+  for (int c = 0; c < n_clouds; ++c) {
+    vrm_cloud& C = clouds[c];
+    C.n_out = 0;
+    C.status = VRM_OK;
+    const int n = C.n, cap = C.capacity;
+    bool bad = n < 0 || cap < n || !std::isfinite(C.dt) || !(C.h > 0) || !std::isfinite(C.h);
+    bad = bad || bad_ptr(C.x, n) || bad_ptr(C.y, n) || bad_ptr(C.gamma_in, n) || bad_ptr(C.gamma_out, cap);
+    bad = bad || (n > 0 && C.gamma_out < C.gamma_in + n && C.gamma_in < C.gamma_out + cap);
+    if (bad) C.status = VRM_ERR_ARG;
+  }
+  for (int c = 0; c < n_clouds; ++c)
+    if (clouds[c].status != VRM_OK) return VRM_ERR_ARG;
+  bool* active = new (std::nothrow) bool[n_clouds > 0 ? n_clouds : 1];
+  if (!active) return VRM_ERR_CUDA;
+  vrm_status result = VRM_OK;
+  bool hit = b->exec != nullptr;
+  VRM_CUDA(cudaStreamSynchronize(stream));
+  for (int c = 0; c < n_clouds && result == VRM_OK; ++c) {
+    vrm_cloud& C = clouds[c];
+    active[c] = C.n > 0;
+    if (!active[c]) {
+      hit = hit && b->key[c].cap == 0;
+      continue;
+    }
+    vrm_params p = b->base;
+    p.h = C.h;
+    if (!b->sub[c]) {
+      if (vrm_create(&p, &b->sub[c]) != VRM_OK) result = VRM_ERR_CUDA;
+    } else if (b->sub[c]->p.h != C.h) {
+      b->sub[c]->p = p;
+      fill_consts(p, b->sub[c]->c);
+      drop_graph(b->sub[c]);
+    }
+    if (result != VRM_OK) break;
+    vrm_ctx* ctx = b->sub[c];
+    if (ensure_scratch(ctx, C.capacity, stream) != cudaSuccess) {
+      result = VRM_ERR_CUDA;
+      break;
+    }
+    StepState P;
+    memset(&P, 0, sizeof(P));
+    P.n = C.n;
+    P.capacity = C.capacity;
+    P.dt = C.dt;
+    P.max_rounds = ctx->p.max_rounds;
+    *ctx->s.h_params = P;
+    const BatchKey& K = b->key[c];
+    hit = hit && K.x == C.x && K.y == C.y && K.gi == C.gamma_in && K.go == C.gamma_out && K.cap == C.capacity &&
+          K.h == C.h && K.scratch_gen == ctx->scratch_gen;
+  }
+  for (int c = n_clouds; c < b->max_clouds && hit; ++c) hit = b->key[c].cap == 0;
+  if (result != VRM_OK) {
+    delete[] active;
+    return result;
+  }
+  bool launched = false;
+  if (b->use_graph) {
+    if (!hit && !capture_batch(b, clouds, n_clouds, active)) b->use_graph = 0;
+    if (b->use_graph) {
+      if (cudaGraphLaunch(b->exec, stream) != cudaSuccess) {
+        delete[] active;
+        return VRM_ERR_CUDA;
+      }
+      launched = true;
+    }
+  }
+  if (!launched) {
+    // one cloud after the other, each step eager
+    for (int c = 0; c < n_clouds && result == VRM_OK; ++c) {
+      if (!active[c]) continue;
+      const vrm_cloud& C = clouds[c];
+      result = run_step_eager(b->sub[c], C.x, C.y, C.capacity, C.gamma_in, C.gamma_out, b->sub[c]->s.diffused, true,
+                              stream);
+    }
+  }
+  if (cudaStreamSynchronize(stream) != cudaSuccess) result = VRM_ERR_CUDA;
+  if (result != VRM_OK) {
+    delete[] active;
+    return result;
+  }
+  vrm_status first_bad = VRM_OK;
+  for (int c = 0; c < n_clouds; ++c) {
+    if (!active[c]) continue;
+    vrm_ctx* ctx = b->sub[c];
+    if (launched) add_launches(b->kernels_outer[c] + b->kernels_body[c] * ctx->s.h_state->round);
+    vrm_stats one;
+    const vrm_status r = finish_cloud(ctx, clouds[c], &one);
+    clouds[c].status = r;
+    if (r != VRM_OK && first_bad == VRM_OK) first_bad = r;
+    if (stats) add_stats(stats, one);
+  }
+  delete[] active;
+  return first_bad;
+}
