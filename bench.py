@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixture_1m", choices=["mixture_1m", "lamb_oseen_h002", "batched_64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
+    ap.add_argument("--schedule-cache", default=None,
+                    help="JSON cache of tuned schedules (default: $VRM_SCHEDULE_CACHE or ~/.cache)")
     return ap.parse_args()
 
 
@@ -196,6 +199,11 @@ def run_ours(args):
     gi = torch.from_numpy(g).to(dev)
     go = torch.zeros(cap, dtype=torch.float64, device=dev)
     ctx = vrm.VRM(h=h, nu=nu)
+    schedule = None
+    if not args.no_autotune:
+        from paper_1508_06379_gb300 import autotune
+        schedule = autotune.Autotuner(args.schedule_cache).apply(
+            ctx, dict(x=xb, y=yb, n=n, gamma_in=gi, gamma_out=go, dt=dt))
     ctx.set_timing(True)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -306,6 +314,7 @@ def run_ours(args):
         "clocks": ck,
         "roofline": roofline,
         "stage_ms": {k: round(v, 4) for k, v in mean_stage.items()},
+        "schedule": schedule,
         "lp": {"small_solved": int(stats["lp_small_solved"]), "small_pivots": int(stats["lp_small_pivots"]),
                "full_solved": int(stats["lp_full_solved"]), "max_pivots": int(stats["max_pivots"])},
         "cpu_baseline": cpu,
@@ -451,6 +460,13 @@ def run_batched(args):
                          gamma_out=torch.zeros(cap, dtype=torch.float64, device=dev), n=n, h=h, dt=dt))
     batch = vrm.VRMBatch(max_clouds=len(devs), nu=nu)
     singles = [vrm.VRM(h=d["h"], nu=nu) for d in devs]
+    schedules = None
+    if not args.no_autotune:
+        from paper_1508_06379_gb300 import autotune
+        chosen = autotune.Autotuner(args.schedule_cache).tune_batch(batch, devs)
+        schedules = {}
+        for k, s in chosen.items():
+            schedules.setdefault("n~2^%d" % autotune.bucket(devs[k]["n"]), s)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -559,7 +575,9 @@ def run_batched(args):
                    "n_diffused": int(stats["n_diffused"]), "n_inserted": int(stats["n_inserted"]),
                    "l2": "flushed between steps (512 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "sequential": {"value": seq_value, "unit": UNIT, "ms_per_step": seq_max / args.steps,
-                       "what": "the same clouds through vrm_step one after the other, each its own captured graph"},
+                       "what": "the same clouds through vrm_step one after the other, each its own captured graph "
+                               "with the default schedule"},
+        "schedules": schedules,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "clocks": ck,

@@ -255,6 +255,37 @@ typedef struct vrm_cloud {
 
 typedef struct vrm_batch vrm_batch;
 
+/*
+ * Launch schedule of the step's three largest kernels.  No field changes any
+ * result (every schedule gives bit-identical output); they trade occupancy,
+ * registers and tail effects, and the best choice depends on the cloud's size.
+ * An autotuner (paper_1508_06379_gb300.autotune) times the candidates and
+ * caches the fastest per size bucket.
+ *   row_cap:          neighbour entries the search keeps per row: 16, 24 or
+ *                     up to k_cap (32 by default).  A step whose rows need
+ *                     more than row_cap but at most k_cap is repeated once
+ *                     with row_cap = k_cap, which the context then keeps.
+ *   search_block:     threads per block of the neighbourhood search (32..256, multiple of 32).
+ *   lp_block:         threads per block of the small-neighbourhood LP, one particle per thread (32..128, multiple of 32).
+ *   lp_blocks_per_sm: the small LP's grid is capped at this many blocks per SM (1..64).
+ *   apply_block:      threads per block of the application (32..256, multiple of 32).
+ * Setting a schedule drops any captured step graph; VRM_ERR_ARG if a field
+ * is out of range.
+ */
+typedef struct vrm_schedule {
+  int32_t row_cap;
+  int32_t search_block;
+  int32_t lp_block;
+  int32_t lp_blocks_per_sm;
+  int32_t apply_block;
+  int32_t reserved[3];
+} vrm_schedule;
+
+vrm_status vrm_get_schedule(const vrm_ctx* ctx, vrm_schedule* out);
+vrm_status vrm_set_schedule(vrm_ctx* ctx, const vrm_schedule* s);
+/* The schedule of cloud slot `slot` of a batch (used from the next vrm_step_batched on). */
+vrm_status vrm_batch_set_schedule(vrm_batch* b, int32_t slot, const vrm_schedule* s);
+
 /* A batch for up to max_clouds clouds; p gives every parameter but h. */
 vrm_status vrm_batch_create(const vrm_params* p, int32_t max_clouds, vrm_batch** out);
 void vrm_batch_destroy(vrm_batch* b);

@@ -51,6 +51,24 @@ class Cloud(ctypes.Structure):
                 ("status", ctypes.c_int32)]
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [("row_cap", ctypes.c_int32), ("search_block", ctypes.c_int32), ("lp_block", ctypes.c_int32),
+                ("lp_blocks_per_sm", ctypes.c_int32), ("apply_block", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+    FIELDS = ("row_cap", "search_block", "lp_block", "lp_blocks_per_sm", "apply_block")
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k in self.FIELDS}
+
+    @classmethod
+    def from_dict(cls, d):
+        s = cls()
+        for k in cls.FIELDS:
+            setattr(s, k, int(d[k]))
+        return s
+
+
 class VRMError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -77,6 +95,9 @@ SIGNATURES = {
     "vrm_batch_create": (ctypes.c_int, [P, I32, P]),
     "vrm_batch_destroy": (None, [P]),
     "vrm_step_batched": (ctypes.c_int, [P, P, I32, P, P]),
+    "vrm_get_schedule": (ctypes.c_int, [P, P]),
+    "vrm_set_schedule": (ctypes.c_int, [P, P]),
+    "vrm_batch_set_schedule": (ctypes.c_int, [P, I32, P]),
 }
 NOALLOC_MAX_N = 65536
 STAGES = ("reduce", "grid", "insert", "search", "lp_small", "lp_full", "apply")
@@ -257,6 +278,15 @@ class VRM:
     def set_timing(self, enable=True):
         self._check(self.lib.vrm_set_timing(self.ctx, int(bool(enable))), "vrm_set_timing")
 
+    def get_schedule(self):
+        s = Schedule()
+        self._check(self.lib.vrm_get_schedule(self.ctx, ctypes.byref(s)), "vrm_get_schedule")
+        return s.as_dict()
+
+    def set_schedule(self, sched):
+        s = Schedule.from_dict(sched)
+        self._check(self.lib.vrm_set_schedule(self.ctx, ctypes.byref(s)), "vrm_set_schedule")
+
     def stage_times(self):
         """Stage durations (ms) of the last step made with timing on."""
         buf = (ctypes.c_float * len(STAGES))()
@@ -304,6 +334,12 @@ class VRMBatch:
             self.close()
         except Exception:
             pass
+
+    def set_schedule(self, slot, sched):
+        s = Schedule.from_dict(sched)
+        st = self.lib.vrm_batch_set_schedule(self.b, int(slot), ctypes.byref(s))
+        if st != VRM_OK:
+            raise VRMError(st, "vrm_batch_set_schedule")
 
     def step(self, clouds, stats=True, raise_on_error=True):
         """clouds: sequence of dicts with x, y, gamma_in, gamma_out (CUDA float64

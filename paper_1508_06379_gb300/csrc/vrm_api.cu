@@ -102,6 +102,7 @@ struct vrm_batch {
   BatchKey* key = nullptr;           // per slot; cap 0 = slot not in the graph
   long long* kernels_outer = nullptr;
   long long* kernels_body = nullptr;
+  vrm_schedule* sched = nullptr;     // per slot; row_cap 0 = default
 };
 
 namespace {
@@ -267,6 +268,7 @@ void fill_consts(const vrm_params& p, Consts& c) {
   c.max_rounds = p.max_rounds;
   c.fallback = p.fallback;
   c.precision = p.precision;
+  default_schedule(c);
 }
 
 cudaError_t read_back(vrm_ctx* ctx, cudaStream_t st) {
@@ -286,6 +288,28 @@ double ratio_from_bits(unsigned long long b) {
 }
 
 bool bad_ptr(const void* p, int n) { return n > 0 && p == nullptr; }
+
+bool block_ok(int b, int hi) { return b >= 32 && b <= hi && b % 32 == 0; }
+
+bool schedule_ok(const vrm_schedule& s, int k_cap) {
+  return s.row_cap >= 8 && s.row_cap <= k_cap && block_ok(s.search_block, kBlock) && block_ok(s.lp_block, 128) &&
+         s.lp_blocks_per_sm >= 1 && s.lp_blocks_per_sm <= 64 && block_ok(s.apply_block, kBlock);
+}
+
+void put_schedule(Consts& c, const vrm_schedule& s) {
+  c.row_cap = s.row_cap;
+  c.search_block = s.search_block;
+  c.lp_block = s.lp_block;
+  c.lp_blocks_per_sm = s.lp_blocks_per_sm;
+  c.apply_block = s.apply_block;
+}
+
+// Constants for the stand-alone stage calls: whole rows (row_cap = k_cap).
+Consts full_rows(const Consts& c) {
+  Consts d = c;
+  d.row_cap = d.k_cap;
+  return d;
+}
 // small and cols rows are read as int4 vectors
 bool misaligned16(const void* p) { return ((uintptr_t)p & 15u) != 0; }
 
@@ -643,8 +667,8 @@ vrm_status vrm_build_neighbourhoods(vrm_ctx* ctx, const double* x, const double*
   VRM_CUDA(cudaMemsetAsync(s.ds, 0, sizeof(DevStats), stream));
   VRM_CUDA(grid_build(x, y, n, ctx->c.Rh, ctx->c.lo2, ctx->c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank,
                       s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp, stream));
-  VRM_CUDA(search_all(ctx->c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, n, nbr_count, nbr_idx,
-                      seg_mask, small, s.ds, stream));
+  VRM_CUDA(search_all(full_rows(ctx->c), s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, n, nbr_count,
+                      nbr_idx, seg_mask, small, s.ds, stream));
   if (max_count) {
     VRM_CUDA(read_back(ctx, stream));
     if (s.h_grid->nonfinite) return VRM_ERR_ARG;
@@ -665,7 +689,7 @@ vrm_status vrm_solve_weights(vrm_ctx* ctx, const double* x, const double* y, int
   if (stats) memset(stats, 0, sizeof(*stats));
   if (n == 0) return VRM_OK;
   Scratch& s = ctx->s;
-  const Consts& c = ctx->c;
+  const Consts c = full_rows(ctx->c);
   VRM_CUDA(ensure_scratch(ctx, n, stream));
   VRM_CUDA(cudaMemsetAsync(s.ds, 0, sizeof(DevStats), stream));
   VRM_CUDA(compact_flags(diffused, n, s.dlist, s.counters + 0, s.pos, s.scan_tmp, stream));
@@ -698,7 +722,7 @@ vrm_status vrm_apply(vrm_ctx* ctx, int32_t n, int32_t n_gamma, const double* gam
       bad_ptr(cols, n) || bad_ptr(f, n) || bad_ptr(fii, n) || bad_ptr(dgamma, n) || misaligned16(cols))
     return VRM_ERR_ARG;
   if (n == 0) return VRM_OK;
-  VRM_CUDA(apply_gather(ctx->c, n, n_gamma, gamma, diffused, nbr_count, nbr_idx, cols, f, fii, nullptr, dgamma,
+  VRM_CUDA(apply_gather(full_rows(ctx->c), n, n_gamma, gamma, diffused, nbr_count, nbr_idx, cols, f, fii, nullptr, dgamma,
                         nullptr, 0.0, stream));
   return VRM_OK;
 }
@@ -727,28 +751,37 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
   P.dt = dt;
   P.max_rounds = ctx->p.max_rounds;
   *s.h_params = P;
-  if (ctx->timing)
-    for (int k = 0; k < VRM_STAGE_COUNT; ++k) ctx->stage_done[k] = 0;
-  bool launched = false;
-  if (ctx->use_graph) {
-    const StepGraph& G = ctx->graph;
-    const bool hit = G.exec && G.x == x && G.y == y && G.gi == gamma_in && G.go == gamma_out && G.cap == capacity &&
-                     G.timing == ctx->timing;
-    if (!hit && !capture_step(ctx, x, y, capacity, gamma_in, gamma_out)) ctx->use_graph = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    if (ctx->timing)
+      for (int k = 0; k < VRM_STAGE_COUNT; ++k) ctx->stage_done[k] = 0;
+    bool launched = false;
     if (ctx->use_graph) {
-      // the captured event nodes record every stage boundary
-      if (ctx->timing)
-        for (int k = 0; k < VRM_STAGE_COUNT; ++k) ctx->stage_done[k] = 1;
-      VRM_CUDA(cudaGraphLaunch(ctx->graph.exec, stream));
-      launched = true;
+      const StepGraph& G = ctx->graph;
+      const bool hit = G.exec && G.x == x && G.y == y && G.gi == gamma_in && G.go == gamma_out &&
+                       G.cap == capacity && G.timing == ctx->timing;
+      if (!hit && !capture_step(ctx, x, y, capacity, gamma_in, gamma_out)) ctx->use_graph = 0;
+      if (ctx->use_graph) {
+        // the captured event nodes record every stage boundary
+        if (ctx->timing)
+          for (int k = 0; k < VRM_STAGE_COUNT; ++k) ctx->stage_done[k] = 1;
+        VRM_CUDA(cudaGraphLaunch(ctx->graph.exec, stream));
+        launched = true;
+      }
     }
+    if (!launched) {
+      vrm_status r = run_step_eager(ctx, x, y, capacity, gamma_in, gamma_out, s.diffused, true, stream);
+      if (r != VRM_OK) return r;
+    }
+    VRM_CUDA(cudaStreamSynchronize(stream));
+    if (launched) add_launches(ctx->graph.kernels_outer + ctx->graph.kernels_body * s.h_state->round);
+    // rows cut by a row_cap below k_cap: the step is repeated with whole rows
+    // (it reads only [0, n) of x, y and gamma_in, so the repeat is exact)
+    const bool cut = !s.h_grid->nonfinite && !s.h_ds->nonfinite && !s.h_state->overflow &&
+                     s.h_ds->max_count > ctx->c.row_cap && ctx->c.row_cap < ctx->p.k_cap;
+    if (!cut) break;
+    ctx->c.row_cap = ctx->p.k_cap;
+    drop_graph(ctx);
   }
-  if (!launched) {
-    vrm_status r = run_step_eager(ctx, x, y, capacity, gamma_in, gamma_out, s.diffused, true, stream);
-    if (r != VRM_OK) return r;
-  }
-  VRM_CUDA(cudaStreamSynchronize(stream));
-  if (launched) add_launches(ctx->graph.kernels_outer + ctx->graph.kernels_body * s.h_state->round);
   if (s.h_grid->nonfinite || s.h_ds->nonfinite) return VRM_ERR_ARG;
   fill_front_stats(ctx, n, st);
   st->small_ok = s.h_ds->small_ok;
@@ -785,7 +818,8 @@ vrm_status vrm_batch_create(const vrm_params* p, int32_t max_clouds, vrm_batch**
   b->key = new (std::nothrow) BatchKey[max_clouds]();
   b->kernels_outer = new (std::nothrow) long long[max_clouds]();
   b->kernels_body = new (std::nothrow) long long[max_clouds]();
-  if (!b->sub || !b->branch || !b->join || !b->key || !b->kernels_outer || !b->kernels_body) {
+  b->sched = new (std::nothrow) vrm_schedule[max_clouds]();
+  if (!b->sub || !b->branch || !b->join || !b->key || !b->kernels_outer || !b->kernels_body || !b->sched) {
     vrm_batch_destroy(b);
     return VRM_ERR_CUDA;
   }
@@ -810,7 +844,38 @@ void vrm_batch_destroy(vrm_batch* b) {
   delete[] b->key;
   delete[] b->kernels_outer;
   delete[] b->kernels_body;
+  delete[] b->sched;
   delete b;
+}
+
+vrm_status vrm_batch_set_schedule(vrm_batch* b, int32_t slot, const vrm_schedule* s) {
+  if (!b || !s || slot < 0 || slot >= b->max_clouds || !schedule_ok(*s, b->base.k_cap)) return VRM_ERR_ARG;
+  b->sched[slot] = *s;
+  if (b->sub[slot]) {
+    put_schedule(b->sub[slot]->c, *s);
+    drop_graph(b->sub[slot]);
+  }
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  return VRM_OK;
+}
+
+vrm_status vrm_get_schedule(const vrm_ctx* ctx, vrm_schedule* out) {
+  if (!ctx || !out) return VRM_ERR_ARG;
+  memset(out, 0, sizeof(*out));
+  out->row_cap = ctx->c.row_cap;
+  out->search_block = ctx->c.search_block;
+  out->lp_block = ctx->c.lp_block;
+  out->lp_blocks_per_sm = ctx->c.lp_blocks_per_sm;
+  out->apply_block = ctx->c.apply_block;
+  return VRM_OK;
+}
+
+vrm_status vrm_set_schedule(vrm_ctx* ctx, const vrm_schedule* s) {
+  if (!ctx || !s || !schedule_ok(*s, ctx->p.k_cap)) return VRM_ERR_ARG;
+  put_schedule(ctx->c, *s);
+  drop_graph(ctx);
+  return VRM_OK;
 }
 
 }  // extern "C"
@@ -942,15 +1007,19 @@ extern "C" vrm_status vrm_step_batched(vrm_batch* b, vrm_cloud* clouds, int32_t 
     }
     vrm_params p = b->base;
     p.h = C.h;
+    bool fresh = false;
     if (!b->sub[c]) {
       if (vrm_create(&p, &b->sub[c]) != VRM_OK) result = VRM_ERR_CUDA;
+      fresh = true;
     } else if (b->sub[c]->p.h != C.h) {
       b->sub[c]->p = p;
       fill_consts(p, b->sub[c]->c);
       drop_graph(b->sub[c]);
+      fresh = true;
     }
     if (result != VRM_OK) break;
     vrm_ctx* ctx = b->sub[c];
+    if (fresh && b->sched[c].row_cap) put_schedule(ctx->c, b->sched[c]);
     if (ensure_scratch(ctx, C.capacity, stream) != cudaSuccess) {
       result = VRM_ERR_CUDA;
       break;
@@ -972,35 +1041,56 @@ extern "C" vrm_status vrm_step_batched(vrm_batch* b, vrm_cloud* clouds, int32_t 
     return result;
   }
   bool launched = false;
-  if (b->use_graph) {
-    if (!hit && !capture_batch(b, clouds, n_clouds, active)) b->use_graph = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    launched = false;
     if (b->use_graph) {
-      if (cudaGraphLaunch(b->exec, stream) != cudaSuccess) {
-        delete[] active;
-        return VRM_ERR_CUDA;
+      if (!hit && !capture_batch(b, clouds, n_clouds, active)) b->use_graph = 0;
+      if (b->use_graph) {
+        if (cudaGraphLaunch(b->exec, stream) != cudaSuccess) {
+          delete[] active;
+          return VRM_ERR_CUDA;
+        }
+        launched = true;
       }
-      launched = true;
     }
-  }
-  if (!launched) {
-    // one cloud after the other, each step eager
-    for (int c = 0; c < n_clouds && result == VRM_OK; ++c) {
+    if (!launched) {
+      // one cloud after the other, each step eager
+      for (int c = 0; c < n_clouds && result == VRM_OK; ++c) {
+        if (!active[c]) continue;
+        const vrm_cloud& C = clouds[c];
+        result = run_step_eager(b->sub[c], C.x, C.y, C.capacity, C.gamma_in, C.gamma_out, b->sub[c]->s.diffused,
+                                true, stream);
+      }
+    }
+    if (cudaStreamSynchronize(stream) != cudaSuccess) result = VRM_ERR_CUDA;
+    if (result != VRM_OK) {
+      delete[] active;
+      return result;
+    }
+    if (launched)
+      for (int c = 0; c < n_clouds; ++c)
+        if (active[c]) add_launches(b->kernels_outer[c] + b->kernels_body[c] * b->sub[c]->s.h_state->round);
+    // clouds whose rows were cut by a row_cap below k_cap: repeat the batch
+    // once with whole rows for them (every step reads only its inputs)
+    bool cut = false;
+    for (int c = 0; c < n_clouds; ++c) {
       if (!active[c]) continue;
-      const vrm_cloud& C = clouds[c];
-      result = run_step_eager(b->sub[c], C.x, C.y, C.capacity, C.gamma_in, C.gamma_out, b->sub[c]->s.diffused, true,
-                              stream);
+      vrm_ctx* ctx = b->sub[c];
+      const Scratch& s = ctx->s;
+      if (!s.h_grid->nonfinite && !s.h_ds->nonfinite && !s.h_state->overflow && s.h_ds->max_count > ctx->c.row_cap &&
+          ctx->c.row_cap < ctx->p.k_cap) {
+        ctx->c.row_cap = ctx->p.k_cap;
+        b->sched[c].row_cap = ctx->p.k_cap;
+        cut = true;
+      }
     }
-  }
-  if (cudaStreamSynchronize(stream) != cudaSuccess) result = VRM_ERR_CUDA;
-  if (result != VRM_OK) {
-    delete[] active;
-    return result;
+    if (!cut) break;
+    hit = false;
   }
   vrm_status first_bad = VRM_OK;
   for (int c = 0; c < n_clouds; ++c) {
     if (!active[c]) continue;
     vrm_ctx* ctx = b->sub[c];
-    if (launched) add_launches(b->kernels_outer[c] + b->kernels_body[c] * ctx->s.h_state->round);
     vrm_stats one;
     const vrm_status r = finish_cloud(ctx, clouds[c], &one);
     clouds[c].status = r;

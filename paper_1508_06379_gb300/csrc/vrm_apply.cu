@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
   for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
     const int j = order ? order[p] : (int)p;
     const int cnt0 = nbr_count[j];
-    const int cnt = cnt0 < c.k_cap ? cnt0 : c.k_cap;
+    const int cnt = cnt0 < c.row_cap ? cnt0 : c.row_cap;
     const int* row = nbr_idx + (size_t)j * c.k_cap;
     const bool self_src = j < n_gamma && diffused[j];
     const double gj = j < n_gamma ? gamma[j] : 0.0;
@@ -68,8 +68,9 @@ cudaError_t apply_gather_dev(const Consts& c, int n_bound, const int* n_dev, int
                              const int* cols, const double* f, const double* fii, const int* order, double* dgamma,
                              double* gamma_out, double dt, const double* dt_dev, cudaStream_t s) {
   if (n_bound <= 0) return cudaSuccess;
-  int blocks = (n_bound + kBlock - 1) / kBlock;
-  k_apply<<<blocks, kBlock, 0, s>>>(c, n_bound, n_dev, n_gamma, n_gamma_dev, gamma, diffused, nbr_count, nbr_idx, cols,
+  const int tb = c.apply_block;
+  const int blocks = (int)(((long)n_bound + tb - 1) / tb);
+  k_apply<<<blocks, tb, 0, s>>>(c, n_bound, n_dev, n_gamma, n_gamma_dev, gamma, diffused, nbr_count, nbr_idx, cols,
                                     f, fii, order, dgamma, gamma_out, dt, dt_dev);
   note_launch();
   return cudaGetLastError();

@@ -28,11 +28,26 @@ struct Consts {
   double h, inv_h, lo2, hi2, Rh, c_bound, nu_over_h2;
   float lo2f, hi2f;
   double ins_dx[8], ins_dy[8];  // insertion offsets 1.5h (cos, sin)((s+1/2) pi/4)
-  int k_cap;
+  int k_cap;      // neighbour row stride
   int max_rounds;
   int fallback;
   int precision;
+  // launch schedule (vrm_schedule); results do not depend on it
+  int row_cap;           // neighbour entries kept per row (<= k_cap)
+  int search_block;      // threads per block of k_search_all
+  int lp_block;          // threads per block of k_lp_small
+  int lp_blocks_per_sm;  // grid cap of k_lp_small
+  int apply_block;       // threads per block of k_apply
 };
+
+// The schedule every context starts with.
+inline void default_schedule(Consts& c) {
+  c.row_cap = c.k_cap;
+  c.search_block = 256;
+  c.lp_block = 128;
+  c.lp_blocks_per_sm = 16;
+  c.apply_block = 256;
+}
 
 // Uniform cell grid, device resident (written by grid_build).
 // Besides FP64 positions, the sorted arrays hold FP32 cell-local coordinates

@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
   for (long t = warp; t < m; t += nwarps) {
     const int i = fail_list[t];
     const int cnt = nbr_count[i];
-    const int K = cnt < c.k_cap ? cnt : c.k_cap;
+    const int K = cnt < c.row_cap ? cnt : c.row_cap;
     const double xi0 = x[i], yi0 = y[i];
     double d2 = 1e300, dx = 0.0, dy = 0.0;
     int j = INT_MAX;
@@ -668,9 +668,10 @@ cudaError_t lp_small(const Consts& c, const double* x, const double* y, const in
                      int cap, const int* small, int* cols, double* f, double* fii, uint8_t* status, int* fail_list,
                      DevStats* ds, double nu_dt, cudaStream_t s, const double* dt_dev, double nu) {
   if (cap <= 0) return cudaSuccess;
-  int blocks = (cap + 127) / 128;
-  if (blocks > 16 * sm_count()) blocks = 16 * sm_count();
-  k_lp_small<<<blocks, 128, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list, ds, nu_dt, dt_dev,
+  const int tb = c.lp_block;
+  int blocks = (int)(((long)cap + tb - 1) / tb);
+  if (blocks > c.lp_blocks_per_sm * sm_count()) blocks = c.lp_blocks_per_sm * sm_count();
+  k_lp_small<<<blocks, tb, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list, ds, nu_dt, dt_dev,
                                     nu); note_launch();
   return cudaGetLastError();
 }

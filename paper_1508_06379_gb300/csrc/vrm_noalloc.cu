@@ -92,6 +92,7 @@ extern "C" vrm_status vrm_build_neighbourhoods_noalloc(const vrm_params* p, cons
   c.hi2 = Rh * Rh;
   c.Rh = Rh;
   c.k_cap = p->k_cap;
+  vrm::default_schedule(c);
   unsigned char* cur = base;
   vrm::Grid* grid = carve<vrm::Grid>(cur, 1);
   vrm::DevStats* ds = carve<vrm::DevStats>(cur, 1);

@@ -14,9 +14,10 @@
 // undecided cases (rare on jittered clouds, frequent on exact lattices) take
 // the FP64 definition, so the result is bit-identical to it.
 //
-// The row is kept sorted by index in a per-thread buffer (the k_cap smallest
-// indices survive); the closest particle of every segment is tracked in
-// registers with ties to the smaller index.
+// The row is kept sorted by index in a per-thread buffer of KCAP entries (the
+// row_cap smallest indices survive; rows are k_cap apart); the closest
+// particle of every segment is tracked in registers with ties to the smaller
+// index.
 #include "vrm_internal.cuh"
 
 namespace vrm {
@@ -49,7 +50,8 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
                                                        DevStats* __restrict__ ds) {
   if (n_dev) n = *n_dev;
   const Grid g = *gp;
-  const int k_cap = c.k_cap;
+  const int k_cap = c.row_cap < KCAP ? c.row_cap : KCAP;  // entries kept
+  const size_t stride = (size_t)c.k_cap;
   const float tie = 2.f * kBand;
   int local_max = 0;
   for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
     }
     nbr_count[i] = cnt;
     const int m = cnt < k_cap ? cnt : k_cap;
-    int* row = nbr_idx + (size_t)i * k_cap;
+    int* row = nbr_idx + (size_t)i * stride;
     for (int t = 0; t < m; ++t) row[t] = list[t];
     seg_mask[i] = (uint8_t)mask;
     int4* sm = reinterpret_cast<int4*>(small + (size_t)i * 8);
@@ -239,9 +241,17 @@ cudaError_t search_all_dev(const Consts& c, const Grid* g, const int* cell_start
                            int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small, DevStats* ds,
                            cudaStream_t s) {
   if (n_bound <= 0) return cudaSuccess;
-  int blocks = (n_bound + kBlock - 1) / kBlock;
-  k_search_all<VRM_KCAP_MAX><<<blocks, kBlock, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n_bound,
-                                                        n_dev, nbr_count, nbr_idx, seg_mask, small, ds);
+  const int tb = c.search_block;
+  const int blocks = (int)(((long)n_bound + tb - 1) / tb);
+  if (c.row_cap <= 16)
+    k_search_all<16><<<blocks, tb, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n_bound, n_dev,
+                                           nbr_count, nbr_idx, seg_mask, small, ds);
+  else if (c.row_cap <= 24)
+    k_search_all<24><<<blocks, tb, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n_bound, n_dev,
+                                           nbr_count, nbr_idx, seg_mask, small, ds);
+  else
+    k_search_all<VRM_KCAP_MAX><<<blocks, tb, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n_bound,
+                                                     n_dev, nbr_count, nbr_idx, seg_mask, small, ds);
   note_launch();
   return cudaGetLastError();
 }
