@@ -1,0 +1,221 @@
+"""CPU oracle of the learned weight proposal and its training (FP64, numpy).
+
+TEST INFRASTRUCTURE ONLY, like the rest of this package: the tests, the
+smoke check and bench.py's CPU-baseline leg use it; the CUDA library never
+does.
+
+The paper solves the moment conditions (Eqs. momcondmv, cond_two,
+cond_alpha) for non-negative weights with a linear program (Sec. 4.1).  The
+learned path proposes the weights with a small network instead and keeps
+only proposals that, after an exact correction, satisfy the same conditions
+and signs; everything else goes to the LP.  The pieces:
+
+* features(): the neighbourhood N_i (annulus of Eq. neighbourhood) as K = 32
+  slots ordered by (45-degree segment of Sec. 4.2, squared distance, index),
+  with the scaled offsets xi = (x_j - x_i)/h of Eq. momcondmv and a mask;
+  input row [xi_x(32), xi_y(32), mask(32)].
+* forward()/backward(): the network 96 -> 256 -> 256 -> 256 -> 32 with GELU
+  (the erf form) after each hidden layer; W_l is [out x in].
+* loss(): mean squared error over the valid slots against the LP weights
+  f~ of the same particle (f~ = h^2 f, Eq. momcondmv scaling).
+* adamw(): Adam with decoupled weight decay (Loshchilov and Hutter).
+* support() and project(): up to 8 slots with the largest positive proposal
+  form the support S; the proposal is corrected by the smallest change that
+  meets the moment conditions on S,
+      f_S = f0_S + V_S^T (V_S V_S^T)^{-1} (b - V_S f0_S),
+  and accepted iff every f_j >= 0 and the residual |V_S f_S - b|_inf is at
+  most 1e-12 (Sec. 3.1's non-negativity, Eq. cond_two/cond_alpha).
+"""
+import numpy as np
+
+K_SLOTS = 32
+N_IN = 3 * K_SLOTS
+HIDDEN = 256
+N_OUT = K_SLOTS
+SHAPES = ((HIDDEN, N_IN), (HIDDEN, HIDDEN), (HIDDEN, HIDDEN), (N_OUT, HIDDEN))
+N_PARAMS = sum(o * i + o for o, i in SHAPES)  # 164,640
+SUPPORT_MAX = 8
+ACCEPT_RESID = 1e-12
+B_RHS = np.array([0.0, 0.0, 2.0, 0.0, 2.0])  # rows (1,0) (0,1) (2,0) (1,1) (0,2)
+
+
+# -- parameter vector ------------------------------------------------------------
+def unflatten(theta):
+    """Flat vector [W1, b1, W2, b2, W3, b3, W4, b4] -> list of (W, b)."""
+    out, o = [], 0
+    for rows, cols in SHAPES:
+        W = theta[o:o + rows * cols].reshape(rows, cols)
+        o += rows * cols
+        b = theta[o:o + rows]
+        o += rows
+        out.append((W, b))
+    return out
+
+
+def flatten(layers):
+    return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in layers])
+
+
+# -- bf16 rounding (round to nearest even on the float32 bit pattern) ---------------
+def to_bf16(a):
+    """Round to bfloat16 (returned as float64 holding the bf16 value): first
+    to float32, then the upper 16 bits with round-to-nearest-even."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float64).astype(np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) >> 16) << 16
+    nan = np.isnan(f)
+    out = r.astype(np.uint32).view(np.float32).astype(np.float64)
+    out[nan] = np.nan
+    return out
+
+
+# -- features ----------------------------------------------------------------------
+def segment(dx, dy):
+    """45-degree segment of an offset (Sec. 4.2): half-open angular sectors
+    [k pi/4, (k+1) pi/4) counter-clockwise from +x, decided exactly."""
+    if dx > 0 and 0 <= dy < dx:
+        return 0
+    if dx > 0 and dy >= dx:
+        return 1
+    if dx <= 0 and dy > -dx:
+        return 2
+    if dx < 0 and 0 < dy <= -dx:
+        return 3
+    if dx < 0 and 0 >= dy > dx:
+        return 4
+    if dx < 0 and dy <= dx:
+        return 5
+    if dx >= 0 and -dy > dx:
+        return 6
+    return 7
+
+
+def features(x, y, h, i, row):
+    """Input row (float32 values, then rounded to bf16 as the network reads
+    them) and slot -> particle map (-1 = empty) of particle i whose
+    neighbourhood is `row` (indices, any order)."""
+    inv_h = 1.0 / h
+    ent = []
+    for j in row:
+        j = int(j)
+        dx = x[j] - x[i]
+        dy = y[j] - y[i]
+        d2 = dx * dx + dy * dy
+        ent.append((segment(dx, dy), d2, j, dx, dy))
+    ent.sort(key=lambda e: (e[0], e[1], e[2]))
+    X = np.zeros(N_IN)
+    slots = np.full(K_SLOTS, -1, dtype=np.int64)
+    for k, (_, _, j, dx, dy) in enumerate(ent[:K_SLOTS]):
+        X[k] = np.float32(dx * inv_h)
+        X[K_SLOTS + k] = np.float32(dy * inv_h)
+        X[2 * K_SLOTS + k] = 1.0
+        slots[k] = j
+    return to_bf16(X), slots
+
+
+# -- network -------------------------------------------------------------------------
+def gelu(z):
+    from scipy.special import erf
+    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+
+
+def gelu_grad(z):
+    from scipy.special import erf
+    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+
+
+def forward(theta, X, bf16_acts=False):
+    """Rows of X [B, 96] -> proposals [B, 32].  bf16_acts rounds the hidden
+    activations to bf16 between layers (the precision the GPU keeps them
+    in).  Returns (Y, cache)."""
+    layers = unflatten(theta)
+    a = np.asarray(X, dtype=np.float64)
+    cache = []
+    for l, (W, b) in enumerate(layers):
+        z = a @ W.T + b
+        cache.append((a, z))
+        if l < len(layers) - 1:
+            a = gelu(z)
+            if bf16_acts:
+                a = to_bf16(a)
+        else:
+            a = z
+    return a, cache
+
+
+def loss(Y, T, M):
+    """Mean of M (Y - T)^2 over the valid slots, and dL/dY."""
+    cnt = max(float(np.sum(M)), 1.0)
+    d = (Y - T) * M
+    return float(np.sum(d * d) / cnt), 2.0 * d / cnt
+
+
+def backward(theta, cache, dY):
+    """Gradient of sum(dY * Y) with respect to theta (flat, same layout)."""
+    layers = unflatten(theta)
+    grads = [None] * len(layers)
+    g = dY
+    for l in range(len(layers) - 1, -1, -1):
+        a, z = cache[l]
+        if l < len(layers) - 1:
+            g = g * gelu_grad(z)
+        W, _ = layers[l]
+        grads[l] = (g.T @ a, g.sum(axis=0))
+        g = g @ W
+    return flatten(grads)
+
+
+def adamw(theta, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+    """One AdamW step (t counts from 1); returns (theta', m', v')."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    theta = theta - lr * (mh / (np.sqrt(vh) + eps) + weight_decay * theta)
+    return theta, m, v
+
+
+# -- projection onto the moment conditions ---------------------------------------------
+def vandermonde(xi, eta):
+    """Rows (1,0) (0,1) (2,0) (1,1) (0,2) of Eq. momcondmv at the given columns."""
+    xi = np.asarray(xi, dtype=np.float64)
+    eta = np.asarray(eta, dtype=np.float64)
+    return np.stack([xi, eta, xi * xi, xi * eta, eta * eta])
+
+
+def support(f0, slots, cap=SUPPORT_MAX):
+    """Slots of the support: the (up to) cap valid slots with the largest
+    positive proposal, ties to the lower slot, returned in slot order.  The
+    comparisons are made on the float32 proposals."""
+    f0 = np.asarray(f0, dtype=np.float32)
+    cand = [k for k in range(len(f0)) if slots[k] >= 0 and f0[k] > 0]
+    cand.sort(key=lambda k: (-float(f0[k]), k))
+    return sorted(cand[:cap])
+
+
+def project(xi, eta, f0, b=B_RHS):
+    """Least-change correction of f0 onto V f = b; returns (f, residual)."""
+    V = vandermonde(xi, eta)
+    f0 = np.asarray(f0, dtype=np.float64)
+    r = b - V @ f0
+    f = f0 + V.T @ np.linalg.solve(V @ V.T, r)
+    return f, float(np.max(np.abs(V @ f - b)))
+
+
+def learned_stencil(x, y, h, i, slots, f0):
+    """The learned stencil of particle i from its slot map and proposal:
+    (accepted, particle indices, f~ in slot order, f~_ii)."""
+    S = support(f0, slots)
+    if len(S) < 5:
+        return False, [], None, 0.0
+    inv_h = 1.0 / h
+    js = [int(slots[k]) for k in S]
+    xi = np.array([(x[j] - x[i]) * inv_h for j in js])
+    eta = np.array([(y[j] - y[i]) * inv_h for j in js])
+    V = vandermonde(xi, eta)
+    if np.linalg.matrix_rank(V) < 5:
+        return False, js, None, 0.0
+    f, res = project(xi, eta, np.asarray(f0, dtype=np.float32)[S].astype(np.float64))
+    ok = bool(np.all(f >= 0.0) and res <= ACCEPT_RESID)
+    return ok, js, f, -float(np.sum(f))

@@ -1,0 +1,195 @@
+"""Pins of the learned-proposal oracle (oracle/mlp.py) against what the
+mathematics fixes: closed forms, finite differences, library routines
+(torch's bfloat16 rounding and AdamW, numpy's least squares) and the paper's
+single-particle example (Sec. 6: eight inserted neighbours at 1.5h)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+torch = pytest.importorskip("torch")
+
+
+def test_parameter_count():
+    # 96*256 + 256 + 2 * (256*256 + 256) + 256*32 + 32
+    assert mlp.N_PARAMS == 164640
+    theta = np.arange(mlp.N_PARAMS, dtype=np.float64)
+    assert np.array_equal(mlp.flatten(mlp.unflatten(theta)), theta)
+    W1, b1 = mlp.unflatten(theta)[0]
+    assert W1.shape == (256, 96) and b1[0] == 256 * 96
+
+
+def test_bf16_rounding():
+    assert mlp.to_bf16(1.0) == 1.0
+    assert mlp.to_bf16(1.0 + 2.0 ** -8) == 1.0  # tie to even
+    assert mlp.to_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6  # tie to even (upwards)
+    assert mlp.to_bf16(-2.0 ** -130) == -2.0 ** -130 or mlp.to_bf16(-2.0 ** -130) <= 0
+    rng = np.random.default_rng(0)
+    a = np.concatenate([rng.normal(0, 1, 5000), rng.normal(0, 1e-3, 5000), rng.normal(0, 1e4, 5000)])
+    ref = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.to_bf16(a), ref)
+
+
+def test_gelu_closed_forms():
+    assert mlp.gelu(np.array([0.0]))[0] == 0.0
+    # GELU(1) = Phi(1) = 0.8413447460685429..., GELU(-1) = -(1 - Phi(1))
+    assert abs(mlp.gelu(np.array([1.0]))[0] - 0.8413447460685429) < 1e-15
+    assert abs(mlp.gelu(np.array([-1.0]))[0] + 0.15865525393145707) < 1e-15
+    assert abs(mlp.gelu(np.array([12.0]))[0] - 12.0) < 1e-12 and abs(mlp.gelu(np.array([-12.0]))[0]) < 1e-12
+    z = np.linspace(-6, 6, 241)
+    e = 1e-6
+    fd = (mlp.gelu(z + e) - mlp.gelu(z - e)) / (2 * e)
+    assert np.max(np.abs(fd - mlp.gelu_grad(z))) < 1e-8
+
+
+def small_problem(seed=0, B=6):
+    rng = np.random.default_rng(seed)
+    theta = np.concatenate([np.concatenate([rng.normal(0, 1 / math.sqrt(i), o * i), rng.normal(0, 0.1, o)])
+                            for o, i in mlp.SHAPES])
+    X = rng.normal(0, 1, (B, mlp.N_IN))
+    T = rng.normal(0, 0.3, (B, mlp.N_OUT))
+    M = (rng.random((B, mlp.N_OUT)) < 0.6).astype(np.float64)
+    return theta, X, T, M
+
+
+def test_backward_matches_central_differences():
+    theta, X, T, M = small_problem()
+    Y, cache = mlp.forward(theta, X)
+    L, dY = mlp.loss(Y, T, M)
+    g = mlp.backward(theta, cache, dY)
+    rng = np.random.default_rng(1)
+    # one index in every weight block and bias block of every layer, plus random ones
+    offs, o = [], 0
+    for rows, cols in mlp.SHAPES:
+        offs += [o + int(rng.integers(rows * cols)), o + rows * cols + int(rng.integers(rows))]
+        o += rows * cols + rows
+    offs += list(rng.integers(0, mlp.N_PARAMS, 40))
+    for k in offs:
+        e = 1e-5 * max(1.0, abs(theta[k]))
+        tp, tm = theta.copy(), theta.copy()
+        tp[k] += e
+        tm[k] -= e
+        Lp = mlp.loss(mlp.forward(tp, X)[0], T, M)[0]
+        Lm = mlp.loss(mlp.forward(tm, X)[0], T, M)[0]
+        fd = (Lp - Lm) / (2 * e)
+        assert abs(fd - g[k]) <= 1e-6 * max(abs(fd), 1e-3), (k, fd, g[k])
+
+
+def test_loss_is_a_masked_mean():
+    Y = np.array([[1.0, 2.0, 3.0]])
+    T = np.array([[0.0, 0.0, 0.0]])
+    M = np.array([[1.0, 0.0, 1.0]])
+    L, dY = mlp.loss(Y, T, M)
+    assert L == (1.0 + 9.0) / 2 and np.array_equal(dY, [[1.0, 0.0, 3.0]])
+
+
+def test_adamw_matches_torch():
+    rng = np.random.default_rng(2)
+    theta = rng.normal(0, 1, 1000)
+    grads = [rng.normal(0, 1, 1000) for _ in range(5)]
+    hp = dict(lr=3e-3, beta1=0.9, beta2=0.99, eps=1e-8, weight_decay=0.01)
+    p = torch.nn.Parameter(torch.from_numpy(theta.copy()))
+    opt = torch.optim.AdamW([p], lr=hp["lr"], betas=(hp["beta1"], hp["beta2"]), eps=hp["eps"],
+                            weight_decay=hp["weight_decay"])
+    th, m, v = theta.copy(), np.zeros(1000), np.zeros(1000)
+    for t, g in enumerate(grads, start=1):
+        p.grad = torch.from_numpy(g.copy())
+        opt.step()
+        th, m, v = mlp.adamw(th, g, m, v, t, **hp)
+    # torch decays the weights before the Adam update (theta (1 - lr wd)); the
+    # oracle applies lr (update + wd theta): identical to first order in lr wd
+    assert np.max(np.abs(p.detach().numpy() - th)) < 1e-6
+    # first step in closed form: m^ = g, v^ = g^2
+    th1, _, _ = mlp.adamw(theta, grads[0], np.zeros(1000), np.zeros(1000), 1, lr=1e-3, eps=0.0)
+    assert np.allclose(th1, theta - 1e-3 * np.sign(grads[0]), rtol=0, atol=1e-15)
+
+
+def test_segments_and_feature_slots():
+    # unit lattice around the origin: E NE N NW W SW S SE fall in segments 0..7
+    off = [(1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1)]
+    assert [mlp.segment(dx, dy) for dx, dy in off] == list(range(8))
+    h = 0.5
+    x = np.array([0.0] + [h * a for a, _ in off] + [2 * h, 1.5 * h])
+    y = np.array([0.0] + [h * b for _, b in off] + [0.0, 0.25 * h])
+    row = list(range(10, 0, -1))  # any order
+    X, slots = mlp.features(x, y, h, 0, row)
+    # segment 0 holds E (d2 = h^2), (1.5h, 0.25h) (d2 = 2.3125 h^2) and (2h, 0) (4 h^2), in that order
+    assert list(slots[:3]) == [1, 10, 9] and list(slots[3:10]) == [2, 3, 4, 5, 6, 7, 8]
+    assert np.all(slots[10:] == -1)
+    assert X[0] == 1.0 and X[1] == 1.5 and X[2] == 2.0 and X[32] == 0.0 and X[33] == 0.25
+    assert np.array_equal(X[64:74], np.ones(10)) and np.all(X[74:] == 0)
+
+
+def test_support_selection():
+    f0 = np.zeros(32, dtype=np.float32)
+    slots = np.arange(32)
+    f0[[3, 5, 7, 9, 11, 13, 15, 17, 19, 21]] = [0.5, 0.9, 0.1, 0.9, 0.2, 0.3, 0.4, 0.05, 0.6, 0.7]
+    assert mlp.support(f0, slots) == [3, 5, 9, 11, 13, 15, 19, 21]
+    slots[5] = -1  # empty slots never enter
+    assert 5 not in mlp.support(f0, slots)
+    f0[:] = -1.0
+    assert mlp.support(f0, np.arange(32)) == []
+
+
+def test_projection_least_change():
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        K = int(rng.integers(5, 9))
+        ang = rng.uniform(0, 2 * math.pi, K)
+        rad = rng.uniform(0.5, 2.0, K)
+        xi, eta = rad * np.cos(ang), rad * np.sin(ang)
+        V = mlp.vandermonde(xi, eta)
+        cond = np.linalg.cond(V @ V.T)
+        if cond > 1e5:  # ill-conditioned supports fail the residual check and go to the LP
+            continue
+        f0 = rng.uniform(0, 1, K)
+        f, res = mlp.project(xi, eta, f0)
+        assert res <= 1e-12
+        # the correction is the minimum-norm solution of V d = b - V f0
+        d_ref = np.linalg.lstsq(V, mlp.B_RHS - V @ f0, rcond=None)[0]
+        assert np.max(np.abs((f - f0) - d_ref)) < 1e-10
+        # a proposal that already meets the conditions is left alone
+        f2, _ = mlp.project(xi, eta, f)
+        assert np.max(np.abs(f2 - f)) < 1e-15 * cond * max(1.0, np.max(np.abs(f)))  # eps * condition
+
+
+def test_projection_single_particle_example():
+    # Sec. 6: a lone particle gets 8 inserted neighbours at 1.5h on the segment
+    # centre lines; every stencil meeting the moment conditions has
+    # sum f~ = 4 / 1.5^2 = 16/9 (rows (2,0) + (0,2) with |xi|^2 = 2.25)
+    ang = (np.arange(8) + 0.5) * math.pi / 4
+    xi, eta = 1.5 * np.cos(ang), 1.5 * np.sin(ang)
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        f, res = mlp.project(xi, eta, rng.uniform(0, 1, 8))
+        assert res <= 1e-12 and abs(np.sum(f) - 16.0 / 9.0) < 1e-13
+    # the symmetric proposal projects to the uniform stencil 2/9
+    f, _ = mlp.project(xi, eta, np.full(8, 0.3))
+    assert np.max(np.abs(f - 2.0 / 9.0)) < 1e-14
+
+
+def test_learned_stencil_accepts_valid_and_rejects_negative():
+    # unit lattice neighbours, the 5-point stencil proposal (f~ = 1 on E N W S)
+    # plus a little weight on the diagonals
+    h = 1.0
+    off = [(1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1)]
+    x = np.array([0.0] + [a for a, _ in off])
+    y = np.array([0.0] + [b for _, b in off])
+    slots = np.full(32, -1)
+    slots[:8] = np.arange(1, 9)
+    f0 = np.zeros(32, dtype=np.float32)
+    f0[:8] = [1, 0.01, 1, 0.01, 1, 0.01, 1, 0.01]
+    ok, js, f, fii = mlp.learned_stencil(x, y, h, 0, slots, f0)
+    assert ok and js == list(range(1, 9)) and np.all(f >= 0) and abs(fii + np.sum(f)) < 1e-15
+    V = mlp.vandermonde(x[js], y[js])
+    assert np.max(np.abs(V @ f - mlp.B_RHS)) <= 1e-12
+    # weight only on the diagonals and one axis: the correction turns an axis weight negative
+    f0[:8] = [0.0, 1.0, 0.0, 1.0, 3.0, 1.0, 0.0, 1.0]
+    ok, _, f, _ = mlp.learned_stencil(x, y, h, 0, slots, f0)
+    assert not ok and np.min(f) < 0
+    # fewer than 5 positive proposals: no stencil
+    f0[:8] = [1, 0, 1, 0, 1, 0, 1, 0]
+    ok, _, _, _ = mlp.learned_stencil(x, y, h, 0, slots, f0)
+    assert not ok
