@@ -295,6 +295,63 @@ void vrm_batch_destroy(vrm_batch* b);
    sums over the clouds (maxima for the max_* fields). */
 vrm_status vrm_step_batched(vrm_batch* b, vrm_cloud* clouds, int32_t n_clouds, vrm_stats* stats, cudaStream_t stream);
 
+/*
+ * The weight-proposal network of the learned path (not in the paper: the
+ * paper solves every stencil with the LP of Sec. 4.1).  A proposal is kept
+ * only if, after the least-change correction onto the moment conditions
+ * (Eqs. momcondmv, cond_two, cond_alpha), every weight is non-negative and
+ * the residual is at most 1e-12; otherwise the LP decides, so the network
+ * changes speed, never validity.
+ *
+ * Input rows: 128 bf16 per particle: xi_x of the 32 neighbour slots, xi_y,
+ * the slot mask (1/0), then 32 zeros.  Slots hold the annulus neighbours
+ * ordered by (45-degree segment, squared distance, index), xi = (x_j - x_i)/h.
+ * Output rows: 32 fp32 proposals f~ (Eq. momcondmv scaling f~ = h^2 f).
+ * Network 96 -> 256 -> 256 -> 256 -> 32, GELU (erf form) on the hidden
+ * layers; parameters one fp32 vector of VRM_MLP_PARAMS entries in the order
+ * W1 (256 x 96, row-major [out][in]), b1, W2 (256 x 256), b2, W3, b3,
+ * W4 (32 x 256), b4.  Products run on the tensor cores with bf16 weights and
+ * activations and fp32 accumulation.
+ *
+ * Training: vrm_mlp_train_step gathers rows batch_idx[0..rows) of a data set
+ * (X_all bf16 [N x 128], T_all fp32 [N x 32] targets, device), runs the
+ * forward and backward passes of the masked mean squared error
+ * sum(mask (Y - T)^2) / sum(mask) and one AdamW step (decoupled weight decay)
+ * with bias corrections for step t >= 1.  rows <= batch_rows; missing rows
+ * are zero and add nothing.  All calls are asynchronous except where noted;
+ * a tensor-core wait that gives up (about a second) makes the synchronous
+ * calls return VRM_ERR_CUDA.
+ */
+#define VRM_MLP_PARAMS 164640
+#define VRM_MLP_IN 128
+#define VRM_MLP_OUT 32
+typedef struct vrm_mlp vrm_mlp;
+typedef struct vrm_adamw {
+  float lr, beta1, beta2, eps, weight_decay;
+  int32_t reserved[3];
+} vrm_adamw;
+/* batch_rows: training batch, a multiple of 128 (<= 2^20).  VRM_ERR_UNSUPPORTED
+   when the driver offers no tensor-map encoder. */
+vrm_status vrm_mlp_create(int32_t batch_rows, vrm_mlp** out);
+void vrm_mlp_destroy(vrm_mlp* net);
+/* theta: VRM_MLP_PARAMS floats (host or device); resets the AdamW moments. */
+vrm_status vrm_mlp_set_params(vrm_mlp* net, const float* theta, cudaStream_t stream);
+vrm_status vrm_mlp_get_params(const vrm_mlp* net, float* theta, cudaStream_t stream);
+/* Y[rows x 32] = network(X).  X: device bf16 rows of VRM_MLP_IN, allocated for
+   rows rounded up to a multiple of 128, 16-byte aligned.  Synchronises. */
+vrm_status vrm_mlp_forward(vrm_mlp* net, const uint16_t* X, int32_t rows, float* Y, cudaStream_t stream);
+/* Gradient (VRM_MLP_PARAMS floats) and loss[0..1] = (loss, sum of the mask)
+   of rows X, T (device) without an update.  Synchronises. */
+vrm_status vrm_mlp_grads(vrm_mlp* net, const uint16_t* X, const float* T, int32_t rows, float* grad, float* loss,
+                         cudaStream_t stream);
+/* One training step on rows batch_idx (device int32, or NULL for rows 0..rows-1). */
+vrm_status vrm_mlp_train_step(vrm_mlp* net, const uint16_t* X_all, const float* T_all, const int32_t* batch_idx,
+                              int32_t rows, const vrm_adamw* hp, int32_t t, float* loss, cudaStream_t stream);
+/* One AdamW step with a given gradient (device, VRM_MLP_PARAMS floats). */
+vrm_status vrm_mlp_adamw(vrm_mlp* net, const float* grad, const vrm_adamw* hp, int32_t t, cudaStream_t stream);
+/* VRM_ERR_CUDA if a tensor-core wait of an earlier asynchronous call gave up.  Synchronises. */
+vrm_status vrm_mlp_error(vrm_mlp* net, cudaStream_t stream);
+
 /* Per-stage timing of vrm_step with CUDA events recorded on the call's
    stream between the stages.  Off by default; enable != 0 turns it on. */
 vrm_status vrm_set_timing(vrm_ctx* ctx, int32_t enable);

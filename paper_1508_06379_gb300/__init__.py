@@ -9,10 +9,10 @@ as the C entry points.
 from .binding import (KCAP_MAX, LP_FULL, LP_NONE, LP_NOT_DIFFUSED, LP_SMALL, STENCIL_W, VRM, VRM_ERR_ARG,
                       VRM_ERR_CAPACITY, VRM_ERR_CUDA, VRM_ERR_UNSUPPORTED, VRM_OK, Params, Stats, VRMError,
                       library_path, load_library, launch_count, STAGES, build_neighbourhoods_noalloc,
-                      NOALLOC_MAX_N, VRMBatch, Cloud, Schedule)
+                      NOALLOC_MAX_N, VRMBatch, Cloud, Schedule, MLP, MLP_PARAMS, MLP_IN, MLP_OUT)
 from .builder import build
 
-__all__ = ["VRM", "VRMBatch", "Cloud", "Schedule", "VRMError", "Params", "Stats", "build", "load_library", "library_path", "launch_count", "STAGES",
+__all__ = ["VRM", "VRMBatch", "Cloud", "Schedule", "MLP", "MLP_PARAMS", "MLP_IN", "MLP_OUT", "VRMError", "Params", "Stats", "build", "load_library", "library_path", "launch_count", "STAGES",
            "build_neighbourhoods_noalloc", "NOALLOC_MAX_N", "STENCIL_W", "KCAP_MAX",
            "LP_NOT_DIFFUSED", "LP_SMALL", "LP_FULL", "LP_NONE", "VRM_OK", "VRM_ERR_ARG", "VRM_ERR_CAPACITY",
            "VRM_ERR_CUDA", "VRM_ERR_UNSUPPORTED"]

@@ -69,6 +69,11 @@ class Schedule(ctypes.Structure):
         return s
 
 
+class AdamW(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("weight_decay", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
+
+
 class VRMError(RuntimeError):
     def __init__(self, status, what):
         self.status = status
@@ -98,7 +103,19 @@ SIGNATURES = {
     "vrm_get_schedule": (ctypes.c_int, [P, P]),
     "vrm_set_schedule": (ctypes.c_int, [P, P]),
     "vrm_batch_set_schedule": (ctypes.c_int, [P, I32, P]),
+    "vrm_mlp_create": (ctypes.c_int, [I32, P]),
+    "vrm_mlp_destroy": (None, [P]),
+    "vrm_mlp_set_params": (ctypes.c_int, [P, P, P]),
+    "vrm_mlp_get_params": (ctypes.c_int, [P, P, P]),
+    "vrm_mlp_forward": (ctypes.c_int, [P, P, I32, P, P]),
+    "vrm_mlp_grads": (ctypes.c_int, [P, P, P, I32, P, P, P]),
+    "vrm_mlp_train_step": (ctypes.c_int, [P, P, P, P, I32, P, I32, P, P]),
+    "vrm_mlp_adamw": (ctypes.c_int, [P, P, P, I32, P]),
+    "vrm_mlp_error": (ctypes.c_int, [P, P]),
 }
+MLP_PARAMS = 164640
+MLP_IN = 128
+MLP_OUT = 32
 NOALLOC_MAX_N = 65536
 STAGES = ("reduce", "grid", "insert", "search", "lp_small", "lp_full", "apply")
 
@@ -361,3 +378,95 @@ class VRMBatch:
         if st != VRM_OK and raise_on_error:
             raise VRMError(st, "vrm_step_batched")
         return out, s.as_dict()
+
+
+def _pad_rows(n, m=128):
+    return (int(n) + m - 1) // m * m
+
+
+class MLP:
+    """The weight-proposal network (vrm_mlp_*): tensor-core forward,
+    backward and AdamW.  Parameters: one float32 vector of MLP_PARAMS."""
+
+    def __init__(self, batch_rows=4096):
+        self.lib = _lib_handle()
+        h_ = ctypes.c_void_p()
+        st = self.lib.vrm_mlp_create(int(batch_rows), ctypes.byref(h_))
+        if st != VRM_OK:
+            raise VRMError(st, "vrm_mlp_create")
+        self.net = h_
+        self.batch_rows = int(batch_rows)
+
+    def close(self):
+        if getattr(self, "net", None):
+            self.lib.vrm_mlp_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != VRM_OK:
+            raise VRMError(st, what)
+
+    def set_params(self, theta):
+        t = theta if isinstance(theta, torch.Tensor) else torch.from_numpy(theta)
+        t = t.to(device="cuda", dtype=torch.float32).contiguous()
+        self._check(self.lib.vrm_mlp_set_params(self.net, _ptr(t, torch.float32, "theta", MLP_PARAMS), _stream()),
+                    "vrm_mlp_set_params")
+
+    def get_params(self):
+        t = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+        self._check(self.lib.vrm_mlp_get_params(self.net, _ptr(t, torch.float32, "theta", MLP_PARAMS), _stream()),
+                    "vrm_mlp_get_params")
+        return t
+
+    def forward(self, X, rows=None):
+        """X: CUDA bfloat16 [>= rows rounded up to 128, 128]; returns fp32 [rows, 32]."""
+        rows = X.shape[0] if rows is None else int(rows)
+        if X.shape[0] < _pad_rows(rows):
+            Xp = torch.zeros(_pad_rows(rows), MLP_IN, dtype=torch.bfloat16, device=X.device)
+            Xp[:rows] = X[:rows]
+            X = Xp
+        Y = torch.empty(max(rows, 1), MLP_OUT, dtype=torch.float32, device=X.device)
+        self._check(self.lib.vrm_mlp_forward(self.net, _ptr(X, torch.bfloat16, "X", rows * MLP_IN), rows,
+                                             _ptr(Y, torch.float32, "Y", rows * MLP_OUT), _stream()),
+                    "vrm_mlp_forward")
+        return Y[:rows]
+
+    def grads(self, X, T):
+        rows = X.shape[0]
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+        loss = torch.empty(2, dtype=torch.float32, device="cuda")
+        self._check(self.lib.vrm_mlp_grads(self.net, _ptr(X, torch.bfloat16, "X", rows * MLP_IN),
+                                           _ptr(T, torch.float32, "T", rows * MLP_OUT), rows,
+                                           _ptr(g, torch.float32, "grad", MLP_PARAMS),
+                                           _ptr(loss, torch.float32, "loss", 2), _stream()), "vrm_mlp_grads")
+        return g, float(loss[0])
+
+    @staticmethod
+    def hyper(lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0):
+        return AdamW(lr, beta1, beta2, eps, weight_decay)
+
+    def adamw(self, grad, t, **hp):
+        a = self.hyper(**hp)
+        self._check(self.lib.vrm_mlp_adamw(self.net, _ptr(grad, torch.float32, "grad", MLP_PARAMS), ctypes.byref(a),
+                                           int(t), _stream()), "vrm_mlp_adamw")
+
+    def train_step(self, X_all, T_all, idx, t, loss_out=None, **hp):
+        """One step on rows idx (CUDA int32) of the data set; the loss (and
+        mask sum) go to loss_out (CUDA float32 [2]) if given."""
+        a = self.hyper(**hp)
+        rows = idx.numel() if idx is not None else X_all.shape[0]
+        self._check(self.lib.vrm_mlp_train_step(
+            self.net, _ptr(X_all, torch.bfloat16, "X_all"), _ptr(T_all, torch.float32, "T_all"),
+            _ptr(idx, torch.int32, "batch_idx", rows) if idx is not None else None, int(rows), ctypes.byref(a),
+            int(t), _ptr(loss_out, torch.float32, "loss", 2) if loss_out is not None else None, _stream()),
+            "vrm_mlp_train_step")
+
+    def check(self):
+        self._check(self.lib.vrm_mlp_error(self.net, _stream()), "vrm_mlp_error")
+

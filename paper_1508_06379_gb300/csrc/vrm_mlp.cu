@@ -1,0 +1,799 @@
+// The weight-proposal network of the learned path and its training, on the
+// tensor cores (tcgen05, bf16 operands, fp32 accumulators in TMEM).
+//
+// Network: 96 inputs (the K = 32 neighbour slots' scaled offsets xi_x, xi_y
+// and mask; padded to 128 columns with zeros) -> 256 -> 256 -> 256 -> 32,
+// GELU (erf form) after each hidden layer.  Parameters are kept as one fp32
+// vector [W1 (256x96), b1, W2 (256x256), b2, W3, b3, W4 (32x256), b4]; the
+// GEMMs read bf16 copies (W1 padded to 256x128) and, for the backward pass,
+// transposed bf16 copies.
+//
+// Every product is one kernel, k_gemm<NT>: C[M x N] = A[M x K] B[N x K]^T with
+// A and B K-major bf16 in global memory.  A CTA of 4 warps owns a 128-row
+// tile of C and NT columns: thread 0 streams 64-column slabs of A and B into
+// a 4-stage shared-memory ring with TMA and issues the MMAs (M = 128, N = NT,
+// K = 16) into a TMEM accumulator; all four warps then read the accumulator
+// (one TMEM lane = one row per thread) and run the fused epilogue (bias,
+// GELU, GELU derivative, bf16 rounding, transposed copies for the next
+// product).  Weight gradients split K (the batch) across CTAs and sum the
+// partials in a fixed order, so training is deterministic.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "vrm_internal.cuh"
+#include "vrm_umma.cuh"
+
+using namespace vrm;
+using bf16 = __nv_bfloat16;
+
+namespace {
+
+constexpr int kIn = 96;       // features
+constexpr int kInPad = 128;   // feature row stride
+constexpr int kHid = 256;
+constexpr int kOut = 32;
+constexpr int kOutPad = 64;   // dY row stride (one K slab)
+constexpr int kBM = 128;      // rows per tile
+constexpr int kBK = 64;       // K per slab
+constexpr int kStages = 4;
+constexpr long long kWaitCycles = 2000000000LL;  // about one second
+
+constexpr long kOffW1 = 0, kOffB1 = kOffW1 + (long)kHid * kIn;
+constexpr long kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + (long)kHid * kHid;
+constexpr long kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + (long)kHid * kHid;
+constexpr long kOffW4 = kOffB3 + kHid, kOffB4 = kOffW4 + (long)kOut * kHid;
+constexpr long kParams = kOffB4 + kOut;
+static_assert(kParams == VRM_MLP_PARAMS, "parameter count");
+
+enum EpiMode { EPI_BIAS_GELU = 0, EPI_BIAS_F32 = 1, EPI_F32 = 2, EPI_GELU_BWD = 3 };
+
+struct Epi {
+  int mode;
+  int M, N;              // logical output rows and columns (stores are guarded)
+  const int* m_dev;      // optional device row count (< M)
+  int k_slabs;           // K slabs of 64 per CTA
+  const float* bias;     // [N]
+  const float* z_in;     // EPI_GELU_BWD: pre-activations, ld_zin
+  int ld_zin;
+  float* out_f32;        // EPI_BIAS_F32 / EPI_F32 (+ blockIdx.z * split_stride)
+  int ld_f32;
+  long long split_stride;
+  bf16* out_bf16;        // row-major, ld_bf16
+  int ld_bf16;
+  bf16* out_t;           // transposed copy out_t[col * ld_t + row], optional
+  int ld_t;
+  float* out_z;          // EPI_BIAS_GELU: pre-activation store, optional
+  int ld_z;
+  int* error;            // set on a wait that gave up
+};
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+template <int NT>
+constexpr size_t gemm_smem_bytes() {
+  return 1024 + (size_t)kStages * (kBM * kBK * 2 + NT * kBK * 2) + 256;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtensorMap tma_a,
+                                                 const __grid_constant__ CUtensorMap tma_b, Epi e) {
+  static_assert(NT == 32 || NT == 64 || NT == 128 || NT == 256, "tile width");
+  extern __shared__ uint8_t smem_raw[];
+  const int m0 = blockIdx.x * kBM;
+  const int n0 = blockIdx.y * NT;
+  int m_limit = e.M;
+  if (e.m_dev) {
+    const int md = *e.m_dev;
+    m_limit = md < m_limit ? md : m_limit;
+  }
+  if (m0 >= m_limit) return;  // the whole CTA leaves before any barrier or TMEM use
+
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sa = base;                                   // kStages x 16 KB
+  uint8_t* sb = base + (size_t)kStages * kBM * kBK * 2;  // kStages x NT*128 B
+  uint64_t* bars = (uint64_t*)(sb + (size_t)kStages * NT * kBK * 2);
+  uint64_t* full = bars;                // TMA -> MMA
+  uint64_t* empty = bars + kStages;     // MMA -> TMA
+  uint64_t* done = bars + 2 * kStages;  // MMA -> epilogue
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * kStages + 1);
+  __shared__ int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    s_fail = 0;
+    for (int s = 0; s < kStages; ++s) {
+      umma::mbar_init(&full[s], 1);
+      umma::mbar_init(&empty[s], 1);
+    }
+    umma::mbar_init(done, 1);
+    umma::fence_barrier_init();
+  }
+  if (warp == 0) umma::tmem_alloc(tmem_slot, NT);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  const int nk = e.k_slabs;
+  const int kslab0 = blockIdx.z * nk;
+  constexpr uint32_t kStageBytes = kBM * kBK * 2 + NT * kBK * 2;
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    const uint32_t idesc = umma::idesc_bf16(kBM, NT);
+    auto load = [&](int stage, int kb) {
+      umma::mbar_arrive_expect_tx(&full[stage], kStageBytes);
+      umma::tma_load_2d(sa + (size_t)stage * kBM * kBK * 2, &tma_a, &full[stage], (kslab0 + kb) * kBK, m0);
+      umma::tma_load_2d(sb + (size_t)stage * NT * kBK * 2, &tma_b, &full[stage], (kslab0 + kb) * kBK, n0);
+    };
+    for (int s = 0; s < kStages && s < nk; ++s) load(s, s);
+    for (int kb = 0; kb < nk && ok; ++kb) {
+      const int s = kb % kStages;
+      if (!umma::mbar_wait(&full[s], (uint32_t)(kb / kStages) & 1u, kWaitCycles)) {
+        ok = false;
+        break;
+      }
+      umma::fence_after_sync();
+      const uint64_t da = umma::desc_sw128(umma::smem_u32(sa + (size_t)s * kBM * kBK * 2));
+      const uint64_t db = umma::desc_sw128(umma::smem_u32(sb + (size_t)s * NT * kBK * 2));
+#pragma unroll
+      for (int k = 0; k < kBK / 16; ++k)  // +32 bytes per K step (encoded >> 4)
+        umma::mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+      umma::mma_commit(&empty[s]);
+      const int kp = kb - 1;  // refill the slot read one slab earlier
+      if (kp >= 0 && kp + kStages < nk) {
+        const int sp = kp % kStages;
+        if (!umma::mbar_wait(&empty[sp], (uint32_t)(kp / kStages) & 1u, kWaitCycles)) {
+          ok = false;
+          break;
+        }
+        load(sp, kp + kStages);
+      }
+    }
+    umma::mma_commit(done);
+    if (!ok) s_fail = 1;
+  }
+  const bool got = umma::mbar_wait(done, 0, 2 * kWaitCycles);
+  umma::fence_after_sync();
+  const bool failed = __syncthreads_or(!got || s_fail) != 0;  // uniform: the TMEM loads below are warp-wide
+  if (failed) {
+    if (threadIdx.x == 0 && e.error) atomicExch(e.error, 1);
+  } else {
+    // epilogue: this thread's TMEM lane is row m0 + 32 warp + lane
+    const int row = m0 + warp * 32 + lane;
+    const bool row_ok = row < m_limit;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+      float v[16];
+      umma::tmem_ld16(trow + (uint32_t)c0, v);
+      const int col0 = n0 + c0;
+      if (!row_ok || col0 >= e.N) continue;
+      if (e.mode == EPI_BIAS_GELU) {
+        __align__(16) bf16 hv[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float z = v[i] + e.bias[col0 + i];
+          if (e.out_z) e.out_z[(size_t)row * e.ld_z + col0 + i] = z;
+          hv[i] = __float2bfloat16_rn(gelu(z));
+        }
+        uint4* dst = reinterpret_cast<uint4*>(e.out_bf16 + (size_t)row * e.ld_bf16 + col0);
+        dst[0] = *reinterpret_cast<uint4*>(&hv[0]);
+        dst[1] = *reinterpret_cast<uint4*>(&hv[8]);
+        if (e.out_t) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) e.out_t[(size_t)(col0 + i) * e.ld_t + row] = hv[i];
+        }
+      } else if (e.mode == EPI_BIAS_F32) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (col0 + i < e.N) e.out_f32[(size_t)row * e.ld_f32 + col0 + i] = v[i] + e.bias[col0 + i];
+      } else if (e.mode == EPI_F32) {
+        float* dst = e.out_f32 + (size_t)blockIdx.z * e.split_stride + (size_t)row * e.ld_f32 + col0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (col0 + i < e.N) dst[i] = v[i];
+      } else {  // EPI_GELU_BWD
+        __align__(16) bf16 hv[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float z = e.z_in[(size_t)row * e.ld_zin + col0 + i];
+          hv[i] = __float2bfloat16_rn(v[i] * gelu_grad(z));
+        }
+        uint4* dst = reinterpret_cast<uint4*>(e.out_bf16 + (size_t)row * e.ld_bf16 + col0);
+        dst[0] = *reinterpret_cast<uint4*>(&hv[0]);
+        dst[1] = *reinterpret_cast<uint4*>(&hv[8]);
+        if (e.out_t) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) e.out_t[(size_t)(col0 + i) * e.ld_t + row] = hv[i];
+        }
+      }
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    umma::fence_after_sync();
+    umma::tmem_dealloc(tmem, NT);
+  }
+}
+
+// ---- small kernels -----------------------------------------------------------------
+
+// Batch assembly: rows idx[r] (or r) of the data set into X [B x 128],
+// X^T [128 x B] and T [B x 32]; rows >= rows are zero (their mask is 0, so
+// they add nothing to the loss or the gradients).
+__global__ void k_gather(const bf16* __restrict__ X_all, const float* __restrict__ T_all,
+                         const int* __restrict__ idx, int rows, int B, bf16* __restrict__ Xb, bf16* __restrict__ Xbt,
+                         float* __restrict__ Tb) {
+  const long total = (long)B * kInPad;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / kInPad), c = (int)(t % kInPad);
+    bf16 v = __float2bfloat16_rn(0.0f);
+    if (r < rows) {
+      const long src = idx ? idx[r] : r;
+      v = X_all[src * kInPad + c];
+      if (c < kOut) Tb[(size_t)r * kOut + c] = T_all[src * kOut + c];
+    } else if (c < kOut) {
+      Tb[(size_t)r * kOut + c] = 0.0f;
+    }
+    Xb[(size_t)r * kInPad + c] = v;
+    Xbt[(size_t)c * B + r] = v;
+  }
+}
+
+// Masked mean squared error and its gradient, one block, fixed summation
+// order: dY = 2 M (Y - T) / sum(M), written as bf16 [B x 64] (columns >= 32
+// zero) and transposed [128 x B] (rows >= 32 zero).
+__global__ void __launch_bounds__(1024) k_loss(const float* __restrict__ Y, const float* __restrict__ T,
+                                               const bf16* __restrict__ Xb, int B, bf16* __restrict__ dY,
+                                               bf16* __restrict__ dYt, float* __restrict__ loss) {
+  __shared__ float red[32];
+  const int tid = threadIdx.x;
+  const long total = (long)B * kOut;
+  auto block_sum = [&](float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    float s = 0.0f;
+    if (tid < 32) {
+      s = tid < (int)(blockDim.x >> 5) ? red[tid] : 0.0f;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    __syncthreads();
+    if (tid == 0) red[0] = s;
+    __syncthreads();
+    const float r = red[0];
+    __syncthreads();
+    return r;
+  };
+  float cnt = 0.0f;
+  for (long t = tid; t < total; t += blockDim.x) {
+    const int r = (int)(t / kOut), k = (int)(t % kOut);
+    cnt += __bfloat162float(Xb[(size_t)r * kInPad + 2 * kOut + k]);
+  }
+  cnt = block_sum(cnt);
+  const float inv = 1.0f / fmaxf(cnt, 1.0f);
+  float l = 0.0f;
+  for (long t = tid; t < total; t += blockDim.x) {
+    const int r = (int)(t / kOut), k = (int)(t % kOut);
+    const float m = __bfloat162float(Xb[(size_t)r * kInPad + 2 * kOut + k]);
+    const float d = m * (Y[t] - T[t]);
+    l += d * d;
+    const bf16 g = __float2bfloat16_rn(2.0f * d * inv);
+    dY[(size_t)r * kOutPad + k] = g;
+    dY[(size_t)r * kOutPad + kOut + k] = __float2bfloat16_rn(0.0f);
+    dYt[(size_t)k * B + r] = g;
+  }
+  l = block_sum(l);
+  if (tid == 0) {
+    loss[0] = l * inv;
+    loss[1] = cnt;
+  }
+}
+
+// out[n] = sum over the B entries of row n of a bf16 [N x B] matrix (one
+// warp per row, fixed order).
+__global__ void k_rowsum(const bf16* __restrict__ m, int N, int B, float* __restrict__ out) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= N) return;
+  float s = 0.0f;
+  for (int r = lane; r < B; r += 32) s += __bfloat162float(m[(size_t)w * B + r]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[w] = s;
+}
+
+// g[r * cols + c] = sum_s part[s][r * ld + c] for r < rows, c < cols.
+__global__ void k_split_sum(const float* __restrict__ part, int splits, long long stride, int rows, int cols, int ld,
+                            float* __restrict__ g) {
+  const long total = (long)rows * cols;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / cols), c = (int)(t % cols);
+    float s = 0.0f;
+    for (int k = 0; k < splits; ++k) s += part[(size_t)k * stride + (size_t)r * ld + c];
+    g[t] = s;
+  }
+}
+
+// AdamW (decoupled weight decay): c1 = 1 - beta1^t, c2 = 1 - beta2^t.
+__global__ void k_adamw(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                        const float* __restrict__ g, long n, float lr, float b1, float b2, float eps, float wd,
+                        float c1, float c2) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / c1, vh = vi / c2;
+    theta[i] = theta[i] - lr * (mh / (sqrtf(vh) + eps) + wd * theta[i]);
+  }
+}
+
+// bf16 weights for the GEMMs from the fp32 parameters: W1 padded to 256 x 128,
+// W2, W3, W4, and transposed copies W2^T, W3^T (256 x 256), W4^T (256 x 64).
+__global__ void k_refresh(const float* __restrict__ th, bf16* __restrict__ W1, bf16* __restrict__ W2,
+                          bf16* __restrict__ W3, bf16* __restrict__ W4, bf16* __restrict__ W2t,
+                          bf16* __restrict__ W3t, bf16* __restrict__ W4t) {
+  const long n1 = (long)kHid * kInPad, n2 = (long)kHid * kHid, n4 = (long)kHid * kOutPad;
+  const long total = n1 + 2 * n2 + n4;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+    if (t < n1) {
+      const int r = (int)(t / kInPad), c = (int)(t % kInPad);
+      W1[t] = __float2bfloat16_rn(c < kIn ? th[kOffW1 + (long)r * kIn + c] : 0.0f);
+    } else if (t < n1 + n2) {
+      const long u = t - n1;
+      const int r = (int)(u / kHid), c = (int)(u % kHid);
+      const bf16 w = __float2bfloat16_rn(th[kOffW2 + u]);
+      W2[u] = w;
+      W2t[(long)c * kHid + r] = w;
+    } else if (t < n1 + 2 * n2) {
+      const long u = t - n1 - n2;
+      const int r = (int)(u / kHid), c = (int)(u % kHid);
+      const bf16 w = __float2bfloat16_rn(th[kOffW3 + u]);
+      W3[u] = w;
+      W3t[(long)c * kHid + r] = w;
+    } else {
+      const long u = t - n1 - 2 * n2;  // W4^T entry (c, r): c < 256, r < 64
+      const int c = (int)(u / kOutPad), r = (int)(u % kOutPad);
+      const bf16 w = __float2bfloat16_rn(r < kOut ? th[kOffW4 + (long)r * kHid + c] : 0.0f);
+      W4t[u] = w;
+      if (r < kOut) W4[(long)r * kHid + c] = w;
+    }
+  }
+}
+
+// ---- host side ----------------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+// Tensor map of a row-major bf16 matrix [rows x cols] read in boxes of
+// 64 columns x box_rows rows with 128-byte swizzle.  The caller keeps every
+// box inside the matrix (rows a multiple of box_rows, cols of 64).
+bool make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || !ptr || ((uintptr_t)ptr & 15u) || cols % 64 || rows % box_rows) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * 2};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int NT>
+cudaError_t launch_gemm_nt(const CUtensorMap& a, const CUtensorMap& b, int m_tiles, int n_tiles, int splits,
+                           const Epi& e, cudaStream_t s) {
+  static bool attr_set = false;
+  const size_t smem = gemm_smem_bytes<NT>();
+  if (!attr_set) {
+    cudaError_t r = cudaFuncSetAttribute(k_gemm<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (r != cudaSuccess) return r;
+    attr_set = true;
+  }
+  dim3 grid(m_tiles, n_tiles, splits);
+  k_gemm<NT><<<grid, 128, smem, s>>>(a, b, e);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// C[M x N] = A[M x K] B[N x K]^T with K split `splits` ways (K / 64 divisible).
+cudaError_t gemm(const CUtensorMap& a, const CUtensorMap& b, int nt, int m_bound, int N, int K, int splits, Epi e,
+                 cudaStream_t s) {
+  if (K % kBK || (K / kBK) % splits) return cudaErrorInvalidValue;
+  e.k_slabs = K / kBK / splits;
+  const int m_tiles = (m_bound + kBM - 1) / kBM;
+  const int n_tiles = (N + nt - 1) / nt;
+  switch (nt) {
+    case 32: return launch_gemm_nt<32>(a, b, m_tiles, n_tiles, splits, e, s);
+    case 64: return launch_gemm_nt<64>(a, b, m_tiles, n_tiles, splits, e, s);
+    case 128: return launch_gemm_nt<128>(a, b, m_tiles, n_tiles, splits, e, s);
+    case 256: return launch_gemm_nt<256>(a, b, m_tiles, n_tiles, splits, e, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+Epi epi(int mode, int M, int N) {
+  Epi e;
+  memset(&e, 0, sizeof(e));
+  e.mode = mode;
+  e.M = M;
+  e.N = N;
+  return e;
+}
+
+int blocks_for_n(long n, int threads) {
+  long b = (n + threads - 1) / threads;
+  const long cap = 8L * sm_count();
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+}  // namespace
+
+struct vrm_mlp {
+  int B = 0;       // training batch rows (multiple of 128)
+  int splits = 1;  // K splits of the weight-gradient products
+  int* err = nullptr;
+  float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *part = nullptr, *loss = nullptr;
+  bf16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W4 = nullptr, *W2t = nullptr, *W3t = nullptr, *W4t = nullptr;
+  bf16 *Xb = nullptr, *Xbt = nullptr;
+  float* Tb = nullptr;
+  float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *Y = nullptr;
+  bf16 *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *H1t = nullptr, *H2t = nullptr, *H3t = nullptr;
+  bf16 *dY = nullptr, *dYt = nullptr;
+  bf16 *dZ1 = nullptr, *dZ2 = nullptr, *dZ3 = nullptr, *dZ1t = nullptr, *dZ2t = nullptr, *dZ3t = nullptr;
+  // inference activations
+  int inf_rows = 0;
+  bf16 *Ha = nullptr, *Hb = nullptr;
+  CUtensorMap mW1, mW2, mW3, mW4, mW2t, mW3t, mW4t;  // weights as B operands
+  CUtensorMap mX, mXt, mH1, mH2, mH3, mH1t, mH2t, mH3t, mdY, mdYt, mdZ1t, mdZ2, mdZ2t, mdZ3, mdZ3t;
+  CUtensorMap mHa, mHb;
+};
+
+namespace vrm {
+
+// Forward pass of `rows` rows (bound; *rows_dev if given) of X (bf16
+// [rows_pad x 128], rows_pad = rows rounded up to 128, 16-byte aligned) into
+// Y (fp32 [rows x 32]).
+cudaError_t mlp_forward(vrm_mlp* net, const bf16* X, int rows, const int* rows_dev, float* Y, cudaStream_t s);
+cudaError_t mlp_reserve(vrm_mlp* net, int rows);
+
+cudaError_t mlp_reserve(vrm_mlp* net, int rows) {
+  const int rp = (rows + kBM - 1) / kBM * kBM;
+  if (rp <= net->inf_rows) return cudaSuccess;
+  if (net->Ha) cudaFree(net->Ha);
+  if (net->Hb) cudaFree(net->Hb);
+  net->Ha = net->Hb = nullptr;
+  net->inf_rows = 0;
+  cudaError_t e = cudaMalloc(&net->Ha, (size_t)rp * kHid * sizeof(bf16));
+  if (e == cudaSuccess) e = cudaMalloc(&net->Hb, (size_t)rp * kHid * sizeof(bf16));
+  if (e != cudaSuccess) return e;
+  if (!make_map(&net->mHa, net->Ha, rp, kHid, kBM) || !make_map(&net->mHb, net->Hb, rp, kHid, kBM))
+    return cudaErrorInvalidValue;
+  net->inf_rows = rp;
+  return cudaSuccess;
+}
+
+cudaError_t mlp_forward(vrm_mlp* net, const bf16* X, int rows, const int* rows_dev, float* Y, cudaStream_t s) {
+  if (rows <= 0) return cudaSuccess;
+  const int rp = (rows + kBM - 1) / kBM * kBM;
+  if (rp > net->inf_rows) return cudaErrorInvalidValue;  // mlp_reserve first (not while capturing)
+  CUtensorMap mXin;
+  if (!make_map(&mXin, X, rp, kInPad, kBM)) return cudaErrorInvalidValue;
+  cudaError_t r;
+  Epi e = epi(EPI_BIAS_GELU, rows, kHid);
+  e.m_dev = rows_dev;
+  e.error = net->err;
+  e.bias = net->theta + kOffB1;
+  e.out_bf16 = net->Ha;
+  e.ld_bf16 = kHid;
+  if ((r = gemm(mXin, net->mW1, 256, rows, kHid, kInPad, 1, e, s)) != cudaSuccess) return r;
+  e.bias = net->theta + kOffB2;
+  e.out_bf16 = net->Hb;
+  if ((r = gemm(net->mHa, net->mW2, 256, rows, kHid, kHid, 1, e, s)) != cudaSuccess) return r;
+  e.bias = net->theta + kOffB3;
+  e.out_bf16 = net->Ha;
+  if ((r = gemm(net->mHb, net->mW3, 256, rows, kHid, kHid, 1, e, s)) != cudaSuccess) return r;
+  Epi f = epi(EPI_BIAS_F32, rows, kOut);
+  f.m_dev = rows_dev;
+  f.error = net->err;
+  f.bias = net->theta + kOffB4;
+  f.out_f32 = Y;
+  f.ld_f32 = kOut;
+  return gemm(net->mHa, net->mW4, 32, rows, kOut, kHid, 1, f, s);
+}
+
+}  // namespace vrm
+
+namespace {
+
+void free_mlp(vrm_mlp* n) {
+  void* ptrs[] = {n->err, n->theta, n->m, n->v, n->grad, n->part, n->loss, n->W1, n->W2, n->W3, n->W4, n->W2t,
+                  n->W3t, n->W4t, n->Xb, n->Xbt, n->Tb, n->Z1, n->Z2, n->Z3, n->Y, n->H1, n->H2, n->H3, n->H1t,
+                  n->H2t, n->H3t, n->dY, n->dYt, n->dZ1, n->dZ2, n->dZ3, n->dZ1t, n->dZ2t, n->dZ3t, n->Ha, n->Hb};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+template <typename T>
+cudaError_t zalloc(T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * count);
+  if (e == cudaSuccess) e = cudaMemset(*p, 0, sizeof(T) * count);
+  return e;
+}
+
+// Forward and backward of the current batch (Xb, Xbt, Tb): loss -> net->loss,
+// gradient -> net->grad.
+cudaError_t forward_backward(vrm_mlp* n, cudaStream_t s) {
+  const int B = n->B;
+  cudaError_t r;
+  // forward, keeping pre-activations and transposed activations
+  Epi e = epi(EPI_BIAS_GELU, B, kHid);
+  e.error = n->err;
+  e.ld_bf16 = kHid;
+  e.ld_t = B;
+  e.ld_z = kHid;
+  e.bias = n->theta + kOffB1, e.out_bf16 = n->H1, e.out_t = n->H1t, e.out_z = n->Z1;
+  if ((r = gemm(n->mX, n->mW1, 256, B, kHid, kInPad, 1, e, s)) != cudaSuccess) return r;
+  e.bias = n->theta + kOffB2, e.out_bf16 = n->H2, e.out_t = n->H2t, e.out_z = n->Z2;
+  if ((r = gemm(n->mH1, n->mW2, 256, B, kHid, kHid, 1, e, s)) != cudaSuccess) return r;
+  e.bias = n->theta + kOffB3, e.out_bf16 = n->H3, e.out_t = n->H3t, e.out_z = n->Z3;
+  if ((r = gemm(n->mH2, n->mW3, 256, B, kHid, kHid, 1, e, s)) != cudaSuccess) return r;
+  Epi f = epi(EPI_BIAS_F32, B, kOut);
+  f.error = n->err;
+  f.bias = n->theta + kOffB4, f.out_f32 = n->Y, f.ld_f32 = kOut;
+  if ((r = gemm(n->mH3, n->mW4, 32, B, kOut, kHid, 1, f, s)) != cudaSuccess) return r;
+  k_loss<<<1, 1024, 0, s>>>(n->Y, n->Tb, n->Xb, B, n->dY, n->dYt, n->loss);
+  note_launch();
+  // backward
+  const long long pstride = (long long)kHid * kHid;
+  Epi w = epi(EPI_F32, kOut, kHid);  // dW4 = dY^T H3
+  w.error = n->err;
+  w.out_f32 = n->part, w.ld_f32 = kHid, w.split_stride = pstride;
+  if ((r = gemm(n->mdYt, n->mH3t, 256, kOut, kHid, B, n->splits, w, s)) != cudaSuccess) return r;
+  k_split_sum<<<blocks_for_n((long)kOut * kHid, 256), 256, 0, s>>>(n->part, n->splits, pstride, kOut, kHid, kHid,
+                                                                    n->grad + kOffW4);
+  note_launch();
+  k_rowsum<<<(kOut * 32 + 255) / 256, 256, 0, s>>>(n->dYt, kOut, B, n->grad + kOffB4);
+  note_launch();
+  Epi d = epi(EPI_GELU_BWD, B, kHid);  // dZ3 = (dY W4) * gelu'(Z3)
+  d.error = n->err;
+  d.ld_bf16 = kHid, d.ld_t = B, d.ld_zin = kHid;
+  d.z_in = n->Z3, d.out_bf16 = n->dZ3, d.out_t = n->dZ3t;
+  if ((r = gemm(n->mdY, n->mW4t, 256, B, kHid, kOutPad, 1, d, s)) != cudaSuccess) return r;
+  w = epi(EPI_F32, kHid, kHid);  // dW3 = dZ3^T H2
+  w.error = n->err;
+  w.out_f32 = n->part, w.ld_f32 = kHid, w.split_stride = pstride;
+  if ((r = gemm(n->mdZ3t, n->mH2t, 256, kHid, kHid, B, n->splits, w, s)) != cudaSuccess) return r;
+  k_split_sum<<<blocks_for_n(pstride, 256), 256, 0, s>>>(n->part, n->splits, pstride, kHid, kHid, kHid,
+                                                          n->grad + kOffW3);
+  note_launch();
+  k_rowsum<<<(kHid * 32 + 255) / 256, 256, 0, s>>>(n->dZ3t, kHid, B, n->grad + kOffB3);
+  note_launch();
+  d.z_in = n->Z2, d.out_bf16 = n->dZ2, d.out_t = n->dZ2t;  // dZ2 = (dZ3 W3) * gelu'(Z2)
+  if ((r = gemm(n->mdZ3, n->mW3t, 256, B, kHid, kHid, 1, d, s)) != cudaSuccess) return r;
+  if ((r = gemm(n->mdZ2t, n->mH1t, 256, kHid, kHid, B, n->splits, w, s)) != cudaSuccess) return r;  // dW2
+  k_split_sum<<<blocks_for_n(pstride, 256), 256, 0, s>>>(n->part, n->splits, pstride, kHid, kHid, kHid,
+                                                          n->grad + kOffW2);
+  note_launch();
+  k_rowsum<<<(kHid * 32 + 255) / 256, 256, 0, s>>>(n->dZ2t, kHid, B, n->grad + kOffB2);
+  note_launch();
+  d.z_in = n->Z1, d.out_bf16 = n->dZ1, d.out_t = n->dZ1t;  // dZ1 = (dZ2 W2) * gelu'(Z1)
+  if ((r = gemm(n->mdZ2, n->mW2t, 256, B, kHid, kHid, 1, d, s)) != cudaSuccess) return r;
+  w = epi(EPI_F32, kHid, kInPad);  // dW1 = dZ1^T X (padded input columns dropped in the sum)
+  w.error = n->err;
+  w.out_f32 = n->part, w.ld_f32 = kInPad, w.split_stride = pstride;
+  if ((r = gemm(n->mdZ1t, n->mXt, 128, kHid, kInPad, B, n->splits, w, s)) != cudaSuccess) return r;
+  k_split_sum<<<blocks_for_n((long)kHid * kIn, 256), 256, 0, s>>>(n->part, n->splits, pstride, kHid, kIn, kInPad,
+                                                                    n->grad + kOffW1);
+  note_launch();
+  k_rowsum<<<(kHid * 32 + 255) / 256, 256, 0, s>>>(n->dZ1t, kHid, B, n->grad + kOffB1);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t refresh(vrm_mlp* n, cudaStream_t s) {
+  const long total = (long)kHid * kInPad + 2L * kHid * kHid + (long)kHid * kOutPad;
+  k_refresh<<<blocks_for_n(total, 256), 256, 0, s>>>(n->theta, n->W1, n->W2, n->W3, n->W4, n->W2t, n->W3t, n->W4t);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t gather(vrm_mlp* n, const bf16* X, const float* T, const int* idx, int rows, cudaStream_t s) {
+  k_gather<<<blocks_for_n((long)n->B * kInPad, 256), 256, 0, s>>>(X, T, idx, rows, n->B, n->Xb, n->Xbt, n->Tb);
+  note_launch();
+  return cudaGetLastError();
+}
+
+vrm_status check_err(vrm_mlp* n, cudaStream_t s) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, n->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return VRM_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return VRM_ERR_CUDA;
+  return h ? VRM_ERR_CUDA : VRM_OK;
+}
+
+bool adamw_ok(const vrm_adamw* a) {
+  return a && a->lr >= 0 && a->beta1 >= 0 && a->beta1 < 1 && a->beta2 >= 0 && a->beta2 < 1 && a->eps >= 0 &&
+         a->weight_decay >= 0 && std::isfinite(a->lr);
+}
+
+vrm_status run_adamw(vrm_mlp* n, const float* grad, const vrm_adamw* a, int32_t t, cudaStream_t s) {
+  const double c1 = 1.0 - std::pow((double)a->beta1, (double)t);
+  const double c2 = 1.0 - std::pow((double)a->beta2, (double)t);
+  k_adamw<<<blocks_for_n(kParams, 256), 256, 0, s>>>(n->theta, n->m, n->v, grad, kParams, a->lr, a->beta1, a->beta2,
+                                                      a->eps, a->weight_decay, (float)c1, (float)c2);
+  note_launch();
+  if (refresh(n, s) != cudaSuccess) return VRM_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? VRM_OK : VRM_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+vrm_status vrm_mlp_create(int32_t batch_rows, vrm_mlp** out) {
+  if (!out) return VRM_ERR_ARG;
+  *out = nullptr;
+  if (batch_rows < kBM || batch_rows % kBM || batch_rows > (1 << 20)) return VRM_ERR_ARG;
+  if (!encode_fn()) return VRM_ERR_UNSUPPORTED;
+  vrm_mlp* n = new (std::nothrow) vrm_mlp();
+  if (!n) return VRM_ERR_CUDA;
+  const int B = batch_rows;
+  n->B = B;
+  // weight-gradient products: K = B split in at most 64 equal pieces of whole
+  // 128-row blocks
+  int splits = 1;
+  for (int d = 64; d >= 1; --d)
+    if ((B / 128) % d == 0) {
+      splits = d;
+      break;
+    }
+  n->splits = splits;
+  cudaError_t e = cudaSuccess;
+#define MLP_ALLOC(p, cnt) \
+  if (e == cudaSuccess) e = zalloc(&(n->p), (size_t)(cnt))
+  MLP_ALLOC(err, 1);
+  MLP_ALLOC(theta, kParams);
+  MLP_ALLOC(m, kParams);
+  MLP_ALLOC(v, kParams);
+  MLP_ALLOC(grad, kParams);
+  MLP_ALLOC(part, (size_t)splits * kHid * kHid);
+  MLP_ALLOC(loss, 2);
+  MLP_ALLOC(W1, (size_t)kHid * kInPad);
+  MLP_ALLOC(W2, (size_t)kHid * kHid);
+  MLP_ALLOC(W3, (size_t)kHid * kHid);
+  MLP_ALLOC(W4, (size_t)kOut * kHid);
+  MLP_ALLOC(W2t, (size_t)kHid * kHid);
+  MLP_ALLOC(W3t, (size_t)kHid * kHid);
+  MLP_ALLOC(W4t, (size_t)kHid * kOutPad);
+  MLP_ALLOC(Xb, (size_t)B * kInPad);
+  MLP_ALLOC(Xbt, (size_t)kInPad * B);
+  MLP_ALLOC(Tb, (size_t)B * kOut);
+  MLP_ALLOC(Z1, (size_t)B * kHid);
+  MLP_ALLOC(Z2, (size_t)B * kHid);
+  MLP_ALLOC(Z3, (size_t)B * kHid);
+  MLP_ALLOC(Y, (size_t)B * kOut);
+  MLP_ALLOC(H1, (size_t)B * kHid);
+  MLP_ALLOC(H2, (size_t)B * kHid);
+  MLP_ALLOC(H3, (size_t)B * kHid);
+  MLP_ALLOC(H1t, (size_t)kHid * B);
+  MLP_ALLOC(H2t, (size_t)kHid * B);
+  MLP_ALLOC(H3t, (size_t)kHid * B);
+  MLP_ALLOC(dY, (size_t)B * kOutPad);
+  MLP_ALLOC(dYt, (size_t)kBM * B);
+  MLP_ALLOC(dZ1, (size_t)B * kHid);
+  MLP_ALLOC(dZ2, (size_t)B * kHid);
+  MLP_ALLOC(dZ3, (size_t)B * kHid);
+  MLP_ALLOC(dZ1t, (size_t)kHid * B);
+  MLP_ALLOC(dZ2t, (size_t)kHid * B);
+  MLP_ALLOC(dZ3t, (size_t)kHid * B);
+#undef MLP_ALLOC
+  bool ok = e == cudaSuccess;
+  // B operands (weights): boxes of NT rows; A operands: 128-row boxes
+  ok = ok && make_map(&n->mW1, n->W1, kHid, kInPad, 256) && make_map(&n->mW2, n->W2, kHid, kHid, 256) &&
+       make_map(&n->mW3, n->W3, kHid, kHid, 256) && make_map(&n->mW4, n->W4, kOut, kHid, 32) &&
+       make_map(&n->mW2t, n->W2t, kHid, kHid, 256) && make_map(&n->mW3t, n->W3t, kHid, kHid, 256) &&
+       make_map(&n->mW4t, n->W4t, kHid, kOutPad, 256);
+  ok = ok && make_map(&n->mX, n->Xb, B, kInPad, kBM) && make_map(&n->mXt, n->Xbt, kInPad, B, 128) &&
+       make_map(&n->mH1, n->H1, B, kHid, kBM) && make_map(&n->mH2, n->H2, B, kHid, kBM) &&
+       make_map(&n->mH3, n->H3, B, kHid, kBM) && make_map(&n->mH1t, n->H1t, kHid, B, 256) &&
+       make_map(&n->mH2t, n->H2t, kHid, B, 256) && make_map(&n->mH3t, n->H3t, kHid, B, 256) &&
+       make_map(&n->mdY, n->dY, B, kOutPad, kBM) && make_map(&n->mdYt, n->dYt, kBM, B, kBM) &&
+       make_map(&n->mdZ1t, n->dZ1t, kHid, B, kBM) && make_map(&n->mdZ2, n->dZ2, B, kHid, kBM) &&
+       make_map(&n->mdZ2t, n->dZ2t, kHid, B, kBM) && make_map(&n->mdZ3, n->dZ3, B, kHid, kBM) &&
+       make_map(&n->mdZ3t, n->dZ3t, kHid, B, kBM);
+  if (!ok) {
+    free_mlp(n);
+    delete n;
+    cudaGetLastError();
+    return e == cudaSuccess ? VRM_ERR_UNSUPPORTED : VRM_ERR_CUDA;
+  }
+  *out = n;
+  return VRM_OK;
+}
+
+void vrm_mlp_destroy(vrm_mlp* n) {
+  if (!n) return;
+  free_mlp(n);
+  delete n;
+}
+
+vrm_status vrm_mlp_set_params(vrm_mlp* n, const float* theta, cudaStream_t s) {
+  if (!n || !theta) return VRM_ERR_ARG;
+  if (cudaMemcpyAsync(n->theta, theta, sizeof(float) * kParams, cudaMemcpyDefault, s) != cudaSuccess)
+    return VRM_ERR_CUDA;
+  if (cudaMemsetAsync(n->m, 0, sizeof(float) * kParams, s) != cudaSuccess) return VRM_ERR_CUDA;
+  if (cudaMemsetAsync(n->v, 0, sizeof(float) * kParams, s) != cudaSuccess) return VRM_ERR_CUDA;
+  if (refresh(n, s) != cudaSuccess) return VRM_ERR_CUDA;
+  return VRM_OK;
+}
+
+vrm_status vrm_mlp_get_params(const vrm_mlp* n, float* theta, cudaStream_t s) {
+  if (!n || !theta) return VRM_ERR_ARG;
+  if (cudaMemcpyAsync(theta, n->theta, sizeof(float) * kParams, cudaMemcpyDefault, s) != cudaSuccess)
+    return VRM_ERR_CUDA;
+  return VRM_OK;
+}
+
+vrm_status vrm_mlp_forward(vrm_mlp* n, const uint16_t* X, int32_t rows, float* Y, cudaStream_t s) {
+  if (!n || rows < 0 || (rows > 0 && (!X || !Y)) || ((uintptr_t)X & 15u)) return VRM_ERR_ARG;
+  if (rows == 0) return VRM_OK;
+  if (mlp_reserve(n, rows) != cudaSuccess) return VRM_ERR_CUDA;
+  if (mlp_forward(n, reinterpret_cast<const bf16*>(X), rows, nullptr, Y, s) != cudaSuccess) return VRM_ERR_CUDA;
+  return check_err(n, s);
+}
+
+vrm_status vrm_mlp_grads(vrm_mlp* n, const uint16_t* X, const float* T, int32_t rows, float* grad, float* loss,
+                         cudaStream_t s) {
+  if (!n || !X || !T || rows < 1 || rows > n->B) return VRM_ERR_ARG;
+  if (gather(n, reinterpret_cast<const bf16*>(X), T, nullptr, rows, s) != cudaSuccess) return VRM_ERR_CUDA;
+  if (forward_backward(n, s) != cudaSuccess) return VRM_ERR_CUDA;
+  if (grad && cudaMemcpyAsync(grad, n->grad, sizeof(float) * kParams, cudaMemcpyDefault, s) != cudaSuccess)
+    return VRM_ERR_CUDA;
+  if (loss && cudaMemcpyAsync(loss, n->loss, sizeof(float) * 2, cudaMemcpyDefault, s) != cudaSuccess)
+    return VRM_ERR_CUDA;
+  return check_err(n, s);
+}
+
+vrm_status vrm_mlp_train_step(vrm_mlp* n, const uint16_t* X_all, const float* T_all, const int32_t* batch_idx,
+                              int32_t rows, const vrm_adamw* hp, int32_t t, float* loss, cudaStream_t s) {
+  if (!n || !X_all || !T_all || rows < 1 || rows > n->B || t < 1 || !adamw_ok(hp)) return VRM_ERR_ARG;
+  if (gather(n, reinterpret_cast<const bf16*>(X_all), T_all, batch_idx, rows, s) != cudaSuccess) return VRM_ERR_CUDA;
+  if (forward_backward(n, s) != cudaSuccess) return VRM_ERR_CUDA;
+  if (loss && cudaMemcpyAsync(loss, n->loss, sizeof(float) * 2, cudaMemcpyDefault, s) != cudaSuccess)
+    return VRM_ERR_CUDA;
+  return run_adamw(n, n->grad, hp, t, s);
+}
+
+vrm_status vrm_mlp_adamw(vrm_mlp* n, const float* grad, const vrm_adamw* hp, int32_t t, cudaStream_t s) {
+  if (!n || !grad || t < 1 || !adamw_ok(hp)) return VRM_ERR_ARG;
+  return run_adamw(n, grad, hp, t, s);
+}
+
+vrm_status vrm_mlp_error(vrm_mlp* n, cudaStream_t s) {
+  if (!n) return VRM_ERR_ARG;
+  return check_err(n, s);
+}
+
+}  // extern "C"

@@ -13,6 +13,9 @@ Workloads (the paper has no dataset; every cloud here is synthetic):
 * ``gaussian_mixture_cloud``: a jittered lattice carrying a sum of Gaussian
   vortices, omega = sum_k Gamma_k/(2 pi s_k^2) exp(-|x-c_k|^2/(2 s_k^2)).
 * ``batched_clouds``: many independent mixture clouds of log-uniform size.
+* ``mlp_params``, ``mlp_rows``, ``mlp_vector``: random parameters, input rows
+  and vectors for the weight-proposal network (rows of exactly
+  bf16-representable values: multiples of 1/64 in [-2, 2] and 0/1 masks).
 """
 import math
 
@@ -129,3 +132,40 @@ def uniform_scatter(n, half_width=1.0, seed=0):
     y = rng.uniform(-half_width, half_width, n)
     g = rng.standard_normal(n)
     return x, y, g
+
+
+MLP_SHAPES = ((256, 96), (256, 256), (256, 256), (32, 256))
+
+
+def mlp_params(seed=SEED_BASE + 4, bias_scale=0.05):
+    """Flat parameter vector [W1, b1, ..., W4, b4]: W ~ N(0, 1/fan_in), b ~ N(0, bias_scale^2)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for out, inp in MLP_SHAPES:
+        parts.append(rng.normal(0.0, 1.0 / math.sqrt(inp), out * inp))
+        parts.append(rng.normal(0.0, bias_scale, out))
+    return np.concatenate(parts)
+
+
+def mlp_rows(rows, seed=SEED_BASE + 5):
+    """Network input rows [rows, 128]: per row a random number k of filled
+    slots (8..32), offsets on the 1/64 grid in [-2, 2], mask 1 on the first k
+    slots, zeros elsewhere; and targets [rows, 32]: on filled slots a smooth
+    non-negative function of the slot's own offsets, max(xi_x, 0)/2 +
+    xi_y^2/8, zero elsewhere (learnable, unlike noise)."""
+    rng = np.random.default_rng(seed)
+    X = np.zeros((rows, 128))
+    T = np.zeros((rows, 32))
+    for r in range(rows):
+        k = int(rng.integers(8, 33))
+        X[r, :k] = rng.integers(-128, 129, k) / 64.0
+        X[r, 32:32 + k] = rng.integers(-128, 129, k) / 64.0
+        X[r, 64:64 + k] = 1.0
+        T[r, :k] = np.maximum(X[r, :k], 0.0) / 2 + X[r, 32:32 + k] ** 2 / 8
+    return X, T
+
+
+def mlp_vector(seed, n=164640, scale=1.0):
+    """A random vector of the parameter length (e.g. a gradient)."""
+    return np.random.default_rng(seed).normal(0.0, scale, n)
+
