@@ -66,6 +66,7 @@ typedef int vrm_status;
 #define VRM_LP_SMALL 1   /* solved on the small neighbourhood (Sec. 4.3) */
 #define VRM_LP_FULL 2    /* solved on the full neighbourhood after a retry */
 #define VRM_LP_NONE 3    /* no non-negative stencil found: zero stencil */
+#define VRM_LP_LEARNED 4 /* the network's proposal, corrected and accepted (vrm_set_mlp) */
 
 /* Precision of the neighbour search (Sec. 2, Eq. neighbourhood). */
 #define VRM_PREC_FP64 0  /* FP64 distances (bit-identical to the FP64 oracle) */
@@ -107,6 +108,8 @@ typedef struct vrm_stats {
   int64_t lp_small_pivots; /* pivots summed over those LPs */
   int64_t lp_full_solved;  /* LPs run on full neighbourhoods */
   int64_t lp_full_pivots;  /* pivots summed over those LPs */
+  int64_t learned_ok;      /* stencils from the learned proposal (vrm_set_mlp) */
+  int64_t learned_rejected; /* proposals rejected (then solved by the LP) */
 } vrm_stats;
 
 /* Stages of vrm_step, for vrm_stage_times. */
@@ -351,6 +354,36 @@ vrm_status vrm_mlp_train_step(vrm_mlp* net, const uint16_t* X_all, const float* 
 vrm_status vrm_mlp_adamw(vrm_mlp* net, const float* grad, const vrm_adamw* hp, int32_t t, cudaStream_t stream);
 /* VRM_ERR_CUDA if a tensor-core wait of an earlier asynchronous call gave up.  Synchronises. */
 vrm_status vrm_mlp_error(vrm_mlp* net, cudaStream_t stream);
+
+/*
+ * The learned proposal in the step.  With a network set, vrm_step and
+ * vrm_solve_weights first build the input rows of every diffused particle,
+ * run the network, correct each proposal onto the moment conditions and
+ * accept it under the test above; only the rejected particles run the LP
+ * (small neighbourhood, then the full-neighbourhood retry).  The network must
+ * outlive its use; its weights may change between steps (training).  NULL
+ * restores the LP for every particle.  The network's time counts in the
+ * VRM_STAGE_LP_SMALL stage.
+ */
+vrm_status vrm_set_mlp(vrm_ctx* ctx, vrm_mlp* net);
+
+/* Input rows of the listed particles (list: device int32 [m], or NULL for
+ * 0..m-1) from their neighbour rows: X bf16 [m rounded up to 128][128] and
+ * slots int32 [m][32] (particle index of each slot, -1 empty). */
+vrm_status vrm_learned_features(vrm_ctx* ctx, const double* x, const double* y, const int32_t* list, int32_t m,
+                                const int32_t* nbr_count, const int32_t* nbr_idx, uint16_t* X, int32_t* slots,
+                                cudaStream_t stream);
+/* Correction and acceptance of given proposals f0 (device fp32 [m][32]) for
+ * the listed particles: accepted stencils are written as by the LP (status
+ * VRM_LP_LEARNED), rejected ones get VRM_LP_NONE and a zero stencil.
+ * *n_accepted (host) receives the count.  Synchronises. */
+vrm_status vrm_learned_project(vrm_ctx* ctx, const double* x, const double* y, const int32_t* list, int32_t m,
+                               const int32_t* slots, const float* f0, int32_t* cols, double* f, double* fii,
+                               uint8_t* status, int32_t* n_accepted, cudaStream_t stream);
+/* Training targets: T fp32 [m][32], the weight f~ of each listed particle's
+ * stencil (cols, f as written by vrm_solve_weights) at each slot's particle. */
+vrm_status vrm_learned_targets(const int32_t* list, int32_t m, const int32_t* slots, const int32_t* cols,
+                               const double* f, float* T, cudaStream_t stream);
 
 /* Per-stage timing of vrm_step with CUDA events recorded on the call's
    stream between the stages.  Off by default; enable != 0 turns it on. */

@@ -24,7 +24,12 @@ and signs; everything else goes to the LP.  The pieces:
   meets the moment conditions on S,
       f_S = f0_S + V_S^T (V_S V_S^T)^{-1} (b - V_S f0_S),
   and accepted iff every f_j >= 0 and the residual |V_S f_S - b|_inf is at
-  most 1e-12 (Sec. 3.1's non-negativity, Eq. cond_two/cond_alpha).
+  most 1e-12 (Sec. 3.1's non-negativity, Eq. cond_two/cond_alpha).  While a
+  corrected weight is negative and |S| > 5, the slot with the smallest
+  corrected weight (ties: the later slot) leaves S and the original proposal
+  is corrected again on the smaller support; at |S| = 5 the correction is the
+  unique solution on those five neighbours.  A Gram matrix V_S V_S^T whose
+  Cholesky pivot falls to 1e-10 of its largest diagonal entry rejects.
 """
 import numpy as np
 
@@ -203,19 +208,47 @@ def project(xi, eta, f0, b=B_RHS):
     return f, float(np.max(np.abs(V @ f - b)))
 
 
+def gram_ok(V, rel=1e-10):
+    """Cholesky of G = V V^T written out; False if a pivot is at most rel
+    times the largest diagonal entry (the rows are then nearly dependent)."""
+    G = V @ V.T
+    n = G.shape[0]
+    L = np.zeros_like(G)
+    gmax = float(np.max(np.diag(G)))
+    for a in range(n):
+        d = G[a, a] - float(np.sum(L[a, :a] ** 2))
+        if not d > rel * gmax:
+            return False
+        L[a, a] = np.sqrt(d)
+        for q in range(a + 1, n):
+            L[q, a] = (G[q, a] - float(np.sum(L[q, :a] * L[a, :a]))) / L[a, a]
+    return True
+
+
+MAX_DROPS = 3
+
+
 def learned_stencil(x, y, h, i, slots, f0):
     """The learned stencil of particle i from its slot map and proposal:
     (accepted, particle indices, f~ in slot order, f~_ii)."""
     S = support(f0, slots)
-    if len(S) < 5:
-        return False, [], None, 0.0
+    p32 = np.asarray(f0, dtype=np.float32)
     inv_h = 1.0 / h
-    js = [int(slots[k]) for k in S]
-    xi = np.array([(x[j] - x[i]) * inv_h for j in js])
-    eta = np.array([(y[j] - y[i]) * inv_h for j in js])
-    V = vandermonde(xi, eta)
-    if np.linalg.matrix_rank(V) < 5:
-        return False, js, None, 0.0
-    f, res = project(xi, eta, np.asarray(f0, dtype=np.float32)[S].astype(np.float64))
-    ok = bool(np.all(f >= 0.0) and res <= ACCEPT_RESID)
-    return ok, js, f, -float(np.sum(f))
+    f = None
+    js = []
+    for _ in range(MAX_DROPS + 1):
+        if len(S) < 5:
+            break
+        js = [int(slots[k]) for k in S]
+        xi = np.array([(x[j] - x[i]) * inv_h for j in js])
+        eta = np.array([(y[j] - y[i]) * inv_h for j in js])
+        if not gram_ok(vandermonde(xi, eta)):
+            return False, js, None, 0.0
+        f, res = project(xi, eta, p32[S].astype(np.float64))
+        if np.all(f >= 0.0) and res <= ACCEPT_RESID:
+            return True, js, f, -float(np.sum(f))
+        if len(S) == 5:
+            break
+        worst = min(range(len(S)), key=lambda p: (f[p], -p))
+        S = S[:worst] + S[worst + 1:]
+    return False, js, f, 0.0

@@ -21,7 +21,7 @@ STENCIL_W = 8
 KCAP_MAX = 32
 PREC_FP64 = 0
 PREC_MIXED = 1
-LP_NOT_DIFFUSED, LP_SMALL, LP_FULL, LP_NONE = 0, 1, 2, 3
+LP_NOT_DIFFUSED, LP_SMALL, LP_FULL, LP_NONE, LP_LEARNED = 0, 1, 2, 3, 4
 
 
 class Params(ctypes.Structure):
@@ -38,7 +38,8 @@ class Stats(ctypes.Structure):
                 ("max_pivots", ctypes.c_int32), ("max_count", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("max_dt_ratio", ctypes.c_double), ("lp_small_solved", ctypes.c_int64),
                 ("lp_small_pivots", ctypes.c_int64), ("lp_full_solved", ctypes.c_int64),
-                ("lp_full_pivots", ctypes.c_int64)]
+                ("lp_full_pivots", ctypes.c_int64), ("learned_ok", ctypes.c_int64),
+                ("learned_rejected", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -112,6 +113,10 @@ SIGNATURES = {
     "vrm_mlp_train_step": (ctypes.c_int, [P, P, P, P, I32, P, I32, P, P]),
     "vrm_mlp_adamw": (ctypes.c_int, [P, P, P, I32, P]),
     "vrm_mlp_error": (ctypes.c_int, [P, P]),
+    "vrm_set_mlp": (ctypes.c_int, [P, P]),
+    "vrm_learned_features": (ctypes.c_int, [P, P, P, P, I32, P, P, P, P, P]),
+    "vrm_learned_project": (ctypes.c_int, [P, P, P, P, I32, P, P, P, P, P, P, P, P]),
+    "vrm_learned_targets": (ctypes.c_int, [P, I32, P, P, P, P, P]),
 }
 MLP_PARAMS = 164640
 MLP_IN = 128
@@ -295,6 +300,44 @@ class VRM:
     def set_timing(self, enable=True):
         self._check(self.lib.vrm_set_timing(self.ctx, int(bool(enable))), "vrm_set_timing")
 
+    def set_mlp(self, net):
+        """Use the network's proposals first (None: the LP for every particle)."""
+        self._check(self.lib.vrm_set_mlp(self.ctx, net.net if net is not None else None), "vrm_set_mlp")
+        self._mlp = net  # keep it alive while the context uses it
+
+    def learned_features(self, x, y, list_, nb, m=None):
+        """Input rows (bf16 [m rounded up to 128, 128]) and slot map (int32 [m, 32])."""
+        m = int(list_.numel()) if m is None else int(m)
+        dev = x.device
+        X = torch.zeros(max((m + 127) // 128 * 128, 128), MLP_IN, dtype=torch.bfloat16, device=dev)
+        slots = torch.empty(max(m, 1), 32, dtype=torch.int32, device=dev)
+        n = x.numel()
+        self._check(self.lib.vrm_learned_features(
+            self.ctx, _ptr(x, torch.float64, "x"), _ptr(y, torch.float64, "y"),
+            _ptr(list_, torch.int32, "list", m) if list_ is not None else None, m,
+            _ptr(nb["count"], torch.int32, "nbr_count"), _ptr(nb["idx"], torch.int32, "nbr_idx"),
+            _ptr(X, torch.bfloat16, "X"), _ptr(slots, torch.int32, "slots"), _stream()), "vrm_learned_features")
+        return X, slots[:m]
+
+    def learned_project(self, x, y, list_, slots, f0, n):
+        """Correction and acceptance of proposals f0 (fp32 [m, 32]); stencils of
+        the n-particle cloud as from solve_weights, plus the accepted count."""
+        m = int(slots.shape[0])
+        dev = x.device
+        W = STENCIL_W
+        cols = torch.full((max(n, 1) * W,), -1, dtype=torch.int32, device=dev)
+        f = torch.zeros(max(n, 1) * W, dtype=torch.float64, device=dev)
+        fii = torch.zeros(max(n, 1), dtype=torch.float64, device=dev)
+        status = torch.zeros(max(n, 1), dtype=torch.uint8, device=dev)
+        acc = ctypes.c_int32(0)
+        self._check(self.lib.vrm_learned_project(
+            self.ctx, _ptr(x, torch.float64, "x"), _ptr(y, torch.float64, "y"),
+            _ptr(list_, torch.int32, "list", m) if list_ is not None else None, m,
+            _ptr(slots.contiguous(), torch.int32, "slots", 32 * m), _ptr(f0.contiguous(), torch.float32, "f0", 32 * m),
+            _ptr(cols, torch.int32, "cols"), _ptr(f, torch.float64, "f"), _ptr(fii, torch.float64, "fii"),
+            _ptr(status, torch.uint8, "status"), ctypes.byref(acc), _stream()), "vrm_learned_project")
+        return dict(cols=cols, f=f, fii=fii, status=status), acc.value
+
     def get_schedule(self):
         s = Schedule()
         self._check(self.lib.vrm_get_schedule(self.ctx, ctypes.byref(s)), "vrm_get_schedule")
@@ -469,4 +512,18 @@ class MLP:
 
     def check(self):
         self._check(self.lib.vrm_mlp_error(self.net, _stream()), "vrm_mlp_error")
+
+
+def learned_targets(list_, slots, cols, f):
+    """Training targets fp32 [m, 32]: each listed particle's stencil weight at
+    each slot's particle."""
+    lib = _lib_handle()
+    m = int(list_.numel())
+    T = torch.empty(max(m, 1), MLP_OUT, dtype=torch.float32, device=list_.device)
+    st = lib.vrm_learned_targets(_ptr(list_, torch.int32, "list", m), m, _ptr(slots, torch.int32, "slots", 32 * m),
+                                 _ptr(cols, torch.int32, "cols"), _ptr(f, torch.float64, "f"),
+                                 _ptr(T, torch.float32, "T"), _stream())
+    if st != VRM_OK:
+        raise VRMError(st, "vrm_learned_targets")
+    return T[:m]
 

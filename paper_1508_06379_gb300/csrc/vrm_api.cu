@@ -16,8 +16,19 @@
 #include <new>
 
 #include "vrm_internal.cuh"
+#include "vrm_mlp.cuh"
 
 using namespace vrm;
+
+// Buffers of the learned proposal (vrm_set_mlp): input rows, slot map,
+// proposals, rejected list, network activations.
+struct Learned {
+  int cap = 0;
+  MlpActs acts;
+  int* slots = nullptr;
+  float* Y = nullptr;
+  int* rlist = nullptr;
+};
 
 struct vrm::Scratch {
   int cap = 0;        // particles the buffers hold
@@ -78,6 +89,9 @@ struct vrm_ctx {
   int use_graph = 1;
   StepGraph graph;
   cudaStream_t cap_stream = nullptr, body_stream = nullptr;
+  // learned proposal
+  vrm_mlp* mlp = nullptr;
+  Learned L;
 };
 
 // What a batch graph was captured for: per cloud the buffers, capacity and
@@ -132,6 +146,54 @@ void free_scratch(Scratch& s) {
     if (p) cudaFreeHost(p);
   Scratch empty;
   s = empty;
+}
+
+void free_learned(Learned& L) {
+  mlp_acts_free(&L.acts);
+  if (L.slots) cudaFree(L.slots);
+  if (L.Y) cudaFree(L.Y);
+  if (L.rlist) cudaFree(L.rlist);
+  L = Learned{};
+}
+
+// Buffers of the learned proposal for `cap` particles (only with a network).
+cudaError_t ensure_learned(vrm_ctx* ctx, int cap, cudaStream_t st) {
+  Learned& L = ctx->L;
+  if (!ctx->mlp || (cap <= L.cap && L.slots)) return cudaSuccess;
+  cudaStreamSynchronize(st);
+  drop_graph(ctx);
+  ++ctx->scratch_gen;
+  free_learned(L);
+  const int n = cap < 128 ? 128 : cap;
+  cudaError_t e = mlp_acts_alloc(&L.acts, n, true);
+  if (e == cudaSuccess) e = cudaMalloc(&L.slots, sizeof(int) * (size_t)n * 32);
+  if (e == cudaSuccess) e = cudaMalloc(&L.Y, sizeof(float) * (size_t)L.acts.rows_pad * 32);
+  if (e == cudaSuccess) e = cudaMalloc(&L.rlist, sizeof(int) * (size_t)n);
+  if (e != cudaSuccess) {
+    free_learned(L);
+    cudaGetLastError();
+    return e;
+  }
+  L.cap = n;
+  return cudaSuccess;
+}
+
+// Learned proposal for the listed particles, then the LP for the rejected
+// ones (their list and count in L.rlist, counters[2]).
+cudaError_t enqueue_learned(vrm_ctx* ctx, const double* x, const double* y, const int* list, const int* list_count,
+                            int cap, const int* nbr_count, const int* nbr_idx, int* cols, double* f, double* fii,
+                            uint8_t* status, const double* dt_dev, cudaStream_t st) {
+  Scratch& s = ctx->s;
+  Learned& L = ctx->L;
+  const Consts& c = ctx->c;
+  cudaError_t e;
+  if ((e = learned_features(c, x, y, list, list_count, cap, nbr_count, nbr_idx, L.acts.X, L.slots, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = mlp_forward(ctx->mlp, L.acts.mX, L.acts, cap, list_count, L.Y, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(s.counters + 2, 0, sizeof(int), st)) != cudaSuccess) return e;
+  return learned_project(c, x, y, list, list_count, cap, L.slots, L.Y, cols, f, fii, status, L.rlist, s.counters + 2,
+                         s.ds, dt_dev, ctx->p.nu, st);
 }
 
 // Scratch for `cap` particles (grown by 25% steps, never shrunk).
@@ -377,8 +439,17 @@ cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const doub
                           s.nbr_idx, s.seg_mask, s.small, s.ds, st)) != cudaSuccess)
     return e;
   if ((e = mark(ctx, VRM_STAGE_LP_SMALL, st)) != cudaSuccess) return e;
-  if ((e = lp_small(c, x, y, s.dlist, s.counters + 0, cap, s.small, s.cols, s.f, s.fii, s.status, s.fail_list, s.ds,
-                    0.0, st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
+  const int* lp_list = s.dlist;
+  const int* lp_count = s.counters + 0;
+  if (ctx->mlp) {
+    if ((e = enqueue_learned(ctx, x, y, s.dlist, s.counters + 0, cap, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii,
+                             s.status, &s.st->dt, st)) != cudaSuccess)
+      return e;
+    lp_list = ctx->L.rlist;
+    lp_count = s.counters + 2;
+  }
+  if ((e = lp_small(c, x, y, lp_list, lp_count, cap, s.small, s.cols, s.f, s.fii, s.status, s.fail_list, s.ds, 0.0,
+                    st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
     return e;
   if ((e = mark(ctx, VRM_STAGE_LP_FULL, st)) != cudaSuccess) return e;
   if ((e = lp_full(c, x, y, s.fail_list, &s.ds->n_fail, cap, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii, s.status,
@@ -583,6 +654,7 @@ void vrm_destroy(vrm_ctx* ctx) {
   if (!ctx) return;
   drop_graph(ctx);
   free_scratch(ctx->s);
+  free_learned(ctx->L);
   if (ctx->events_ready)
     for (int k = 0; k <= VRM_STAGE_COUNT; ++k) cudaEventDestroy(ctx->ev[k]);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -692,10 +764,22 @@ vrm_status vrm_solve_weights(vrm_ctx* ctx, const double* x, const double* y, int
   const Consts c = full_rows(ctx->c);
   VRM_CUDA(ensure_scratch(ctx, n, stream));
   VRM_CUDA(cudaMemsetAsync(s.ds, 0, sizeof(DevStats), stream));
+  VRM_CUDA(ensure_learned(ctx, n, stream));
   VRM_CUDA(compact_flags(diffused, n, s.dlist, s.counters + 0, s.pos, s.scan_tmp, stream));
   VRM_CUDA(lp_clear(n, diffused, cols, f, fii, status, stream));
-  VRM_CUDA(lp_small(c, x, y, s.dlist, s.counters + 0, n, small, cols, f, fii, status, s.fail_list, s.ds, 0.0,
-                    stream));
+  const int* lp_list = s.dlist;
+  const int* lp_count = s.counters + 0;
+  if (ctx->mlp) {
+    const Consts keep = ctx->c;
+    ctx->c = c;  // whole rows
+    const cudaError_t le = enqueue_learned(ctx, x, y, s.dlist, s.counters + 0, n, nbr_count, nbr_idx, cols, f, fii,
+                                           status, nullptr, stream);
+    ctx->c = keep;
+    VRM_CUDA(le);
+    lp_list = ctx->L.rlist;
+    lp_count = s.counters + 2;
+  }
+  VRM_CUDA(lp_small(c, x, y, lp_list, lp_count, n, small, cols, f, fii, status, s.fail_list, s.ds, 0.0, stream));
   VRM_CUDA(lp_full(c, x, y, s.fail_list, &s.ds->n_fail, n, nbr_count, nbr_idx, cols, f, fii, status, s.ds, 0.0,
                    stream));
   if (stats) {
@@ -710,7 +794,57 @@ vrm_status vrm_solve_weights(vrm_ctx* ctx, const double* x, const double* y, int
     stats->lp_small_pivots = (int64_t)s.h_ds->lp_small_pivots;
     stats->lp_full_solved = s.h_ds->lp_full_solved;
     stats->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
+    stats->learned_ok = s.h_ds->learned_ok;
+    stats->learned_rejected = s.h_ds->learned_rejected;
   }
+  if (ctx->mlp && vrm_mlp_error(ctx->mlp, stream) != VRM_OK) return VRM_ERR_CUDA;
+  return VRM_OK;
+}
+
+vrm_status vrm_set_mlp(vrm_ctx* ctx, vrm_mlp* net) {
+  if (!ctx) return VRM_ERR_ARG;
+  if (ctx->mlp != net) {
+    ctx->mlp = net;
+    drop_graph(ctx);
+    ++ctx->scratch_gen;
+  }
+  return VRM_OK;
+}
+
+vrm_status vrm_learned_features(vrm_ctx* ctx, const double* x, const double* y, const int32_t* list, int32_t m,
+                                const int32_t* nbr_count, const int32_t* nbr_idx, uint16_t* X, int32_t* slots,
+                                cudaStream_t stream) {
+  if (!ctx || m < 0) return VRM_ERR_ARG;
+  if (m == 0) return VRM_OK;
+  if (!x || !y || !nbr_count || !nbr_idx || !X || !slots || misaligned16(X)) return VRM_ERR_ARG;
+  VRM_CUDA(learned_features(full_rows(ctx->c), x, y, list, nullptr, m, nbr_count, nbr_idx,
+                            reinterpret_cast<__nv_bfloat16*>(X), slots, stream));
+  return VRM_OK;
+}
+
+vrm_status vrm_learned_project(vrm_ctx* ctx, const double* x, const double* y, const int32_t* list, int32_t m,
+                               const int32_t* slots, const float* f0, int32_t* cols, double* f, double* fii,
+                               uint8_t* status, int32_t* n_accepted, cudaStream_t stream) {
+  if (!ctx || m < 0) return VRM_ERR_ARG;
+  if (n_accepted) *n_accepted = 0;
+  if (m == 0) return VRM_OK;
+  if (!x || !y || !slots || !f0 || !cols || !f || !fii || !status) return VRM_ERR_ARG;
+  Scratch& s = ctx->s;
+  VRM_CUDA(ensure_scratch(ctx, m, stream));
+  VRM_CUDA(cudaMemsetAsync(s.ds, 0, sizeof(DevStats), stream));
+  VRM_CUDA(learned_project(ctx->c, x, y, list, nullptr, m, slots, f0, cols, f, fii, status, nullptr, nullptr, s.ds,
+                           nullptr, ctx->p.nu, stream));
+  VRM_CUDA(read_back(ctx, stream));
+  if (n_accepted) *n_accepted = s.h_ds->learned_ok;
+  return VRM_OK;
+}
+
+vrm_status vrm_learned_targets(const int32_t* list, int32_t m, const int32_t* slots, const int32_t* cols,
+                               const double* f, float* T, cudaStream_t stream) {
+  if (m < 0) return VRM_ERR_ARG;
+  if (m == 0) return VRM_OK;
+  if (!list || !slots || !cols || !f || !T) return VRM_ERR_ARG;
+  VRM_CUDA(learned_targets(list, m, slots, cols, f, T, stream));
   return VRM_OK;
 }
 
@@ -741,6 +875,7 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
   }
   Scratch& s = ctx->s;
   VRM_CUDA(ensure_scratch(ctx, capacity, stream));
+  VRM_CUDA(ensure_learned(ctx, capacity, stream));
   // the pinned parameter block is read by the step's head copy: wait for any
   // earlier step on this stream before rewriting it
   VRM_CUDA(cudaStreamSynchronize(stream));
@@ -782,6 +917,7 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
     ctx->c.row_cap = ctx->p.k_cap;
     drop_graph(ctx);
   }
+  if (ctx->mlp && vrm_mlp_error(ctx->mlp, stream) != VRM_OK) return VRM_ERR_CUDA;
   if (s.h_grid->nonfinite || s.h_ds->nonfinite) return VRM_ERR_ARG;
   fill_front_stats(ctx, n, st);
   st->small_ok = s.h_ds->small_ok;
@@ -794,6 +930,8 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
   st->lp_small_pivots = (int64_t)s.h_ds->lp_small_pivots;
   st->lp_full_solved = s.h_ds->lp_full_solved;
   st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
+  st->learned_ok = s.h_ds->learned_ok;
+  st->learned_rejected = s.h_ds->learned_rejected;
   if (s.h_state->overflow) return VRM_ERR_CAPACITY;
   *n_out = s.h_state->n_cur;
   if (s.h_ds->max_count > ctx->p.k_cap) return VRM_ERR_CAPACITY;
@@ -949,6 +1087,8 @@ vrm_status finish_cloud(vrm_ctx* ctx, vrm_cloud& C, vrm_stats* st) {
   st->lp_small_pivots = (int64_t)s.h_ds->lp_small_pivots;
   st->lp_full_solved = s.h_ds->lp_full_solved;
   st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
+  st->learned_ok = s.h_ds->learned_ok;
+  st->learned_rejected = s.h_ds->learned_rejected;
   C.n_out = st->n_out;
   if (s.h_state->overflow) return VRM_ERR_CAPACITY;
   if (s.h_ds->max_count > ctx->p.k_cap) return VRM_ERR_CAPACITY;
@@ -972,6 +1112,8 @@ void add_stats(vrm_stats* t, const vrm_stats& a) {
   t->lp_small_pivots += a.lp_small_pivots;
   t->lp_full_solved += a.lp_full_solved;
   t->lp_full_pivots += a.lp_full_pivots;
+  t->learned_ok += a.learned_ok;
+  t->learned_rejected += a.learned_rejected;
 }
 
 }  // namespace

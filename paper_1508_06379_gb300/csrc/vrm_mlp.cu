@@ -25,6 +25,7 @@
 #include <new>
 
 #include "vrm_internal.cuh"
+#include "vrm_mlp.cuh"
 #include "vrm_umma.cuh"
 
 using namespace vrm;
@@ -463,65 +464,67 @@ struct vrm_mlp {
   bf16 *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *H1t = nullptr, *H2t = nullptr, *H3t = nullptr;
   bf16 *dY = nullptr, *dYt = nullptr;
   bf16 *dZ1 = nullptr, *dZ2 = nullptr, *dZ3 = nullptr, *dZ1t = nullptr, *dZ2t = nullptr, *dZ3t = nullptr;
-  // inference activations
-  int inf_rows = 0;
-  bf16 *Ha = nullptr, *Hb = nullptr;
+  vrm::MlpActs acts;  // activations of vrm_mlp_forward
   CUtensorMap mW1, mW2, mW3, mW4, mW2t, mW3t, mW4t;  // weights as B operands
   CUtensorMap mX, mXt, mH1, mH2, mH3, mH1t, mH2t, mH3t, mdY, mdYt, mdZ1t, mdZ2, mdZ2t, mdZ3, mdZ3t;
-  CUtensorMap mHa, mHb;
 };
 
 namespace vrm {
 
-// Forward pass of `rows` rows (bound; *rows_dev if given) of X (bf16
-// [rows_pad x 128], rows_pad = rows rounded up to 128, 16-byte aligned) into
-// Y (fp32 [rows x 32]).
-cudaError_t mlp_forward(vrm_mlp* net, const bf16* X, int rows, const int* rows_dev, float* Y, cudaStream_t s);
-cudaError_t mlp_reserve(vrm_mlp* net, int rows);
-
-cudaError_t mlp_reserve(vrm_mlp* net, int rows) {
+cudaError_t mlp_acts_alloc(MlpActs* a, int rows, bool with_x) {
+  mlp_acts_free(a);
   const int rp = (rows + kBM - 1) / kBM * kBM;
-  if (rp <= net->inf_rows) return cudaSuccess;
-  if (net->Ha) cudaFree(net->Ha);
-  if (net->Hb) cudaFree(net->Hb);
-  net->Ha = net->Hb = nullptr;
-  net->inf_rows = 0;
-  cudaError_t e = cudaMalloc(&net->Ha, (size_t)rp * kHid * sizeof(bf16));
-  if (e == cudaSuccess) e = cudaMalloc(&net->Hb, (size_t)rp * kHid * sizeof(bf16));
-  if (e != cudaSuccess) return e;
-  if (!make_map(&net->mHa, net->Ha, rp, kHid, kBM) || !make_map(&net->mHb, net->Hb, rp, kHid, kBM))
+  cudaError_t e = cudaMalloc(&a->Ha, (size_t)rp * kHid * sizeof(bf16));
+  if (e == cudaSuccess) e = cudaMalloc(&a->Hb, (size_t)rp * kHid * sizeof(bf16));
+  if (e == cudaSuccess && with_x) e = cudaMalloc(&a->X, (size_t)rp * kInPad * sizeof(bf16));
+  if (e != cudaSuccess) {
+    mlp_acts_free(a);
+    return e;
+  }
+  if (!make_map(&a->mHa, a->Ha, rp, kHid, kBM) || !make_map(&a->mHb, a->Hb, rp, kHid, kBM) ||
+      (with_x && !make_map(&a->mX, a->X, rp, kInPad, kBM))) {
+    mlp_acts_free(a);
     return cudaErrorInvalidValue;
-  net->inf_rows = rp;
+  }
+  a->rows_pad = rp;
   return cudaSuccess;
 }
 
-cudaError_t mlp_forward(vrm_mlp* net, const bf16* X, int rows, const int* rows_dev, float* Y, cudaStream_t s) {
+void mlp_acts_free(MlpActs* a) {
+  if (a->X) cudaFree(a->X);
+  if (a->Ha) cudaFree(a->Ha);
+  if (a->Hb) cudaFree(a->Hb);
+  a->X = a->Ha = a->Hb = nullptr;
+  a->rows_pad = 0;
+}
+
+bool mlp_input_map(CUtensorMap* m, const bf16* X, int rows_pad) { return make_map(m, X, rows_pad, kInPad, kBM); }
+
+cudaError_t mlp_forward(vrm_mlp* net, const CUtensorMap& mX, const MlpActs& a, int rows, const int* rows_dev,
+                        float* Y, cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
-  const int rp = (rows + kBM - 1) / kBM * kBM;
-  if (rp > net->inf_rows) return cudaErrorInvalidValue;  // mlp_reserve first (not while capturing)
-  CUtensorMap mXin;
-  if (!make_map(&mXin, X, rp, kInPad, kBM)) return cudaErrorInvalidValue;
+  if ((rows + kBM - 1) / kBM * kBM > a.rows_pad) return cudaErrorInvalidValue;
   cudaError_t r;
   Epi e = epi(EPI_BIAS_GELU, rows, kHid);
   e.m_dev = rows_dev;
   e.error = net->err;
   e.bias = net->theta + kOffB1;
-  e.out_bf16 = net->Ha;
+  e.out_bf16 = a.Ha;
   e.ld_bf16 = kHid;
-  if ((r = gemm(mXin, net->mW1, 256, rows, kHid, kInPad, 1, e, s)) != cudaSuccess) return r;
+  if ((r = gemm(mX, net->mW1, 256, rows, kHid, kInPad, 1, e, s)) != cudaSuccess) return r;
   e.bias = net->theta + kOffB2;
-  e.out_bf16 = net->Hb;
-  if ((r = gemm(net->mHa, net->mW2, 256, rows, kHid, kHid, 1, e, s)) != cudaSuccess) return r;
+  e.out_bf16 = a.Hb;
+  if ((r = gemm(a.mHa, net->mW2, 256, rows, kHid, kHid, 1, e, s)) != cudaSuccess) return r;
   e.bias = net->theta + kOffB3;
-  e.out_bf16 = net->Ha;
-  if ((r = gemm(net->mHb, net->mW3, 256, rows, kHid, kHid, 1, e, s)) != cudaSuccess) return r;
+  e.out_bf16 = a.Ha;
+  if ((r = gemm(a.mHb, net->mW3, 256, rows, kHid, kHid, 1, e, s)) != cudaSuccess) return r;
   Epi f = epi(EPI_BIAS_F32, rows, kOut);
   f.m_dev = rows_dev;
   f.error = net->err;
   f.bias = net->theta + kOffB4;
   f.out_f32 = Y;
   f.ld_f32 = kOut;
-  return gemm(net->mHa, net->mW4, 32, rows, kOut, kHid, 1, f, s);
+  return gemm(a.mHa, net->mW4, 32, rows, kOut, kHid, 1, f, s);
 }
 
 }  // namespace vrm
@@ -531,9 +534,10 @@ namespace {
 void free_mlp(vrm_mlp* n) {
   void* ptrs[] = {n->err, n->theta, n->m, n->v, n->grad, n->part, n->loss, n->W1, n->W2, n->W3, n->W4, n->W2t,
                   n->W3t, n->W4t, n->Xb, n->Xbt, n->Tb, n->Z1, n->Z2, n->Z3, n->Y, n->H1, n->H2, n->H3, n->H1t,
-                  n->H2t, n->H3t, n->dY, n->dYt, n->dZ1, n->dZ2, n->dZ3, n->dZ1t, n->dZ2t, n->dZ3t, n->Ha, n->Hb};
+                  n->H2t, n->H3t, n->dY, n->dYt, n->dZ1, n->dZ2, n->dZ3, n->dZ1t, n->dZ2t, n->dZ3t};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  vrm::mlp_acts_free(&n->acts);
 }
 
 template <typename T>
@@ -759,8 +763,14 @@ vrm_status vrm_mlp_get_params(const vrm_mlp* n, float* theta, cudaStream_t s) {
 vrm_status vrm_mlp_forward(vrm_mlp* n, const uint16_t* X, int32_t rows, float* Y, cudaStream_t s) {
   if (!n || rows < 0 || (rows > 0 && (!X || !Y)) || ((uintptr_t)X & 15u)) return VRM_ERR_ARG;
   if (rows == 0) return VRM_OK;
-  if (mlp_reserve(n, rows) != cudaSuccess) return VRM_ERR_CUDA;
-  if (mlp_forward(n, reinterpret_cast<const bf16*>(X), rows, nullptr, Y, s) != cudaSuccess) return VRM_ERR_CUDA;
+  const int rp = (rows + kBM - 1) / kBM * kBM;
+  if (rp > n->acts.rows_pad) {
+    if (cudaStreamSynchronize(s) != cudaSuccess) return VRM_ERR_CUDA;
+    if (vrm::mlp_acts_alloc(&n->acts, rows, false) != cudaSuccess) return VRM_ERR_CUDA;
+  }
+  CUtensorMap mX;
+  if (!vrm::mlp_input_map(&mX, reinterpret_cast<const bf16*>(X), rp)) return VRM_ERR_ARG;
+  if (vrm::mlp_forward(n, mX, n->acts, rows, nullptr, Y, s) != cudaSuccess) return VRM_ERR_CUDA;
   return check_err(n, s);
 }
 

@@ -1,0 +1,41 @@
+// Inference side of the weight-proposal network (vrm_mlp.cu) as used by the
+// step (vrm_api.cu): activation buffers with their tensor maps, owned by the
+// caller so that a captured graph keeps valid pointers.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "vrm_internal.cuh"
+
+namespace vrm {
+
+struct MlpActs {
+  int rows_pad = 0;                // rows the buffers hold (multiple of 128)
+  __nv_bfloat16* X = nullptr;      // input rows [rows_pad x 128] (if owned)
+  __nv_bfloat16* Ha = nullptr;     // hidden activations [rows_pad x 256]
+  __nv_bfloat16* Hb = nullptr;
+  CUtensorMap mX, mHa, mHb;
+};
+
+// Buffers for `rows` rows (rounded up to 128); with_x also allocates X.
+cudaError_t mlp_acts_alloc(MlpActs* a, int rows, bool with_x);
+void mlp_acts_free(MlpActs* a);
+// Tensor map of caller-owned input rows X [rows_pad x 128].
+bool mlp_input_map(CUtensorMap* m, const __nv_bfloat16* X, int rows_pad);
+// Y[rows x 32] = network(X) for rows_bound rows (or *rows_dev <= rows_bound).
+cudaError_t mlp_forward(vrm_mlp* net, const CUtensorMap& mX, const MlpActs& a, int rows_bound, const int* rows_dev,
+                        float* Y, cudaStream_t s);
+
+// vrm_learned.cu
+cudaError_t learned_features(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
+                             int m_bound, const int* nbr_count, const int* nbr_idx, __nv_bfloat16* X, int* slots,
+                             cudaStream_t s);
+cudaError_t learned_project(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
+                            int m_bound, const int* slots, const float* f0, int* cols, double* f, double* fii,
+                            uint8_t* status, int* reject_list, int* reject_count, DevStats* ds, const double* dt_dev,
+                            double nu, cudaStream_t s);
+cudaError_t learned_targets(const int* list, int m, const int* slots, const int* cols, const double* f, float* T,
+                            cudaStream_t s);
+
+}  // namespace vrm

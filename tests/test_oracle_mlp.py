@@ -193,3 +193,38 @@ def test_learned_stencil_accepts_valid_and_rejects_negative():
     f0[:8] = [1, 0, 1, 0, 1, 0, 1, 0]
     ok, _, _, _ = mlp.learned_stencil(x, y, h, 0, slots, f0)
     assert not ok
+
+
+def test_support_refinement_reaches_a_vertex():
+    # unit lattice neighbours; the proposal puts weight on all 8 with the
+    # diagonals too heavy: the first correction turns some weight negative,
+    # dropping slots down to five neighbours gives a valid vertex stencil
+    h = 1.0
+    off = [(1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1)]
+    x = np.array([0.0] + [a for a, _ in off])
+    y = np.array([0.0] + [b for _, b in off])
+    slots = np.full(32, -1)
+    slots[:8] = np.arange(1, 9)
+    f0 = np.zeros(32, dtype=np.float32)
+    f0[:8] = [0.9, 0.05, 1.0, 0.02, 1.1, 0.03, 0.95, 0.04]
+    S0 = mlp.support(f0, slots)
+    xi = x[slots[S0]]
+    eta = y[slots[S0]]
+    f_first, _ = mlp.project(xi, eta, f0[S0].astype(np.float64))
+    ok, js, f, fii = mlp.learned_stencil(x, y, h, 0, slots, f0)
+    assert ok and 5 <= len(js) <= 8 and np.all(f >= 0)
+    V = mlp.vandermonde(x[js], y[js])
+    assert np.max(np.abs(V @ f - mlp.B_RHS)) <= 1e-12
+    # with five neighbours the stencil is the unique solution on them
+    if len(js) == 5:
+        assert np.allclose(f, np.linalg.solve(V, mlp.B_RHS), rtol=0, atol=1e-13)
+    # nearly dependent rows (four neighbours on one line plus one) reject
+    xl = np.array([0.0, 1.0, 2.0, -1.0, -2.0, 0.0])
+    yl = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 1.0])
+    sl = np.full(32, -1)
+    sl[:5] = np.arange(1, 6)
+    f0l = np.zeros(32, dtype=np.float32)
+    f0l[:5] = 1.0
+    ok, _, _, _ = mlp.learned_stencil(xl, yl, 1.0, 0, sl, f0l)
+    assert not ok
+    assert not mlp.gram_ok(mlp.vandermonde(xl[1:], yl[1:]))
