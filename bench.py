@@ -46,7 +46,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mixture_1m", choices=["mixture_1m", "lamb_oseen_h002", "batched_64"])
+    ap.add_argument("--workload", default="mixture_1m",
+                    choices=["mixture_1m", "lamb_oseen_h002", "batched_64", "learned_4m"])
+    ap.add_argument("--train-rows", type=int, default=10_000_000,
+                    help="LP solutions the network of the learned workload is trained on")
+    ap.add_argument("--train-epochs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
     ap.add_argument("--schedule-cache", default=None,
@@ -593,12 +597,106 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
+LEARNED_DESC = ("jittered lattice 2001x2001 (h=1e-3 on [-1,1]^2, jitter 0.3h), 8-Gaussian mixture, nu=1e-3, "
+                "C_diff=1, insertion on; stencils from the trained network (corrected, LP fallback) vs the LP alone")
+
+
+def run_learned(args):
+    """The 4M-particle cloud stepped with the learned proposal and with the LP
+    alone: throughput of both, acceptance, and how far the two results are
+    apart (both are valid discretisations; the learned stencils meet the
+    moment conditions to 1e-12)."""
+    import numpy as np
+    import torch
+
+    import paper_1508_06379_gb300 as vrm
+    import vrm_inputs
+    from paper_1508_06379_gb300 import learn
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    vrm.build()
+    dev = torch.device("cuda", local)
+    t0 = time.time()
+    X, T, N = learn.make_dataset(args.train_rows)
+    t_data = time.time() - t0
+    t0 = time.time()
+    net, losses = learn.train(X, T, N, epochs=args.train_epochs, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    del X, T
+    h, nu = 1e-3, 1e-3
+    x, y, g = vrm_inputs.gaussian_mixture_cloud(h=h, side=2001, jitter=0.3, seed=vrm_inputs.SEED_BASE + 4,
+                                                half_width=1.0)
+    dt = (0.5 * h) ** 2 / (4 * nu) / 8
+    n = len(x)
+    cap = int(n * 1.6) + 4096
+    xb = torch.zeros(cap, dtype=torch.float64, device=dev)
+    yb = torch.zeros(cap, dtype=torch.float64, device=dev)
+    xb[:n] = torch.from_numpy(x).to(dev)
+    yb[:n] = torch.from_numpy(y).to(dev)
+    gi = torch.from_numpy(g).to(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name in ("lp", "learned"):
+        ctx = vrm.VRM(h=h, nu=nu)
+        if name == "learned":
+            ctx.set_mlp(net)
+        ctx.set_timing(True)
+        go = torch.zeros(cap, dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            ctx.step(xb, yb, n, gi, go, dt)
+        ms, parts, stage = 0.0, 0, {}
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            n2, st = ctx.step(xb, yb, n, gi, go, dt)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            parts += n2
+            for k, v in ctx.stage_times().items():
+                stage.setdefault(k, []).append(v)
+        out[name] = dict(value=parts / (ms * 1e-3), ms=ms / args.steps, stats=st, n2=n2, gamma=go[:n2].clone(),
+                         stage={k: round(sum(v) / len(v), 4) for k, v in stage.items()})
+    a, b = out["lp"], out["learned"]
+    g0 = torch.zeros(a["n2"], dtype=torch.float64, device=dev)
+    g0[:n] = gi
+    inc_lp = a["gamma"] - g0
+    inc_le = b["gamma"] - g0
+    rel = float(torch.linalg.norm(inc_le - inc_lp) / torch.linalg.norm(inc_lp))
+    st = b["stats"]
+    line = {
+        "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": b["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (network bf16/fp32)", "data": "synthetic",
+        "config": {"workload": LEARNED_DESC, "n": n, "n_out": int(b["n2"]), "n_diffused": int(st["n_diffused"]),
+                   "h": h, "nu": nu, "dt": dt, "l2": "flushed between steps (512 MB write)",
+                   "train_rows": int(N), "train_epochs": args.train_epochs, "train_loss_first_last":
+                   [losses[0][1], losses[-1][1]], "data_s": round(t_data, 2), "train_s": round(t_train, 2)},
+        "plain_lp": {"value": a["value"], "unit": UNIT, "ms_per_step": a["ms"], "stage_ms": a["stage"]},
+        "learned": {"accepted": int(st["learned_ok"]), "rejected": int(st["learned_rejected"]),
+                    "accepted_on_five_slot_basis": int(st["learned_square"]),
+                    "acceptance": st["learned_ok"] / max(1, st["n_diffused"]),
+                    "lp_small_solved": int(st["lp_small_solved"]), "stage_ms": b["stage"],
+                    "increment_rel_diff_vs_lp": rel},
+        "speedup_vs_plain": b["value"] / a["value"],
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched_64":
         run_batched(args)
+    elif args.workload == "learned_4m":
+        run_learned(args)
     else:
         run_ours(args)
 

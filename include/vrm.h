@@ -110,6 +110,7 @@ typedef struct vrm_stats {
   int64_t lp_full_pivots;  /* pivots summed over those LPs */
   int64_t learned_ok;      /* stencils from the learned proposal (vrm_set_mlp) */
   int64_t learned_rejected; /* proposals rejected (then solved by the LP) */
+  int64_t learned_square;  /* of learned_ok: accepted on the network's five-slot basis alone */
 } vrm_stats;
 
 /* Stages of vrm_step, for vrm_stage_times. */

@@ -13,7 +13,8 @@ and signs; everything else goes to the LP.  The pieces:
 * features(): the neighbourhood N_i (annulus of Eq. neighbourhood) as K = 32
   slots ordered by (45-degree segment of Sec. 4.2, squared distance, index),
   with the scaled offsets xi = (x_j - x_i)/h of Eq. momcondmv and a mask;
-  input row [xi_x(32), xi_y(32), mask(32)].
+  input row [xi_x(32), xi_y(32), mask(32)].  The order and xi are float32
+  quantities (the network's input precision); only x_j - x_i is FP64.
 * forward()/backward(): the network 96 -> 256 -> 256 -> 256 -> 32 with GELU
   (the erf form) after each hidden layer; W_l is [out x in].
 * loss(): mean squared error over the valid slots against the LP weights
@@ -30,6 +31,11 @@ and signs; everything else goes to the LP.  The pieces:
   is corrected again on the smaller support; at |S| = 5 the correction is the
   unique solution on those five neighbours.  A Gram matrix V_S V_S^T whose
   Cholesky pivot falls to 1e-10 of its largest diagonal entry rejects.
+  Before all that, the five slots with the largest proposals are tried alone:
+  the square system V_5 f = b (Gaussian elimination with partial pivoting,
+  a pivot at most 1e-12 of the largest |entry| counts as singular) gives the
+  vertex stencil on the network's choice of basis, accepted under the same
+  test; only if it fails does the least-change path above run.
 """
 import numpy as np
 
@@ -97,23 +103,27 @@ def segment(dx, dy):
 
 
 def features(x, y, h, i, row):
-    """Input row (float32 values, then rounded to bf16 as the network reads
-    them) and slot -> particle map (-1 = empty) of particle i whose
-    neighbourhood is `row` (indices, any order)."""
-    inv_h = 1.0 / h
+    """Input row (bf16 values) and slot -> particle map (-1 = empty) of
+    particle i whose neighbourhood is `row` (indices, any order).  The offset
+    dx = x_j - x_i is one FP64 subtraction, then rounded to float32; the slot
+    order key (segment, squared distance, index) and xi = dx * (1/h) are
+    float32 computations on those rounded offsets (products and sums rounded
+    separately, 1/h computed in FP64 and rounded to float32)."""
+    f32 = np.float32
+    inv_h = f32(1.0 / h)
     ent = []
     for j in row:
         j = int(j)
-        dx = x[j] - x[i]
-        dy = y[j] - y[i]
-        d2 = dx * dx + dy * dy
+        dx = f32(x[j] - x[i])
+        dy = f32(y[j] - y[i])
+        d2 = f32(f32(dx * dx) + f32(dy * dy))
         ent.append((segment(dx, dy), d2, j, dx, dy))
     ent.sort(key=lambda e: (e[0], e[1], e[2]))
     X = np.zeros(N_IN)
     slots = np.full(K_SLOTS, -1, dtype=np.int64)
     for k, (_, _, j, dx, dy) in enumerate(ent[:K_SLOTS]):
-        X[k] = np.float32(dx * inv_h)
-        X[K_SLOTS + k] = np.float32(dy * inv_h)
+        X[k] = f32(dx * inv_h)
+        X[K_SLOTS + k] = f32(dy * inv_h)
         X[2 * K_SLOTS + k] = 1.0
         slots[k] = j
     return to_bf16(X), slots
@@ -228,20 +238,59 @@ def gram_ok(V, rel=1e-10):
 MAX_DROPS = 3
 
 
+def square_solve(V, b, rel=1e-12):
+    """Solution of the 5 x 5 system V f = b by Gaussian elimination with
+    partial pivoting (first largest |pivot| in the column, full row swaps),
+    or None when a pivot is at most rel times the largest |entry| of V."""
+    A = np.array(V, dtype=np.float64)
+    r = np.array(b, dtype=np.float64)
+    n = A.shape[0]
+    vmax = float(np.max(np.abs(A)))
+    for k in range(n):
+        p = k + int(np.argmax(np.abs(A[k:, k])))
+        if not abs(A[p, k]) > rel * vmax:
+            return None
+        if p != k:
+            A[[k, p]] = A[[p, k]]
+            r[[k, p]] = r[[p, k]]
+        for q in range(k + 1, n):
+            m = A[q, k] / A[k, k]
+            A[q, k:] = A[q, k:] - m * A[k, k:]
+            r[q] = r[q] - m * r[k]
+    f = np.zeros(n)
+    for k in range(n - 1, -1, -1):
+        f[k] = (r[k] - float(np.dot(A[k, k + 1:], f[k + 1:]))) / A[k, k]
+    return f
+
+
 def learned_stencil(x, y, h, i, slots, f0):
     """The learned stencil of particle i from its slot map and proposal:
     (accepted, particle indices, f~ in slot order, f~_ii)."""
-    S = support(f0, slots)
     p32 = np.asarray(f0, dtype=np.float32)
     inv_h = 1.0 / h
+
+    def offsets(S):
+        js = [int(slots[k]) for k in S]
+        xi = np.array([(x[j] - x[i]) * inv_h for j in js])
+        eta = np.array([(y[j] - y[i]) * inv_h for j in js])
+        return js, xi, eta
+
+    # the network's basis alone: the square system on the top five slots
+    S5 = support(f0, slots, cap=5)
+    if len(S5) == 5:
+        js, xi, eta = offsets(S5)
+        V = vandermonde(xi, eta)
+        f = square_solve(V, B_RHS)
+        if f is not None and np.all(f >= 0.0) and float(np.max(np.abs(V @ f - B_RHS))) <= ACCEPT_RESID:
+            return True, js, f, -float(np.sum(f))
+    # least change on up to eight slots, dropping the most negative
+    S = support(f0, slots)
     f = None
     js = []
     for _ in range(MAX_DROPS + 1):
         if len(S) < 5:
             break
-        js = [int(slots[k]) for k in S]
-        xi = np.array([(x[j] - x[i]) * inv_h for j in js])
-        eta = np.array([(y[j] - y[i]) * inv_h for j in js])
+        js, xi, eta = offsets(S)
         if not gram_ok(vandermonde(xi, eta)):
             return False, js, None, 0.0
         f, res = project(xi, eta, p32[S].astype(np.float64))

@@ -39,7 +39,7 @@ class Stats(ctypes.Structure):
                 ("max_dt_ratio", ctypes.c_double), ("lp_small_solved", ctypes.c_int64),
                 ("lp_small_pivots", ctypes.c_int64), ("lp_full_solved", ctypes.c_int64),
                 ("lp_full_pivots", ctypes.c_int64), ("learned_ok", ctypes.c_int64),
-                ("learned_rejected", ctypes.c_int64)]
+                ("learned_rejected", ctypes.c_int64), ("learned_square", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

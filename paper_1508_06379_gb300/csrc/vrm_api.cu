@@ -165,7 +165,7 @@ cudaError_t ensure_learned(vrm_ctx* ctx, int cap, cudaStream_t st) {
   ++ctx->scratch_gen;
   free_learned(L);
   const int n = cap < 128 ? 128 : cap;
-  cudaError_t e = mlp_acts_alloc(&L.acts, n, true);
+  cudaError_t e = mlp_acts_alloc(&L.acts, n);
   if (e == cudaSuccess) e = cudaMalloc(&L.slots, sizeof(int) * (size_t)n * 32);
   if (e == cudaSuccess) e = cudaMalloc(&L.Y, sizeof(float) * (size_t)L.acts.rows_pad * 32);
   if (e == cudaSuccess) e = cudaMalloc(&L.rlist, sizeof(int) * (size_t)n);
@@ -190,7 +190,7 @@ cudaError_t enqueue_learned(vrm_ctx* ctx, const double* x, const double* y, cons
   if ((e = learned_features(c, x, y, list, list_count, cap, nbr_count, nbr_idx, L.acts.X, L.slots, st)) !=
       cudaSuccess)
     return e;
-  if ((e = mlp_forward(ctx->mlp, L.acts.mX, L.acts, cap, list_count, L.Y, st)) != cudaSuccess) return e;
+  if ((e = mlp_forward(ctx->mlp, L.acts.mX, cap, list_count, L.Y, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(s.counters + 2, 0, sizeof(int), st)) != cudaSuccess) return e;
   return learned_project(c, x, y, list, list_count, cap, L.slots, L.Y, cols, f, fii, status, L.rlist, s.counters + 2,
                          s.ds, dt_dev, ctx->p.nu, st);
@@ -796,6 +796,7 @@ vrm_status vrm_solve_weights(vrm_ctx* ctx, const double* x, const double* y, int
     stats->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
     stats->learned_ok = s.h_ds->learned_ok;
     stats->learned_rejected = s.h_ds->learned_rejected;
+    stats->learned_square = s.h_ds->learned_square;
   }
   if (ctx->mlp && vrm_mlp_error(ctx->mlp, stream) != VRM_OK) return VRM_ERR_CUDA;
   return VRM_OK;
@@ -932,6 +933,7 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
   st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
   st->learned_ok = s.h_ds->learned_ok;
   st->learned_rejected = s.h_ds->learned_rejected;
+  st->learned_square = s.h_ds->learned_square;
   if (s.h_state->overflow) return VRM_ERR_CAPACITY;
   *n_out = s.h_state->n_cur;
   if (s.h_ds->max_count > ctx->p.k_cap) return VRM_ERR_CAPACITY;
@@ -1089,6 +1091,7 @@ vrm_status finish_cloud(vrm_ctx* ctx, vrm_cloud& C, vrm_stats* st) {
   st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
   st->learned_ok = s.h_ds->learned_ok;
   st->learned_rejected = s.h_ds->learned_rejected;
+  st->learned_square = s.h_ds->learned_square;
   C.n_out = st->n_out;
   if (s.h_state->overflow) return VRM_ERR_CAPACITY;
   if (s.h_ds->max_count > ctx->p.k_cap) return VRM_ERR_CAPACITY;
@@ -1114,6 +1117,7 @@ void add_stats(vrm_stats* t, const vrm_stats& a) {
   t->lp_full_pivots += a.lp_full_pivots;
   t->learned_ok += a.learned_ok;
   t->learned_rejected += a.learned_rejected;
+  t->learned_square += a.learned_square;
 }
 
 }  // namespace

@@ -80,7 +80,7 @@ struct DevStats {
   unsigned long long max_dt_ratio_bits;  // positive double, as bits
   unsigned long long lp_small_pivots, lp_full_pivots;
   int lp_small_solved, lp_full_solved;
-  int learned_ok, learned_rejected;
+  int learned_ok, learned_rejected, learned_square;
 };
 
 // Growth-control selection state (device resident).

@@ -8,7 +8,10 @@
 // Input row: xi_x of the slots, xi_y, mask, 32 zeros (bf16), xi = (x_j -
 // x_i) / h (Eq. momcondmv scaling) rounded to fp32 and then bf16.
 //
-// Correction (FP64): S = the up to 8 slots with the largest positive
+// First the square system V_5 f = b on the five slots with the largest
+// proposals (the network's choice of basis; Gaussian elimination with partial
+// pivoting, FP64): its solution is accepted under the test below.  Otherwise,
+// correction (FP64): S = the up to 8 slots with the largest positive
 // proposal (ties to the lower slot), in slot order; with V_S the rows (1,0)
 // (0,1) (2,0) (1,1) (0,2) of Eq. momcondmv at S and b = (0, 0, 2, 0, 2)
 // (Eqs. cond_two, cond_alpha),
@@ -34,14 +37,14 @@ constexpr double kAcceptResid = 1e-12;
 constexpr double kGramPivot = 1e-10;  // relative to the largest diagonal entry
 constexpr int kMaxDrops = 3;          // support refinements (8 -> 5 slots)
 
-__device__ __forceinline__ bool key_less(int sa, double da, int ja, int sb, double db, int jb) {
-  return sa < sb || (sa == sb && (da < db || (da == db && ja < jb)));
-}
-
 }  // namespace
 
 // One warp per listed particle: lane l takes neighbour l of the row, the
-// warp sorts the (segment, d2, index) keys and lane l writes slot l.
+// warp sorts the keys (segment, squared distance, index) and lane l writes
+// slot l.  Only x_j - x_i is FP64; it is rounded to fp32, and the segment,
+// the squared distance (products and sum rounded separately) and xi =
+// dx * fp32(1/h) are fp32 (the network's input precision).  d2 >= 0 is
+// compared through its bit pattern, so the sort runs on the integer pipes.
 __global__ void k_features(Consts c, const double* __restrict__ x, const double* __restrict__ y,
                            const int* __restrict__ list, const int* __restrict__ list_count, int m_bound,
                            const int* __restrict__ nbr_count, const int* __restrict__ nbr_idx,
@@ -50,50 +53,141 @@ __global__ void k_features(Consts c, const double* __restrict__ x, const double*
   const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long nwarps = ((long)gridDim.x * blockDim.x) >> 5;
   const int m = list_count ? *list_count : m_bound;
+  const float inv_hf = __double2float_rn(c.inv_h);
   for (long t = warp; t < m; t += nwarps) {
     const int i = list ? list[t] : (int)t;
     const int cnt = nbr_count[i];
     const int K = cnt < c.row_cap ? cnt : c.row_cap;
-    int seg = 8, j = INT_MAX;
-    double d2 = 1e300, dx = 0.0, dy = 0.0;
+    unsigned long long key = ~0ull;  // segment (8 = empty) << 32 | d2 bits
+    int j = INT_MAX;
+    float fdx = 0.0f, fdy = 0.0f;
     if (lane < K) {
       j = nbr_idx[(size_t)i * c.k_cap + lane];
-      dx = __dsub_rn(x[j], x[i]);
-      dy = __dsub_rn(y[j], y[i]);
-      d2 = dist2(dx, dy);
-      seg = segment_of(dx, dy);
+      fdx = __double2float_rn(__dsub_rn(x[j], x[i]));
+      fdy = __double2float_rn(__dsub_rn(y[j], y[i]));
+      const float d2 = dist2f(fdx, fdy);
+      key = ((unsigned long long)segment_of(fdx, fdy) << 32) | __float_as_uint(d2);
     }
+    int src = lane;
     for (int size = 2; size <= 32; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        const int oseg = __shfl_xor_sync(0xffffffffu, seg, stride);
-        const double od2 = __shfl_xor_sync(0xffffffffu, d2, stride);
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, stride);
         const int oj = __shfl_xor_sync(0xffffffffu, j, stride);
-        const double odx = __shfl_xor_sync(0xffffffffu, dx, stride);
-        const double ody = __shfl_xor_sync(0xffffffffu, dy, stride);
+        const int os = __shfl_xor_sync(0xffffffffu, src, stride);
         const bool up = ((lane & size) == 0);
         const bool lower = ((lane & stride) == 0);
-        const bool other_less = key_less(oseg, od2, oj, seg, d2, j);
-        const bool same = oseg == seg && od2 == d2 && oj == j;
+        const bool other_less = ok < key || (ok == key && oj < j);
+        const bool same = ok == key && oj == j;
         const bool take = (lower == up) ? other_less : (!other_less && !same);
         if (take) {
-          seg = oseg;
-          d2 = od2;
+          key = ok;
           j = oj;
-          dx = odx;
-          dy = ody;
+          src = os;
         }
       }
     }
     const bool valid = lane < K;
-    const float fx = valid ? __double2float_rn(__dmul_rn(dx, c.inv_h)) : 0.0f;
-    const float fy = valid ? __double2float_rn(__dmul_rn(dy, c.inv_h)) : 0.0f;
+    const float sdx = __shfl_sync(0xffffffffu, fdx, src);
+    const float sdy = __shfl_sync(0xffffffffu, fdy, src);
     __nv_bfloat16* row = X + (size_t)t * kRow;
-    row[lane] = __float2bfloat16_rn(fx);
-    row[kSlots + lane] = __float2bfloat16_rn(fy);
+    row[lane] = __float2bfloat16_rn(valid ? __fmul_rn(sdx, inv_hf) : 0.0f);
+    row[kSlots + lane] = __float2bfloat16_rn(valid ? __fmul_rn(sdy, inv_hf) : 0.0f);
     row[2 * kSlots + lane] = __float2bfloat16_rn(valid ? 1.0f : 0.0f);
     row[3 * kSlots + lane] = __float2bfloat16_rn(0.0f);
     slots[(size_t)t * kSlots + lane] = valid ? j : -1;
   }
+}
+
+// |d| through the bit pattern (integer compares: GB300's FP64 pipe is narrow).
+__device__ __forceinline__ unsigned long long abs_bits(double d) {
+  return (unsigned long long)__double_as_longlong(d) & 0x7FFFFFFFFFFFFFFFull;
+}
+// d >= 0 (and not NaN) through the bit pattern.
+__device__ __forceinline__ bool nonneg_bits(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  return b <= 0x7FF0000000000000ull || b == 0x8000000000000000ull;
+}
+
+// The square system V f = b on five neighbours (columns xi, eta) by Gaussian
+// elimination with partial pivoting (first largest |pivot|), FP64.  Returns
+// false when a pivot is at most 1e-12 of the largest |entry| or the result
+// is not a non-negative solution with residual <= kAcceptResid.
+__device__ __forceinline__ bool square_stencil(const double* xi, const double* eta, double* fo) {
+  double A[5][6], V[5][5];
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    V[0][s] = xi[s];
+    V[1][s] = eta[s];
+    V[2][s] = xi[s] * xi[s];
+    V[3][s] = xi[s] * eta[s];
+    V[4][s] = eta[s] * eta[s];
+  }
+  unsigned long long vmax = 0;
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+      A[r][s] = V[r][s];
+      const unsigned long long ab = abs_bits(V[r][s]);
+      vmax = ab > vmax ? ab : vmax;
+    }
+    A[r][5] = (r == 2 || r == 4) ? 2.0 : 0.0;
+  }
+  const unsigned long long tiny = abs_bits(1e-12 * __longlong_as_double((long long)vmax));
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    int p = k;
+    unsigned long long best = abs_bits(A[k][k]);
+#pragma unroll
+    for (int r = k + 1; r < 5; ++r) {
+      const unsigned long long ab = abs_bits(A[r][k]);
+      if (ab > best) {
+        best = ab;
+        p = r;
+      }
+    }
+    if (best <= tiny) return false;
+#pragma unroll
+    for (int r = k + 1; r < 5; ++r) {
+      if (r == p) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const double tmp = A[k][q];
+          A[k][q] = A[r][q];
+          A[r][q] = tmp;
+        }
+      }
+    }
+    const double inv = 1.0 / A[k][k];
+#pragma unroll
+    for (int r = k + 1; r < 5; ++r) {
+      const double mlt = A[r][k] * inv;
+#pragma unroll
+      for (int q = k; q < 6; ++q) A[r][q] = fma(-mlt, A[k][q], A[r][q]);
+    }
+  }
+  double f[5];
+#pragma unroll
+  for (int k = 4; k >= 0; --k) {
+    double acc = A[k][5];
+#pragma unroll
+    for (int q = k + 1; q < 5; ++q) acc = fma(-A[k][q], f[q], acc);
+    f[k] = acc / A[k][k];
+  }
+  bool ok = true;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) ok = ok && nonneg_bits(f[s]);
+  const unsigned long long lim = abs_bits(kAcceptResid);
+#pragma unroll
+  for (int r = 0; r < 5; ++r) {
+    double acc = (r == 2 || r == 4) ? -2.0 : 0.0;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) acc = fma(V[r][s], f[s], acc);
+    ok = ok && abs_bits(acc) <= lim;
+  }
+#pragma unroll
+  for (int s = 0; s < 5; ++s) fo[s] = f[s];
+  return ok;
 }
 
 // One thread per listed particle.  Accepted stencils are written like the
@@ -111,7 +205,7 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
   const int m = list_count ? *list_count : m_bound;
   const double nu_dt = dt_dev ? nu * *dt_dev : 0.0;
   const double inv_h2 = 1.0 / (c.h * c.h);
-  int n_ok = 0, n_rej = 0;
+  int n_ok = 0, n_rej = 0, n_square = 0;
   double st_ratio = 0.0;
   const long stride = (long)gridDim.x * blockDim.x;
   for (long base = (long)blockIdx.x * blockDim.x; base < m; base += stride) {
@@ -130,7 +224,7 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
         v[k] = p[k];
         if (sl[k] >= 0 && v[k] > 0.0f) ok_mask |= 1u << k;
       }
-      unsigned sup = 0;
+      unsigned sup = 0, sup5 = 0;
 #pragma unroll
       for (int k = 0; k < kSlots; ++k) {
         if (!((ok_mask >> k) & 1u)) continue;
@@ -139,9 +233,47 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
         for (int q = 0; q < kSlots; ++q)
           rank += ((ok_mask >> q) & 1u) && (v[q] > v[k] || (v[q] == v[k] && q < k));
         if (rank < kSup) sup |= 1u << k;
+        if (rank < 5) sup5 |= 1u << k;
       }
       const int ns = __popc(sup);
-      if (ns >= 5) {
+      // the network's basis alone: the square system on the top five slots
+      if (__popc(sup5) == 5) {
+        int j5[5];
+        double xi5[5], eta5[5], f5[5];
+        int q5 = 0;
+        const double xi0 = x[i], yi0 = y[i];
+#pragma unroll
+        for (int k = 0; k < kSlots; ++k) {
+          if (((sup5 >> k) & 1u) && q5 < 5) {
+            j5[q5] = sl[k];
+            ++q5;
+          }
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < 5; ++s2) {
+          xi5[s2] = __dmul_rn(__dsub_rn(x[j5[s2]], xi0), c.inv_h);
+          eta5[s2] = __dmul_rn(__dsub_rn(y[j5[s2]], yi0), c.inv_h);
+        }
+        if (square_stencil(xi5, eta5, f5)) {
+          accepted = true;
+          int* crow = cols + (size_t)i * VRM_STENCIL_W;
+          double* frow = f + (size_t)i * VRM_STENCIL_W;
+          double sum = 0.0;
+#pragma unroll
+          for (int s2 = 0; s2 < VRM_STENCIL_W; ++s2) {
+            crow[s2] = s2 < 5 ? j5[s2] : -1;
+            frow[s2] = s2 < 5 ? f5[s2] : 0.0;
+            if (s2 < 5) sum = __dadd_rn(sum, f5[s2]);
+          }
+          fii[i] = -sum;
+          status[i] = VRM_LP_LEARNED;
+          const double qr = __dmul_rn(__dmul_rn(nu_dt, sum), inv_h2);
+          st_ratio = qr > st_ratio ? qr : st_ratio;
+          ++n_square;
+        }
+      }
+      if (!accepted && ns >= 5) {
+
         int js[kSup];
         double xi[kSup], eta[kSup], f0s[kSup], fs[kSup];
         int q = 0;
@@ -323,6 +455,7 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
   }
   n_ok = __reduce_add_sync(0xffffffffu, n_ok);
   n_rej = __reduce_add_sync(0xffffffffu, n_rej);
+  n_square = __reduce_add_sync(0xffffffffu, n_square);
   unsigned long long rb = (unsigned long long)__double_as_longlong(st_ratio);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -332,6 +465,7 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
   if ((threadIdx.x & 31) == 0) {
     if (n_ok) atomicAdd(&ds->learned_ok, n_ok);
     if (n_rej) atomicAdd(&ds->learned_rejected, n_rej);
+    if (n_square) atomicAdd(&ds->learned_square, n_square);
     if (rb) atomicMax(&ds->max_dt_ratio_bits, rb);
   }
 }

@@ -224,6 +224,201 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
   }
 }
 
+// ---- fused inference ------------------------------------------------------------------
+//
+// The whole network for 128-row tiles in one persistent kernel: the tile's
+// activations never leave shared memory.  16 warps; thread 0 streams the
+// weight slabs (64 input columns of one layer: W1, W2, W3 with 256 rows,
+// W4 with 32) through a 4-stage ring with TMA and issues the MMAs; after
+// each layer every warp reads a 32-row x 64-column block of the TMEM
+// accumulator (warp w: rows 32 (w mod 4), columns 64 (w div 4)), adds the
+// bias, applies GELU and writes bf16 back into the activation tile in the
+// MMA operand layout (128-byte swizzle), which the next layer reads as A.
+// The input tile is loaded into the first two slabs of the activation tile
+// as soon as the previous tile's last layer has consumed it.
+
+constexpr int kFusedThreads = 512;
+constexpr int kRing = 4;
+constexpr int kSlabsPerTile = 14;  // W1: 2, W2: 4, W3: 4, W4: 4
+constexpr uint32_t kRingBytes = 256 * kBK * 2;  // one 256-row slab
+constexpr size_t kFusedSmem = 1024 + 4 * (size_t)kBM * kBK * 2 + (size_t)kRing * kRingBytes +
+                              (size_t)(3 * kHid + kOut) * 4 + 256;
+
+__device__ __forceinline__ void slab_of(int s, int* layer, int* kb) {
+  if (s < 2) {
+    *layer = 0, *kb = s;
+  } else if (s < 6) {
+    *layer = 1, *kb = s - 2;
+  } else if (s < 10) {
+    *layer = 2, *kb = s - 6;
+  } else {
+    *layer = 3, *kb = s - 10;
+  }
+}
+
+struct FusedArgs {
+  const float* bias;  // theta: b1, b2, b3, b4 at their offsets
+  float* Y;           // [rows x 32]
+  int rows;           // bound
+  const int* rows_dev;
+  int* error;
+};
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    k_mlp_fused(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap tw1,
+                const __grid_constant__ CUtensorMap tw2, const __grid_constant__ CUtensorMap tw3,
+                const __grid_constant__ CUtensorMap tw4, FusedArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  int rows = a.rows;
+  if (a.rows_dev) {
+    const int r = *a.rows_dev;
+    rows = r < rows ? r : rows;
+  }
+  const int ntiles = (rows + kBM - 1) / kBM;
+  if ((int)blockIdx.x >= ntiles) return;
+  const int my_tiles = (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
+  const int total = my_tiles * kSlabsPerTile;
+
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* H = base;                                   // 4 slabs x 16 KB
+  uint8_t* ring = base + 4 * (size_t)kBM * kBK * 2;    // kRing x 32 KB
+  float* sbias = (float*)(ring + (size_t)kRing * kRingBytes);
+  uint64_t* bars = (uint64_t*)(sbias + 3 * kHid + kOut);
+  uint64_t* xfull = bars;
+  uint64_t* wfull = bars + 1;
+  uint64_t* wempty = bars + 1 + kRing;
+  uint64_t* acc = bars + 1 + 2 * kRing;
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 + 2 * kRing);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = threadIdx.x; k < 3 * kHid + kOut; k += blockDim.x) {
+    const long off = k < kHid ? kOffB1 + k : k < 2 * kHid ? kOffB2 + k - kHid : k < 3 * kHid ? kOffB3 + k - 2 * kHid
+                                                                                      : kOffB4 + k - 3 * kHid;
+    sbias[k] = a.bias[off];
+  }
+  if (threadIdx.x == 0) {
+    umma::mbar_init(xfull, 1);
+    for (int s = 0; s < kRing; ++s) {
+      umma::mbar_init(&wfull[s], 1);
+      umma::mbar_init(&wempty[s], 1);
+    }
+    umma::mbar_init(acc, 1);
+    umma::fence_barrier_init();
+  }
+  if (warp == 0) umma::tmem_alloc(tmem_slot, 256);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  const CUtensorMap* wmap[4] = {&tw1, &tw2, &tw3, &tw4};
+  int g_load = 0;  // next weight slab to load (thread 0)
+  bool fail = false;
+  auto load_w = [&](int g) {
+    int layer, kb;
+    slab_of(g % kSlabsPerTile, &layer, &kb);
+    const int st = g % kRing;
+    umma::mbar_arrive_expect_tx(&wfull[st], layer == 3 ? (uint32_t)kOut * kBK * 2 : kRingBytes);
+    umma::tma_load_2d(ring + (size_t)st * kRingBytes, wmap[layer], &wfull[st], kb * kBK, 0);
+  };
+  auto load_x = [&](int tile) {
+    umma::mbar_arrive_expect_tx(xfull, 2u * kBM * kBK * 2);
+    umma::tma_load_2d(H, &tx, xfull, 0, tile * kBM);
+    umma::tma_load_2d(H + (size_t)kBM * kBK * 2, &tx, xfull, kBK, tile * kBM);
+  };
+  if (threadIdx.x == 0) {
+    load_x(blockIdx.x);
+    for (; g_load < kRing && g_load < total; ++g_load) load_w(g_load);
+  }
+  int acc_phase = 0;
+  const int layer_start[4] = {0, 2, 6, 10};
+  const int layer_nk[4] = {2, 4, 4, 4};
+  for (int it = 0; it < my_tiles; ++it) {
+    const int tile = blockIdx.x + it * gridDim.x;
+    for (int l = 0; l < 4; ++l) {
+      if (threadIdx.x == 0) {
+        if (l == 0 && !umma::mbar_wait(xfull, (uint32_t)it & 1u, kWaitCycles)) fail = true;
+        const uint32_t idesc = umma::idesc_bf16(kBM, l == 3 ? kOut : kHid);
+        for (int kb = 0; kb < layer_nk[l] && !fail; ++kb) {
+          const int g = it * kSlabsPerTile + layer_start[l] + kb;
+          const int st = g % kRing;
+          if (!umma::mbar_wait(&wfull[st], (uint32_t)(g / kRing) & 1u, kWaitCycles)) {
+            fail = true;
+            break;
+          }
+          umma::fence_after_sync();
+          const uint64_t da = umma::desc_sw128(umma::smem_u32(H + (size_t)kb * kBM * kBK * 2));
+          const uint64_t db = umma::desc_sw128(umma::smem_u32(ring + (size_t)st * kRingBytes));
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) umma::mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+          umma::mma_commit(&wempty[st]);
+          // refill the slot of the previous slab (its MMAs were issued earlier)
+          const int gp = g - 1;
+          if (gp >= 0 && gp + kRing < total && g_load == gp + kRing) {
+            if (!umma::mbar_wait(&wempty[gp % kRing], (uint32_t)(gp / kRing) & 1u, kWaitCycles)) {
+              fail = true;
+              break;
+            }
+            load_w(g_load++);
+          }
+        }
+        umma::mma_commit(acc);
+      }
+      const bool got = umma::mbar_wait(acc, (uint32_t)acc_phase & 1u, 2 * kWaitCycles);
+      ++acc_phase;
+      umma::fence_after_sync();
+      // the last layer has consumed the activation tile: bring in the next input
+      if (l == 3 && threadIdx.x == 0 && got && !fail && it + 1 < my_tiles) load_x(tile + gridDim.x);
+      const int q = warp & 3, cg = warp >> 2;
+      const int r = q * 32 + lane;  // row within the tile
+      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
+      if (l < 3) {
+        const float* b = sbias + l * kHid;
+#pragma unroll 1
+        for (int c0 = cg * 64; c0 < cg * 64 + 64; c0 += 16) {
+          float v[16];
+          umma::tmem_ld16(trow + (uint32_t)c0, v);
+          __align__(16) bf16 hv[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) hv[i] = __float2bfloat16_rn(gelu(v[i] + b[c0 + i]));
+          uint8_t* slab = H + (size_t)(c0 >> 6) * kBM * kBK * 2 + (size_t)r * 128;
+          const int ch = (c0 & 63) >> 3;
+          *reinterpret_cast<uint4*>(slab + (((ch) ^ (r & 7)) << 4)) = *reinterpret_cast<uint4*>(&hv[0]);
+          *reinterpret_cast<uint4*>(slab + (((ch + 1) ^ (r & 7)) << 4)) = *reinterpret_cast<uint4*>(&hv[8]);
+        }
+      } else if (cg < 2) {
+        const int c0 = cg * 16;
+        float v[16];
+        umma::tmem_ld16(trow + (uint32_t)c0, v);
+        const int row = tile * kBM + r;
+        if (row < rows) {
+          float4* dst = reinterpret_cast<float4*>(a.Y + (size_t)row * kOut + c0);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            dst[i] = make_float4(v[4 * i] + sbias[3 * kHid + c0 + 4 * i], v[4 * i + 1] + sbias[3 * kHid + c0 + 4 * i + 1],
+                                 v[4 * i + 2] + sbias[3 * kHid + c0 + 4 * i + 2],
+                                 v[4 * i + 3] + sbias[3 * kHid + c0 + 4 * i + 3]);
+        }
+      }
+      umma::fence_proxy_async_smem();  // the activation writes feed the next MMAs (async proxy)
+      umma::fence_before_sync();
+      const bool abort = __syncthreads_or(!got || fail) != 0;
+      umma::fence_after_sync();
+      if (abort) {
+        if (threadIdx.x == 0 && a.error) atomicExch(a.error, 1);
+        it = my_tiles;  // leave both loops
+        break;
+      }
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    umma::fence_after_sync();
+    umma::tmem_dealloc(tmem, 256);
+  }
+}
+
 // ---- small kernels -----------------------------------------------------------------
 
 // Batch assembly: rows idx[r] (or r) of the data set into X [B x 128],
@@ -464,25 +659,22 @@ struct vrm_mlp {
   bf16 *H1 = nullptr, *H2 = nullptr, *H3 = nullptr, *H1t = nullptr, *H2t = nullptr, *H3t = nullptr;
   bf16 *dY = nullptr, *dYt = nullptr;
   bf16 *dZ1 = nullptr, *dZ2 = nullptr, *dZ3 = nullptr, *dZ1t = nullptr, *dZ2t = nullptr, *dZ3t = nullptr;
-  vrm::MlpActs acts;  // activations of vrm_mlp_forward
   CUtensorMap mW1, mW2, mW3, mW4, mW2t, mW3t, mW4t;  // weights as B operands
   CUtensorMap mX, mXt, mH1, mH2, mH3, mH1t, mH2t, mH3t, mdY, mdYt, mdZ1t, mdZ2, mdZ2t, mdZ3, mdZ3t;
 };
 
 namespace vrm {
 
-cudaError_t mlp_acts_alloc(MlpActs* a, int rows, bool with_x) {
+cudaError_t mlp_acts_alloc(MlpActs* a, int rows) {
   mlp_acts_free(a);
   const int rp = (rows + kBM - 1) / kBM * kBM;
-  cudaError_t e = cudaMalloc(&a->Ha, (size_t)rp * kHid * sizeof(bf16));
-  if (e == cudaSuccess) e = cudaMalloc(&a->Hb, (size_t)rp * kHid * sizeof(bf16));
-  if (e == cudaSuccess && with_x) e = cudaMalloc(&a->X, (size_t)rp * kInPad * sizeof(bf16));
+  cudaError_t e = cudaMalloc(&a->X, (size_t)rp * kInPad * sizeof(bf16));
+  if (e == cudaSuccess) e = cudaMemset(a->X, 0, (size_t)rp * kInPad * sizeof(bf16));
   if (e != cudaSuccess) {
     mlp_acts_free(a);
     return e;
   }
-  if (!make_map(&a->mHa, a->Ha, rp, kHid, kBM) || !make_map(&a->mHb, a->Hb, rp, kHid, kBM) ||
-      (with_x && !make_map(&a->mX, a->X, rp, kInPad, kBM))) {
+  if (!make_map(&a->mX, a->X, rp, kInPad, kBM)) {
     mlp_acts_free(a);
     return cudaErrorInvalidValue;
   }
@@ -492,39 +684,32 @@ cudaError_t mlp_acts_alloc(MlpActs* a, int rows, bool with_x) {
 
 void mlp_acts_free(MlpActs* a) {
   if (a->X) cudaFree(a->X);
-  if (a->Ha) cudaFree(a->Ha);
-  if (a->Hb) cudaFree(a->Hb);
-  a->X = a->Ha = a->Hb = nullptr;
+  a->X = nullptr;
   a->rows_pad = 0;
 }
 
 bool mlp_input_map(CUtensorMap* m, const bf16* X, int rows_pad) { return make_map(m, X, rows_pad, kInPad, kBM); }
 
-cudaError_t mlp_forward(vrm_mlp* net, const CUtensorMap& mX, const MlpActs& a, int rows, const int* rows_dev,
-                        float* Y, cudaStream_t s) {
+cudaError_t mlp_forward(vrm_mlp* net, const CUtensorMap& mX, int rows, const int* rows_dev, float* Y,
+                        cudaStream_t s) {
   if (rows <= 0) return cudaSuccess;
-  if ((rows + kBM - 1) / kBM * kBM > a.rows_pad) return cudaErrorInvalidValue;
-  cudaError_t r;
-  Epi e = epi(EPI_BIAS_GELU, rows, kHid);
-  e.m_dev = rows_dev;
-  e.error = net->err;
-  e.bias = net->theta + kOffB1;
-  e.out_bf16 = a.Ha;
-  e.ld_bf16 = kHid;
-  if ((r = gemm(mX, net->mW1, 256, rows, kHid, kInPad, 1, e, s)) != cudaSuccess) return r;
-  e.bias = net->theta + kOffB2;
-  e.out_bf16 = a.Hb;
-  if ((r = gemm(a.mHa, net->mW2, 256, rows, kHid, kHid, 1, e, s)) != cudaSuccess) return r;
-  e.bias = net->theta + kOffB3;
-  e.out_bf16 = a.Ha;
-  if ((r = gemm(a.mHb, net->mW3, 256, rows, kHid, kHid, 1, e, s)) != cudaSuccess) return r;
-  Epi f = epi(EPI_BIAS_F32, rows, kOut);
-  f.m_dev = rows_dev;
-  f.error = net->err;
-  f.bias = net->theta + kOffB4;
-  f.out_f32 = Y;
-  f.ld_f32 = kOut;
-  return gemm(a.mHa, net->mW4, 32, rows, kOut, kHid, 1, f, s);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t r = cudaFuncSetAttribute(k_mlp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFusedSmem);
+    if (r != cudaSuccess) return r;
+    attr_set = true;
+  }
+  const int ntiles = (rows + kBM - 1) / kBM;
+  const int grid = ntiles < sm_count() ? ntiles : sm_count();
+  FusedArgs fa;
+  fa.bias = net->theta;
+  fa.Y = Y;
+  fa.rows = rows;
+  fa.rows_dev = rows_dev;
+  fa.error = net->err;
+  k_mlp_fused<<<grid, kFusedThreads, kFusedSmem, s>>>(mX, net->mW1, net->mW2, net->mW3, net->mW4, fa);
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace vrm
@@ -537,7 +722,6 @@ void free_mlp(vrm_mlp* n) {
                   n->H2t, n->H3t, n->dY, n->dYt, n->dZ1, n->dZ2, n->dZ3, n->dZ1t, n->dZ2t, n->dZ3t};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  vrm::mlp_acts_free(&n->acts);
 }
 
 template <typename T>
@@ -764,13 +948,9 @@ vrm_status vrm_mlp_forward(vrm_mlp* n, const uint16_t* X, int32_t rows, float* Y
   if (!n || rows < 0 || (rows > 0 && (!X || !Y)) || ((uintptr_t)X & 15u)) return VRM_ERR_ARG;
   if (rows == 0) return VRM_OK;
   const int rp = (rows + kBM - 1) / kBM * kBM;
-  if (rp > n->acts.rows_pad) {
-    if (cudaStreamSynchronize(s) != cudaSuccess) return VRM_ERR_CUDA;
-    if (vrm::mlp_acts_alloc(&n->acts, rows, false) != cudaSuccess) return VRM_ERR_CUDA;
-  }
   CUtensorMap mX;
   if (!vrm::mlp_input_map(&mX, reinterpret_cast<const bf16*>(X), rp)) return VRM_ERR_ARG;
-  if (vrm::mlp_forward(n, mX, n->acts, rows, nullptr, Y, s) != cudaSuccess) return VRM_ERR_CUDA;
+  if (vrm::mlp_forward(n, mX, rows, nullptr, Y, s) != cudaSuccess) return VRM_ERR_CUDA;
   return check_err(n, s);
 }
 

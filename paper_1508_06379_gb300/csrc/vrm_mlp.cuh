@@ -1,6 +1,7 @@
 // Inference side of the weight-proposal network (vrm_mlp.cu) as used by the
-// step (vrm_api.cu): activation buffers with their tensor maps, owned by the
-// caller so that a captured graph keeps valid pointers.
+// step (vrm_api.cu): the input-row buffer with its tensor map, owned by the
+// caller so that a captured graph keeps valid pointers (the activations stay
+// in shared memory).
 #pragma once
 
 #include <cuda.h>
@@ -11,21 +12,20 @@
 namespace vrm {
 
 struct MlpActs {
-  int rows_pad = 0;                // rows the buffers hold (multiple of 128)
-  __nv_bfloat16* X = nullptr;      // input rows [rows_pad x 128] (if owned)
-  __nv_bfloat16* Ha = nullptr;     // hidden activations [rows_pad x 256]
-  __nv_bfloat16* Hb = nullptr;
-  CUtensorMap mX, mHa, mHb;
+  int rows_pad = 0;            // rows the buffer holds (multiple of 128)
+  __nv_bfloat16* X = nullptr;  // input rows [rows_pad x 128]
+  CUtensorMap mX;
 };
 
-// Buffers for `rows` rows (rounded up to 128); with_x also allocates X.
-cudaError_t mlp_acts_alloc(MlpActs* a, int rows, bool with_x);
+// Input rows for `rows` rows (rounded up to 128).
+cudaError_t mlp_acts_alloc(MlpActs* a, int rows);
 void mlp_acts_free(MlpActs* a);
 // Tensor map of caller-owned input rows X [rows_pad x 128].
 bool mlp_input_map(CUtensorMap* m, const __nv_bfloat16* X, int rows_pad);
-// Y[rows x 32] = network(X) for rows_bound rows (or *rows_dev <= rows_bound).
-cudaError_t mlp_forward(vrm_mlp* net, const CUtensorMap& mX, const MlpActs& a, int rows_bound, const int* rows_dev,
-                        float* Y, cudaStream_t s);
+// Y[rows x 32] = network(X) for rows_bound rows (or *rows_dev <= rows_bound);
+// X (through its tensor map) holds rows_bound rounded up to 128 rows.
+cudaError_t mlp_forward(vrm_mlp* net, const CUtensorMap& mX, int rows_bound, const int* rows_dev, float* Y,
+                        cudaStream_t s);
 
 // vrm_learned.cu
 cudaError_t learned_features(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,

@@ -172,7 +172,8 @@ def test_projection_single_particle_example():
 
 def test_learned_stencil_accepts_valid_and_rejects_negative():
     # unit lattice neighbours, the 5-point stencil proposal (f~ = 1 on E N W S)
-    # plus a little weight on the diagonals
+    # plus a little weight on the diagonals: the top five slots (E N W S and
+    # the first diagonal) solve square to the 5-point stencil
     h = 1.0
     off = [(1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1)]
     x = np.array([0.0] + [a for a, _ in off])
@@ -182,13 +183,17 @@ def test_learned_stencil_accepts_valid_and_rejects_negative():
     f0 = np.zeros(32, dtype=np.float32)
     f0[:8] = [1, 0.01, 1, 0.01, 1, 0.01, 1, 0.01]
     ok, js, f, fii = mlp.learned_stencil(x, y, h, 0, slots, f0)
-    assert ok and js == list(range(1, 9)) and np.all(f >= 0) and abs(fii + np.sum(f)) < 1e-15
+    assert ok and js == [1, 2, 3, 5, 7] and np.all(f >= 0) and abs(fii + np.sum(f)) < 1e-15
     V = mlp.vandermonde(x[js], y[js])
     assert np.max(np.abs(V @ f - mlp.B_RHS)) <= 1e-12
-    # weight only on the diagonals and one axis: the correction turns an axis weight negative
+    # the diagonals and W: the square system gives the rotated 5-point stencil
     f0[:8] = [0.0, 1.0, 0.0, 1.0, 3.0, 1.0, 0.0, 1.0]
-    ok, _, f, _ = mlp.learned_stencil(x, y, h, 0, slots, f0)
-    assert not ok and np.min(f) < 0
+    ok, js, f, _ = mlp.learned_stencil(x, y, h, 0, slots, f0)
+    assert ok and js == [2, 4, 5, 6, 8] and np.allclose(f, [0.5, 0.5, 0.0, 0.5, 0.5], rtol=0, atol=1e-15)
+    # weight only on the upper half plane: rows (0,1) and (0,2) coincide there, no stencil
+    f0[:8] = [1, 1, 1, 1, 1, 0, 0, 0]
+    ok, _, _, _ = mlp.learned_stencil(x, y, h, 0, slots, f0)
+    assert not ok
     # fewer than 5 positive proposals: no stencil
     f0[:8] = [1, 0, 1, 0, 1, 0, 1, 0]
     ok, _, _, _ = mlp.learned_stencil(x, y, h, 0, slots, f0)
@@ -228,3 +233,31 @@ def test_support_refinement_reaches_a_vertex():
     ok, _, _, _ = mlp.learned_stencil(xl, yl, 1.0, 0, sl, f0l)
     assert not ok
     assert not mlp.gram_ok(mlp.vandermonde(xl[1:], yl[1:]))
+
+
+def test_square_solve_is_gaussian_elimination():
+    rng = np.random.default_rng(7)
+    for _ in range(50):
+        V = rng.normal(0, 1, (5, 5))
+        b = rng.normal(0, 1, 5)
+        f = mlp.square_solve(V, b)
+        assert np.allclose(f, np.linalg.solve(V, b), rtol=1e-10, atol=1e-12)
+    # a zero column is singular
+    V = rng.normal(0, 1, (5, 5))
+    V[:, 2] = 0.0
+    assert mlp.square_solve(V, np.ones(5)) is None
+
+
+def test_top_five_basis_gives_the_vertex():
+    # E, N, W, S and NE on the unit lattice: the unique stencil on these five
+    # neighbours is the 5-point Laplacian (1 on E, N, W, S; 0 on NE)
+    off = [(1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1)]
+    x = np.array([0.0] + [a for a, _ in off])
+    y = np.array([0.0] + [b for _, b in off])
+    slots = np.full(32, -1)
+    slots[:8] = np.arange(1, 9)
+    f0 = np.zeros(32, dtype=np.float32)
+    f0[:8] = [0.8, 0.3, 0.9, 0.01, 1.1, 0.02, 0.7, 0.03]
+    ok, js, f, fii = mlp.learned_stencil(x, y, 1.0, 0, slots, f0)
+    assert ok and js == [1, 2, 3, 5, 7]
+    assert np.allclose(f, [1.0, 0.0, 1.0, 1.0, 1.0], rtol=0, atol=1e-14) and fii == -4.0
