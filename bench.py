@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--train-rows", type=int, default=10_000_000,
                     help="LP solutions the network of the learned workload is trained on")
     ap.add_argument("--train-epochs", type=int, default=3)
+    ap.add_argument("--learned-side", type=int, default=2001,
+                    help="lattice side of the learned workload's cloud (2001: the 4M-particle cloud)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
     ap.add_argument("--schedule-cache", default=None,
@@ -597,8 +599,8 @@ def run_batched(args):
         dist.destroy_process_group()
 
 
-LEARNED_DESC = ("jittered lattice 2001x2001 (h=1e-3 on [-1,1]^2, jitter 0.3h), 8-Gaussian mixture, nu=1e-3, "
-                "C_diff=1, insertion on; stencils from the trained network (corrected, LP fallback) vs the LP alone")
+LEARNED_DESC = ("jittered lattice %dx%d (h=1e-3, jitter 0.3h), 8-Gaussian mixture, nu=1e-3, C_diff=1, insertion "
+                "on; stencils from the trained network (corrected, LP fallback) vs the LP alone")
 
 
 def run_learned(args):
@@ -626,8 +628,9 @@ def run_learned(args):
     t_train = time.time() - t0
     del X, T
     h, nu = 1e-3, 1e-3
-    x, y, g = vrm_inputs.gaussian_mixture_cloud(h=h, side=2001, jitter=0.3, seed=vrm_inputs.SEED_BASE + 4,
-                                                half_width=1.0)
+    side = args.learned_side
+    x, y, g = vrm_inputs.gaussian_mixture_cloud(h=h, side=side, jitter=0.3, seed=vrm_inputs.SEED_BASE + 4,
+                                                half_width=0.5 * (side - 1) * h)
     dt = (0.5 * h) ** 2 / (4 * nu) / 8
     n = len(x)
     cap = int(n * 1.6) + 4096
@@ -673,7 +676,7 @@ def run_learned(args):
         "metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": b["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 (network bf16/fp32)", "data": "synthetic",
-        "config": {"workload": LEARNED_DESC, "n": n, "n_out": int(b["n2"]), "n_diffused": int(st["n_diffused"]),
+        "config": {"workload": LEARNED_DESC % (side, side), "n": n, "n_out": int(b["n2"]), "n_diffused": int(st["n_diffused"]),
                    "h": h, "nu": nu, "dt": dt, "l2": "flushed between steps (512 MB write)",
                    "train_rows": int(N), "train_epochs": args.train_epochs, "train_loss_first_last":
                    [losses[0][1], losses[-1][1]], "data_s": round(t_data, 2), "train_s": round(t_train, 2)},

@@ -311,7 +311,7 @@ vrm_status vrm_step_batched(vrm_batch* b, vrm_cloud* clouds, int32_t n_clouds, v
  * the slot mask (1/0), then 32 zeros.  Slots hold the annulus neighbours
  * ordered by (45-degree segment, squared distance, index), xi = (x_j - x_i)/h.
  * Output rows: 32 fp32 proposals f~ (Eq. momcondmv scaling f~ = h^2 f).
- * Network 96 -> 256 -> 256 -> 256 -> 32, GELU (erf form) on the hidden
+ * Network 96 -> 256 -> 256 -> 256 -> 32, GELU (tanh form) on the hidden
  * layers; parameters one fp32 vector of VRM_MLP_PARAMS entries in the order
  * W1 (256 x 96, row-major [out][in]), b1, W2 (256 x 256), b2, W3, b3,
  * W4 (32 x 256), b4.  Products run on the tensor cores with bf16 weights and
@@ -368,19 +368,22 @@ vrm_status vrm_mlp_error(vrm_mlp* net, cudaStream_t stream);
  */
 vrm_status vrm_set_mlp(vrm_ctx* ctx, vrm_mlp* net);
 
-/* Input rows of the listed particles (list: device int32 [m], or NULL for
- * 0..m-1) from their neighbour rows: X bf16 [m rounded up to 128][128] and
- * slots int32 [m][32] (particle index of each slot, -1 empty). */
-vrm_status vrm_learned_features(vrm_ctx* ctx, const double* x, const double* y, const int32_t* list, int32_t m,
-                                const int32_t* nbr_count, const int32_t* nbr_idx, uint16_t* X, int32_t* slots,
-                                cudaStream_t stream);
+/* Input rows of the listed particles of an n-particle cloud (list: device
+ * int32 [m], or NULL for 0..m-1) from their neighbour rows: X bf16 [m rounded
+ * up to 128][128] and slots int32 [m][32] (particle index of each slot, -1
+ * empty).  Offsets are taken between fp32-rounded positions. */
+vrm_status vrm_learned_features(vrm_ctx* ctx, const double* x, const double* y, int32_t n, const int32_t* list,
+                                int32_t m, const int32_t* nbr_count, const int32_t* nbr_idx, uint16_t* X,
+                                int32_t* slots, cudaStream_t stream);
 /* Correction and acceptance of given proposals f0 (device fp32 [m][32]) for
- * the listed particles: accepted stencils are written as by the LP (status
+ * the listed particles; the candidates are the slots holding the small
+ * neighbourhood (small: device int32 [n][8] as from vrm_build_neighbourhoods,
+ * 16-byte aligned): accepted stencils are written as by the LP (status
  * VRM_LP_LEARNED), rejected ones get VRM_LP_NONE and a zero stencil.
  * *n_accepted (host) receives the count.  Synchronises. */
 vrm_status vrm_learned_project(vrm_ctx* ctx, const double* x, const double* y, const int32_t* list, int32_t m,
-                               const int32_t* slots, const float* f0, int32_t* cols, double* f, double* fii,
-                               uint8_t* status, int32_t* n_accepted, cudaStream_t stream);
+                               const int32_t* slots, const float* f0, const int32_t* small, int32_t* cols, double* f,
+                               double* fii, uint8_t* status, int32_t* n_accepted, cudaStream_t stream);
 /* Training targets: T fp32 [m][32], the weight f~ of each listed particle's
  * stencil (cols, f as written by vrm_solve_weights) at each slot's particle. */
 vrm_status vrm_learned_targets(const int32_t* list, int32_t m, const int32_t* slots, const int32_t* cols,

@@ -14,14 +14,16 @@ and signs; everything else goes to the LP.  The pieces:
   slots ordered by (45-degree segment of Sec. 4.2, squared distance, index),
   with the scaled offsets xi = (x_j - x_i)/h of Eq. momcondmv and a mask;
   input row [xi_x(32), xi_y(32), mask(32)].  The order and xi are float32
-  quantities (the network's input precision); only x_j - x_i is FP64.
+  quantities from float32 positions (the network's input precision).
 * forward()/backward(): the network 96 -> 256 -> 256 -> 256 -> 32 with GELU
-  (the erf form) after each hidden layer; W_l is [out x in].
+  (the tanh form) after each hidden layer; W_l is [out x in].
 * loss(): mean squared error over the valid slots against the LP weights
   f~ of the same particle (f~ = h^2 f, Eq. momcondmv scaling).
 * adamw(): Adam with decoupled weight decay (Loshchilov and Hutter).
-* support() and project(): up to 8 slots with the largest positive proposal
-  form the support S; the proposal is corrected by the smallest change that
+* support() and project(): the candidates are the slots holding the small
+  neighbourhood of Sec. 4.3 (the closest particle of every segment: the
+  columns the LP itself works on); up to 8 of them with the largest positive
+  proposal form the support S; the proposal is corrected by the smallest change that
   meets the moment conditions on S,
       f_S = f0_S + V_S^T (V_S V_S^T)^{-1} (b - V_S f0_S),
   and accepted iff every f_j >= 0 and the residual |V_S f_S - b|_inf is at
@@ -104,24 +106,26 @@ def segment(dx, dy):
 
 def features(x, y, h, i, row):
     """Input row (bf16 values) and slot -> particle map (-1 = empty) of
-    particle i whose neighbourhood is `row` (indices, any order).  The offset
-    dx = x_j - x_i is one FP64 subtraction, then rounded to float32; the slot
-    order key (segment, squared distance, index) and xi = dx * (1/h) are
-    float32 computations on those rounded offsets (products and sums rounded
-    separately, 1/h computed in FP64 and rounded to float32)."""
+    particle i whose neighbourhood is `row` (indices, any order).  All float32:
+    positions rounded to float32, dx = x_j - x_i, the squared distance d2 and
+    xi = dx * (1/h) (products and sums rounded separately, 1/h computed in
+    FP64 and rounded to float32).  Slots are ordered by the 32-bit key
+    segment * 2^28 + (bit pattern of d2) / 8 (the 3 lowest mantissa bits
+    dropped), then by index."""
     f32 = np.float32
     inv_h = f32(1.0 / h)
     ent = []
     for j in row:
         j = int(j)
-        dx = f32(x[j] - x[i])
-        dy = f32(y[j] - y[i])
+        dx = f32(f32(x[j]) - f32(x[i]))
+        dy = f32(f32(y[j]) - f32(y[i]))
         d2 = f32(f32(dx * dx) + f32(dy * dy))
-        ent.append((segment(dx, dy), d2, j, dx, dy))
-    ent.sort(key=lambda e: (e[0], e[1], e[2]))
+        key = (segment(dx, dy) << 28) | (int(np.array(d2, dtype=np.float32).view(np.uint32)) >> 3)
+        ent.append((key, j, dx, dy))
+    ent.sort(key=lambda e: (e[0], e[1]))
     X = np.zeros(N_IN)
     slots = np.full(K_SLOTS, -1, dtype=np.int64)
-    for k, (_, _, j, dx, dy) in enumerate(ent[:K_SLOTS]):
+    for k, (_, j, dx, dy) in enumerate(ent[:K_SLOTS]):
         X[k] = f32(dx * inv_h)
         X[K_SLOTS + k] = f32(dy * inv_h)
         X[2 * K_SLOTS + k] = 1.0
@@ -130,14 +134,18 @@ def features(x, y, h, i, row):
 
 
 # -- network -------------------------------------------------------------------------
+GELU_C = np.sqrt(2.0 / np.pi)
+GELU_A = 0.044715
+
+
 def gelu(z):
-    from scipy.special import erf
-    return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+    """GELU in its tanh form: 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3)))."""
+    return 0.5 * z * (1.0 + np.tanh(GELU_C * (z + GELU_A * z ** 3)))
 
 
 def gelu_grad(z):
-    from scipy.special import erf
-    return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+    t = np.tanh(GELU_C * (z + GELU_A * z ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * GELU_C * (1.0 + 3.0 * GELU_A * z * z)
 
 
 def forward(theta, X, bf16_acts=False):
@@ -199,12 +207,14 @@ def vandermonde(xi, eta):
     return np.stack([xi, eta, xi * xi, xi * eta, eta * eta])
 
 
-def support(f0, slots, cap=SUPPORT_MAX):
-    """Slots of the support: the (up to) cap valid slots with the largest
-    positive proposal, ties to the lower slot, returned in slot order.  The
-    comparisons are made on the float32 proposals."""
+def support(f0, slots, cap=SUPPORT_MAX, allowed=None):
+    """Slots of the support: the (up to) cap valid slots (holding a particle
+    of `allowed`, if given) with the largest positive proposal, ties to the
+    lower slot, returned in slot order.  The comparisons are made on the
+    float32 proposals."""
     f0 = np.asarray(f0, dtype=np.float32)
-    cand = [k for k in range(len(f0)) if slots[k] >= 0 and f0[k] > 0]
+    ok = set(int(a) for a in allowed if a >= 0) if allowed is not None else None
+    cand = [k for k in range(len(f0)) if slots[k] >= 0 and f0[k] > 0 and (ok is None or int(slots[k]) in ok)]
     cand.sort(key=lambda k: (-float(f0[k]), k))
     return sorted(cand[:cap])
 
@@ -263,9 +273,10 @@ def square_solve(V, b, rel=1e-12):
     return f
 
 
-def learned_stencil(x, y, h, i, slots, f0):
-    """The learned stencil of particle i from its slot map and proposal:
-    (accepted, particle indices, f~ in slot order, f~_ii)."""
+def learned_stencil(x, y, h, i, slots, f0, small=None):
+    """The learned stencil of particle i from its slot map, proposal and
+    small neighbourhood (8 indices, -1 empty; None: every slot is a
+    candidate): (accepted, particle indices, f~ in slot order, f~_ii)."""
     p32 = np.asarray(f0, dtype=np.float32)
     inv_h = 1.0 / h
 
@@ -276,7 +287,7 @@ def learned_stencil(x, y, h, i, slots, f0):
         return js, xi, eta
 
     # the network's basis alone: the square system on the top five slots
-    S5 = support(f0, slots, cap=5)
+    S5 = support(f0, slots, cap=5, allowed=small)
     if len(S5) == 5:
         js, xi, eta = offsets(S5)
         V = vandermonde(xi, eta)
@@ -284,7 +295,7 @@ def learned_stencil(x, y, h, i, slots, f0):
         if f is not None and np.all(f >= 0.0) and float(np.max(np.abs(V @ f - B_RHS))) <= ACCEPT_RESID:
             return True, js, f, -float(np.sum(f))
     # least change on up to eight slots, dropping the most negative
-    S = support(f0, slots)
+    S = support(f0, slots, allowed=small)
     f = None
     js = []
     for _ in range(MAX_DROPS + 1):

@@ -114,8 +114,8 @@ SIGNATURES = {
     "vrm_mlp_adamw": (ctypes.c_int, [P, P, P, I32, P]),
     "vrm_mlp_error": (ctypes.c_int, [P, P]),
     "vrm_set_mlp": (ctypes.c_int, [P, P]),
-    "vrm_learned_features": (ctypes.c_int, [P, P, P, P, I32, P, P, P, P, P]),
-    "vrm_learned_project": (ctypes.c_int, [P, P, P, P, I32, P, P, P, P, P, P, P, P]),
+    "vrm_learned_features": (ctypes.c_int, [P, P, P, I32, P, I32, P, P, P, P, P]),
+    "vrm_learned_project": (ctypes.c_int, [P, P, P, P, I32, P, P, P, P, P, P, P, P, P]),
     "vrm_learned_targets": (ctypes.c_int, [P, I32, P, P, P, P, P]),
 }
 MLP_PARAMS = 164640
@@ -313,13 +313,13 @@ class VRM:
         slots = torch.empty(max(m, 1), 32, dtype=torch.int32, device=dev)
         n = x.numel()
         self._check(self.lib.vrm_learned_features(
-            self.ctx, _ptr(x, torch.float64, "x"), _ptr(y, torch.float64, "y"),
+            self.ctx, _ptr(x, torch.float64, "x", n), _ptr(y, torch.float64, "y", n), int(n),
             _ptr(list_, torch.int32, "list", m) if list_ is not None else None, m,
             _ptr(nb["count"], torch.int32, "nbr_count"), _ptr(nb["idx"], torch.int32, "nbr_idx"),
             _ptr(X, torch.bfloat16, "X"), _ptr(slots, torch.int32, "slots"), _stream()), "vrm_learned_features")
         return X, slots[:m]
 
-    def learned_project(self, x, y, list_, slots, f0, n):
+    def learned_project(self, x, y, list_, slots, f0, n, small):
         """Correction and acceptance of proposals f0 (fp32 [m, 32]); stencils of
         the n-particle cloud as from solve_weights, plus the accepted count."""
         m = int(slots.shape[0])
@@ -334,7 +334,7 @@ class VRM:
             self.ctx, _ptr(x, torch.float64, "x"), _ptr(y, torch.float64, "y"),
             _ptr(list_, torch.int32, "list", m) if list_ is not None else None, m,
             _ptr(slots.contiguous(), torch.int32, "slots", 32 * m), _ptr(f0.contiguous(), torch.float32, "f0", 32 * m),
-            _ptr(cols, torch.int32, "cols"), _ptr(f, torch.float64, "f"), _ptr(fii, torch.float64, "fii"),
+            _ptr(small, torch.int32, "small", 8 * n), _ptr(cols, torch.int32, "cols"), _ptr(f, torch.float64, "f"), _ptr(fii, torch.float64, "fii"),
             _ptr(status, torch.uint8, "status"), ctypes.byref(acc), _stream()), "vrm_learned_project")
         return dict(cols=cols, f=f, fii=fii, status=status), acc.value
 

@@ -28,6 +28,7 @@ struct Learned {
   int* slots = nullptr;
   float* Y = nullptr;
   int* rlist = nullptr;
+  float2* xyf = nullptr;  // fp32 positions
 };
 
 struct vrm::Scratch {
@@ -153,6 +154,7 @@ void free_learned(Learned& L) {
   if (L.slots) cudaFree(L.slots);
   if (L.Y) cudaFree(L.Y);
   if (L.rlist) cudaFree(L.rlist);
+  if (L.xyf) cudaFree(L.xyf);
   L = Learned{};
 }
 
@@ -169,6 +171,7 @@ cudaError_t ensure_learned(vrm_ctx* ctx, int cap, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMalloc(&L.slots, sizeof(int) * (size_t)n * 32);
   if (e == cudaSuccess) e = cudaMalloc(&L.Y, sizeof(float) * (size_t)L.acts.rows_pad * 32);
   if (e == cudaSuccess) e = cudaMalloc(&L.rlist, sizeof(int) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&L.xyf, sizeof(float2) * (size_t)n);
   if (e != cudaSuccess) {
     free_learned(L);
     cudaGetLastError();
@@ -180,20 +183,20 @@ cudaError_t ensure_learned(vrm_ctx* ctx, int cap, cudaStream_t st) {
 
 // Learned proposal for the listed particles, then the LP for the rejected
 // ones (their list and count in L.rlist, counters[2]).
-cudaError_t enqueue_learned(vrm_ctx* ctx, const double* x, const double* y, const int* list, const int* list_count,
-                            int cap, const int* nbr_count, const int* nbr_idx, int* cols, double* f, double* fii,
-                            uint8_t* status, const double* dt_dev, cudaStream_t st) {
+cudaError_t enqueue_learned(vrm_ctx* ctx, const double* x, const double* y, const int* n_dev, const int* list,
+                            const int* list_count, int cap, const int* nbr_count, const int* nbr_idx, const int* small, int* cols, double* f,
+                            double* fii, uint8_t* status, const double* dt_dev, cudaStream_t st) {
   Scratch& s = ctx->s;
   Learned& L = ctx->L;
   const Consts& c = ctx->c;
   cudaError_t e;
-  if ((e = learned_features(c, x, y, list, list_count, cap, nbr_count, nbr_idx, L.acts.X, L.slots, st)) !=
-      cudaSuccess)
+  if ((e = learned_features(c, x, y, cap, n_dev, L.xyf, list, list_count, cap, nbr_count, nbr_idx, L.acts.X, L.slots,
+                            st)) != cudaSuccess)
     return e;
   if ((e = mlp_forward(ctx->mlp, L.acts.mX, cap, list_count, L.Y, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(s.counters + 2, 0, sizeof(int), st)) != cudaSuccess) return e;
-  return learned_project(c, x, y, list, list_count, cap, L.slots, L.Y, cols, f, fii, status, L.rlist, s.counters + 2,
-                         s.ds, dt_dev, ctx->p.nu, st);
+  return learned_project(c, x, y, list, list_count, cap, L.slots, L.Y, small, cols, f, fii, status, L.rlist,
+                         s.counters + 2, s.ds, dt_dev, ctx->p.nu, st);
 }
 
 // Scratch for `cap` particles (grown by 25% steps, never shrunk).
@@ -442,8 +445,8 @@ cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const doub
   const int* lp_list = s.dlist;
   const int* lp_count = s.counters + 0;
   if (ctx->mlp) {
-    if ((e = enqueue_learned(ctx, x, y, s.dlist, s.counters + 0, cap, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii,
-                             s.status, &s.st->dt, st)) != cudaSuccess)
+    if ((e = enqueue_learned(ctx, x, y, &s.st->n_cur, s.dlist, s.counters + 0, cap, s.nbr_count, s.nbr_idx, s.small, s.cols, s.f,
+                             s.fii, s.status, &s.st->dt, st)) != cudaSuccess)
       return e;
     lp_list = ctx->L.rlist;
     lp_count = s.counters + 2;
@@ -772,8 +775,8 @@ vrm_status vrm_solve_weights(vrm_ctx* ctx, const double* x, const double* y, int
   if (ctx->mlp) {
     const Consts keep = ctx->c;
     ctx->c = c;  // whole rows
-    const cudaError_t le = enqueue_learned(ctx, x, y, s.dlist, s.counters + 0, n, nbr_count, nbr_idx, cols, f, fii,
-                                           status, nullptr, stream);
+    const cudaError_t le = enqueue_learned(ctx, x, y, nullptr, s.dlist, s.counters + 0, n, nbr_count, nbr_idx, small, cols, f,
+                                           fii, status, nullptr, stream);
     ctx->c = keep;
     VRM_CUDA(le);
     lp_list = ctx->L.rlist;
@@ -812,29 +815,32 @@ vrm_status vrm_set_mlp(vrm_ctx* ctx, vrm_mlp* net) {
   return VRM_OK;
 }
 
-vrm_status vrm_learned_features(vrm_ctx* ctx, const double* x, const double* y, const int32_t* list, int32_t m,
-                                const int32_t* nbr_count, const int32_t* nbr_idx, uint16_t* X, int32_t* slots,
-                                cudaStream_t stream) {
-  if (!ctx || m < 0) return VRM_ERR_ARG;
+vrm_status vrm_learned_features(vrm_ctx* ctx, const double* x, const double* y, int32_t n, const int32_t* list,
+                                int32_t m, const int32_t* nbr_count, const int32_t* nbr_idx, uint16_t* X,
+                                int32_t* slots, cudaStream_t stream) {
+  if (!ctx || m < 0 || n < 0) return VRM_ERR_ARG;
   if (m == 0) return VRM_OK;
-  if (!x || !y || !nbr_count || !nbr_idx || !X || !slots || misaligned16(X)) return VRM_ERR_ARG;
-  VRM_CUDA(learned_features(full_rows(ctx->c), x, y, list, nullptr, m, nbr_count, nbr_idx,
-                            reinterpret_cast<__nv_bfloat16*>(X), slots, stream));
+  if (!x || !y || n == 0 || !nbr_count || !nbr_idx || !X || !slots || misaligned16(X)) return VRM_ERR_ARG;
+  if (!list && m > n) return VRM_ERR_ARG;
+  VRM_CUDA(ensure_scratch(ctx, n, stream));
+  // the fp32 position copy lives in the step's weight scratch (8 doubles per particle)
+  VRM_CUDA(learned_features(full_rows(ctx->c), x, y, n, nullptr, reinterpret_cast<float2*>(ctx->s.f), list, nullptr,
+                            m, nbr_count, nbr_idx, reinterpret_cast<__nv_bfloat16*>(X), slots, stream));
   return VRM_OK;
 }
 
 vrm_status vrm_learned_project(vrm_ctx* ctx, const double* x, const double* y, const int32_t* list, int32_t m,
-                               const int32_t* slots, const float* f0, int32_t* cols, double* f, double* fii,
-                               uint8_t* status, int32_t* n_accepted, cudaStream_t stream) {
+                               const int32_t* slots, const float* f0, const int32_t* small, int32_t* cols, double* f,
+                               double* fii, uint8_t* status, int32_t* n_accepted, cudaStream_t stream) {
   if (!ctx || m < 0) return VRM_ERR_ARG;
   if (n_accepted) *n_accepted = 0;
   if (m == 0) return VRM_OK;
-  if (!x || !y || !slots || !f0 || !cols || !f || !fii || !status) return VRM_ERR_ARG;
+  if (!x || !y || !slots || !f0 || !small || !cols || !f || !fii || !status || misaligned16(small)) return VRM_ERR_ARG;
   Scratch& s = ctx->s;
   VRM_CUDA(ensure_scratch(ctx, m, stream));
   VRM_CUDA(cudaMemsetAsync(s.ds, 0, sizeof(DevStats), stream));
-  VRM_CUDA(learned_project(ctx->c, x, y, list, nullptr, m, slots, f0, cols, f, fii, status, nullptr, nullptr, s.ds,
-                           nullptr, ctx->p.nu, stream));
+  VRM_CUDA(learned_project(ctx->c, x, y, list, nullptr, m, slots, f0, small, cols, f, fii, status, nullptr, nullptr,
+                           s.ds, nullptr, ctx->p.nu, stream));
   VRM_CUDA(read_back(ctx, stream));
   if (n_accepted) *n_accepted = s.h_ds->learned_ok;
   return VRM_OK;

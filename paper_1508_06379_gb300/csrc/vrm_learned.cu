@@ -6,9 +6,11 @@
 // Slots: the annulus neighbours of particle i (Eq. neighbourhood) ordered by
 // (45-degree segment of Sec. 4.2, squared distance, index), at most 32.
 // Input row: xi_x of the slots, xi_y, mask, 32 zeros (bf16), xi = (x_j -
-// x_i) / h (Eq. momcondmv scaling) rounded to fp32 and then bf16.
+// x_i) / h (Eq. momcondmv scaling) in fp32 from fp32 positions, then bf16.
 //
-// First the square system V_5 f = b on the five slots with the largest
+// Candidates are the slots holding the small neighbourhood of Sec. 4.3 (the
+// closest particle of every segment, the LP's own columns).
+// First the square system V_5 f = b on the five candidates with the largest
 // proposals (the network's choice of basis; Gaussian elimination with partial
 // pivoting, FP64): its solution is accepted under the test below.  Otherwise,
 // correction (FP64): S = the up to 8 slots with the largest positive
@@ -39,13 +41,23 @@ constexpr int kMaxDrops = 3;          // support refinements (8 -> 5 slots)
 
 }  // namespace
 
+// fp32 copy of the positions (the network's input precision).
+__global__ void k_mirror(const double* __restrict__ x, const double* __restrict__ y, int n_bound,
+                         const int* __restrict__ n_dev, float2* __restrict__ xyf) {
+  const int n = n_dev ? *n_dev : n_bound;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    xyf[i] = make_float2(__double2float_rn(x[i]), __double2float_rn(y[i]));
+}
+
 // One warp per listed particle: lane l takes neighbour l of the row, the
 // warp sorts the keys (segment, squared distance, index) and lane l writes
-// slot l.  Only x_j - x_i is FP64; it is rounded to fp32, and the segment,
-// the squared distance (products and sum rounded separately) and xi =
-// dx * fp32(1/h) are fp32 (the network's input precision).  d2 >= 0 is
-// compared through its bit pattern, so the sort runs on the integer pipes.
-__global__ void k_features(Consts c, const double* __restrict__ x, const double* __restrict__ y,
+// slot l.  Everything is fp32 (the network's input precision): the offset
+// is fp32(x_j) - fp32(x_i), then the segment, the squared distance
+// (products and sum rounded separately) and xi = dx * fp32(1/h).  The sort
+// key is one 32-bit word, segment << 28 | bits(d2) >> 3 (d2 >= 0, so its bit
+// pattern orders like the value; the 3 lowest mantissa bits are dropped),
+// with the index breaking ties: the sort runs on the integer pipes.
+__global__ void k_features(Consts c, const float2* __restrict__ xyf,
                            const int* __restrict__ list, const int* __restrict__ list_count, int m_bound,
                            const int* __restrict__ nbr_count, const int* __restrict__ nbr_idx,
                            __nv_bfloat16* __restrict__ X, int* __restrict__ slots) {
@@ -58,20 +70,21 @@ __global__ void k_features(Consts c, const double* __restrict__ x, const double*
     const int i = list ? list[t] : (int)t;
     const int cnt = nbr_count[i];
     const int K = cnt < c.row_cap ? cnt : c.row_cap;
-    unsigned long long key = ~0ull;  // segment (8 = empty) << 32 | d2 bits
+    unsigned key = 0xFFFFFFFFu;  // empty slots last
     int j = INT_MAX;
     float fdx = 0.0f, fdy = 0.0f;
     if (lane < K) {
       j = nbr_idx[(size_t)i * c.k_cap + lane];
-      fdx = __double2float_rn(__dsub_rn(x[j], x[i]));
-      fdy = __double2float_rn(__dsub_rn(y[j], y[i]));
+      const float2 pj = xyf[j], pi = xyf[i];
+      fdx = __fsub_rn(pj.x, pi.x);
+      fdy = __fsub_rn(pj.y, pi.y);
       const float d2 = dist2f(fdx, fdy);
-      key = ((unsigned long long)segment_of(fdx, fdy) << 32) | __float_as_uint(d2);
+      key = ((unsigned)segment_of(fdx, fdy) << 28) | (__float_as_uint(d2) >> 3);
     }
     int src = lane;
     for (int size = 2; size <= 32; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, stride);
+        const unsigned ok = __shfl_xor_sync(0xffffffffu, key, stride);
         const int oj = __shfl_xor_sync(0xffffffffu, j, stride);
         const int os = __shfl_xor_sync(0xffffffffu, src, stride);
         const bool up = ((lane & size) == 0);
@@ -108,6 +121,42 @@ __device__ __forceinline__ bool nonneg_bits(double d) {
   return b <= 0x7FF0000000000000ull || b == 0x8000000000000000ull;
 }
 
+// binary32 seed of |a| from the bit pattern (mantissa rounded to 23 bits,
+// exponent rebiased; |a| must lie in the binary32 normal range), by integer ops.
+__device__ __forceinline__ float seed32(double a) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long mr = (b + 0x10000000ull) >> 29;
+  const int e32 = (int)((mr >> 23) & 0x7FF) - 1023 + 127;
+  return __int_as_float((e32 << 23) | (int)(mr & 0x7FFFFF));
+}
+// binary32 value widened to binary64 by integer ops (normal range).
+__device__ __forceinline__ double widen32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long d = ((unsigned long long)(u >> 31) << 63) |
+                               ((unsigned long long)((int)((u >> 23) & 0xFF) - 127 + 1023) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFF) << 29);
+  return __longlong_as_double((long long)d);
+}
+// 1/a for |a| in the binary32 normal range: binary32 seed, two Newton steps
+// r <- r + r (1 - a r) in FP64 (full FP64 accuracy; no FP64 division).
+__device__ __forceinline__ double rcp64(double a) {
+  float r32 = __frcp_rn(seed32(a));
+  if (__double_as_longlong(a) < 0) r32 = -r32;
+  double r = widen32(r32);
+  r = fma(r, fma(-a, r, 1.0), r);
+  r = fma(r, fma(-a, r, 1.0), r);
+  return r;
+}
+// 1/sqrt(d) for d > 0 in the binary32 normal range: binary32 seed, two
+// Newton steps y <- y + y (1/2 - (d y / 2) y) in FP64.
+__device__ __forceinline__ double rsqrt64(double d) {
+  double y = widen32(__frsqrt_rn(seed32(d)));
+  const double hd = 0.5 * d;
+  y = fma(y, fma(-hd * y, y, 0.5), y);
+  y = fma(y, fma(-hd * y, y, 0.5), y);
+  return y;
+}
+
 // The square system V f = b on five neighbours (columns xi, eta) by Gaussian
 // elimination with partial pivoting (first largest |pivot|), FP64.  Returns
 // false when a pivot is at most 1e-12 of the largest |entry| or the result
@@ -134,6 +183,7 @@ __device__ __forceinline__ bool square_stencil(const double* xi, const double* e
     A[r][5] = (r == 2 || r == 4) ? 2.0 : 0.0;
   }
   const unsigned long long tiny = abs_bits(1e-12 * __longlong_as_double((long long)vmax));
+  double inv[5];
 #pragma unroll
   for (int k = 0; k < 5; ++k) {
     int p = k;
@@ -149,19 +199,18 @@ __device__ __forceinline__ bool square_stencil(const double* xi, const double* e
     if (best <= tiny) return false;
 #pragma unroll
     for (int r = k + 1; r < 5; ++r) {
-      if (r == p) {
+      const bool sw = r == p;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-          const double tmp = A[k][q];
-          A[k][q] = A[r][q];
-          A[r][q] = tmp;
-        }
+      for (int q = 0; q < 6; ++q) {
+        const double a = A[k][q], b = A[r][q];
+        A[k][q] = sw ? b : a;
+        A[r][q] = sw ? a : b;
       }
     }
-    const double inv = 1.0 / A[k][k];
+    inv[k] = rcp64(A[k][k]);
 #pragma unroll
     for (int r = k + 1; r < 5; ++r) {
-      const double mlt = A[r][k] * inv;
+      const double mlt = A[r][k] * inv[k];
 #pragma unroll
       for (int q = k; q < 6; ++q) A[r][q] = fma(-mlt, A[k][q], A[r][q]);
     }
@@ -172,7 +221,7 @@ __device__ __forceinline__ bool square_stencil(const double* xi, const double* e
     double acc = A[k][5];
 #pragma unroll
     for (int q = k + 1; q < 5; ++q) acc = fma(-A[k][q], f[q], acc);
-    f[k] = acc / A[k][k];
+    f[k] = acc * inv[k];
   }
   bool ok = true;
 #pragma unroll
@@ -190,6 +239,124 @@ __device__ __forceinline__ bool square_stencil(const double* xi, const double* e
   return ok;
 }
 
+// Least-change correction of the proposal f0 (active positions of the 8
+// columns) onto V f = b: Cholesky of the Gram matrix V V^T (pivots checked
+// against kGramPivot of its largest diagonal entry), FP64.  Writes the
+// corrected weights (0 on inactive positions); returns 0 on success, 1 if a
+// weight is negative or the residual too large, 2 if the Gram matrix is
+// nearly singular.
+__device__ __forceinline__ int least_change(const double* xi, const double* eta, const double* f0s, unsigned act,
+                                            double* fs) {
+  double V[5][kSup];
+#pragma unroll
+  for (int s = 0; s < kSup; ++s) {
+    const bool on = (act >> s) & 1u;
+    V[0][s] = on ? xi[s] : 0.0;
+    V[1][s] = on ? eta[s] : 0.0;
+    V[2][s] = on ? xi[s] * xi[s] : 0.0;
+    V[3][s] = on ? xi[s] * eta[s] : 0.0;
+    V[4][s] = on ? eta[s] * eta[s] : 0.0;
+    fs[s] = on ? f0s[s] : 0.0;
+  }
+  const double b[5] = {0.0, 0.0, 2.0, 0.0, 2.0};
+  double G[5][5], r[5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    double acc = 0.0;
+#pragma unroll
+    for (int s = 0; s < kSup; ++s) acc = fma(V[a][s], fs[s], acc);
+    r[a] = b[a] - acc;
+#pragma unroll
+    for (int e = 0; e <= a; ++e) {
+      double g = 0.0;
+#pragma unroll
+      for (int s = 0; s < kSup; ++s) g = fma(V[a][s], V[e][s], g);
+      G[a][e] = g;
+    }
+  }
+  unsigned long long gmax = 0;
+#pragma unroll
+  for (int a = 0; a < 5; ++a) gmax = abs_bits(G[a][a]) > gmax ? abs_bits(G[a][a]) : gmax;
+  const long long piv_min = __double_as_longlong(kGramPivot * __longlong_as_double((long long)gmax));
+  double dinv[5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    double d = G[a][a];
+#pragma unroll
+    for (int e = 0; e < a; ++e) d = fma(-G[a][e], G[a][e], d);
+    if (!(__double_as_longlong(d) > piv_min)) return 2;  // also catches d <= 0
+    dinv[a] = rsqrt64(d);
+    G[a][a] = d * dinv[a];
+#pragma unroll
+    for (int q = a + 1; q < 5; ++q) {
+      double s3 = G[q][a];
+#pragma unroll
+      for (int e = 0; e < a; ++e) s3 = fma(-G[q][e], G[a][e], s3);
+      G[q][a] = s3 * dinv[a];
+    }
+  }
+  double w[5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    double s3 = r[a];
+#pragma unroll
+    for (int e = 0; e < a; ++e) s3 = fma(-G[a][e], w[e], s3);
+    w[a] = s3 * dinv[a];
+  }
+#pragma unroll
+  for (int a = 4; a >= 0; --a) {
+    double s3 = w[a];
+#pragma unroll
+    for (int e = a + 1; e < 5; ++e) s3 = fma(-G[e][a], w[e], s3);
+    w[a] = s3 * dinv[a];
+  }
+  bool nonneg = true;
+#pragma unroll
+  for (int s = 0; s < kSup; ++s) {
+    double acc = fs[s];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) acc = fma(V[a][s], w[a], acc);
+    const bool on = (act >> s) & 1u;
+    fs[s] = on ? acc : 0.0;
+    nonneg = nonneg && nonneg_bits(fs[s]);
+  }
+  const unsigned long long lim = abs_bits(kAcceptResid);
+  bool small_res = true;
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    double acc = -b[a];
+#pragma unroll
+    for (int s = 0; s < kSup; ++s) acc = fma(V[a][s], fs[s], acc);
+    small_res = small_res && abs_bits(acc) <= lim;
+  }
+  return nonneg && small_res ? 0 : 1;
+}
+
+// Writes an accepted stencil (positions `act` of the 8 columns, in order).
+__device__ __forceinline__ double write_stencil(int i, const int* js, const double* fs, unsigned act, int* cols,
+                                                double* f, double* fii, uint8_t* status) {
+  int* crow = cols + (size_t)i * VRM_STENCIL_W;
+  double* frow = f + (size_t)i * VRM_STENCIL_W;
+  double sum = 0.0;
+  int o = 0;
+#pragma unroll
+  for (int s = 0; s < kSup; ++s) {
+    if ((act >> s) & 1u) {
+      crow[o] = js[s];
+      frow[o] = fs[s];
+      sum = __dadd_rn(sum, fs[s]);
+      ++o;
+    }
+  }
+  for (; o < VRM_STENCIL_W; ++o) {
+    crow[o] = -1;
+    frow[o] = 0.0;
+  }
+  fii[i] = -sum;
+  status[i] = VRM_LP_LEARNED;
+  return sum;
+}
+
 // One thread per listed particle.  Accepted stencils are written like the
 // LP's (columns in slot order, f~, f~_ii = -sum in that order, status
 // VRM_LP_LEARNED); rejected particles are appended to reject_list (if given)
@@ -197,11 +364,11 @@ __device__ __forceinline__ bool square_stencil(const double* xi, const double* e
 __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restrict__ x, const double* __restrict__ y,
                                                  const int* __restrict__ list, const int* __restrict__ list_count,
                                                  int m_bound, const int* __restrict__ slots, const float* __restrict__ f0,
-                                                 int* __restrict__ cols, double* __restrict__ f,
-                                                 double* __restrict__ fii, uint8_t* __restrict__ status,
-                                                 int* __restrict__ reject_list, int* __restrict__ reject_count,
-                                                 DevStats* __restrict__ ds, const double* __restrict__ dt_dev,
-                                                 double nu) {
+                                                 const int* __restrict__ small, int* __restrict__ cols,
+                                                 double* __restrict__ f, double* __restrict__ fii,
+                                                 uint8_t* __restrict__ status, int* __restrict__ reject_list,
+                                                 int* __restrict__ reject_count, DevStats* __restrict__ ds,
+                                                 const double* __restrict__ dt_dev, double nu) {
   const int m = list_count ? *list_count : m_bound;
   const double nu_dt = dt_dev ? nu * *dt_dev : 0.0;
   const double inv_h2 = 1.0 / (c.h * c.h);
@@ -210,221 +377,106 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
   const long stride = (long)gridDim.x * blockDim.x;
   for (long base = (long)blockIdx.x * blockDim.x; base < m; base += stride) {
     const long t = base + threadIdx.x;
-    bool accepted = false, active = t < m;
+    bool accepted = false;
+    const bool active = t < m;
     int i = -1;
     if (active) {
       i = list ? list[t] : (int)t;
       const float* p = f0 + (size_t)t * kSlots;
       const int* sl = slots + (size_t)t * kSlots;
-      // support: rank each positive valid slot among the positive valid ones
-      float v[kSlots];
-      unsigned ok_mask = 0;
+      // candidates: slots holding a small-neighbourhood particle with a
+      // positive proposal (at most 8, one per segment), in slot order
+      const int4 s0 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[0];
+      const int4 s1 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[1];
+      unsigned cand = 0;
 #pragma unroll
       for (int k = 0; k < kSlots; ++k) {
-        v[k] = p[k];
-        if (sl[k] >= 0 && v[k] > 0.0f) ok_mask |= 1u << k;
+        const int j = sl[k];
+        const bool in_small = j >= 0 && (j == s0.x || j == s0.y || j == s0.z || j == s0.w || j == s1.x ||
+                                         j == s1.y || j == s1.z || j == s1.w);
+        if (in_small && p[k] > 0.0f) cand |= 1u << k;
       }
-      unsigned sup = 0, sup5 = 0;
+      const int nc = __popc(cand) < kSup ? __popc(cand) : kSup;
+      int js[kSup], kk[kSup];
+      float cv[kSup];
+      double xi[kSup], eta[kSup], f0s[kSup];
+      const double xi0 = x[i], yi0 = y[i];
 #pragma unroll
-      for (int k = 0; k < kSlots; ++k) {
-        if (!((ok_mask >> k) & 1u)) continue;
+      for (int s = 0; s < kSup; ++s) {
+        kk[s] = s < nc ? (int)__fns(cand, 0, s + 1) : 0;
+        js[s] = s < nc ? sl[kk[s]] : -1;
+        cv[s] = s < nc ? p[kk[s]] : 0.0f;
+        f0s[s] = (double)cv[s];
+        xi[s] = s < nc ? __dmul_rn(__dsub_rn(x[js[s]], xi0), c.inv_h) : 0.0;
+        eta[s] = s < nc ? __dmul_rn(__dsub_rn(y[js[s]], yi0), c.inv_h) : 0.0;
+      }
+      // rank of every candidate (larger proposal first, ties to the lower slot)
+      unsigned in5 = 0;
+#pragma unroll
+      for (int s = 0; s < kSup; ++s) {
         int rank = 0;
 #pragma unroll
-        for (int q = 0; q < kSlots; ++q)
-          rank += ((ok_mask >> q) & 1u) && (v[q] > v[k] || (v[q] == v[k] && q < k));
-        if (rank < kSup) sup |= 1u << k;
-        if (rank < 5) sup5 |= 1u << k;
+        for (int q = 0; q < kSup; ++q)
+          rank += (q < nc && q != s) && (cv[q] > cv[s] || (cv[q] == cv[s] && q < s));
+        if (s < nc && rank < 5) in5 |= 1u << s;
       }
-      const int ns = __popc(sup);
-      // the network's basis alone: the square system on the top five slots
-      if (__popc(sup5) == 5) {
-        int j5[5];
-        double xi5[5], eta5[5], f5[5];
-        int q5 = 0;
-        const double xi0 = x[i], yi0 = y[i];
+      // the network's basis alone: the square system on the top five
+      if (nc >= 5) {
+        double x5[5], e5[5], f5[5];
 #pragma unroll
-        for (int k = 0; k < kSlots; ++k) {
-          if (((sup5 >> k) & 1u) && q5 < 5) {
-            j5[q5] = sl[k];
-            ++q5;
+        for (int q = 0; q < 5; ++q) {
+          const int pos = (int)__fns(in5, 0, q + 1);
+          double a = xi[0], b = eta[0];
+#pragma unroll
+          for (int s = 1; s < kSup; ++s) {
+            a = pos == s ? xi[s] : a;
+            b = pos == s ? eta[s] : b;
           }
+          x5[q] = a;
+          e5[q] = b;
         }
+        if (square_stencil(x5, e5, f5)) {
+          double fs[kSup];
+          int q = 0;
 #pragma unroll
-        for (int s2 = 0; s2 < 5; ++s2) {
-          xi5[s2] = __dmul_rn(__dsub_rn(x[j5[s2]], xi0), c.inv_h);
-          eta5[s2] = __dmul_rn(__dsub_rn(y[j5[s2]], yi0), c.inv_h);
-        }
-        if (square_stencil(xi5, eta5, f5)) {
-          accepted = true;
-          int* crow = cols + (size_t)i * VRM_STENCIL_W;
-          double* frow = f + (size_t)i * VRM_STENCIL_W;
-          double sum = 0.0;
+          for (int s = 0; s < kSup; ++s) {
+            double v = 0.0;
 #pragma unroll
-          for (int s2 = 0; s2 < VRM_STENCIL_W; ++s2) {
-            crow[s2] = s2 < 5 ? j5[s2] : -1;
-            frow[s2] = s2 < 5 ? f5[s2] : 0.0;
-            if (s2 < 5) sum = __dadd_rn(sum, f5[s2]);
+            for (int u = 0; u < 5; ++u) v = (((in5 >> s) & 1u) && q == u) ? f5[u] : v;
+            fs[s] = v;
+            q += (in5 >> s) & 1u;
           }
-          fii[i] = -sum;
-          status[i] = VRM_LP_LEARNED;
+          const double sum = write_stencil(i, js, fs, in5, cols, f, fii, status);
           const double qr = __dmul_rn(__dmul_rn(nu_dt, sum), inv_h2);
           st_ratio = qr > st_ratio ? qr : st_ratio;
+          accepted = true;
           ++n_square;
         }
       }
-      if (!accepted && ns >= 5) {
-
-        int js[kSup];
-        double xi[kSup], eta[kSup], f0s[kSup], fs[kSup];
-        int q = 0;
+      // least change on all candidates, dropping the smallest corrected weight
+      unsigned act = nc >= 5 ? (1u << nc) - 1u : 0u;
+      for (int attempt = 0; attempt <= kMaxDrops && !accepted && __popc(act) >= 5; ++attempt) {
+        double fs[kSup];
+        const int rc = least_change(xi, eta, f0s, act, fs);
+        if (rc == 0) {
+          const double sum = write_stencil(i, js, fs, act, cols, f, fii, status);
+          const double qr = __dmul_rn(__dmul_rn(nu_dt, sum), inv_h2);
+          st_ratio = qr > st_ratio ? qr : st_ratio;
+          accepted = true;
+          break;
+        }
+        if (rc == 2 || __popc(act) == 5) break;
+        int worst = 0;
+        unsigned long long wv = ~0ull;
 #pragma unroll
-        for (int k = 0; k < kSlots; ++k) {
-          if (((sup >> k) & 1u) && q < kSup) {
-            js[q] = sl[k];
-            f0s[q] = (double)v[k];
-            ++q;
+        for (int s = 0; s < kSup; ++s) {
+          const unsigned long long key = ordered_bits(fs[s]);
+          if (((act >> s) & 1u) && key <= wv) {
+            wv = key;
+            worst = s;
           }
         }
-        const double xi0 = x[i], yi0 = y[i];
-#pragma unroll
-        for (int s2 = 0; s2 < kSup; ++s2) {
-          if (s2 < ns) {
-            xi[s2] = __dmul_rn(__dsub_rn(x[js[s2]], xi0), c.inv_h);
-            eta[s2] = __dmul_rn(__dsub_rn(y[js[s2]], yi0), c.inv_h);
-          } else {
-            js[s2] = -1;
-            xi[s2] = eta[s2] = f0s[s2] = 0.0;
-          }
-        }
-        const double b[5] = {0.0, 0.0, 2.0, 0.0, 2.0};
-        unsigned act = (1u << ns) - 1u;  // support positions still in S
-        for (int attempt = 0; attempt <= kMaxDrops; ++attempt) {
-          const int na = __popc(act);
-          if (na < 5) break;
-          double V[5][kSup];
-#pragma unroll
-          for (int s2 = 0; s2 < kSup; ++s2) {
-            const bool on = (act >> s2) & 1u;
-            V[0][s2] = on ? xi[s2] : 0.0;
-            V[1][s2] = on ? eta[s2] : 0.0;
-            V[2][s2] = on ? xi[s2] * xi[s2] : 0.0;
-            V[3][s2] = on ? xi[s2] * eta[s2] : 0.0;
-            V[4][s2] = on ? eta[s2] * eta[s2] : 0.0;
-            fs[s2] = on ? f0s[s2] : 0.0;
-          }
-          // Gram matrix G = V V^T (lower triangle) and r = b - V f0
-          double G[5][5], r[5];
-#pragma unroll
-          for (int a = 0; a < 5; ++a) {
-            double acc = 0.0;
-#pragma unroll
-            for (int s2 = 0; s2 < kSup; ++s2) acc = fma(V[a][s2], fs[s2], acc);
-            r[a] = b[a] - acc;
-#pragma unroll
-            for (int e = 0; e <= a; ++e) {
-              double g = 0.0;
-#pragma unroll
-              for (int s2 = 0; s2 < kSup; ++s2) g = fma(V[a][s2], V[e][s2], g);
-              G[a][e] = g;
-            }
-          }
-          // Cholesky G = L L^T in place (lower triangle), pivots checked
-          double gmax = 0.0;
-#pragma unroll
-          for (int a = 0; a < 5; ++a) gmax = G[a][a] > gmax ? G[a][a] : gmax;
-          bool spd = true;
-          double dinv[5];
-#pragma unroll
-          for (int a = 0; a < 5; ++a) {
-            double d = G[a][a];
-#pragma unroll
-            for (int e = 0; e < a; ++e) d = fma(-G[a][e], G[a][e], d);
-            spd = spd && d > kGramPivot * gmax;
-            const double l = sqrt(d > 0.0 ? d : 1.0);
-            G[a][a] = l;
-            dinv[a] = 1.0 / l;
-#pragma unroll
-            for (int q2 = a + 1; q2 < 5; ++q2) {
-              double s3 = G[q2][a];
-#pragma unroll
-              for (int e = 0; e < a; ++e) s3 = fma(-G[q2][e], G[a][e], s3);
-              G[q2][a] = s3 * dinv[a];
-            }
-          }
-          if (!spd) break;  // nearly dependent rows: reject
-          // solve L z = r, L^T w = z
-          double w[5];
-#pragma unroll
-          for (int a = 0; a < 5; ++a) {
-            double s3 = r[a];
-#pragma unroll
-            for (int e = 0; e < a; ++e) s3 = fma(-G[a][e], w[e], s3);
-            w[a] = s3 * dinv[a];
-          }
-#pragma unroll
-          for (int a = 4; a >= 0; --a) {
-            double s3 = w[a];
-#pragma unroll
-            for (int e = a + 1; e < 5; ++e) s3 = fma(-G[e][a], w[e], s3);
-            w[a] = s3 * dinv[a];
-          }
-          // f = f0 + V^T w on S, then the sign test and the residual in FP64
-          bool nonneg = true;
-#pragma unroll
-          for (int s2 = 0; s2 < kSup; ++s2) {
-            double acc = fs[s2];
-#pragma unroll
-            for (int a = 0; a < 5; ++a) acc = fma(V[a][s2], w[a], acc);
-            const bool on = (act >> s2) & 1u;
-            fs[s2] = on ? acc : 0.0;
-            nonneg = nonneg && fs[s2] >= 0.0;
-          }
-          double rmax = 0.0;
-#pragma unroll
-          for (int a = 0; a < 5; ++a) {
-            double acc = 0.0;
-#pragma unroll
-            for (int s2 = 0; s2 < kSup; ++s2) acc = fma(V[a][s2], fs[s2], acc);
-            const double e2 = fabs(acc - b[a]);
-            rmax = e2 > rmax ? e2 : rmax;
-          }
-          if (nonneg && rmax <= kAcceptResid) {
-            accepted = true;
-            int* crow = cols + (size_t)i * VRM_STENCIL_W;
-            double* frow = f + (size_t)i * VRM_STENCIL_W;
-            double sum = 0.0;
-            int o = 0;
-#pragma unroll
-            for (int s2 = 0; s2 < kSup; ++s2) {
-              if ((act >> s2) & 1u) {
-                crow[o] = js[s2];
-                frow[o] = fs[s2];
-                sum = __dadd_rn(sum, fs[s2]);
-                ++o;
-              }
-            }
-            for (; o < VRM_STENCIL_W; ++o) {
-              crow[o] = -1;
-              frow[o] = 0.0;
-            }
-            fii[i] = -sum;
-            status[i] = VRM_LP_LEARNED;
-            const double qr = __dmul_rn(__dmul_rn(nu_dt, sum), inv_h2);
-            st_ratio = qr > st_ratio ? qr : st_ratio;
-            break;
-          }
-          if (na == 5) break;
-          // drop the smallest corrected weight (ties: the later position)
-          int worst = 0;
-          double wv = 1e308;
-#pragma unroll
-          for (int s2 = 0; s2 < kSup; ++s2)
-            if (((act >> s2) & 1u) && fs[s2] <= wv) {
-              wv = fs[s2];
-              worst = s2;
-            }
-          act &= ~(1u << worst);
-        }
+        act &= ~(1u << worst);
       }
       if (accepted) {
         ++n_ok;
@@ -489,25 +541,31 @@ __global__ void k_targets(const int* __restrict__ list, int m, const int* __rest
   }
 }
 
-cudaError_t learned_features(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
-                             int m_bound, const int* nbr_count, const int* nbr_idx, __nv_bfloat16* X, int* slots,
-                             cudaStream_t s) {
-  if (m_bound <= 0) return cudaSuccess;
+cudaError_t learned_features(const Consts& c, const double* x, const double* y, int n_bound, const int* n_dev,
+                             float2* xyf, const int* list, const int* list_count, int m_bound, const int* nbr_count,
+                             const int* nbr_idx, __nv_bfloat16* X, int* slots, cudaStream_t s) {
+  if (m_bound <= 0 || n_bound <= 0) return cudaSuccess;
+  long mb = ((long)n_bound + 255) / 256;
+  if (mb > 8L * sm_count()) mb = 8L * sm_count();
+  k_mirror<<<(int)mb, 256, 0, s>>>(x, y, n_bound, n_dev, xyf);
+  note_launch();
   long blocks = ((long)m_bound * 32 + 255) / 256;
   if (blocks > 16L * sm_count()) blocks = 16L * sm_count();
-  k_features<<<(int)blocks, 256, 0, s>>>(c, x, y, list, list_count, m_bound, nbr_count, nbr_idx, X, slots);
+  k_features<<<(int)blocks, 256, 0, s>>>(c, xyf, list, list_count, m_bound, nbr_count, nbr_idx, X, slots);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t learned_project(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
-                            int m_bound, const int* slots, const float* f0, int* cols, double* f, double* fii,
+                            int m_bound, const int* slots, const float* f0, const int* small, int* cols, double* f,
+                            double* fii,
                             uint8_t* status, int* reject_list, int* reject_count, DevStats* ds, const double* dt_dev,
                             double nu, cudaStream_t s) {
   if (m_bound <= 0) return cudaSuccess;
   int blocks = (m_bound + 127) / 128;
   if (blocks > 16 * sm_count()) blocks = 16 * sm_count();
-  k_project<<<blocks, 128, 0, s>>>(c, x, y, list, list_count, m_bound, slots, f0, cols, f, fii, status, reject_list,
+  k_project<<<blocks, 128, 0, s>>>(c, x, y, list, list_count, m_bound, slots, f0, small, cols, f, fii, status,
+                                   reject_list,
                                    reject_count, ds, dt_dev, nu);
   note_launch();
   return cudaGetLastError();

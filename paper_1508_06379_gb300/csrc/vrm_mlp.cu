@@ -3,7 +3,7 @@
 //
 // Network: 96 inputs (the K = 32 neighbour slots' scaled offsets xi_x, xi_y
 // and mask; padded to 128 columns with zeros) -> 256 -> 256 -> 256 -> 32,
-// GELU (erf form) after each hidden layer.  Parameters are kept as one fp32
+// GELU (tanh form) after each hidden layer.  Parameters are kept as one fp32
 // vector [W1 (256x96), b1, W2 (256x256), b2, W3, b3, W4 (32x256), b4]; the
 // GEMMs read bf16 copies (W1 padded to 256x128) and, for the backward pass,
 // transposed bf16 copies.
@@ -72,9 +72,26 @@ struct Epi {
   int* error;            // set on a wait that gave up
 };
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU in its tanh form, 0.5 z (1 + tanh(c (z + a z^3))) with c = sqrt(2/pi),
+// a = 0.044715, on the hardware tanh (tanh.approx.f32, relative error about
+// 2^-11, below the bf16 rounding of the activations).
+constexpr float kGeluC = 0.7978845608028654f, kGeluA = 0.044715f;
+__device__ __forceinline__ float tanh_hw(float u) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
+  return t;
+}
+__device__ __forceinline__ float gelu(float z) {
+  const float u = kGeluC * fmaf(kGeluA * z, z * z, z);
+  const float hz = 0.5f * z;
+  return fmaf(hz, tanh_hw(u), hz);
+}
+// d/dz of the same: 0.5 (1 + t) + 0.5 z (1 - t^2) c (1 + 3 a z^2).
 __device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+  const float z2 = z * z;
+  const float t = tanh_hw(kGeluC * fmaf(kGeluA * z, z2, z));
+  const float du = kGeluC * fmaf(3.0f * kGeluA, z2, 1.0f);
+  return fmaf(0.5f * z * du, fmaf(-t, t, 1.0f), 0.5f * (1.0f + t));
 }
 
 template <int NT>
@@ -378,13 +395,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         for (int c0 = cg * 64; c0 < cg * 64 + 64; c0 += 16) {
           float v[16];
           umma::tmem_ld16(trow + (uint32_t)c0, v);
-          __align__(16) bf16 hv[16];
+          __align__(16) __nv_bfloat162 hv[8];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) hv[i] = __float2bfloat16_rn(gelu(v[i] + b[c0 + i]));
+          for (int i = 0; i < 8; ++i)
+            hv[i] = __floats2bfloat162_rn(gelu(v[2 * i] + b[c0 + 2 * i]), gelu(v[2 * i + 1] + b[c0 + 2 * i + 1]));
           uint8_t* slab = H + (size_t)(c0 >> 6) * kBM * kBK * 2 + (size_t)r * 128;
           const int ch = (c0 & 63) >> 3;
           *reinterpret_cast<uint4*>(slab + (((ch) ^ (r & 7)) << 4)) = *reinterpret_cast<uint4*>(&hv[0]);
-          *reinterpret_cast<uint4*>(slab + (((ch + 1) ^ (r & 7)) << 4)) = *reinterpret_cast<uint4*>(&hv[8]);
+          *reinterpret_cast<uint4*>(slab + (((ch + 1) ^ (r & 7)) << 4)) = *reinterpret_cast<uint4*>(&hv[4]);
         }
       } else if (cg < 2) {
         const int c0 = cg * 16;

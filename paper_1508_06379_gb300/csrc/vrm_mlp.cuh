@@ -28,11 +28,14 @@ cudaError_t mlp_forward(vrm_mlp* net, const CUtensorMap& mX, int rows_bound, con
                         cudaStream_t s);
 
 // vrm_learned.cu
-cudaError_t learned_features(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
-                             int m_bound, const int* nbr_count, const int* nbr_idx, __nv_bfloat16* X, int* slots,
-                             cudaStream_t s);
+// Input rows and slot maps of the listed particles; xyf (n_bound entries)
+// receives the fp32 positions first.
+cudaError_t learned_features(const Consts& c, const double* x, const double* y, int n_bound, const int* n_dev,
+                             float2* xyf, const int* list, const int* list_count, int m_bound, const int* nbr_count,
+                             const int* nbr_idx, __nv_bfloat16* X, int* slots, cudaStream_t s);
 cudaError_t learned_project(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
-                            int m_bound, const int* slots, const float* f0, int* cols, double* f, double* fii,
+                            int m_bound, const int* slots, const float* f0, const int* small, int* cols, double* f,
+                            double* fii,
                             uint8_t* status, int* reject_list, int* reject_count, DevStats* ds, const double* dt_dev,
                             double nu, cudaStream_t s);
 cudaError_t learned_targets(const int* list, int m, const int* slots, const int* cols, const double* f, float* T,

@@ -108,13 +108,13 @@ def test_projection_matches_oracle(lib, orc):
         base = oracle_slot_stencil(ow, i, S[i])
         noise = rng.normal(0, 0.05, 32) * (base > 0) + (rng.random(32) < 0.1) * rng.uniform(0, 0.05, 32)
         f0[i] = np.where(S[i] >= 0, base + noise, 0.0)
-    stc, acc = ctx.learned_project(xd, yd, lst, slots, cu(f0), n)
+    stc, acc = ctx.learned_project(xd, yd, lst, slots, cu(f0), n, nb["small"])
     cols = stc["cols"].cpu().numpy().reshape(n, W)
     f = stc["f"].cpu().numpy().reshape(n, W)
     status = stc["status"].cpu().numpy()
     n_acc, mismatched = 0, 0
     for i in range(n):
-        ok, js, fo, fii = omlp.learned_stencil(x, y, h, i, S[i], f0[i])
+        ok, js, fo, fii = omlp.learned_stencil(x, y, h, i, S[i], f0[i], onb["small"][i])
         got = status[i] == lib.LP_LEARNED
         if ok != got:
             # only borderline cases may differ: a weight within rounding of zero

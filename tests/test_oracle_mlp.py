@@ -34,9 +34,14 @@ def test_bf16_rounding():
 
 def test_gelu_closed_forms():
     assert mlp.gelu(np.array([0.0]))[0] == 0.0
-    # GELU(1) = Phi(1) = 0.8413447460685429..., GELU(-1) = -(1 - Phi(1))
-    assert abs(mlp.gelu(np.array([1.0]))[0] - 0.8413447460685429) < 1e-15
-    assert abs(mlp.gelu(np.array([-1.0]))[0] + 0.15865525393145707) < 1e-15
+    # tanh form at 1: 0.5 (1 + tanh(sqrt(2/pi) 1.044715)) = 0.8411919906082768; it
+    # stays within 2e-4 of the erf form Phi(1) = 0.8413447460685429
+    assert abs(mlp.gelu(np.array([1.0]))[0] - 0.5 * (1 + math.tanh(math.sqrt(2 / math.pi) * 1.044715))) < 1e-15
+    assert abs(mlp.gelu(np.array([1.0]))[0] - 0.8413447460685429) < 2e-4
+    assert abs(mlp.gelu(np.array([-1.0]))[0] + 0.15865525393145707) < 2e-4
+    # odd part: gelu(z) - gelu(-z) = z
+    z = np.linspace(-5, 5, 101)
+    assert np.max(np.abs(mlp.gelu(z) - mlp.gelu(-z) - z)) < 1e-14
     assert abs(mlp.gelu(np.array([12.0]))[0] - 12.0) < 1e-12 and abs(mlp.gelu(np.array([-12.0]))[0]) < 1e-12
     z = np.linspace(-6, 6, 241)
     e = 1e-6
@@ -261,3 +266,21 @@ def test_top_five_basis_gives_the_vertex():
     ok, js, f, fii = mlp.learned_stencil(x, y, 1.0, 0, slots, f0)
     assert ok and js == [1, 2, 3, 5, 7]
     assert np.allclose(f, [1.0, 0.0, 1.0, 1.0, 1.0], rtol=0, atol=1e-14) and fii == -4.0
+
+
+def test_candidates_are_the_small_neighbourhood():
+    # a second ring of neighbours carries large proposals but is not in the
+    # small neighbourhood: only the eight closest (one per segment) count
+    off = [(1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1)]
+    x = np.array([0.0] + [a for a, _ in off] + [1.5 * a for a, _ in off])
+    y = np.array([0.0] + [b for _, b in off] + [1.5 * b for _, b in off])
+    row = list(range(1, 17))
+    X, slots = mlp.features(x, y, 1.0, 0, row)
+    f0 = np.zeros(32, dtype=np.float32)
+    for k in range(16):
+        j = slots[k]
+        f0[k] = 5.0 if j > 8 else (1.0 if j in (1, 3, 5, 7) else 0.01)
+    small = np.arange(1, 9)
+    ok, js, f, _ = mlp.learned_stencil(x, y, 1.0, 0, slots, f0, small)
+    assert ok and set(js) <= set(range(1, 9))
+    assert mlp.support(f0, slots, allowed=small) == sorted(k for k in range(16) if slots[k] <= 8)
