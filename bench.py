@@ -603,6 +603,50 @@ LEARNED_DESC = ("jittered lattice %dx%d (h=1e-3, jitter 0.3h), 8-Gaussian mixtur
                 "on; stencils from the trained network (corrected, LP fallback) vs the LP alone")
 
 
+def lamb_oseen_weak_errors(vrm, net, h=1 / 128):
+    """Heat-equation Lamb-Oseen run (Gamma = 1, nu = 1e-3, t = 1 -> 1.125, Euler
+    with dt = (1/8)(r h)^2/(4 nu)) with the LP stencils and with the learned
+    ones; the weak error against the closed form (Gaussian test functions of
+    width 0.03 at five centres) of both."""
+    import numpy as np
+    import torch
+
+    import vrm_inputs
+    gamma, nu, t0, t1 = 1.0, 1e-3, 1.0, 1.125
+    centres = [(0.0, 0.0), (0.03, 0.0), (0.05, 0.04), (-0.08, 0.02), (0.0, -0.1)]
+    out = {}
+    for name in ("lp", "learned"):
+        x, y, g = vrm_inputs.lamb_oseen_lattice(h, gamma, nu, t0, eps=1e-8)
+        dt = (0.5 * h) ** 2 / (4 * nu) / 8
+        steps = int(round((t1 - t0) / dt))
+        dt = (t1 - t0) / steps
+        ctx = vrm.VRM(h=h, nu=nu)
+        if name == "learned":
+            ctx.set_mlp(net)
+        n = len(x)
+        cap = 8 * n + 4096
+        xb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        yb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        xb[:n] = torch.from_numpy(x).cuda()
+        yb[:n] = torch.from_numpy(y).cuda()
+        bufs = [torch.zeros(cap, dtype=torch.float64, device="cuda") for _ in range(2)]
+        bufs[0][:n] = torch.from_numpy(g).cuda()
+        learned = diffused = 0
+        for k in range(steps):
+            n, st = ctx.step(xb, yb, n, bufs[k % 2], bufs[(k + 1) % 2], dt)
+            learned += st["learned_ok"]
+            diffused += st["n_diffused"]
+        X, Y, G = xb[:n].cpu().numpy(), yb[:n].cpu().numpy(), bufs[steps % 2][:n].cpu().numpy()
+        s2 = 2 * nu * t1 + 0.03 ** 2
+        err = max(abs(np.sum(G * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * 0.03 ** 2))) -
+                      gamma * 0.03 ** 2 / s2 * np.exp(-(cx * cx + cy * cy) / (2 * s2))) / gamma
+                  for cx, cy in centres)
+        out[name] = {"weak_error": float(err), "steps": steps, "n_final": int(n),
+                     "learned_fraction": learned / max(1, diffused)}
+    out["h"] = h
+    return out
+
+
 def run_learned(args):
     """The 4M-particle cloud stepped with the learned proposal and with the LP
     alone: throughput of both, acceptance, and how far the two results are
@@ -687,6 +731,7 @@ def run_learned(args):
                     "lp_small_solved": int(st["lp_small_solved"]), "stage_ms": b["stage"],
                     "increment_rel_diff_vs_lp": rel},
         "speedup_vs_plain": b["value"] / a["value"],
+        "lamb_oseen": lamb_oseen_weak_errors(vrm, net),
     }
     print(json.dumps(line))
     sys.stdout.flush()

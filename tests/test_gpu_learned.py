@@ -213,3 +213,55 @@ def test_trained_network_steps(lib, orc, trained):
     ctx.set_mlp(None)
     ctx.set_mlp(net)
     check_step(lib, orc, x, y, g, h, ctx, (0.5 * h) ** 2 / (4 * NU) / 8)
+
+
+def weak_error(x, y, g, gamma, nu, t, centres, sigma):
+    """max_k |sum_i Gamma_i phi_k(x_i) - int omega(t) phi_k| / Gamma with
+    Gaussian test functions phi_k of width sigma (closed form of the
+    Lamb-Oseen integral: Gamma s^2/(2 nu t + s^2) exp(-|c|^2/(2 (2 nu t + s^2))))."""
+    err = 0.0
+    s2 = 2 * nu * t + sigma ** 2
+    for cx, cy in centres:
+        num = np.sum(g * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * sigma ** 2)))
+        ex = gamma * sigma ** 2 / s2 * np.exp(-(cx * cx + cy * cy) / (2 * s2))
+        err = max(err, abs(num - ex) / gamma)
+    return err
+
+
+def test_learned_and_lp_paths_reach_the_same_lamb_oseen_error(lib, trained):
+    # heat-equation Lamb-Oseen run (Gamma = 1, nu = 1e-3, t0 = 1 -> 1.125,
+    # dt = (1/8)(r h)^2/(4 nu)) on the h = 1/64 lattice, once with the LP
+    # stencils and once with the learned ones: both errors against the closed
+    # form are of the same size (the learned stencils are valid ones)
+    net, _ = trained
+    gamma, nu, t0, t1, h = 1.0, 1e-3, 1.0, 1.125, 1 / 64
+    centres = [(0.0, 0.0), (0.03, 0.0), (0.05, 0.04), (-0.08, 0.02), (0.0, -0.1)]
+    errs = {}
+    for name in ("lp", "learned"):
+        x, y, g = vrm_inputs.lamb_oseen_lattice(h, gamma, nu, t0, eps=1e-8)
+        g0 = g.sum()
+        dt = (0.5 * h) ** 2 / (4 * nu) / 8
+        steps = int(round((t1 - t0) / dt))
+        dt = (t1 - t0) / steps
+        ctx = lib.VRM(h=h, nu=nu)
+        if name == "learned":
+            ctx.set_mlp(net)
+        cap = 8 * len(x) + 4096
+        n = len(x)
+        xb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        yb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        xb[:n] = cu(x)
+        yb[:n] = cu(y)
+        gi = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        gi[:n] = cu(g)
+        go = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        learned = 0
+        for _ in range(steps):
+            n, st = ctx.step(xb, yb, n, gi, go, dt)
+            gi, go = go, gi
+            learned += st["learned_ok"]
+        X, Y, G = xb[:n].cpu().numpy(), yb[:n].cpu().numpy(), gi[:n].cpu().numpy()
+        assert abs(G.sum() - g0) < 1e-12
+        errs[name] = (weak_error(X, Y, G, gamma, nu, t1, centres, 0.03), learned)
+    assert errs["learned"][1] > 0
+    assert errs["learned"][0] <= 2.0 * errs["lp"][0] + 1e-6, errs
