@@ -34,27 +34,46 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
     const bool self_src = j < n_gamma && diffused[j];
     const double gj = j < n_gamma ? gamma[j] : 0.0;
     const double selfv = self_src ? __dmul_rn(fii[j], gj) : 0.0;
-    bool self_done = !self_src;
-    double acc = 0.0;
+    // integer pass: which row entries are sources whose stencil holds j (and
+    // in which slot, 4 bits per entry), and where the self term goes (before
+    // the first i > j)
+    unsigned match = 0;
+    unsigned long long slot_lo = 0, slot_hi = 0;
+    int selfpos = cnt;
     for (int t = 0; t < cnt; ++t) {
       const int i = row[t];
-      if (!self_done && i > j) {
-        acc = __dadd_rn(acc, selfv);
-        self_done = true;
-      }
+      if (selfpos == cnt && i > j) selfpos = t;
       if (i >= n_gamma || !diffused[i]) continue;
       const int4* cr = reinterpret_cast<const int4*>(cols + (size_t)i * VRM_STENCIL_W);
       const int4 a = cr[0], b = cr[1];
       int slot = -1;
-      slot = (a.x == j) ? 0 : slot;
-      slot = (a.y == j) ? 1 : slot;
-      slot = (a.z == j) ? 2 : slot;
-      slot = (a.w == j) ? 3 : slot;
-      slot = (b.x == j) ? 4 : slot;
-      slot = (b.y == j) ? 5 : slot;
-      slot = (b.z == j) ? 6 : slot;
       slot = (b.w == j) ? 7 : slot;
-      if (slot >= 0) acc = __dadd_rn(acc, __dmul_rn(f[(size_t)i * VRM_STENCIL_W + slot], gamma[i]));
+      slot = (b.z == j) ? 6 : slot;
+      slot = (b.y == j) ? 5 : slot;
+      slot = (b.x == j) ? 4 : slot;
+      slot = (a.w == j) ? 3 : slot;
+      slot = (a.z == j) ? 2 : slot;
+      slot = (a.y == j) ? 1 : slot;
+      slot = (a.x == j) ? 0 : slot;
+      if (slot < 0) continue;
+      match |= 1u << t;
+      if (t < 16)
+        slot_lo |= (unsigned long long)slot << (4 * t);
+      else
+        slot_hi |= (unsigned long long)slot << (4 * (t - 16));
+    }
+    // FP64 pass over the matches only, in ascending i
+    double acc = 0.0;
+    bool self_done = !self_src;
+    for (unsigned rest = match; rest; rest &= rest - 1) {
+      const int t = __ffs(rest) - 1;
+      if (!self_done && t >= selfpos) {
+        acc = __dadd_rn(acc, selfv);
+        self_done = true;
+      }
+      const int i = row[t];
+      const int slot = (int)(((t < 16 ? slot_lo >> (4 * t) : slot_hi >> (4 * (t - 16)))) & 15ull);
+      acc = __dadd_rn(acc, __dmul_rn(f[(size_t)i * VRM_STENCIL_W + slot], gamma[i]));
     }
     if (!self_done) acc = __dadd_rn(acc, selfv);
     const double dg = __dmul_rn(c.nu_over_h2, acc);
