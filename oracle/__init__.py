@@ -246,3 +246,73 @@ def pipeline(x, y, gamma, h, nu, r=0.5, R=2.0, c_diff=1.0, order=1, k_cap=32, ma
     w = solve_weights(x2, y2, d2, nb, h, order, fallback)
     dg = apply(n2, gamma, d2, w, c["nu_over_h2"])
     return dict(diffused=d2, x=x2, y=y2, rounds=rounds, open=open_, nb=nb, w=w, dgamma=dg, const=c)
+
+
+def lamb_oseen_velocity(x, y, gamma, nu, t, x0=0.0, y0=0.0):
+    """Azimuthal velocity of the Lamb-Oseen vortex (Sec. 6):
+    u_theta = Gamma/(2 pi r) (1 - exp(-r^2/(4 nu t))), as
+    (u, v) = (-(y - y0), x - x0) * k with k = Gamma/(2 pi r^2) * (-expm1(-r^2/(4 nu t)));
+    products and sums rounded separately, k = 0 at r = 0."""
+    dx = np.asarray(x, dtype=np.float64) - x0
+    dy = np.asarray(y, dtype=np.float64) - y0
+    r2 = dx * dx + dy * dy
+    with np.errstate(divide="ignore", invalid="ignore"):
+        a = r2 / ((4.0 * nu) * t)
+        k = (gamma / ((2.0 * np.pi) * r2)) * (-np.expm1(-a))
+    k = np.where(r2 > 0.0, k, 0.0)
+    return -dy * k, dx * k
+
+
+def rk3_step(x, y, gamma, h, nu, t, dt, vel=None, r=0.5, R=2.0, c_diff=1.0, order=1, k_cap=32, max_rounds=8,
+             fallback=True):
+    """One SSP-RK3 (Shu-Osher) step of dx/dt = u(x, t), dGamma/dt = L(x) Gamma
+    (the reduced operator of Sec. 3.5 with the diffused set fixed at the start
+    of the step): growth control and insertion once on the step's initial
+    cloud, neighbourhoods and weights at every stage's positions.
+        X1 = X0 + dt u(X0, t),           G1 = G0 + dt L(X0) G0
+        X2 = 3/4 X0 + 1/4 (X1 + dt u(X1, t + dt)),   G2 likewise with L(X1) G1
+        X3 = 1/3 X0 + 2/3 (X2 + dt u(X2, t + dt/2)), G3 likewise with L(X2) G2
+    vel: dict(gamma, nu, x0, y0) of the Lamb-Oseen field, or None (no
+    advection: the positions stay those of the start).  Products and sums
+    rounded separately.  Returns (x', y',
+    gamma', stats)."""
+    c = constants(h, r, R, nu, c_diff, order)
+    n = len(x)
+    diffused = reduce(gamma, c["c_bound"])
+    X0, Y0, rounds, open_ = insert(x, y, diffused, h, r, R, max_rounds)
+    n2 = len(X0)
+    d2 = np.zeros(n2, dtype=np.uint8)
+    d2[:n] = diffused
+    G0 = np.zeros(n2)
+    G0[:n] = gamma
+    third, two_thirds = 1.0 / 3.0, 2.0 / 3.0
+    coef = [(None, None), (0.75, 0.25), (third, two_thirds)]
+    times = [t, t + dt, t + 0.5 * dt]
+    Xs, Ys, Gs = X0, Y0, G0
+    stats = dict(n_in=n, n_out=n2, n_diffused=int(diffused.sum()), n_inserted=n2 - n, rounds=rounds,
+                 small_ok=0, full_ok=0, no_stencil=0)
+    for s in range(3):
+        nb = neighbours(Xs, Ys, h, r, R, k_cap)
+        w = solve_weights(Xs, Ys, d2, nb, h, order, fallback)
+        stats["small_ok"] += int(np.sum(w["status"] == 1))
+        stats["full_ok"] += int(np.sum(w["status"] == 2))
+        stats["no_stencil"] += int(np.sum(w["status"] == 3))
+        dg = apply(n2, Gs, d2, w, c["nu_over_h2"])
+        Ge = Gs + dt * dg
+        if vel is not None:
+            u, v = lamb_oseen_velocity(Xs, Ys, vel["gamma"], vel["nu"], times[s], vel.get("x0", 0.0),
+                                       vel.get("y0", 0.0))
+            Xe = Xs + dt * u
+            Ye = Ys + dt * v
+        if s == 0:
+            Gs = Ge
+            if vel is not None:
+                Xs, Ys = Xe, Ye
+        else:
+            a, b = coef[s]
+            Gs = a * G0 + b * Ge
+            if vel is not None:
+                Xs = a * X0 + b * Xe
+                Ys = a * Y0 + b * Ye
+    return Xs, Ys, Gs, stats
+
