@@ -389,6 +389,33 @@ vrm_status vrm_learned_project(vrm_ctx* ctx, const double* x, const double* y, c
 vrm_status vrm_learned_targets(const int32_t* list, int32_t m, const int32_t* slots, const int32_t* cols,
                                const double* f, float* T, cudaStream_t stream);
 
+/*
+ * One SSP-RK3 (Shu-Osher) step of the viscous particle method: positions
+ * move with an analytic velocity, circulations follow the diffusion operator
+ * (the heat part of Sec. 3; the velocity of Sec. 6's Lamb-Oseen test case
+ * stands in for the Biot-Savart law).  Growth control and insertion run once,
+ * on the step's initial cloud; neighbourhoods and weights (LP, or the learned
+ * proposal with vrm_set_mlp) are rebuilt at each of the three stages:
+ *   X1 = X0 + dt u(X0, t),                        G1 = G0 + dt L(X0) G0
+ *   X2 = 3/4 X0 + 1/4 (X1 + dt u(X1, t + dt)),    G2 = 3/4 G0 + 1/4 (G1 + dt L(X1) G1)
+ *   X3 = 1/3 X0 + 2/3 (X2 + dt u(X2, t + dt/2)),  G3 = 1/3 G0 + 2/3 (G2 + dt L(X2) G2)
+ * products and sums rounded separately.  x, y (capacity entries) receive X3
+ * (inserted particles appended), gamma_out receives G3; t is the field time
+ * of the state.  Without a velocity (vel NULL or kind VRM_VEL_NONE) the
+ * positions stay.  Stats sum over the three stages (n_in, n_out, insertion
+ * and growth-control counts are the step's).  Errors as vrm_step.
+ */
+#define VRM_VEL_NONE 0
+#define VRM_VEL_LAMB_OSEEN 1 /* u_theta = gamma/(2 pi r) (1 - exp(-r^2/(4 nu t))) about (x0, y0) */
+typedef struct vrm_velocity {
+  int32_t kind;
+  int32_t reserved;
+  double gamma, nu, x0, y0;
+} vrm_velocity;
+vrm_status vrm_rk3_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capacity, const double* gamma_in,
+                        double* gamma_out, double t, double dt, const vrm_velocity* vel, int32_t* n_out,
+                        vrm_stats* stats, cudaStream_t stream);
+
 /* Per-stage timing of vrm_step with CUDA events recorded on the call's
    stream between the stages.  Off by default; enable != 0 turns it on. */
 vrm_status vrm_set_timing(vrm_ctx* ctx, int32_t enable);

@@ -248,17 +248,46 @@ def pipeline(x, y, gamma, h, nu, r=0.5, R=2.0, c_diff=1.0, order=1, k_cap=32, ma
     return dict(diffused=d2, x=x2, y=y2, rounds=rounds, open=open_, nb=nb, w=w, dgamma=dg, const=c)
 
 
+# 1/k for the series below, and ln 2 split so that k * LN2_HI is exact for
+# |k| < 2^20 (Cody and Waite's range reduction)
+INV_K = [1.0 / k if k else 0.0 for k in range(20)]
+LN2_HI = 6.93147180369123816490e-01
+LN2_LO = 1.90821492927058770002e-10
+INV_LN2 = 1.44269504088896338700e+00
+
+
+def one_minus_exp_neg(a):
+    """1 - exp(-a) for a >= 0, by a fixed sequence of separately rounded
+    operations (the same on every platform): for a <= 1/4 the series
+    a (1 - a/2 (1 - a/3 (... (1 - a/16)))); otherwise exp(-a) = 2^-k exp(-r),
+    k = floor(a / ln 2 + 1/2), r = (a - k LN2_HI) - k LN2_LO, exp(-r) by its
+    Taylor series to degree 18 in Horner form, and 1 - that; 1 for a > 700."""
+    a = np.asarray(a, dtype=np.float64)
+    p = np.ones_like(a)
+    for k in range(16, 1, -1):
+        p = 1.0 - (a * INV_K[k]) * p
+    small = a * p
+    ac = np.minimum(a, 700.0)
+    kk = np.floor(ac * INV_LN2 + 0.5)
+    r = (ac - kk * LN2_HI) - kk * LN2_LO
+    q = np.ones_like(a)
+    for k in range(18, 0, -1):
+        q = 1.0 + ((-r) * INV_K[k] if k < len(INV_K) else (-r) / k) * q
+    big = 1.0 - np.ldexp(q, -kk.astype(np.int64))
+    return np.where(a <= 0.25, small, np.where(a > 700.0, 1.0, big))
+
+
 def lamb_oseen_velocity(x, y, gamma, nu, t, x0=0.0, y0=0.0):
     """Azimuthal velocity of the Lamb-Oseen vortex (Sec. 6):
     u_theta = Gamma/(2 pi r) (1 - exp(-r^2/(4 nu t))), as
-    (u, v) = (-(y - y0), x - x0) * k with k = Gamma/(2 pi r^2) * (-expm1(-r^2/(4 nu t)));
+    (u, v) = (-(y - y0), x - x0) * k with k = Gamma/(2 pi r^2) * one_minus_exp_neg(r^2/(4 nu t));
     products and sums rounded separately, k = 0 at r = 0."""
     dx = np.asarray(x, dtype=np.float64) - x0
     dy = np.asarray(y, dtype=np.float64) - y0
     r2 = dx * dx + dy * dy
     with np.errstate(divide="ignore", invalid="ignore"):
         a = r2 / ((4.0 * nu) * t)
-        k = (gamma / ((2.0 * np.pi) * r2)) * (-np.expm1(-a))
+        k = (gamma / ((2.0 * np.pi) * r2)) * one_minus_exp_neg(a)
     k = np.where(r2 > 0.0, k, 0.0)
     return -dy * k, dx * k
 

@@ -70,6 +70,14 @@ class Schedule(ctypes.Structure):
         return s
 
 
+class Velocity(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("nu", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double)]
+
+
+VEL_NONE, VEL_LAMB_OSEEN = 0, 1
+
+
 class AdamW(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("weight_decay", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
@@ -114,6 +122,7 @@ SIGNATURES = {
     "vrm_mlp_adamw": (ctypes.c_int, [P, P, P, I32, P]),
     "vrm_mlp_error": (ctypes.c_int, [P, P]),
     "vrm_set_mlp": (ctypes.c_int, [P, P]),
+    "vrm_rk3_step": (ctypes.c_int, [P, P, P, I32, I32, P, P, ctypes.c_double, ctypes.c_double, P, P, P, P]),
     "vrm_learned_features": (ctypes.c_int, [P, P, P, I32, P, I32, P, P, P, P, P]),
     "vrm_learned_project": (ctypes.c_int, [P, P, P, P, I32, P, P, P, P, P, P, P, P, P]),
     "vrm_learned_targets": (ctypes.c_int, [P, I32, P, P, P, P, P]),
@@ -296,6 +305,25 @@ class VRM:
             _ptr(dgamma, torch.float64, "dgamma", n), _stream())
         self._check(st, "vrm_apply")
         return dgamma
+
+    def rk3_step(self, x, y, n, gamma_in, gamma_out, t, dt, lamb_oseen=None, stats=True):
+        """One SSP-RK3 step (vrm_rk3_step); lamb_oseen: dict(gamma, nu[, x0, y0])
+        of the advecting Lamb-Oseen field, or None (positions stay)."""
+        cap = x.numel()
+        v = Velocity()
+        if lamb_oseen is not None:
+            v.kind = VEL_LAMB_OSEEN
+            v.gamma, v.nu = float(lamb_oseen["gamma"]), float(lamb_oseen["nu"])
+            v.x0, v.y0 = float(lamb_oseen.get("x0", 0.0)), float(lamb_oseen.get("y0", 0.0))
+        n_out = ctypes.c_int32(0)
+        s = Stats()
+        st = self.lib.vrm_rk3_step(self.ctx, _ptr(x, torch.float64, "x", n), _ptr(y, torch.float64, "y", cap),
+                                   int(n), int(cap), _ptr(gamma_in, torch.float64, "gamma_in", n),
+                                   _ptr(gamma_out, torch.float64, "gamma_out", cap), float(t), float(dt),
+                                   ctypes.byref(v), ctypes.byref(n_out), ctypes.byref(s) if stats else None,
+                                   _stream())
+        self._check(st, "vrm_rk3_step")
+        return n_out.value, s.as_dict()
 
     def set_timing(self, enable=True):
         self._check(self.lib.vrm_set_timing(self.ctx, int(bool(enable))), "vrm_set_timing")

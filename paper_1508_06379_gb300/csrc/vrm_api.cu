@@ -93,6 +93,10 @@ struct vrm_ctx {
   // learned proposal
   vrm_mlp* mlp = nullptr;
   Learned L;
+  // stage buffers of vrm_rk3_step
+  int rk_cap = 0;
+  double *rk_x1 = nullptr, *rk_y1 = nullptr, *rk_x2 = nullptr, *rk_y2 = nullptr;
+  double *rk_g1 = nullptr, *rk_g2 = nullptr, *rk_dg = nullptr;
 };
 
 // What a batch graph was captured for: per cloud the buffers, capacity and
@@ -197,6 +201,64 @@ cudaError_t enqueue_learned(vrm_ctx* ctx, const double* x, const double* y, cons
   if ((e = cudaMemsetAsync(s.counters + 2, 0, sizeof(int), st)) != cudaSuccess) return e;
   return learned_project(c, x, y, list, list_count, cap, L.slots, L.Y, small, cols, f, fii, status, L.rlist,
                          s.counters + 2, s.ds, dt_dev, ctx->p.nu, st);
+}
+
+void free_rk(vrm_ctx* ctx) {
+  double* ptrs[] = {ctx->rk_x1, ctx->rk_y1, ctx->rk_x2, ctx->rk_y2, ctx->rk_g1, ctx->rk_g2, ctx->rk_dg};
+  for (double* p : ptrs)
+    if (p) cudaFree(p);
+  ctx->rk_x1 = ctx->rk_y1 = ctx->rk_x2 = ctx->rk_y2 = ctx->rk_g1 = ctx->rk_g2 = ctx->rk_dg = nullptr;
+  ctx->rk_cap = 0;
+}
+
+cudaError_t ensure_rk(vrm_ctx* ctx, int cap, cudaStream_t st) {
+  if (cap <= ctx->rk_cap) return cudaSuccess;
+  cudaStreamSynchronize(st);
+  free_rk(ctx);
+  cudaError_t e = cudaSuccess;
+  double** ptrs[] = {&ctx->rk_x1, &ctx->rk_y1, &ctx->rk_x2, &ctx->rk_y2, &ctx->rk_g1, &ctx->rk_g2, &ctx->rk_dg};
+  for (double** p : ptrs)
+    if (e == cudaSuccess) e = cudaMalloc((void**)p, sizeof(double) * (size_t)cap);
+  if (e != cudaSuccess) {
+    free_rk(ctx);
+    cudaGetLastError();
+    return e;
+  }
+  ctx->rk_cap = cap;
+  return cudaSuccess;
+}
+
+// Neighbourhoods and weights of every diffused particle (list s.dlist) at
+// positions (x, y) of the n_cur particles: cell grid, search, learned
+// proposal (with a network) and LP.
+cudaError_t enqueue_stage_weights(vrm_ctx* ctx, const double* x, const double* y, int cap, cudaStream_t st) {
+  Scratch& s = ctx->s;
+  const Consts& c = ctx->c;
+  const int* n_cur = &s.st->n_cur;
+  cudaError_t e;
+  // the full-neighbourhood queue of this stage starts empty
+  if ((e = cudaMemsetAsync(&s.ds->n_fail, 0, sizeof(int), st)) != cudaSuccess) return e;
+  if ((e = grid_build_dev(x, y, cap, n_cur, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank,
+                          s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
+                          st)) != cudaSuccess)
+    return e;
+  if ((e = search_all_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, cap, n_cur, s.nbr_count,
+                          s.nbr_idx, s.seg_mask, s.small, s.ds, st)) != cudaSuccess)
+    return e;
+  const int* lp_list = s.dlist;
+  const int* lp_count = s.counters + 0;
+  if (ctx->mlp) {
+    if ((e = enqueue_learned(ctx, x, y, n_cur, s.dlist, s.counters + 0, cap, s.nbr_count, s.nbr_idx, s.small, s.cols,
+                             s.f, s.fii, s.status, &s.st->dt, st)) != cudaSuccess)
+      return e;
+    lp_list = ctx->L.rlist;
+    lp_count = s.counters + 2;
+  }
+  if ((e = lp_small(c, x, y, lp_list, lp_count, cap, s.small, s.cols, s.f, s.fii, s.status, s.fail_list, s.ds, 0.0,
+                    st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
+    return e;
+  return lp_full(c, x, y, s.fail_list, &s.ds->n_fail, cap, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii, s.status,
+                 s.ds, 0.0, st, &s.st->dt, ctx->p.nu);
 }
 
 // Scratch for `cap` particles (grown by 25% steps, never shrunk).
@@ -658,6 +720,7 @@ void vrm_destroy(vrm_ctx* ctx) {
   drop_graph(ctx);
   free_scratch(ctx->s);
   free_learned(ctx->L);
+  free_rk(ctx);
   if (ctx->events_ready)
     for (int k = 0; k <= VRM_STAGE_COUNT; ++k) cudaEventDestroy(ctx->ev[k]);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -802,6 +865,95 @@ vrm_status vrm_solve_weights(vrm_ctx* ctx, const double* x, const double* y, int
     stats->learned_square = s.h_ds->learned_square;
   }
   if (ctx->mlp && vrm_mlp_error(ctx->mlp, stream) != VRM_OK) return VRM_ERR_CUDA;
+  return VRM_OK;
+}
+
+vrm_status vrm_rk3_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capacity, const double* gamma_in,
+                        double* gamma_out, double t, double dt, const vrm_velocity* vel, int32_t* n_out,
+                        vrm_stats* stats, cudaStream_t stream) {
+  if (!ctx || !n_out || n < 0 || capacity < n || !std::isfinite(dt) || !std::isfinite(t)) return VRM_ERR_ARG;
+  if (bad_ptr(x, n) || bad_ptr(y, n) || bad_ptr(gamma_in, n) || bad_ptr(gamma_out, capacity)) return VRM_ERR_ARG;
+  if (n > 0 && gamma_out < gamma_in + n && gamma_in < gamma_out + capacity) return VRM_ERR_ARG;
+  Velocity V;
+  memset(&V, 0, sizeof(V));
+  V.kind = vel ? vel->kind : VRM_VEL_NONE;
+  if (V.kind != VRM_VEL_NONE) {
+    if (V.kind != VRM_VEL_LAMB_OSEEN) return VRM_ERR_ARG;
+    if (!(vel->nu > 0) || !std::isfinite(vel->gamma) || !std::isfinite(vel->x0) || !std::isfinite(vel->y0))
+      return VRM_ERR_ARG;
+    if (!(t > 0 && t + 0.5 * dt > 0 && t + dt > 0)) return VRM_ERR_ARG;
+    V.gamma = vel->gamma;
+    V.nu = vel->nu;
+    V.x0 = vel->x0;
+    V.y0 = vel->y0;
+  }
+  vrm_stats local;
+  vrm_stats* st = stats ? stats : &local;
+  memset(st, 0, sizeof(*st));
+  if (n == 0) {
+    *n_out = 0;
+    return VRM_OK;
+  }
+  Scratch& s = ctx->s;
+  VRM_CUDA(ensure_scratch(ctx, capacity, stream));
+  VRM_CUDA(ensure_learned(ctx, capacity, stream));
+  VRM_CUDA(ensure_rk(ctx, capacity, stream));
+  VRM_CUDA(cudaStreamSynchronize(stream));
+  StepState P;
+  memset(&P, 0, sizeof(P));
+  P.n = n;
+  P.capacity = capacity;
+  P.dt = dt;
+  P.max_rounds = ctx->p.max_rounds;
+  *s.h_params = P;
+  const int timing = ctx->timing;
+  ctx->timing = 0;
+  // growth control and insertion once, on the step's initial cloud
+  vrm_status r = run_step_eager(ctx, x, y, capacity, gamma_in, nullptr, s.diffused, false, stream);
+  ctx->timing = timing;
+  if (r != VRM_OK) return r;
+  VRM_CUDA(read_back(ctx, stream));
+  if (s.h_grid->nonfinite || s.h_ds->nonfinite) return VRM_ERR_ARG;
+  fill_front_stats(ctx, n, st);
+  if (s.h_state->overflow) return VRM_ERR_CAPACITY;
+  const int* n_cur = &s.st->n_cur;
+  double* Xs[3] = {x, ctx->rk_x1, ctx->rk_x2};
+  double* Ys[3] = {y, ctx->rk_y1, ctx->rk_y2};
+  const double* Gs[3] = {gamma_in, ctx->rk_g1, ctx->rk_g2};
+  double* Xo[3] = {ctx->rk_x1, ctx->rk_x2, x};
+  double* Yo[3] = {ctx->rk_y1, ctx->rk_y2, y};
+  double* Go[3] = {ctx->rk_g1, ctx->rk_g2, gamma_out};
+  const double ts[3] = {t, t + dt, t + 0.5 * dt};
+  const bool move = V.kind != VRM_VEL_NONE;
+  for (int k = 0; k < 3; ++k) {
+    // without a velocity every stage sits at the initial positions
+    const double* px = move ? Xs[k] : x;
+    const double* py = move ? Ys[k] : y;
+    VRM_CUDA(enqueue_stage_weights(ctx, px, py, capacity, stream));
+    VRM_CUDA(apply_gather_dev(ctx->c, capacity, n_cur, k == 0 ? n : capacity, k == 0 ? nullptr : n_cur, Gs[k],
+                              s.diffused, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii, s.sorted_idx, ctx->rk_dg,
+                              nullptr, 0.0, nullptr, stream));
+    VRM_CUDA(rk3_stage(k, capacity, n_cur, dt, ts[k], V, x, y, gamma_in, n, px, py, Gs[k], ctx->rk_dg, Xo[k], Yo[k],
+                       Go[k], stream));
+  }
+  VRM_CUDA(read_back(ctx, stream));
+  if (ctx->mlp && vrm_mlp_error(ctx->mlp, stream) != VRM_OK) return VRM_ERR_CUDA;
+  if (s.h_grid->nonfinite || s.h_ds->nonfinite) return VRM_ERR_ARG;
+  st->small_ok = s.h_ds->small_ok;
+  st->full_ok = s.h_ds->full_ok;
+  st->no_stencil = s.h_ds->no_stencil;
+  st->max_pivots = s.h_ds->max_pivots;
+  st->max_count = s.h_ds->max_count;
+  st->max_dt_ratio = ratio_from_bits(s.h_ds->max_dt_ratio_bits);
+  st->lp_small_solved = s.h_ds->lp_small_solved;
+  st->lp_small_pivots = (int64_t)s.h_ds->lp_small_pivots;
+  st->lp_full_solved = s.h_ds->lp_full_solved;
+  st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
+  st->learned_ok = s.h_ds->learned_ok;
+  st->learned_rejected = s.h_ds->learned_rejected;
+  st->learned_square = s.h_ds->learned_square;
+  *n_out = s.h_state->n_cur;
+  if (s.h_ds->max_count > ctx->c.row_cap) return VRM_ERR_CAPACITY;
   return VRM_OK;
 }
 

@@ -172,6 +172,12 @@ __device__ __forceinline__ int segment_or_ambiguous(float du, float dv, float ep
   return segment_of(du, dv);
 }
 
+// Analytic velocity of the RK3 step (vrm_velocity).
+struct Velocity {
+  int kind;
+  double gamma, nu, x0, y0;
+};
+
 // ---- launch helpers (host) -----------------------------------------------
 
 int persistent_blocks(int block_threads, int per_sm);
@@ -296,5 +302,13 @@ cudaError_t apply_gather_dev(const Consts& c, int n_bound, const int* n_dev, int
                              const double* gamma, const uint8_t* diffused, const int* nbr_count, const int* nbr_idx,
                              const int* cols, const double* f, const double* fii, const int* order, double* dgamma,
                              double* gamma_out, double dt, const double* dt_dev, cudaStream_t s);
+
+// vrm_rk3.cu
+// One stage update of the SSP-RK3 step (positions by the velocity, circulations
+// by the stage's dGamma), for n particles (*n_dev if given).
+cudaError_t rk3_stage(int stage, int n_bound, const int* n_dev, double dt, double t_s, const Velocity& vel,
+                      const double* X0, const double* Y0, const double* G0, int n_g0, const double* Xs,
+                      const double* Ys, const double* Gs, const double* dg, double* Xo, double* Yo, double* Go,
+                      cudaStream_t s);
 
 }  // namespace vrm
