@@ -47,7 +47,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixture_1m",
-                    choices=["mixture_1m", "lamb_oseen_h002", "batched_64", "learned_4m"])
+                    choices=["mixture_1m", "lamb_oseen_h002", "batched_64", "learned_4m", "viscous_16m"])
+    ap.add_argument("--viscous-h", type=float, default=7 * 2.0 ** -16,
+                    help="lattice spacing of the viscous Lamb-Oseen workload (7 2^-16 = 1.068e-4: about 15.5M "
+                         "particles, binary-exact lattice coordinates)")
     ap.add_argument("--train-rows", type=int, default=10_000_000,
                     help="LP solutions the network of the learned workload is trained on")
     ap.add_argument("--train-epochs", type=int, default=3)
@@ -737,6 +740,89 @@ def run_learned(args):
     sys.stdout.flush()
 
 
+VISCOUS_DESC = ("Lamb-Oseen vortex (Gamma=1, nu=5e-4, t0=1) on a lattice of h=%.3g, |omega|>1e-10 kept, advected by "
+                "its analytic velocity, SSP-RK3 with the diffusion operator at every stage (growth control and "
+                "insertion once per step), dt=min((rh)^2/(4nu), h/(4 max|u|)), FP64")
+
+
+def run_viscous(args):
+    """Config 5: the viscous Lamb-Oseen run with advection, vrm_rk3_step per
+    step; particles/s counted after insertion, each step = three operator
+    evaluations; the weak error against the closed form after the timed steps."""
+    import numpy as np
+    import torch
+
+    import paper_1508_06379_gb300 as vrm
+    import vrm_inputs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    vrm.build()
+    dev = torch.device("cuda", local)
+    gamma, nu, t0, h = 1.0, 5e-4, 1.0, args.viscous_h
+    x, y, g = vrm_inputs.lamb_oseen_lattice(h, gamma, nu, t0, eps=1e-10, lo=-0.25, hi=0.25)
+    umax = 0.64 * gamma / (2 * math.pi * 2.24 * math.sqrt(nu * t0))  # peak azimuthal speed
+    dt = min((0.5 * h) ** 2 / (4 * nu), 0.25 * h / umax)
+    n0 = len(x)
+    # insertion adds particles every step (about half of n0 in the first one:
+    # on a lattice whose coordinates are not binary-exact the axis
+    # neighbours fall on either side of the segment rays)
+    cap = 3 * n0 + 4096
+    xb = torch.zeros(cap, dtype=torch.float64, device=dev)
+    yb = torch.zeros(cap, dtype=torch.float64, device=dev)
+    xb[:n0] = torch.from_numpy(x).to(dev)
+    yb[:n0] = torch.from_numpy(y).to(dev)
+    bufs = [torch.zeros(cap, dtype=torch.float64, device=dev) for _ in range(2)]
+    bufs[0][:n0] = torch.from_numpy(g).to(dev)
+    ctx = vrm.VRM(h=h, nu=nu)
+    vel = dict(gamma=gamma, nu=nu)
+    stream = torch.cuda.current_stream()
+    n, t, k = n0, t0, 0
+    for _ in range(args.warmup):
+        n, _ = ctx.rk3_step(xb, yb, n, bufs[k % 2], bufs[(k + 1) % 2], t, dt, vel)
+        t += dt
+        k += 1
+    torch.cuda.synchronize()
+    clocks = Clocks(None)
+    time.sleep(0.3)
+    t_wall0 = time.time()
+    launches0 = vrm.launch_count()
+    ms, parts, st = 0.0, 0, None
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n, st = ctx.rk3_step(xb, yb, n, bufs[k % 2], bufs[(k + 1) % 2], t, dt, vel)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        parts += n
+        t += dt
+        k += 1
+    t_wall1 = time.time()
+    launches = vrm.launch_count() - launches0
+    ck = clocks.stop(t_wall0, t_wall1)
+    X, Y, G = xb[:n].cpu().numpy(), yb[:n].cpu().numpy(), bufs[k % 2][:n].cpu().numpy()
+    s2 = 2 * nu * t + 0.03 ** 2
+    err = max(abs(np.sum(G * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * 0.03 ** 2))) -
+                  gamma * 0.03 ** 2 / s2 * np.exp(-(cx * cx + cy * cy) / (2 * s2))) / gamma
+              for cx, cy in [(0.0, 0.0), (0.03, 0.0), (0.05, 0.04), (-0.08, 0.02), (0.0, -0.1)])
+    line = {
+        "metric": METRIC, "value": parts / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": VISCOUS_DESC % h, "n_initial": int(n0), "n_final": int(n), "h": h, "nu": nu,
+                   "dt": dt, "t_final": t, "operator_evaluations_per_step": 3,
+                   "l2": "inputs larger than L2 (no flush)", "parallelism": "1 GPU"},
+        "circulation_drift": float(abs(G.sum() - g.sum())),
+        "weak_error_vs_closed_form": float(err),
+        "stats_last_step": {k2: int(st[k2]) for k2 in ("n_diffused", "n_inserted", "small_ok", "full_ok", "no_stencil")},
+        "gpu_launches": int(launches), "clocks": ck, "roofline": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -745,6 +831,8 @@ def main():
         run_batched(args)
     elif args.workload == "learned_4m":
         run_learned(args)
+    elif args.workload == "viscous_16m":
+        run_viscous(args)
     else:
         run_ours(args)
 
