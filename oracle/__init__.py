@@ -301,9 +301,10 @@ def rk3_step(x, y, gamma, h, nu, t, dt, vel=None, r=0.5, R=2.0, c_diff=1.0, orde
         X1 = X0 + dt u(X0, t),           G1 = G0 + dt L(X0) G0
         X2 = 3/4 X0 + 1/4 (X1 + dt u(X1, t + dt)),   G2 likewise with L(X1) G1
         X3 = 1/3 X0 + 2/3 (X2 + dt u(X2, t + dt/2)), G3 likewise with L(X2) G2
-    vel: dict(gamma, nu, x0, y0) of the Lamb-Oseen field, or None (no
-    advection: the positions stay those of the start).  Products and sums
-    rounded separately.  Returns (x', y',
+    vel: dict(gamma, nu, x0, y0) of the Lamb-Oseen field, dict(eps=...) for
+    the particles' own smoothed Biot-Savart velocity (direct sum, stage
+    circulations), or None (no advection: the positions stay those of the
+    start).  Products and sums rounded separately.  Returns (x', y',
     gamma', stats)."""
     c = constants(h, r, R, nu, c_diff, order)
     n = len(x)
@@ -329,8 +330,11 @@ def rk3_step(x, y, gamma, h, nu, t, dt, vel=None, r=0.5, R=2.0, c_diff=1.0, orde
         dg = apply(n2, Gs, d2, w, c["nu_over_h2"])
         Ge = Gs + dt * dg
         if vel is not None:
-            u, v = lamb_oseen_velocity(Xs, Ys, vel["gamma"], vel["nu"], times[s], vel.get("x0", 0.0),
-                                       vel.get("y0", 0.0))
+            if "eps" in vel:
+                u, v = biot_savart(Xs, Ys, Gs, Xs, Ys, vel["eps"])
+            else:
+                u, v = lamb_oseen_velocity(Xs, Ys, vel["gamma"], vel["nu"], times[s], vel.get("x0", 0.0),
+                                           vel.get("y0", 0.0))
             Xe = Xs + dt * u
             Ye = Ys + dt * v
         if s == 0:
@@ -344,4 +348,27 @@ def rk3_step(x, y, gamma, h, nu, t, dt, vel=None, r=0.5, R=2.0, c_diff=1.0, orde
                 Xs = a * X0 + b * Xe
                 Ys = a * Y0 + b * Ye
     return Xs, Ys, Gs, stats
+
+
+def biot_savart(xs, ys, gamma, xt, yt, eps, block=2048):
+    """Smoothed Biot-Savart velocity at the targets (Sec. 6, Eq. smoothkernel):
+    u_h(x) = sum_j Gamma_j K_eps(x - x_j),
+    K_eps(x) = (-y, x) / (2 pi |x|^2) (1 - exp(-|x/eps|^2)),  K_eps(0) = 0;
+    direct sum in FP64 (1 - exp(-q) as -expm1(-q)), targets in blocks."""
+    xs = np.asarray(xs, dtype=np.float64)
+    ys = np.asarray(ys, dtype=np.float64)
+    g = np.asarray(gamma, dtype=np.float64)
+    xt = np.asarray(xt, dtype=np.float64)
+    yt = np.asarray(yt, dtype=np.float64)
+    u = np.zeros(len(xt))
+    v = np.zeros(len(xt))
+    for a in range(0, len(xt), block):
+        dx = xt[a:a + block, None] - xs[None, :]
+        dy = yt[a:a + block, None] - ys[None, :]
+        r2 = dx * dx + dy * dy
+        with np.errstate(divide="ignore", invalid="ignore"):
+            k = np.where(r2 > 0.0, -np.expm1(-r2 / (eps * eps)) / ((2.0 * np.pi) * r2), 0.0)
+        u[a:a + block] = -(dy * k) @ g
+        v[a:a + block] = (dx * k) @ g
+    return u, v
 

@@ -89,3 +89,23 @@ def test_rk3_lamb_oseen_conserves_and_tracks_the_closed_form(orc):
     I2 = np.sum(g * (x * x + y * y))
     I2_0 = 4 * nu * t0 * g0  # closed form of the Lamb-Oseen second moment
     assert abs(I2 - 4 * nu * t * g0) < 0.05 * (I2 - I2_0 + 1e-30) + 1e-6
+
+
+def test_rk3_two_point_vortices_corotate(orc):
+    # self-induced velocity (direct sum): two equal vortices d apart (d >> eps,
+    # no neighbours, growth-control bound >= 1 so nothing diffuses) turn about
+    # their midpoint at Gamma_total / (2 pi d^2); RK3 keeps the distance
+    gamma, d, eps = 1.0, 5.0, 0.1
+    x, y, g = np.array([-d / 2, d / 2]), np.array([0.0, 0.0]), np.array([gamma, gamma])
+    om = 2 * gamma / (2 * math.pi * d * d)
+    T = 0.5 / om
+    steps = 40
+    dt = T / steps
+    t = 1.0
+    for _ in range(steps):
+        x, y, g, st = orc.rk3_step(x, y, g, 1.0, 1e-3, t, dt, vel=dict(eps=eps))
+        t += dt
+    assert len(x) == 2 and st["n_diffused"] == 0
+    ang = om * T
+    assert abs(x[1] - d / 2 * math.cos(ang)) < 1e-5 and abs(y[1] - d / 2 * math.sin(ang)) < 1e-5
+    assert abs(math.hypot(x[1] - x[0], y[1] - y[0]) - d) < 1e-5
