@@ -407,11 +407,27 @@ vrm_status vrm_learned_targets(const int32_t* list, int32_t m, const int32_t* sl
  */
 #define VRM_VEL_NONE 0
 #define VRM_VEL_LAMB_OSEEN 1 /* u_theta = gamma/(2 pi r) (1 - exp(-r^2/(4 nu t))) about (x0, y0) */
+#define VRM_VEL_BIOT_SAVART 2 /* the particles' own smoothed velocity (vrm_biot_savart, core eps) */
 typedef struct vrm_velocity {
   int32_t kind;
   int32_t reserved;
   double gamma, nu, x0, y0;
+  double eps;
 } vrm_velocity;
+
+/*
+ * Smoothed Biot-Savart velocity by direct summation (Sec. 6, Eq.
+ * smoothkernel): u_h(x) = sum_j Gamma_j K_eps(x - x_j) with
+ * K_eps(x) = (-y, x)/(2 pi |x|^2) (1 - exp(-|x/eps|^2)), K_eps(0) = 0, at the m
+ * targets (xt, yt) from the n sources (xs, ys, gamma); all device pointers,
+ * u and v receive m values.  Pair terms in fp32 on hi/lo-split positions,
+ * tile sums in FP64: relative error about 1e-6 of sum_j |Gamma_j K_eps|.
+ * O(n m) work (the fast multipole method of the paper is not part of this
+ * library).  Asynchronous.
+ */
+vrm_status vrm_biot_savart(vrm_ctx* ctx, const double* xs, const double* ys, const double* gamma, int32_t n,
+                           const double* xt, const double* yt, int32_t m, double eps, double* u, double* v,
+                           cudaStream_t stream);
 vrm_status vrm_rk3_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capacity, const double* gamma_in,
                         double* gamma_out, double t, double dt, const vrm_velocity* vel, int32_t* n_out,
                         vrm_stats* stats, cudaStream_t stream);

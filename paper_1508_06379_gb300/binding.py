@@ -72,10 +72,10 @@ class Schedule(ctypes.Structure):
 
 class Velocity(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("gamma", ctypes.c_double),
-                ("nu", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double)]
+                ("nu", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("eps", ctypes.c_double)]
 
 
-VEL_NONE, VEL_LAMB_OSEEN = 0, 1
+VEL_NONE, VEL_LAMB_OSEEN, VEL_BIOT_SAVART = 0, 1, 2
 
 
 class AdamW(ctypes.Structure):
@@ -123,6 +123,7 @@ SIGNATURES = {
     "vrm_mlp_error": (ctypes.c_int, [P, P]),
     "vrm_set_mlp": (ctypes.c_int, [P, P]),
     "vrm_rk3_step": (ctypes.c_int, [P, P, P, I32, I32, P, P, ctypes.c_double, ctypes.c_double, P, P, P, P]),
+    "vrm_biot_savart": (ctypes.c_int, [P, P, P, P, I32, P, P, I32, ctypes.c_double, P, P, P]),
     "vrm_learned_features": (ctypes.c_int, [P, P, P, I32, P, I32, P, P, P, P, P]),
     "vrm_learned_project": (ctypes.c_int, [P, P, P, P, I32, P, P, P, P, P, P, P, P, P]),
     "vrm_learned_targets": (ctypes.c_int, [P, I32, P, P, P, P, P]),
@@ -308,10 +309,14 @@ class VRM:
 
     def rk3_step(self, x, y, n, gamma_in, gamma_out, t, dt, lamb_oseen=None, stats=True):
         """One SSP-RK3 step (vrm_rk3_step); lamb_oseen: dict(gamma, nu[, x0, y0])
-        of the advecting Lamb-Oseen field, or None (positions stay)."""
+        of the advecting Lamb-Oseen field, dict(eps=...) for the particles'
+        own smoothed velocity, or None (positions stay)."""
         cap = x.numel()
         v = Velocity()
-        if lamb_oseen is not None:
+        if lamb_oseen is not None and "eps" in lamb_oseen:
+            v.kind = VEL_BIOT_SAVART
+            v.eps = float(lamb_oseen["eps"])
+        elif lamb_oseen is not None:
             v.kind = VEL_LAMB_OSEEN
             v.gamma, v.nu = float(lamb_oseen["gamma"]), float(lamb_oseen["nu"])
             v.x0, v.y0 = float(lamb_oseen.get("x0", 0.0)), float(lamb_oseen.get("y0", 0.0))
@@ -324,6 +329,18 @@ class VRM:
                                    _stream())
         self._check(st, "vrm_rk3_step")
         return n_out.value, s.as_dict()
+
+    def biot_savart(self, xs, ys, gamma, n, xt, yt, m, eps, u=None, v=None):
+        """Smoothed Biot-Savart velocity at m targets from n sources (vrm_biot_savart)."""
+        dev = xs.device
+        u = u if u is not None else torch.empty(max(m, 1), dtype=torch.float64, device=dev)
+        v = v if v is not None else torch.empty(max(m, 1), dtype=torch.float64, device=dev)
+        self._check(self.lib.vrm_biot_savart(
+            self.ctx, _ptr(xs, torch.float64, "xs", n), _ptr(ys, torch.float64, "ys", n),
+            _ptr(gamma, torch.float64, "gamma", n), int(n), _ptr(xt, torch.float64, "xt", m),
+            _ptr(yt, torch.float64, "yt", m), int(m), float(eps), _ptr(u, torch.float64, "u", m),
+            _ptr(v, torch.float64, "v", m), _stream()), "vrm_biot_savart")
+        return u[:m], v[:m]
 
     def set_timing(self, enable=True):
         self._check(self.lib.vrm_set_timing(self.ctx, int(bool(enable))), "vrm_set_timing")

@@ -96,7 +96,11 @@ struct vrm_ctx {
   // stage buffers of vrm_rk3_step
   int rk_cap = 0;
   double *rk_x1 = nullptr, *rk_y1 = nullptr, *rk_x2 = nullptr, *rk_y2 = nullptr;
-  double *rk_g1 = nullptr, *rk_g2 = nullptr, *rk_dg = nullptr;
+  double *rk_g1 = nullptr, *rk_g2 = nullptr, *rk_dg = nullptr, *rk_u = nullptr, *rk_v = nullptr;
+  // direct-sum velocity: fp32-split sources and targets
+  int bs_src_cap = 0, bs_tgt_cap = 0;
+  float4 *bs_src = nullptr, *bs_tgt = nullptr;
+  float* bs_g = nullptr;
 };
 
 // What a batch graph was captured for: per cloud the buffers, capacity and
@@ -204,11 +208,41 @@ cudaError_t enqueue_learned(vrm_ctx* ctx, const double* x, const double* y, cons
 }
 
 void free_rk(vrm_ctx* ctx) {
-  double* ptrs[] = {ctx->rk_x1, ctx->rk_y1, ctx->rk_x2, ctx->rk_y2, ctx->rk_g1, ctx->rk_g2, ctx->rk_dg};
+  double* ptrs[] = {ctx->rk_x1, ctx->rk_y1, ctx->rk_x2, ctx->rk_y2, ctx->rk_g1, ctx->rk_g2, ctx->rk_dg, ctx->rk_u,
+                    ctx->rk_v};
   for (double* p : ptrs)
     if (p) cudaFree(p);
   ctx->rk_x1 = ctx->rk_y1 = ctx->rk_x2 = ctx->rk_y2 = ctx->rk_g1 = ctx->rk_g2 = ctx->rk_dg = nullptr;
+  ctx->rk_u = ctx->rk_v = nullptr;
   ctx->rk_cap = 0;
+}
+
+void free_bs(vrm_ctx* ctx) {
+  if (ctx->bs_src) cudaFree(ctx->bs_src);
+  if (ctx->bs_tgt) cudaFree(ctx->bs_tgt);
+  if (ctx->bs_g) cudaFree(ctx->bs_g);
+  ctx->bs_src = ctx->bs_tgt = nullptr;
+  ctx->bs_g = nullptr;
+  ctx->bs_src_cap = ctx->bs_tgt_cap = 0;
+}
+
+cudaError_t ensure_bs(vrm_ctx* ctx, int n, int m, cudaStream_t st) {
+  if (n <= ctx->bs_src_cap && m <= ctx->bs_tgt_cap) return cudaSuccess;
+  cudaStreamSynchronize(st);
+  const int ns = n > ctx->bs_src_cap ? n : ctx->bs_src_cap;
+  const int mt = m > ctx->bs_tgt_cap ? m : ctx->bs_tgt_cap;
+  free_bs(ctx);
+  cudaError_t e = cudaMalloc(&ctx->bs_src, sizeof(float4) * (size_t)(ns > 0 ? ns : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->bs_g, sizeof(float) * (size_t)(ns > 0 ? ns : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->bs_tgt, sizeof(float4) * (size_t)(mt > 0 ? mt : 1));
+  if (e != cudaSuccess) {
+    free_bs(ctx);
+    cudaGetLastError();
+    return e;
+  }
+  ctx->bs_src_cap = ns;
+  ctx->bs_tgt_cap = mt;
+  return cudaSuccess;
 }
 
 cudaError_t ensure_rk(vrm_ctx* ctx, int cap, cudaStream_t st) {
@@ -216,7 +250,8 @@ cudaError_t ensure_rk(vrm_ctx* ctx, int cap, cudaStream_t st) {
   cudaStreamSynchronize(st);
   free_rk(ctx);
   cudaError_t e = cudaSuccess;
-  double** ptrs[] = {&ctx->rk_x1, &ctx->rk_y1, &ctx->rk_x2, &ctx->rk_y2, &ctx->rk_g1, &ctx->rk_g2, &ctx->rk_dg};
+  double** ptrs[] = {&ctx->rk_x1, &ctx->rk_y1, &ctx->rk_x2, &ctx->rk_y2, &ctx->rk_g1,
+                     &ctx->rk_g2, &ctx->rk_dg, &ctx->rk_u,  &ctx->rk_v};
   for (double** p : ptrs)
     if (e == cudaSuccess) e = cudaMalloc((void**)p, sizeof(double) * (size_t)cap);
   if (e != cudaSuccess) {
@@ -721,6 +756,7 @@ void vrm_destroy(vrm_ctx* ctx) {
   free_scratch(ctx->s);
   free_learned(ctx->L);
   free_rk(ctx);
+  free_bs(ctx);
   if (ctx->events_ready)
     for (int k = 0; k <= VRM_STAGE_COUNT; ++k) cudaEventDestroy(ctx->ev[k]);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -877,8 +913,7 @@ vrm_status vrm_rk3_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t c
   Velocity V;
   memset(&V, 0, sizeof(V));
   V.kind = vel ? vel->kind : VRM_VEL_NONE;
-  if (V.kind != VRM_VEL_NONE) {
-    if (V.kind != VRM_VEL_LAMB_OSEEN) return VRM_ERR_ARG;
+  if (V.kind == VRM_VEL_LAMB_OSEEN) {
     if (!(vel->nu > 0) || !std::isfinite(vel->gamma) || !std::isfinite(vel->x0) || !std::isfinite(vel->y0))
       return VRM_ERR_ARG;
     if (!(t > 0 && t + 0.5 * dt > 0 && t + dt > 0)) return VRM_ERR_ARG;
@@ -886,6 +921,10 @@ vrm_status vrm_rk3_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t c
     V.nu = vel->nu;
     V.x0 = vel->x0;
     V.y0 = vel->y0;
+  } else if (V.kind == VRM_VEL_BIOT_SAVART) {
+    if (!(vel->eps > 0) || !std::isfinite(vel->eps)) return VRM_ERR_ARG;
+  } else if (V.kind != VRM_VEL_NONE) {
+    return VRM_ERR_ARG;
   }
   vrm_stats local;
   vrm_stats* st = stats ? stats : &local;
@@ -898,6 +937,7 @@ vrm_status vrm_rk3_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t c
   VRM_CUDA(ensure_scratch(ctx, capacity, stream));
   VRM_CUDA(ensure_learned(ctx, capacity, stream));
   VRM_CUDA(ensure_rk(ctx, capacity, stream));
+  if (V.kind == VRM_VEL_BIOT_SAVART) VRM_CUDA(ensure_bs(ctx, capacity, capacity, stream));
   VRM_CUDA(cudaStreamSynchronize(stream));
   StepState P;
   memset(&P, 0, sizeof(P));
@@ -933,8 +973,25 @@ vrm_status vrm_rk3_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t c
     VRM_CUDA(apply_gather_dev(ctx->c, capacity, n_cur, k == 0 ? n : capacity, k == 0 ? nullptr : n_cur, Gs[k],
                               s.diffused, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii, s.sorted_idx, ctx->rk_dg,
                               nullptr, 0.0, nullptr, stream));
-    VRM_CUDA(rk3_stage(k, capacity, n_cur, dt, ts[k], V, x, y, gamma_in, n, px, py, Gs[k], ctx->rk_dg, Xo[k], Yo[k],
-                       Go[k], stream));
+    const double *us = nullptr, *vs = nullptr;
+    if (V.kind == VRM_VEL_BIOT_SAVART) {
+      // the stage's own velocity at every stage particle; in the first stage
+      // only the n given particles carry circulation (gamma_in holds n)
+      if (k == 0) {
+        VRM_CUDA(bs_split(px, py, gamma_in, n, nullptr, ctx->bs_src, ctx->bs_g, stream));
+        VRM_CUDA(bs_split(px, py, nullptr, capacity, n_cur, ctx->bs_tgt, nullptr, stream));
+        VRM_CUDA(bs_direct(ctx->bs_src, ctx->bs_g, n, nullptr, ctx->bs_tgt, capacity, n_cur, vel->eps, ctx->rk_u,
+                           ctx->rk_v, stream));
+      } else {
+        VRM_CUDA(bs_split(px, py, Gs[k], capacity, n_cur, ctx->bs_src, ctx->bs_g, stream));
+        VRM_CUDA(bs_direct(ctx->bs_src, ctx->bs_g, capacity, n_cur, ctx->bs_src, capacity, n_cur, vel->eps,
+                           ctx->rk_u, ctx->rk_v, stream));
+      }
+      us = ctx->rk_u;
+      vs = ctx->rk_v;
+    }
+    VRM_CUDA(rk3_stage(k, capacity, n_cur, dt, ts[k], V, x, y, gamma_in, n, px, py, Gs[k], ctx->rk_dg, us, vs, Xo[k],
+                       Yo[k], Go[k], stream));
   }
   VRM_CUDA(read_back(ctx, stream));
   if (ctx->mlp && vrm_mlp_error(ctx->mlp, stream) != VRM_OK) return VRM_ERR_CUDA;
@@ -954,6 +1011,26 @@ vrm_status vrm_rk3_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t c
   st->learned_square = s.h_ds->learned_square;
   *n_out = s.h_state->n_cur;
   if (s.h_ds->max_count > ctx->c.row_cap) return VRM_ERR_CAPACITY;
+  return VRM_OK;
+}
+
+vrm_status vrm_biot_savart(vrm_ctx* ctx, const double* xs, const double* ys, const double* gamma, int32_t n,
+                           const double* xt, const double* yt, int32_t m, double eps, double* u, double* v,
+                           cudaStream_t stream) {
+  if (!ctx || n < 0 || m < 0 || !(eps > 0) || !std::isfinite(eps)) return VRM_ERR_ARG;
+  if (bad_ptr(xs, n) || bad_ptr(ys, n) || bad_ptr(gamma, n) || bad_ptr(xt, m) || bad_ptr(yt, m) || bad_ptr(u, m) ||
+      bad_ptr(v, m))
+    return VRM_ERR_ARG;
+  if (m == 0) return VRM_OK;
+  if (n == 0) {
+    VRM_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * (size_t)m, stream));
+    VRM_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * (size_t)m, stream));
+    return VRM_OK;
+  }
+  VRM_CUDA(ensure_bs(ctx, n, m, stream));
+  VRM_CUDA(bs_split(xs, ys, gamma, n, nullptr, ctx->bs_src, ctx->bs_g, stream));
+  VRM_CUDA(bs_split(xt, yt, nullptr, m, nullptr, ctx->bs_tgt, nullptr, stream));
+  VRM_CUDA(bs_direct(ctx->bs_src, ctx->bs_g, n, nullptr, ctx->bs_tgt, m, nullptr, eps, u, v, stream));
   return VRM_OK;
 }
 

@@ -306,9 +306,18 @@ cudaError_t apply_gather_dev(const Consts& c, int n_bound, const int* n_dev, int
 // vrm_rk3.cu
 // One stage update of the SSP-RK3 step (positions by the velocity, circulations
 // by the stage's dGamma), for n particles (*n_dev if given).
+// us, vs: precomputed stage velocities (or null: the analytic field of vel).
 cudaError_t rk3_stage(int stage, int n_bound, const int* n_dev, double dt, double t_s, const Velocity& vel,
                       const double* X0, const double* Y0, const double* G0, int n_g0, const double* Xs,
-                      const double* Ys, const double* Gs, const double* dg, double* Xo, double* Yo, double* Go,
-                      cudaStream_t s);
+                      const double* Ys, const double* Gs, const double* dg, const double* us, const double* vs,
+                      double* Xo, double* Yo, double* Go, cudaStream_t s);
+
+// vrm_bs.cu: smoothed Biot-Savart velocity by direct summation.
+// Splits FP64 positions into fp32 hi/lo pairs (and circulations to fp32).
+cudaError_t bs_split(const double* x, const double* y, const double* g, int n_bound, const int* n_dev, float4* pos,
+                     float* gf, cudaStream_t s);
+// u, v at the m targets from the n sources (counts on the device if given).
+cudaError_t bs_direct(const float4* src, const float* gs, int n_bound, const int* n_dev, const float4* tgt,
+                      int m_bound, const int* m_dev, double eps, double* u, double* v, cudaStream_t s);
 
 }  // namespace vrm

@@ -8,7 +8,8 @@
 //   stage 2: X3 = 1/3 X0 + 2/3 (X2 + dt u(X2, t + dt/2)),  G3 likewise
 //
 // Products and sums are rounded separately; without a velocity the positions
-// stay those of the step's start.  The Lamb-Oseen velocity is
+// stay those of the step's start.  With the particles' own velocity (direct
+// sum, vrm_bs.cu) the stage velocities come precomputed.  The Lamb-Oseen velocity is
 // (u, v) = (-(y - y0), x - x0) k, k = Gamma / (2 pi r^2) (1 - exp(-r^2/(4 nu t))),
 // k = 0 at r = 0, with 1 - exp(-a) by a fixed sequence of separately rounded
 // operations (so that every platform gets the same bits): the series
@@ -62,7 +63,8 @@ __device__ __forceinline__ void lamb_oseen_uv(const Velocity& v, double x, doubl
 __global__ void k_rk3_stage(int stage, int n_bound, const int* __restrict__ n_dev, double dt, double t_s, Velocity vel,
                             const double* X0, const double* Y0, const double* __restrict__ G0, int n_g0,
                             const double* Xs, const double* Ys, const double* Gs, const double* __restrict__ dg,
-                            double* Xo, double* Yo, double* Go) {
+                            const double* __restrict__ us, const double* __restrict__ vs, double* Xo, double* Yo,
+                            double* Go) {
   const int n = n_dev ? *n_dev : n_bound;
   const double third = 1.0 / 3.0, two_thirds = 2.0 / 3.0;
   for (long j = (long)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (long)gridDim.x * blockDim.x) {
@@ -73,7 +75,12 @@ __global__ void k_rk3_stage(int stage, int n_bound, const int* __restrict__ n_de
     const bool move = vel.kind != VRM_VEL_NONE;
     if (move) {
       double u, w;
-      lamb_oseen_uv(vel, Xs[j], Ys[j], t_s, &u, &w);
+      if (us) {
+        u = us[j];
+        w = vs[j];
+      } else {
+        lamb_oseen_uv(vel, Xs[j], Ys[j], t_s, &u, &w);
+      }
       xe = __dadd_rn(Xs[j], __dmul_rn(dt, u));
       ye = __dadd_rn(Ys[j], __dmul_rn(dt, w));
     }
@@ -97,13 +104,13 @@ __global__ void k_rk3_stage(int stage, int n_bound, const int* __restrict__ n_de
 
 cudaError_t rk3_stage(int stage, int n_bound, const int* n_dev, double dt, double t_s, const Velocity& vel,
                       const double* X0, const double* Y0, const double* G0, int n_g0, const double* Xs,
-                      const double* Ys, const double* Gs, const double* dg, double* Xo, double* Yo, double* Go,
-                      cudaStream_t s) {
+                      const double* Ys, const double* Gs, const double* dg, const double* us, const double* vs,
+                      double* Xo, double* Yo, double* Go, cudaStream_t s) {
   if (n_bound <= 0) return cudaSuccess;
   int blocks = (n_bound + kBlock - 1) / kBlock;
   if (blocks > 8 * sm_count()) blocks = 8 * sm_count();
-  k_rk3_stage<<<blocks, kBlock, 0, s>>>(stage, n_bound, n_dev, dt, t_s, vel, X0, Y0, G0, n_g0, Xs, Ys, Gs, dg, Xo, Yo,
-                                        Go);
+  k_rk3_stage<<<blocks, kBlock, 0, s>>>(stage, n_bound, n_dev, dt, t_s, vel, X0, Y0, G0, n_g0, Xs, Ys, Gs, dg, us, vs,
+                                        Xo, Yo, Go);
   note_launch();
   return cudaGetLastError();
 }
