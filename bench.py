@@ -807,10 +807,30 @@ def run_viscous(args):
     err = max(abs(np.sum(G * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * 0.03 ** 2))) -
                   gamma * 0.03 ** 2 / s2 * np.exp(-(cx * cx + cy * cy) / (2 * s2))) / gamma
               for cx, cy in [(0.0, 0.0), (0.03, 0.0), (0.05, 0.04), (-0.08, 0.02), (0.0, -0.1)])
+    # e_u (Sec. 6): L2 error of the smoothed particle velocity (eps = 3h,
+    # direct sum) against the Lamb-Oseen velocity, midpoint rule on a
+    # 200 x 200 grid over A = [-1.5, 1.5]^2
+    gq = -1.5 + (np.arange(200) + 0.5) * 0.015
+    QX, QY = np.meshgrid(gq, gq)
+    qx, qy = torch.from_numpy(QX.ravel().copy()).to(dev), torch.from_numpy(QY.ravel().copy()).to(dev)
+    ev = torch.cuda.Event(enable_timing=True)
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev.record(stream)
+    uh, vh = ctx.biot_savart(xb, yb, bufs[k % 2], n, qx, qy, qx.numel(), 3 * h)
+    ev2.record(stream)
+    ev2.synchronize()
+    bs_ms = ev.elapsed_time(ev2)
+    r2 = QX.ravel() ** 2 + QY.ravel() ** 2
+    kq = gamma / (2 * math.pi * r2) * -np.expm1(-r2 / (4 * nu * t))
+    ue, ve = -QY.ravel() * kq, QX.ravel() * kq
+    uh, vh = uh.cpu().numpy(), vh.cpu().numpy()
+    e_u = math.sqrt(np.sum((uh - ue) ** 2 + (vh - ve) ** 2) / np.sum(ue ** 2 + ve ** 2))
     line = {
         "metric": METRIC, "value": parts / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "e_u": {"value": e_u, "targets": int(qx.numel()), "sources": int(n), "eps": 3 * h, "direct_sum_ms": bs_ms,
+                "interactions_per_s": qx.numel() * n / (bs_ms * 1e-3)},
         "config": {"workload": VISCOUS_DESC % h, "n_initial": int(n0), "n_final": int(n), "h": h, "nu": nu,
                    "dt": dt, "t_final": t, "operator_evaluations_per_step": 3,
                    "l2": "inputs larger than L2 (no flush)", "parallelism": "1 GPU"},
