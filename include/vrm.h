@@ -68,10 +68,14 @@ typedef int vrm_status;
 #define VRM_LP_NONE 3    /* no non-negative stencil found: zero stencil */
 #define VRM_LP_LEARNED 4 /* the network's proposal, corrected and accepted (vrm_set_mlp) */
 
-/* Precision of the neighbour search (Sec. 2, Eq. neighbourhood). */
-#define VRM_PREC_FP64 0  /* FP64 distances (bit-identical to the FP64 oracle) */
-#define VRM_PREC_MIXED 1 /* FP32 distances on FP32-rounded positions; the LP
-                            and the application stay FP64 */
+/* Precision of the step.  The neighbourhoods are always those of the FP64
+   definition (FP32 measures with an exact fallback), the LP and the
+   corrections always FP64. */
+#define VRM_PREC_FP64 0  /* FP64 application: bit-identical to the FP64 oracle */
+#define VRM_PREC_MIXED 1 /* the application (Eq. nsode) accumulates fp32 products
+                            of fp32-rounded weights and circulations; dGamma is
+                            within 1e-5 (nu/h^2) sum_i |f~_ij Gamma_i| of the FP64
+                            value; the Euler update stays FP64 */
 
 /* ---- parameters ---------------------------------------------------------- */
 typedef struct vrm_params {

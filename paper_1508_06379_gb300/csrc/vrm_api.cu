@@ -396,7 +396,7 @@ vrm_status check_params(const vrm_params* p) {
   if (p->k_cap < 8 || p->k_cap > VRM_KCAP_MAX) return VRM_ERR_ARG;
   if (p->max_rounds < 0 || p->max_rounds > 1000) return VRM_ERR_ARG;
   if (p->order != 1) return VRM_ERR_UNSUPPORTED;
-  if (p->precision != VRM_PREC_FP64) return VRM_ERR_UNSUPPORTED;
+  if (p->precision != VRM_PREC_FP64 && p->precision != VRM_PREC_MIXED) return VRM_ERR_UNSUPPORTED;
   return VRM_OK;
 }
 

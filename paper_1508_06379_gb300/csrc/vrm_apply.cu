@@ -15,6 +15,22 @@
 
 namespace vrm {
 
+// Products and sums of the application: FP64 rounded separately, or the
+// mixed precision's fp32 (weights and circulations rounded to fp32 first).
+template <typename Acc>
+__device__ __forceinline__ Acc mul_acc(double a, double b);
+template <>
+__device__ __forceinline__ double mul_acc<double>(double a, double b) {
+  return __dmul_rn(a, b);
+}
+template <>
+__device__ __forceinline__ float mul_acc<float>(double a, double b) {
+  return __fmul_rn(__double2float_rn(a), __double2float_rn(b));
+}
+__device__ __forceinline__ double add_acc(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_acc(float a, float b) { return __fadd_rn(a, b); }
+
+template <typename Acc>
 __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __restrict__ n_dev, int n_gamma,
                                                   const int* __restrict__ n_gamma_dev, const double* __restrict__ gamma,
                                                   const uint8_t* __restrict__ diffused,
@@ -33,7 +49,7 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
     const int* row = nbr_idx + (size_t)j * c.k_cap;
     const bool self_src = j < n_gamma && diffused[j];
     const double gj = j < n_gamma ? gamma[j] : 0.0;
-    const double selfv = self_src ? __dmul_rn(fii[j], gj) : 0.0;
+    const Acc selfv = self_src ? mul_acc<Acc>(fii[j], gj) : Acc(0);
     // integer pass: which row entries are sources whose stencil holds j (and
     // in which slot, 4 bits per entry), and where the self term goes (before
     // the first i > j)
@@ -62,21 +78,21 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
       else
         slot_hi |= (unsigned long long)slot << (4 * (t - 16));
     }
-    // FP64 pass over the matches only, in ascending i
-    double acc = 0.0;
+    // FP64 (or fp32) pass over the matches only, in ascending i
+    Acc acc = Acc(0);
     bool self_done = !self_src;
     for (unsigned rest = match; rest; rest &= rest - 1) {
       const int t = __ffs(rest) - 1;
       if (!self_done && t >= selfpos) {
-        acc = __dadd_rn(acc, selfv);
+        acc = add_acc(acc, selfv);
         self_done = true;
       }
       const int i = row[t];
       const int slot = (int)(((t < 16 ? slot_lo >> (4 * t) : slot_hi >> (4 * (t - 16)))) & 15ull);
-      acc = __dadd_rn(acc, __dmul_rn(f[(size_t)i * VRM_STENCIL_W + slot], gamma[i]));
+      acc = add_acc(acc, mul_acc<Acc>(f[(size_t)i * VRM_STENCIL_W + slot], gamma[i]));
     }
-    if (!self_done) acc = __dadd_rn(acc, selfv);
-    const double dg = __dmul_rn(c.nu_over_h2, acc);
+    if (!self_done) acc = add_acc(acc, selfv);
+    const double dg = __dmul_rn(c.nu_over_h2, (double)acc);
     if (dgamma) dgamma[j] = dg;
     if (gamma_out) gamma_out[j] = __fma_rn(dt, dg, gj);
   }
@@ -89,7 +105,11 @@ cudaError_t apply_gather_dev(const Consts& c, int n_bound, const int* n_dev, int
   if (n_bound <= 0) return cudaSuccess;
   const int tb = c.apply_block;
   const int blocks = (int)(((long)n_bound + tb - 1) / tb);
-  k_apply<<<blocks, tb, 0, s>>>(c, n_bound, n_dev, n_gamma, n_gamma_dev, gamma, diffused, nbr_count, nbr_idx, cols,
+  if (c.precision == VRM_PREC_MIXED)
+    k_apply<float><<<blocks, tb, 0, s>>>(c, n_bound, n_dev, n_gamma, n_gamma_dev, gamma, diffused, nbr_count, nbr_idx,
+                                         cols, f, fii, order, dgamma, gamma_out, dt, dt_dev);
+  else
+    k_apply<double><<<blocks, tb, 0, s>>>(c, n_bound, n_dev, n_gamma, n_gamma_dev, gamma, diffused, nbr_count, nbr_idx, cols,
                                     f, fii, order, dgamma, gamma_out, dt, dt_dev);
   note_launch();
   return cudaGetLastError();

@@ -382,3 +382,32 @@ def test_graph_and_eager_steps_agree(lib, orc, monkeypatch):
     # and the first against the oracle
     x2, y2, g2, st_o = orc.step(x, y, g, h, nu, dt)
     assert outs[0][0][0] == len(x2) and np.array_equal(outs[0][0][2], g2)
+
+
+@pytest.mark.parametrize("case", CLOUDS[:4], ids=IDS[:4])
+def test_mixed_precision_step(lib, orc, case):
+    # VRM_PREC_MIXED: the application accumulates fp32 products; dGamma is
+    # within 1e-5 (nu/h^2) sum_i |f~_ij Gamma_i| of the FP64 oracle, the
+    # positions and everything else stay exact
+    name, x, y, g, h = case
+    nu = 1e-3
+    dt = (0.5 * h) ** 2 / (4 * nu) / 8
+    x2, y2, g2, st_o = orc.step(x, y, g, h, nu, dt)
+    n = len(x)
+    cap = len(x2) + 128
+    ctx = lib.VRM(h=h, nu=nu, precision="mixed")
+    xb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    yb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    xb[:n] = cu(x)
+    yb[:n] = cu(y)
+    go = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    n2, st = ctx.step(xb, yb, n, cu(g), go, dt)
+    assert n2 == len(x2) and np.array_equal(xb.cpu().numpy()[:n2], x2)
+    p = orc.pipeline(x, y, g, h, nu)
+    scale = dgamma_scale(n2, g, p["diffused"], p["w"], p["const"]["nu_over_h2"]) * dt
+    got = go.cpu().numpy()[:n2]
+    err = np.abs(got - g2)
+    assert np.all(err <= 1e-5 * scale + 4 * np.spacing(np.abs(g2))), float(np.max(err / np.maximum(scale, 1e-300)))
+    # the fp32 accumulation is visible (not silently FP64) where anything diffuses
+    if st_o["n_diffused"] > 0:
+        assert not np.array_equal(got, g2)
