@@ -47,7 +47,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixture_1m",
-                    choices=["mixture_1m", "lamb_oseen_h002", "batched_64", "learned_4m", "viscous_16m"])
+                    choices=["mixture_1m", "mixture_1m_n2", "lamb_oseen_h002", "batched_64", "learned_4m",
+                             "viscous_16m"])
+    ap.add_argument("--learned", action="store_true",
+                    help="viscous workload: stencils from a trained proposal network (LP fallback)")
     ap.add_argument("--viscous-h", type=float, default=7 * 2.0 ** -16,
                     help="lattice spacing of the viscous Lamb-Oseen workload (7 2^-16 = 1.068e-4: about 15.5M "
                          "particles, binary-exact lattice coordinates)")
@@ -67,16 +70,21 @@ def parse():
 
 def workload(name, rank=0):
     import vrm_inputs
-    if name == "mixture_1m":
+    if name in ("mixture_1m", "mixture_1m_n2"):
         h, nu = 2e-3, 1e-3
         x, y, g = vrm_inputs.gaussian_mixture_cloud(h=h, jitter=0.3, seed=vrm_inputs.SEED_BASE + 2 + 1000 * rank)
         desc = {"workload": "jittered lattice 1001x1001, h=2e-3, jitter 0.3h, 8-Gaussian mixture, nu=1e-3, "
-                            "C_diff=1, insertion on, FP64", "n": int(len(x)), "h": h, "nu": nu}
+                            "C_diff=1, insertion on, FP64", "n": int(len(x)), "h": h, "nu": nu, "order": 1, "R": 2.0}
+        if name == "mixture_1m_n2":
+            # n = 2: nine moment rows; R = 2.5 because with R = 2 about a
+            # third of the jittered particles have no non-negative stencil
+            desc.update(order=2, R=2.5)
+            desc["workload"] = desc["workload"].replace("FP64", "n=2 (cubic moments), R=2.5, FP64")
     else:
         h, nu = 0.02, 1e-3
         x, y, g = vrm_inputs.lamb_oseen_lattice(h, 1.0, nu, 1.0, eps=1e-10)
         desc = {"workload": "Lamb-Oseen lattice h=0.02, Gamma=1, nu=1e-3, t0=1, |omega|>1e-10", "n": int(len(x)),
-                "h": h, "nu": nu}
+                "h": h, "nu": nu, "order": 1, "R": 2.0}
     dt = (0.5 * h) ** 2 / (4 * nu) / 8
     desc["dt"] = dt
     return x, y, g, h, nu, dt, desc
@@ -174,14 +182,19 @@ class Clocks:
                 "source": "nvml" if self.nvml is not None else "nvidia-smi"}
 
 
-def lp_small_flops(n_lp, pivots):
-    """Algorithmic FP64 flops of the small-neighbourhood LPs (m = 5 rows,
-    K = 8 columns): per LP 120 for the Vandermonde columns and phase-I cost
-    row (8 x [2 offsets + 3 distance + 2 scalings + 3 products + 5 sums]) and
-    93 for the final residual (40 multiply-adds, 5 differences) and f~_ii
-    (8 sums); per pivot 122: 5 ratio divisions, 9 pivot-row scalings and the
-    (m+1)(K+1) = 54 multiply-adds of the tableau update."""
-    return n_lp * (120 + 93) + pivots * 122
+def lp_flops(n_lp, pivots, m=5, K=8, cols=None, col_pivots=None):
+    """Algorithmic FP64 flops of phase-I LPs with m rows on K columns (a
+    multiply-add counts 2): per LP, per column 2 offsets + 3 distance + 2
+    scalings + (m - 2) Vandermonde products + m cost-row sums, then the final
+    residual (m K multiply-adds, m differences) and f~_ii (K sums); per pivot
+    m ratio divisions, K + 1 pivot-row scalings and the (m + 1)(K + 1)
+    multiply-adds of the tableau update.  m = 5, K = 8: 213 per LP and 122 per
+    pivot.  For the full-neighbourhood LPs K varies: `cols` = sum of K and
+    `col_pivots` = sum of K x pivots over the LPs."""
+    if cols is None:
+        cols, col_pivots = n_lp * K, pivots * K
+    per_col = 7 + (m - 2) + m + 2 * m + 1
+    return cols * per_col + n_lp * m + pivots * (m + 1 + 2 * (m + 1)) + col_pivots * (1 + 2 * (m + 1))
 
 
 def run_ours(args):
@@ -209,7 +222,7 @@ def run_ours(args):
     yb[:n] = torch.from_numpy(y).to(dev)
     gi = torch.from_numpy(g).to(dev)
     go = torch.zeros(cap, dtype=torch.float64, device=dev)
-    ctx = vrm.VRM(h=h, nu=nu, precision=args.precision)
+    ctx = vrm.VRM(h=h, nu=nu, precision=args.precision, order=desc["order"], R=desc["R"])
     schedule = None
     if not args.no_autotune:
         from paper_1508_06379_gb300 import autotune
@@ -306,7 +319,7 @@ def run_ours(args):
 
     mean_stage = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage_ms.items()}
     dom = max(mean_stage, key=mean_stage.get)
-    roofline = roofline_for(dom, mean_stage[dom], stats, n) if mean_stage[dom] > 0 else None
+    roofline = roofline_for(dom, mean_stage[dom], stats, n, desc["order"]) if mean_stage[dom] > 0 else None
     if rank != 0:
         if dist:
             dist.barrier()
@@ -328,7 +341,10 @@ def run_ours(args):
         "stage_ms": {k: round(v, 4) for k, v in mean_stage.items()},
         "schedule": schedule,
         "lp": {"small_solved": int(stats["lp_small_solved"]), "small_pivots": int(stats["lp_small_pivots"]),
-               "full_solved": int(stats["lp_full_solved"]), "max_pivots": int(stats["max_pivots"])},
+               "full_solved": int(stats["lp_full_solved"]), "full_pivots": int(stats["lp_full_pivots"]),
+               "full_columns": int(stats["lp_full_columns"]), "max_pivots": int(stats["max_pivots"]),
+               "small_ok": int(stats["small_ok"]), "full_ok": int(stats["full_ok"]),
+               "no_stencil": int(stats["no_stencil"])},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
@@ -354,13 +370,19 @@ def traffic_for(kernel):
         return None
 
 
-def roofline_for(stage, ms, stats, n):
-    if stage == "lp_small":
-        flops = lp_small_flops(stats["lp_small_solved"], stats["lp_small_pivots"])
+def roofline_for(stage, ms, stats, n, order=1):
+    m = 9 if order == 2 else 5
+    if stage in ("lp_small", "lp_full"):
+        if stage == "lp_small":
+            flops = lp_flops(stats["lp_small_solved"], stats["lp_small_pivots"], m)
+        else:
+            flops = lp_flops(stats["lp_full_solved"], stats["lp_full_pivots"], m, cols=stats["lp_full_columns"],
+                             col_pivots=stats["lp_full_column_pivots"])
+        kern = "k_lp_" + stage[3:]
         ach = flops / (ms * 1e-3) / 1e12
         peak = FP64_PEAK_GFLOPS / 1000.0
-        return {"kernel": "k_lp_small", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": traffic_for("k_lp_small"),
+        return {"kernel": kern, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": traffic_for(kern) if order == 1 else None,
                 "peak_source": "FP64: 152 SMs x 2 FMA lanes/clk x 2 flop x 2.07 GHz (derived; measured FMA loop "
                                "1.198 TFLOP/s)"}
     hbm = None
@@ -389,11 +411,11 @@ def cpu_baseline(name, frac=1.0):
     workload, all host cores."""
     import oracle
     oracle.build()
-    x, y, g, h, nu, dt, _ = workload(name)
-    if name == "mixture_1m" and frac < 1.0:
+    x, y, g, h, nu, dt, desc = workload(name)
+    if name.startswith("mixture_1m") and frac < 1.0:
         x, y, g = sample_window(x, y, g, frac)
     t0 = time.time()
-    x2, y2, g2, st = oracle.step(x, y, g, h, nu, dt)
+    x2, y2, g2, st = oracle.step(x, y, g, h, nu, dt, order=desc["order"], R=desc["R"])
     t = time.time() - t0
     return {"value": len(x2) / t, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "one oracle step on %s of the workload (%d particles in, %d after insertion), %.1f s" % (
@@ -407,15 +429,16 @@ def run_reference(args):
     import oracle
     oracle.build()
     x, y, g, h, nu, dt, desc = workload(args.workload)
-    frac = 0.06 if args.workload == "mixture_1m" else 1.0
+    frac = 0.06 if args.workload.startswith("mixture_1m") else 1.0
     if frac < 1.0:
         x, y, g = sample_window(x, y, g, frac)
+    kw = dict(order=desc.get("order", 1), R=desc.get("R", 2.0))
     for _ in range(args.warmup):
-        oracle.step(x, y, g, h, nu, dt)
+        oracle.step(x, y, g, h, nu, dt, **kw)
     t0 = time.time()
     parts = 0
     for _ in range(args.steps):
-        x2, y2, g2, st = oracle.step(x, y, g, h, nu, dt)
+        x2, y2, g2, st = oracle.step(x, y, g, h, nu, dt, **kw)
         parts += len(x2)
     t = time.time() - t0
     value = parts / t
@@ -595,7 +618,10 @@ def run_batched(args):
         "clocks": ck,
         "roofline": None,
         "lp": {"small_solved": int(stats["lp_small_solved"]), "small_pivots": int(stats["lp_small_pivots"]),
-               "full_solved": int(stats["lp_full_solved"]), "max_pivots": int(stats["max_pivots"])},
+               "full_solved": int(stats["lp_full_solved"]), "full_pivots": int(stats["lp_full_pivots"]),
+               "full_columns": int(stats["lp_full_columns"]), "max_pivots": int(stats["max_pivots"]),
+               "small_ok": int(stats["small_ok"]), "full_ok": int(stats["full_ok"]),
+               "no_stencil": int(stats["no_stencil"])},
         "cpu_baseline": None,
     }
     print(json.dumps(line))
@@ -732,7 +758,8 @@ def run_learned(args):
                    [losses[0][1], losses[-1][1]], "data_s": round(t_data, 2), "train_s": round(t_train, 2)},
         "plain_lp": {"value": a["value"], "unit": UNIT, "ms_per_step": a["ms"], "stage_ms": a["stage"]},
         "learned": {"accepted": int(st["learned_ok"]), "rejected": int(st["learned_rejected"]),
-                    "accepted_on_five_slot_basis": int(st["learned_square"]),
+                    "accepted_on_first_support": int(st["learned_square"]),
+                    "supports_screened_per_particle": st["learned_screens"] / max(1, st["n_diffused"]),
                     "acceptance": st["learned_ok"] / max(1, st["n_diffused"]),
                     "lp_small_solved": int(st["lp_small_solved"]), "stage_ms": b["stage"],
                     "increment_rel_diff_vs_lp": rel},
@@ -777,10 +804,21 @@ def run_viscous(args):
     yb[:n0] = torch.from_numpy(y).to(dev)
     bufs = [torch.zeros(cap, dtype=torch.float64, device=dev) for _ in range(2)]
     bufs[0][:n0] = torch.from_numpy(g).to(dev)
-    ctx = vrm.VRM(h=h, nu=nu)
+    ctx = vrm.VRM(h=h, nu=nu, precision=args.precision)
+    train_s = None
+    if args.learned:
+        from paper_1508_06379_gb300 import learn
+        t_tr = time.time()
+        X, T, N = learn.make_dataset(args.train_rows)
+        net, _ = learn.train(X, T, N, epochs=args.train_epochs, batch=4096, lr=2e-3)
+        del X, T
+        torch.cuda.synchronize()
+        train_s = time.time() - t_tr
+        ctx.set_mlp(net)
     vel = dict(gamma=gamma, nu=nu)
     stream = torch.cuda.current_stream()
     n, t, k = n0, t0, 0
+    learned_ok = diffused_sum = 0
     for _ in range(args.warmup):
         n, _ = ctx.rk3_step(xb, yb, n, bufs[k % 2], bufs[(k + 1) % 2], t, dt, vel)
         t += dt
@@ -802,6 +840,8 @@ def run_viscous(args):
         parts += n
         t += dt
         k += 1
+        learned_ok += st["learned_ok"]
+        diffused_sum += 3 * st["n_diffused"]
     t_wall1 = time.time()
     launches = vrm.launch_count() - launches0
     ck = clocks.stop(t_wall0, t_wall1)
@@ -831,7 +871,11 @@ def run_viscous(args):
     line = {
         "metric": METRIC, "value": parts / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": ("f64" if args.precision == "fp64" else "f64 (application fp32)") +
+                 (", learned proposal bf16" if args.learned else ""), "data": "synthetic",
+        "learned": {"on": bool(args.learned), "fraction_of_stencils": learned_ok / max(1, diffused_sum),
+                    "train_s": train_s},
         "e_u": {"value": e_u, "targets": int(qx.numel()), "sources": int(n), "eps": 3 * h, "direct_sum_ms": bs_ms,
                 "interactions_per_s": qx.numel() * n / (bs_ms * 1e-3)},
         "config": {"workload": VISCOUS_DESC % h, "n_initial": int(n0), "n_final": int(n), "h": h, "nu": nu,

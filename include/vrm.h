@@ -18,13 +18,14 @@
  *   - Neighbour rows are "ELL" rows of width k_cap: row i occupies
  *     nbr_idx[i*k_cap .. i*k_cap + min(nbr_count[i], k_cap)), ascending
  *     global indices; entries past the count are not written.
- *   - Stencils have width VRM_STENCIL_W: stencil i occupies
+ *   - Stencils have width W = vrm_stencil_width(order) (VRM_STENCIL_W = 8
+ *     for n = 1, VRM_STENCIL_W2 = 12 for n = 2): stencil i occupies
  *     cols[i*W .. i*W+W), f[i*W .. i*W+W): the nonzero h-scaled weights
  *     f~_ij = h^2 f_ij in the LP's column order, padded with -1 / 0.0;
  *     fii[i] = f~_ii.
- *   - small (n*8 int32) and cols (n*VRM_STENCIL_W int32) must start on a
- *     16-byte boundary (their rows are read as 16-byte vectors); a
- *     misaligned pointer gives VRM_ERR_ARG.
+ *   - small (n*8 int32) and cols (n*W int32) must start on a 16-byte
+ *     boundary (their rows are read as 16-byte vectors); a misaligned
+ *     pointer gives VRM_ERR_ARG.
  *   - Every call is asynchronous on the given stream, except that a call
  *     which returns a size or statistics to a host pointer synchronises the
  *     stream before it returns.
@@ -33,7 +34,8 @@
  *     output arrays are unspecified.
  *   - Derived constants are computed once in vrm_create, in FP64, as
  *       lo2 = (r h)^2, hi2 = (R h)^2         annulus bounds (Eq. neighbourhood)
- *       c_bound = C_diff * ((h*h)*h)         growth-control bound (Eq. reduced_bound, n = 1)
+ *       c_bound = C_diff * ((h*h)*h)         growth-control bound h^{n+2} (Eq. reduced_bound), n = 1
+ *       c_bound = C_diff * (((h*h)*h)*h)                                                      n = 2
  *       nu_over_h2 = nu / (h*h)
  *       inv_h = 1 / h
  *     so that a caller can reproduce every decision bit for bit.
@@ -56,8 +58,11 @@ typedef int vrm_status;
 #define VRM_ERR_CUDA 3       /* a CUDA runtime call failed */
 #define VRM_ERR_UNSUPPORTED 4 /* a parameter value this build does not support */
 
-/* Stencil width: columns kept per particle (small neighbourhood = 8). */
-#define VRM_STENCIL_W 8
+/* Stencil width: columns kept per particle.  A basic solution of the m-row
+   LP has at most m nonzero weights: m = 5 for n = 1 (the small neighbourhood's
+   8 columns fit), m = 9 for n = 2 (Eq. momcondmv). */
+#define VRM_STENCIL_W 8   /* n = 1 */
+#define VRM_STENCIL_W2 12 /* n = 2 */
 /* Largest neighbour-row width (k_cap) the library accepts. */
 #define VRM_KCAP_MAX 32
 
@@ -84,7 +89,8 @@ typedef struct vrm_params {
   double R;          /* outer annulus radius in units of h (paper: 2) */
   double nu;         /* kinematic viscosity */
   double c_diff;     /* growth-control constant C_diff (Eq. reduced_bound) */
-  int32_t order;     /* consistency order n; this build supports n = 1 (m = 5 rows) */
+  int32_t order;     /* consistency order n: 1 (m = 5 moment rows) or 2 (m = 9, cubic
+                        moments added; Eqs. cond_two, cond_alpha) */
   int32_t k_cap;     /* neighbour-row width, 8 <= k_cap <= VRM_KCAP_MAX */
   int32_t max_rounds;/* insertion rounds per step (Sec. 4.2), >= 0 */
   int32_t fallback;  /* 1: retry failed small neighbourhoods on the full one (Sec. 4.3) */
@@ -114,7 +120,10 @@ typedef struct vrm_stats {
   int64_t lp_full_pivots;  /* pivots summed over those LPs */
   int64_t learned_ok;      /* stencils from the learned proposal (vrm_set_mlp) */
   int64_t learned_rejected; /* proposals rejected (then solved by the LP) */
-  int64_t learned_square;  /* of learned_ok: accepted on the network's five-slot basis alone */
+  int64_t learned_square;  /* of learned_ok: accepted on the first support tried (the network's top five) */
+  int64_t lp_full_columns;       /* columns summed over the full-neighbourhood LPs */
+  int64_t lp_full_column_pivots; /* columns x pivots summed over them (their algorithmic work) */
+  int64_t learned_screens; /* five-slot supports screened by the learned path (binary32 solves) */
 } vrm_stats;
 
 /* Stages of vrm_step, for vrm_stage_times. */
@@ -132,6 +141,10 @@ typedef struct vrm_ctx vrm_ctx;
 /* Paper defaults: r = 1/2, R = 2, n = 1, C_diff = 1 (Sec. 4.2, 6), k_cap = 32,
    8 insertion rounds, fallback on, FP64; h and nu set to 1. */
 void vrm_default_params(vrm_params* p);
+
+/* Stencil width W of consistency order n (8 for n = 1, 12 for n = 2, -1
+   otherwise): the row length of cols and f in every call below. */
+int32_t vrm_stencil_width(int32_t order);
 
 /* Text of a status code (static storage). */
 const char* vrm_status_string(vrm_status s);
@@ -189,7 +202,10 @@ vrm_status vrm_build_neighbourhoods(vrm_ctx* ctx, const double* x, const double*
  * Redistribution weights (Sec. 2 Eq. momcondmv, Sec. 4.1, 4.3) of every
  * particle with diffused[i] = 1: the phase-I simplex on the small
  * neighbourhood (columns ordered by (|r_ij|^2, j)), rows
- * (1,0) (0,1) (2,0) (1,1) (0,2) in xi = r_ij / h with b = (0,0,2,0,2);
+ * (1,0) (0,1) (2,0) (1,1) (0,2) in xi = r_ij / h with b = (0,0,2,0,2), for
+ * n = 2 followed by (3,0) (2,1) (1,2) (0,3) with b = 0, each monomial a
+ * product of separately rounded factors ((xi xi) xi, (xi xi) eta,
+ * xi (eta eta), (eta eta) eta);
  * artificials start the basis; entering column = lowest index with reduced
  * cost < -1e-9; leaving row = minimum ratio over pivots > 1e-9 (basic values
  * <= 1e-11 count as zero), ties within 1e-12 max(1, ratio) to the lowest
@@ -200,7 +216,8 @@ vrm_status vrm_build_neighbourhoods(vrm_ctx* ctx, const double* x, const double*
  * ordered by (|r_ij|^2, j)); if that fails too the stencil is zero.
  * f~_ii = -sum_j f~_ij in column order.
  * Inputs are the outputs of vrm_build_neighbourhoods on the same x, y, n.
- * cols, f:  n*VRM_STENCIL_W out; fii: n out; status: n out (VRM_LP_*).
+ * cols, f:  n*W out (W = vrm_stencil_width(order)); fii: n out; status: n
+ *           out (VRM_LP_*).
  * stats:    host, optional; fills small_ok, full_ok, no_stencil, max_pivots,
  *           n_diffused and synchronises.
  */
@@ -368,7 +385,8 @@ vrm_status vrm_mlp_error(vrm_mlp* net, cudaStream_t stream);
  * (small neighbourhood, then the full-neighbourhood retry).  The network must
  * outlive its use; its weights may change between steps (training).  NULL
  * restores the LP for every particle.  The network's time counts in the
- * VRM_STAGE_LP_SMALL stage.
+ * VRM_STAGE_LP_SMALL stage.  The network proposes n = 1 stencils: a context
+ * of order 2 gives VRM_ERR_UNSUPPORTED for a non-NULL net.
  */
 vrm_status vrm_set_mlp(vrm_ctx* ctx, vrm_mlp* net);
 
@@ -384,12 +402,14 @@ vrm_status vrm_learned_features(vrm_ctx* ctx, const double* x, const double* y, 
  * neighbourhood (small: device int32 [n][8] as from vrm_build_neighbourhoods,
  * 16-byte aligned): accepted stencils are written as by the LP (status
  * VRM_LP_LEARNED), rejected ones get VRM_LP_NONE and a zero stencil.
- * *n_accepted (host) receives the count.  Synchronises. */
+ * *n_accepted (host) receives the count.  Synchronises.  n = 1 only
+ * (VRM_ERR_UNSUPPORTED for a context of order 2); stencil width 8. */
 vrm_status vrm_learned_project(vrm_ctx* ctx, const double* x, const double* y, const int32_t* list, int32_t m,
                                const int32_t* slots, const float* f0, const int32_t* small, int32_t* cols, double* f,
                                double* fii, uint8_t* status, int32_t* n_accepted, cudaStream_t stream);
 /* Training targets: T fp32 [m][32], the weight f~ of each listed particle's
- * stencil (cols, f as written by vrm_solve_weights) at each slot's particle. */
+ * stencil (cols, f as written by vrm_solve_weights for n = 1, width 8) at
+ * each slot's particle. */
 vrm_status vrm_learned_targets(const int32_t* list, int32_t m, const int32_t* slots, const int32_t* cols,
                                const double* f, float* T, cudaStream_t stream);
 

@@ -59,6 +59,8 @@ def lib():
                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P]
         L.orc_rows.restype = ctypes.c_int
         L.orc_rows.argtypes = [ctypes.c_int]
+        L.orc_stencil_width.restype = ctypes.c_int
+        L.orc_stencil_width.argtypes = [ctypes.c_int]
         L.orc_vandermonde_column.restype = None
         L.orc_vandermonde_column.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, P]
         L.orc_phase1.restype = ctypes.c_int
@@ -181,7 +183,13 @@ def phase1(V, b):
     return st, f[:K], npiv.value, res.value
 
 
-def solve_weights(x, y, diffused, nb, h, order=1, fallback=True, W=8):
+def stencil_width(order):
+    """Slots per stencil: at most m nonzero weights (m = 5 for n = 1, 9 for n = 2)."""
+    return lib().orc_stencil_width(int(order))
+
+
+def solve_weights(x, y, diffused, nb, h, order=1, fallback=True, W=None):
+    W = stencil_width(order) if W is None else W
     x, y = _f64(x), _f64(y)
     n = len(x)
     k_cap = nb["idx"].shape[1]

@@ -20,25 +20,30 @@ and signs; everything else goes to the LP.  The pieces:
 * loss(): mean squared error over the valid slots against the LP weights
   f~ of the same particle (f~ = h^2 f, Eq. momcondmv scaling).
 * adamw(): Adam with decoupled weight decay (Loshchilov and Hutter).
-* support() and project(): the candidates are the slots holding the small
+* learned_stencil(): the candidates are the slots holding the small
   neighbourhood of Sec. 4.3 (the closest particle of every segment: the
-  columns the LP itself works on); up to 8 of them with the largest positive
-  proposal form the support S; the proposal is corrected by the smallest change that
-  meets the moment conditions on S,
-      f_S = f0_S + V_S^T (V_S V_S^T)^{-1} (b - V_S f0_S),
-  and accepted iff every f_j >= 0 and the residual |V_S f_S - b|_inf is at
-  most 1e-12 (Sec. 3.1's non-negativity, Eq. cond_two/cond_alpha).  While a
-  corrected weight is negative and |S| > 5, the slot with the smallest
-  corrected weight (ties: the later slot) leaves S and the original proposal
-  is corrected again on the smaller support; at |S| = 5 the correction is the
-  unique solution on those five neighbours.  A Gram matrix V_S V_S^T whose
-  Cholesky pivot falls to 1e-10 of its largest diagonal entry rejects.
-  Before all that, the five slots with the largest proposals are tried alone:
-  the square system V_5 f = b (Gaussian elimination with partial pivoting,
-  a pivot at most 1e-12 of the largest |entry| counts as singular) gives the
-  vertex stencil on the network's choice of basis, accepted under the same
-  test; only if it fails does the least-change path above run.
+  columns the LP itself works on), ranked by the network's proposal (larger
+  first, ties to the lower slot).  The proposal chooses the stencil's
+  support: five candidates at a time, in the order subset_order() fixes
+  (increasing sum of ranks, ties lexicographic: the top five first), the
+  moment conditions V_S f = b (rows (1,0) (0,1) (2,0) (1,1) (0,2) of Eq.
+  momcondmv, b from Eqs. cond_two, cond_alpha) are solved on the support S.
+  The first support whose solution is non-negative (Sec. 3.1) with residual
+  |V_S f - b|_inf <= 1e-12 is the stencil: the projection of the proposal
+  onto the moment conditions within its support, an exact vertex of the same
+  feasible set the LP searches.  Each support is screened first in binary32
+  (square_solve32: every operation rounded to float32, the same sequence as
+  the GPU's), and only a support whose binary32 weights all exceed -1e-6 is
+  solved in FP64 (square_solve) and tested; FP64 weights in [-1e-13, 0) are
+  zeros of the vertex.  No passing support: the particle goes to the LP.
+* support(), project(), gram_ok(): the least-change correction
+      f_S = f0_S + V_S^T (V_S V_S^T)^{-1} (b - V_S f0_S)
+  of a proposal on a support of up to eight slots (the smallest change that
+  meets the moment conditions), with its conditioning test; reference
+  pieces for the square solve (on five slots the two coincide).
 """
+import itertools
+
 import numpy as np
 
 K_SLOTS = 32
@@ -245,7 +250,6 @@ def gram_ok(V, rel=1e-10):
     return True
 
 
-MAX_DROPS = 3
 
 
 def square_solve(V, b, rel=1e-12):
@@ -273,42 +277,102 @@ def square_solve(V, b, rel=1e-12):
     return f
 
 
-def learned_stencil(x, y, h, i, slots, f0, small=None):
-    """The learned stencil of particle i from its slot map, proposal and
-    small neighbourhood (8 indices, -1 empty; None: every slot is a
-    candidate): (accepted, particle indices, f~ in slot order, f~_ii)."""
-    p32 = np.asarray(f0, dtype=np.float32)
-    inv_h = 1.0 / h
+SCREEN_TOL = np.float32(1e-6)  # binary32 screen: weights above -SCREEN_TOL go to the FP64 solve
+SCREEN_PIVOT = np.float32(1e-6)  # binary32 screen: relative pivot threshold
+SNAP = 1e-13  # FP64 weights in [-SNAP, 0) are zeros of the vertex
 
-    def offsets(S):
+
+def subset_order(nc):
+    """The 5-subsets of candidate ranks 0..nc-1 in the order they are tried:
+    increasing sum of ranks, ties in lexicographic order (the network's top
+    five first, then one rank swapped in at a time, and so on)."""
+    return sorted(itertools.combinations(range(nc), 5), key=lambda r: (sum(r), r))
+
+
+def square_solve32(xi, eta):
+    """Binary32 Gaussian elimination of V_S f = b on five columns, every
+    product, quotient and difference rounded to float32 in this order:
+    V entries xi, eta, xi*xi, xi*eta, eta*eta from float32(xi), float32(eta);
+    pivot = first largest |entry| of the column at or below the diagonal,
+    None if it is not above SCREEN_PIVOT * (largest |V entry|); rows below
+    get A[q][c] - (A[q][k] / A[k][k]) * A[k][c] for c > k and the right-hand
+    side alike; back substitution f_k = (r_k - sum_q A[k][q] f_q) / A[k][k]
+    with the sum taken q = k+1, ..., 4."""
+    f32 = np.float32
+    A = []
+    for r in range(5):
+        A.append([f32(0)] * 6)
+    for c in range(5):
+        a, e = f32(xi[c]), f32(eta[c])
+        col = (a, e, f32(a * a), f32(a * e), f32(e * e))
+        for r in range(5):
+            A[r][c] = col[r]
+    for r in range(5):
+        A[r][5] = f32(2.0) if r in (2, 4) else f32(0.0)
+    vmax = f32(0.0)
+    for r in range(5):
+        for c in range(5):
+            vmax = max(vmax, abs(A[r][c]))
+    tiny = f32(SCREEN_PIVOT * vmax)
+    for k in range(5):
+        p = k
+        for q in range(k + 1, 5):
+            if abs(A[q][k]) > abs(A[p][k]):
+                p = q
+        if not abs(A[p][k]) > tiny:
+            return None
+        A[k], A[p] = A[p], A[k]
+        for q in range(k + 1, 5):
+            m = f32(A[q][k] / A[k][k])
+            for c in range(k + 1, 6):
+                A[q][c] = f32(A[q][c] - f32(m * A[k][c]))
+    f = [f32(0.0)] * 5
+    for k in range(4, -1, -1):
+        acc = A[k][5]
+        for q in range(k + 1, 5):
+            acc = f32(acc - f32(A[k][q] * f[q]))
+        f[k] = f32(acc / A[k][k])
+    return np.array(f, dtype=np.float32)
+
+
+def candidates(f0, slots, small=None, cap=SUPPORT_MAX):
+    """Candidate slots ranked by proposal (larger first, ties to the lower
+    slot): the slots holding a small-neighbourhood particle (small: its 8
+    indices, -1 empty), or, without small, the cap best valid slots."""
+    p32 = np.asarray(f0, dtype=np.float32)
+    ok = set(int(a) for a in small if a >= 0) if small is not None else None
+    c = [k for k in range(len(p32)) if slots[k] >= 0 and (ok is None or int(slots[k]) in ok)]
+    c.sort(key=lambda k: (-float(p32[k]), k))
+    return c[:cap]
+
+
+def learned_stencil(x, y, h, i, slots, f0, small=None, trials=False):
+    """The learned stencil of particle i from its slot map, proposal and
+    small neighbourhood (8 indices, -1 empty; None: the 8 best valid slots
+    are the candidates): (accepted, particle indices, f~, f~_ii), the nonzero
+    weights in slot order; with trials=True also the number of supports
+    screened."""
+    ranked = candidates(f0, slots, small)
+    inv_h = 1.0 / h
+    tried = 0
+    for sub in subset_order(len(ranked)):
+        tried += 1
+        S = sorted(ranked[r] for r in sub)
         js = [int(slots[k]) for k in S]
         xi = np.array([(x[j] - x[i]) * inv_h for j in js])
         eta = np.array([(y[j] - y[i]) * inv_h for j in js])
-        return js, xi, eta
-
-    # the network's basis alone: the square system on the top five slots
-    S5 = support(f0, slots, cap=5, allowed=small)
-    if len(S5) == 5:
-        js, xi, eta = offsets(S5)
+        f32 = square_solve32(xi, eta)
+        if f32 is None or not np.all(f32 >= -SCREEN_TOL):
+            continue
         V = vandermonde(xi, eta)
         f = square_solve(V, B_RHS)
-        if f is not None and np.all(f >= 0.0) and float(np.max(np.abs(V @ f - B_RHS))) <= ACCEPT_RESID:
-            return True, js, f, -float(np.sum(f))
-    # least change on up to eight slots, dropping the most negative
-    S = support(f0, slots, allowed=small)
-    f = None
-    js = []
-    for _ in range(MAX_DROPS + 1):
-        if len(S) < 5:
-            break
-        js, xi, eta = offsets(S)
-        if not gram_ok(vandermonde(xi, eta)):
-            return False, js, None, 0.0
-        f, res = project(xi, eta, p32[S].astype(np.float64))
-        if np.all(f >= 0.0) and res <= ACCEPT_RESID:
-            return True, js, f, -float(np.sum(f))
-        if len(S) == 5:
-            break
-        worst = min(range(len(S)), key=lambda p: (f[p], -p))
-        S = S[:worst] + S[worst + 1:]
-    return False, js, f, 0.0
+        if f is None:
+            continue
+        f = np.where((f < 0.0) & (f >= -SNAP), 0.0, f)
+        if np.all(f >= 0.0) and float(np.max(np.abs(V @ f - B_RHS))) <= ACCEPT_RESID:
+            nz = [q for q in range(5) if f[q] != 0.0]
+            fo = f[nz]
+            out = (True, [js[q] for q in nz], fo, -float(np.sum(fo)))
+            return out + (tried,) if trials else out
+    out = (False, [], None, 0.0)
+    return out + (tried,) if trials else out

@@ -475,6 +475,11 @@ long orc_insert(double* x, double* y, long n, long capacity, const unsigned char
 /* Number of moment rows: multi-indices 1 <= |alpha| <= n+1 (Eq. momcondmv). */
 int orc_rows(int order) { return order == 2 ? 9 : 5; }
 
+/* Stencil slots kept per particle: a basic solution of the m-row LP has at
+   most m nonzero weights, so 8 slots hold every n = 1 stencil (m = 5) and
+   12 every n = 2 stencil (m = 9). */
+int orc_stencil_width(int order) { return order == 2 ? 12 : 8; }
+
 /*
  * Column of the Vandermonde matrix for one neighbour (Eq. momcondmv), rows in
  * the order (1,0) (0,1) (2,0) (1,1) (0,2) [(3,0) (2,1) (1,2) (0,3)], in the
@@ -869,7 +874,7 @@ long orc_step(double* x, double* y, long n, long capacity, const double* gamma_i
   st->open_segments = open;
   st->n_inserted = n2 - n;
   st->n_out = n2;
-  int W = 8;
+  int W = orc_stencil_width(order);
   int* count = (int*)malloc(sizeof(int) * (size_t)n2);
   int* idx = (int*)malloc(sizeof(int) * (size_t)n2 * (size_t)k_cap);
   unsigned char* mask = (unsigned char*)malloc((size_t)n2);

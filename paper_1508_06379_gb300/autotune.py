@@ -16,9 +16,9 @@ its own stage of the step (CUDA events recorded inside the step's graph):
 
 Every candidate's output (positions and Gamma after the step) is checked to
 be bit-identical to the default schedule's; a difference is an error.
-Results are cached as JSON per device, k_cap and size bucket (nearest power
-of two of the particle count); batches take the schedule of each cloud's
-bucket.
+Results are cached as JSON per device, k_cap, consistency order and size
+bucket (nearest power of two of the particle count); batches take the
+schedule of each cloud's bucket.
 """
 import json
 import math
@@ -38,8 +38,9 @@ def bucket(n):
     return int(round(math.log2(max(int(n), 1))))
 
 
-def cache_key(device, k_cap, n):
-    return "%s|k%d|n2^%d" % (device, int(k_cap), bucket(n))
+def cache_key(device, k_cap, n, order=1):
+    o = "" if int(order) == 1 else "|o%d" % int(order)
+    return "%s|k%d%s|n2^%d" % (device, int(k_cap), o, bucket(n))
 
 
 def default_cache_path():
@@ -118,8 +119,8 @@ def tune_context(ctx, x, y, n, gamma_in, gamma_out, dt, reps=5):
 
 
 class Autotuner:
-    """Schedules per (device, k_cap, size bucket), tuned on first use and
-    kept in a JSON file."""
+    """Schedules per (device, k_cap, order, size bucket), tuned on first use
+    and kept in a JSON file."""
 
     def __init__(self, path=None, reps=5):
         self.path = path or default_cache_path()
@@ -140,13 +141,13 @@ class Autotuner:
             json.dump(self.table, f, indent=1, sort_keys=True)
         os.replace(tmp, self.path)
 
-    def lookup(self, k_cap, n):
-        return self.table.get(cache_key(device_name(), k_cap, n))
+    def lookup(self, k_cap, n, order=1):
+        return self.table.get(cache_key(device_name(), k_cap, n, order))
 
     def schedule_for(self, ctx, cloud):
         """Cached schedule of the cloud's bucket, tuned on this cloud if
         missing.  cloud: dict with x, y, n, gamma_in, gamma_out, dt."""
-        key = cache_key(device_name(), ctx.k_cap, cloud["n"])
+        key = cache_key(device_name(), ctx.k_cap, cloud["n"], getattr(ctx, "order", 1))
         if key not in self.table:
             best, _ = tune_context(ctx, cloud["x"], cloud["y"], cloud["n"], cloud["gamma_in"], cloud["gamma_out"],
                                    cloud["dt"], self.reps)
@@ -173,7 +174,7 @@ class Autotuner:
                 by_bucket.setdefault(bucket(c["n"]), []).append(k)
         chosen = {}
         for b, slots in sorted(by_bucket.items()):
-            key = cache_key(device_name(), p.k_cap, clouds[slots[0]]["n"])
+            key = cache_key(device_name(), p.k_cap, clouds[slots[0]]["n"], p.order)
             if key not in self.table:
                 rep = max(slots, key=lambda k: int(clouds[k]["n"]))
                 c = clouds[rep]

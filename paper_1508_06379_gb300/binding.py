@@ -17,7 +17,8 @@ VRM_ERR_ARG = 1
 VRM_ERR_CAPACITY = 2
 VRM_ERR_CUDA = 3
 VRM_ERR_UNSUPPORTED = 4
-STENCIL_W = 8
+STENCIL_W = 8    # n = 1
+STENCIL_W2 = 12  # n = 2
 KCAP_MAX = 32
 PREC_FP64 = 0
 PREC_MIXED = 1
@@ -39,7 +40,9 @@ class Stats(ctypes.Structure):
                 ("max_dt_ratio", ctypes.c_double), ("lp_small_solved", ctypes.c_int64),
                 ("lp_small_pivots", ctypes.c_int64), ("lp_full_solved", ctypes.c_int64),
                 ("lp_full_pivots", ctypes.c_int64), ("learned_ok", ctypes.c_int64),
-                ("learned_rejected", ctypes.c_int64), ("learned_square", ctypes.c_int64)]
+                ("learned_rejected", ctypes.c_int64), ("learned_square", ctypes.c_int64),
+                ("lp_full_columns", ctypes.c_int64), ("lp_full_column_pivots", ctypes.c_int64),
+                ("learned_screens", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -95,6 +98,7 @@ I32 = ctypes.c_int32
 SIGNATURES = {
     "vrm_default_params": (None, [P]),
     "vrm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "vrm_stencil_width": (ctypes.c_int32, [I32]),
     "vrm_create": (ctypes.c_int, [P, P]),
     "vrm_destroy": (None, [P]),
     "vrm_insert_reduce": (ctypes.c_int, [P, P, P, I32, I32, P, P, P, P, P]),
@@ -224,6 +228,8 @@ class VRM:
         p.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[precision]
         self.params = p
         self.k_cap = int(k_cap)
+        self.order = int(order)
+        self.W = int(self.lib.vrm_stencil_width(int(order)))  # stencil row length
         h_ = ctypes.c_void_p()
         st = self.lib.vrm_create(ctypes.byref(p), ctypes.byref(h_))
         if st != VRM_OK:
@@ -278,7 +284,7 @@ class VRM:
     def solve_weights(self, x, y, n, diffused, nb, out=None, stats=True):
         dev = x.device
         o = out or {}
-        W = STENCIL_W
+        W = self.W
         cols = o.get("cols", torch.empty(max(n, 1) * W, dtype=torch.int32, device=dev))
         f = o.get("f", torch.empty(max(n, 1) * W, dtype=torch.float64, device=dev))
         fii = o.get("fii", torch.empty(max(n, 1), dtype=torch.float64, device=dev))
@@ -297,7 +303,7 @@ class VRM:
     def apply(self, n, n_gamma, gamma, diffused, nb, w, dgamma=None):
         if dgamma is None:
             dgamma = torch.empty(max(n, 1), dtype=torch.float64, device=gamma.device)
-        W = STENCIL_W
+        W = self.W
         st = self.lib.vrm_apply(
             self.ctx, int(n), int(n_gamma), _ptr(gamma, torch.float64, "gamma", n_gamma),
             _ptr(diffused, torch.uint8, "diffused", n), _ptr(nb["count"], torch.int32, "nbr_count", n),

@@ -359,11 +359,11 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.nbr_count, n);
   VRM_ALLOC(s.nbr_idx, (long)n * k);
   VRM_ALLOC(s.small, (long)n * 8);
-  VRM_ALLOC(s.cols, (long)n * VRM_STENCIL_W);
+  VRM_ALLOC(s.cols, (long)n * ctx->c.w);
   VRM_ALLOC(s.fail_list, n);
   VRM_ALLOC(s.seg_mask, n);
   VRM_ALLOC(s.status, n);
-  VRM_ALLOC(s.f, (long)n * VRM_STENCIL_W);
+  VRM_ALLOC(s.f, (long)n * ctx->c.w);
   VRM_ALLOC(s.fii, n);
   VRM_ALLOC(s.ds, 1);
   VRM_ALLOC(s.counters, 8);
@@ -395,7 +395,7 @@ vrm_status check_params(const vrm_params* p) {
   if (!(p->c_diff >= 0) || !std::isfinite(p->c_diff)) return VRM_ERR_ARG;
   if (p->k_cap < 8 || p->k_cap > VRM_KCAP_MAX) return VRM_ERR_ARG;
   if (p->max_rounds < 0 || p->max_rounds > 1000) return VRM_ERR_ARG;
-  if (p->order != 1) return VRM_ERR_UNSUPPORTED;
+  if (p->order != 1 && p->order != 2) return VRM_ERR_UNSUPPORTED;
   if (p->precision != VRM_PREC_FP64 && p->precision != VRM_PREC_MIXED) return VRM_ERR_UNSUPPORTED;
   return VRM_OK;
 }
@@ -413,7 +413,8 @@ void fill_consts(const vrm_params& p, Consts& c) {
   c.Rh = Rh;
   volatile double hh = h * h;  // keep the documented rounding order
   volatile double hhh = hh * h;
-  c.c_bound = p.c_diff * hhh;
+  volatile double hp = p.order == 2 ? hhh * h : hhh;  // h^{n+2}
+  c.c_bound = p.c_diff * hp;
   c.nu_over_h2 = p.nu / hh;
   // insertion offsets: radius 1.5 h on the segment centre lines (s + 1/2) pi/4,
   // with cos and sin of 22.5 degrees from the half-angle identities
@@ -430,6 +431,8 @@ void fill_consts(const vrm_params& p, Consts& c) {
   c.max_rounds = p.max_rounds;
   c.fallback = p.fallback;
   c.precision = p.precision;
+  c.order = p.order;
+  c.w = vrm_stencil_width(p.order);
   default_schedule(c);
 }
 
@@ -720,6 +723,10 @@ void vrm_default_params(vrm_params* p) {
   p->precision = VRM_PREC_FP64;
 }
 
+int32_t vrm_stencil_width(int32_t order) {
+  return order == 1 ? VRM_STENCIL_W : order == 2 ? VRM_STENCIL_W2 : -1;
+}
+
 const char* vrm_status_string(vrm_status s) {
   switch (s) {
     case VRM_OK: return "ok";
@@ -868,7 +875,7 @@ vrm_status vrm_solve_weights(vrm_ctx* ctx, const double* x, const double* y, int
   VRM_CUDA(cudaMemsetAsync(s.ds, 0, sizeof(DevStats), stream));
   VRM_CUDA(ensure_learned(ctx, n, stream));
   VRM_CUDA(compact_flags(diffused, n, s.dlist, s.counters + 0, s.pos, s.scan_tmp, stream));
-  VRM_CUDA(lp_clear(n, diffused, cols, f, fii, status, stream));
+  VRM_CUDA(lp_clear(n, c.w, diffused, cols, f, fii, status, stream));
   const int* lp_list = s.dlist;
   const int* lp_count = s.counters + 0;
   if (ctx->mlp) {
@@ -896,9 +903,12 @@ vrm_status vrm_solve_weights(vrm_ctx* ctx, const double* x, const double* y, int
     stats->lp_small_pivots = (int64_t)s.h_ds->lp_small_pivots;
     stats->lp_full_solved = s.h_ds->lp_full_solved;
     stats->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
+    stats->lp_full_columns = (int64_t)s.h_ds->lp_full_columns;
+    stats->lp_full_column_pivots = (int64_t)s.h_ds->lp_full_column_pivots;
     stats->learned_ok = s.h_ds->learned_ok;
     stats->learned_rejected = s.h_ds->learned_rejected;
     stats->learned_square = s.h_ds->learned_square;
+    stats->learned_screens = (int64_t)s.h_ds->learned_screens;
   }
   if (ctx->mlp && vrm_mlp_error(ctx->mlp, stream) != VRM_OK) return VRM_ERR_CUDA;
   return VRM_OK;
@@ -1006,9 +1016,12 @@ vrm_status vrm_rk3_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t c
   st->lp_small_pivots = (int64_t)s.h_ds->lp_small_pivots;
   st->lp_full_solved = s.h_ds->lp_full_solved;
   st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
+  st->lp_full_columns = (int64_t)s.h_ds->lp_full_columns;
+  st->lp_full_column_pivots = (int64_t)s.h_ds->lp_full_column_pivots;
   st->learned_ok = s.h_ds->learned_ok;
   st->learned_rejected = s.h_ds->learned_rejected;
   st->learned_square = s.h_ds->learned_square;
+  st->learned_screens = (int64_t)s.h_ds->learned_screens;
   *n_out = s.h_state->n_cur;
   if (s.h_ds->max_count > ctx->c.row_cap) return VRM_ERR_CAPACITY;
   return VRM_OK;
@@ -1036,6 +1049,7 @@ vrm_status vrm_biot_savart(vrm_ctx* ctx, const double* xs, const double* ys, con
 
 vrm_status vrm_set_mlp(vrm_ctx* ctx, vrm_mlp* net) {
   if (!ctx) return VRM_ERR_ARG;
+  if (net && ctx->p.order != 1) return VRM_ERR_UNSUPPORTED;  // the network proposes n = 1 stencils
   if (ctx->mlp != net) {
     ctx->mlp = net;
     drop_graph(ctx);
@@ -1065,6 +1079,7 @@ vrm_status vrm_learned_project(vrm_ctx* ctx, const double* x, const double* y, c
   if (n_accepted) *n_accepted = 0;
   if (m == 0) return VRM_OK;
   if (!x || !y || !slots || !f0 || !small || !cols || !f || !fii || !status || misaligned16(small)) return VRM_ERR_ARG;
+  if (ctx->p.order != 1) return VRM_ERR_UNSUPPORTED;
   Scratch& s = ctx->s;
   VRM_CUDA(ensure_scratch(ctx, m, stream));
   VRM_CUDA(cudaMemsetAsync(s.ds, 0, sizeof(DevStats), stream));
@@ -1166,9 +1181,12 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
   st->lp_small_pivots = (int64_t)s.h_ds->lp_small_pivots;
   st->lp_full_solved = s.h_ds->lp_full_solved;
   st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
+  st->lp_full_columns = (int64_t)s.h_ds->lp_full_columns;
+  st->lp_full_column_pivots = (int64_t)s.h_ds->lp_full_column_pivots;
   st->learned_ok = s.h_ds->learned_ok;
   st->learned_rejected = s.h_ds->learned_rejected;
   st->learned_square = s.h_ds->learned_square;
+  st->learned_screens = (int64_t)s.h_ds->learned_screens;
   if (s.h_state->overflow) return VRM_ERR_CAPACITY;
   *n_out = s.h_state->n_cur;
   if (s.h_ds->max_count > ctx->p.k_cap) return VRM_ERR_CAPACITY;
@@ -1324,9 +1342,12 @@ vrm_status finish_cloud(vrm_ctx* ctx, vrm_cloud& C, vrm_stats* st) {
   st->lp_small_pivots = (int64_t)s.h_ds->lp_small_pivots;
   st->lp_full_solved = s.h_ds->lp_full_solved;
   st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
+  st->lp_full_columns = (int64_t)s.h_ds->lp_full_columns;
+  st->lp_full_column_pivots = (int64_t)s.h_ds->lp_full_column_pivots;
   st->learned_ok = s.h_ds->learned_ok;
   st->learned_rejected = s.h_ds->learned_rejected;
   st->learned_square = s.h_ds->learned_square;
+  st->learned_screens = (int64_t)s.h_ds->learned_screens;
   C.n_out = st->n_out;
   if (s.h_state->overflow) return VRM_ERR_CAPACITY;
   if (s.h_ds->max_count > ctx->p.k_cap) return VRM_ERR_CAPACITY;
@@ -1350,9 +1371,12 @@ void add_stats(vrm_stats* t, const vrm_stats& a) {
   t->lp_small_pivots += a.lp_small_pivots;
   t->lp_full_solved += a.lp_full_solved;
   t->lp_full_pivots += a.lp_full_pivots;
+  t->lp_full_columns += a.lp_full_columns;
+  t->lp_full_column_pivots += a.lp_full_column_pivots;
   t->learned_ok += a.learned_ok;
   t->learned_rejected += a.learned_rejected;
   t->learned_square += a.learned_square;
+  t->learned_screens += a.learned_screens;
 }
 
 }  // namespace

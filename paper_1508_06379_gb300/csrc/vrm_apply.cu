@@ -30,7 +30,8 @@ __device__ __forceinline__ float mul_acc<float>(double a, double b) {
 __device__ __forceinline__ double add_acc(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float add_acc(float a, float b) { return __fadd_rn(a, b); }
 
-template <typename Acc>
+// W: stencil width (8 for n = 1, 12 for n = 2); slot numbers fit 4 bits.
+template <typename Acc, int W>
 __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __restrict__ n_dev, int n_gamma,
                                                   const int* __restrict__ n_gamma_dev, const double* __restrict__ gamma,
                                                   const uint8_t* __restrict__ diffused,
@@ -60,17 +61,16 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
       const int i = row[t];
       if (selfpos == cnt && i > j) selfpos = t;
       if (i >= n_gamma || !diffused[i]) continue;
-      const int4* cr = reinterpret_cast<const int4*>(cols + (size_t)i * VRM_STENCIL_W);
-      const int4 a = cr[0], b = cr[1];
+      const int4* cr = reinterpret_cast<const int4*>(cols + (size_t)i * W);
       int slot = -1;
-      slot = (b.w == j) ? 7 : slot;
-      slot = (b.z == j) ? 6 : slot;
-      slot = (b.y == j) ? 5 : slot;
-      slot = (b.x == j) ? 4 : slot;
-      slot = (a.w == j) ? 3 : slot;
-      slot = (a.z == j) ? 2 : slot;
-      slot = (a.y == j) ? 1 : slot;
-      slot = (a.x == j) ? 0 : slot;
+#pragma unroll
+      for (int q = W / 4 - 1; q >= 0; --q) {
+        const int4 a = cr[q];
+        slot = (a.w == j) ? 4 * q + 3 : slot;
+        slot = (a.z == j) ? 4 * q + 2 : slot;
+        slot = (a.y == j) ? 4 * q + 1 : slot;
+        slot = (a.x == j) ? 4 * q : slot;
+      }
       if (slot < 0) continue;
       match |= 1u << t;
       if (t < 16)
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
       }
       const int i = row[t];
       const int slot = (int)(((t < 16 ? slot_lo >> (4 * t) : slot_hi >> (4 * (t - 16)))) & 15ull);
-      acc = add_acc(acc, mul_acc<Acc>(f[(size_t)i * VRM_STENCIL_W + slot], gamma[i]));
+      acc = add_acc(acc, mul_acc<Acc>(f[(size_t)i * W + slot], gamma[i]));
     }
     if (!self_done) acc = add_acc(acc, selfv);
     const double dg = __dmul_rn(c.nu_over_h2, (double)acc);
@@ -105,12 +105,10 @@ cudaError_t apply_gather_dev(const Consts& c, int n_bound, const int* n_dev, int
   if (n_bound <= 0) return cudaSuccess;
   const int tb = c.apply_block;
   const int blocks = (int)(((long)n_bound + tb - 1) / tb);
-  if (c.precision == VRM_PREC_MIXED)
-    k_apply<float><<<blocks, tb, 0, s>>>(c, n_bound, n_dev, n_gamma, n_gamma_dev, gamma, diffused, nbr_count, nbr_idx,
-                                         cols, f, fii, order, dgamma, gamma_out, dt, dt_dev);
-  else
-    k_apply<double><<<blocks, tb, 0, s>>>(c, n_bound, n_dev, n_gamma, n_gamma_dev, gamma, diffused, nbr_count, nbr_idx, cols,
-                                    f, fii, order, dgamma, gamma_out, dt, dt_dev);
+  auto kern = c.precision == VRM_PREC_MIXED ? (c.order == 2 ? k_apply<float, 12> : k_apply<float, 8>)
+                                             : (c.order == 2 ? k_apply<double, 12> : k_apply<double, 8>);
+  kern<<<blocks, tb, 0, s>>>(c, n_bound, n_dev, n_gamma, n_gamma_dev, gamma, diffused, nbr_count, nbr_idx, cols, f,
+                             fii, order, dgamma, gamma_out, dt, dt_dev);
   note_launch();
   return cudaGetLastError();
 }

@@ -32,6 +32,8 @@ struct Consts {
   int max_rounds;
   int fallback;
   int precision;
+  int order;      // consistency order n (1 or 2)
+  int w;          // stencil width: 8 for n = 1, 12 for n = 2
   // launch schedule (vrm_schedule); results do not depend on it
   int row_cap;           // neighbour entries kept per row (<= k_cap)
   int search_block;      // threads per block of k_search_all
@@ -81,6 +83,9 @@ struct DevStats {
   unsigned long long lp_small_pivots, lp_full_pivots;
   int lp_small_solved, lp_full_solved;
   int learned_ok, learned_rejected, learned_square;
+  unsigned long long learned_screens;        // supports screened by the learned path
+  unsigned long long lp_full_columns;        // columns summed over the full-neighbourhood LPs
+  unsigned long long lp_full_column_pivots;  // columns x pivots summed over them
 };
 
 // Growth-control selection state (device resident).
@@ -291,7 +296,7 @@ cudaError_t lp_full(const Consts& c, const double* x, const double* y, const int
                     int cap, const int* nbr_count, const int* nbr_idx, int* cols, double* f, double* fii,
                     uint8_t* status, DevStats* ds, double nu_dt, cudaStream_t s, const double* dt_dev = nullptr,
                     double nu = 0.0);
-cudaError_t lp_clear(int n, const uint8_t* diffused, int* cols, double* f, double* fii, uint8_t* status,
+cudaError_t lp_clear(int n, int w, const uint8_t* diffused, int* cols, double* f, double* fii, uint8_t* status,
                      cudaStream_t s);
 
 // vrm_apply.cu

@@ -9,21 +9,21 @@
 // x_i) / h (Eq. momcondmv scaling) in fp32 from fp32 positions, then bf16.
 //
 // Candidates are the slots holding the small neighbourhood of Sec. 4.3 (the
-// closest particle of every segment, the LP's own columns).
-// First the square system V_5 f = b on the five candidates with the largest
-// proposals (the network's choice of basis; Gaussian elimination with partial
-// pivoting, FP64): its solution is accepted under the test below.  Otherwise,
-// correction (FP64): S = the up to 8 slots with the largest positive
-// proposal (ties to the lower slot), in slot order; with V_S the rows (1,0)
-// (0,1) (2,0) (1,1) (0,2) of Eq. momcondmv at S and b = (0, 0, 2, 0, 2)
-// (Eqs. cond_two, cond_alpha),
-//   f_S = f0_S + V_S^T (V_S V_S^T)^{-1} (b - V_S f0_S),
-// the least change of f0_S that meets V_S f = b (Cholesky of the 5 x 5
-// Gram matrix).  Accepted iff |S| >= 5, the Gram matrix is well conditioned,
-// every f_j >= 0 (Sec. 3.1's non-negativity) and |V_S f_S - b|_inf <= 1e-12.
-// While a corrected weight is negative and |S| > 5, the position with the
-// smallest corrected weight (ties: the later one) leaves S and the original
-// proposal is corrected again on the rest (at most three times).
+// closest particle of every segment, the LP's own columns), ranked by the
+// network's proposal (larger first, ties to the lower slot).  The proposal
+// chooses the stencil's support: five candidates at a time, in a fixed
+// order (increasing sum of ranks, ties lexicographic: the network's top five
+// first), the moment conditions V_S f = b (rows (1,0) (0,1) (2,0) (1,1)
+// (0,2) of Eq. momcondmv, b = (0, 0, 2, 0, 2) from Eqs. cond_two and
+// cond_alpha) are solved on the support S, and the first support whose
+// solution is non-negative (Sec. 3.1) with |V_S f - b|_inf <= 1e-12 gives
+// the stencil: the projection of the proposal onto the moment conditions
+// within its support, an exact vertex of the set the LP searches.  Every
+// support is first screened in binary32 (GB300 runs fp32 at about 60 times
+// its FP64 rate): Gaussian elimination with every operation rounded to
+// float32, passed on when all weights are >= -1e-6; only then the FP64
+// solve (FP64 weights in [-1e-13, 0) are zeros of the vertex and dropped).
+// A particle with no passing support goes to the LP.
 #include <cuda_bf16.h>
 
 #include "vrm_internal.cuh"
@@ -36,8 +36,10 @@ constexpr int kSlots = 32;
 constexpr int kRow = 128;  // input row stride
 constexpr int kSup = 8;    // support cap (= stencil width)
 constexpr double kAcceptResid = 1e-12;
-constexpr double kGramPivot = 1e-10;  // relative to the largest diagonal entry
-constexpr int kMaxDrops = 3;          // support refinements (8 -> 5 slots)
+constexpr double kSnap = 1e-13;        // FP64 weights in [-kSnap, 0) are zeros
+constexpr float kScreenTol = 1e-6f;    // binary32 screen: weights >= -kScreenTol pass
+constexpr float kScreenPivot = 1e-6f;  // binary32 screen: relative pivot threshold
+constexpr int kSubsets = 56;           // 5-subsets of 8 candidate ranks
 
 }  // namespace
 
@@ -147,20 +149,11 @@ __device__ __forceinline__ double rcp64(double a) {
   r = fma(r, fma(-a, r, 1.0), r);
   return r;
 }
-// 1/sqrt(d) for d > 0 in the binary32 normal range: binary32 seed, two
-// Newton steps y <- y + y (1/2 - (d y / 2) y) in FP64.
-__device__ __forceinline__ double rsqrt64(double d) {
-  double y = widen32(__frsqrt_rn(seed32(d)));
-  const double hd = 0.5 * d;
-  y = fma(y, fma(-hd * y, y, 0.5), y);
-  y = fma(y, fma(-hd * y, y, 0.5), y);
-  return y;
-}
-
 // The square system V f = b on five neighbours (columns xi, eta) by Gaussian
 // elimination with partial pivoting (first largest |pivot|), FP64.  Returns
 // false when a pivot is at most 1e-12 of the largest |entry| or the result
-// is not a non-negative solution with residual <= kAcceptResid.
+// (weights in [-kSnap, 0) set to zero) is not a non-negative solution with
+// residual <= kAcceptResid.
 __device__ __forceinline__ bool square_stencil(const double* xi, const double* eta, double* fo) {
   double A[5][6], V[5][5];
 #pragma unroll
@@ -223,9 +216,14 @@ __device__ __forceinline__ bool square_stencil(const double* xi, const double* e
     for (int q = k + 1; q < 5; ++q) acc = fma(-A[k][q], f[q], acc);
     f[k] = acc * inv[k];
   }
+  // weights in [-kSnap, 0) are rounding zeros of the vertex
+  const unsigned long long snap = abs_bits(kSnap);
   bool ok = true;
 #pragma unroll
-  for (int s = 0; s < 5; ++s) ok = ok && nonneg_bits(f[s]);
+  for (int s = 0; s < 5; ++s) {
+    if (!nonneg_bits(f[s]) && abs_bits(f[s]) <= snap) f[s] = 0.0;
+    ok = ok && nonneg_bits(f[s]);
+  }
   const unsigned long long lim = abs_bits(kAcceptResid);
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
@@ -239,100 +237,140 @@ __device__ __forceinline__ bool square_stencil(const double* xi, const double* e
   return ok;
 }
 
-// Least-change correction of the proposal f0 (active positions of the 8
-// columns) onto V f = b: Cholesky of the Gram matrix V V^T (pivots checked
-// against kGramPivot of its largest diagonal entry), FP64.  Writes the
-// corrected weights (0 on inactive positions); returns 0 on success, 1 if a
-// weight is negative or the residual too large, 2 if the Gram matrix is
-// nearly singular.
-__device__ __forceinline__ int least_change(const double* xi, const double* eta, const double* f0s, unsigned act,
-                                            double* fs) {
-  double V[5][kSup];
-#pragma unroll
-  for (int s = 0; s < kSup; ++s) {
-    const bool on = (act >> s) & 1u;
-    V[0][s] = on ? xi[s] : 0.0;
-    V[1][s] = on ? eta[s] : 0.0;
-    V[2][s] = on ? xi[s] * xi[s] : 0.0;
-    V[3][s] = on ? xi[s] * eta[s] : 0.0;
-    V[4][s] = on ? eta[s] * eta[s] : 0.0;
-    fs[s] = on ? f0s[s] : 0.0;
+// 5-subsets of the candidate ranks 0..7 in the order they are tried
+// (increasing sum of ranks, ties in lexicographic order of the sorted rank
+// tuple), as bit masks over ranks, with the highest rank each one uses.
+struct SubsetOrder {
+  unsigned char mask[kSubsets];
+  unsigned char top[kSubsets];
+};
+
+// Of two 5-subsets with equal rank sums, the one holding the lowest rank at
+// which they differ comes first (lexicographic order of the sorted tuples).
+constexpr bool tuple_less(int a, int b) {
+  for (int bit = 0; bit < 8; ++bit) {
+    const int x = (a >> bit) & 1, y = (b >> bit) & 1;
+    if (x != y) return x > y;
   }
-  const double b[5] = {0.0, 0.0, 2.0, 0.0, 2.0};
-  double G[5][5], r[5];
-#pragma unroll
-  for (int a = 0; a < 5; ++a) {
-    double acc = 0.0;
-#pragma unroll
-    for (int s = 0; s < kSup; ++s) acc = fma(V[a][s], fs[s], acc);
-    r[a] = b[a] - acc;
-#pragma unroll
-    for (int e = 0; e <= a; ++e) {
-      double g = 0.0;
-#pragma unroll
-      for (int s = 0; s < kSup; ++s) g = fma(V[a][s], V[e][s], g);
-      G[a][e] = g;
-    }
-  }
-  unsigned long long gmax = 0;
-#pragma unroll
-  for (int a = 0; a < 5; ++a) gmax = abs_bits(G[a][a]) > gmax ? abs_bits(G[a][a]) : gmax;
-  const long long piv_min = __double_as_longlong(kGramPivot * __longlong_as_double((long long)gmax));
-  double dinv[5];
-#pragma unroll
-  for (int a = 0; a < 5; ++a) {
-    double d = G[a][a];
-#pragma unroll
-    for (int e = 0; e < a; ++e) d = fma(-G[a][e], G[a][e], d);
-    if (!(__double_as_longlong(d) > piv_min)) return 2;  // also catches d <= 0
-    dinv[a] = rsqrt64(d);
-    G[a][a] = d * dinv[a];
-#pragma unroll
-    for (int q = a + 1; q < 5; ++q) {
-      double s3 = G[q][a];
-#pragma unroll
-      for (int e = 0; e < a; ++e) s3 = fma(-G[q][e], G[a][e], s3);
-      G[q][a] = s3 * dinv[a];
-    }
-  }
-  double w[5];
-#pragma unroll
-  for (int a = 0; a < 5; ++a) {
-    double s3 = r[a];
-#pragma unroll
-    for (int e = 0; e < a; ++e) s3 = fma(-G[a][e], w[e], s3);
-    w[a] = s3 * dinv[a];
-  }
-#pragma unroll
-  for (int a = 4; a >= 0; --a) {
-    double s3 = w[a];
-#pragma unroll
-    for (int e = a + 1; e < 5; ++e) s3 = fma(-G[e][a], w[e], s3);
-    w[a] = s3 * dinv[a];
-  }
-  bool nonneg = true;
-#pragma unroll
-  for (int s = 0; s < kSup; ++s) {
-    double acc = fs[s];
-#pragma unroll
-    for (int a = 0; a < 5; ++a) acc = fma(V[a][s], w[a], acc);
-    const bool on = (act >> s) & 1u;
-    fs[s] = on ? acc : 0.0;
-    nonneg = nonneg && nonneg_bits(fs[s]);
-  }
-  const unsigned long long lim = abs_bits(kAcceptResid);
-  bool small_res = true;
-#pragma unroll
-  for (int a = 0; a < 5; ++a) {
-    double acc = -b[a];
-#pragma unroll
-    for (int s = 0; s < kSup; ++s) acc = fma(V[a][s], fs[s], acc);
-    small_res = small_res && abs_bits(acc) <= lim;
-  }
-  return nonneg && small_res ? 0 : 1;
+  return false;
 }
 
-// Writes an accepted stencil (positions `act` of the 8 columns, in order).
+constexpr SubsetOrder make_subset_order() {
+  SubsetOrder o{};
+  int sums[kSubsets] = {};
+  int k = 0;
+  for (int m = 0; m < 256; ++m) {
+    int cnt = 0, sm = 0, top = 0;
+    for (int b = 0; b < 8; ++b)
+      if ((m >> b) & 1) {
+        ++cnt;
+        sm += b;
+        top = b;
+      }
+    if (cnt != 5) continue;
+    o.mask[k] = (unsigned char)m;
+    o.top[k] = (unsigned char)top;
+    sums[k] = sm;
+    ++k;
+  }
+  // insertion sort by (sum of ranks, lexicographic rank tuple)
+  for (int a = 1; a < kSubsets; ++a)
+    for (int b = a; b > 0; --b) {
+      const bool less = sums[b] < sums[b - 1] || (sums[b] == sums[b - 1] && tuple_less(o.mask[b], o.mask[b - 1]));
+      if (!less) break;
+      const unsigned char tm = o.mask[b], tt = o.top[b];
+      const int ts = sums[b];
+      o.mask[b] = o.mask[b - 1];
+      o.top[b] = o.top[b - 1];
+      sums[b] = sums[b - 1];
+      o.mask[b - 1] = tm;
+      o.top[b - 1] = tt;
+      sums[b - 1] = ts;
+    }
+  return o;
+}
+
+// read by broadcast: the support loop is warp-uniform
+__constant__ SubsetOrder kOrder = make_subset_order();
+
+// One column of the binary32 elimination: pivot = first largest |entry| at
+// or below the diagonal (one row swap), then the rows below get
+// A[q][c] - (A[q][K] / A[K][K]) A[K][c].  A template per column so that the
+// matrix stays in registers.
+template <int K>
+__device__ __forceinline__ void screen_column(float (&A)[5][6], float tiny, bool& ok) {
+  int p = K;
+  float best = fabsf(A[K][K]);
+#pragma unroll
+  for (int q = K + 1; q < 5; ++q) {
+    const float v = fabsf(A[q][K]);
+    p = v > best ? q : p;
+    best = v > best ? v : best;
+  }
+  ok = ok && best > tiny;
+#pragma unroll
+  for (int q = K + 1; q < 5; ++q) {
+    const bool sw = q == p;
+#pragma unroll
+    for (int c = K; c < 6; ++c) {
+      const float a = A[K][c], b = A[q][c];
+      A[K][c] = sw ? b : a;
+      A[q][c] = sw ? a : b;
+    }
+  }
+#pragma unroll
+  for (int q = K + 1; q < 5; ++q) {
+    const float m = __fdiv_rn(A[q][K], A[K][K]);
+#pragma unroll
+    for (int c = K + 1; c < 6; ++c) A[q][c] = __fsub_rn(A[q][c], __fmul_rn(m, A[K][c]));
+  }
+}
+
+// Binary32 screen of a support (columns xs, es = float32 xi, eta): Gaussian
+// elimination of V_S f = b with every product, quotient and difference
+// rounded to float32 in a fixed order (the oracle repeats it operation by
+// operation).  True iff no pivot is at most kScreenPivot times the largest
+// |entry| of V_S and every weight is >= -kScreenTol.  (After a failed pivot
+// the remaining arithmetic runs on but its result is not used.)
+__device__ __forceinline__ bool screen32(const float* xs, const float* es) {
+  float A[5][6];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    const float a = xs[c], e = es[c];
+    A[0][c] = a;
+    A[1][c] = e;
+    A[2][c] = __fmul_rn(a, a);
+    A[3][c] = __fmul_rn(a, e);
+    A[4][c] = __fmul_rn(e, e);
+  }
+#pragma unroll
+  for (int r = 0; r < 5; ++r) A[r][5] = (r == 2 || r == 4) ? 2.0f : 0.0f;
+  float vmax = 0.0f;
+#pragma unroll
+  for (int r = 0; r < 5; ++r)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) vmax = fmaxf(vmax, fabsf(A[r][c]));
+  const float tiny = __fmul_rn(kScreenPivot, vmax);
+  bool ok = true;
+  screen_column<0>(A, tiny, ok);
+  screen_column<1>(A, tiny, ok);
+  screen_column<2>(A, tiny, ok);
+  screen_column<3>(A, tiny, ok);
+  screen_column<4>(A, tiny, ok);
+  float f[5];
+#pragma unroll
+  for (int k = 4; k >= 0; --k) {
+    float acc = A[k][5];
+#pragma unroll
+    for (int q = k + 1; q < 5; ++q) acc = __fsub_rn(acc, __fmul_rn(A[k][q], f[q]));
+    f[k] = __fdiv_rn(acc, A[k][k]);
+    ok = ok && f[k] >= -kScreenTol;
+  }
+  return ok;
+}
+
+// Writes an accepted stencil: the nonzero weights at positions `act` of the
+// 8 candidates, in slot order.
 __device__ __forceinline__ double write_stencil(int i, const int* js, const double* fs, unsigned act, int* cols,
                                                 double* f, double* fii, uint8_t* status) {
   int* crow = cols + (size_t)i * VRM_STENCIL_W;
@@ -341,7 +379,7 @@ __device__ __forceinline__ double write_stencil(int i, const int* js, const doub
   int o = 0;
 #pragma unroll
   for (int s = 0; s < kSup; ++s) {
-    if ((act >> s) & 1u) {
+    if (((act >> s) & 1u) && abs_bits(fs[s]) != 0) {
       crow[o] = js[s];
       frow[o] = fs[s];
       sum = __dadd_rn(sum, fs[s]);
@@ -358,9 +396,11 @@ __device__ __forceinline__ double write_stencil(int i, const int* js, const doub
 }
 
 // One thread per listed particle.  Accepted stencils are written like the
-// LP's (columns in slot order, f~, f~_ii = -sum in that order, status
+// LP's (nonzero weights in slot order, f~_ii = -sum in that order, status
 // VRM_LP_LEARNED); rejected particles are appended to reject_list (if given)
-// or marked VRM_LP_NONE.
+// or marked VRM_LP_NONE.  The support loop runs warp-uniformly (all lanes
+// step through the subset order together until every lane has its answer)
+// so that the subset table in constant memory is read by broadcast.
 __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restrict__ x, const double* __restrict__ y,
                                                  const int* __restrict__ list, const int* __restrict__ list_count,
                                                  int m_bound, const int* __restrict__ slots, const float* __restrict__ f0,
@@ -373,19 +413,29 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
   const double nu_dt = dt_dev ? nu * *dt_dev : 0.0;
   const double inv_h2 = 1.0 / (c.h * c.h);
   int n_ok = 0, n_rej = 0, n_square = 0;
+  unsigned long long n_trials = 0;
   double st_ratio = 0.0;
   const long stride = (long)gridDim.x * blockDim.x;
   for (long base = (long)blockIdx.x * blockDim.x; base < m; base += stride) {
     const long t = base + threadIdx.x;
-    bool accepted = false;
     const bool active = t < m;
-    int i = -1;
+    int i = -1, nc = 0;
+    int js[kSup], rank[kSup];
+    double xi[kSup], eta[kSup];
+    float xf[kSup], ef[kSup];
+#pragma unroll
+    for (int s = 0; s < kSup; ++s) {
+      js[s] = -1;
+      rank[s] = kSup;
+      xi[s] = eta[s] = 0.0;
+      xf[s] = ef[s] = 0.0f;
+    }
     if (active) {
       i = list ? list[t] : (int)t;
       const float* p = f0 + (size_t)t * kSlots;
       const int* sl = slots + (size_t)t * kSlots;
-      // candidates: slots holding a small-neighbourhood particle with a
-      // positive proposal (at most 8, one per segment), in slot order
+      // candidates: the slots holding a small-neighbourhood particle (at
+      // most 8, one per segment), in slot order
       const int4 s0 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[0];
       const int4 s1 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[1];
       unsigned cand = 0;
@@ -394,92 +444,93 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
         const int j = sl[k];
         const bool in_small = j >= 0 && (j == s0.x || j == s0.y || j == s0.z || j == s0.w || j == s1.x ||
                                          j == s1.y || j == s1.z || j == s1.w);
-        if (in_small && p[k] > 0.0f) cand |= 1u << k;
+        if (in_small) cand |= 1u << k;
       }
-      const int nc = __popc(cand) < kSup ? __popc(cand) : kSup;
-      int js[kSup], kk[kSup];
+      nc = __popc(cand) < kSup ? __popc(cand) : kSup;
       float cv[kSup];
-      double xi[kSup], eta[kSup], f0s[kSup];
       const double xi0 = x[i], yi0 = y[i];
 #pragma unroll
       for (int s = 0; s < kSup; ++s) {
-        kk[s] = s < nc ? (int)__fns(cand, 0, s + 1) : 0;
-        js[s] = s < nc ? sl[kk[s]] : -1;
-        cv[s] = s < nc ? p[kk[s]] : 0.0f;
-        f0s[s] = (double)cv[s];
+        const int kk = s < nc ? (int)__fns(cand, 0, s + 1) : 0;
+        js[s] = s < nc ? sl[kk] : -1;
+        cv[s] = s < nc ? p[kk] : 0.0f;
         xi[s] = s < nc ? __dmul_rn(__dsub_rn(x[js[s]], xi0), c.inv_h) : 0.0;
         eta[s] = s < nc ? __dmul_rn(__dsub_rn(y[js[s]], yi0), c.inv_h) : 0.0;
+        xf[s] = __double2float_rn(xi[s]);
+        ef[s] = __double2float_rn(eta[s]);
       }
       // rank of every candidate (larger proposal first, ties to the lower slot)
-      unsigned in5 = 0;
 #pragma unroll
       for (int s = 0; s < kSup; ++s) {
-        int rank = 0;
+        int r = 0;
 #pragma unroll
-        for (int q = 0; q < kSup; ++q)
-          rank += (q < nc && q != s) && (cv[q] > cv[s] || (cv[q] == cv[s] && q < s));
-        if (s < nc && rank < 5) in5 |= 1u << s;
+        for (int q = 0; q < kSup; ++q) r += (q < nc && q != s) && (cv[q] > cv[s] || (cv[q] == cv[s] && q < s));
+        rank[s] = s < nc ? r : kSup;
       }
-      // the network's basis alone: the square system on the top five
-      if (nc >= 5) {
-        double x5[5], e5[5], f5[5];
+    }
+    // supports in the fixed order: binary32 screen, then the FP64 solve
+    bool done = nc < 5, accepted = false;
+    unsigned act = 0;
+    double fs[kSup];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          const int pos = (int)__fns(in5, 0, q + 1);
-          double a = xi[0], b = eta[0];
+    for (int s = 0; s < kSup; ++s) fs[s] = 0.0;
+    int trials = 0;
+    for (int u = 0; u < kSubsets; ++u) {
+      if (__all_sync(0xffffffffu, done)) break;
+      if (done || kOrder.top[u] >= nc) continue;
+      ++trials;
+      const unsigned rm = kOrder.mask[u];
+      unsigned pm = 0;  // the support as positions (slot order)
 #pragma unroll
-          for (int s = 1; s < kSup; ++s) {
-            a = pos == s ? xi[s] : a;
-            b = pos == s ? eta[s] : b;
-          }
-          x5[q] = a;
-          e5[q] = b;
+      for (int s = 0; s < kSup; ++s) pm |= ((rm >> (rank[s] & 7)) & (rank[s] < kSup ? 1u : 0u)) << s;
+      float xs[5], es[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        const int pos = (int)__fns(pm, 0, q + 1);
+        float a = xf[0], b = ef[0];
+#pragma unroll
+        for (int s = 1; s < kSup; ++s) {
+          a = pos == s ? xf[s] : a;
+          b = pos == s ? ef[s] : b;
         }
-        if (square_stencil(x5, e5, f5)) {
-          double fs[kSup];
-          int q = 0;
-#pragma unroll
-          for (int s = 0; s < kSup; ++s) {
-            double v = 0.0;
-#pragma unroll
-            for (int u = 0; u < 5; ++u) v = (((in5 >> s) & 1u) && q == u) ? f5[u] : v;
-            fs[s] = v;
-            q += (in5 >> s) & 1u;
-          }
-          const double sum = write_stencil(i, js, fs, in5, cols, f, fii, status);
-          const double qr = __dmul_rn(__dmul_rn(nu_dt, sum), inv_h2);
-          st_ratio = qr > st_ratio ? qr : st_ratio;
-          accepted = true;
-          ++n_square;
-        }
+        xs[q] = a;
+        es[q] = b;
       }
-      // least change on all candidates, dropping the smallest corrected weight
-      unsigned act = nc >= 5 ? (1u << nc) - 1u : 0u;
-      for (int attempt = 0; attempt <= kMaxDrops && !accepted && __popc(act) >= 5; ++attempt) {
-        double fs[kSup];
-        const int rc = least_change(xi, eta, f0s, act, fs);
-        if (rc == 0) {
-          const double sum = write_stencil(i, js, fs, act, cols, f, fii, status);
-          const double qr = __dmul_rn(__dmul_rn(nu_dt, sum), inv_h2);
-          st_ratio = qr > st_ratio ? qr : st_ratio;
-          accepted = true;
-          break;
-        }
-        if (rc == 2 || __popc(act) == 5) break;
-        int worst = 0;
-        unsigned long long wv = ~0ull;
+      if (!screen32(xs, es)) continue;
+      double x5[5], e5[5], f5[5];
 #pragma unroll
-        for (int s = 0; s < kSup; ++s) {
-          const unsigned long long key = ordered_bits(fs[s]);
-          if (((act >> s) & 1u) && key <= wv) {
-            wv = key;
-            worst = s;
-          }
+      for (int q = 0; q < 5; ++q) {
+        const int pos = (int)__fns(pm, 0, q + 1);
+        double a = xi[0], b = eta[0];
+#pragma unroll
+        for (int s = 1; s < kSup; ++s) {
+          a = pos == s ? xi[s] : a;
+          b = pos == s ? eta[s] : b;
         }
-        act &= ~(1u << worst);
+        x5[q] = a;
+        e5[q] = b;
       }
+      if (!square_stencil(x5, e5, f5)) continue;
+      int q = 0;
+#pragma unroll
+      for (int s = 0; s < kSup; ++s) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < 5; ++w) v = (((pm >> s) & 1u) && q == w) ? f5[w] : v;
+        fs[s] = v;
+        q += (pm >> s) & 1u;
+      }
+      act = pm;
+      accepted = done = true;
+    }
+    if (active) {
+      n_trials += trials;
       if (accepted) {
+        const double sum = write_stencil(i, js, fs, act, cols, f, fii, status);
+        const double qr = __dmul_rn(__dmul_rn(nu_dt, sum), inv_h2);
+        st_ratio = qr > st_ratio ? qr : st_ratio;
         ++n_ok;
+        n_square += trials == 1;
       } else {
         ++n_rej;
         if (!reject_list) {
@@ -508,6 +559,7 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
   n_ok = __reduce_add_sync(0xffffffffu, n_ok);
   n_rej = __reduce_add_sync(0xffffffffu, n_rej);
   n_square = __reduce_add_sync(0xffffffffu, n_square);
+  n_trials = __reduce_add_sync(0xffffffffu, (unsigned)n_trials);
   unsigned long long rb = (unsigned long long)__double_as_longlong(st_ratio);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -518,6 +570,7 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
     if (n_ok) atomicAdd(&ds->learned_ok, n_ok);
     if (n_rej) atomicAdd(&ds->learned_rejected, n_rej);
     if (n_square) atomicAdd(&ds->learned_square, n_square);
+    if (n_trials) atomicAdd(&ds->learned_screens, n_trials);
     if (rb) atomicMax(&ds->max_dt_ratio_bits, rb);
   }
 }
@@ -565,8 +618,7 @@ cudaError_t learned_project(const Consts& c, const double* x, const double* y, c
   int blocks = (m_bound + 127) / 128;
   if (blocks > 16 * sm_count()) blocks = 16 * sm_count();
   k_project<<<blocks, 128, 0, s>>>(c, x, y, list, list_count, m_bound, slots, f0, small, cols, f, fii, status,
-                                   reject_list,
-                                   reject_count, ds, dt_dev, nu);
+                                   reject_list, reject_count, ds, dt_dev, nu);
   note_launch();
   return cudaGetLastError();
 }

@@ -2,21 +2,25 @@
 // momcondmv, Sec. 4.1, small neighbourhoods Sec. 4.3).
 //
 // The LP  V f = b, f >= 0  has m = 5 rows (1,0) (0,1) (2,0) (1,1) (0,2) in
-// xi = r_ij / h and b = (0,0,2,0,2).  Phase I minimises the sum of m
-// artificials; they start the basis and, once they leave, never re-enter.
+// xi = r_ij / h for n = 1, and m = 9 with (3,0) (2,1) (1,2) (0,3) added for
+// n = 2 (Eqs. cond_two, cond_alpha); b = 2 on (2,0) and (0,2), 0 elsewhere.
+// Phase I minimises the sum of m artificials; they start the basis and, once
+// they leave, never re-enter.  Both kernels are templates on m and on the
+// stencil width W (8 for n = 1, 12 for n = 2: a basic solution has at most m
+// nonzero weights).
 // Rules (identical to the FP64 oracle, which solves the basis systems by LU
 // every iteration while this code updates a tableau):
 //   entering: lowest column with reduced cost < -1e-9 (Bland);
 //   leaving:  minimum ratio over pivot elements > 1e-9, basic values at or
 //             below 1e-11 taken as zero; ratios within 1e-12 max(1, min)
 //             tie, the tie goes to the basic variable of lowest index
-//             (artificials 0..4 before structurals 5..);
+//             (artificials 0..m-1 before structurals m..);
 //   at most 64 pivots; feasible iff the phase-I objective <= 1e-10 and
 //   max |V f - b| <= 1e-10; basic values <= 1e-11 are zeros.
 //
 // GB300 has about 1/60 of its FP32 rate in FP64, and every FP64 instruction
 // of a warp costs the same whether its lanes are busy or not.  The small
-// neighbourhood LP therefore runs one particle per thread with the 5 x 8
+// neighbourhood LP therefore runs one particle per thread with the m x 8
 // tableau in registers: every FP64 lane-operation does useful work, and
 // pivot row/column selections are register selects on the integer pipes.
 // The rare full-neighbourhood retry runs one particle per warp, one tableau
@@ -34,7 +38,6 @@ constexpr double kTolPhase1 = 1e-10;
 constexpr double kTolSnap = 1e-11;
 constexpr double kTolResid = 1e-10;
 constexpr int kPivotCap = 64;
-constexpr int kM = 5;
 
 // FP64 comparisons on the integer pipes: for non-NaN doubles the signed
 // 64-bit pattern orders the non-negative values, so these tests spend no
@@ -105,12 +108,22 @@ __device__ __forceinline__ void sort8(double* d2, int* j, double* a, double* b) 
   cswap(d2, j, a, b, 1, 2); cswap(d2, j, a, b, 3, 4); cswap(d2, j, a, b, 5, 6);
 }
 
+// Vandermonde column r^alpha of one neighbour, xi = r_ij / h (Eq. momcondmv),
+// each product rounded once: the cubic rows are (xi xi) xi, (xi xi) eta,
+// xi (eta eta), (eta eta) eta.
+template <int M>
 __device__ __forceinline__ void vcol(double xi, double eta, double* v) {
   v[0] = xi;
   v[1] = eta;
   v[2] = __dmul_rn(xi, xi);
   v[3] = __dmul_rn(xi, eta);
   v[4] = __dmul_rn(eta, eta);
+  if constexpr (M == 9) {
+    v[5] = __dmul_rn(v[2], xi);
+    v[6] = __dmul_rn(v[2], eta);
+    v[7] = __dmul_rn(xi, v[4]);
+    v[8] = __dmul_rn(v[4], eta);
+  }
 }
 
 __device__ __forceinline__ double b_of(int r) { return (r == 2 || r == 4) ? 2.0 : 0.0; }
@@ -120,25 +133,26 @@ __device__ __forceinline__ double b_of(int r) { return (r == 2 || r == 4) ? 2.0 
 // basis solves (partial pivoting on the first largest |pivot|, full row
 // swaps, multipliers A[r][k] * (1/A[k][k]), products and differences rounded
 // separately), so that equal bases give bit-identical weights.  Column k of
-// B is the unit vector e_v for an artificial v = basis[k] < 5, else the
+// B is the unit vector e_v for an artificial v = basis[k] < m, else the
 // Vandermonde column of (bxi[k], beta[k]).  Returns false if B is singular.
+template <int M>
 __device__ __forceinline__ bool basis_solve(const int* basis, const double* bxi, const double* beta, double* z) {
-  double A[kM][kM];
+  double A[M][M];
 #pragma unroll
-  for (int k = 0; k < kM; ++k) {
-    double v[kM];
-    vcol(bxi[k], beta[k], v);
+  for (int k = 0; k < M; ++k) {
+    double v[M];
+    vcol<M>(bxi[k], beta[k], v);
 #pragma unroll
-    for (int r = 0; r < kM; ++r) A[r][k] = basis[k] < kM ? (basis[k] == r ? 1.0 : 0.0) : v[r];
+    for (int r = 0; r < M; ++r) A[r][k] = basis[k] < M ? (basis[k] == r ? 1.0 : 0.0) : v[r];
   }
-  int piv[kM];
-  double rcp[kM];
+  int piv[M];
+  double rcp[M];
 #pragma unroll
-  for (int k = 0; k < kM; ++k) {
+  for (int k = 0; k < M; ++k) {
     int p = k;
     double best = A[k][k];
 #pragma unroll
-    for (int r = k + 1; r < kM; ++r)
+    for (int r = k + 1; r < M; ++r)
       if (abs_gt(A[r][k], best)) {
         best = A[r][k];
         p = r;
@@ -146,40 +160,40 @@ __device__ __forceinline__ bool basis_solve(const int* basis, const double* bxi,
     piv[k] = p;
     if ((dbits(best) & 0x7FFFFFFFFFFFFFFFLL) == 0) return false;
 #pragma unroll
-    for (int r = k + 1; r < kM; ++r)
+    for (int r = k + 1; r < M; ++r)
 #pragma unroll
-      for (int c = 0; c < kM; ++c) {
+      for (int c = 0; c < M; ++c) {
         const double a = A[k][c], b = A[r][c];
         A[k][c] = (p == r) ? b : a;
         A[r][c] = (p == r) ? a : b;
       }
     rcp[k] = __drcp_rn(A[k][k]);
 #pragma unroll
-    for (int r = k + 1; r < kM; ++r) {
+    for (int r = k + 1; r < M; ++r) {
       const double l = __dmul_rn(A[r][k], rcp[k]);
       A[r][k] = l;
 #pragma unroll
-      for (int c = k + 1; c < kM; ++c) A[r][c] = __dsub_rn(A[r][c], __dmul_rn(l, A[k][c]));
+      for (int c = k + 1; c < M; ++c) A[r][c] = __dsub_rn(A[r][c], __dmul_rn(l, A[k][c]));
     }
   }
 #pragma unroll
-  for (int r = 0; r < kM; ++r) z[r] = b_of(r);
+  for (int r = 0; r < M; ++r) z[r] = b_of(r);
 #pragma unroll
-  for (int k = 0; k < kM; ++k)
+  for (int k = 0; k < M; ++k)
 #pragma unroll
-    for (int r = k + 1; r < kM; ++r) {
+    for (int r = k + 1; r < M; ++r) {
       const double a = z[k], b = z[r];
       z[k] = (piv[k] == r) ? b : a;
       z[r] = (piv[k] == r) ? a : b;
     }
 #pragma unroll
-  for (int r = 1; r < kM; ++r)
+  for (int r = 1; r < M; ++r)
 #pragma unroll
     for (int c = 0; c < r; ++c) z[r] = __dsub_rn(z[r], __dmul_rn(A[r][c], z[c]));
 #pragma unroll
-  for (int r = kM - 1; r >= 0; --r) {
+  for (int r = M - 1; r >= 0; --r) {
 #pragma unroll
-    for (int c = r + 1; c < kM; ++c) z[r] = __dsub_rn(z[r], __dmul_rn(A[r][c], z[c]));
+    for (int c = r + 1; c < M; ++c) z[r] = __dsub_rn(z[r], __dmul_rn(A[r][c], z[c]));
     z[r] = __dmul_rn(z[r], rcp[r]);
   }
   return true;
@@ -213,6 +227,7 @@ __device__ __forceinline__ void flush_stats(DevStats* ds, int ok, int none, int 
   }
 }
 
+template <int M, int W>
 __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __restrict__ x,
                                                   const double* __restrict__ y, const int* __restrict__ list,
                                                   const int* __restrict__ list_count, const int* __restrict__ small,
@@ -257,25 +272,27 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         ceta[k] = __dmul_rn(ceta[k], c.inv_h);
       }
       // tableau: T[r][k] = (B^-1 V)_rk, rhs = B^-1 b, d = phase-I reduced costs
-      double T[kM][8], rhs[kM], d[8];
+      double T[M][8], rhs[M], d[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        double v[kM];
-        vcol(cxi[k], ceta[k], v);
+        double v[M];
+        vcol<M>(cxi[k], ceta[k], v);
         double s = 0.0;
 #pragma unroll
-        for (int r = 0; r < kM; ++r) {
+        for (int r = 0; r < M; ++r) {
           T[r][k] = v[r];
           s = __dadd_rn(s, v[r]);
         }
         d[k] = dneg(s);
       }
 #pragma unroll
-      for (int r = 0; r < kM; ++r) rhs[r] = b_of(r);
-      int basis[kM] = {0, 1, 2, 3, 4};
+      for (int r = 0; r < M; ++r) rhs[r] = b_of(r);
+      int basis[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) basis[r] = r;
       unsigned basic = 0;
       int it = 0, code = 0;
-      int n_art = kM;  // artificials in the basis
+      int n_art = M;  // artificials in the basis
       for (;;) {
         // with no artificial left the phase-I costs of the basis are zero, so
         // every reduced cost is exactly zero: phase I is over (the updated
@@ -290,9 +307,9 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
           code = 2;
           break;
         }
-        double a[kM];
+        double a[M];
 #pragma unroll
-        for (int r = 0; r < kM; ++r) {
+        for (int r = 0; r < M; ++r) {
           double v = T[r][0];
 #pragma unroll
           for (int k = 1; k < 8; ++k) v = (q == k) ? T[r][k] : v;
@@ -300,10 +317,10 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         }
         // ratio test: basic values <= kTolSnap are zeros; ratios by a
         // Newton reciprocal (relative error ~2^-45, far inside the tie window)
-        double ratio[kM], theta = 1e308;
-        bool elig[kM], any = false;
+        double ratio[M], theta = 1e308;
+        bool elig[M], any = false;
 #pragma unroll
-        for (int r = 0; r < kM; ++r) {
+        for (int r = 0; r < M; ++r) {
           elig[r] = gt_pos(a[r], kTolPivot);
           const double num = gt_pos(rhs[r], kTolSnap) ? rhs[r] : 0.0;
           ratio[r] = elig[r] ? __dmul_rn(num, rcp_newton<1>(a[r])) : 1e308;
@@ -319,14 +336,14 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         const double lim = __fma_rn(kTolTie, gt_pos(theta, 1.0) ? theta : 1.0, theta);
         int leave = -1, lbas = INT_MAX;
 #pragma unroll
-        for (int r = 0; r < kM; ++r)
+        for (int r = 0; r < M; ++r)
           if (elig[r] && !lt_nonneg(lim, ratio[r]) && basis[r] < lbas) {
             leave = r;
             lbas = basis[r];
           }
         double piv = a[0], prhs_raw = rhs[0];
 #pragma unroll
-        for (int r = 1; r < kM; ++r) {
+        for (int r = 1; r < M; ++r) {
           piv = (leave == r) ? a[r] : piv;
           prhs_raw = (leave == r) ? rhs[r] : prhs_raw;
         }
@@ -336,7 +353,7 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         for (int k = 0; k < 8; ++k) {
           double v = T[0][k];
 #pragma unroll
-          for (int r = 1; r < kM; ++r) v = (leave == r) ? T[r][k] : v;
+          for (int r = 1; r < M; ++r) v = (leave == r) ? T[r][k] : v;
           prow[k] = (k == q) ? 1.0 : __dmul_rn(v, rcp);
         }
         const double prhs = __dmul_rn(prhs_raw, rcp);
@@ -344,7 +361,7 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         // (zeroed, multiplier -1), and column q becomes exactly e_leave
         // because prow[q] = 1 and T[r][q] = a_r
 #pragma unroll
-        for (int r = 0; r < kM; ++r) {
+        for (int r = 0; r < M; ++r) {
           const bool lr = (leave == r);
           const double ar = lr ? -1.0 : a[r];
 #pragma unroll
@@ -356,11 +373,11 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         for (int k = 1; k < 8; ++k) dq = (q == k) ? d[k] : dq;
 #pragma unroll
         for (int k = 0; k < 8; ++k) d[k] = __fma_rn(-dq, prow[k], d[k]);
-        if (lbas >= kM) basic &= ~(1u << (lbas - kM));
+        if (lbas >= M) basic &= ~(1u << (lbas - M));
         else --n_art;
         basic |= 1u << q;
 #pragma unroll
-        for (int r = 0; r < kM; ++r) basis[r] = (leave == r) ? kM + q : basis[r];
+        for (int r = 0; r < M; ++r) basis[r] = (leave == r) ? M + q : basis[r];
         ++it;
       }
       // basic solution of the final basis (fresh LU solve, bit-identical to
@@ -370,45 +387,45 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
       for (int k = 0; k < 8; ++k) fv[k] = 0.0;
       double wsum = 0.0, rmax = 0.0;
       if (code == 0) {
-        double bxi[kM], beta[kM], xB[kM];
+        double bxi[M], beta[M], xB[M];
 #pragma unroll
-        for (int r = 0; r < kM; ++r) {
+        for (int r = 0; r < M; ++r) {
           double a = 0.0, e = 0.0;
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
-            a = (basis[r] == kM + k) ? cxi[k] : a;
-            e = (basis[r] == kM + k) ? ceta[k] : e;
+            a = (basis[r] == M + k) ? cxi[k] : a;
+            e = (basis[r] == M + k) ? ceta[k] : e;
           }
           bxi[r] = a;
           beta[r] = e;
         }
-        if (!basis_solve(basis, bxi, beta, xB)) code = 2;
-        double acc[kM];
+        if (!basis_solve<M>(basis, bxi, beta, xB)) code = 2;
+        double acc[M];
 #pragma unroll
-        for (int r = 0; r < kM; ++r) acc[r] = dneg(b_of(r));
+        for (int r = 0; r < M; ++r) acc[r] = dneg(b_of(r));
 #pragma unroll
-        for (int r = 0; r < kM; ++r) {
-          if (basis[r] < kM) {
+        for (int r = 0; r < M; ++r) {
+          if (basis[r] < M) {
             wsum = __dadd_rn(wsum, xB[r]);
           } else {
             const double v = gt_pos(xB[r], kTolSnap) ? xB[r] : 0.0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == kM + k) ? v : fv[k];
-            double col[kM];
-            vcol(bxi[r], beta[r], col);
+            for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == M + k) ? v : fv[k];
+            double col[M];
+            vcol<M>(bxi[r], beta[r], col);
 #pragma unroll
-            for (int q = 0; q < kM; ++q) acc[q] = __fma_rn(col[q], v, acc[q]);
+            for (int q = 0; q < M; ++q) acc[q] = __fma_rn(col[q], v, acc[q]);
           }
         }
 #pragma unroll
-        for (int r = 0; r < kM; ++r) rmax = abs_gt(acc[r], rmax) ? fabs(acc[r]) : rmax;
+        for (int r = 0; r < M; ++r) rmax = abs_gt(acc[r], rmax) ? fabs(acc[r]) : rmax;
       }
       const bool feasible = code == 0 && !gt_pos(wsum, kTolPhase1) && !gt_pos(rmax, kTolResid);
       st_maxpiv = it > st_maxpiv ? it : st_maxpiv;
       ++st_solved;
       st_pivots += it;
-      int* crow = cols + (size_t)i * VRM_STENCIL_W;
-      double* frow = f + (size_t)i * VRM_STENCIL_W;
+      int* crow = cols + (size_t)i * W;
+      double* frow = f + (size_t)i * W;
       if (feasible) {
         int slot = 0;
         double s = 0.0;
@@ -420,7 +437,7 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
             ++slot;
             s = __dadd_rn(s, fv[k]);
           }
-        for (int k = slot; k < VRM_STENCIL_W; ++k) {
+        for (int k = slot; k < W; ++k) {
           crow[k] = -1;
           frow[k] = 0.0;
         }
@@ -432,7 +449,7 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
       } else if (c.fallback) {
         fail_list[atomicAdd(&ds->n_fail, 1)] = i;
       } else {
-        for (int k = 0; k < VRM_STENCIL_W; ++k) {
+        for (int k = 0; k < W; ++k) {
           crow[k] = -1;
           frow[k] = 0.0;
         }
@@ -446,6 +463,7 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
 }
 
 // Full-neighbourhood retry: one warp per particle, lane l holds column l.
+template <int M, int W>
 __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restrict__ x,
                                                  const double* __restrict__ y, const int* __restrict__ fail_list,
                                                  const int* __restrict__ fail_count,
@@ -461,6 +479,8 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
   const int m = *fail_count;
   const double inv_h2 = 1.0 / (c.h * c.h);
   int st_ok = 0, st_none = 0, st_maxpiv = 0, st_solved = 0, st_pivots = 0;
+  unsigned st_cols = 0;
+  unsigned long long st_colpiv = 0;
   double st_ratio = 0.0;
   for (long t = warp; t < m; t += nwarps) {
     const int i = fail_list[t];
@@ -495,22 +515,24 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
       }
     }
     const double cxi = __dmul_rn(dx, c.inv_h), ceta = __dmul_rn(dy, c.inv_h);
-    double T[kM], v[kM];
-    vcol(cxi, ceta, v);
+    double T[M], v[M];
+    vcol<M>(cxi, ceta, v);
     double s = 0.0;
 #pragma unroll
-    for (int r = 0; r < kM; ++r) {
+    for (int r = 0; r < M; ++r) {
       T[r] = v[r];
       s = __dadd_rn(s, v[r]);
     }
     double d = 0.0 - s;
-    double rhs[kM], w = 4.0;
+    double rhs[M], w = 4.0;
 #pragma unroll
-    for (int r = 0; r < kM; ++r) rhs[r] = b_of(r);
-    int basis[kM] = {0, 1, 2, 3, 4};
+    for (int r = 0; r < M; ++r) rhs[r] = b_of(r);
+    int basis[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) basis[r] = r;
     bool isb = false;
     int it = 0, code = 0;
-    int n_art = kM;
+    int n_art = M;
     for (;;) {
       if (n_art == 0) break;  // phase I over: every reduced cost is zero
       const unsigned cand = __ballot_sync(0xffffffffu, lane < K && !isb && d < -kTolPrice);
@@ -520,13 +542,13 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
         break;
       }
       const int q = __ffs(cand) - 1;
-      double a[kM];
+      double a[M];
 #pragma unroll
-      for (int r = 0; r < kM; ++r) a[r] = __shfl_sync(0xffffffffu, T[r], q);
-      double ratio[kM], theta = 1e308;
+      for (int r = 0; r < M; ++r) a[r] = __shfl_sync(0xffffffffu, T[r], q);
+      double ratio[M], theta = 1e308;
       bool any = false;
 #pragma unroll
-      for (int r = 0; r < kM; ++r) {
+      for (int r = 0; r < M; ++r) {
         ratio[r] = a[r] > kTolPivot ? __ddiv_rn(rhs[r] > kTolSnap ? rhs[r] : 0.0, a[r]) : 1e308;
         if (a[r] > kTolPivot) {
           any = true;
@@ -540,14 +562,14 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
       const double lim = theta + kTolTie * (theta > 1.0 ? theta : 1.0);
       int leave = -1, lbas = INT_MAX;
 #pragma unroll
-      for (int r = 0; r < kM; ++r)
+      for (int r = 0; r < M; ++r)
         if (a[r] > kTolPivot && ratio[r] <= lim && basis[r] < lbas) {
           leave = r;
           lbas = basis[r];
         }
       double piv = a[0], prhs_raw = rhs[0], prow_raw = T[0];
 #pragma unroll
-      for (int r = 1; r < kM; ++r) {
+      for (int r = 1; r < M; ++r) {
         piv = (leave == r) ? a[r] : piv;
         prhs_raw = (leave == r) ? rhs[r] : prhs_raw;
         prow_raw = (leave == r) ? T[r] : prow_raw;
@@ -556,7 +578,7 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
       const double prow = (lane == q) ? 1.0 : __dmul_rn(prow_raw, rcp);
       const double prhs = __dmul_rn(prhs_raw, rcp);
 #pragma unroll
-      for (int r = 0; r < kM; ++r) {
+      for (int r = 0; r < M; ++r) {
         const bool lr = (leave == r);
         const double ar = lr ? 0.0 : a[r];
         const double u = __fma_rn(-ar, prow, T[r]);
@@ -567,34 +589,34 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
       const double dq = __shfl_sync(0xffffffffu, d, q);
       d = (lane == q) ? 0.0 : __fma_rn(-dq, prow, d);
       w = __fma_rn(-dq, prhs, w);
-      if (lbas >= kM && lane == lbas - kM) isb = false;
-      if (lbas < kM) --n_art;
+      if (lbas >= M && lane == lbas - M) isb = false;
+      if (lbas < M) --n_art;
       if (lane == q) isb = true;
 #pragma unroll
-      for (int r = 0; r < kM; ++r) basis[r] = (leave == r) ? kM + q : basis[r];
+      for (int r = 0; r < M; ++r) basis[r] = (leave == r) ? M + q : basis[r];
       ++it;
     }
     // basic solution of the final basis by the oracle's LU sequence; every
     // lane solves the same system from the broadcast basic columns
     double fv = 0.0, wsum = 0.0;
     if (code == 0) {
-      double bxi[kM], beta[kM], xB[kM];
+      double bxi[M], beta[M], xB[M];
 #pragma unroll
-      for (int r = 0; r < kM; ++r) {
-        const int src = basis[r] >= kM ? basis[r] - kM : 0;
+      for (int r = 0; r < M; ++r) {
+        const int src = basis[r] >= M ? basis[r] - M : 0;
         bxi[r] = __shfl_sync(0xffffffffu, cxi, src);
         beta[r] = __shfl_sync(0xffffffffu, ceta, src);
       }
-      if (!basis_solve(basis, bxi, beta, xB)) code = 2;
+      if (!basis_solve<M>(basis, bxi, beta, xB)) code = 2;
 #pragma unroll
-      for (int r = 0; r < kM; ++r) {
-        if (basis[r] < kM) wsum = __dadd_rn(wsum, xB[r]);
-        else if (basis[r] == kM + lane) fv = xB[r] > kTolSnap ? xB[r] : 0.0;
+      for (int r = 0; r < M; ++r) {
+        if (basis[r] < M) wsum = __dadd_rn(wsum, xB[r]);
+        else if (basis[r] == M + lane) fv = xB[r] > kTolSnap ? xB[r] : 0.0;
       }
     }
     double rmax = 0.0;
 #pragma unroll
-    for (int r = 0; r < kM; ++r) {
+    for (int r = 0; r < M; ++r) {
       double p = __dmul_rn(v[r], fv);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) p = __dadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
@@ -602,17 +624,17 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
       rmax = e > rmax ? e : rmax;
     }
     const bool feasible = code == 0 && wsum <= kTolPhase1 && rmax <= kTolResid;
-    int* crow = cols + (size_t)i * VRM_STENCIL_W;
-    double* frow = f + (size_t)i * VRM_STENCIL_W;
+    int* crow = cols + (size_t)i * W;
+    double* frow = f + (size_t)i * W;
     const unsigned nz = __ballot_sync(0xffffffffu, feasible && fv != 0.0);
     if (feasible) {
       const int slot = __popc(nz & ((1u << lane) - 1u));
-      if (fv != 0.0 && slot < VRM_STENCIL_W) {
+      if (fv != 0.0 && slot < W) {
         crow[slot] = j;
         frow[slot] = fv;
       }
       const int used = __popc(nz);
-      if (lane >= used && lane < VRM_STENCIL_W) {
+      if (lane >= used && lane < W) {
         crow[lane] = -1;
         frow[lane] = 0.0;
       }
@@ -632,7 +654,7 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
         st_ratio = q > st_ratio ? q : st_ratio;
       }
     } else {
-      if (lane < VRM_STENCIL_W) {
+      if (lane < W) {
         crow[lane] = -1;
         frow[lane] = 0.0;
       }
@@ -646,18 +668,27 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
     if (lane == 0) {
       ++st_solved;
       st_pivots += it;
+      st_cols += K;
+      st_colpiv += (unsigned long long)K * it;
     }
   }
   flush_stats(ds, st_ok, st_none, st_maxpiv, st_ratio, true, st_solved, st_pivots);
+  st_cols = __reduce_add_sync(0xffffffffu, (unsigned)st_cols);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) st_colpiv += __shfl_xor_sync(0xffffffffu, st_colpiv, o);
+  if (lane == 0 && st_cols) {
+    atomicAdd(&ds->lp_full_columns, (unsigned long long)st_cols);
+    atomicAdd(&ds->lp_full_column_pivots, st_colpiv);
+  }
 }
 
-__global__ void k_lp_clear(int n, const uint8_t* __restrict__ diffused, int* __restrict__ cols,
+__global__ void k_lp_clear(int n, int w, const uint8_t* __restrict__ diffused, int* __restrict__ cols,
                            double* __restrict__ f, double* __restrict__ fii, uint8_t* __restrict__ status) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     if (diffused[i]) continue;
-    for (int k = 0; k < VRM_STENCIL_W; ++k) {
-      cols[i * VRM_STENCIL_W + k] = -1;
-      f[i * VRM_STENCIL_W + k] = 0.0;
+    for (int k = 0; k < w; ++k) {
+      cols[i * w + k] = -1;
+      f[i * w + k] = 0.0;
     }
     fii[i] = 0.0;
     status[i] = VRM_LP_NOT_DIFFUSED;
@@ -671,8 +702,13 @@ cudaError_t lp_small(const Consts& c, const double* x, const double* y, const in
   const int tb = c.lp_block;
   int blocks = (int)(((long)cap + tb - 1) / tb);
   if (blocks > c.lp_blocks_per_sm * sm_count()) blocks = c.lp_blocks_per_sm * sm_count();
-  k_lp_small<<<blocks, tb, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list, ds, nu_dt, dt_dev,
-                                    nu); note_launch();
+  if (c.order == 2)
+    k_lp_small<9, 12><<<blocks, tb, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list, ds,
+                                            nu_dt, dt_dev, nu);
+  else
+    k_lp_small<5, 8><<<blocks, tb, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list, ds,
+                                           nu_dt, dt_dev, nu);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -683,17 +719,22 @@ cudaError_t lp_full(const Consts& c, const double* x, const double* y, const int
   long warps = cap;
   long blocks = (warps * 32 + 127) / 128;
   if (blocks > 4 * sm_count()) blocks = 4 * sm_count();
-  k_lp_full<<<(int)blocks, 128, 0, s>>>(c, x, y, fail_list, fail_count, nbr_count, nbr_idx, cols, f, fii, status, ds,
-                                        nu_dt, dt_dev, nu); note_launch();
+  if (c.order == 2)
+    k_lp_full<9, 12><<<(int)blocks, 128, 0, s>>>(c, x, y, fail_list, fail_count, nbr_count, nbr_idx, cols, f, fii,
+                                                 status, ds, nu_dt, dt_dev, nu);
+  else
+    k_lp_full<5, 8><<<(int)blocks, 128, 0, s>>>(c, x, y, fail_list, fail_count, nbr_count, nbr_idx, cols, f, fii,
+                                                status, ds, nu_dt, dt_dev, nu);
+  note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t lp_clear(int n, const uint8_t* diffused, int* cols, double* f, double* fii, uint8_t* status,
+cudaError_t lp_clear(int n, int w, const uint8_t* diffused, int* cols, double* f, double* fii, uint8_t* status,
                      cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   int blocks = (n + kBlock - 1) / kBlock;
   if (blocks > 8 * sm_count()) blocks = 8 * sm_count();
-  k_lp_clear<<<blocks, kBlock, 0, s>>>(n, diffused, cols, f, fii, status); note_launch();
+  k_lp_clear<<<blocks, kBlock, 0, s>>>(n, w, diffused, cols, f, fii, status); note_launch();
   return cudaGetLastError();
 }
 

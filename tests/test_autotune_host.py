@@ -62,6 +62,7 @@ def test_buckets_and_keys():
     assert autotune.bucket(1) == 0 and autotune.bucket(1024) == 10 and autotune.bucket(1500) == 11
     assert autotune.bucket(0) == 0
     assert autotune.cache_key("GB300|sm103", 32, 5e5) == "GB300|sm103|k32|n2^19"
+    assert autotune.cache_key("GB300|sm103", 32, 5e5, order=2) == "GB300|sm103|k32|o2|n2^19"
 
 
 def test_cache_round_trip(tmp_path, monkeypatch):

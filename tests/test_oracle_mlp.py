@@ -175,60 +175,120 @@ def test_projection_single_particle_example():
     assert np.max(np.abs(f - 2.0 / 9.0)) < 1e-14
 
 
-def test_learned_stencil_accepts_valid_and_rejects_negative():
-    # unit lattice neighbours, the 5-point stencil proposal (f~ = 1 on E N W S)
-    # plus a little weight on the diagonals: the top five slots (E N W S and
-    # the first diagonal) solve square to the 5-point stencil
-    h = 1.0
+def lattice8():
     off = [(1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1)]
     x = np.array([0.0] + [a for a, _ in off])
     y = np.array([0.0] + [b for _, b in off])
     slots = np.full(32, -1)
     slots[:8] = np.arange(1, 9)
+    return x, y, slots
+
+
+def test_learned_stencil_accepts_valid_and_rejects_infeasible():
+    # unit lattice neighbours, the 5-point stencil proposal (f~ = 1 on E N W S)
+    # plus a little weight on the diagonals: the top five slots (E N W S and
+    # the first diagonal) solve square to the 5-point stencil, whose zero
+    # weight on the diagonal is not kept
+    h = 1.0
+    x, y, slots = lattice8()
     f0 = np.zeros(32, dtype=np.float32)
     f0[:8] = [1, 0.01, 1, 0.01, 1, 0.01, 1, 0.01]
-    ok, js, f, fii = mlp.learned_stencil(x, y, h, 0, slots, f0)
-    assert ok and js == [1, 2, 3, 5, 7] and np.all(f >= 0) and abs(fii + np.sum(f)) < 1e-15
-    V = mlp.vandermonde(x[js], y[js])
-    assert np.max(np.abs(V @ f - mlp.B_RHS)) <= 1e-12
+    ok, js, f, fii, tried = mlp.learned_stencil(x, y, h, 0, slots, f0, trials=True)
+    assert ok and tried == 1 and js == [1, 3, 5, 7] and np.all(f == 1.0) and fii == -4.0
     # the diagonals and W: the square system gives the rotated 5-point stencil
     f0[:8] = [0.0, 1.0, 0.0, 1.0, 3.0, 1.0, 0.0, 1.0]
     ok, js, f, _ = mlp.learned_stencil(x, y, h, 0, slots, f0)
-    assert ok and js == [2, 4, 5, 6, 8] and np.allclose(f, [0.5, 0.5, 0.0, 0.5, 0.5], rtol=0, atol=1e-15)
-    # weight only on the upper half plane: rows (0,1) and (0,2) coincide there, no stencil
-    f0[:8] = [1, 1, 1, 1, 1, 0, 0, 0]
-    ok, _, _, _ = mlp.learned_stencil(x, y, h, 0, slots, f0)
-    assert not ok
-    # fewer than 5 positive proposals: no stencil
-    f0[:8] = [1, 0, 1, 0, 1, 0, 1, 0]
-    ok, _, _, _ = mlp.learned_stencil(x, y, h, 0, slots, f0)
-    assert not ok
+    assert ok and js == [2, 4, 6, 8] and np.allclose(f, 0.5, rtol=0, atol=1e-15)
+    # neighbours in the upper half plane only: sum f eta = 0 forces f = 0 on
+    # them, no support passes (Sec. 4.2's motive for insertion)
+    up = [k for k in range(1, 9) if y[k] > 0] + [k for k in range(1, 9) if y[k] == 0]
+    sl = np.full(32, -1)
+    sl[:len(up)] = up
+    ok, _, _, _, tried = mlp.learned_stencil(x, y, h, 0, sl, np.ones(32, np.float32), trials=True)
+    assert not ok and tried == 1  # five candidates: one support
+    # fewer than five candidates: nothing to solve
+    sl = np.full(32, -1)
+    sl[:4] = [1, 3, 5, 7]
+    ok, _, _, _, tried = mlp.learned_stencil(x, y, h, 0, sl, np.ones(32, np.float32), trials=True)
+    assert not ok and tried == 0
 
 
-def test_support_refinement_reaches_a_vertex():
-    # unit lattice neighbours; the proposal puts weight on all 8 with the
-    # diagonals too heavy: the first correction turns some weight negative,
-    # dropping slots down to five neighbours gives a valid vertex stencil
-    h = 1.0
-    off = [(1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1)]
-    x = np.array([0.0] + [a for a, _ in off])
-    y = np.array([0.0] + [b for _, b in off])
+def test_first_passing_support_in_subset_order():
+    # jittered rings of 8 candidates, weights well away from zero on every
+    # support (so the binary32 screen and the FP64 test agree): the chosen
+    # support is the first one, in subset_order, whose exact solution is
+    # non-negative (brute force with numpy's solver)
+    rng = np.random.default_rng(31)
+    seen = 0
+    for case in range(200):
+        th = np.arange(8) * np.pi / 4 + rng.uniform(0, np.pi / 4, 8)
+        rad = rng.uniform(0.6, 1.9, 8)
+        x = np.concatenate([[0.0], rad * np.cos(th)])
+        y = np.concatenate([[0.0], rad * np.sin(th)])
+        slots = np.full(32, -1)
+        slots[:8] = np.arange(1, 9)
+        f0 = np.zeros(32, dtype=np.float32)
+        f0[:8] = rng.uniform(0, 1, 8)
+        ranked = mlp.candidates(f0, slots)
+        expect, margin_ok = None, True
+        for sub in mlp.subset_order(8):
+            S = sorted(ranked[r] for r in sub)
+            V = mlp.vandermonde(x[slots[S]], y[slots[S]])
+            if abs(np.linalg.det(V)) < 1e-9:
+                continue
+            f = np.linalg.solve(V, mlp.B_RHS)
+            if np.min(np.abs(f)) < 1e-5:
+                margin_ok = False
+                break
+            if np.all(f > 0):
+                expect = [int(slots[k]) for k in S]
+                break
+        if not margin_ok:
+            continue
+        seen += 1
+        ok, js, f, _ = mlp.learned_stencil(x, y, 1.0, 0, slots, f0)
+        assert ok == (expect is not None) and (not ok or js == expect), case
+    assert seen > 150
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_support_search_finds_a_stencil_iff_the_lp_does(orc, seed):
+    # every feasible LP on the eight columns has a basic feasible solution
+    # on five of them, so searching all supports is complete: the learned
+    # stencil exists exactly when the oracle's phase-I simplex finds one
+    rng = np.random.default_rng(400 + seed)
+    th = np.arange(8) * np.pi / 4 + rng.uniform(0, np.pi / 4, 8)
+    if seed % 3 == 0:
+        th = rng.uniform(0, 1.6 * np.pi, 8)  # some with an open sector
+    rad = rng.uniform(0.5, 2.0, 8)
+    x = np.concatenate([[0.0], rad * np.cos(th)])
+    y = np.concatenate([[0.0], rad * np.sin(th)])
     slots = np.full(32, -1)
     slots[:8] = np.arange(1, 9)
     f0 = np.zeros(32, dtype=np.float32)
-    f0[:8] = [0.9, 0.05, 1.0, 0.02, 1.1, 0.03, 0.95, 0.04]
-    S0 = mlp.support(f0, slots)
-    xi = x[slots[S0]]
-    eta = y[slots[S0]]
-    f_first, _ = mlp.project(xi, eta, f0[S0].astype(np.float64))
-    ok, js, f, fii = mlp.learned_stencil(x, y, h, 0, slots, f0)
-    assert ok and 5 <= len(js) <= 8 and np.all(f >= 0)
-    V = mlp.vandermonde(x[js], y[js])
-    assert np.max(np.abs(V @ f - mlp.B_RHS)) <= 1e-12
-    # with five neighbours the stencil is the unique solution on them
-    if len(js) == 5:
-        assert np.allclose(f, np.linalg.solve(V, mlp.B_RHS), rtol=0, atol=1e-13)
-    # nearly dependent rows (four neighbours on one line plus one) reject
+    f0[:8] = rng.uniform(0, 1, 8)
+    ok, js, f, _ = mlp.learned_stencil(x, y, 1.0, 0, slots, f0)
+    st, _, _, _ = orc.phase1(orc.vandermonde(1, x[1:], y[1:]), mlp.B_RHS)
+    assert ok == (st == 0)
+    if ok:
+        V = mlp.vandermonde(x[js], y[js])
+        assert np.all(f > 0) and np.max(np.abs(V @ f - mlp.B_RHS)) <= 1e-12
+
+
+def test_subset_order():
+    from math import comb
+    for nc in range(5, 9):
+        order = mlp.subset_order(nc)
+        assert len(order) == len(set(order)) == comb(nc, 5)
+        assert order[0] == (0, 1, 2, 3, 4)
+        sums = [sum(r) for r in order]
+        assert sums == sorted(sums)
+    assert mlp.subset_order(4) == []
+
+
+def test_nearly_dependent_rows_reject():
+    # four neighbours on one line plus one: rows (1,0) and (2,0) ... leave the
+    # five columns dependent in (0,1)/(1,1)/(0,2); no support solves
     xl = np.array([0.0, 1.0, 2.0, -1.0, -2.0, 0.0])
     yl = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 1.0])
     sl = np.full(32, -1)
@@ -253,6 +313,27 @@ def test_square_solve_is_gaussian_elimination():
     assert mlp.square_solve(V, np.ones(5)) is None
 
 
+def test_square_solve32_is_binary32_elimination():
+    # well-conditioned jittered supports: within binary32 accuracy of the
+    # exact solution; the 5-point supports are exact in binary32
+    rng = np.random.default_rng(8)
+    for _ in range(200):
+        th = np.arange(5) * 2 * np.pi / 5 + rng.uniform(-0.3, 0.3, 5)
+        rad = rng.uniform(0.7, 1.8, 5)
+        xi, eta = rad * np.cos(th), rad * np.sin(th)
+        V = mlp.vandermonde(xi, eta)
+        if np.linalg.cond(V) > 1e3:
+            continue
+        f = np.linalg.solve(V, mlp.B_RHS)
+        f32 = mlp.square_solve32(xi, eta)
+        assert f32.dtype == np.float32
+        assert np.max(np.abs(f32 - f)) <= 1e-4 * np.max(np.abs(f))
+    f32 = mlp.square_solve32(np.array([1.0, 1.0, 0.0, -1.0, 0.0]), np.array([0.0, 1.0, 1.0, 0.0, -1.0]))
+    assert np.array_equal(f32, np.array([1, 0, 1, 1, 1], np.float32))
+    # a repeated column is singular
+    assert mlp.square_solve32(np.array([1.0, 1.0, 0.0, -1.0, 0.0]), np.array([0.0, 0.0, 1.0, 0.0, -1.0])) is None
+
+
 def test_top_five_basis_gives_the_vertex():
     # E, N, W, S and NE on the unit lattice: the unique stencil on these five
     # neighbours is the 5-point Laplacian (1 on E, N, W, S; 0 on NE)
@@ -264,8 +345,8 @@ def test_top_five_basis_gives_the_vertex():
     f0 = np.zeros(32, dtype=np.float32)
     f0[:8] = [0.8, 0.3, 0.9, 0.01, 1.1, 0.02, 0.7, 0.03]
     ok, js, f, fii = mlp.learned_stencil(x, y, 1.0, 0, slots, f0)
-    assert ok and js == [1, 2, 3, 5, 7]
-    assert np.allclose(f, [1.0, 0.0, 1.0, 1.0, 1.0], rtol=0, atol=1e-14) and fii == -4.0
+    assert ok and js == [1, 3, 5, 7]  # the zero weight on NE is not kept
+    assert np.all(f == 1.0) and fii == -4.0
 
 
 def test_candidates_are_the_small_neighbourhood():
