@@ -35,7 +35,8 @@ and signs; everything else goes to the LP.  The pieces:
   (square_solve32: every operation rounded to float32, the same sequence as
   the GPU's), and only a support whose binary32 weights all exceed -1e-6 is
   solved in FP64 (square_solve) and tested; FP64 weights in [-1e-13, 0) are
-  zeros of the vertex.  No passing support: the particle goes to the LP.
+  zeros of the vertex; at most MAX_SOLVES = 4 supports reach the FP64
+  solve.  No passing support: the particle goes to the LP.
 * support(), project(), gram_ok(): the least-change correction
       f_S = f0_S + V_S^T (V_S V_S^T)^{-1} (b - V_S f0_S)
   of a proposal on a support of up to eight slots (the smallest change that
@@ -280,6 +281,7 @@ def square_solve(V, b, rel=1e-12):
 SCREEN_TOL = np.float32(1e-6)  # binary32 screen: weights above -SCREEN_TOL go to the FP64 solve
 SCREEN_PIVOT = np.float32(1e-6)  # binary32 screen: relative pivot threshold
 SNAP = 1e-13  # FP64 weights in [-SNAP, 0) are zeros of the vertex
+MAX_SOLVES = 4  # FP64 solves per particle at most (supports that passed the screen)
 
 
 def subset_order(nc):
@@ -291,13 +293,14 @@ def subset_order(nc):
 
 def square_solve32(xi, eta):
     """Binary32 Gaussian elimination of V_S f = b on five columns, every
-    product, quotient and difference rounded to float32 in this order:
+    product, reciprocal and difference rounded to float32 in this order:
     V entries xi, eta, xi*xi, xi*eta, eta*eta from float32(xi), float32(eta);
     pivot = first largest |entry| of the column at or below the diagonal,
-    None if it is not above SCREEN_PIVOT * (largest |V entry|); rows below
-    get A[q][c] - (A[q][k] / A[k][k]) * A[k][c] for c > k and the right-hand
-    side alike; back substitution f_k = (r_k - sum_q A[k][q] f_q) / A[k][k]
-    with the sum taken q = k+1, ..., 4."""
+    None if it is not above SCREEN_PIVOT * (largest |V entry|); rcp_k =
+    1 / A[k][k] (one rounding); rows below get A[q][c] - (A[q][k] rcp_k) *
+    A[k][c] for c > k and the right-hand side alike; back substitution
+    f_k = (r_k - sum_q A[k][q] f_q) * rcp_k with the sum taken
+    q = k+1, ..., 4."""
     f32 = np.float32
     A = []
     for r in range(5):
@@ -314,6 +317,7 @@ def square_solve32(xi, eta):
         for c in range(5):
             vmax = max(vmax, abs(A[r][c]))
     tiny = f32(SCREEN_PIVOT * vmax)
+    rcp = [f32(0.0)] * 5
     for k in range(5):
         p = k
         for q in range(k + 1, 5):
@@ -322,8 +326,9 @@ def square_solve32(xi, eta):
         if not abs(A[p][k]) > tiny:
             return None
         A[k], A[p] = A[p], A[k]
+        rcp[k] = f32(f32(1.0) / A[k][k])
         for q in range(k + 1, 5):
-            m = f32(A[q][k] / A[k][k])
+            m = f32(A[q][k] * rcp[k])
             for c in range(k + 1, 6):
                 A[q][c] = f32(A[q][c] - f32(m * A[k][c]))
     f = [f32(0.0)] * 5
@@ -331,7 +336,7 @@ def square_solve32(xi, eta):
         acc = A[k][5]
         for q in range(k + 1, 5):
             acc = f32(acc - f32(A[k][q] * f[q]))
-        f[k] = f32(acc / A[k][k])
+        f[k] = f32(acc * rcp[k])
     return np.array(f, dtype=np.float32)
 
 
@@ -354,7 +359,7 @@ def learned_stencil(x, y, h, i, slots, f0, small=None, trials=False):
     screened."""
     ranked = candidates(f0, slots, small)
     inv_h = 1.0 / h
-    tried = 0
+    tried = solves = 0
     for sub in subset_order(len(ranked)):
         tried += 1
         S = sorted(ranked[r] for r in sub)
@@ -364,15 +369,17 @@ def learned_stencil(x, y, h, i, slots, f0, small=None, trials=False):
         f32 = square_solve32(xi, eta)
         if f32 is None or not np.all(f32 >= -SCREEN_TOL):
             continue
+        solves += 1
         V = vandermonde(xi, eta)
         f = square_solve(V, B_RHS)
-        if f is None:
-            continue
-        f = np.where((f < 0.0) & (f >= -SNAP), 0.0, f)
-        if np.all(f >= 0.0) and float(np.max(np.abs(V @ f - B_RHS))) <= ACCEPT_RESID:
-            nz = [q for q in range(5) if f[q] != 0.0]
-            fo = f[nz]
-            out = (True, [js[q] for q in nz], fo, -float(np.sum(fo)))
-            return out + (tried,) if trials else out
+        if f is not None:
+            f = np.where((f < 0.0) & (f >= -SNAP), 0.0, f)
+            if np.all(f >= 0.0) and float(np.max(np.abs(V @ f - B_RHS))) <= ACCEPT_RESID:
+                nz = [q for q in range(5) if f[q] != 0.0]
+                fo = f[nz]
+                out = (True, [js[q] for q in nz], fo, -float(np.sum(fo)))
+                return out + (tried,) if trials else out
+        if solves == MAX_SOLVES:
+            break
     out = (False, [], None, 0.0)
     return out + (tried,) if trials else out

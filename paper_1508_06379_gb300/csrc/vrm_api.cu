@@ -29,6 +29,7 @@ struct Learned {
   float* Y = nullptr;
   int* rlist = nullptr;
   float2* xyf = nullptr;  // fp32 positions
+  ProjScratch proj;       // correction rounds
 };
 
 struct vrm::Scratch {
@@ -163,7 +164,21 @@ void free_learned(Learned& L) {
   if (L.Y) cudaFree(L.Y);
   if (L.rlist) cudaFree(L.rlist);
   if (L.xyf) cudaFree(L.xyf);
+  proj_free(&L.proj);
   L = Learned{};
+}
+
+// Correction-round scratch for m listed particles (the network's stages
+// use ensure_learned, which sizes it too).
+cudaError_t ensure_proj(vrm_ctx* ctx, int m, cudaStream_t st) {
+  ProjScratch& P = ctx->L.proj;
+  if (m <= P.cap && P.sel) return cudaSuccess;
+  cudaStreamSynchronize(st);
+  drop_graph(ctx);
+  ++ctx->scratch_gen;
+  const cudaError_t e = proj_alloc(&P, m < 128 ? 128 : m);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e;
 }
 
 // Buffers of the learned proposal for `cap` particles (only with a network).
@@ -180,6 +195,7 @@ cudaError_t ensure_learned(vrm_ctx* ctx, int cap, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMalloc(&L.Y, sizeof(float) * (size_t)L.acts.rows_pad * 32);
   if (e == cudaSuccess) e = cudaMalloc(&L.rlist, sizeof(int) * (size_t)n);
   if (e == cudaSuccess) e = cudaMalloc(&L.xyf, sizeof(float2) * (size_t)n);
+  if (e == cudaSuccess) e = proj_alloc(&L.proj, n);
   if (e != cudaSuccess) {
     free_learned(L);
     cudaGetLastError();
@@ -204,7 +220,7 @@ cudaError_t enqueue_learned(vrm_ctx* ctx, const double* x, const double* y, cons
   if ((e = mlp_forward(ctx->mlp, L.acts.mX, cap, list_count, L.Y, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(s.counters + 2, 0, sizeof(int), st)) != cudaSuccess) return e;
   return learned_project(c, x, y, list, list_count, cap, L.slots, L.Y, small, cols, f, fii, status, L.rlist,
-                         s.counters + 2, s.ds, dt_dev, ctx->p.nu, st);
+                         s.counters + 2, s.ds, dt_dev, ctx->p.nu, &L.proj, st);
 }
 
 void free_rk(vrm_ctx* ctx) {
@@ -1082,9 +1098,10 @@ vrm_status vrm_learned_project(vrm_ctx* ctx, const double* x, const double* y, c
   if (ctx->p.order != 1) return VRM_ERR_UNSUPPORTED;
   Scratch& s = ctx->s;
   VRM_CUDA(ensure_scratch(ctx, m, stream));
+  VRM_CUDA(ensure_proj(ctx, m, stream));
   VRM_CUDA(cudaMemsetAsync(s.ds, 0, sizeof(DevStats), stream));
   VRM_CUDA(learned_project(ctx->c, x, y, list, nullptr, m, slots, f0, small, cols, f, fii, status, nullptr, nullptr,
-                           s.ds, nullptr, ctx->p.nu, stream));
+                           s.ds, nullptr, ctx->p.nu, &ctx->L.proj, stream));
   VRM_CUDA(read_back(ctx, stream));
   if (n_accepted) *n_accepted = s.h_ds->learned_ok;
   return VRM_OK;

@@ -22,11 +22,12 @@
 // support is first screened in binary32 (GB300 runs fp32 at about 60 times
 // its FP64 rate): Gaussian elimination with every operation rounded to
 // float32, passed on when all weights are >= -1e-6; only then the FP64
-// solve (FP64 weights in [-1e-13, 0) are zeros of the vertex and dropped).
-// A particle with no passing support goes to the LP.
+// solve (FP64 weights in [-1e-13, 0) are zeros of the vertex and dropped),
+// at most four FP64 solves per particle.  A particle with no passing support
+// goes to the LP.
 #include <cuda_bf16.h>
 
-#include "vrm_internal.cuh"
+#include "vrm_mlp.cuh"
 
 namespace vrm {
 
@@ -40,6 +41,7 @@ constexpr double kSnap = 1e-13;        // FP64 weights in [-kSnap, 0) are zeros
 constexpr float kScreenTol = 1e-6f;    // binary32 screen: weights >= -kScreenTol pass
 constexpr float kScreenPivot = 1e-6f;  // binary32 screen: relative pivot threshold
 constexpr int kSubsets = 56;           // 5-subsets of 8 candidate ranks
+constexpr int kMaxSolves = kProjRounds;  // FP64 solves per particle at most
 
 }  // namespace
 
@@ -155,22 +157,21 @@ __device__ __forceinline__ double rcp64(double a) {
 // (weights in [-kSnap, 0) set to zero) is not a non-negative solution with
 // residual <= kAcceptResid.
 __device__ __forceinline__ bool square_stencil(const double* xi, const double* eta, double* fo) {
-  double A[5][6], V[5][5];
+  double A[5][6];
 #pragma unroll
   for (int s = 0; s < 5; ++s) {
-    V[0][s] = xi[s];
-    V[1][s] = eta[s];
-    V[2][s] = xi[s] * xi[s];
-    V[3][s] = xi[s] * eta[s];
-    V[4][s] = eta[s] * eta[s];
+    A[0][s] = xi[s];
+    A[1][s] = eta[s];
+    A[2][s] = xi[s] * xi[s];
+    A[3][s] = xi[s] * eta[s];
+    A[4][s] = eta[s] * eta[s];
   }
   unsigned long long vmax = 0;
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
 #pragma unroll
     for (int s = 0; s < 5; ++s) {
-      A[r][s] = V[r][s];
-      const unsigned long long ab = abs_bits(V[r][s]);
+      const unsigned long long ab = abs_bits(A[r][s]);
       vmax = ab > vmax ? ab : vmax;
     }
     A[r][5] = (r == 2 || r == 4) ? 2.0 : 0.0;
@@ -205,7 +206,7 @@ __device__ __forceinline__ bool square_stencil(const double* xi, const double* e
     for (int r = k + 1; r < 5; ++r) {
       const double mlt = A[r][k] * inv[k];
 #pragma unroll
-      for (int q = k; q < 6; ++q) A[r][q] = fma(-mlt, A[k][q], A[r][q]);
+      for (int q = k + 1; q < 6; ++q) A[r][q] = fma(-mlt, A[k][q], A[r][q]);
     }
   }
   double f[5];
@@ -225,11 +226,16 @@ __device__ __forceinline__ bool square_stencil(const double* xi, const double* e
     ok = ok && nonneg_bits(f[s]);
   }
   const unsigned long long lim = abs_bits(kAcceptResid);
+  // residual with the Vandermonde entries formed again (fewer live registers)
 #pragma unroll
   for (int r = 0; r < 5; ++r) {
     double acc = (r == 2 || r == 4) ? -2.0 : 0.0;
 #pragma unroll
-    for (int s = 0; s < 5; ++s) acc = fma(V[r][s], f[s], acc);
+    for (int s = 0; s < 5; ++s) {
+      const double vr = r == 0 ? xi[s] : r == 1 ? eta[s] : r == 2 ? xi[s] * xi[s] : r == 3 ? xi[s] * eta[s]
+                                                                                           : eta[s] * eta[s];
+      acc = fma(vr, f[s], acc);
+    }
     ok = ok && abs_bits(acc) <= lim;
   }
 #pragma unroll
@@ -298,7 +304,7 @@ __constant__ SubsetOrder kOrder = make_subset_order();
 // A[q][c] - (A[q][K] / A[K][K]) A[K][c].  A template per column so that the
 // matrix stays in registers.
 template <int K>
-__device__ __forceinline__ void screen_column(float (&A)[5][6], float tiny, bool& ok) {
+__device__ __forceinline__ void screen_column(float (&A)[5][6], float (&rcp)[5], float tiny, bool& ok) {
   int p = K;
   float best = fabsf(A[K][K]);
 #pragma unroll
@@ -318,17 +324,19 @@ __device__ __forceinline__ void screen_column(float (&A)[5][6], float tiny, bool
       A[q][c] = sw ? a : b;
     }
   }
+  rcp[K] = __frcp_rn(A[K][K]);
 #pragma unroll
   for (int q = K + 1; q < 5; ++q) {
-    const float m = __fdiv_rn(A[q][K], A[K][K]);
+    const float m = __fmul_rn(A[q][K], rcp[K]);
 #pragma unroll
     for (int c = K + 1; c < 6; ++c) A[q][c] = __fsub_rn(A[q][c], __fmul_rn(m, A[K][c]));
   }
 }
 
 // Binary32 screen of a support (columns xs, es = float32 xi, eta): Gaussian
-// elimination of V_S f = b with every product, quotient and difference
-// rounded to float32 in a fixed order (the oracle repeats it operation by
+// elimination of V_S f = b with every product, reciprocal and difference
+// rounded to float32 in a fixed order (back substitution multiplies by the
+// pivots' reciprocals) (the oracle repeats it operation by
 // operation).  True iff no pivot is at most kScreenPivot times the largest
 // |entry| of V_S and every weight is >= -kScreenTol.  (After a failed pivot
 // the remaining arithmetic runs on but its result is not used.)
@@ -352,86 +360,99 @@ __device__ __forceinline__ bool screen32(const float* xs, const float* es) {
     for (int c = 0; c < 5; ++c) vmax = fmaxf(vmax, fabsf(A[r][c]));
   const float tiny = __fmul_rn(kScreenPivot, vmax);
   bool ok = true;
-  screen_column<0>(A, tiny, ok);
-  screen_column<1>(A, tiny, ok);
-  screen_column<2>(A, tiny, ok);
-  screen_column<3>(A, tiny, ok);
-  screen_column<4>(A, tiny, ok);
+  float rcp[5];
+  screen_column<0>(A, rcp, tiny, ok);
+  screen_column<1>(A, rcp, tiny, ok);
+  screen_column<2>(A, rcp, tiny, ok);
+  screen_column<3>(A, rcp, tiny, ok);
+  screen_column<4>(A, rcp, tiny, ok);
   float f[5];
 #pragma unroll
   for (int k = 4; k >= 0; --k) {
     float acc = A[k][5];
 #pragma unroll
     for (int q = k + 1; q < 5; ++q) acc = __fsub_rn(acc, __fmul_rn(A[k][q], f[q]));
-    f[k] = __fdiv_rn(acc, A[k][k]);
+    f[k] = __fmul_rn(acc, rcp[k]);
     ok = ok && f[k] >= -kScreenTol;
   }
   return ok;
 }
 
-// Writes an accepted stencil: the nonzero weights at positions `act` of the
-// 8 candidates, in slot order.
-__device__ __forceinline__ double write_stencil(int i, const int* js, const double* fs, unsigned act, int* cols,
-                                                double* f, double* fii, uint8_t* status) {
-  int* crow = cols + (size_t)i * VRM_STENCIL_W;
-  double* frow = f + (size_t)i * VRM_STENCIL_W;
-  double sum = 0.0;
-  int o = 0;
-#pragma unroll
-  for (int s = 0; s < kSup; ++s) {
-    if (((act >> s) & 1u) && abs_bits(fs[s]) != 0) {
-      crow[o] = js[s];
-      frow[o] = fs[s];
-      sum = __dadd_rn(sum, fs[s]);
-      ++o;
-    }
-  }
-  for (; o < VRM_STENCIL_W; ++o) {
-    crow[o] = -1;
-    frow[o] = 0.0;
-  }
-  fii[i] = -sum;
-  status[i] = VRM_LP_LEARNED;
-  return sum;
+// Per listed particle, what the screen chose: the five particles of the
+// support in slot order, the next support index, and whether it was the
+// first support tried (stats).
+struct ProjSel {
+  int j[5];
+  int next;
+  int first;
+  int pad;
+};
+
+// Appends v to list (warp-aggregated; the whole warp calls it converged).
+__device__ __forceinline__ void warp_append(bool take, int v, int* list, int* count) {
+  const unsigned bal = __ballot_sync(0xffffffffu, take);
+  int basepos = 0;
+  if ((threadIdx.x & 31) == 0 && bal) basepos = atomicAdd(count, __popc(bal));
+  basepos = __shfl_sync(0xffffffffu, basepos, 0);
+  if (take) list[basepos + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = v;
 }
 
-// One thread per listed particle.  Accepted stencils are written like the
-// LP's (nonzero weights in slot order, f~_ii = -sum in that order, status
-// VRM_LP_LEARNED); rejected particles are appended to reject_list (if given)
-// or marked VRM_LP_NONE.  The support loop runs warp-uniformly (all lanes
-// step through the subset order together until every lane has its answer)
-// so that the subset table in constant memory is read by broadcast.
-__global__ void __launch_bounds__(128) k_project(Consts c, const double* __restrict__ x, const double* __restrict__ y,
-                                                 const int* __restrict__ list, const int* __restrict__ list_count,
-                                                 int m_bound, const int* __restrict__ slots, const float* __restrict__ f0,
-                                                 const int* __restrict__ small, int* __restrict__ cols,
-                                                 double* __restrict__ f, double* __restrict__ fii,
-                                                 uint8_t* __restrict__ status, int* __restrict__ reject_list,
-                                                 int* __restrict__ reject_count, DevStats* __restrict__ ds,
-                                                 const double* __restrict__ dt_dev, double nu) {
-  const int m = list_count ? *list_count : m_bound;
-  const double nu_dt = dt_dev ? nu * *dt_dev : 0.0;
-  const double inv_h2 = 1.0 / (c.h * c.h);
-  int n_ok = 0, n_rej = 0, n_square = 0;
+// A rejected particle: to the LP's list (reject_list) or a zero stencil
+// with status VRM_LP_NONE.  Called converged by the whole warp.
+__device__ __forceinline__ void reject_particle(bool rej, int i, int* cols, double* f, double* fii, uint8_t* status,
+                                                int* reject_list, int* reject_count) {
+  if (reject_list) {
+    warp_append(rej, i, reject_list, reject_count);
+  } else if (rej) {
+    int* crow = cols + (size_t)i * VRM_STENCIL_W;
+    double* frow = f + (size_t)i * VRM_STENCIL_W;
+#pragma unroll
+    for (int s = 0; s < VRM_STENCIL_W; ++s) {
+      crow[s] = -1;
+      frow[s] = 0.0;
+    }
+    fii[i] = 0.0;
+    status[i] = VRM_LP_NONE;
+  }
+}
+
+// Screening: one thread per entry (round 0: every listed particle from the
+// first support; later rounds: the particles whose FP64 solve failed, from
+// their next support).  The support loop runs warp-uniformly (all lanes step
+// through the subset order together until each has a support passing the
+// binary32 screen or none is left), so that the subset table in constant
+// memory is read by broadcast.  A particle with a passing support goes to
+// solve_list, one without any to the rejects.
+__global__ void __launch_bounds__(128) k_screen(Consts c, const double* __restrict__ x, const double* __restrict__ y,
+                                                const int* __restrict__ list, const int* __restrict__ list_count,
+                                                int m_bound, const int* __restrict__ in_list,
+                                                const int* __restrict__ in_count, const int* __restrict__ slots,
+                                                const float* __restrict__ f0, const int* __restrict__ small,
+                                                ProjSel* __restrict__ sel, int* __restrict__ solve_list,
+                                                int* __restrict__ solve_count, int* __restrict__ cols,
+                                                double* __restrict__ f, double* __restrict__ fii,
+                                                uint8_t* __restrict__ status, int* __restrict__ reject_list,
+                                                int* __restrict__ reject_count, DevStats* __restrict__ ds) {
+  const int m = in_list ? *in_count : (list_count ? *list_count : m_bound);
   unsigned long long n_trials = 0;
-  double st_ratio = 0.0;
+  int n_rej = 0;
   const long stride = (long)gridDim.x * blockDim.x;
   for (long base = (long)blockIdx.x * blockDim.x; base < m; base += stride) {
-    const long t = base + threadIdx.x;
-    const bool active = t < m;
-    int i = -1, nc = 0;
+    const long e = base + threadIdx.x;
+    const bool active = e < m;
+    int t = 0, i = -1, nc = 0, start = 0;
     int js[kSup], rank[kSup];
-    double xi[kSup], eta[kSup];
     float xf[kSup], ef[kSup];
 #pragma unroll
     for (int s = 0; s < kSup; ++s) {
       js[s] = -1;
       rank[s] = kSup;
-      xi[s] = eta[s] = 0.0;
       xf[s] = ef[s] = 0.0f;
     }
     if (active) {
-      i = list ? list[t] : (int)t;
+      t = in_list ? in_list[e] : (int)e;
+      start = in_list ? sel[t].next : 0;
+      i = list ? list[t] : t;
       const float* p = f0 + (size_t)t * kSlots;
       const int* sl = slots + (size_t)t * kSlots;
       // candidates: the slots holding a small-neighbourhood particle (at
@@ -454,10 +475,10 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
         const int kk = s < nc ? (int)__fns(cand, 0, s + 1) : 0;
         js[s] = s < nc ? sl[kk] : -1;
         cv[s] = s < nc ? p[kk] : 0.0f;
-        xi[s] = s < nc ? __dmul_rn(__dsub_rn(x[js[s]], xi0), c.inv_h) : 0.0;
-        eta[s] = s < nc ? __dmul_rn(__dsub_rn(y[js[s]], yi0), c.inv_h) : 0.0;
-        xf[s] = __double2float_rn(xi[s]);
-        ef[s] = __double2float_rn(eta[s]);
+        const double xi = s < nc ? __dmul_rn(__dsub_rn(x[js[s]], xi0), c.inv_h) : 0.0;
+        const double eta = s < nc ? __dmul_rn(__dsub_rn(y[js[s]], yi0), c.inv_h) : 0.0;
+        xf[s] = __double2float_rn(xi);
+        ef[s] = __double2float_rn(eta);
       }
       // rank of every candidate (larger proposal first, ties to the lower slot)
 #pragma unroll
@@ -468,25 +489,21 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
         rank[s] = s < nc ? r : kSup;
       }
     }
-    // supports in the fixed order: binary32 screen, then the FP64 solve
-    bool done = nc < 5, accepted = false;
-    unsigned act = 0;
-    double fs[kSup];
-#pragma unroll
-    for (int s = 0; s < kSup; ++s) fs[s] = 0.0;
-    int trials = 0;
+    bool done = !active || nc < 5, have = false;
+    unsigned pm = 0;
+    int trials = 0, u_pass = 0;
     for (int u = 0; u < kSubsets; ++u) {
       if (__all_sync(0xffffffffu, done)) break;
-      if (done || kOrder.top[u] >= nc) continue;
+      if (done || u < start || kOrder.top[u] >= nc) continue;
       ++trials;
       const unsigned rm = kOrder.mask[u];
-      unsigned pm = 0;  // the support as positions (slot order)
+      unsigned um = 0;  // the support as positions (slot order)
 #pragma unroll
-      for (int s = 0; s < kSup; ++s) pm |= ((rm >> (rank[s] & 7)) & (rank[s] < kSup ? 1u : 0u)) << s;
+      for (int s = 0; s < kSup; ++s) um |= ((rm >> (rank[s] & 7)) & (rank[s] < kSup ? 1u : 0u)) << s;
       float xs[5], es[5];
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
-        const int pos = (int)__fns(pm, 0, q + 1);
+        const int pos = (int)__fns(um, 0, q + 1);
         float a = xf[0], b = ef[0];
 #pragma unroll
         for (int s = 1; s < kSup; ++s) {
@@ -496,70 +513,113 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
         xs[q] = a;
         es[q] = b;
       }
-      if (!screen32(xs, es)) continue;
-      double x5[5], e5[5], f5[5];
+      if (screen32(xs, es)) {
+        have = done = true;
+        pm = um;
+        u_pass = u;
+      }
+    }
+    if (have) {
+      ProjSel o;
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
         const int pos = (int)__fns(pm, 0, q + 1);
-        double a = xi[0], b = eta[0];
+        int jj = js[0];
 #pragma unroll
-        for (int s = 1; s < kSup; ++s) {
-          a = pos == s ? xi[s] : a;
-          b = pos == s ? eta[s] : b;
-        }
-        x5[q] = a;
-        e5[q] = b;
+        for (int s = 1; s < kSup; ++s) jj = pos == s ? js[s] : jj;
+        o.j[q] = jj;
       }
-      if (!square_stencil(x5, e5, f5)) continue;
-      int q = 0;
-#pragma unroll
-      for (int s = 0; s < kSup; ++s) {
-        double v = 0.0;
-#pragma unroll
-        for (int w = 0; w < 5; ++w) v = (((pm >> s) & 1u) && q == w) ? f5[w] : v;
-        fs[s] = v;
-        q += (pm >> s) & 1u;
-      }
-      act = pm;
-      accepted = done = true;
+      o.next = u_pass + 1;
+      o.first = !in_list && trials == 1;
+      o.pad = 0;
+      sel[t] = o;
     }
+    n_trials += trials;
+    const bool rej = active && !have;
+    n_rej += rej;
+    warp_append(have, t, solve_list, solve_count);
+    reject_particle(rej, i, cols, f, fii, status, reject_list, reject_count);
+  }
+  n_rej = __reduce_add_sync(0xffffffffu, n_rej);
+  n_trials = __reduce_add_sync(0xffffffffu, (unsigned)n_trials);
+  if ((threadIdx.x & 31) == 0) {
+    if (n_rej) atomicAdd(&ds->learned_rejected, n_rej);
+    if (n_trials) atomicAdd(&ds->learned_screens, n_trials);
+  }
+}
+
+// FP64 solve of the screened supports: one thread per entry of solve_list,
+// all lanes on the same work (the FP64 pipe runs full warps).  Accepted
+// stencils are written like the LP's (nonzero weights in slot order,
+// f~_ii = -sum in that order, status VRM_LP_LEARNED); a failed solve sends
+// the particle to retry_list (its next support), in the last round to the
+// rejects.
+__global__ void __launch_bounds__(128) k_solve(Consts c, const double* __restrict__ x, const double* __restrict__ y,
+                                               const int* __restrict__ list, const int* __restrict__ solve_list,
+                                               const int* __restrict__ solve_count, const ProjSel* __restrict__ sel,
+                                               int* __restrict__ retry_list, int* __restrict__ retry_count,
+                                               bool last_round, int* __restrict__ cols, double* __restrict__ f,
+                                               double* __restrict__ fii, uint8_t* __restrict__ status,
+                                               int* __restrict__ reject_list, int* __restrict__ reject_count,
+                                               DevStats* __restrict__ ds, const double* __restrict__ dt_dev, double nu) {
+  const int m = *solve_count;
+  const double nu_dt = dt_dev ? nu * *dt_dev : 0.0;
+  const double inv_h2 = 1.0 / (c.h * c.h);
+  int n_ok = 0, n_rej = 0, n_square = 0;
+  double st_ratio = 0.0;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long base = (long)blockIdx.x * blockDim.x; base < m; base += stride) {
+    const long e = base + threadIdx.x;
+    const bool active = e < m;
+    bool ok = false;
+    int t = 0, i = -1;
+    ProjSel o{};
     if (active) {
-      n_trials += trials;
-      if (accepted) {
-        const double sum = write_stencil(i, js, fs, act, cols, f, fii, status);
+      t = solve_list[e];
+      i = list ? list[t] : t;
+      o = sel[t];
+      const double xi0 = x[i], yi0 = y[i];
+      double x5[5], e5[5], f5[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        x5[q] = __dmul_rn(__dsub_rn(x[o.j[q]], xi0), c.inv_h);
+        e5[q] = __dmul_rn(__dsub_rn(y[o.j[q]], yi0), c.inv_h);
+      }
+      ok = square_stencil(x5, e5, f5);
+      if (ok) {
+        int* crow = cols + (size_t)i * VRM_STENCIL_W;
+        double* frow = f + (size_t)i * VRM_STENCIL_W;
+        double sum = 0.0;
+        int w = 0;
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+          if (abs_bits(f5[q]) != 0) {
+            crow[w] = o.j[q];
+            frow[w] = f5[q];
+            sum = __dadd_rn(sum, f5[q]);
+            ++w;
+          }
+        for (; w < VRM_STENCIL_W; ++w) {
+          crow[w] = -1;
+          frow[w] = 0.0;
+        }
+        fii[i] = -sum;
+        status[i] = VRM_LP_LEARNED;
         const double qr = __dmul_rn(__dmul_rn(nu_dt, sum), inv_h2);
         st_ratio = qr > st_ratio ? qr : st_ratio;
         ++n_ok;
-        n_square += trials == 1;
-      } else {
-        ++n_rej;
-        if (!reject_list) {
-          int* crow = cols + (size_t)i * VRM_STENCIL_W;
-          double* frow = f + (size_t)i * VRM_STENCIL_W;
-#pragma unroll
-          for (int s = 0; s < VRM_STENCIL_W; ++s) {
-            crow[s] = -1;
-            frow[s] = 0.0;
-          }
-          fii[i] = 0.0;
-          status[i] = VRM_LP_NONE;
-        }
+        n_square += o.first;
       }
     }
-    // warp-aggregated append of the rejected particles (the warp is converged here)
-    if (reject_list) {
-      const bool rej = active && !accepted;
-      const unsigned bal = __ballot_sync(0xffffffffu, rej);
-      int basepos = 0;
-      if ((threadIdx.x & 31) == 0 && bal) basepos = atomicAdd(reject_count, __popc(bal));
-      basepos = __shfl_sync(0xffffffffu, basepos, 0);
-      if (rej) reject_list[basepos + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = i;
-    }
+    const bool failed = active && !ok;
+    const bool rej = failed && last_round;
+    n_rej += rej;
+    warp_append(failed && !last_round, t, retry_list, retry_count);
+    reject_particle(rej, i, cols, f, fii, status, reject_list, reject_count);
   }
   n_ok = __reduce_add_sync(0xffffffffu, n_ok);
   n_rej = __reduce_add_sync(0xffffffffu, n_rej);
   n_square = __reduce_add_sync(0xffffffffu, n_square);
-  n_trials = __reduce_add_sync(0xffffffffu, (unsigned)n_trials);
   unsigned long long rb = (unsigned long long)__double_as_longlong(st_ratio);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -570,7 +630,6 @@ __global__ void __launch_bounds__(128) k_project(Consts c, const double* __restr
     if (n_ok) atomicAdd(&ds->learned_ok, n_ok);
     if (n_rej) atomicAdd(&ds->learned_rejected, n_rej);
     if (n_square) atomicAdd(&ds->learned_square, n_square);
-    if (n_trials) atomicAdd(&ds->learned_screens, n_trials);
     if (rb) atomicMax(&ds->max_dt_ratio_bits, rb);
   }
 }
@@ -609,17 +668,57 @@ cudaError_t learned_features(const Consts& c, const double* x, const double* y, 
   return cudaGetLastError();
 }
 
+cudaError_t proj_alloc(ProjScratch* p, int cap) {
+  proj_free(p);
+  cudaError_t e = cudaMalloc(&p->sel, sizeof(ProjSel) * (size_t)cap);
+  if (e == cudaSuccess) e = cudaMalloc(&p->list_s, sizeof(int) * (size_t)cap);
+  if (e == cudaSuccess) e = cudaMalloc(&p->list_r, sizeof(int) * (size_t)cap);
+  if (e == cudaSuccess) e = cudaMalloc(&p->counts, sizeof(int) * 2 * kProjRounds);
+  if (e != cudaSuccess) {
+    proj_free(p);
+    return e;
+  }
+  p->cap = cap;
+  return cudaSuccess;
+}
+
+void proj_free(ProjScratch* p) {
+  cudaFree(p->sel);
+  cudaFree(p->list_s);
+  cudaFree(p->list_r);
+  cudaFree(p->counts);
+  *p = ProjScratch{};
+}
+
+// Rounds of (screen, FP64 solve): round r screens the particles whose solve
+// of round r-1 failed, from their next support; a particle reaches at most
+// kProjRounds = kMaxSolves FP64 solves.  Fixed launches (graph-capturable),
+// the lists and their sizes on the device.
 cudaError_t learned_project(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
                             int m_bound, const int* slots, const float* f0, const int* small, int* cols, double* f,
-                            double* fii,
-                            uint8_t* status, int* reject_list, int* reject_count, DevStats* ds, const double* dt_dev,
-                            double nu, cudaStream_t s) {
+                            double* fii, uint8_t* status, int* reject_list, int* reject_count, DevStats* ds,
+                            const double* dt_dev, double nu, ProjScratch* ps, cudaStream_t s) {
   if (m_bound <= 0) return cudaSuccess;
+  if (!ps || ps->cap < m_bound) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(ps->counts, 0, sizeof(int) * 2 * kProjRounds, s);
+  if (e != cudaSuccess) return e;
   int blocks = (m_bound + 127) / 128;
   if (blocks > 16 * sm_count()) blocks = 16 * sm_count();
-  k_project<<<blocks, 128, 0, s>>>(c, x, y, list, list_count, m_bound, slots, f0, small, cols, f, fii, status,
-                                   reject_list, reject_count, ds, dt_dev, nu);
-  note_launch();
+  for (int r = 0; r < kProjRounds; ++r) {
+    int* solve_count = ps->counts + 2 * r;
+    int* retry_count = ps->counts + 2 * r + 1;
+    const int* in_list = r == 0 ? nullptr : ps->list_r;
+    const int* in_count = r == 0 ? nullptr : ps->counts + 2 * r - 1;
+    // the round's retry list is read by its screen before the solve rewrites it
+    k_screen<<<blocks, 128, 0, s>>>(c, x, y, list, list_count, m_bound, in_list, in_count, slots, f0, small,
+                                    reinterpret_cast<ProjSel*>(ps->sel), ps->list_s, solve_count, cols, f, fii,
+                                    status, reject_list, reject_count, ds);
+    note_launch();
+    k_solve<<<blocks, 128, 0, s>>>(c, x, y, list, ps->list_s, solve_count, reinterpret_cast<const ProjSel*>(ps->sel),
+                                   ps->list_r, retry_count, r == kProjRounds - 1, cols, f, fii, status, reject_list,
+                                   reject_count, ds, dt_dev, nu);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 

@@ -462,7 +462,63 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
   flush_stats(ds, st_ok, st_none, st_maxpiv, st_ratio, false, st_solved, st_pivots);
 }
 
-// Full-neighbourhood retry: one warp per particle, lane l holds column l.
+// Monomial of Vandermonde row r at (xi, eta), rounded exactly as vcol<M>
+// rounds it: rows 0, 1 are xi, eta; 2, 3, 4 are xi xi, xi eta, eta eta; 5 to
+// 8 are (xi xi) xi, (xi xi) eta, xi (eta eta), (eta eta) eta.
+__device__ __forceinline__ double vrow(int r, double xi, double eta) {
+  const double u = (r == 4 || r == 7 || r == 8) ? eta : xi;
+  const double v = (r == 2 || r == 5 || r == 6) ? xi : eta;
+  const double quad = __dmul_rn(u, v);
+  const double cub = __dmul_rn(quad, (r == 5 || r == 7) ? xi : eta);
+  return r == 0 ? xi : r == 1 ? eta : r < 5 ? quad : cub;
+}
+
+// One column K of the lane-parallel LU of an M x M matrix (row r on lane
+// r): the first largest |A[r][K]| at or below the diagonal is the pivot, its
+// row and the right-hand side swap with row K, rcpd[K] = 1 / pivot, and the
+// rows below store the multiplier A[r][K] rcpd[K] and subtract it times the
+// pivot row, products and differences rounded separately.  Recursion over K
+// keeps every index static (the matrix stays in registers).
+template <int K, int M>
+__device__ __forceinline__ void lu_rows(double (&A)[M], double& z, double (&rcpd)[M], bool& sing, int lane) {
+  if constexpr (K < M) {
+    constexpr unsigned kAll = 0xffffffffu;
+    const bool rowk = lane >= K && lane < M;
+    const unsigned long long key = rowk ? (unsigned long long)(dbits(A[K]) & 0x7FFFFFFFFFFFFFFFLL) : 0ull;
+    unsigned long long best = key;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(kAll, best, o);
+      best = ob > best ? ob : best;
+    }
+    sing = sing || best == 0ull;
+    const int p = __ffs(__ballot_sync(kAll, rowk && key == best)) - 1;
+    const int partner = lane == K ? p : (lane == p ? K : lane);
+#pragma unroll
+    for (int q = 0; q < M; ++q) A[q] = __shfl_sync(kAll, A[q], partner);
+    z = __shfl_sync(kAll, z, partner);
+    rcpd[K] = __drcp_rn(__shfl_sync(kAll, A[K], K));
+    const bool below = lane > K && lane < M;
+    const double l = __dmul_rn(A[K], rcpd[K]);
+    if (below) A[K] = l;
+#pragma unroll
+    for (int q = K + 1; q < M; ++q) {
+      const double pq = __shfl_sync(kAll, A[q], K);
+      if (below) A[q] = __dsub_rn(A[q], __dmul_rn(l, pq));
+    }
+    lu_rows<K + 1, M>(A, z, rcpd, sing, lane);
+  }
+}
+
+// Full-neighbourhood retry: one warp per particle.  Lane l holds tableau
+// column l (K <= 32 columns, the FP64 work of the pivots); the per-row
+// quantities (right-hand side, basic variable, ratio) live on lane r for row
+// r, so that the ratio test costs one reciprocal per lane and a warp minimum
+// instead of m divisions on every lane.  The final basis is factored with
+// row r on lane r (the oracle's LU sequence: first largest pivot, full row
+// swaps, multipliers times the pivot's reciprocal, separately rounded
+// updates), forward substitution in column order, back substitution row by
+// row; the result is bit-identical to the oracle's basis solve.
 template <int M, int W>
 __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restrict__ x,
                                                  const double* __restrict__ y, const int* __restrict__ fail_list,
@@ -472,6 +528,7 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
                                                  double* __restrict__ fii, uint8_t* __restrict__ status,
                                                  DevStats* __restrict__ ds, double nu_dt,
                                                  const double* __restrict__ dt_dev, double nu) {
+  constexpr unsigned kAll = 0xffffffffu;
   if (dt_dev) nu_dt = nu * *dt_dev;
   const int lane = threadIdx.x & 31;
   const long warp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -498,14 +555,15 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
     // bitonic sort of (d2, j) across the warp, ascending
     for (int size = 2; size <= 32; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        const double od2 = __shfl_xor_sync(0xffffffffu, d2, stride);
-        const int oj = __shfl_xor_sync(0xffffffffu, j, stride);
-        const double odx = __shfl_xor_sync(0xffffffffu, dx, stride);
-        const double ody = __shfl_xor_sync(0xffffffffu, dy, stride);
+        const double od2 = __shfl_xor_sync(kAll, d2, stride);
+        const int oj = __shfl_xor_sync(kAll, j, stride);
+        const double odx = __shfl_xor_sync(kAll, dx, stride);
+        const double ody = __shfl_xor_sync(kAll, dy, stride);
         const bool up = ((lane & size) == 0);
         const bool lower = ((lane & stride) == 0);
-        const bool other_less = (od2 < d2) || (od2 == d2 && oj < j);
-        const bool take = (lower == up) ? other_less : !other_less && !(od2 == d2 && oj == j);
+        const bool eq = dbits(od2) == dbits(d2);  // d2 >= +0: bit order is value order
+        const bool other_less = lt_nonneg(od2, d2) || (eq && oj < j);
+        const bool take = (lower == up) ? other_less : !other_less && !(eq && oj == j);
         if (take) {
           d2 = od2;
           j = oj;
@@ -524,57 +582,55 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
       s = __dadd_rn(s, v[r]);
     }
     double d = 0.0 - s;
-    double rhs[M], w = 4.0;
-#pragma unroll
-    for (int r = 0; r < M; ++r) rhs[r] = b_of(r);
-    int basis[M];
-#pragma unroll
-    for (int r = 0; r < M; ++r) basis[r] = r;
+    // row r on lane r: right-hand side and basic variable (artificials first)
+    double rhs = lane < M ? b_of(lane) : 0.0;
+    int bas = lane < M ? lane : INT_MAX;
     bool isb = false;
     int it = 0, code = 0;
     int n_art = M;
     for (;;) {
       if (n_art == 0) break;  // phase I over: every reduced cost is zero
-      const unsigned cand = __ballot_sync(0xffffffffu, lane < K && !isb && d < -kTolPrice);
+      const unsigned cand = __ballot_sync(kAll, lane < K && !isb && lt_neg(d, kTolPrice));
       if (!cand) break;
       if (it == kPivotCap) {
         code = 2;
         break;
       }
       const int q = __ffs(cand) - 1;
-      double a[M];
-#pragma unroll
-      for (int r = 0; r < M; ++r) a[r] = __shfl_sync(0xffffffffu, T[r], q);
-      double ratio[M], theta = 1e308;
-      bool any = false;
+      double a[M], amine = 0.0;
 #pragma unroll
       for (int r = 0; r < M; ++r) {
-        ratio[r] = a[r] > kTolPivot ? __ddiv_rn(rhs[r] > kTolSnap ? rhs[r] : 0.0, a[r]) : 1e308;
-        if (a[r] > kTolPivot) {
-          any = true;
-          theta = ratio[r] < theta ? ratio[r] : theta;
-        }
+        a[r] = __shfl_sync(kAll, T[r], q);
+        amine = (lane == r) ? a[r] : amine;
       }
-      if (!any) {
+      // ratio test, row r on lane r: basic values <= kTolSnap are zeros,
+      // ratios by a Newton reciprocal (relative error ~2^-45, far inside the
+      // tie window); theta = the smallest ratio (non-negative: bit order)
+      const bool elig = lane < M && gt_pos(amine, kTolPivot);
+      const double num = gt_pos(rhs, kTolSnap) ? rhs : 0.0;
+      const double ratio = elig ? __dmul_rn(num, rcp_newton<1>(amine)) : 1e308;
+      unsigned long long rb = elig ? (unsigned long long)dbits(ratio) : ~0ull;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(kAll, rb, o);
+        rb = ob < rb ? ob : rb;
+      }
+      if (rb == ~0ull) {
         code = 2;
         break;
       }
-      const double lim = theta + kTolTie * (theta > 1.0 ? theta : 1.0);
-      int leave = -1, lbas = INT_MAX;
+      const double theta = __longlong_as_double((long long)rb);
+      const double lim = __fma_rn(kTolTie, gt_pos(theta, 1.0) ? theta : 1.0, theta);
+      // leaving row: the lowest basic variable among the tied rows
+      const int key = (elig && !lt_nonneg(lim, ratio)) ? bas : INT_MAX;
+      const int lbas = __reduce_min_sync(kAll, key);
+      const int leave = __ffs(__ballot_sync(kAll, key == lbas)) - 1;
+      const double piv = __shfl_sync(kAll, amine, leave);
+      const double prhs_raw = __shfl_sync(kAll, rhs, leave);
+      double prow_raw = T[0];
 #pragma unroll
-      for (int r = 0; r < M; ++r)
-        if (a[r] > kTolPivot && ratio[r] <= lim && basis[r] < lbas) {
-          leave = r;
-          lbas = basis[r];
-        }
-      double piv = a[0], prhs_raw = rhs[0], prow_raw = T[0];
-#pragma unroll
-      for (int r = 1; r < M; ++r) {
-        piv = (leave == r) ? a[r] : piv;
-        prhs_raw = (leave == r) ? rhs[r] : prhs_raw;
-        prow_raw = (leave == r) ? T[r] : prow_raw;
-      }
-      const double rcp = __drcp_rn(piv);
+      for (int r = 1; r < M; ++r) prow_raw = (leave == r) ? T[r] : prow_raw;
+      const double rcp = rcp_newton<2>(piv);
       const double prow = (lane == q) ? 1.0 : __dmul_rn(prow_raw, rcp);
       const double prhs = __dmul_rn(prhs_raw, rcp);
 #pragma unroll
@@ -583,35 +639,54 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
         const double ar = lr ? 0.0 : a[r];
         const double u = __fma_rn(-ar, prow, T[r]);
         T[r] = lr ? prow : ((lane == q) ? 0.0 : u);
-        const double ur = __fma_rn(-ar, prhs, rhs[r]);
-        rhs[r] = lr ? prhs : ur;
       }
-      const double dq = __shfl_sync(0xffffffffu, d, q);
+      rhs = (lane == leave) ? prhs : __fma_rn(-amine, prhs, rhs);
+      const double dq = __shfl_sync(kAll, d, q);
       d = (lane == q) ? 0.0 : __fma_rn(-dq, prow, d);
-      w = __fma_rn(-dq, prhs, w);
       if (lbas >= M && lane == lbas - M) isb = false;
       if (lbas < M) --n_art;
       if (lane == q) isb = true;
-#pragma unroll
-      for (int r = 0; r < M; ++r) basis[r] = (leave == r) ? M + q : basis[r];
+      if (lane == leave) bas = M + q;
       ++it;
     }
-    // basic solution of the final basis by the oracle's LU sequence; every
-    // lane solves the same system from the broadcast basic columns
+    // basic solution of the final basis by the oracle's LU sequence, row r of
+    // B on lane r: column k is e_v for an artificial v = basis[k] < m, else
+    // the Vandermonde column of the basic structural
     double fv = 0.0, wsum = 0.0;
     if (code == 0) {
-      double bxi[M], beta[M], xB[M];
+      double A[M];
+      int bk[M];
 #pragma unroll
-      for (int r = 0; r < M; ++r) {
-        const int src = basis[r] >= M ? basis[r] - M : 0;
-        bxi[r] = __shfl_sync(0xffffffffu, cxi, src);
-        beta[r] = __shfl_sync(0xffffffffu, ceta, src);
+      for (int k = 0; k < M; ++k) {
+        bk[k] = __shfl_sync(kAll, bas, k);
+        const int src = bk[k] >= M ? bk[k] - M : 0;
+        const double bx = __shfl_sync(kAll, cxi, src), be = __shfl_sync(kAll, ceta, src);
+        A[k] = bk[k] < M ? (bk[k] == lane ? 1.0 : 0.0) : vrow(lane, bx, be);
       }
-      if (!basis_solve<M>(basis, bxi, beta, xB)) code = 2;
+      double z = lane < M ? b_of(lane) : 0.0;
+      double rcpd[M];
+      bool sing = false;
+      lu_rows<0, M>(A, z, rcpd, sing, lane);
+      // forward substitution: row r takes its terms in ascending column order
 #pragma unroll
-      for (int r = 0; r < M; ++r) {
-        if (basis[r] < M) wsum = __dadd_rn(wsum, xB[r]);
-        else if (basis[r] == M + lane) fv = xB[r] > kTolSnap ? xB[r] : 0.0;
+      for (int q = 0; q < M - 1; ++q) {
+        const double zq = __shfl_sync(kAll, z, q);
+        if (lane > q && lane < M) z = __dsub_rn(z, __dmul_rn(A[q], zq));
+      }
+      // back substitution row by row (ascending columns within a row)
+      double xB[M];
+#pragma unroll
+      for (int r = M - 1; r >= 0; --r) {
+        double acc = z;
+#pragma unroll
+        for (int q = r + 1; q < M; ++q) acc = __dsub_rn(acc, __dmul_rn(A[q], xB[q]));
+        xB[r] = __shfl_sync(kAll, __dmul_rn(acc, rcpd[r]), r);
+      }
+      if (sing) code = 2;
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        if (bk[k] < M) wsum = __dadd_rn(wsum, xB[k]);
+        else if (bk[k] == M + lane) fv = gt_pos(xB[k], kTolSnap) ? xB[k] : 0.0;
       }
     }
     double rmax = 0.0;
@@ -619,17 +694,17 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
     for (int r = 0; r < M; ++r) {
       double p = __dmul_rn(v[r], fv);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) p = __dadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
+      for (int o = 16; o > 0; o >>= 1) p = __dadd_rn(p, __shfl_xor_sync(kAll, p, o));
       const double e = fabs(__dsub_rn(p, b_of(r)));
-      rmax = e > rmax ? e : rmax;
+      rmax = abs_gt(e, rmax) ? e : rmax;
     }
-    const bool feasible = code == 0 && wsum <= kTolPhase1 && rmax <= kTolResid;
+    const bool feasible = code == 0 && !gt_pos(wsum, kTolPhase1) && !gt_pos(rmax, kTolResid);
     int* crow = cols + (size_t)i * W;
     double* frow = f + (size_t)i * W;
-    const unsigned nz = __ballot_sync(0xffffffffu, feasible && fv != 0.0);
+    const unsigned nz = __ballot_sync(kAll, feasible && dbits(fv) != 0);
     if (feasible) {
       const int slot = __popc(nz & ((1u << lane) - 1u));
-      if (fv != 0.0 && slot < W) {
+      if (dbits(fv) != 0 && slot < W) {
         crow[slot] = j;
         frow[slot] = fv;
       }
@@ -644,14 +719,14 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
       while (rest) {
         const int l = __ffs(rest) - 1;
         rest &= rest - 1;
-        sacc = __dadd_rn(sacc, __shfl_sync(0xffffffffu, fv, l));
+        sacc = __dadd_rn(sacc, __shfl_sync(kAll, fv, l));
       }
       if (lane == 0) {
         fii[i] = -sacc;
         status[i] = VRM_LP_FULL;
         ++st_ok;
-        const double q = __dmul_rn(__dmul_rn(nu_dt, sacc), inv_h2);
-        st_ratio = q > st_ratio ? q : st_ratio;
+        const double qr = __dmul_rn(__dmul_rn(nu_dt, sacc), inv_h2);
+        st_ratio = qr > st_ratio ? qr : st_ratio;
       }
     } else {
       if (lane < W) {
@@ -673,9 +748,9 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
     }
   }
   flush_stats(ds, st_ok, st_none, st_maxpiv, st_ratio, true, st_solved, st_pivots);
-  st_cols = __reduce_add_sync(0xffffffffu, (unsigned)st_cols);
+  st_cols = __reduce_add_sync(kAll, (unsigned)st_cols);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) st_colpiv += __shfl_xor_sync(0xffffffffu, st_colpiv, o);
+  for (int o = 16; o > 0; o >>= 1) st_colpiv += __shfl_xor_sync(kAll, st_colpiv, o);
   if (lane == 0 && st_cols) {
     atomicAdd(&ds->lp_full_columns, (unsigned long long)st_cols);
     atomicAdd(&ds->lp_full_column_pivots, st_colpiv);

@@ -243,24 +243,37 @@ __global__ void __launch_bounds__(128, 1) k_gemm(const __grid_constant__ CUtenso
 
 // ---- fused inference ------------------------------------------------------------------
 //
-// The whole network for 128-row tiles in one persistent kernel: the tile's
-// activations never leave shared memory.  16 warps; thread 0 streams the
-// weight slabs (64 input columns of one layer: W1, W2, W3 with 256 rows,
-// W4 with 32) through a 4-stage ring with TMA and issues the MMAs; after
-// each layer every warp reads a 32-row x 64-column block of the TMEM
-// accumulator (warp w: rows 32 (w mod 4), columns 64 (w div 4)), adds the
-// bias, applies GELU and writes bf16 back into the activation tile in the
-// MMA operand layout (128-byte swizzle), which the next layer reads as A.
-// The input tile is loaded into the first two slabs of the activation tile
-// as soon as the previous tile's last layer has consumed it.
+// The whole network for 128-row tiles in one persistent kernel; a tile's
+// activations never leave shared memory.  Two tiles are in flight per CTA
+// (slots 0 and 1: activation tiles H[0], H[1], TMEM columns 0-255 and
+// 256-511) so that the MMAs of one overlap the epilogue of the other:
+//   warp 16 (one thread): streams the weight slabs (64 input columns of one
+//     layer: W1, W2, W3 with 256 rows, W4 with 32) through a 3-stage ring
+//     with TMA, loads the input tiles, and issues the MMAs layer by layer,
+//     alternating the slots (a weight slab is loaded once per slot);
+//   warps 0-15: the epilogue of each (slot, layer) as its accumulator
+//     completes: warp w reads TMEM lanes 32 (w mod 4), columns 64 (w div 4),
+//     adds the bias, applies GELU and writes bf16 back into the slot's
+//     activation tile in the MMA operand layout (128-byte swizzle), which the
+//     next layer reads as A; the last layer writes the 32 proposals.
+// Barriers per slot: xfull (input tile loaded), accf (the layer's MMAs are
+// complete: commit), actr (the layer's epilogue is done: 16 warp arrivals,
+// so the next layer may overwrite TMEM and read the activations), hfree (the
+// last layer's MMAs are complete: the next input may replace the tile).
+// Every wait is bounded; one that gives up raises a shared abort flag that
+// every role checks before its next wait, and the error flag in global
+// memory.
 
-constexpr int kFusedThreads = 512;
-constexpr int kRing = 4;
+constexpr int kEpiWarps = 16;
+constexpr int kFusedThreads = (kEpiWarps + 1) * 32;
+constexpr int kRing = 3;
 constexpr int kSlabsPerTile = 14;  // W1: 2, W2: 4, W3: 4, W4: 4
-constexpr uint32_t kRingBytes = 256 * kBK * 2;  // one 256-row slab
-constexpr size_t kFusedSmem = 1024 + 4 * (size_t)kBM * kBK * 2 + (size_t)kRing * kRingBytes +
-                              (size_t)(3 * kHid + kOut) * 4 + 256;
+constexpr int kSlabsPerPair = 2 * kSlabsPerTile;
+constexpr uint32_t kSlabBytes = kBM * kBK * 2;  // one 128-row activation slab
+constexpr uint32_t kRingBytes = 256 * kBK * 2;  // one 256-row weight slab
+constexpr size_t kFusedSmem = 1024 + 2 * 4 * (size_t)kSlabBytes + (size_t)kRing * kRingBytes + 256;
 
+// Layer and K slab of the g-th weight slab a single tile consumes.
 __device__ __forceinline__ void slab_of(int s, int* layer, int* kb) {
   if (s < 2) {
     *layer = 0, *kb = s;
@@ -270,6 +283,26 @@ __device__ __forceinline__ void slab_of(int s, int* layer, int* kb) {
     *layer = 2, *kb = s - 6;
   } else {
     *layer = 3, *kb = s - 10;
+  }
+}
+
+// Layer and K slab of the g-th weight slab the producer consumes: whole
+// pairs of tiles take each layer's slabs twice (slot 0, then slot 1); a
+// last unpaired tile takes them once.
+__device__ __forceinline__ void slab_at(int g, int pairs, int* layer, int* kb) {
+  if (g < pairs * kSlabsPerPair) {
+    const int r = g % kSlabsPerPair;
+    if (r < 4) {
+      *layer = 0, *kb = r & 1;
+    } else if (r < 12) {
+      *layer = 1, *kb = (r - 4) & 3;
+    } else if (r < 20) {
+      *layer = 2, *kb = (r - 12) & 3;
+    } else {
+      *layer = 3, *kb = (r - 20) & 3;
+    }
+  } else {
+    slab_of(g - pairs * kSlabsPerPair, layer, kb);
   }
 }
 
@@ -294,146 +327,199 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
   const int ntiles = (rows + kBM - 1) / kBM;
   if ((int)blockIdx.x >= ntiles) return;
   const int my_tiles = (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
-  const int total = my_tiles * kSlabsPerTile;
+  const int pairs_full = my_tiles / 2;
+  const int npairs = (my_tiles + 1) / 2;
+  const int total = pairs_full * kSlabsPerPair + (my_tiles & 1) * kSlabsPerTile;
 
   uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint8_t* H = base;                                   // 4 slabs x 16 KB
-  uint8_t* ring = base + 4 * (size_t)kBM * kBK * 2;    // kRing x 32 KB
-  float* sbias = (float*)(ring + (size_t)kRing * kRingBytes);
-  uint64_t* bars = (uint64_t*)(sbias + 3 * kHid + kOut);
+  uint8_t* H = base;                         // 2 slots x 4 slabs x 16 KB
+  uint8_t* ring = base + 8 * (size_t)kSlabBytes;  // kRing x 32 KB
+  uint64_t* bars = (uint64_t*)(ring + (size_t)kRing * kRingBytes);
   uint64_t* xfull = bars;
-  uint64_t* wfull = bars + 1;
-  uint64_t* wempty = bars + 1 + kRing;
-  uint64_t* acc = bars + 1 + 2 * kRing;
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 + 2 * kRing);
+  uint64_t* accf = bars + 2;
+  uint64_t* actr = bars + 4;
+  uint64_t* hfree = bars + 6;
+  uint64_t* wfull = bars + 8;
+  uint64_t* wempty = bars + 8 + kRing;
+  uint64_t* drain = bars + 8 + 2 * kRing;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int k = threadIdx.x; k < 3 * kHid + kOut; k += blockDim.x) {
-    const long off = k < kHid ? kOffB1 + k : k < 2 * kHid ? kOffB2 + k - kHid : k < 3 * kHid ? kOffB3 + k - 2 * kHid
-                                                                                      : kOffB4 + k - 3 * kHid;
-    sbias[k] = a.bias[off];
-  }
   if (threadIdx.x == 0) {
-    umma::mbar_init(xfull, 1);
+    for (int s = 0; s < 2; ++s) {
+      umma::mbar_init(&xfull[s], 1);
+      umma::mbar_init(&accf[s], 1);
+      umma::mbar_init(&actr[s], kEpiWarps);
+      umma::mbar_init(&hfree[s], 1);
+    }
     for (int s = 0; s < kRing; ++s) {
       umma::mbar_init(&wfull[s], 1);
       umma::mbar_init(&wempty[s], 1);
     }
-    umma::mbar_init(acc, 1);
+    umma::mbar_init(drain, 1);
+    *abort_flag = 0;
     umma::fence_barrier_init();
   }
-  if (warp == 0) umma::tmem_alloc(tmem_slot, 256);
+  if (warp == 0) umma::tmem_alloc(tmem_slot, 512);
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
-  const CUtensorMap* wmap[4] = {&tw1, &tw2, &tw3, &tw4};
-  int g_load = 0;  // next weight slab to load (thread 0)
-  bool fail = false;
-  auto load_w = [&](int g) {
-    int layer, kb;
-    slab_of(g % kSlabsPerTile, &layer, &kb);
-    const int st = g % kRing;
-    umma::mbar_arrive_expect_tx(&wfull[st], layer == 3 ? (uint32_t)kOut * kBK * 2 : kRingBytes);
-    umma::tma_load_2d(ring + (size_t)st * kRingBytes, wmap[layer], &wfull[st], kb * kBK, 0);
-  };
-  auto load_x = [&](int tile) {
-    umma::mbar_arrive_expect_tx(xfull, 2u * kBM * kBK * 2);
-    umma::tma_load_2d(H, &tx, xfull, 0, tile * kBM);
-    umma::tma_load_2d(H + (size_t)kBM * kBK * 2, &tx, xfull, kBK, tile * kBM);
-  };
-  if (threadIdx.x == 0) {
-    load_x(blockIdx.x);
-    for (; g_load < kRing && g_load < total; ++g_load) load_w(g_load);
-  }
-  int acc_phase = 0;
-  const int layer_start[4] = {0, 2, 6, 10};
-  const int layer_nk[4] = {2, 4, 4, 4};
-  for (int it = 0; it < my_tiles; ++it) {
-    const int tile = blockIdx.x + it * gridDim.x;
-    for (int l = 0; l < 4; ++l) {
-      if (threadIdx.x == 0) {
-        if (l == 0 && !umma::mbar_wait(xfull, (uint32_t)it & 1u, kWaitCycles)) fail = true;
-        const uint32_t idesc = umma::idesc_bf16(kBM, l == 3 ? kOut : kHid);
-        for (int kb = 0; kb < layer_nk[l] && !fail; ++kb) {
-          const int g = it * kSlabsPerTile + layer_start[l] + kb;
-          const int st = g % kRing;
-          if (!umma::mbar_wait(&wfull[st], (uint32_t)(g / kRing) & 1u, kWaitCycles)) {
-            fail = true;
-            break;
-          }
-          umma::fence_after_sync();
-          const uint64_t da = umma::desc_sw128(umma::smem_u32(H + (size_t)kb * kBM * kBK * 2));
-          const uint64_t db = umma::desc_sw128(umma::smem_u32(ring + (size_t)st * kRingBytes));
-#pragma unroll
-          for (int k = 0; k < kBK / 16; ++k) umma::mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
-          umma::mma_commit(&wempty[st]);
-          // refill the slot of the previous slab (its MMAs were issued earlier)
-          const int gp = g - 1;
-          if (gp >= 0 && gp + kRing < total && g_load == gp + kRing) {
-            if (!umma::mbar_wait(&wempty[gp % kRing], (uint32_t)(gp / kRing) & 1u, kWaitCycles)) {
+  if (warp == kEpiWarps) {
+    // ---- producer / MMA issue (one thread) ----
+    if (lane == 0) {
+      const CUtensorMap* wmap[4] = {&tw1, &tw2, &tw3, &tw4};
+      auto load_w = [&](int gl) {
+        int layer, kb;
+        slab_at(gl, pairs_full, &layer, &kb);
+        const int st = gl % kRing;
+        umma::mbar_arrive_expect_tx(&wfull[st], layer == 3 ? (uint32_t)kOut * kBK * 2 : kRingBytes);
+        umma::tma_load_2d(ring + (size_t)st * kRingBytes, wmap[layer], &wfull[st], kb * kBK, 0);
+      };
+      auto load_x = [&](int s, int tile) {
+        uint8_t* h = H + (size_t)s * 4 * kSlabBytes;
+        umma::mbar_arrive_expect_tx(&xfull[s], 2u * kSlabBytes);
+        umma::tma_load_2d(h, &tx, &xfull[s], 0, tile * kBM);
+        umma::tma_load_2d(h + kSlabBytes, &tx, &xfull[s], kBK, tile * kBM);
+      };
+      load_x(0, blockIdx.x);
+      if (my_tiles > 1) load_x(1, blockIdx.x + gridDim.x);
+      int g_load = 0;
+      for (; g_load < kRing && g_load < total; ++g_load) load_w(g_load);
+      bool fail = false;
+      int g = 0;
+      for (int p = 0; p < npairs && !fail; ++p) {
+        const int nslot = (2 * p + 1 < my_tiles) ? 2 : 1;
+        for (int l = 0; l < 4 && !fail; ++l) {
+          for (int s = 0; s < nslot && !fail; ++s) {
+            if (*abort_flag) {
               fail = true;
               break;
             }
-            load_w(g_load++);
+            if (l == 0 && !umma::mbar_wait(&xfull[s], (uint32_t)p & 1u, kWaitCycles)) {
+              fail = true;
+              break;
+            }
+            const int e = 4 * p + l;  // epilogues of this slot that must be done
+            if (e > 0 && !umma::mbar_wait(&actr[s], (uint32_t)(e - 1) & 1u, kWaitCycles)) {
+              fail = true;
+              break;
+            }
+            umma::fence_after_sync();
+            const uint32_t idesc = umma::idesc_bf16(kBM, l == 3 ? kOut : kHid);
+            const int nk = l == 0 ? 2 : 4;
+            uint8_t* h = H + (size_t)s * 4 * kSlabBytes;
+            for (int kb = 0; kb < nk; ++kb, ++g) {
+              const int st = g % kRing;
+              if (!umma::mbar_wait(&wfull[st], (uint32_t)(g / kRing) & 1u, kWaitCycles)) {
+                fail = true;
+                break;
+              }
+              umma::fence_after_sync();
+              const uint64_t da = umma::desc_sw128(umma::smem_u32(h + (size_t)kb * kSlabBytes));
+              const uint64_t db = umma::desc_sw128(umma::smem_u32(ring + (size_t)st * kRingBytes));
+#pragma unroll
+              for (int k = 0; k < kBK / 16; ++k)
+                umma::mma_bf16(tmem + (uint32_t)(s * 256), da + 2 * k, db + 2 * k, idesc, (kb | k) != 0);
+              umma::mma_commit(&wempty[st]);
+              // refill the slot of the previous slab (its MMAs were issued earlier)
+              const int gp = g - 1;
+              if (gp >= 0 && gp + kRing < total && g_load == gp + kRing) {
+                if (!umma::mbar_wait(&wempty[gp % kRing], (uint32_t)(gp / kRing) & 1u, kWaitCycles)) {
+                  fail = true;
+                  break;
+                }
+                load_w(g_load++);
+              }
+            }
+            if (fail) break;
+            umma::mma_commit(&accf[s]);
+            if (l == 3) umma::mma_commit(&hfree[s]);
           }
         }
-        umma::mma_commit(acc);
+        // the next inputs, once the last layer's MMAs of a slot have read its tile
+        for (int s = 0; s < nslot && !fail; ++s) {
+          const int nt = 2 * (p + 1) + s;
+          if (nt >= my_tiles) continue;
+          if (!umma::mbar_wait(&hfree[s], (uint32_t)p & 1u, kWaitCycles)) {
+            fail = true;
+            break;
+          }
+          load_x(s, blockIdx.x + nt * gridDim.x);
+        }
       }
-      const bool got = umma::mbar_wait(acc, (uint32_t)acc_phase & 1u, 2 * kWaitCycles);
-      ++acc_phase;
-      umma::fence_after_sync();
-      // the last layer has consumed the activation tile: bring in the next input
-      if (l == 3 && threadIdx.x == 0 && got && !fail && it + 1 < my_tiles) load_x(tile + gridDim.x);
-      const int q = warp & 3, cg = warp >> 2;
-      const int r = q * 32 + lane;  // row within the tile
-      const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-      if (l < 3) {
-        const float* b = sbias + l * kHid;
+      if (fail) *abort_flag = 1;
+      // every MMA issued completes before the TMEM is released
+      umma::mma_commit(drain);
+      if (!umma::mbar_wait(drain, 0u, kWaitCycles)) *abort_flag = 1;
+    }
+  } else {
+    // ---- epilogue warps ----
+    const int q = warp & 3, cg = warp >> 2;
+    const int r = q * 32 + lane;  // row within the tile
+    bool stop = false;
+    for (int p = 0; p < npairs && !stop; ++p) {
+      const int nslot = (2 * p + 1 < my_tiles) ? 2 : 1;
+      for (int l = 0; l < 4 && !stop; ++l) {
+        for (int s = 0; s < nslot; ++s) {
+          if (*abort_flag) {
+            stop = true;
+            break;
+          }
+          if (!umma::mbar_wait(&accf[s], (uint32_t)(4 * p + l) & 1u, 2 * kWaitCycles)) {
+            *abort_flag = 1;
+            stop = true;
+            break;
+          }
+          umma::fence_after_sync();
+          const uint32_t trow = tmem + (uint32_t)(s * 256) + ((uint32_t)(q * 32) << 16);
+          uint8_t* h = H + (size_t)s * 4 * kSlabBytes;
+          if (l < 3) {
+            const float* b = a.bias + (l == 0 ? kOffB1 : l == 1 ? kOffB2 : kOffB3);
 #pragma unroll 1
-        for (int c0 = cg * 64; c0 < cg * 64 + 64; c0 += 16) {
-          float v[16];
-          umma::tmem_ld16(trow + (uint32_t)c0, v);
-          __align__(16) __nv_bfloat162 hv[8];
+            for (int c0 = cg * 64; c0 < cg * 64 + 64; c0 += 16) {
+              float v[16];
+              umma::tmem_ld16(trow + (uint32_t)c0, v);
+              __align__(16) __nv_bfloat162 hv[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            hv[i] = __floats2bfloat162_rn(gelu(v[2 * i] + b[c0 + 2 * i]), gelu(v[2 * i + 1] + b[c0 + 2 * i + 1]));
-          uint8_t* slab = H + (size_t)(c0 >> 6) * kBM * kBK * 2 + (size_t)r * 128;
-          const int ch = (c0 & 63) >> 3;
-          *reinterpret_cast<uint4*>(slab + (((ch) ^ (r & 7)) << 4)) = *reinterpret_cast<uint4*>(&hv[0]);
-          *reinterpret_cast<uint4*>(slab + (((ch + 1) ^ (r & 7)) << 4)) = *reinterpret_cast<uint4*>(&hv[4]);
-        }
-      } else if (cg < 2) {
-        const int c0 = cg * 16;
-        float v[16];
-        umma::tmem_ld16(trow + (uint32_t)c0, v);
-        const int row = tile * kBM + r;
-        if (row < rows) {
-          float4* dst = reinterpret_cast<float4*>(a.Y + (size_t)row * kOut + c0);
+              for (int i = 0; i < 8; ++i)
+                hv[i] = __floats2bfloat162_rn(gelu(v[2 * i] + __ldg(b + c0 + 2 * i)),
+                                              gelu(v[2 * i + 1] + __ldg(b + c0 + 2 * i + 1)));
+              uint8_t* slab = h + (size_t)(c0 >> 6) * kSlabBytes + (size_t)r * 128;
+              const int ch = (c0 & 63) >> 3;
+              *reinterpret_cast<uint4*>(slab + (((ch) ^ (r & 7)) << 4)) = *reinterpret_cast<uint4*>(&hv[0]);
+              *reinterpret_cast<uint4*>(slab + (((ch + 1) ^ (r & 7)) << 4)) = *reinterpret_cast<uint4*>(&hv[4]);
+            }
+          } else if (cg < 2) {
+            const int c0 = cg * 16;
+            float v[16];
+            umma::tmem_ld16(trow + (uint32_t)c0, v);
+            const int row = (blockIdx.x + (2 * p + s) * gridDim.x) * kBM + r;
+            if (row < rows) {
+              const float* b = a.bias + kOffB4 + c0;
+              float4* dst = reinterpret_cast<float4*>(a.Y + (size_t)row * kOut + c0);
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
-            dst[i] = make_float4(v[4 * i] + sbias[3 * kHid + c0 + 4 * i], v[4 * i + 1] + sbias[3 * kHid + c0 + 4 * i + 1],
-                                 v[4 * i + 2] + sbias[3 * kHid + c0 + 4 * i + 2],
-                                 v[4 * i + 3] + sbias[3 * kHid + c0 + 4 * i + 3]);
+              for (int i = 0; i < 4; ++i)
+                dst[i] = make_float4(v[4 * i] + __ldg(b + 4 * i), v[4 * i + 1] + __ldg(b + 4 * i + 1),
+                                     v[4 * i + 2] + __ldg(b + 4 * i + 2), v[4 * i + 3] + __ldg(b + 4 * i + 3));
+            }
+          }
+          umma::fence_proxy_async_smem();  // the activation writes feed the next MMAs (async proxy)
+          umma::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) umma::mbar_arrive(&actr[s]);
         }
-      }
-      umma::fence_proxy_async_smem();  // the activation writes feed the next MMAs (async proxy)
-      umma::fence_before_sync();
-      const bool abort = __syncthreads_or(!got || fail) != 0;
-      umma::fence_after_sync();
-      if (abort) {
-        if (threadIdx.x == 0 && a.error) atomicExch(a.error, 1);
-        it = my_tiles;  // leave both loops
-        break;
       }
     }
   }
   umma::fence_before_sync();
   __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag && a.error) atomicExch(a.error, 1);
   if (warp == 0) {
     umma::fence_after_sync();
-    umma::tmem_dealloc(tmem, 256);
+    umma::tmem_dealloc(tmem, 512);
   }
 }
 

@@ -33,11 +33,22 @@ cudaError_t mlp_forward(vrm_mlp* net, const CUtensorMap& mX, int rows_bound, con
 cudaError_t learned_features(const Consts& c, const double* x, const double* y, int n_bound, const int* n_dev,
                              float2* xyf, const int* list, const int* list_count, int m_bound, const int* nbr_count,
                              const int* nbr_idx, __nv_bfloat16* X, int* slots, cudaStream_t s);
+// Scratch of the correction rounds: per listed particle the screened
+// support, two work lists and the rounds' list sizes.
+constexpr int kProjRounds = 4;
+struct ProjScratch {
+  int cap = 0;
+  void* sel = nullptr;  // ProjSel[cap] (vrm_learned.cu)
+  int* list_s = nullptr;
+  int* list_r = nullptr;
+  int* counts = nullptr;  // [2 * kProjRounds]
+};
+cudaError_t proj_alloc(ProjScratch* p, int cap);
+void proj_free(ProjScratch* p);
 cudaError_t learned_project(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
                             int m_bound, const int* slots, const float* f0, const int* small, int* cols, double* f,
-                            double* fii,
-                            uint8_t* status, int* reject_list, int* reject_count, DevStats* ds, const double* dt_dev,
-                            double nu, cudaStream_t s);
+                            double* fii, uint8_t* status, int* reject_list, int* reject_count, DevStats* ds,
+                            const double* dt_dev, double nu, ProjScratch* ps, cudaStream_t s);
 cudaError_t learned_targets(const int* list, int m, const int* slots, const int* cols, const double* f, float* T,
                             cudaStream_t s);
 

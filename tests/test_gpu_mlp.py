@@ -54,7 +54,9 @@ def blocks(v):
     return out
 
 
-@pytest.mark.parametrize("rows", [128, 1000, 4096])
+# 40,000 and 60,000 rows: 313 and 469 tiles, so that the persistent CTAs
+# (one per SM) take two to four tiles each, whole pairs and a last single one
+@pytest.mark.parametrize("rows", [128, 1000, 4096, 40000, 60000])
 def test_forward_matches_oracle(lib, rows):
     theta = vrm_inputs.mlp_params()
     X, _ = vrm_inputs.mlp_rows(rows, seed=11)
