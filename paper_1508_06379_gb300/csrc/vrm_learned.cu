@@ -41,7 +41,6 @@ constexpr double kSnap = 1e-13;        // FP64 weights in [-kSnap, 0) are zeros
 constexpr float kScreenTol = 1e-6f;    // binary32 screen: weights >= -kScreenTol pass
 constexpr float kScreenPivot = 1e-6f;  // binary32 screen: relative pivot threshold
 constexpr int kSubsets = 56;           // 5-subsets of 8 candidate ranks
-constexpr int kMaxSolves = kProjRounds;  // FP64 solves per particle at most
 
 }  // namespace
 
@@ -60,7 +59,8 @@ __global__ void k_mirror(const double* __restrict__ x, const double* __restrict_
 // (products and sum rounded separately) and xi = dx * fp32(1/h).  The sort
 // key is one 32-bit word, segment << 28 | bits(d2) >> 3 (d2 >= 0, so its bit
 // pattern orders like the value; the 3 lowest mantissa bits are dropped),
-// with the index breaking ties: the sort runs on the integer pipes.
+// with the index breaking ties: the sort runs on the integer pipes, on one
+// 64-bit value per lane.
 __global__ void k_features(Consts c, const float2* __restrict__ xyf,
                            const int* __restrict__ list, const int* __restrict__ list_count, int m_bound,
                            const int* __restrict__ nbr_count, const int* __restrict__ nbr_idx,
@@ -85,25 +85,22 @@ __global__ void k_features(Consts c, const float2* __restrict__ xyf,
       const float d2 = dist2f(fdx, fdy);
       key = ((unsigned)segment_of(fdx, fdy) << 28) | (__float_as_uint(d2) >> 3);
     }
-    int src = lane;
+    // the row holds ascending indices, so the lane breaks ties as the index
+    // does: one distinct 64-bit value per lane, (key << 5) | lane
+    unsigned long long v = ((unsigned long long)key << 5) | (unsigned)lane;
     for (int size = 2; size <= 32; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        const unsigned ok = __shfl_xor_sync(0xffffffffu, key, stride);
-        const int oj = __shfl_xor_sync(0xffffffffu, j, stride);
-        const int os = __shfl_xor_sync(0xffffffffu, src, stride);
+        const unsigned long long ov = __shfl_xor_sync(0xffffffffu, v, stride);
         const bool up = ((lane & size) == 0);
         const bool lower = ((lane & stride) == 0);
-        const bool other_less = ok < key || (ok == key && oj < j);
-        const bool same = ok == key && oj == j;
-        const bool take = (lower == up) ? other_less : (!other_less && !same);
-        if (take) {
-          key = ok;
-          j = oj;
-          src = os;
-        }
+        // ascending runs keep the smaller value in the lower lane
+        const bool take = (lower == up) ? ov < v : ov > v;
+        v = take ? ov : v;
       }
     }
+    const int src = (int)(v & 31u);
     const bool valid = lane < K;
+    j = __shfl_sync(0xffffffffu, j, src);
     const float sdx = __shfl_sync(0xffffffffu, fdx, src);
     const float sdy = __shfl_sync(0xffffffffu, fdy, src);
     __nv_bfloat16* row = X + (size_t)t * kRow;
@@ -692,7 +689,7 @@ void proj_free(ProjScratch* p) {
 
 // Rounds of (screen, FP64 solve): round r screens the particles whose solve
 // of round r-1 failed, from their next support; a particle reaches at most
-// kProjRounds = kMaxSolves FP64 solves.  Fixed launches (graph-capturable),
+// kProjRounds = 4 FP64 solves.  Fixed launches (graph-capturable),
 // the lists and their sizes on the device.
 cudaError_t learned_project(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
                             int m_bound, const int* slots, const float* f0, const int* small, int* cols, double* f,
