@@ -88,7 +88,10 @@ __global__ void k_features(Consts c, const float2* __restrict__ xyf,
     // the row holds ascending indices, so the lane breaks ties as the index
     // does: one distinct 64-bit value per lane, (key << 5) | lane
     unsigned long long v = ((unsigned long long)key << 5) | (unsigned)lane;
-    for (int size = 2; size <= 32; size <<= 1) {
+    // a row of K <= 8 (16) entries sits in lanes 0..7 (0..15): a bitonic
+    // network of that width sorts it (lanes past it keep their empties)
+    const int width = K <= 8 ? 8 : K <= 16 ? 16 : 32;
+    for (int size = 2; size <= width; size <<= 1) {
       for (int stride = size >> 1; stride > 0; stride >>= 1) {
         const unsigned long long ov = __shfl_xor_sync(0xffffffffu, v, stride);
         const bool up = ((lane & size) == 0);
@@ -450,28 +453,37 @@ __global__ void __launch_bounds__(128) k_screen(Consts c, const double* __restri
       t = in_list ? in_list[e] : (int)e;
       start = in_list ? sel[t].next : 0;
       i = list ? list[t] : t;
-      const float* p = f0 + (size_t)t * kSlots;
-      const int* sl = slots + (size_t)t * kSlots;
+      const int* slr = slots + (size_t)t * kSlots;
+      const float* pr = f0 + (size_t)t * kSlots;
       // candidates: the slots holding a small-neighbourhood particle (at
-      // most 8, one per segment), in slot order
+      // most 8, one per segment), in slot order; the slot row read in
+      // 16-byte loads (the scalar reads below then hit the same lines)
       const int4 s0 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[0];
       const int4 s1 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[1];
       unsigned cand = 0;
 #pragma unroll
-      for (int k = 0; k < kSlots; ++k) {
-        const int j = sl[k];
-        const bool in_small = j >= 0 && (j == s0.x || j == s0.y || j == s0.z || j == s0.w || j == s1.x ||
-                                         j == s1.y || j == s1.z || j == s1.w);
-        if (in_small) cand |= 1u << k;
+      for (int k4 = 0; k4 < kSlots / 4; ++k4) {
+        const int4 a4 = reinterpret_cast<const int4*>(slr)[k4];
+        const int jv[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = jv[u];
+          const bool in_small = j >= 0 && (j == s0.x || j == s0.y || j == s0.z || j == s0.w || j == s1.x ||
+                                           j == s1.y || j == s1.z || j == s1.w);
+          if (in_small) cand |= 1u << (4 * k4 + u);
+        }
       }
       nc = __popc(cand) < kSup ? __popc(cand) : kSup;
       float cv[kSup];
-      const double xi0 = x[i], yi0 = y[i];
 #pragma unroll
       for (int s = 0; s < kSup; ++s) {
         const int kk = s < nc ? (int)__fns(cand, 0, s + 1) : 0;
-        js[s] = s < nc ? sl[kk] : -1;
-        cv[s] = s < nc ? p[kk] : 0.0f;
+        js[s] = s < nc ? slr[kk] : -1;
+        cv[s] = s < nc ? pr[kk] : 0.0f;
+      }
+      const double xi0 = x[i], yi0 = y[i];
+#pragma unroll
+      for (int s = 0; s < kSup; ++s) {
         const double xi = s < nc ? __dmul_rn(__dsub_rn(x[js[s]], xi0), c.inv_h) : 0.0;
         const double eta = s < nc ? __dmul_rn(__dsub_rn(y[js[s]], yi0), c.inv_h) : 0.0;
         xf[s] = __double2float_rn(xi);
