@@ -57,6 +57,14 @@ def lib():
         L.orc_insert.restype = ctypes.c_long
         L.orc_insert.argtypes = [P, P, ctypes.c_long, ctypes.c_long, P, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, P, P]
+        L.orc_close.restype = ctypes.c_long
+        L.orc_close.argtypes = [P, P, P, ctypes.c_long, ctypes.c_double, ctypes.c_double, P]
+        L.orc_remove_weights.restype = None
+        L.orc_remove_weights.argtypes = [P, P, ctypes.c_long, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, P, P, P]
+        L.orc_remove.restype = ctypes.c_long
+        L.orc_remove.argtypes = [P, P, P, ctypes.c_long, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P,
+                                 P, P]
         L.orc_rows.restype = ctypes.c_int
         L.orc_rows.argtypes = [ctypes.c_int]
         L.orc_stencil_width.restype = ctypes.c_int
@@ -380,3 +388,25 @@ def biot_savart(xs, ys, gamma, xt, yt, eps, block=2048):
         v[a:a + block] = (dx * k) @ g
     return u, v
 
+
+
+def remove_close(x, y, gamma, h, r=0.5, R=2.0):
+    """Particle removal (outlook of Sec. 7): returns (x', y', gamma', removed
+    flags, number of candidates, stencils dict(cols, w) [n x 4], close flags)."""
+    x, y, g = _f64(x), _f64(y), _f64(gamma)
+    n = len(x)
+    m = max(n, 1)
+    xo, yo, go = np.zeros(m), np.zeros(m), np.zeros(m)
+    removed = np.zeros(m, dtype=np.uint8)
+    cand = ctypes.c_long(0)
+    k = lib().orc_remove(_p(x), _p(y), _p(g), n, float(h), float(r), float(R), _p(xo), _p(yo), _p(go), _p(removed),
+                         ctypes.byref(cand))
+    rh, Rh = r * h, R * h
+    close = np.zeros(m, dtype=np.uint8)
+    lib().orc_close(_p(x), _p(y), _p(g), n, rh * rh, Rh, _p(close))
+    cols = np.full((m, 4), -1, dtype=np.int32)
+    w = np.zeros((m, 4))
+    rem2 = np.zeros(m, dtype=np.uint8)
+    lib().orc_remove_weights(_p(x), _p(y), n, _p(close), float(h), rh * rh, Rh * Rh, Rh, _p(rem2), _p(cols), _p(w))
+    return (xo[:k].copy(), yo[:k].copy(), go[:k].copy(), removed[:n].copy(), cand.value,
+            dict(cols=cols[:n], w=w[:n]), close[:n].copy())

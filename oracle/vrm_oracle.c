@@ -912,3 +912,183 @@ long orc_step(double* x, double* y, long n, long capacity, const double* gamma_i
   free(npiv);
   return n2;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Particle removal (the outlook of Sec. 7): a particle that has come too    */
+/* close to another is redistributed to its neighbours by an approximation  */
+/* of the identity operator, then removed.                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Key of the removal order: (|Gamma|, index); of two particles closer than
+   r h the one with the smaller key goes. */
+static int removal_key_less(const double* gamma, long a, long b) {
+  double ga = fabs(gamma[a]), gb = fabs(gamma[b]);
+  if (ga != gb) return ga < gb;
+  return a < b;
+}
+
+/*
+ * close[i] = 1 iff a particle j != i lies strictly closer than r h
+ * (dx*dx + dy*dy < lo2, the inner bound of Eq. neighbourhood) and has the
+ * larger key.  Returns the number of such candidates.
+ */
+long orc_close(const double* x, const double* y, const double* gamma, long n, double lo2, double Rh,
+               unsigned char* close) {
+  orc_grid g;
+  grid_build(&g, x, y, n, Rh);
+  long cnt = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : cnt)
+  for (long i = 0; i < n; ++i) {
+    long cx, cy;
+    grid_cell(&g, x[i], y[i], &cx, &cy);
+    unsigned char c = 0;
+    for (long by = cy - 1; by <= cy + 1 && !c; ++by) {
+      if (by < 0 || by >= g.ny) continue;
+      for (long bx = cx - 1; bx <= cx + 1 && !c; ++bx) {
+        if (bx < 0 || bx >= g.nx) continue;
+        long b = by * g.nx + bx;
+        for (long t = g.start[b]; t < g.start[b + 1]; ++t) {
+          long j = g.items[t];
+          if (j == i) continue;
+          double dx = x[j] - x[i], dy = y[j] - y[i];
+          double d2 = dx * dx + dy * dy;
+          if (d2 < lo2 && removal_key_less(gamma, i, j)) {
+            c = 1;
+            break;
+          }
+        }
+      }
+    }
+    close[i] = c;
+    cnt += c;
+  }
+  grid_free(&g);
+  return cnt;
+}
+
+/*
+ * Identity stencils of the candidates.  Columns: the closest kept particle
+ * (close[j] == 0) of every 45-degree segment of the annulus of i (ties to
+ * the smaller index), ordered by (d2, j).  Rows (0,0) (1,0) (0,1) in
+ * xi = r_ij / h with b = (1, 0, 0): sum_j g_ij = 1 and sum_j g_ij r_ij = 0,
+ * g >= 0 (the moment conditions of the identity that non-negative weights
+ * can meet: the second moments of g are positive).  The phase-I simplex of
+ * orc_phase1.  removed[i] = 1 with the nonzero weights in column order
+ * (at most 3, slots of 4, padded -1 / 0) where it is feasible; otherwise the
+ * candidate stays.
+ */
+void orc_remove_weights(const double* x, const double* y, long n, const unsigned char* close, double h, double lo2,
+                        double hi2, double Rh, unsigned char* removed, int* cols, double* w) {
+  orc_grid g;
+  grid_build(&g, x, y, n, Rh);
+  double inv_h = 1.0 / h;
+#pragma omp parallel for schedule(dynamic, 256)
+  for (long i = 0; i < n; ++i) {
+    removed[i] = 0;
+    for (int t = 0; t < 4; ++t) {
+      cols[(size_t)i * 4 + t] = -1;
+      w[(size_t)i * 4 + t] = 0.0;
+    }
+    if (!close[i]) continue;
+    long cx, cy;
+    grid_cell(&g, x[i], y[i], &cx, &cy);
+    double best_d2[8];
+    long best_j[8];
+    for (int s = 0; s < 8; ++s) {
+      best_d2[s] = INFINITY;
+      best_j[s] = -1;
+    }
+    for (long by = cy - 1; by <= cy + 1; ++by) {
+      if (by < 0 || by >= g.ny) continue;
+      for (long bx = cx - 1; bx <= cx + 1; ++bx) {
+        if (bx < 0 || bx >= g.nx) continue;
+        long b = by * g.nx + bx;
+        for (long t = g.start[b]; t < g.start[b + 1]; ++t) {
+          long j = g.items[t];
+          if (j == i || close[j]) continue;
+          double d2;
+          int s;
+          if (!annulus(x, y, i, j, lo2, hi2, 0, &d2, &s)) continue;
+          if (d2 < best_d2[s] || (d2 == best_d2[s] && j < best_j[s])) {
+            best_d2[s] = d2;
+            best_j[s] = j;
+          }
+        }
+      }
+    }
+    orc_col cl[8];
+    int K = 0;
+    for (int s = 0; s < 8; ++s) {
+      if (best_j[s] < 0) continue;
+      long j = best_j[s];
+      cl[K].j = j;
+      cl[K].dx = x[j] - x[i];
+      cl[K].dy = y[j] - y[i];
+      cl[K].d2 = cl[K].dx * cl[K].dx + cl[K].dy * cl[K].dy;
+      ++K;
+    }
+    qsort(cl, (size_t)K, sizeof(orc_col), cmp_col);
+    double V[3 * 8], b3[3] = {1.0, 0.0, 0.0}, f[8];
+    for (int k = 0; k < K; ++k) {
+      V[0 * K + k] = 1.0;
+      V[1 * K + k] = cl[k].dx * inv_h;
+      V[2 * K + k] = cl[k].dy * inv_h;
+    }
+    int np;
+    double res;
+    if (orc_phase1(3, K, V, b3, f, &np, &res) != 0) continue;
+    removed[i] = 1;
+    int t = 0;
+    for (int k = 0; k < K; ++k) {
+      if (f[k] == 0.0) continue;
+      if (t < 4) {
+        cols[(size_t)i * 4 + t] = (int)cl[k].j;
+        w[(size_t)i * 4 + t] = f[k];
+      }
+      ++t;
+    }
+  }
+  grid_free(&g);
+}
+
+/*
+ * One removal pass: candidates (orc_close), their identity stencils, then
+ * Gamma_j + sum_i g_ij Gamma_i for every kept j, the removed i taken in
+ * ascending order (products and sums rounded separately), and the kept
+ * particles compacted in index order into x_out, y_out, gamma_out.
+ * removed: n flags out.  Returns the number kept.
+ */
+long orc_remove(const double* x, const double* y, const double* gamma, long n, double h, double r, double R,
+                double* x_out, double* y_out, double* gamma_out, unsigned char* removed, long* candidates) {
+  double rh = r * h, Rh = R * h;
+  double lo2 = rh * rh, hi2 = Rh * Rh;
+  unsigned char* close = (unsigned char*)malloc((size_t)(n > 0 ? n : 1));
+  int* cols = (int*)malloc(sizeof(int) * 4 * (size_t)(n > 0 ? n : 1));
+  double* w = (double*)malloc(sizeof(double) * 4 * (size_t)(n > 0 ? n : 1));
+  double* acc = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  *candidates = orc_close(x, y, gamma, n, lo2, Rh, close);
+  orc_remove_weights(x, y, n, close, h, lo2, hi2, Rh, removed, cols, w);
+  for (long j = 0; j < n; ++j) acc[j] = gamma[j];
+  for (long i = 0; i < n; ++i) {
+    if (!removed[i]) continue;
+    for (int t = 0; t < 4; ++t) {
+      int j = cols[(size_t)i * 4 + t];
+      if (j < 0) continue;
+      double p = w[(size_t)i * 4 + t] * gamma[i];
+      acc[j] = acc[j] + p;
+    }
+  }
+  long k = 0;
+  for (long i = 0; i < n; ++i) {
+    if (removed[i]) continue;
+    x_out[k] = x[i];
+    y_out[k] = y[i];
+    gamma_out[k] = acc[i];
+    ++k;
+  }
+  free(close);
+  free(cols);
+  free(w);
+  free(acc);
+  return k;
+}
