@@ -124,6 +124,7 @@ typedef struct vrm_stats {
   int64_t lp_full_columns;       /* columns summed over the full-neighbourhood LPs */
   int64_t lp_full_column_pivots; /* columns x pivots summed over them (their algorithmic work) */
   int64_t learned_screens; /* five-slot supports screened by the learned path (binary32 solves) */
+  int64_t remove_candidates; /* vrm_remove_close: particles closer than r h to one of larger key */
 } vrm_stats;
 
 /* Stages of vrm_step, for vrm_stage_times. */
@@ -467,6 +468,34 @@ vrm_status vrm_stage_times(vrm_ctx* ctx, float* ms);
 /* Kernels launched by this library in this process so far (all contexts),
    kernels run by replays of a captured step graph included. */
 int64_t vrm_launch_count(void);
+
+/*
+ * Particle removal (the outlook of Sec. 7): where particles have come closer
+ * than r h to one another (inside the inner bound of Eq. neighbourhood),
+ * redistribute one of each such pair to its neighbours by an approximation
+ * of the identity operator and remove it.
+ *   1. Candidates: i with a particle j != i at dx*dx + dy*dy < (r h)^2 (FP64,
+ *      separately rounded) whose key (|Gamma_j|, j) is larger than i's.
+ *   2. Weights: on the closest non-candidate particle of every 45-degree
+ *      segment of i's annulus (ties to the smaller index; columns ordered by
+ *      (|r_ij|^2, j)), the phase-I simplex of vrm_solve_weights with rows
+ *      (0,0) (1,0) (0,1) in xi = r_ij / h and b = (1, 0, 0): sum_j g_ij = 1,
+ *      sum_j g_ij r_ij = 0, g_ij >= 0 (circulation and its first moments are
+ *      kept; non-negative weights cannot also keep the second moments).  A
+ *      candidate without such weights is kept.
+ *   3. gamma_out of a kept j: Gamma_j + sum_i g_ij Gamma_i over the removed i
+ *      in ascending order, products and sums rounded separately.
+ *   4. The kept particles are written to x_out, y_out, gamma_out in index
+ *      order; *n_out (host) receives their number.  Synchronises.
+ * x, y, gamma: n inputs (device, read only); the outputs hold n entries and
+ * must not overlap the inputs.  stats (host, optional): n_in, n_out,
+ * max_count, remove_candidates.
+ * Errors: VRM_ERR_ARG (null pointers, NaN/Inf input); VRM_ERR_CAPACITY if a
+ * neighbour row exceeds k_cap (outputs unspecified).
+ */
+vrm_status vrm_remove_close(vrm_ctx* ctx, const double* x, const double* y, const double* gamma, int32_t n,
+                            double* x_out, double* y_out, double* gamma_out, int32_t* n_out, vrm_stats* stats,
+                            cudaStream_t stream);
 
 /* Largest cloud vrm_build_neighbourhoods_noalloc accepts. */
 #define VRM_NOALLOC_MAX_N 65536

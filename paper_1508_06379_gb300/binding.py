@@ -42,7 +42,7 @@ class Stats(ctypes.Structure):
                 ("lp_full_pivots", ctypes.c_int64), ("learned_ok", ctypes.c_int64),
                 ("learned_rejected", ctypes.c_int64), ("learned_square", ctypes.c_int64),
                 ("lp_full_columns", ctypes.c_int64), ("lp_full_column_pivots", ctypes.c_int64),
-                ("learned_screens", ctypes.c_int64)]
+                ("learned_screens", ctypes.c_int64), ("remove_candidates", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -128,6 +128,7 @@ SIGNATURES = {
     "vrm_set_mlp": (ctypes.c_int, [P, P]),
     "vrm_rk3_step": (ctypes.c_int, [P, P, P, I32, I32, P, P, ctypes.c_double, ctypes.c_double, P, P, P, P]),
     "vrm_biot_savart": (ctypes.c_int, [P, P, P, P, I32, P, P, I32, ctypes.c_double, P, P, P]),
+    "vrm_remove_close": (ctypes.c_int, [P, P, P, P, I32, P, P, P, P, P, P]),
     "vrm_learned_features": (ctypes.c_int, [P, P, P, I32, P, I32, P, P, P, P, P]),
     "vrm_learned_project": (ctypes.c_int, [P, P, P, P, I32, P, P, P, P, P, P, P, P, P]),
     "vrm_learned_targets": (ctypes.c_int, [P, I32, P, P, P, P, P]),
@@ -335,6 +336,23 @@ class VRM:
                                    _stream())
         self._check(st, "vrm_rk3_step")
         return n_out.value, s.as_dict()
+
+    def remove_close(self, x, y, gamma, n):
+        """Particle removal (vrm_remove_close): returns (x', y', gamma', n',
+        stats) with the kept particles in index order."""
+        dev = x.device
+        xo = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+        yo = torch.empty_like(xo)
+        go = torch.empty_like(xo)
+        n_out = ctypes.c_int32(0)
+        s = Stats()
+        self._check(self.lib.vrm_remove_close(
+            self.ctx, _ptr(x, torch.float64, "x", n), _ptr(y, torch.float64, "y", n),
+            _ptr(gamma, torch.float64, "gamma", n), int(n), _ptr(xo, torch.float64, "x_out", n),
+            _ptr(yo, torch.float64, "y_out", n), _ptr(go, torch.float64, "gamma_out", n), ctypes.byref(n_out),
+            ctypes.byref(s), _stream()), "vrm_remove_close")
+        k = n_out.value
+        return xo[:k], yo[:k], go[:k], k, s.as_dict()
 
     def biot_savart(self, xs, ys, gamma, n, xt, yt, m, eps, u=None, v=None):
         """Smoothed Biot-Savart velocity at m targets from n sources (vrm_biot_savart)."""

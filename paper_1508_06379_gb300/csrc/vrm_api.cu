@@ -102,6 +102,11 @@ struct vrm_ctx {
   int bs_src_cap = 0, bs_tgt_cap = 0;
   float4 *bs_src = nullptr, *bs_tgt = nullptr;
   float* bs_g = nullptr;
+  // particle removal (vrm_remove_close)
+  int rm_cap = 0;
+  uint8_t *rm_close = nullptr, *rm_removed = nullptr, *rm_keep = nullptr;
+  int *rm_clist = nullptr, *rm_klist = nullptr, *rm_cols4 = nullptr;
+  double *rm_w4 = nullptr, *rm_gnew = nullptr;
 };
 
 // What a batch graph was captured for: per cloud the buffers, capacity and
@@ -240,6 +245,40 @@ void free_bs(vrm_ctx* ctx) {
   ctx->bs_src = ctx->bs_tgt = nullptr;
   ctx->bs_g = nullptr;
   ctx->bs_src_cap = ctx->bs_tgt_cap = 0;
+}
+
+void free_rm(vrm_ctx* ctx) {
+  void* ptrs[] = {ctx->rm_close, ctx->rm_removed, ctx->rm_keep, ctx->rm_clist, ctx->rm_klist, ctx->rm_cols4,
+                  ctx->rm_w4, ctx->rm_gnew};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  ctx->rm_close = ctx->rm_removed = ctx->rm_keep = nullptr;
+  ctx->rm_clist = ctx->rm_klist = ctx->rm_cols4 = nullptr;
+  ctx->rm_w4 = ctx->rm_gnew = nullptr;
+  ctx->rm_cap = 0;
+}
+
+// Buffers of the removal pass for n particles (grown, never shrunk).
+cudaError_t ensure_rm(vrm_ctx* ctx, int n, cudaStream_t st) {
+  if (n <= ctx->rm_cap && ctx->rm_close) return cudaSuccess;
+  cudaStreamSynchronize(st);
+  free_rm(ctx);
+  const size_t m = (size_t)(n < 1024 ? 1024 : n);
+  cudaError_t e = cudaMalloc(&ctx->rm_close, m);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->rm_removed, m);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->rm_keep, m);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->rm_clist, sizeof(int) * m);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->rm_klist, sizeof(int) * m);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->rm_cols4, sizeof(int) * 4 * m);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->rm_w4, sizeof(double) * 4 * m);
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->rm_gnew, sizeof(double) * m);
+  if (e != cudaSuccess) {
+    free_rm(ctx);
+    cudaGetLastError();
+    return e;
+  }
+  ctx->rm_cap = (int)m;
+  return cudaSuccess;
 }
 
 cudaError_t ensure_bs(vrm_ctx* ctx, int n, int m, cudaStream_t st) {
@@ -780,11 +819,54 @@ void vrm_destroy(vrm_ctx* ctx) {
   free_learned(ctx->L);
   free_rk(ctx);
   free_bs(ctx);
+  free_rm(ctx);
   if (ctx->events_ready)
     for (int k = 0; k <= VRM_STAGE_COUNT; ++k) cudaEventDestroy(ctx->ev[k]);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
   delete ctx;
+}
+
+vrm_status vrm_remove_close(vrm_ctx* ctx, const double* x, const double* y, const double* gamma, int32_t n,
+                            double* x_out, double* y_out, double* gamma_out, int32_t* n_out, vrm_stats* stats,
+                            cudaStream_t stream) {
+  if (!ctx || n < 0 || !n_out) return VRM_ERR_ARG;
+  *n_out = 0;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  if (bad_ptr(x, n) || bad_ptr(y, n) || bad_ptr(gamma, n) || bad_ptr(x_out, n) || bad_ptr(y_out, n) ||
+      bad_ptr(gamma_out, n))
+    return VRM_ERR_ARG;
+  if (n == 0) return VRM_OK;
+  Scratch& s = ctx->s;
+  const Consts c = full_rows(ctx->c);
+  VRM_CUDA(ensure_scratch(ctx, n, stream));
+  VRM_CUDA(ensure_rm(ctx, n, stream));
+  VRM_CUDA(cudaMemsetAsync(s.ds, 0, sizeof(DevStats), stream));
+  VRM_CUDA(grid_build(x, y, n, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank, s.cell_count,
+                      s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp, stream));
+  VRM_CUDA(search_all(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, n, s.nbr_count, s.nbr_idx,
+                      s.seg_mask, s.small, s.ds, stream));
+  VRM_CUDA(remove_close_flags(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, n, gamma,
+                              ctx->rm_close, stream));
+  VRM_CUDA(compact_flags(ctx->rm_close, n, ctx->rm_clist, s.counters + 3, s.pos, s.scan_tmp, stream));
+  VRM_CUDA(cudaMemsetAsync(ctx->rm_removed, 0, (size_t)n, stream));
+  VRM_CUDA(lp_identity(c, x, y, ctx->rm_clist, s.counters + 3, n, s.nbr_count, s.nbr_idx, ctx->rm_close,
+                       ctx->rm_removed, ctx->rm_cols4, ctx->rm_w4, stream));
+  VRM_CUDA(remove_gather(c, n, gamma, ctx->rm_removed, s.nbr_count, s.nbr_idx, ctx->rm_cols4, ctx->rm_w4,
+                         ctx->rm_gnew, ctx->rm_keep, s.ds, stream));
+  VRM_CUDA(compact_flags(ctx->rm_keep, n, ctx->rm_klist, s.counters + 4, s.pos, s.scan_tmp, stream));
+  VRM_CUDA(remove_out(n, s.counters + 4, ctx->rm_klist, x, y, ctx->rm_gnew, x_out, y_out, gamma_out, stream));
+  VRM_CUDA(read_back(ctx, stream));
+  if (s.h_grid->nonfinite || s.h_ds->nonfinite) return VRM_ERR_ARG;
+  if (stats) {
+    stats->n_in = n;
+    stats->n_out = s.h_counters[4];
+    stats->max_count = s.h_ds->max_count;
+    stats->remove_candidates = s.h_counters[3];
+  }
+  if (s.h_ds->max_count > ctx->p.k_cap) return VRM_ERR_CAPACITY;
+  *n_out = s.h_counters[4];
+  return VRM_OK;
 }
 
 vrm_status vrm_set_timing(vrm_ctx* ctx, int32_t enable) {

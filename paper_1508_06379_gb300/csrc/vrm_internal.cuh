@@ -296,6 +296,11 @@ cudaError_t lp_full(const Consts& c, const double* x, const double* y, const int
                     int cap, const int* nbr_count, const int* nbr_idx, int* cols, double* f, double* fii,
                     uint8_t* status, DevStats* ds, double nu_dt, cudaStream_t s, const double* dt_dev = nullptr,
                     double nu = 0.0);
+// Identity weights of the removal candidates (list, *list_count on the
+// device): removed[i], cols4/w4 [n x 4] (vrm_remove.cu drives it).
+cudaError_t lp_identity(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
+                        int cap, const int* nbr_count, const int* nbr_idx, const uint8_t* close, uint8_t* removed,
+                        int* cols4, double* w4, cudaStream_t s);
 cudaError_t lp_clear(int n, int w, const uint8_t* diffused, int* cols, double* f, double* fii, uint8_t* status,
                      cudaStream_t s);
 
@@ -307,6 +312,16 @@ cudaError_t apply_gather_dev(const Consts& c, int n_bound, const int* n_dev, int
                              const double* gamma, const uint8_t* diffused, const int* nbr_count, const int* nbr_idx,
                              const int* cols, const double* f, const double* fii, const int* order, double* dgamma,
                              double* gamma_out, double dt, const double* dt_dev, cudaStream_t s);
+
+// vrm_remove.cu: particle removal (candidates, gather, compaction).
+cudaError_t remove_close_flags(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
+                               const float2* sorted_loc, const int* sorted_idx, int n, const double* gamma,
+                               uint8_t* close, cudaStream_t s);
+cudaError_t remove_gather(const Consts& c, int n, const double* gamma, const uint8_t* removed, const int* nbr_count,
+                          const int* nbr_idx, const int* cols4, const double* w4, double* gnew, uint8_t* keep,
+                          DevStats* ds, cudaStream_t s);
+cudaError_t remove_out(int n, const int* n_keep, const int* klist, const double* x, const double* y,
+                       const double* gnew, double* x_out, double* y_out, double* g_out, cudaStream_t s);
 
 // vrm_rk3.cu
 // One stage update of the SSP-RK3 step (positions by the velocity, circulations

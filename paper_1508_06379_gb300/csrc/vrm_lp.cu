@@ -128,6 +128,14 @@ __device__ __forceinline__ void vcol(double xi, double eta, double* v) {
 
 __device__ __forceinline__ double b_of(int r) { return (r == 2 || r == 4) ? 2.0 : 0.0; }
 
+// The identity's rows of the removal LP: (0,0) (1,0) (0,1), b = (1, 0, 0).
+__device__ __forceinline__ void vcol_id(double xi, double eta, double* v) {
+  v[0] = 1.0;
+  v[1] = xi;
+  v[2] = eta;
+}
+__device__ __forceinline__ double b_id(int r) { return r == 0 ? 1.0 : 0.0; }
+
 
 // Basic solution of the final basis, by the same LU sequence as the oracle's
 // basis solves (partial pivoting on the first largest |pivot|, full row
@@ -135,13 +143,16 @@ __device__ __forceinline__ double b_of(int r) { return (r == 2 || r == 4) ? 2.0 
 // separately), so that equal bases give bit-identical weights.  Column k of
 // B is the unit vector e_v for an artificial v = basis[k] < m, else the
 // Vandermonde column of (bxi[k], beta[k]).  Returns false if B is singular.
-template <int M>
+template <int M, bool ID = false>
 __device__ __forceinline__ bool basis_solve(const int* basis, const double* bxi, const double* beta, double* z) {
   double A[M][M];
 #pragma unroll
   for (int k = 0; k < M; ++k) {
     double v[M];
-    vcol<M>(bxi[k], beta[k], v);
+    if constexpr (ID)
+      vcol_id(bxi[k], beta[k], v);
+    else
+      vcol<M>(bxi[k], beta[k], v);
 #pragma unroll
     for (int r = 0; r < M; ++r) A[r][k] = basis[k] < M ? (basis[k] == r ? 1.0 : 0.0) : v[r];
   }
@@ -177,7 +188,7 @@ __device__ __forceinline__ bool basis_solve(const int* basis, const double* bxi,
     }
   }
 #pragma unroll
-  for (int r = 0; r < M; ++r) z[r] = b_of(r);
+  for (int r = 0; r < M; ++r) z[r] = ID ? b_id(r) : b_of(r);
 #pragma unroll
   for (int k = 0; k < M; ++k)
 #pragma unroll
@@ -757,6 +768,227 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
   }
 }
 
+// Identity weights of the removal candidates (particle removal, the outlook
+// of Sec. 7): the phase-I simplex of k_lp_small with rows (0,0) (1,0) (0,1)
+// of r_ij / h and b = (1, 0, 0), i.e. sum g = 1 and sum g r = 0 with g >= 0,
+// on the closest kept particle (close[j] == 0) of every 45-degree segment of
+// the candidate's annulus row (ties to the smaller index), columns ordered by
+// (d2, j).  The same entering, leaving, snapping and feasibility rules; the
+// final basis solved by the oracle's LU sequence.  One candidate per thread.
+// removed[i] = 1 and the nonzero weights (at most 3 of the 4 slots, column
+// order, padded -1 / 0) where feasible; otherwise the candidate stays.
+__global__ void __launch_bounds__(128) k_lp_identity(Consts c, const double* __restrict__ x,
+                                                     const double* __restrict__ y, const int* __restrict__ list,
+                                                     const int* __restrict__ list_count,
+                                                     const int* __restrict__ nbr_count,
+                                                     const int* __restrict__ nbr_idx,
+                                                     const uint8_t* __restrict__ close, uint8_t* __restrict__ removed,
+                                                     int* __restrict__ cols4, double* __restrict__ w4) {
+  constexpr int M = 3;
+  const int m = *list_count;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) {
+    const int i = list[t];
+    const double xi0 = x[i], yi0 = y[i];
+    const int cnt0 = nbr_count[i];
+    const int K = cnt0 < c.row_cap ? cnt0 : c.row_cap;
+    const int* row = nbr_idx + (size_t)i * c.k_cap;
+    // closest kept member of every segment
+    double cd2[8], cxi[8], ceta[8];
+    int cj[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      cd2[s] = 1e300;
+      cj[s] = INT_MAX;
+      cxi[s] = ceta[s] = 0.0;
+    }
+    for (int e = 0; e < K; ++e) {
+      const int j = row[e];
+      if (close[j]) continue;
+      const double dx = __dsub_rn(x[j], xi0), dy = __dsub_rn(y[j], yi0);
+      const double d2 = dist2(dx, dy);
+      const int sg = segment_of(dx, dy);
+      double cb = cd2[0];
+      int cjb = cj[0];
+#pragma unroll
+      for (int s = 1; s < 8; ++s) {
+        cb = (sg == s) ? cd2[s] : cb;
+        cjb = (sg == s) ? cj[s] : cjb;
+      }
+      const bool take = lt_nonneg(d2, cb) || (dbits(d2) == dbits(cb) && j < cjb);
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const bool here = take && sg == s;
+        cd2[s] = here ? d2 : cd2[s];
+        cj[s] = here ? j : cj[s];
+        cxi[s] = here ? dx : cxi[s];
+        ceta[s] = here ? dy : ceta[s];
+      }
+    }
+    sort8(cd2, cj, cxi, ceta);
+    unsigned basic = 0;  // empty columns never enter
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (cj[k] == INT_MAX) basic |= 1u << k;
+      cxi[k] = __dmul_rn(cxi[k], c.inv_h);
+      ceta[k] = __dmul_rn(ceta[k], c.inv_h);
+    }
+    double T[M][8], rhs[M], d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      double v[M];
+      vcol_id(cxi[k], ceta[k], v);
+      double s = 0.0;
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        T[r][k] = v[r];
+        s = __dadd_rn(s, v[r]);
+      }
+      d[k] = dneg(s);
+    }
+#pragma unroll
+    for (int r = 0; r < M; ++r) rhs[r] = b_id(r);
+    int basis[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) basis[r] = r;
+    int it = 0, code = 0, n_art = M;
+    for (;;) {
+      if (n_art == 0) break;  // phase I over
+      int q = -1;
+#pragma unroll
+      for (int k = 7; k >= 0; --k)
+        if (!((basic >> k) & 1u) && lt_neg(d[k], kTolPrice)) q = k;
+      if (q < 0) break;
+      if (it == kPivotCap) {
+        code = 2;
+        break;
+      }
+      double a[M];
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        double v = T[r][0];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) v = (q == k) ? T[r][k] : v;
+        a[r] = v;
+      }
+      double ratio[M], theta = 1e308;
+      bool elig[M], any = false;
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        elig[r] = gt_pos(a[r], kTolPivot);
+        const double num = gt_pos(rhs[r], kTolSnap) ? rhs[r] : 0.0;
+        ratio[r] = elig[r] ? __dmul_rn(num, rcp_newton<1>(a[r])) : 1e308;
+        if (elig[r]) {
+          any = true;
+          theta = lt_nonneg(ratio[r], theta) ? ratio[r] : theta;
+        }
+      }
+      if (!any) {
+        code = 2;
+        break;
+      }
+      const double lim = __fma_rn(kTolTie, gt_pos(theta, 1.0) ? theta : 1.0, theta);
+      int leave = -1, lbas = INT_MAX;
+#pragma unroll
+      for (int r = 0; r < M; ++r)
+        if (elig[r] && !lt_nonneg(lim, ratio[r]) && basis[r] < lbas) {
+          leave = r;
+          lbas = basis[r];
+        }
+      double piv = a[0], prhs_raw = rhs[0];
+#pragma unroll
+      for (int r = 1; r < M; ++r) {
+        piv = (leave == r) ? a[r] : piv;
+        prhs_raw = (leave == r) ? rhs[r] : prhs_raw;
+      }
+      const double rcp = rcp_newton<2>(piv);
+      double prow[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        double v = T[0][k];
+#pragma unroll
+        for (int r = 1; r < M; ++r) v = (leave == r) ? T[r][k] : v;
+        prow[k] = (k == q) ? 1.0 : __dmul_rn(v, rcp);
+      }
+      const double prhs = __dmul_rn(prhs_raw, rcp);
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        const bool lr = (leave == r);
+        const double ar = lr ? -1.0 : a[r];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) T[r][k] = __fma_rn(-ar, prow[k], lr ? 0.0 : T[r][k]);
+        rhs[r] = __fma_rn(-ar, prhs, lr ? 0.0 : rhs[r]);
+      }
+      double dq = d[0];
+#pragma unroll
+      for (int k = 1; k < 8; ++k) dq = (q == k) ? d[k] : dq;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) d[k] = __fma_rn(-dq, prow[k], d[k]);
+      if (lbas >= M) basic &= ~(1u << (lbas - M));
+      else --n_art;
+      basic |= 1u << q;
+#pragma unroll
+      for (int r = 0; r < M; ++r) basis[r] = (leave == r) ? M + q : basis[r];
+      ++it;
+    }
+    double fv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fv[k] = 0.0;
+    double wsum = 0.0, rmax = 0.0;
+    if (code == 0) {
+      double bxi[M], beta[M], xB[M];
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        double av = 0.0, ev = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          av = (basis[r] == M + k) ? cxi[k] : av;
+          ev = (basis[r] == M + k) ? ceta[k] : ev;
+        }
+        bxi[r] = av;
+        beta[r] = ev;
+      }
+      if (!basis_solve<M, true>(basis, bxi, beta, xB)) code = 2;
+      double acc[M];
+#pragma unroll
+      for (int r = 0; r < M; ++r) acc[r] = dneg(b_id(r));
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        if (basis[r] < M) {
+          wsum = __dadd_rn(wsum, xB[r]);
+        } else {
+          const double v = gt_pos(xB[r], kTolSnap) ? xB[r] : 0.0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == M + k) ? v : fv[k];
+          double col[M];
+          vcol_id(bxi[r], beta[r], col);
+#pragma unroll
+          for (int qq = 0; qq < M; ++qq) acc[qq] = __fma_rn(col[qq], v, acc[qq]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < M; ++r) rmax = abs_gt(acc[r], rmax) ? fabs(acc[r]) : rmax;
+    }
+    const bool feasible = code == 0 && !gt_pos(wsum, kTolPhase1) && !gt_pos(rmax, kTolResid);
+    int* crow = cols4 + (size_t)i * 4;
+    double* wrow = w4 + (size_t)i * 4;
+    int slot = 0;
+    if (feasible) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (dbits(fv[k]) != 0 && slot < 4) {
+          crow[slot] = cj[k];
+          wrow[slot] = fv[k];
+          ++slot;
+        }
+    }
+    for (; slot < 4; ++slot) {
+      crow[slot] = -1;
+      wrow[slot] = 0.0;
+    }
+    removed[i] = feasible ? 1 : 0;
+  }
+}
+
 __global__ void k_lp_clear(int n, int w, const uint8_t* __restrict__ diffused, int* __restrict__ cols,
                            double* __restrict__ f, double* __restrict__ fii, uint8_t* __restrict__ status) {
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -810,6 +1042,17 @@ cudaError_t lp_clear(int n, int w, const uint8_t* diffused, int* cols, double* f
   int blocks = (n + kBlock - 1) / kBlock;
   if (blocks > 8 * sm_count()) blocks = 8 * sm_count();
   k_lp_clear<<<blocks, kBlock, 0, s>>>(n, w, diffused, cols, f, fii, status); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t lp_identity(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
+                        int cap, const int* nbr_count, const int* nbr_idx, const uint8_t* close, uint8_t* removed,
+                        int* cols4, double* w4, cudaStream_t s) {
+  if (cap <= 0) return cudaSuccess;
+  int blocks = (cap + 127) / 128;
+  if (blocks > 16 * sm_count()) blocks = 16 * sm_count();
+  k_lp_identity<<<blocks, 128, 0, s>>>(c, x, y, list, list_count, nbr_count, nbr_idx, close, removed, cols4, w4);
+  note_launch();
   return cudaGetLastError();
 }
 
