@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mixture_1m",
                     choices=["mixture_1m", "mixture_1m_n2", "lamb_oseen_h002", "batched_64", "learned_4m",
-                             "viscous_16m"])
+                             "viscous_16m", "removal_1m"])
     ap.add_argument("--learned", action="store_true",
                     help="viscous workload: stencils from a trained proposal network (LP fallback)")
     ap.add_argument("--viscous-h", type=float, default=7 * 2.0 ** -16,
@@ -890,6 +890,84 @@ def run_viscous(args):
     sys.stdout.flush()
 
 
+REMOVAL_DESC = ("particle removal pass (vrm_remove_close) on the jittered lattice 1001x1001, h=2e-3, jitter 0.3h, "
+                "8-Gaussian mixture, plus 10%% extra particles within 0.3h of existing ones carrying a U(-1,1) "
+                "fraction of their circulation: %d particles in")
+
+
+def removal_workload():
+    import numpy as np
+    import vrm_inputs
+    h = 2e-3
+    x, y, g = vrm_inputs.gaussian_mixture_cloud(h=h, jitter=0.3, seed=vrm_inputs.SEED_BASE + 2)
+    rng = np.random.default_rng(vrm_inputs.SEED_BASE + 6)
+    m = len(x) // 10
+    k = rng.choice(len(x), m, replace=False)
+    x = np.concatenate([x, x[k] + rng.uniform(-0.3, 0.3, m) * h])
+    y = np.concatenate([y, y[k] + rng.uniform(-0.3, 0.3, m) * h])
+    g = np.concatenate([g, g[k] * rng.uniform(-1, 1, m)])
+    return x, y, g, h
+
+
+def run_removal(args):
+    """Particle removal (outlook of Sec. 7) on a crowded 1.1M cloud: input
+    particles per second of whole passes, and the oracle's pass on the host
+    cores for context."""
+    import torch
+
+    import paper_1508_06379_gb300 as vrm
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    vrm.build()
+    dev = torch.device("cuda", local)
+    x, y, g, h = removal_workload()
+    n = len(x)
+    xd, yd, gd = (torch.from_numpy(a).to(dev) for a in (x, y, g))
+    ctx = vrm.VRM(h=h, nu=1e-3)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ctx.remove_close(xd, yd, gd, n)
+    torch.cuda.synchronize()
+    clocks = Clocks(None)
+    time.sleep(0.3)
+    t_wall0 = time.time()
+    launches0 = vrm.launch_count()
+    ms, st, k = 0.0, None, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, _, k, st = ctx.remove_close(xd, yd, gd, n)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    t_wall1 = time.time()
+    launches = vrm.launch_count() - launches0
+    ck = clocks.stop(t_wall0, t_wall1)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        t0 = time.time()
+        xo, _, _, _, _, _, _ = oracle.remove_close(x, y, g, h)
+        tc = time.time() - t0
+        cpu = {"value": n / tc, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "one oracle removal pass on the whole workload (%d in, %d kept), %.2f s" % (n, len(xo), tc)}
+    line = {
+        "metric": "particles/s per particle-removal pass on 1 GB300", "value": n * args.steps / (ms * 1e-3),
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": REMOVAL_DESC % n, "n": n, "n_kept": int(k), "candidates": int(st["remove_candidates"]),
+                   "h": h, "l2": "flushed between passes (512 MB write)", "parallelism": "1 GPU"},
+        "gpu_launches": int(launches), "clocks": ck, "roofline": None, "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    sys.stdout.flush()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -900,6 +978,8 @@ def main():
         run_learned(args)
     elif args.workload == "viscous_16m":
         run_viscous(args)
+    elif args.workload == "removal_1m":
+        run_removal(args)
     else:
         run_ours(args)
 
