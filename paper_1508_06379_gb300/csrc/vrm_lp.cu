@@ -81,6 +81,15 @@ __device__ __forceinline__ double rcp_newton(double a) {
   return r;
 }
 
+// Binary32 value of a double in the binary32 normal range, from the bit
+// pattern (mantissa rounded to 23 bits, exponent rebiased; integer ops only).
+__device__ __forceinline__ float f32_of(double a) {
+  const unsigned long long b = (unsigned long long)dbits(a);
+  const unsigned long long mr = ((b & 0x7FFFFFFFFFFFFFFFULL) + 0x10000000ULL) >> 29;
+  const int e32 = (int)((mr >> 23) & 0x7FF) - 1023 + 127;
+  return __int_as_float((int)((b >> 32) & 0x80000000u) | (e32 << 23) | (int)(mr & 0x7FFFFF));
+}
+
 __device__ __forceinline__ void cswap(double* d2, int* j, double* a, double* b, int p, int q) {
   const unsigned long long bq = (unsigned long long)dbits(d2[q]), bp = (unsigned long long)dbits(d2[p]);
   bool sw = (bq < bp) || (bq == bp && j[q] < j[p]);
@@ -326,29 +335,54 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
           for (int k = 1; k < 8; ++k) v = (q == k) ? T[r][k] : v;
           a[r] = v;
         }
-        // ratio test: basic values <= kTolSnap are zeros; ratios by a
-        // Newton reciprocal (relative error ~2^-45, far inside the tie window)
-        double ratio[M], theta = 1e308;
+        // ratio test: basic values <= kTolSnap are zeros.  The ratios are
+        // screened in binary32 (operands rounded from their bit patterns:
+        // relative error < 1e-6, no FP64 instruction); the rows within 1e-5
+        // of the smallest binary32 ratio are the only ones that can lie in
+        // the FP64 tie window (1e-12), so the leaving row is decided without
+        // FP64 unless two of them differ and are not exact zeros, and then
+        // in FP64 (Newton reciprocal, relative error ~2^-45) on those rows
         bool elig[M], any = false;
+        float r32[M], m32 = 3.0e38f;
 #pragma unroll
         for (int r = 0; r < M; ++r) {
           elig[r] = gt_pos(a[r], kTolPivot);
-          const double num = gt_pos(rhs[r], kTolSnap) ? rhs[r] : 0.0;
-          ratio[r] = elig[r] ? __dmul_rn(num, rcp_newton<1>(a[r])) : 1e308;
-          if (elig[r]) {
-            any = true;
-            theta = lt_nonneg(ratio[r], theta) ? ratio[r] : theta;
-          }
+          const bool nz = gt_pos(rhs[r], kTolSnap);
+          r32[r] = !elig[r] ? 3.0e38f : nz ? __fmul_rn(f32_of(rhs[r]), __frcp_rn(f32_of(a[r]))) : 0.0f;
+          any = any || elig[r];
+          m32 = fminf(m32, r32[r]);
         }
         if (!any) {
           code = 2;
           break;
         }
-        const double lim = __fma_rn(kTolTie, gt_pos(theta, 1.0) ? theta : 1.0, theta);
+        const float marg = __fmaf_rn(1e-5f, fmaxf(m32, 1.0f), m32);
+        unsigned cont = 0;
+        bool allzero = true;
+#pragma unroll
+        for (int r = 0; r < M; ++r)
+          if (elig[r] && r32[r] <= marg) {
+            cont |= 1u << r;
+            allzero = allzero && r32[r] == 0.0f;
+          }
+        if (__popc(cont) > 1 && !allzero) {
+          double ratio[M], theta = 1e308;
+#pragma unroll
+          for (int r = 0; r < M; ++r) {
+            const double num = gt_pos(rhs[r], kTolSnap) ? rhs[r] : 0.0;
+            ratio[r] = ((cont >> r) & 1u) ? __dmul_rn(num, rcp_newton<1>(a[r])) : 1e308;
+            theta = lt_nonneg(ratio[r], theta) ? ratio[r] : theta;
+          }
+          const double lim = __fma_rn(kTolTie, gt_pos(theta, 1.0) ? theta : 1.0, theta);
+#pragma unroll
+          for (int r = 0; r < M; ++r)
+            if (((cont >> r) & 1u) && lt_nonneg(lim, ratio[r])) cont &= ~(1u << r);
+        }
+        // the tied rows: the one with the lowest basic variable leaves
         int leave = -1, lbas = INT_MAX;
 #pragma unroll
         for (int r = 0; r < M; ++r)
-          if (elig[r] && !lt_nonneg(lim, ratio[r]) && basis[r] < lbas) {
+          if (((cont >> r) & 1u) && basis[r] < lbas) {
             leave = r;
             lbas = basis[r];
           }
