@@ -1,10 +1,13 @@
 """Training of the weight-proposal network on LP solutions (the learned path).
 
-Data: jittered lattices (jitter amplitude per cloud uniform in [0.1h, 0.4h]);
-for every particle the library builds the neighbourhood, solves the
-small-neighbourhood LP (vrm_solve_weights, every particle marked diffused)
-and, where the LP succeeded, stores the input row (vrm_learned_features) and
-the LP weights at the slots (vrm_learned_targets).  Training: vrm_mlp_train_step
+Data: jittered lattices (jitter amplitude per cloud uniform in [0.1h, 0.4h])
+put through the step's own insertion (vrm_insert_reduce with every particle
+diffusing), so that the neighbourhoods hold the zero-strength particles the
+step inserts at 1.5h, as they do when the network is used; for every
+original particle the library builds the neighbourhood of the cloud after
+insertion, solves the small-neighbourhood LP (vrm_solve_weights) and, where
+it succeeded, stores the input row (vrm_learned_features) and the LP
+weights at the slots (vrm_learned_targets).  Training: vrm_mlp_train_step
 (tensor-core forward/backward, AdamW) over shuffled batches with a cosine
 learning-rate decay.  Everything runs on the GPU through the C ABI; torch
 only holds the buffers and draws the batch permutations.
@@ -29,14 +32,24 @@ def cloud(side, h, jitter, seed):
     return x, y
 
 
-def lp_samples(x, y, h, nu=1e-3, device="cuda"):
-    """(X rows, targets) of every particle of the cloud whose small LP succeeded."""
-    n = len(x)
+def lp_samples(x, y, h, nu=1e-3, device="cuda", insert=True):
+    """(X rows, targets) of every original particle of the cloud whose small
+    LP succeeded, on the cloud after the step's insertion (insert=True) or
+    on the cloud as given."""
+    n0 = len(x)
     ctx = B.VRM(h=h, nu=nu)
-    xd = torch.from_numpy(np.ascontiguousarray(x)).to(device)
-    yd = torch.from_numpy(np.ascontiguousarray(y)).to(device)
+    cap = 2 * n0 + 1024 if insert else n0
+    xb = torch.zeros(cap, dtype=torch.float64, device=device)
+    yb = torch.zeros(cap, dtype=torch.float64, device=device)
+    xb[:n0] = torch.from_numpy(np.ascontiguousarray(x)).to(device)
+    yb[:n0] = torch.from_numpy(np.ascontiguousarray(y)).to(device)
+    n = n0
+    if insert:
+        n, _, _ = ctx.insert_reduce(xb, yb, n0, torch.ones(n0, dtype=torch.float64, device=device))
+    xd, yd = xb[:n].contiguous(), yb[:n].contiguous()
     nb = ctx.build_neighbourhoods(xd, yd, n)
-    diffused = torch.ones(n, dtype=torch.uint8, device=device)
+    diffused = torch.zeros(n, dtype=torch.uint8, device=device)
+    diffused[:n0] = 1
     w = ctx.solve_weights(xd, yd, n, diffused, nb)
     ok = torch.nonzero(w["status"][:n] == B.LP_SMALL).flatten().to(torch.int32)
     m = int(ok.numel())
