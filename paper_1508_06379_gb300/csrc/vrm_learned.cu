@@ -41,6 +41,7 @@ constexpr double kSnap = 1e-13;        // FP64 weights in [-kSnap, 0) are zeros
 constexpr float kScreenTol = 1e-6f;    // binary32 screen: weights >= -kScreenTol pass
 constexpr float kScreenPivot = 1e-6f;  // binary32 screen: relative pivot threshold
 constexpr int kSubsets = 56;           // 5-subsets of 8 candidate ranks
+constexpr int kMaxSolves = 4;          // FP64 solves per particle at most
 
 }  // namespace
 
@@ -383,9 +384,9 @@ __device__ __forceinline__ bool screen32(const float* xs, const float* es) {
 // first support tried (stats).
 struct ProjSel {
   int j[5];
-  int next;
-  int first;
-  int pad;
+  int next;    // the next support to screen
+  int first;   // the support is the first one tried (stats)
+  int solves;  // FP64 solves made so far
 };
 
 // Appends v to list (warp-aggregated; the whole warp calls it converged).
@@ -428,8 +429,10 @@ __global__ void __launch_bounds__(128) k_screen(Consts c, const double* __restri
                                                 int m_bound, const int* __restrict__ in_list,
                                                 const int* __restrict__ in_count, const int* __restrict__ slots,
                                                 const float* __restrict__ f0, const int* __restrict__ small,
-                                                ProjSel* __restrict__ sel, int* __restrict__ solve_list,
-                                                int* __restrict__ solve_count, int* __restrict__ cols,
+                                                ProjSel* __restrict__ sel, int budget,
+                                                int* __restrict__ solve_list, int* __restrict__ solve_count,
+                                                int* __restrict__ pend_list, int* __restrict__ pend_count,
+                                                int* __restrict__ cols,
                                                 double* __restrict__ f, double* __restrict__ fii,
                                                 uint8_t* __restrict__ status, int* __restrict__ reject_list,
                                                 int* __restrict__ reject_count, DevStats* __restrict__ ds) {
@@ -440,7 +443,7 @@ __global__ void __launch_bounds__(128) k_screen(Consts c, const double* __restri
   for (long base = (long)blockIdx.x * blockDim.x; base < m; base += stride) {
     const long e = base + threadIdx.x;
     const bool active = e < m;
-    int t = 0, i = -1, nc = 0, start = 0;
+    int t = 0, i = -1, nc = 0, start = 0, solves = 0;
     int js[kSup], rank[kSup];
     float xf[kSup], ef[kSup];
 #pragma unroll
@@ -452,6 +455,7 @@ __global__ void __launch_bounds__(128) k_screen(Consts c, const double* __restri
     if (active) {
       t = in_list ? in_list[e] : (int)e;
       start = in_list ? sel[t].next : 0;
+      solves = in_list ? sel[t].solves : 0;
       i = list ? list[t] : t;
       const int* slr = slots + (size_t)t * kSlots;
       const float* pr = f0 + (size_t)t * kSlots;
@@ -498,12 +502,17 @@ __global__ void __launch_bounds__(128) k_screen(Consts c, const double* __restri
         rank[s] = s < nc ? r : kSup;
       }
     }
-    bool done = !active || nc < 5, have = false;
+    bool done = !active || nc < 5, have = false, pend = false;
     unsigned pm = 0;
     int trials = 0, u_pass = 0;
     for (int u = 0; u < kSubsets; ++u) {
       if (__all_sync(0xffffffffu, done)) break;
       if (done || u < start || kOrder.top[u] >= nc) continue;
+      if (trials == budget) {  // this round's screens are spent: go on next round from u
+        done = pend = true;
+        u_pass = u - 1;
+        continue;
+      }
       ++trials;
       const unsigned rm = kOrder.mask[u];
       unsigned um = 0;  // the support as positions (slot order)
@@ -528,7 +537,7 @@ __global__ void __launch_bounds__(128) k_screen(Consts c, const double* __restri
         u_pass = u;
       }
     }
-    if (have) {
+    if (have || pend) {
       ProjSel o;
 #pragma unroll
       for (int q = 0; q < 5; ++q) {
@@ -539,14 +548,15 @@ __global__ void __launch_bounds__(128) k_screen(Consts c, const double* __restri
         o.j[q] = jj;
       }
       o.next = u_pass + 1;
-      o.first = !in_list && trials == 1;
-      o.pad = 0;
+      o.first = have && !in_list && trials == 1;
+      o.solves = solves;
       sel[t] = o;
     }
     n_trials += trials;
-    const bool rej = active && !have;
+    const bool rej = active && !have && !pend;
     n_rej += rej;
     warp_append(have, t, solve_list, solve_count);
+    warp_append(pend, t, pend_list, pend_count);
     reject_particle(rej, i, cols, f, fii, status, reject_list, reject_count);
   }
   n_rej = __reduce_add_sync(0xffffffffu, n_rej);
@@ -561,11 +571,12 @@ __global__ void __launch_bounds__(128) k_screen(Consts c, const double* __restri
 // all lanes on the same work (the FP64 pipe runs full warps).  Accepted
 // stencils are written like the LP's (nonzero weights in slot order,
 // f~_ii = -sum in that order, status VRM_LP_LEARNED); a failed solve sends
-// the particle to retry_list (its next support), in the last round to the
+// the particle to retry_list (the next round screens on from its next
+// support), after its kMaxSolves-th solve or in the last round to the
 // rejects.
 __global__ void __launch_bounds__(128) k_solve(Consts c, const double* __restrict__ x, const double* __restrict__ y,
                                                const int* __restrict__ list, const int* __restrict__ solve_list,
-                                               const int* __restrict__ solve_count, const ProjSel* __restrict__ sel,
+                                               const int* __restrict__ solve_count, ProjSel* __restrict__ sel,
                                                int* __restrict__ retry_list, int* __restrict__ retry_count,
                                                bool last_round, int* __restrict__ cols, double* __restrict__ f,
                                                double* __restrict__ fii, uint8_t* __restrict__ status,
@@ -595,6 +606,7 @@ __global__ void __launch_bounds__(128) k_solve(Consts c, const double* __restric
         e5[q] = __dmul_rn(__dsub_rn(y[o.j[q]], yi0), c.inv_h);
       }
       ok = square_stencil(x5, e5, f5);
+      if (!ok) sel[t].solves = o.solves + 1;
       if (ok) {
         int* crow = cols + (size_t)i * VRM_STENCIL_W;
         double* frow = f + (size_t)i * VRM_STENCIL_W;
@@ -621,9 +633,9 @@ __global__ void __launch_bounds__(128) k_solve(Consts c, const double* __restric
       }
     }
     const bool failed = active && !ok;
-    const bool rej = failed && last_round;
+    const bool rej = failed && (last_round || o.solves + 1 >= kMaxSolves);
     n_rej += rej;
-    warp_append(failed && !last_round, t, retry_list, retry_count);
+    warp_append(failed && !rej, t, retry_list, retry_count);
     reject_particle(rej, i, cols, f, fii, status, reject_list, reject_count);
   }
   n_ok = __reduce_add_sync(0xffffffffu, n_ok);
@@ -682,6 +694,7 @@ cudaError_t proj_alloc(ProjScratch* p, int cap) {
   cudaError_t e = cudaMalloc(&p->sel, sizeof(ProjSel) * (size_t)cap);
   if (e == cudaSuccess) e = cudaMalloc(&p->list_s, sizeof(int) * (size_t)cap);
   if (e == cudaSuccess) e = cudaMalloc(&p->list_r, sizeof(int) * (size_t)cap);
+  if (e == cudaSuccess) e = cudaMalloc(&p->list_p, sizeof(int) * (size_t)cap);
   if (e == cudaSuccess) e = cudaMalloc(&p->counts, sizeof(int) * 2 * kProjRounds);
   if (e != cudaSuccess) {
     proj_free(p);
@@ -695,36 +708,43 @@ void proj_free(ProjScratch* p) {
   cudaFree(p->sel);
   cudaFree(p->list_s);
   cudaFree(p->list_r);
+  cudaFree(p->list_p);
   cudaFree(p->counts);
   *p = ProjScratch{};
 }
 
-// Rounds of (screen, FP64 solve): round r screens the particles whose solve
-// of round r-1 failed, from their next support; a particle reaches at most
-// kProjRounds = 4 FP64 solves.  Fixed launches (graph-capturable),
-// the lists and their sizes on the device.
+// Rounds of (screen, FP64 solve).  Round r screens at most kBudget[r]
+// supports per particle: the particles still searching when their budget is
+// spent, and those whose FP64 solve failed, form the next round's list
+// (compacted, so later rounds run full warps on the few that need many
+// screens), each from its next support.  The budgets grow to the whole
+// subset order and a particle makes at most kMaxSolves FP64 solves, so
+// kProjRounds rounds cover every particle's full search.  Fixed launches
+// (graph-capturable), the lists and their sizes on the device.
 cudaError_t learned_project(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
                             int m_bound, const int* slots, const float* f0, const int* small, int* cols, double* f,
                             double* fii, uint8_t* status, int* reject_list, int* reject_count, DevStats* ds,
                             const double* dt_dev, double nu, ProjScratch* ps, cudaStream_t s) {
+  static const int kBudget[kProjRounds] = {2, 4, 8, kSubsets, kSubsets, kSubsets, kSubsets};
   if (m_bound <= 0) return cudaSuccess;
   if (!ps || ps->cap < m_bound) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(ps->counts, 0, sizeof(int) * 2 * kProjRounds, s);
   if (e != cudaSuccess) return e;
   int blocks = (m_bound + 127) / 128;
   if (blocks > 16 * sm_count()) blocks = 16 * sm_count();
+  int* lists[2] = {ps->list_r, ps->list_p};
   for (int r = 0; r < kProjRounds; ++r) {
     int* solve_count = ps->counts + 2 * r;
-    int* retry_count = ps->counts + 2 * r + 1;
-    const int* in_list = r == 0 ? nullptr : ps->list_r;
+    int* next_count = ps->counts + 2 * r + 1;
+    const int* in_list = r == 0 ? nullptr : lists[(r - 1) & 1];
     const int* in_count = r == 0 ? nullptr : ps->counts + 2 * r - 1;
-    // the round's retry list is read by its screen before the solve rewrites it
+    int* next_list = lists[r & 1];
     k_screen<<<blocks, 128, 0, s>>>(c, x, y, list, list_count, m_bound, in_list, in_count, slots, f0, small,
-                                    reinterpret_cast<ProjSel*>(ps->sel), ps->list_s, solve_count, cols, f, fii,
-                                    status, reject_list, reject_count, ds);
+                                    reinterpret_cast<ProjSel*>(ps->sel), kBudget[r], ps->list_s, solve_count,
+                                    next_list, next_count, cols, f, fii, status, reject_list, reject_count, ds);
     note_launch();
-    k_solve<<<blocks, 128, 0, s>>>(c, x, y, list, ps->list_s, solve_count, reinterpret_cast<const ProjSel*>(ps->sel),
-                                   ps->list_r, retry_count, r == kProjRounds - 1, cols, f, fii, status, reject_list,
+    k_solve<<<blocks, 128, 0, s>>>(c, x, y, list, ps->list_s, solve_count, reinterpret_cast<ProjSel*>(ps->sel),
+                                   next_list, next_count, r == kProjRounds - 1, cols, f, fii, status, reject_list,
                                    reject_count, ds, dt_dev, nu);
     note_launch();
   }

@@ -35,12 +35,13 @@ cudaError_t learned_features(const Consts& c, const double* x, const double* y, 
                              const int* nbr_idx, __nv_bfloat16* X, int* slots, cudaStream_t s);
 // Scratch of the correction rounds: per listed particle the screened
 // support, two work lists and the rounds' list sizes.
-constexpr int kProjRounds = 4;
+constexpr int kProjRounds = 7;
 struct ProjScratch {
   int cap = 0;
   void* sel = nullptr;  // ProjSel[cap] (vrm_learned.cu)
-  int* list_s = nullptr;
-  int* list_r = nullptr;
+  int* list_s = nullptr;  // the round's particles with a support to solve
+  int* list_r = nullptr;  // the next round's particles (two, alternating)
+  int* list_p = nullptr;
   int* counts = nullptr;  // [2 * kProjRounds]
 };
 cudaError_t proj_alloc(ProjScratch* p, int cap);
