@@ -81,8 +81,10 @@ __device__ __forceinline__ float tanh_hw(float u) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(u));
   return t;
 }
+// c (z + a z^3) as z (c + (c a) z^2): five fp32 operations and the tanh.
+constexpr float kGeluCA = kGeluC * kGeluA;
 __device__ __forceinline__ float gelu(float z) {
-  const float u = kGeluC * fmaf(kGeluA * z, z * z, z);
+  const float u = z * fmaf(kGeluCA, z * z, kGeluC);
   const float hz = 0.5f * z;
   return fmaf(hz, tanh_hw(u), hz);
 }
@@ -479,18 +481,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
           if (l < 3) {
             const float* b = a.bias + (l == 0 ? kOffB1 : l == 1 ? kOffB2 : kOffB3);
 #pragma unroll 1
-            for (int c0 = cg * 64; c0 < cg * 64 + 64; c0 += 16) {
-              float v[16];
-              umma::tmem_ld16(trow + (uint32_t)c0, v);
-              __align__(16) __nv_bfloat162 hv[8];
+            for (int c0 = cg * 64; c0 < cg * 64 + 64; c0 += 32) {
+              float v[32];
+              umma::tmem_ld32(trow + (uint32_t)c0, v);
+              __align__(16) __nv_bfloat162 hv[16];
 #pragma unroll
-              for (int i = 0; i < 8; ++i)
+              for (int i = 0; i < 16; ++i)
                 hv[i] = __floats2bfloat162_rn(gelu(v[2 * i] + __ldg(b + c0 + 2 * i)),
                                               gelu(v[2 * i + 1] + __ldg(b + c0 + 2 * i + 1)));
               uint8_t* slab = h + (size_t)(c0 >> 6) * kSlabBytes + (size_t)r * 128;
               const int ch = (c0 & 63) >> 3;
-              *reinterpret_cast<uint4*>(slab + (((ch) ^ (r & 7)) << 4)) = *reinterpret_cast<uint4*>(&hv[0]);
-              *reinterpret_cast<uint4*>(slab + (((ch + 1) ^ (r & 7)) << 4)) = *reinterpret_cast<uint4*>(&hv[4]);
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                *reinterpret_cast<uint4*>(slab + (((ch + u) ^ (r & 7)) << 4)) = *reinterpret_cast<uint4*>(&hv[4 * u]);
             }
           } else if (cg < 2) {
             const int c0 = cg * 16;
