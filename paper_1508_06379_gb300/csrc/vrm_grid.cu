@@ -140,6 +140,42 @@ __global__ void k_tile_scan(const T* __restrict__ in, int n, const int* __restri
   if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_sums[ntiles];
 }
 
+// Tile scan that forms the tile's exclusive prefix itself: the block sums
+// the totals of the tiles before it (tile_sums from k_tile_sums; at most
+// kFusedScanTiles of them, a few KB read from L2), which saves the
+// single-block scan of the tile sums and its launch.  out[n] = the total.
+constexpr int kFusedScanTiles = 2048;
+template <typename T>
+__global__ void k_tile_scan_fused(const T* __restrict__ in, int n, const int* __restrict__ n_dev,
+                                  const int* __restrict__ tile_sums, int* __restrict__ out) {
+  if (n_dev) n = *n_dev;
+  const int ntiles = (n + kScanTile - 1) / kScanTile;
+  __shared__ int total;
+  if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int part = 0;
+    for (int k = threadIdx.x; k < t; k += kScanThreads) part += tile_sums[k];
+    block_exclusive_scan(part, &total);
+    const int pre = total;
+    long base = (long)t * kScanTile + (long)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      v[k] = load_count(in, base + k, n);
+      s += v[k];
+    }
+    int ex = block_exclusive_scan(s, &total) + pre;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      if (base + k < n) out[base + k] = ex;
+      ex += v[k];
+    }
+    if (t == ntiles - 1 && threadIdx.x == 0) out[n] = pre + total;
+    __syncthreads();
+  }
+}
+
 static int scan_grid(int n_bound) {
   int ntiles = (n_bound + kScanTile - 1) / kScanTile;
   int cap = 4 * sm_count();
@@ -151,8 +187,12 @@ static cudaError_t scan_impl(const T* in, int* out, int n, const int* n_dev, int
   if (!n_dev && n <= 0) return cudaMemsetAsync(out, 0, sizeof(int), s);
   const int g = scan_grid(n);
   k_tile_sums<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp); note_launch();
-  k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(tmp, n, n_dev); note_launch();
-  k_tile_scan<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp, out); note_launch();
+  if ((n + kScanTile - 1) / kScanTile <= kFusedScanTiles) {
+    k_tile_scan_fused<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp, out); note_launch();
+  } else {
+    k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(tmp, n, n_dev); note_launch();
+    k_tile_scan<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp, out); note_launch();
+  }
   return cudaGetLastError();
 }
 
