@@ -197,6 +197,16 @@ def lp_flops(n_lp, pivots, m=5, K=8, cols=None, col_pivots=None):
     return cols * per_col + n_lp * m + pivots * (m + 1 + 2 * (m + 1)) + col_pivots * (1 + 2 * (m + 1))
 
 
+def lp_flops_certified(n_lp, n_rechecked, pivots, K=8):
+    """FP64 flops of the small LPs with certified binary32 pivots (n = 1):
+    per LP the column setup (7 per column) and the FP64 solve of the final
+    basis (5 x 5 LU 75, substitutions 45, basis columns 15, residual 65,
+    sums 12: 212), and for the LPs re-run with FP64 pivots their whole FP64
+    LP (lp_flops, at the mean pivot count)."""
+    mean_piv = pivots / max(n_lp, 1)
+    return n_lp * (7 * K + 212) + lp_flops(n_rechecked, n_rechecked * mean_piv, 5, K)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -319,7 +329,8 @@ def run_ours(args):
 
     mean_stage = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage_ms.items()}
     dom = max(mean_stage, key=mean_stage.get)
-    roofline = roofline_for(dom, mean_stage[dom], stats, n, desc["order"]) if mean_stage[dom] > 0 else None
+    roofline = (roofline_for(dom, mean_stage[dom], stats, n, desc["order"], ctx.get_schedule()["lp_fp64_pivots"])
+                if mean_stage[dom] > 0 else None)
     if rank != 0:
         if dist:
             dist.barrier()
@@ -344,7 +355,7 @@ def run_ours(args):
                "full_solved": int(stats["lp_full_solved"]), "full_pivots": int(stats["lp_full_pivots"]),
                "full_columns": int(stats["lp_full_columns"]), "max_pivots": int(stats["max_pivots"]),
                "small_ok": int(stats["small_ok"]), "full_ok": int(stats["full_ok"]),
-               "no_stencil": int(stats["no_stencil"])},
+               "no_stencil": int(stats["no_stencil"]), "small_rechecked": int(stats["lp_small_rechecked"])},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line))
@@ -370,10 +381,13 @@ def traffic_for(kernel):
         return None
 
 
-def roofline_for(stage, ms, stats, n, order=1):
+def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1):
     m = 9 if order == 2 else 5
     if stage in ("lp_small", "lp_full"):
-        if stage == "lp_small":
+        if stage == "lp_small" and order == 1 and not lp_fp64_pivots:
+            flops = lp_flops_certified(stats["lp_small_solved"], stats["lp_small_rechecked"],
+                                       stats["lp_small_pivots"])
+        elif stage == "lp_small":
             flops = lp_flops(stats["lp_small_solved"], stats["lp_small_pivots"], m)
         else:
             flops = lp_flops(stats["lp_full_solved"], stats["lp_full_pivots"], m, cols=stats["lp_full_columns"],
@@ -621,7 +635,7 @@ def run_batched(args):
                "full_solved": int(stats["lp_full_solved"]), "full_pivots": int(stats["lp_full_pivots"]),
                "full_columns": int(stats["lp_full_columns"]), "max_pivots": int(stats["max_pivots"]),
                "small_ok": int(stats["small_ok"]), "full_ok": int(stats["full_ok"]),
-               "no_stencil": int(stats["no_stencil"])},
+               "no_stencil": int(stats["no_stencil"]), "small_rechecked": int(stats["lp_small_rechecked"])},
         "cpu_baseline": None,
     }
     print(json.dumps(line))

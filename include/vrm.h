@@ -125,6 +125,8 @@ typedef struct vrm_stats {
   int64_t lp_full_column_pivots; /* columns x pivots summed over them (their algorithmic work) */
   int64_t learned_screens; /* five-slot supports screened by the learned path (binary32 solves) */
   int64_t remove_candidates; /* vrm_remove_close: particles closer than r h to one of larger key */
+  int64_t lp_small_rechecked; /* of lp_small_solved: LPs whose binary32 pivot decisions were not all
+                                 certain and that were re-run with FP64 pivots (same result either way) */
 } vrm_stats;
 
 /* Stages of vrm_step, for vrm_stage_times. */
@@ -295,6 +297,11 @@ typedef struct vrm_batch vrm_batch;
  *   lp_block:         threads per block of the small-neighbourhood LP, one particle per thread (32..128, multiple of 32).
  *   lp_blocks_per_sm: the small LP's grid is capped at this many blocks per SM (1..64).
  *   apply_block:      threads per block of the application (32..256, multiple of 32).
+ *   lp_fp64_pivots:   0 (default): the small-neighbourhood LPs (n = 1) pivot
+ *                     in binary32 with certified decisions, and the few whose
+ *                     decisions are not all certain are re-run with FP64
+ *                     pivots; 1: every LP pivots in FP64.  The final basis,
+ *                     hence every weight, is the same bit for bit.
  * Setting a schedule drops any captured step graph; VRM_ERR_ARG if a field
  * is out of range.
  */
@@ -304,7 +311,8 @@ typedef struct vrm_schedule {
   int32_t lp_block;
   int32_t lp_blocks_per_sm;
   int32_t apply_block;
-  int32_t reserved[3];
+  int32_t lp_fp64_pivots;
+  int32_t reserved[2];
 } vrm_schedule;
 
 vrm_status vrm_get_schedule(const vrm_ctx* ctx, vrm_schedule* out);

@@ -42,7 +42,8 @@ class Stats(ctypes.Structure):
                 ("lp_full_pivots", ctypes.c_int64), ("learned_ok", ctypes.c_int64),
                 ("learned_rejected", ctypes.c_int64), ("learned_square", ctypes.c_int64),
                 ("lp_full_columns", ctypes.c_int64), ("lp_full_column_pivots", ctypes.c_int64),
-                ("learned_screens", ctypes.c_int64), ("remove_candidates", ctypes.c_int64)]
+                ("learned_screens", ctypes.c_int64), ("remove_candidates", ctypes.c_int64),
+                ("lp_small_rechecked", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -58,9 +59,9 @@ class Cloud(ctypes.Structure):
 class Schedule(ctypes.Structure):
     _fields_ = [("row_cap", ctypes.c_int32), ("search_block", ctypes.c_int32), ("lp_block", ctypes.c_int32),
                 ("lp_blocks_per_sm", ctypes.c_int32), ("apply_block", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("lp_fp64_pivots", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
-    FIELDS = ("row_cap", "search_block", "lp_block", "lp_blocks_per_sm", "apply_block")
+    FIELDS = ("row_cap", "search_block", "lp_block", "lp_blocks_per_sm", "apply_block", "lp_fp64_pivots")
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k in self.FIELDS}
@@ -69,7 +70,7 @@ class Schedule(ctypes.Structure):
     def from_dict(cls, d):
         s = cls()
         for k in cls.FIELDS:
-            setattr(s, k, int(d[k]))
+            setattr(s, k, int(d.get(k, 0)))
         return s
 
 

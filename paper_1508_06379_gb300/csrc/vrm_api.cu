@@ -54,6 +54,7 @@ struct vrm::Scratch {
   RoundBufs rb = {};
   // neighbourhoods and weights of vrm_step
   int *nbr_count = nullptr, *nbr_idx = nullptr, *small = nullptr, *cols = nullptr, *fail_list = nullptr;
+  int* retry_list = nullptr;  // small LPs re-run in FP64
   uint8_t *seg_mask = nullptr, *status = nullptr;
   double *f = nullptr, *fii = nullptr;
   // counters and state
@@ -153,7 +154,7 @@ void free_scratch(Scratch& s) {
                   s.mask, r.open, r.open_next, r.cnt, r.cpos, r.keep_flag, r.keep_pos, r.cx, r.cy, r.keep, r.apos,
                   r.cg.grid, r.cg.cell_key, r.cg.cell_rank, r.cg.cell_count, r.cg.cell_start, r.cg.sorted_idx,
                   r.cg.sorted_xy, r.cg.sorted_loc, r.cg.bbox, r.scan_tmp, s.nbr_count, s.nbr_idx, s.small, s.cols,
-                  s.fail_list, s.seg_mask, s.status, s.f, s.fii, s.ds, s.counters, s.st};
+                  s.fail_list, s.retry_list, s.seg_mask, s.status, s.f, s.fii, s.ds, s.counters, s.st};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   void* hp[] = {s.h_ds, s.h_counters, s.h_grid, s.h_params, s.h_state};
@@ -344,8 +345,8 @@ cudaError_t enqueue_stage_weights(vrm_ctx* ctx, const double* x, const double* y
     lp_list = ctx->L.rlist;
     lp_count = s.counters + 2;
   }
-  if ((e = lp_small(c, x, y, lp_list, lp_count, cap, s.small, s.cols, s.f, s.fii, s.status, s.fail_list, s.ds, 0.0,
-                    st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
+  if ((e = lp_small(c, x, y, lp_list, lp_count, cap, s.small, s.cols, s.f, s.fii, s.status, s.fail_list, s.retry_list, s.ds,
+                    0.0, st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
     return e;
   return lp_full(c, x, y, s.fail_list, &s.ds->n_fail, cap, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii, s.status,
                  s.ds, 0.0, st, &s.st->dt, ctx->p.nu);
@@ -416,6 +417,7 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.small, (long)n * 8);
   VRM_ALLOC(s.cols, (long)n * ctx->c.w);
   VRM_ALLOC(s.fail_list, n);
+  VRM_ALLOC(s.retry_list, n);
   VRM_ALLOC(s.seg_mask, n);
   VRM_ALLOC(s.status, n);
   VRM_ALLOC(s.f, (long)n * ctx->c.w);
@@ -513,7 +515,8 @@ bool block_ok(int b, int hi) { return b >= 32 && b <= hi && b % 32 == 0; }
 
 bool schedule_ok(const vrm_schedule& s, int k_cap) {
   return s.row_cap >= 8 && s.row_cap <= k_cap && block_ok(s.search_block, kBlock) && block_ok(s.lp_block, 128) &&
-         s.lp_blocks_per_sm >= 1 && s.lp_blocks_per_sm <= 64 && block_ok(s.apply_block, kBlock);
+         s.lp_blocks_per_sm >= 1 && s.lp_blocks_per_sm <= 64 && block_ok(s.apply_block, kBlock) &&
+         (s.lp_fp64_pivots == 0 || s.lp_fp64_pivots == 1);
 }
 
 void put_schedule(Consts& c, const vrm_schedule& s) {
@@ -521,6 +524,7 @@ void put_schedule(Consts& c, const vrm_schedule& s) {
   c.search_block = s.search_block;
   c.lp_block = s.lp_block;
   c.lp_blocks_per_sm = s.lp_blocks_per_sm;
+  c.lp_fp64_pivots = s.lp_fp64_pivots;
   c.apply_block = s.apply_block;
 }
 
@@ -606,8 +610,8 @@ cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const doub
     lp_list = ctx->L.rlist;
     lp_count = s.counters + 2;
   }
-  if ((e = lp_small(c, x, y, lp_list, lp_count, cap, s.small, s.cols, s.f, s.fii, s.status, s.fail_list, s.ds, 0.0,
-                    st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
+  if ((e = lp_small(c, x, y, lp_list, lp_count, cap, s.small, s.cols, s.f, s.fii, s.status, s.fail_list, s.retry_list, s.ds,
+                    0.0, st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
     return e;
   if ((e = mark(ctx, VRM_STAGE_LP_FULL, st)) != cudaSuccess) return e;
   if ((e = lp_full(c, x, y, s.fail_list, &s.ds->n_fail, cap, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii, s.status,
@@ -986,7 +990,8 @@ vrm_status vrm_solve_weights(vrm_ctx* ctx, const double* x, const double* y, int
     lp_list = ctx->L.rlist;
     lp_count = s.counters + 2;
   }
-  VRM_CUDA(lp_small(c, x, y, lp_list, lp_count, n, small, cols, f, fii, status, s.fail_list, s.ds, 0.0, stream));
+  VRM_CUDA(lp_small(c, x, y, lp_list, lp_count, n, small, cols, f, fii, status, s.fail_list, s.retry_list, s.ds,
+                      0.0, stream));
   VRM_CUDA(lp_full(c, x, y, s.fail_list, &s.ds->n_fail, n, nbr_count, nbr_idx, cols, f, fii, status, s.ds, 0.0,
                    stream));
   if (stats) {
@@ -1003,6 +1008,7 @@ vrm_status vrm_solve_weights(vrm_ctx* ctx, const double* x, const double* y, int
     stats->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
     stats->lp_full_columns = (int64_t)s.h_ds->lp_full_columns;
     stats->lp_full_column_pivots = (int64_t)s.h_ds->lp_full_column_pivots;
+    stats->lp_small_rechecked = (int64_t)s.h_ds->lp_small_retries;
     stats->learned_ok = s.h_ds->learned_ok;
     stats->learned_rejected = s.h_ds->learned_rejected;
     stats->learned_square = s.h_ds->learned_square;
@@ -1116,6 +1122,7 @@ vrm_status vrm_rk3_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t c
   st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
   st->lp_full_columns = (int64_t)s.h_ds->lp_full_columns;
   st->lp_full_column_pivots = (int64_t)s.h_ds->lp_full_column_pivots;
+  st->lp_small_rechecked = (int64_t)s.h_ds->lp_small_retries;
   st->learned_ok = s.h_ds->learned_ok;
   st->learned_rejected = s.h_ds->learned_rejected;
   st->learned_square = s.h_ds->learned_square;
@@ -1282,6 +1289,7 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
   st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
   st->lp_full_columns = (int64_t)s.h_ds->lp_full_columns;
   st->lp_full_column_pivots = (int64_t)s.h_ds->lp_full_column_pivots;
+  st->lp_small_rechecked = (int64_t)s.h_ds->lp_small_retries;
   st->learned_ok = s.h_ds->learned_ok;
   st->learned_rejected = s.h_ds->learned_rejected;
   st->learned_square = s.h_ds->learned_square;
@@ -1359,6 +1367,7 @@ vrm_status vrm_get_schedule(const vrm_ctx* ctx, vrm_schedule* out) {
   out->search_block = ctx->c.search_block;
   out->lp_block = ctx->c.lp_block;
   out->lp_blocks_per_sm = ctx->c.lp_blocks_per_sm;
+  out->lp_fp64_pivots = ctx->c.lp_fp64_pivots;
   out->apply_block = ctx->c.apply_block;
   return VRM_OK;
 }
@@ -1443,6 +1452,7 @@ vrm_status finish_cloud(vrm_ctx* ctx, vrm_cloud& C, vrm_stats* st) {
   st->lp_full_pivots = (int64_t)s.h_ds->lp_full_pivots;
   st->lp_full_columns = (int64_t)s.h_ds->lp_full_columns;
   st->lp_full_column_pivots = (int64_t)s.h_ds->lp_full_column_pivots;
+  st->lp_small_rechecked = (int64_t)s.h_ds->lp_small_retries;
   st->learned_ok = s.h_ds->learned_ok;
   st->learned_rejected = s.h_ds->learned_rejected;
   st->learned_square = s.h_ds->learned_square;
@@ -1472,6 +1482,7 @@ void add_stats(vrm_stats* t, const vrm_stats& a) {
   t->lp_full_pivots += a.lp_full_pivots;
   t->lp_full_columns += a.lp_full_columns;
   t->lp_full_column_pivots += a.lp_full_column_pivots;
+  t->lp_small_rechecked += a.lp_small_rechecked;
   t->learned_ok += a.learned_ok;
   t->learned_rejected += a.learned_rejected;
   t->learned_square += a.learned_square;

@@ -39,6 +39,7 @@ struct Consts {
   int search_block;      // threads per block of k_search_all
   int lp_block;          // threads per block of k_lp_small
   int lp_blocks_per_sm;  // grid cap of k_lp_small
+  int lp_fp64_pivots;    // 1: small LPs pivot in FP64; 0: certified binary32 pivots, FP64 re-runs
   int apply_block;       // threads per block of k_apply
 };
 
@@ -48,6 +49,7 @@ inline void default_schedule(Consts& c) {
   c.search_block = 256;
   c.lp_block = 128;
   c.lp_blocks_per_sm = 16;
+  c.lp_fp64_pivots = 0;
   c.apply_block = 256;
 }
 
@@ -86,6 +88,8 @@ struct DevStats {
   unsigned long long learned_screens;        // supports screened by the learned path
   unsigned long long lp_full_columns;        // columns summed over the full-neighbourhood LPs
   unsigned long long lp_full_column_pivots;  // columns x pivots summed over them
+  int n_retry;                               // retry list of the current small-LP pass (FP64 re-runs)
+  unsigned long long lp_small_retries;       // small LPs re-run in FP64 (uncertain binary32 decision)
 };
 
 // Growth-control selection state (device resident).
@@ -291,6 +295,7 @@ cudaError_t rounds_finish(StepState* st, const int* open, const uint8_t* mask, i
 // nu_dt = nu * dt for the stability statistic; with dt_dev it is nu * *dt_dev.
 cudaError_t lp_small(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
                      int cap, const int* small, int* cols, double* f, double* fii, uint8_t* status, int* fail_list,
+                     int* retry_list,
                      DevStats* ds, double nu_dt, cudaStream_t s, const double* dt_dev = nullptr, double nu = 0.0);
 cudaError_t lp_full(const Consts& c, const double* x, const double* y, const int* fail_list, const int* fail_count,
                     int cap, const int* nbr_count, const int* nbr_idx, int* cols, double* f, double* fii,

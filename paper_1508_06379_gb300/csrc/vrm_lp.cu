@@ -90,7 +90,8 @@ __device__ __forceinline__ float f32_of(double a) {
   return __int_as_float((int)((b >> 32) & 0x80000000u) | (e32 << 23) | (int)(mr & 0x7FFFFF));
 }
 
-__device__ __forceinline__ void cswap(double* d2, int* j, double* a, double* b, int p, int q) {
+template <typename P>
+__device__ __forceinline__ void cswap(double* d2, int* j, P* a, P* b, int p, int q) {
   const unsigned long long bq = (unsigned long long)dbits(d2[q]), bp = (unsigned long long)dbits(d2[p]);
   bool sw = (bq < bp) || (bq == bp && j[q] < j[p]);
   double t0 = sw ? d2[q] : d2[p], t1 = sw ? d2[p] : d2[q];
@@ -99,16 +100,17 @@ __device__ __forceinline__ void cswap(double* d2, int* j, double* a, double* b, 
   int u0 = sw ? j[q] : j[p], u1 = sw ? j[p] : j[q];
   j[p] = u0;
   j[q] = u1;
-  double v0 = sw ? a[q] : a[p], v1 = sw ? a[p] : a[q];
+  P v0 = sw ? a[q] : a[p], v1 = sw ? a[p] : a[q];
   a[p] = v0;
   a[q] = v1;
-  double w0 = sw ? b[q] : b[p], w1 = sw ? b[p] : b[q];
+  P w0 = sw ? b[q] : b[p], w1 = sw ? b[p] : b[q];
   b[p] = w0;
   b[q] = w1;
 }
 
 // Batcher odd-even merge sort of 8 (d2, j) keys with two payloads.
-__device__ __forceinline__ void sort8(double* d2, int* j, double* a, double* b) {
+template <typename P>
+__device__ __forceinline__ void sort8(double* d2, int* j, P* a, P* b) {
   cswap(d2, j, a, b, 0, 1); cswap(d2, j, a, b, 2, 3); cswap(d2, j, a, b, 4, 5); cswap(d2, j, a, b, 6, 7);
   cswap(d2, j, a, b, 0, 2); cswap(d2, j, a, b, 1, 3); cswap(d2, j, a, b, 4, 6); cswap(d2, j, a, b, 5, 7);
   cswap(d2, j, a, b, 1, 2); cswap(d2, j, a, b, 5, 6);
@@ -247,6 +249,139 @@ __device__ __forceinline__ void flush_stats(DevStats* ds, int ok, int none, int 
   }
 }
 
+// Columns of one small-neighbourhood LP: the occupied slots of particle i's
+// small neighbourhood ordered by (d2, index) (Sec. 4.3), offsets in units of
+// h; empty slots get index INT_MAX and zero offsets (a zero column).
+__device__ __forceinline__ void lp_columns(const Consts& c, const double* __restrict__ x,
+                                           const double* __restrict__ y, const int* __restrict__ small, int i,
+                                           int (&cj)[8], double (&cxi)[8], double (&ceta)[8]) {
+  const double xi0 = x[i], yi0 = y[i];
+  const int4 s0 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[0];
+  const int4 s1 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[1];
+  cj[0] = s0.x; cj[1] = s0.y; cj[2] = s0.z; cj[3] = s0.w;
+  cj[4] = s1.x; cj[5] = s1.y; cj[6] = s1.z; cj[7] = s1.w;
+  double cd2[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (cj[k] >= 0) {
+      const double dx = __dsub_rn(x[cj[k]], xi0), dy = __dsub_rn(y[cj[k]], yi0);
+      cd2[k] = dist2(dx, dy);
+      cxi[k] = dx;
+      ceta[k] = dy;
+    } else {
+      cd2[k] = 1e300;
+      cj[k] = INT_MAX;
+      cxi[k] = 0.0;
+      ceta[k] = 0.0;
+    }
+  }
+  sort8(cd2, cj, cxi, ceta);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    cxi[k] = __dmul_rn(cxi[k], c.inv_h);
+    ceta[k] = __dmul_rn(ceta[k], c.inv_h);
+  }
+}
+
+struct LpTally {
+  int ok = 0, none = 0, maxpiv = 0, solved = 0, pivots = 0;
+  double ratio = 0.0;
+};
+
+// Basic solution of the final basis (fresh LU solve, bit-identical to the
+// oracle's), snapped; feasibility from the phase-I objective and the
+// residual over the basic columns; the stencil (or the fallback queue, or a
+// zero stencil) written out.
+// Offsets of the basic columns (zero for artificials) selected from the
+// columns' offsets.
+template <int M>
+__device__ __forceinline__ void basic_offsets(const int (&basis)[M], const double (&cxi)[8],
+                                              const double (&ceta)[8], double (&bxi)[M], double (&beta)[M]) {
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+    double a = 0.0, e = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      a = (basis[r] == M + k) ? cxi[k] : a;
+      e = (basis[r] == M + k) ? ceta[k] : e;
+    }
+    bxi[r] = a;
+    beta[r] = e;
+  }
+}
+
+template <int M, int W>
+__device__ __forceinline__ void lp_finish(const Consts& c, int i, int code, const int (&basis)[M], int it,
+                                          const int (&cj)[8], const double (&bxi)[M], const double (&beta)[M],
+                                          int* __restrict__ cols, double* __restrict__ f, double* __restrict__ fii,
+                                          uint8_t* __restrict__ status, int* __restrict__ fail_list,
+                                          DevStats* __restrict__ ds, double nu_dt, double inv_h2, LpTally& tl) {
+  double fv[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) fv[k] = 0.0;
+  double wsum = 0.0, rmax = 0.0;
+  if (code == 0) {
+    double xB[M];
+    if (!basis_solve<M>(basis, bxi, beta, xB)) code = 2;
+    double acc[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) acc[r] = dneg(b_of(r));
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+      if (basis[r] < M) {
+        wsum = __dadd_rn(wsum, xB[r]);
+      } else {
+        const double v = gt_pos(xB[r], kTolSnap) ? xB[r] : 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == M + k) ? v : fv[k];
+        double col[M];
+        vcol<M>(bxi[r], beta[r], col);
+#pragma unroll
+        for (int q = 0; q < M; ++q) acc[q] = __fma_rn(col[q], v, acc[q]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < M; ++r) rmax = abs_gt(acc[r], rmax) ? fabs(acc[r]) : rmax;
+  }
+  const bool feasible = code == 0 && !gt_pos(wsum, kTolPhase1) && !gt_pos(rmax, kTolResid);
+  tl.maxpiv = it > tl.maxpiv ? it : tl.maxpiv;
+  ++tl.solved;
+  tl.pivots += it;
+  int* crow = cols + (size_t)i * W;
+  double* frow = f + (size_t)i * W;
+  if (feasible) {
+    int slot = 0;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (dbits(fv[k]) != 0) {
+        crow[slot] = cj[k];
+        frow[slot] = fv[k];
+        ++slot;
+        s = __dadd_rn(s, fv[k]);
+      }
+    for (int k = slot; k < W; ++k) {
+      crow[k] = -1;
+      frow[k] = 0.0;
+    }
+    fii[i] = -s;
+    status[i] = VRM_LP_SMALL;
+    ++tl.ok;
+    const double q = __dmul_rn(__dmul_rn(nu_dt, s), inv_h2);
+    tl.ratio = q > tl.ratio ? q : tl.ratio;
+  } else if (c.fallback) {
+    fail_list[atomicAdd(&ds->n_fail, 1)] = i;
+  } else {
+    for (int k = 0; k < W; ++k) {
+      crow[k] = -1;
+      frow[k] = 0.0;
+    }
+    fii[i] = 0.0;
+    status[i] = VRM_LP_NONE;
+    ++tl.none;
+  }
+}
+
 template <int M, int W>
 __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __restrict__ x,
                                                   const double* __restrict__ y, const int* __restrict__ list,
@@ -258,39 +393,16 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
   if (dt_dev) nu_dt = nu * *dt_dev;
   const int m = *list_count;
   const double inv_h2 = 1.0 / (c.h * c.h);
-  int st_ok = 0, st_none = 0, st_maxpiv = 0, st_solved = 0, st_pivots = 0;
-  double st_ratio = 0.0;
+  LpTally tl;
   // grid-stride over whole warps so that the warp-level statistics below run converged
   const long stride = (long)gridDim.x * blockDim.x;
   for (long base = (long)blockIdx.x * blockDim.x; base < m; base += stride) {
     const long t = base + threadIdx.x;
     if (t < m) {
       const int i = list[t];
-      const double xi0 = x[i], yi0 = y[i];
-      const int4 s0 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[0];
-      const int4 s1 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[1];
-      int cj[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
-      double cd2[8], cxi[8], ceta[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (cj[k] >= 0) {
-          const double dx = __dsub_rn(x[cj[k]], xi0), dy = __dsub_rn(y[cj[k]], yi0);
-          cd2[k] = dist2(dx, dy);
-          cxi[k] = dx;
-          ceta[k] = dy;
-        } else {
-          cd2[k] = 1e300;
-          cj[k] = INT_MAX;
-          cxi[k] = 0.0;
-          ceta[k] = 0.0;
-        }
-      }
-      sort8(cd2, cj, cxi, ceta);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        cxi[k] = __dmul_rn(cxi[k], c.inv_h);
-        ceta[k] = __dmul_rn(ceta[k], c.inv_h);
-      }
+      int cj[8];
+      double cxi[8], ceta[8];
+      lp_columns(c, x, y, small, i, cj, cxi, ceta);
       // tableau: T[r][k] = (B^-1 V)_rk, rhs = B^-1 b, d = phase-I reduced costs
       double T[M][8], rhs[M], d[8];
 #pragma unroll
@@ -425,86 +537,348 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
         for (int r = 0; r < M; ++r) basis[r] = (leave == r) ? M + q : basis[r];
         ++it;
       }
-      // basic solution of the final basis (fresh LU solve, bit-identical to
-      // the oracle's), snapped, and its residual over the basic columns
-      double fv[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) fv[k] = 0.0;
-      double wsum = 0.0, rmax = 0.0;
-      if (code == 0) {
-        double bxi[M], beta[M], xB[M];
-#pragma unroll
-        for (int r = 0; r < M; ++r) {
-          double a = 0.0, e = 0.0;
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            a = (basis[r] == M + k) ? cxi[k] : a;
-            e = (basis[r] == M + k) ? ceta[k] : e;
-          }
-          bxi[r] = a;
-          beta[r] = e;
-        }
-        if (!basis_solve<M>(basis, bxi, beta, xB)) code = 2;
-        double acc[M];
-#pragma unroll
-        for (int r = 0; r < M; ++r) acc[r] = dneg(b_of(r));
-#pragma unroll
-        for (int r = 0; r < M; ++r) {
-          if (basis[r] < M) {
-            wsum = __dadd_rn(wsum, xB[r]);
-          } else {
-            const double v = gt_pos(xB[r], kTolSnap) ? xB[r] : 0.0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == M + k) ? v : fv[k];
-            double col[M];
-            vcol<M>(bxi[r], beta[r], col);
-#pragma unroll
-            for (int q = 0; q < M; ++q) acc[q] = __fma_rn(col[q], v, acc[q]);
-          }
-        }
-#pragma unroll
-        for (int r = 0; r < M; ++r) rmax = abs_gt(acc[r], rmax) ? fabs(acc[r]) : rmax;
-      }
-      const bool feasible = code == 0 && !gt_pos(wsum, kTolPhase1) && !gt_pos(rmax, kTolResid);
-      st_maxpiv = it > st_maxpiv ? it : st_maxpiv;
-      ++st_solved;
-      st_pivots += it;
-      int* crow = cols + (size_t)i * W;
-      double* frow = f + (size_t)i * W;
-      if (feasible) {
-        int slot = 0;
-        double s = 0.0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          if (dbits(fv[k]) != 0) {
-            crow[slot] = cj[k];
-            frow[slot] = fv[k];
-            ++slot;
-            s = __dadd_rn(s, fv[k]);
-          }
-        for (int k = slot; k < W; ++k) {
-          crow[k] = -1;
-          frow[k] = 0.0;
-        }
-        fii[i] = -s;
-        status[i] = VRM_LP_SMALL;
-        ++st_ok;
-        const double q = __dmul_rn(__dmul_rn(nu_dt, s), inv_h2);
-        st_ratio = q > st_ratio ? q : st_ratio;
-      } else if (c.fallback) {
-        fail_list[atomicAdd(&ds->n_fail, 1)] = i;
-      } else {
-        for (int k = 0; k < W; ++k) {
-          crow[k] = -1;
-          frow[k] = 0.0;
-        }
-        fii[i] = 0.0;
-        status[i] = VRM_LP_NONE;
-        ++st_none;
-      }
+      double bxi[M], beta[M];
+      basic_offsets<M>(basis, cxi, ceta, bxi, beta);
+      lp_finish<M, W>(c, i, code, basis, it, cj, bxi, beta, cols, f, fii, status, fail_list, ds, nu_dt, inv_h2, tl);
     }
   }
-  flush_stats(ds, st_ok, st_none, st_maxpiv, st_ratio, false, st_solved, st_pivots);
+  flush_stats(ds, tl.ok, tl.none, tl.maxpiv, tl.ratio, false, tl.solved, tl.pivots);
+}
+
+// ---------------------------------------------------------------------------
+// Certified binary32 pivoting.  Every pivot decision of the phase-I simplex
+// (entering column, eligible pivot rows, zero basic values, the minimum
+// ratio and its ties) is a comparison of a tableau quantity with a
+// threshold.  k_lp_small32 runs the tableau in binary32 and carries, for
+// every entry, a rigorous bound on its distance from the exact rational
+// tableau of the same pivot sequence started from the FP64 Vandermonde
+// matrix (running error analysis: each update adds the propagated operand
+// bounds and the rounding of its own result, u = 2^-24).  A decision whose
+// binary32 value lies farther from the threshold than its bound is the
+// decision of exact arithmetic, and therefore the decision of the FP64
+// tableau, whose own distance from exact is smaller by 2^-29 (the safety
+// factor 1.25 covers it and the rounding of the bound arithmetic).  So a
+// run whose decisions are all certified ends on the FP64 run's basis with
+// its pivot count, and the weights come from the same FP64 LU solve of that
+// basis (lp_finish): bit-identical output.  A particle with one uncertain
+// decision (near-degenerate ratios, entries near the tolerances, growth of
+// the bounds under small pivots) goes to a retry list that k_lp_small
+// solves in FP64.  This moves the m x 8 tableau updates (about 60% of the
+// FP64 instructions of an LP) to the binary32 pipes, which GB300 runs at
+// about 64 times the FP64 rate.
+// ---------------------------------------------------------------------------
+constexpr float kU32 = 5.9604644775390625e-8f;  // 2^-24, unit roundoff of binary32
+constexpr float kCertSafety = 1.25f;
+// a product by an approximate reciprocal (at most 1 ulp = 2u) and its rounding
+constexpr float kRcpMul = 3.01f * kU32;
+// FP64 tolerances bracketed by binary32 values (below, above)
+constexpr float kTolPriceLo = 0.99999994e-9f, kTolPriceHi = 1.0000001e-9f;
+constexpr float kTolPivotLo = 0.99999994e-9f, kTolPivotHi = 1.0000001e-9f;
+constexpr float kTolSnapLo = 0.99999994e-11f, kTolSnapHi = 1.0000001e-11f;
+constexpr float kTolTieLo = 0.9999999e-12f, kTolTieHi = 1.0000001e-12f;
+
+// Approximate binary32 reciprocal (PTX rcp.approx: at most 1 ulp from 1/a
+// for normal a); the error bounds below account for it.
+__device__ __forceinline__ float rcp_approx(float a) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+
+// Binary32 value of an FP64 offset (f32_of), zero kept; magnitudes outside
+// [2^-100, 2^100] set `bad` (the bounds assume normal binary32 operands).
+__device__ __forceinline__ float f32_checked(double a, bool& bad) {
+  const long long b = dbits(a) & 0x7FFFFFFFFFFFFFFFLL;
+  if (b == 0) return 0.0f;
+  const int e = (int)(b >> 52) - 1023;
+  bad = bad || e < -100 || e > 100;
+  return f32_of(a);
+}
+
+// Columns of one LP as in lp_columns, carrying binary32 offsets
+// xi32 = f32(dx) * f32(1/h) (within 3.01 u of the FP64 offset) instead of
+// the FP64 ones.
+__device__ __forceinline__ void lp_columns32(const double* __restrict__ x, const double* __restrict__ y,
+                                             const int* __restrict__ small, int i, double xi0, double yi0,
+                                             float inv_h32, int (&cj)[8], float (&xs)[8], float (&es)[8],
+                                             bool& bad) {
+  const int4 s0 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[0];
+  const int4 s1 = reinterpret_cast<const int4*>(small + (size_t)i * 8)[1];
+  cj[0] = s0.x; cj[1] = s0.y; cj[2] = s0.z; cj[3] = s0.w;
+  cj[4] = s1.x; cj[5] = s1.y; cj[6] = s1.z; cj[7] = s1.w;
+  double cd2[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (cj[k] >= 0) {
+      const double dx = __dsub_rn(x[cj[k]], xi0), dy = __dsub_rn(y[cj[k]], yi0);
+      cd2[k] = dist2(dx, dy);
+      xs[k] = __fmul_rn(f32_checked(dx, bad), inv_h32);
+      es[k] = __fmul_rn(f32_checked(dy, bad), inv_h32);
+    } else {
+      cd2[k] = 1e300;
+      cj[k] = INT_MAX;
+      xs[k] = 0.0f;
+      es[k] = 0.0f;
+    }
+  }
+  sort8(cd2, cj, xs, es);
+}
+
+template <int M, int W>
+__global__ void __launch_bounds__(128, 3) k_lp_small32(Consts c, const double* __restrict__ x,
+                                                    const double* __restrict__ y, const int* __restrict__ list,
+                                                    const int* __restrict__ list_count, const int* __restrict__ small,
+                                                    int* __restrict__ cols, double* __restrict__ f,
+                                                    double* __restrict__ fii, uint8_t* __restrict__ status,
+                                                    int* __restrict__ fail_list, int* __restrict__ retry_list,
+                                                    DevStats* __restrict__ ds, double nu_dt,
+                                                    const double* __restrict__ dt_dev, double nu) {
+  static_assert(M == 5, "certified binary32 pivoting is written for the n = 1 rows");
+  if (dt_dev) nu_dt = nu * *dt_dev;
+  const int m = *list_count;
+  const double inv_h2 = 1.0 / (c.h * c.h);
+  const float inv_h32 = f32_of(c.inv_h);
+  LpTally tl;
+  int n_retry = 0;
+  const unsigned lane = threadIdx.x & 31;
+  // the sorted column indices wait in shared memory while the tableau holds the registers
+  __shared__ int s_cj[8][128];
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long base = (long)blockIdx.x * blockDim.x; base < m; base += stride) {
+    const long t = base + threadIdx.x;
+    const bool active = t < m;
+    int i = 0, it = 0, code = 0;
+    int basis[M];
+    bool unc = false;
+#pragma unroll
+    for (int r = 0; r < M; ++r) basis[r] = r;
+    if (active) {
+      i = list[t];
+      float xs[8], es[8];
+      {
+        int cj[8];
+        lp_columns32(x, y, small, i, x[i], y[i], inv_h32, cj, xs, es, unc);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s_cj[k][threadIdx.x] = cj[k];
+      }
+      // T, rhs: tableau; E, Eb: bounds on their distance from exact; d, Ed:
+      // phase-I reduced costs and bounds
+      float T[M][8], E[M][8], d[8], Ed[8], rhs[M], Eb[M];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float v[M] = {xs[k], es[k], __fmul_rn(xs[k], xs[k]), __fmul_rn(xs[k], es[k]), __fmul_rn(es[k], es[k])};
+        float sum = 0.0f, sa = 0.0f, se = 0.0f;
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+          T[r][k] = v[r];
+          // offsets within 3.01 u of the FP64 ones; their products within 7.01 u
+          E[r][k] = (r < 2 ? 3.01f : 7.01f) * kU32 * fabsf(v[r]);
+          sum = __fadd_rn(sum, v[r]);
+          sa += fabsf(v[r]);
+          se += E[r][k];
+        }
+        d[k] = -sum;
+        Ed[k] = __fmaf_rn(4.01f * kU32, sa, se);
+      }
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        rhs[r] = (r == 2 || r == 4) ? 2.0f : 0.0f;
+        Eb[r] = 0.0f;
+      }
+      unsigned basic = 0;
+      int n_art = M;
+      for (;;) {
+        if (unc || n_art == 0) break;
+        // entering column: the lowest k certainly below -tol; a lower column
+        // that is not certainly above it makes the choice uncertain
+        unsigned yes = 0, un = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const float mg = kCertSafety * Ed[k];
+          const bool nb = !((basic >> k) & 1u);
+          yes |= (nb && d[k] < -kTolPriceHi - mg) ? 1u << k : 0u;
+          un |= (nb && !(d[k] < -kTolPriceHi - mg) && !(d[k] > -kTolPriceLo + mg)) ? 1u << k : 0u;
+        }
+        if (yes == 0) {
+          unc = un != 0;
+          break;
+        }
+        const int q = __ffs(yes) - 1;
+        unc = (un & ((1u << q) - 1u)) != 0;
+        if (it == kPivotCap) {
+          code = 2;
+          break;
+        }
+        float a[M], ea[M];
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+          float v = T[r][0], e = E[r][0];
+#pragma unroll
+          for (int k = 1; k < 8; ++k) {
+            v = (q == k) ? T[r][k] : v;
+            e = (q == k) ? E[r][k] : e;
+          }
+          a[r] = v;
+          ea[r] = e;
+        }
+        // eligible rows, zero basic values, ratios with bounds
+        unsigned elig = 0;
+        float lo[M], hi[M], thlo = 3.0e38f, thhi = 3.0e38f;
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+          const float mg = kCertSafety * ea[r];
+          const bool el = a[r] > kTolPivotHi + mg;
+          unc = unc || (!el && !(a[r] < kTolPivotLo - mg));
+          const float mb = kCertSafety * Eb[r];
+          const bool nzr = rhs[r] > kTolSnapHi + mb;
+          unc = unc || (el && !nzr && !(rhs[r] < kTolSnapLo - mb));
+          const float inv = rcp_approx(a[r]);
+          const float ratio = nzr ? rhs[r] * inv : 0.0f;
+          const float g = ea[r] * inv;  // relative bound of the pivot element (<= 1/2 used below)
+          const float er = nzr ? kCertSafety * __fmaf_rn(kRcpMul, ratio, (Eb[r] + 2.0f * (rhs[r] + Eb[r]) * g) * inv)
+                               : 0.0f;
+          unc = unc || (el && nzr && (!(g <= 0.5f) || !(er < 1.0e30f)));
+          elig |= el ? 1u << r : 0u;
+          lo[r] = el ? fmaxf(ratio - er, 0.0f) : 3.0e38f;  // exact ratios of eligible rows are >= 0
+          hi[r] = el ? ratio + er : 3.0e38f;
+          thlo = fminf(thlo, lo[r]);
+          thhi = fminf(thhi, hi[r]);
+        }
+        if (elig == 0) {
+          code = 2;
+          break;
+        }
+        // a row can tie with the minimum only if its interval reaches the
+        // largest possible tie limit theta + 1e-12 max(theta, 1)
+        const float l0 = __fmaf_rn(kTolTieLo, fmaxf(thlo, 1.0f), thlo);
+        const float l1 = __fmaf_rn(kTolTieHi, fmaxf(thhi, 1.0f), thhi);
+        const float limlo = __fmaf_rn(-4.0f * kU32, fabsf(l0), l0);
+        const float limhi = __fmaf_rn(4.0f * kU32, fabsf(l1), l1);
+        unsigned poss = 0, tied = 0;
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+          poss |= (((elig >> r) & 1u) && lo[r] <= limhi) ? 1u << r : 0u;
+          tied |= (hi[r] <= limlo) ? 1u << r : 0u;
+        }
+        if (__popc(poss) == 1)
+          tied = poss;
+        else
+          unc = unc || (poss & ~tied) != 0;
+        tied &= poss;
+        int leave = 0, lbas = INT_MAX;
+#pragma unroll
+        for (int r = 0; r < M; ++r)
+          if (((tied >> r) & 1u) && basis[r] < lbas) {
+            leave = r;
+            lbas = basis[r];
+          }
+        float piv = a[0], pe = ea[0], prhs_raw = rhs[0], pebr = Eb[0];
+#pragma unroll
+        for (int r = 1; r < M; ++r) {
+          piv = (leave == r) ? a[r] : piv;
+          pe = (leave == r) ? ea[r] : pe;
+          prhs_raw = (leave == r) ? rhs[r] : prhs_raw;
+          pebr = (leave == r) ? Eb[r] : pebr;
+        }
+        const float P = rcp_approx(piv);
+        const float rho = pe * P;  // relative bound of the pivot; the bounds below take rho <= 1/2
+        unc = unc || !(rho <= 0.5f);
+        if (unc) break;
+        // pivot on (leave, q)
+        float prow[8], Ep[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          float v = T[0][k], e = E[0][k];
+#pragma unroll
+          for (int r = 1; r < M; ++r) {
+            v = (leave == r) ? T[r][k] : v;
+            e = (leave == r) ? E[r][k] : e;
+          }
+          const float pr = v * P, eP = e * P;
+          prow[k] = (k == q) ? 1.0f : pr;
+          Ep[k] = (k == q) ? 0.0f : __fmaf_rn(kRcpMul, fabsf(pr), __fmaf_rn(2.0f * rho, fabsf(pr) + eP, eP));
+        }
+        const float prhs = prhs_raw * P, ebP = pebr * P;
+        const float Ebp = __fmaf_rn(kRcpMul, fabsf(prhs), __fmaf_rn(2.0f * rho, fabsf(prhs) + ebP, ebP));
+#pragma unroll
+        for (int r = 0; r < M; ++r) {
+          const bool lr = (leave == r);
+          const float ar = lr ? -1.0f : a[r];
+          const float ear = lr ? 0.0f : ea[r];
+          const float aar = fabsf(ar) + ear;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            // column q of the other rows becomes an exact 0 (its bound stays, conservatively)
+            const float tn = __fmaf_rn(-ar, prow[k], lr ? 0.0f : T[r][k]);
+            const float en = __fmaf_rn(kU32, fabsf(tn), __fmaf_rn(aar, Ep[k], __fmaf_rn(ear, fabsf(prow[k]), E[r][k])));
+            T[r][k] = tn;
+            E[r][k] = lr ? Ep[k] : en;
+          }
+          const float rn = __fmaf_rn(-ar, prhs, lr ? 0.0f : rhs[r]);
+          const float ebn = __fmaf_rn(kU32, fabsf(rn), __fmaf_rn(aar, Ebp, __fmaf_rn(ear, fabsf(prhs), Eb[r])));
+          rhs[r] = rn;
+          Eb[r] = lr ? Ebp : ebn;
+        }
+        float dq = d[0], edq = Ed[0];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {
+          dq = (q == k) ? d[k] : dq;
+          edq = (q == k) ? Ed[k] : edq;
+        }
+        const float adq = fabsf(dq) + edq;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          d[k] = __fmaf_rn(-dq, prow[k], d[k]);
+          Ed[k] = __fmaf_rn(kU32, fabsf(d[k]), __fmaf_rn(adq, Ep[k], __fmaf_rn(edq, fabsf(prow[k]), Ed[k])));
+        }
+        if (lbas >= M)
+          basic &= ~(1u << (lbas - M));
+        else
+          --n_art;
+        basic |= 1u << q;
+#pragma unroll
+        for (int r = 0; r < M; ++r) basis[r] = (leave == r) ? M + q : basis[r];
+        ++it;
+      }
+    }
+    // the lanes leave the pivot loop at different counts: join them so that
+    // the FP64 solve below runs once per warp
+    __syncwarp();
+    const bool retry = active && unc;
+    if (active && !unc) {
+      // FP64 offsets of the basic columns, computed as lp_columns computes them
+      int cj[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) cj[k] = s_cj[k][threadIdx.x];
+      const double xi0 = x[i], yi0 = y[i];
+      double bxi[M], beta[M];
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        int j = INT_MAX;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) j = (basis[r] == M + k) ? cj[k] : j;
+        bxi[r] = 0.0;
+        beta[r] = 0.0;
+        if (j != INT_MAX) {
+          bxi[r] = __dmul_rn(__dsub_rn(x[j], xi0), c.inv_h);
+          beta[r] = __dmul_rn(__dsub_rn(y[j], yi0), c.inv_h);
+        }
+      }
+      lp_finish<M, W>(c, i, code, basis, it, cj, bxi, beta, cols, f, fii, status, fail_list, ds, nu_dt, inv_h2, tl);
+    }
+    // warp-aggregated append to the FP64 retry list
+    const unsigned rb = __ballot_sync(0xffffffffu, retry);
+    if (rb) {
+      const int lead = __ffs(rb) - 1;
+      int slot0 = 0;
+      if ((int)lane == lead) slot0 = atomicAdd(&ds->n_retry, __popc(rb));
+      slot0 = __shfl_sync(0xffffffffu, slot0, lead);
+      if (retry) retry_list[slot0 + __popc(rb & ((1u << lane) - 1u))] = i;
+      n_retry += (lane == 0) ? __popc(rb) : 0;
+    }
+  }
+  flush_stats(ds, tl.ok, tl.none, tl.maxpiv, tl.ratio, false, tl.solved, tl.pivots);
+  if (lane == 0 && n_retry) atomicAdd(&ds->lp_small_retries, (unsigned long long)n_retry);
 }
 
 // Monomial of Vandermonde row r at (xi, eta), rounded exactly as vcol<M>
@@ -1038,18 +1412,30 @@ __global__ void k_lp_clear(int n, int w, const uint8_t* __restrict__ diffused, i
 
 cudaError_t lp_small(const Consts& c, const double* x, const double* y, const int* list, const int* list_count,
                      int cap, const int* small, int* cols, double* f, double* fii, uint8_t* status, int* fail_list,
-                     DevStats* ds, double nu_dt, cudaStream_t s, const double* dt_dev, double nu) {
+                     int* retry_list, DevStats* ds, double nu_dt, cudaStream_t s, const double* dt_dev, double nu) {
   if (cap <= 0) return cudaSuccess;
   const int tb = c.lp_block;
   int blocks = (int)(((long)cap + tb - 1) / tb);
   if (blocks > c.lp_blocks_per_sm * sm_count()) blocks = c.lp_blocks_per_sm * sm_count();
-  if (c.order == 2)
+  if (c.order == 2) {
     k_lp_small<9, 12><<<blocks, tb, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list, ds,
                                             nu_dt, dt_dev, nu);
-  else
+    note_launch();
+  } else if (c.lp_fp64_pivots || !(c.inv_h > 1e-20 && c.inv_h < 1e20)) {
     k_lp_small<5, 8><<<blocks, tb, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list, ds,
                                            nu_dt, dt_dev, nu);
-  note_launch();
+    note_launch();
+  } else {
+    // certified binary32 pivots, then the uncertain particles in FP64
+    cudaError_t e = cudaMemsetAsync(&ds->n_retry, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_lp_small32<5, 8><<<blocks, tb, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list,
+                                             retry_list, ds, nu_dt, dt_dev, nu);
+    note_launch();
+    k_lp_small<5, 8><<<blocks, tb, 0, s>>>(c, x, y, retry_list, &ds->n_retry, small, cols, f, fii, status,
+                                           fail_list, ds, nu_dt, dt_dev, nu);
+    note_launch();
+  }
   return cudaGetLastError();
 }
 

@@ -14,7 +14,8 @@ def fake_measure(costs, changed=None):
     def measure(s):
         calls.append(dict(s))
         search = costs["row_cap"][s["row_cap"]] + costs["search_block"][s["search_block"]]
-        lp = costs["lp_block"][s["lp_block"]] + costs["lp_blocks_per_sm"][s["lp_blocks_per_sm"]]
+        lp = (costs["lp_block"][s["lp_block"]] + costs["lp_blocks_per_sm"][s["lp_blocks_per_sm"]] +
+              costs["lp_fp64_pivots"][s["lp_fp64_pivots"]])
         ap = costs["apply_block"][s["apply_block"]]
         same = not (changed and changed(s))
         return {"search": search, "lp_small": lp, "apply": ap, "reduce": 1.0}, same
@@ -28,15 +29,17 @@ COSTS = {
     "lp_block": {32: 0.5, 64: 0.1, 128: 0.2},
     "lp_blocks_per_sm": {4: 0.3, 8: 0.2, 16: 0.01, 32: 0.4},
     "apply_block": {64: 0.2, 128: 0.3, 256: 0.1},
+    "lp_fp64_pivots": {0: 0.05, 1: 0.5},
 }
 
 
 def test_descent_picks_the_fastest_option_of_every_group():
     measure, calls = fake_measure(COSTS)
     best, report = autotune.descend(measure, k_cap=32, max_count=12)
-    assert best == dict(row_cap=16, search_block=128, lp_block=64, lp_blocks_per_sm=16, apply_block=256)
-    # 9 search + 12 LP + 3 apply candidates, each measured once
-    assert len(calls) == 24 and len(report) == 24
+    assert best == dict(row_cap=16, search_block=128, lp_block=64, lp_blocks_per_sm=16, apply_block=256,
+                        lp_fp64_pivots=0)
+    # 9 search + 12 + 2 LP + 3 apply candidates, each measured once
+    assert len(calls) == 26 and len(report) == 26
 
 
 def test_row_caps_below_the_widest_row_are_not_tried():
