@@ -393,6 +393,8 @@ def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1):
             flops = lp_flops(stats["lp_full_solved"], stats["lp_full_pivots"], m, cols=stats["lp_full_columns"],
                              col_pivots=stats["lp_full_column_pivots"])
         kern = "k_lp_" + stage[3:]
+        if stage == "lp_small" and order == 1 and not lp_fp64_pivots:
+            kern = "k_lp_small32"
         ach = flops / (ms * 1e-3) / 1e12
         peak = FP64_PEAK_GFLOPS / 1000.0
         return {"kernel": kern, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
