@@ -142,9 +142,9 @@ __global__ void k_tile_scan(const T* __restrict__ in, int n, const int* __restri
 
 // Tile scan that forms the tile's exclusive prefix itself: the block sums
 // the totals of the tiles before it (tile_sums from k_tile_sums; at most
-// kFusedScanTiles of them, a few KB read from L2), which saves the
+// kFusedScanTiles of them, at most 16 KB read from L2), which saves the
 // single-block scan of the tile sums and its launch.  out[n] = the total.
-constexpr int kFusedScanTiles = 2048;
+constexpr int kFusedScanTiles = 4096;
 template <typename T>
 __global__ void k_tile_scan_fused(const T* __restrict__ in, int n, const int* __restrict__ n_dev,
                                   const int* __restrict__ tile_sums, int* __restrict__ out) {

@@ -54,6 +54,12 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
   const size_t stride = (size_t)c.k_cap;
   const float tie = 2.f * kBand;
   int local_max = 0;
+  // closest member of every segment so far (FP32 squared distance, index),
+  // one column per thread: read and written with a dynamic segment index
+  // (conflict-free: the row stride is a multiple of 32 words)
+  __shared__ float s_bf[8][kBlock];
+  __shared__ int s_bj[8][kBlock];
+  const int tx = threadIdx.x;
   for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
     const int i = sidx[p];
     const double2 pi = sxy[p];
@@ -61,12 +67,10 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
     const int cx = grid_cell_x(g, pi.x), cy = grid_cell_y(g, pi.y);
     int list[KCAP];
     int cnt = 0;
-    float bf[8];
-    int bj[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-      bf[t] = 3e38f;
-      bj[t] = -1;
+      s_bf[t][tx] = 3e38f;
+      s_bj[t][tx] = -1;
     }
     unsigned mask = 0, amb = 0;
     for (int by = cy - 1; by <= cy + 1; ++by) {
@@ -92,23 +96,15 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
             if (s < 0) continue;
           }
           mask |= 1u << s;
-          float cb = bf[0];
-          int cjb = bj[0];
-#pragma unroll
-          for (int t = 1; t < 8; ++t) {
-            cb = (s == t) ? bf[t] : cb;
-            cjb = (s == t) ? bj[t] : cjb;
-          }
+          const float cb = s_bf[s][tx];
+          const int cjb = s_bj[s][tx];
           const bool take = cjb < 0 || d2f < cb || (d2f == cb && j < cjb);
           // conservative: the displaced or the new member is close to the best
           const bool close = cjb >= 0 && fabsf(d2f - cb) <= tie;
           if (close) amb |= 1u << s;
           if (take) {
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-              bf[t] = (s == t) ? d2f : bf[t];
-              bj[t] = (s == t) ? j : bj[t];
-            }
+            s_bf[s][tx] = d2f;
+            s_bj[s][tx] = j;
           }
           if (cnt < k_cap || j < list[k_cap - 1]) {
             int pos = cnt < k_cap ? cnt : k_cap - 1;
@@ -122,6 +118,9 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
         }
       }
     }
+    int bj[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) bj[t] = s_bj[t][tx];
     if (amb) {
       // exact FP64 order (ties to the smaller index) for the flagged segments
       double bd[8];
