@@ -266,11 +266,31 @@ __global__ void k_bbox(const double* __restrict__ x, const double* __restrict__ 
     mxy = t > mxy ? t : mxy;
   }
   bad = __any_sync(0xffffffffu, bad);
+  // one atomic per block and quantity (per-warp atomics on four addresses
+  // serialise at L2)
+  __shared__ unsigned long long w_mn[2][32], w_mx[2][32];
+  __shared__ int w_bad[32];
+  const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   if ((threadIdx.x & 31) == 0) {
-    atomicMin(&bb[0], mnx);
-    atomicMax(&bb[1], mxx);
-    atomicMin(&bb[2], mny);
-    atomicMax(&bb[3], mxy);
+    w_mn[0][warp] = mnx;
+    w_mx[0][warp] = mxx;
+    w_mn[1][warp] = mny;
+    w_mx[1][warp] = mxy;
+    w_bad[warp] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) {
+      mnx = w_mn[0][w] < mnx ? w_mn[0][w] : mnx;
+      mxx = w_mx[0][w] > mxx ? w_mx[0][w] : mxx;
+      mny = w_mn[1][w] < mny ? w_mn[1][w] : mny;
+      mxy = w_mx[1][w] > mxy ? w_mx[1][w] : mxy;
+      bad |= w_bad[w];
+    }
+    if (mnx != ~0ull) atomicMin(&bb[0], mnx);
+    if (mxx) atomicMax(&bb[1], mxx);
+    if (mny != ~0ull) atomicMin(&bb[2], mny);
+    if (mxy) atomicMax(&bb[3], mxy);
     if (bad) atomicOr(&bb[4], 1ull);
   }
 }

@@ -103,6 +103,7 @@ struct ReduceState {
   int k_tie;                     // particles with key == T that stay out (lowest indices)
   int all_out;                   // 1: every particle stays out (sum within bound)
   unsigned int blocks_done;      // blocks of the current pass that have merged their histogram
+  int n_sub;                     // particles matching the first two chosen bytes (listed by pass 2)
   unsigned long long hist[256][4];  // per digit: limb sums (3 x 32-bit limbs) and count
 };
 

@@ -73,6 +73,7 @@ __global__ void k_reduce_init(ReduceState* st) {
     st->k_tie = 0;
     st->all_out = 0;
     st->blocks_done = 0;
+    st->n_sub = 0;
   }
 }
 
@@ -95,7 +96,20 @@ __global__ void k_absmax(const double* __restrict__ g, int n, const int* __restr
     m = t > m ? t : m;
   }
   bad = __any_sync(0xffffffffu, bad);
+  // one atomic per block (per-warp atomics on one address serialise at L2)
+  __shared__ unsigned long long w_m[32];
+  __shared__ int w_bad[32];
+  const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   if ((threadIdx.x & 31) == 0) {
+    w_m[warp] = m;
+    w_bad[warp] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) {
+      m = w_m[w] > m ? w_m[w] : m;
+      bad |= w_bad[w];
+    }
     if (m) atomicMax(&st->amax_bits, m);
     if (bad) atomicOr(&ds->nonfinite, 1);
   }
@@ -171,10 +185,17 @@ __device__ void choose_digit(ReduceState* st, double c_bound, int pass) {
 }
 
 // One pass: block histograms of the exact q-sums per byte of the key, merged
-// into st->hist; the last block to finish chooses the byte.
+// into st->hist; the last block to finish chooses the byte.  Passes 0 to 2
+// read every particle; pass 2 also lists the particles that match the two
+// chosen bytes (sign, exponent and the top mantissa bits: a sixteenth of a
+// binade of |Gamma|, a small fraction), and passes 3 to 7 read that list
+// only.  The sums are exact integers, so the list's order (atomic appends)
+// does not matter.
 __global__ void __launch_bounds__(256) k_reduce_pass(const double* __restrict__ g, int n, const int* __restrict__ n_dev,
-                                                     ReduceState* __restrict__ st, double c_bound, int pass) {
+                                                     ReduceState* __restrict__ st, double c_bound, int pass,
+                                                     int* __restrict__ sub) {
   if (n_dev) n = *n_dev;
+  if (pass >= 3) n = st->n_sub;
   __shared__ unsigned long long h[256][4];
   __shared__ bool last;
   for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b][0] = h[b][1] = h[b][2] = h[b][3] = 0;
@@ -194,10 +215,11 @@ __global__ void __launch_bounds__(256) k_reduce_pass(const double* __restrict__ 
     for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
       const long i = base + lane;
       bool pending = false;
-      int d = 0;
+      int d = 0, idx = 0;
       unsigned long long l0 = 0, l1 = 0, l2 = 0;
       if (i < n) {
-        const unsigned long long key = (unsigned long long)__double_as_longlong(g[i]) & 0x7FFFFFFFFFFFFFFFull;
+        idx = pass >= 3 ? sub[i] : (int)i;
+        const unsigned long long key = (unsigned long long)__double_as_longlong(g[idx]) & 0x7FFFFFFFFFFFFFFFull;
         if (pass == 0 || (key >> (shift + 8)) == prefix) {
           pending = true;
           d = (int)((key >> shift) & 0xFF);
@@ -208,6 +230,25 @@ __global__ void __launch_bounds__(256) k_reduce_pass(const double* __restrict__ 
         }
       }
       unsigned todo = __ballot_sync(0xffffffffu, pending);
+      if (pass == 2 && todo) {
+        // list the matches for the later passes (warp-aggregated append)
+        const int lead = __ffs(todo) - 1;
+        int slot0 = 0;
+        if (lane == lead) slot0 = atomicAdd(&st->n_sub, __popc(todo));
+        slot0 = __shfl_sync(0xffffffffu, slot0, lead);
+        if (pending) sub[slot0 + __popc(todo & ((1u << lane) - 1u))] = idx;
+      }
+      if (pass > 0) {
+        // bytes after the first are spread over many values: one shared
+        // atomic per lane and limb (equal bytes in a warp serialise, rarely)
+        if (pending) {
+          if (l0) atomicAdd(&h[d][0], l0);
+          if (l1) atomicAdd(&h[d][1], l1);
+          if (l2) atomicAdd(&h[d][2], l2);
+          atomicAdd(&h[d][3], 1ull);
+        }
+        todo = 0;
+      }
       while (todo) {
         const int leader = __ffs(todo) - 1;
         const int dl = __shfl_sync(0xffffffffu, d, leader);
@@ -298,7 +339,9 @@ cudaError_t reduce_select_dev(const double* gamma, int n_bound, const int* n_dev
   k_absmax<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, ds); note_launch();
   k_reduce_prepare<<<1, 1, 0, s>>>(st, c_bound); note_launch();
   for (int pass = 0; pass < 8; ++pass) {
-    k_reduce_pass<<<pblocks, 256, 0, s>>>(gamma, n_bound, n_dev, st, c_bound, pass); note_launch();
+    // the later passes read the short list of pass 2 (kept in tie_rank, free until the tie scan)
+    const int pb = pass >= 3 ? (pblocks < sm_count() ? pblocks : sm_count()) : pblocks;
+    k_reduce_pass<<<pb, 256, 0, s>>>(gamma, n_bound, n_dev, st, c_bound, pass, tie_rank); note_launch();
   }
   k_reduce_mark<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, diffused, tie_flag); note_launch();
   cudaError_t e = scan_exclusive_u8_dev(tie_flag, tie_rank, n_bound, n_dev, scan_tmp, s);

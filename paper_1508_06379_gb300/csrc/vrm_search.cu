@@ -176,12 +176,15 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
     sm[1] = make_int4(bj[4], bj[5], bj[6], bj[7]);
     local_max = cnt > local_max ? cnt : local_max;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    int t = __shfl_xor_sync(0xffffffffu, local_max, o);
-    local_max = t > local_max ? t : local_max;
+  // one atomic per block (one per warp on a single address serialises at L2)
+  local_max = (int)__reduce_max_sync(0xffffffffu, (unsigned)local_max);
+  __shared__ int w_max[kBlock / 32];
+  if ((threadIdx.x & 31) == 0) w_max[threadIdx.x >> 5] = local_max;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) local_max = w_max[w] > local_max ? w_max[w] : local_max;
+    if (local_max > 0) atomicMax(&ds->max_count, local_max);
   }
-  if ((threadIdx.x & 31) == 0 && local_max > 0) atomicMax(&ds->max_count, local_max);
 }
 
 // Segment mask only, for the particles with flag[i] set (insertion rounds).
