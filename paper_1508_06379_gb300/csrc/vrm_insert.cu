@@ -196,24 +196,24 @@ __global__ void k_cand_emit_dev(Consts c, const int* __restrict__ open, const St
   }
 }
 
-__global__ void k_copy_grid(const Grid* __restrict__ src, Grid* __restrict__ dst) { *dst = *src; }
-
-// Accepted count; capacity check (then the round appends nothing and the
-// loop stops with the overflow flag).
-__global__ void k_round_check(StepState* st, const int* __restrict__ apos) {
-  const int a = apos[st->n_cand];
-  st->accepted = a;
-  if ((long)st->n_cur + a > st->capacity) {
-    st->overflow = 1;
-    st->n_needed = st->n_cur + a;
-  }
-}
-
+// Appends the accepted proposals.  Every block checks the capacity itself
+// (accepted count apos[n_cand]); block 0 records the count and, when the
+// cloud would outgrow its buffers, the overflow flag (then the round appends
+// nothing and the loop stops).
 __global__ void k_append_dev(const double* __restrict__ cx, const double* __restrict__ cy,
                              const uint8_t* __restrict__ keep, const int* __restrict__ apos,
-                             const StepState* __restrict__ st, double* __restrict__ x, double* __restrict__ y) {
-  if (st->overflow) return;
+                             StepState* __restrict__ st, double* __restrict__ x, double* __restrict__ y) {
   const int n_cand = st->n_cand, n_cur = st->n_cur;
+  const int a = apos[n_cand];
+  const bool over = (long)n_cur + a > st->capacity;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->accepted = a;
+    if (over) {
+      st->overflow = 1;
+      st->n_needed = n_cur + a;
+    }
+  }
+  if (over) return;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_cand; t += (long)gridDim.x * blockDim.x)
     if (keep[t]) {
       x[n_cur + apos[t]] = cx[t];
@@ -269,19 +269,17 @@ cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const 
   k_cand_emit_dev<<<bo, kBlock, 0, s>>>(c, rb.open, st, mask, rb.cpos, x, y, rb.cx, rb.cy); note_launch();
   // proposals binned on the particle grid's geometry (cells >= R h; points
   // outside it clamp into the edge cells, which keeps 3 x 3 scans complete)
-  k_copy_grid<<<1, 1, 0, s>>>(pgrid, rb.cg.grid); note_launch();
-  e = grid_bin_dev(rb.cx, rb.cy, (int)cand_cap, &st->n_cand, rb.ncell_cap, rb.cg.grid, rb.cg.cell_key,
+  e = grid_bin_dev(rb.cx, rb.cy, (int)cand_cap, &st->n_cand, rb.ncell_cap, pgrid, rb.cg.cell_key,
                    rb.cg.cell_rank, rb.cg.cell_count, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
                    rb.cg.sorted_idx, rb.scan_tmp, s);
   if (e != cudaSuccess) return e;
-  k_conflict<<<bc, kBlock, 0, s>>>(c, rb.cg.grid, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
+  k_conflict<<<bc, kBlock, 0, s>>>(c, pgrid, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
                                    rb.cg.sorted_idx, &st->n_cand, rb.keep);
   note_launch();
   e = scan_exclusive_u8_dev(rb.keep, rb.apos, (int)cand_cap, &st->n_cand, rb.scan_tmp, s);
   if (e != cudaSuccess) return e;
-  k_round_check<<<1, 1, 0, s>>>(st, rb.apos); note_launch();
   k_append_dev<<<bc, kBlock, 0, s>>>(rb.cx, rb.cy, rb.keep, rb.apos, st, x, y); note_launch();
-  k_mask_update<<<bo, kBlock, 0, s>>>(c, rb.cg.grid, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
+  k_mask_update<<<bo, kBlock, 0, s>>>(c, pgrid, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
                                       rb.cg.sorted_idx, rb.keep, x, y, rb.open, &st->n_open, mask, rb.keep_flag);
   note_launch();
   e = scan_exclusive_u8_dev(rb.keep_flag, rb.keep_pos, cap, &st->n_open, rb.scan_tmp, s);

@@ -734,8 +734,11 @@ __global__ void __launch_bounds__(128, 3) k_lp_small32(Consts c, const double* _
           unc = unc || (el && !nzr && !(rhs[r] < kTolSnapLo - mb));
           const float inv = rcp_approx(a[r]);
           const float ratio = nzr ? rhs[r] * inv : 0.0f;
-          const float g = ea[r] * inv;  // relative bound of the pivot element (<= 1/2 used below)
-          const float er = nzr ? kCertSafety * __fmaf_rn(kRcpMul, ratio, (Eb[r] + 2.0f * (rhs[r] + Eb[r]) * g) * inv)
+          // relative bound of the pivot element; for g <= 1/2,
+          // |1/a - 1/a*| <= (g / a) / (1 - g) <= (g / a) (1 + 2 g)
+          const float g = ea[r] * inv;
+          const float gg = __fmaf_rn(2.0f * g, g, g);
+          const float er = nzr ? kCertSafety * __fmaf_rn(kRcpMul, ratio, __fmaf_rn(gg, rhs[r] + Eb[r], Eb[r]) * inv)
                                : 0.0f;
           unc = unc || (el && nzr && (!(g <= 0.5f) || !(er < 1.0e30f)));
           elig |= el ? 1u << r : 0u;
@@ -783,6 +786,7 @@ __global__ void __launch_bounds__(128, 3) k_lp_small32(Consts c, const double* _
         const float P = rcp_approx(piv);
         const float rho = pe * P;  // relative bound of the pivot; the bounds below take rho <= 1/2
         unc = unc || !(rho <= 0.5f);
+        const float rr = __fmaf_rn(2.0f * rho, rho, rho);  // rho / (1 - rho) <= rho (1 + 2 rho)
         if (unc) break;
         // pivot on (leave, q)
         float prow[8], Ep[8];
@@ -796,10 +800,10 @@ __global__ void __launch_bounds__(128, 3) k_lp_small32(Consts c, const double* _
           }
           const float pr = v * P, eP = e * P;
           prow[k] = (k == q) ? 1.0f : pr;
-          Ep[k] = (k == q) ? 0.0f : __fmaf_rn(kRcpMul, fabsf(pr), __fmaf_rn(2.0f * rho, fabsf(pr) + eP, eP));
+          Ep[k] = (k == q) ? 0.0f : __fmaf_rn(kRcpMul, fabsf(pr), __fmaf_rn(rr, fabsf(pr) + eP, eP));
         }
         const float prhs = prhs_raw * P, ebP = pebr * P;
-        const float Ebp = __fmaf_rn(kRcpMul, fabsf(prhs), __fmaf_rn(2.0f * rho, fabsf(prhs) + ebP, ebP));
+        const float Ebp = __fmaf_rn(kRcpMul, fabsf(prhs), __fmaf_rn(rr, fabsf(prhs) + ebP, ebP));
 #pragma unroll
         for (int r = 0; r < M; ++r) {
           const bool lr = (leave == r);
