@@ -10,6 +10,8 @@
 // no result depends on it (neighbour rows are sorted by index afterwards).
 #include <atomic>
 
+#include <cstddef>
+
 #include "vrm_internal.cuh"
 
 namespace vrm {
@@ -378,14 +380,25 @@ cudaError_t grid_build_dev(const double* x, const double* y, int n_bound, const 
                       sorted_loc, sorted_idx, scan_tmp, s);
 }
 
+// Zeroes the counts of the grid's own cells (g->ncell of them, at most the
+// capacity the buffers were sized for).
+__global__ void k_zero_cells(const Grid* __restrict__ g, int* __restrict__ cell_count) {
+  const int m = g->ncell;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x)
+    cell_count[t] = 0;
+}
+
 cudaError_t grid_bin_dev(const double* x, const double* y, int n_bound, const int* n_dev, int ncell_cap, const Grid* g,
                          int* cell_key, int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy,
                          float2* sorted_loc, int* sorted_idx, int* scan_tmp, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(cell_count, 0, sizeof(int) * (size_t)ncell_cap, s);
-  if (e != cudaSuccess) return e;
+  // only the grid's own cells (g->ncell, known on the device) are counted
+  // and scanned, not the whole capacity: a cloud of spacing h has about
+  // (extent / 2h)^2 cells, far fewer than the capacity's 2 per particle
+  const int* ncell_dev = reinterpret_cast<const int*>(reinterpret_cast<const char*>(g) + offsetof(Grid, ncell));
+  k_zero_cells<<<stream_grid(ncell_cap, 4), kBlock, 0, s>>>(g, cell_count); note_launch();
   const int b = stream_grid(n_bound, 8);
   k_bin<<<b, kBlock, 0, s>>>(x, y, n_bound, n_dev, g, cell_key, cell_rank, cell_count); note_launch();
-  e = scan_exclusive_i32(cell_count, cell_start, ncell_cap, scan_tmp, s);
+  cudaError_t e = scan_exclusive_i32_dev(cell_count, cell_start, ncell_cap, ncell_dev, scan_tmp, s);
   if (e != cudaSuccess) return e;
   k_scatter<<<b, kBlock, 0, s>>>(x, y, n_bound, n_dev, g, cell_key, cell_rank, cell_start, sorted_xy, sorted_loc,
                                  sorted_idx);
