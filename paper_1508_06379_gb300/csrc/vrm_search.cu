@@ -81,12 +81,20 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
         const float dub = (float)(bx - cx) - li.x;
         const int cell = by * g.nx + bx;
         const int q0 = cell_start[cell], q1 = cell_start[cell + 1];
+        // the next candidate's coordinates and index are loaded while this
+        // one is tested (the loop is bound by load latency)
+        float2 lnext = q0 < q1 ? sloc[q0] : make_float2(0.f, 0.f);
+        int jnext = q0 < q1 ? sidx[q0] : 0;
         for (int q = q0; q < q1; ++q) {
-          const float2 lj = sloc[q];
+          const float2 lj = lnext;
+          const int j = jnext;
+          if (q + 1 < q1) {
+            lnext = sloc[q + 1];
+            jnext = sidx[q + 1];
+          }
           const float du = dub + lj.x, dv = dvb + lj.y;
           const float d2f = __fmaf_rn(du, du, dv * dv);
           if (d2f < g.lo_out || d2f > g.hi_out) continue;
-          const int j = sidx[q];
           if (j == i) continue;
           const bool certain_in = d2f > g.lo_in && d2f < g.hi_in;
           int s = certain_in ? segment_or_ambiguous(du, dv, g.seg_eps) : -1;
