@@ -323,25 +323,52 @@ __device__ __forceinline__ void lp_finish(const Consts& c, int i, int code, cons
   if (code == 0) {
     double xB[M];
     if (!basis_solve<M>(basis, bxi, beta, xB)) code = 2;
-    double acc[M];
-#pragma unroll
-    for (int r = 0; r < M; ++r) acc[r] = dneg(b_of(r));
+    // Residual certificate.  When every basic variable is structural (the
+    // phase-I sum is then exactly 0) and none is snapped, the residual
+    // V f - b is the backward error of the LU solve: with partial pivoting
+    // (|L| <= 1, growth <= 2^(m-1) = 16) it is at most
+    // gamma_15 (5 * 16 max|B|) 5 max|x| = 400 gamma_15 max|B| max|x|,
+    // doubled for the multipliers and quotients taken through reciprocals
+    // (two roundings each), plus the residual's own rounding: below
+    // 1.4e-12 max|B| max|x|, so max|x| <= c.lp_xlim keeps it under
+    // 0.5e-10, and any FP64 evaluation of it (the oracle's) passes the
+    // 1e-10 test.  Then the residual is not computed.
+    bool all_struct = true, snapped = false;
+    unsigned long long xmax = 0;
 #pragma unroll
     for (int r = 0; r < M; ++r) {
-      if (basis[r] < M) {
-        wsum = __dadd_rn(wsum, xB[r]);
-      } else {
-        const double v = gt_pos(xB[r], kTolSnap) ? xB[r] : 0.0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == M + k) ? v : fv[k];
-        double col[M];
-        vcol<M>(bxi[r], beta[r], col);
-#pragma unroll
-        for (int q = 0; q < M; ++q) acc[q] = __fma_rn(col[q], v, acc[q]);
-      }
+      all_struct = all_struct && basis[r] >= M;
+      snapped = snapped || !gt_pos(xB[r], kTolSnap);
+      const unsigned long long b = (unsigned long long)dbits(xB[r]) & 0x7FFFFFFFFFFFFFFFull;
+      xmax = b > xmax ? b : xmax;
     }
+    const bool certified = M == 5 && all_struct && !snapped && xmax < (unsigned long long)dbits(c.lp_xlim);
+    if (certified) {
 #pragma unroll
-    for (int r = 0; r < M; ++r) rmax = abs_gt(acc[r], rmax) ? fabs(acc[r]) : rmax;
+      for (int r = 0; r < M; ++r)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == M + k) ? xB[r] : fv[k];
+    } else {
+      double acc[M];
+#pragma unroll
+      for (int r = 0; r < M; ++r) acc[r] = dneg(b_of(r));
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        if (basis[r] < M) {
+          wsum = __dadd_rn(wsum, xB[r]);
+        } else {
+          const double v = gt_pos(xB[r], kTolSnap) ? xB[r] : 0.0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == M + k) ? v : fv[k];
+          double col[M];
+          vcol<M>(bxi[r], beta[r], col);
+#pragma unroll
+          for (int q = 0; q < M; ++q) acc[q] = __fma_rn(col[q], v, acc[q]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < M; ++r) rmax = abs_gt(acc[r], rmax) ? fabs(acc[r]) : rmax;
+    }
   }
   const bool feasible = code == 0 && !gt_pos(wsum, kTolPhase1) && !gt_pos(rmax, kTolResid);
   tl.maxpiv = it > tl.maxpiv ? it : tl.maxpiv;
