@@ -119,7 +119,7 @@ __global__ void k_scan_tile_sums(int* __restrict__ tile_sums, int n, const int* 
 
 template <typename T>
 __global__ void k_tile_scan(const T* __restrict__ in, int n, const int* __restrict__ n_dev,
-                            const int* __restrict__ tile_sums, int* __restrict__ out) {
+                            const int* __restrict__ tile_sums, int* __restrict__ out, int* __restrict__ total_out) {
   if (n_dev) n = *n_dev;
   const int ntiles = (n + kScanTile - 1) / kScanTile;
   __shared__ int total;
@@ -139,7 +139,10 @@ __global__ void k_tile_scan(const T* __restrict__ in, int n, const int* __restri
       ex += v[k];
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = tile_sums[ntiles];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    out[n] = tile_sums[ntiles];
+    if (total_out) *total_out = tile_sums[ntiles];
+  }
 }
 
 // Tile scan that forms the tile's exclusive prefix itself: the block sums
@@ -149,11 +152,15 @@ __global__ void k_tile_scan(const T* __restrict__ in, int n, const int* __restri
 constexpr int kFusedScanTiles = 4096;
 template <typename T>
 __global__ void k_tile_scan_fused(const T* __restrict__ in, int n, const int* __restrict__ n_dev,
-                                  const int* __restrict__ tile_sums, int* __restrict__ out) {
+                                  const int* __restrict__ tile_sums, int* __restrict__ out,
+                                  int* __restrict__ total_out) {
   if (n_dev) n = *n_dev;
   const int ntiles = (n + kScanTile - 1) / kScanTile;
   __shared__ int total;
-  if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
+  if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    out[0] = 0;
+    if (total_out) *total_out = 0;
+  }
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int part = 0;
     for (int k = threadIdx.x; k < t; k += kScanThreads) part += tile_sums[k];
@@ -173,7 +180,10 @@ __global__ void k_tile_scan_fused(const T* __restrict__ in, int n, const int* __
       if (base + k < n) out[base + k] = ex;
       ex += v[k];
     }
-    if (t == ntiles - 1 && threadIdx.x == 0) out[n] = pre + total;
+    if (t == ntiles - 1 && threadIdx.x == 0) {
+      out[n] = pre + total;
+      if (total_out) *total_out = pre + total;
+    }
     __syncthreads();
   }
 }
@@ -185,15 +195,20 @@ static int scan_grid(int n_bound) {
 }
 
 template <typename T>
-static cudaError_t scan_impl(const T* in, int* out, int n, const int* n_dev, int* tmp, cudaStream_t s) {
-  if (!n_dev && n <= 0) return cudaMemsetAsync(out, 0, sizeof(int), s);
+static cudaError_t scan_impl(const T* in, int* out, int n, const int* n_dev, int* tmp, cudaStream_t s,
+                             int* total_out = nullptr) {
+  if (!n_dev && n <= 0) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int), s);
+    if (e == cudaSuccess && total_out) e = cudaMemsetAsync(total_out, 0, sizeof(int), s);
+    return e;
+  }
   const int g = scan_grid(n);
   k_tile_sums<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp); note_launch();
   if ((n + kScanTile - 1) / kScanTile <= kFusedScanTiles) {
-    k_tile_scan_fused<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp, out); note_launch();
+    k_tile_scan_fused<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp, out, total_out); note_launch();
   } else {
     k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(tmp, n, n_dev); note_launch();
-    k_tile_scan<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp, out); note_launch();
+    k_tile_scan<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp, out, total_out); note_launch();
   }
   return cudaGetLastError();
 }
@@ -204,8 +219,9 @@ cudaError_t scan_exclusive_i32(const int* in, int* out, int n, int* tmp, cudaStr
 cudaError_t scan_exclusive_u8(const uint8_t* in, int* out, int n, int* tmp, cudaStream_t s) {
   return scan_impl<uint8_t>(in, out, n, nullptr, tmp, s);
 }
-cudaError_t scan_exclusive_i32_dev(const int* in, int* out, int n_bound, const int* n_dev, int* tmp, cudaStream_t s) {
-  return scan_impl<int>(in, out, n_bound, n_dev, tmp, s);
+cudaError_t scan_exclusive_i32_dev(const int* in, int* out, int n_bound, const int* n_dev, int* tmp, cudaStream_t s,
+                                   int* total_out) {
+  return scan_impl<int>(in, out, n_bound, n_dev, tmp, s, total_out);
 }
 cudaError_t scan_exclusive_u8_dev(const uint8_t* in, int* out, int n_bound, const int* n_dev, int* tmp,
                                   cudaStream_t s) {

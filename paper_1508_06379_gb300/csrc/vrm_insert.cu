@@ -175,8 +175,6 @@ __global__ void k_cand_count_dev(const int* __restrict__ open, const StepState* 
     cnt[t] = __popc((~(unsigned)mask[open[t]]) & 0xFFu);
 }
 
-__global__ void k_set_ncand(StepState* st, const int* __restrict__ cpos) { st->n_cand = cpos[st->n_open]; }
-
 __global__ void k_cand_emit_dev(Consts c, const int* __restrict__ open, const StepState* __restrict__ st,
                                 const uint8_t* __restrict__ mask, const int* __restrict__ cpos,
                                 const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ cx,
@@ -263,9 +261,8 @@ cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const 
   const long cand_cap = 8L * cap;
   const int bc = blocks_for((int)(cand_cap < 0x7FFFFFFF ? cand_cap : 0x7FFFFFFF));
   k_cand_count_dev<<<bo, kBlock, 0, s>>>(rb.open, st, mask, rb.cnt); note_launch();
-  cudaError_t e = scan_exclusive_i32_dev(rb.cnt, rb.cpos, cap, &st->n_open, rb.scan_tmp, s);
+  cudaError_t e = scan_exclusive_i32_dev(rb.cnt, rb.cpos, cap, &st->n_open, rb.scan_tmp, s, &st->n_cand);
   if (e != cudaSuccess) return e;
-  k_set_ncand<<<1, 1, 0, s>>>(st, rb.cpos); note_launch();
   k_cand_emit_dev<<<bo, kBlock, 0, s>>>(c, rb.open, st, mask, rb.cpos, x, y, rb.cx, rb.cy); note_launch();
   // proposals binned on the particle grid's geometry (cells >= R h; points
   // outside it clamp into the edge cells, which keeps 3 x 3 scans complete)

@@ -219,7 +219,9 @@ cudaError_t grid_bin_dev(const double* x, const double* y, int n_bound, const in
 // Exclusive scan of n ints into out[0..n] (out[n] = total).
 cudaError_t scan_exclusive_i32(const int* in, int* out, int n, int* tmp, cudaStream_t s);
 // Scans and compaction with the count in device memory (*n_dev <= n_bound).
-cudaError_t scan_exclusive_i32_dev(const int* in, int* out, int n_bound, const int* n_dev, int* tmp, cudaStream_t s);
+// total_out (optional, device): receives the total, as out[n] does.
+cudaError_t scan_exclusive_i32_dev(const int* in, int* out, int n_bound, const int* n_dev, int* tmp, cudaStream_t s,
+                                   int* total_out = nullptr);
 cudaError_t scan_exclusive_u8_dev(const uint8_t* in, int* out, int n_bound, const int* n_dev, int* tmp,
                                   cudaStream_t s);
 cudaError_t compact_flags_dev(const uint8_t* flags, int n_bound, const int* n_dev, int* list, int* count, int* pos,
