@@ -6,11 +6,13 @@
 // computed as a gather, one thread per target j and no floating-point
 // atomics: the annulus relation is symmetric (dx and dy only change sign when
 // i and j swap, so d2 is bit-identical), hence every source i whose stencil
-// contains j is in j's neighbour row, and the row is sorted by index.  The
-// terms are added in ascending i with the self term f~_jj Gamma_j at i = j,
+// contains j is in j's neighbour row (in any order).  The terms are added in
+// ascending i with the self term f~_jj Gamma_j at i = j,
 // each product and sum rounded separately, which fixes the result bit for
 // bit given the weights.  Targets are visited in cell order so that the
 // stencils of the neighbours of a warp's targets share cache lines.
+#include <climits>
+
 #include "vrm_internal.cuh"
 
 namespace vrm {
@@ -52,14 +54,11 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
     const double gj = j < n_gamma ? gamma[j] : 0.0;
     const Acc selfv = self_src ? mul_acc<Acc>(fii[j], gj) : Acc(0);
     // integer pass: which row entries are sources whose stencil holds j (and
-    // in which slot, 4 bits per entry), and where the self term goes (before
-    // the first i > j)
+    // in which slot, 4 bits per entry)
     unsigned match = 0;
     unsigned long long slot_lo = 0, slot_hi = 0;
-    int selfpos = cnt;
     for (int t = 0; t < cnt; ++t) {
       const int i = row[t];
-      if (selfpos == cnt && i > j) selfpos = t;
       if (i >= n_gamma || !diffused[i]) continue;
       const int4* cr = reinterpret_cast<const int4*>(cols + (size_t)i * W);
       int slot = -1;
@@ -78,18 +77,28 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
       else
         slot_hi |= (unsigned long long)slot << (4 * (t - 16));
     }
-    // FP64 (or fp32) pass over the matches only, in ascending i
+    // FP64 (or fp32) pass over the matches only, in ascending i (rows may
+    // be in visiting order: the next match is the remaining one of smallest
+    // index), the self term before the first i > j
     Acc acc = Acc(0);
     bool self_done = !self_src;
-    for (unsigned rest = match; rest; rest &= rest - 1) {
-      const int t = __ffs(rest) - 1;
-      if (!self_done && t >= selfpos) {
+    for (unsigned rest = match; rest;) {
+      int tb = 0, ib = INT_MAX;
+      for (unsigned r2 = rest; r2; r2 &= r2 - 1) {
+        const int t = __ffs(r2) - 1;
+        const int i = row[t];
+        if (i < ib) {
+          ib = i;
+          tb = t;
+        }
+      }
+      rest &= ~(1u << tb);
+      if (!self_done && ib > j) {
         acc = add_acc(acc, selfv);
         self_done = true;
       }
-      const int i = row[t];
-      const int slot = (int)(((t < 16 ? slot_lo >> (4 * t) : slot_hi >> (4 * (t - 16)))) & 15ull);
-      acc = add_acc(acc, mul_acc<Acc>(f[(size_t)i * W + slot], gamma[i]));
+      const int slot = (int)(((tb < 16 ? slot_lo >> (4 * tb) : slot_hi >> (4 * (tb - 16)))) & 15ull);
+      acc = add_acc(acc, mul_acc<Acc>(f[(size_t)ib * W + slot], gamma[ib]));
     }
     if (!self_done) acc = add_acc(acc, selfv);
     const double dg = __dmul_rn(c.nu_over_h2, (double)acc);

@@ -14,10 +14,13 @@
 // undecided cases (rare on jittered clouds, frequent on exact lattices) take
 // the FP64 definition, so the result is bit-identical to it.
 //
-// The row is kept sorted by index in a per-thread buffer of KCAP entries (the
-// row_cap smallest indices survive; rows are k_cap apart); the closest
-// particle of every segment is tracked in registers with ties to the smaller
-// index.
+// The row is kept in a per-thread buffer of KCAP entries (rows are k_cap
+// apart): sorted by index for the library's neighbourhood calls, in visiting
+// order inside a step (SORTED = false: the application orders the few
+// matches itself, and a sorted insertion per member was a third of the
+// kernel); a row that overflows keeps the row_cap smallest indices either
+// way.  The closest particle of every segment is tracked in shared memory
+// with ties to the smaller index.
 #include "vrm_internal.cuh"
 
 namespace vrm {
@@ -38,7 +41,7 @@ __device__ __forceinline__ int exact_member(const Consts& c, const double2& pi, 
 // distance and its particle, and a flag `amb` set when another member of
 // the segment lies within 2 bands of it (then the FP32 order may differ from
 // the FP64 order, and a second pass decides that segment exactly).
-template <int KCAP>
+template <int KCAP, bool SORTED>
 __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __restrict__ gp,
                                                        const int* __restrict__ cell_start,
                                                        const double2* __restrict__ sxy,
@@ -114,13 +117,30 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
             s_bf[s][tx] = d2f;
             s_bj[s][tx] = j;
           }
-          if (cnt < k_cap || j < list[k_cap - 1]) {
-            int pos = cnt < k_cap ? cnt : k_cap - 1;
-            while (pos > 0 && list[pos - 1] > j) {
-              list[pos] = list[pos - 1];
-              --pos;
+          if (SORTED || cnt >= k_cap) {
+            if (!SORTED && cnt == k_cap) {
+              // the row overflows (rare): order the entries kept so far, so
+              // that it keeps the k_cap smallest indices like a sorted row
+              for (int a = 1; a < k_cap; ++a) {
+                const int v = list[a];
+                int b = a;
+                while (b > 0 && list[b - 1] > v) {
+                  list[b] = list[b - 1];
+                  --b;
+                }
+                list[b] = v;
+              }
             }
-            list[pos] = j;
+            if (cnt < k_cap || j < list[k_cap - 1]) {
+              int pos = cnt < k_cap ? cnt : k_cap - 1;
+              while (pos > 0 && list[pos - 1] > j) {
+                list[pos] = list[pos - 1];
+                --pos;
+              }
+              list[pos] = j;
+            }
+          } else {
+            list[cnt] = j;  // unsorted row: append in visiting order
           }
           ++cnt;
         }
@@ -249,19 +269,21 @@ __global__ void __launch_bounds__(kBlock) k_search_masks(Consts c, const Grid* _
 cudaError_t search_all_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
                            const float2* sorted_loc, const int* sorted_idx, int n_bound, const int* n_dev,
                            int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small, DevStats* ds,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool sorted) {
   if (n_bound <= 0) return cudaSuccess;
   const int tb = c.search_block;
   const int blocks = (int)(((long)n_bound + tb - 1) / tb);
-  if (c.row_cap <= 16)
-    k_search_all<16><<<blocks, tb, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n_bound, n_dev,
-                                           nbr_count, nbr_idx, seg_mask, small, ds);
-  else if (c.row_cap <= 24)
-    k_search_all<24><<<blocks, tb, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n_bound, n_dev,
-                                           nbr_count, nbr_idx, seg_mask, small, ds);
-  else
-    k_search_all<VRM_KCAP_MAX><<<blocks, tb, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n_bound,
-                                                     n_dev, nbr_count, nbr_idx, seg_mask, small, ds);
+#define VRM_SEARCH_LAUNCH(K, S)                                                                                     \
+  k_search_all<K, S><<<blocks, tb, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n_bound, n_dev,    \
+                                           nbr_count, nbr_idx, seg_mask, small, ds)
+  if (c.row_cap <= 16) {
+    if (sorted) VRM_SEARCH_LAUNCH(16, true); else VRM_SEARCH_LAUNCH(16, false);
+  } else if (c.row_cap <= 24) {
+    if (sorted) VRM_SEARCH_LAUNCH(24, true); else VRM_SEARCH_LAUNCH(24, false);
+  } else {
+    if (sorted) VRM_SEARCH_LAUNCH(VRM_KCAP_MAX, true); else VRM_SEARCH_LAUNCH(VRM_KCAP_MAX, false);
+  }
+#undef VRM_SEARCH_LAUNCH
   note_launch();
   return cudaGetLastError();
 }
@@ -270,7 +292,7 @@ cudaError_t search_all(const Consts& c, const Grid* g, const int* cell_start, co
                        const float2* sorted_loc, const int* sorted_idx, int n, int* nbr_count, int* nbr_idx,
                        uint8_t* seg_mask, int* small, DevStats* ds, cudaStream_t s) {
   return search_all_dev(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n, nullptr, nbr_count, nbr_idx,
-                        seg_mask, small, ds, s);
+                        seg_mask, small, ds, s, true);
 }
 
 cudaError_t search_masks_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
