@@ -334,10 +334,10 @@ cudaError_t enqueue_stage_weights(vrm_ctx* ctx, const double* x, const double* y
                           s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
                           st)) != cudaSuccess)
     return e;
-  // rows in visiting order unless the learned path reads them (its slot
-  // order breaks ties by row position)
+  // rows in visiting order (the application and the learned slots order
+  // their entries themselves)
   if ((e = search_all_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, cap, n_cur, s.nbr_count,
-                          s.nbr_idx, s.seg_mask, s.small, s.ds, st, ctx->mlp != nullptr)) != cudaSuccess)
+                          s.nbr_idx, s.seg_mask, s.small, s.ds, st, false)) != cudaSuccess)
     return e;
   const int* lp_list = s.dlist;
   const int* lp_count = s.counters + 0;
@@ -605,10 +605,10 @@ cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const doub
                           s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
                           st)) != cudaSuccess)
     return e;
-  // rows in visiting order unless the learned path reads them (its slot
-  // order breaks ties by row position)
+  // rows in visiting order (the application and the learned slots order
+  // their entries themselves)
   if ((e = search_all_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, cap, n_cur, s.nbr_count,
-                          s.nbr_idx, s.seg_mask, s.small, s.ds, st, ctx->mlp != nullptr)) != cudaSuccess)
+                          s.nbr_idx, s.seg_mask, s.small, s.ds, st, false)) != cudaSuccess)
     return e;
   if ((e = mark(ctx, VRM_STAGE_LP_SMALL, st)) != cudaSuccess) return e;
   const int* lp_list = s.dlist;

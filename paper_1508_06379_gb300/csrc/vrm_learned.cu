@@ -61,7 +61,7 @@ __global__ void k_mirror(const double* __restrict__ x, const double* __restrict_
 // key is one 32-bit word, segment << 28 | bits(d2) >> 3 (d2 >= 0, so its bit
 // pattern orders like the value; the 3 lowest mantissa bits are dropped),
 // with the index breaking ties: the sort runs on the integer pipes, on one
-// 64-bit value per lane.
+// 64-bit value per lane, and does not depend on the row's order.
 __global__ void k_features(Consts c, const float2* __restrict__ xyf,
                            const int* __restrict__ list, const int* __restrict__ list_count, int m_bound,
                            const int* __restrict__ nbr_count, const int* __restrict__ nbr_idx,
@@ -86,9 +86,9 @@ __global__ void k_features(Consts c, const float2* __restrict__ xyf,
       const float d2 = dist2f(fdx, fdy);
       key = ((unsigned)segment_of(fdx, fdy) << 28) | (__float_as_uint(d2) >> 3);
     }
-    // the row holds ascending indices, so the lane breaks ties as the index
-    // does: one distinct 64-bit value per lane, (key << 5) | lane
-    unsigned long long v = ((unsigned long long)key << 5) | (unsigned)lane;
+    // ties are broken by the index (rows may be in any order): one distinct
+    // 64-bit value per lane, (key << 32) | j
+    unsigned long long v = ((unsigned long long)key << 32) | (unsigned)j;
     // a row of K <= 8 (16) entries sits in lanes 0..7 (0..15): a bitonic
     // network of that width sorts it (lanes past it keep their empties)
     const int width = K <= 8 ? 8 : K <= 16 ? 16 : 32;
@@ -102,11 +102,14 @@ __global__ void k_features(Consts c, const float2* __restrict__ xyf,
         v = take ? ov : v;
       }
     }
-    const int src = (int)(v & 31u);
     const bool valid = lane < K;
-    j = __shfl_sync(0xffffffffu, j, src);
-    const float sdx = __shfl_sync(0xffffffffu, fdx, src);
-    const float sdy = __shfl_sync(0xffffffffu, fdy, src);
+    j = (int)(unsigned)(v & 0xFFFFFFFFull);
+    float sdx = 0.0f, sdy = 0.0f;
+    if (valid) {  // the sorted entry's offset, recomputed as above
+      const float2 pj = xyf[j], pi = xyf[i];
+      sdx = __fsub_rn(pj.x, pi.x);
+      sdy = __fsub_rn(pj.y, pi.y);
+    }
     __nv_bfloat16* row = X + (size_t)t * kRow;
     row[lane] = __float2bfloat16_rn(valid ? __fmul_rn(sdx, inv_hf) : 0.0f);
     row[kSlots + lane] = __float2bfloat16_rn(valid ? __fmul_rn(sdy, inv_hf) : 0.0f);
