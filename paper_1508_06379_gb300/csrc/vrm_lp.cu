@@ -651,6 +651,198 @@ __device__ __forceinline__ void lp_columns32(const double* __restrict__ x, const
   sort8(cd2, cj, xs, es);
 }
 
+// The certified binary32 phase-I pivots of one LP whose columns have the
+// binary32 offsets xs, es: the final basis, the pivot count and the code
+// (2: pivot cap or no eligible row), or `unc` when a decision could not be
+// certified (the LP then goes to the FP64 re-run).
+template <int M>
+__device__ __forceinline__ void lp_pivots32(const float (&xs)[8], const float (&es)[8], int (&basis)[M], int& it,
+                                            int& code, bool& unc) {
+  // T, rhs: tableau; E, Eb: bounds on their distance from exact; d, Ed:
+  // phase-I reduced costs and bounds
+  float T[M][8], E[M][8], d[8], Ed[8], rhs[M], Eb[M];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float v[M] = {xs[k], es[k], __fmul_rn(xs[k], xs[k]), __fmul_rn(xs[k], es[k]), __fmul_rn(es[k], es[k])};
+    float sum = 0.0f, sa = 0.0f, se = 0.0f;
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+      T[r][k] = v[r];
+      // offsets within 3.01 u of the FP64 ones; their products within 7.01 u
+      E[r][k] = (r < 2 ? 3.01f : 7.01f) * kU32 * fabsf(v[r]);
+      sum = __fadd_rn(sum, v[r]);
+      sa += fabsf(v[r]);
+      se += E[r][k];
+    }
+    d[k] = -sum;
+    Ed[k] = __fmaf_rn(4.01f * kU32, sa, se);
+  }
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+    rhs[r] = (r == 2 || r == 4) ? 2.0f : 0.0f;
+    Eb[r] = 0.0f;
+  }
+  unsigned basic = 0;
+  int n_art = M;
+  for (;;) {
+    if (unc || n_art == 0) break;
+    // entering column: the lowest k certainly below -tol; a lower column
+    // that is not certainly above it makes the choice uncertain
+    unsigned yes = 0, un = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float mg = kCertSafety * Ed[k];
+      const bool nb = !((basic >> k) & 1u);
+      yes |= (nb && d[k] < -kTolPriceHi - mg) ? 1u << k : 0u;
+      un |= (nb && !(d[k] < -kTolPriceHi - mg) && !(d[k] > -kTolPriceLo + mg)) ? 1u << k : 0u;
+    }
+    if (yes == 0) {
+      unc = un != 0;
+      break;
+    }
+    const int q = __ffs(yes) - 1;
+    unc = (un & ((1u << q) - 1u)) != 0;
+    if (it == kPivotCap) {
+      code = 2;
+      break;
+    }
+    float a[M], ea[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+      float v = T[r][0], e = E[r][0];
+#pragma unroll
+      for (int k = 1; k < 8; ++k) {
+        v = (q == k) ? T[r][k] : v;
+        e = (q == k) ? E[r][k] : e;
+      }
+      a[r] = v;
+      ea[r] = e;
+    }
+    // eligible rows, zero basic values, ratios with bounds
+    unsigned elig = 0;
+    float lo[M], hi[M], thlo = 3.0e38f, thhi = 3.0e38f;
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+      const float mg = kCertSafety * ea[r];
+      const bool el = a[r] > kTolPivotHi + mg;
+      unc = unc || (!el && !(a[r] < kTolPivotLo - mg));
+      const float mb = kCertSafety * Eb[r];
+      const bool nzr = rhs[r] > kTolSnapHi + mb;
+      unc = unc || (el && !nzr && !(rhs[r] < kTolSnapLo - mb));
+      const float inv = rcp_approx(a[r]);
+      const float ratio = nzr ? rhs[r] * inv : 0.0f;
+      // relative bound of the pivot element; for g <= 1/2,
+      // |1/a - 1/a*| <= (g / a) / (1 - g) <= (g / a) (1 + 2 g)
+      const float g = ea[r] * inv;
+      const float gg = __fmaf_rn(2.0f * g, g, g);
+      const float er = nzr ? kCertSafety * __fmaf_rn(kRcpMul, ratio, __fmaf_rn(gg, rhs[r] + Eb[r], Eb[r]) * inv)
+                           : 0.0f;
+      unc = unc || (el && nzr && (!(g <= 0.5f) || !(er < 1.0e30f)));
+      elig |= el ? 1u << r : 0u;
+      lo[r] = el ? fmaxf(ratio - er, 0.0f) : 3.0e38f;  // exact ratios of eligible rows are >= 0
+      hi[r] = el ? ratio + er : 3.0e38f;
+      thlo = fminf(thlo, lo[r]);
+      thhi = fminf(thhi, hi[r]);
+    }
+    if (elig == 0) {
+      code = 2;
+      break;
+    }
+    // a row can tie with the minimum only if its interval reaches the
+    // largest possible tie limit theta + 1e-12 max(theta, 1)
+    const float l0 = __fmaf_rn(kTolTieLo, fmaxf(thlo, 1.0f), thlo);
+    const float l1 = __fmaf_rn(kTolTieHi, fmaxf(thhi, 1.0f), thhi);
+    const float limlo = __fmaf_rn(-4.0f * kU32, fabsf(l0), l0);
+    const float limhi = __fmaf_rn(4.0f * kU32, fabsf(l1), l1);
+    unsigned poss = 0, tied = 0;
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+      poss |= (((elig >> r) & 1u) && lo[r] <= limhi) ? 1u << r : 0u;
+      tied |= (hi[r] <= limlo) ? 1u << r : 0u;
+    }
+    if (__popc(poss) == 1)
+      tied = poss;
+    else
+      unc = unc || (poss & ~tied) != 0;
+    tied &= poss;
+    int leave = 0, lbas = INT_MAX;
+#pragma unroll
+    for (int r = 0; r < M; ++r)
+      if (((tied >> r) & 1u) && basis[r] < lbas) {
+        leave = r;
+        lbas = basis[r];
+      }
+    float piv = a[0], pe = ea[0], prhs_raw = rhs[0], pebr = Eb[0];
+#pragma unroll
+    for (int r = 1; r < M; ++r) {
+      piv = (leave == r) ? a[r] : piv;
+      pe = (leave == r) ? ea[r] : pe;
+      prhs_raw = (leave == r) ? rhs[r] : prhs_raw;
+      pebr = (leave == r) ? Eb[r] : pebr;
+    }
+    const float P = rcp_approx(piv);
+    const float rho = pe * P;  // relative bound of the pivot; the bounds below take rho <= 1/2
+    unc = unc || !(rho <= 0.5f);
+    const float rr = __fmaf_rn(2.0f * rho, rho, rho);  // rho / (1 - rho) <= rho (1 + 2 rho)
+    if (unc) break;
+    // pivot on (leave, q)
+    float prow[8], Ep[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float v = T[0][k], e = E[0][k];
+#pragma unroll
+      for (int r = 1; r < M; ++r) {
+        v = (leave == r) ? T[r][k] : v;
+        e = (leave == r) ? E[r][k] : e;
+      }
+      const float pr = v * P, eP = e * P;
+      prow[k] = (k == q) ? 1.0f : pr;
+      Ep[k] = (k == q) ? 0.0f : __fmaf_rn(kRcpMul, fabsf(pr), __fmaf_rn(rr, fabsf(pr) + eP, eP));
+    }
+    const float prhs = prhs_raw * P, ebP = pebr * P;
+    const float Ebp = __fmaf_rn(kRcpMul, fabsf(prhs), __fmaf_rn(rr, fabsf(prhs) + ebP, ebP));
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+      const bool lr = (leave == r);
+      const float ar = lr ? -1.0f : a[r];
+      const float ear = lr ? 0.0f : ea[r];
+      const float aar = fabsf(ar) + ear;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        // column q of the other rows becomes an exact 0 (its bound stays, conservatively)
+        const float tn = __fmaf_rn(-ar, prow[k], lr ? 0.0f : T[r][k]);
+        const float en = __fmaf_rn(kU32, fabsf(tn), __fmaf_rn(aar, Ep[k], __fmaf_rn(ear, fabsf(prow[k]), E[r][k])));
+        T[r][k] = tn;
+        E[r][k] = lr ? Ep[k] : en;
+      }
+      const float rn = __fmaf_rn(-ar, prhs, lr ? 0.0f : rhs[r]);
+      const float ebn = __fmaf_rn(kU32, fabsf(rn), __fmaf_rn(aar, Ebp, __fmaf_rn(ear, fabsf(prhs), Eb[r])));
+      rhs[r] = rn;
+      Eb[r] = lr ? Ebp : ebn;
+    }
+    float dq = d[0], edq = Ed[0];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+      dq = (q == k) ? d[k] : dq;
+      edq = (q == k) ? Ed[k] : edq;
+    }
+    const float adq = fabsf(dq) + edq;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      d[k] = __fmaf_rn(-dq, prow[k], d[k]);
+      Ed[k] = __fmaf_rn(kU32, fabsf(d[k]), __fmaf_rn(adq, Ep[k], __fmaf_rn(edq, fabsf(prow[k]), Ed[k])));
+    }
+    if (lbas >= M)
+      basic &= ~(1u << (lbas - M));
+    else
+      --n_art;
+    basic |= 1u << q;
+#pragma unroll
+    for (int r = 0; r < M; ++r) basis[r] = (leave == r) ? M + q : basis[r];
+    ++it;
+  }
+}
+
 template <int M, int W>
 __global__ void __launch_bounds__(128, 3) k_lp_small32(Consts c, const double* __restrict__ x,
                                                     const double* __restrict__ y, const int* __restrict__ list,
@@ -688,189 +880,7 @@ __global__ void __launch_bounds__(128, 3) k_lp_small32(Consts c, const double* _
 #pragma unroll
         for (int k = 0; k < 8; ++k) s_cj[k][threadIdx.x] = cj[k];
       }
-      // T, rhs: tableau; E, Eb: bounds on their distance from exact; d, Ed:
-      // phase-I reduced costs and bounds
-      float T[M][8], E[M][8], d[8], Ed[8], rhs[M], Eb[M];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const float v[M] = {xs[k], es[k], __fmul_rn(xs[k], xs[k]), __fmul_rn(xs[k], es[k]), __fmul_rn(es[k], es[k])};
-        float sum = 0.0f, sa = 0.0f, se = 0.0f;
-#pragma unroll
-        for (int r = 0; r < M; ++r) {
-          T[r][k] = v[r];
-          // offsets within 3.01 u of the FP64 ones; their products within 7.01 u
-          E[r][k] = (r < 2 ? 3.01f : 7.01f) * kU32 * fabsf(v[r]);
-          sum = __fadd_rn(sum, v[r]);
-          sa += fabsf(v[r]);
-          se += E[r][k];
-        }
-        d[k] = -sum;
-        Ed[k] = __fmaf_rn(4.01f * kU32, sa, se);
-      }
-#pragma unroll
-      for (int r = 0; r < M; ++r) {
-        rhs[r] = (r == 2 || r == 4) ? 2.0f : 0.0f;
-        Eb[r] = 0.0f;
-      }
-      unsigned basic = 0;
-      int n_art = M;
-      for (;;) {
-        if (unc || n_art == 0) break;
-        // entering column: the lowest k certainly below -tol; a lower column
-        // that is not certainly above it makes the choice uncertain
-        unsigned yes = 0, un = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const float mg = kCertSafety * Ed[k];
-          const bool nb = !((basic >> k) & 1u);
-          yes |= (nb && d[k] < -kTolPriceHi - mg) ? 1u << k : 0u;
-          un |= (nb && !(d[k] < -kTolPriceHi - mg) && !(d[k] > -kTolPriceLo + mg)) ? 1u << k : 0u;
-        }
-        if (yes == 0) {
-          unc = un != 0;
-          break;
-        }
-        const int q = __ffs(yes) - 1;
-        unc = (un & ((1u << q) - 1u)) != 0;
-        if (it == kPivotCap) {
-          code = 2;
-          break;
-        }
-        float a[M], ea[M];
-#pragma unroll
-        for (int r = 0; r < M; ++r) {
-          float v = T[r][0], e = E[r][0];
-#pragma unroll
-          for (int k = 1; k < 8; ++k) {
-            v = (q == k) ? T[r][k] : v;
-            e = (q == k) ? E[r][k] : e;
-          }
-          a[r] = v;
-          ea[r] = e;
-        }
-        // eligible rows, zero basic values, ratios with bounds
-        unsigned elig = 0;
-        float lo[M], hi[M], thlo = 3.0e38f, thhi = 3.0e38f;
-#pragma unroll
-        for (int r = 0; r < M; ++r) {
-          const float mg = kCertSafety * ea[r];
-          const bool el = a[r] > kTolPivotHi + mg;
-          unc = unc || (!el && !(a[r] < kTolPivotLo - mg));
-          const float mb = kCertSafety * Eb[r];
-          const bool nzr = rhs[r] > kTolSnapHi + mb;
-          unc = unc || (el && !nzr && !(rhs[r] < kTolSnapLo - mb));
-          const float inv = rcp_approx(a[r]);
-          const float ratio = nzr ? rhs[r] * inv : 0.0f;
-          // relative bound of the pivot element; for g <= 1/2,
-          // |1/a - 1/a*| <= (g / a) / (1 - g) <= (g / a) (1 + 2 g)
-          const float g = ea[r] * inv;
-          const float gg = __fmaf_rn(2.0f * g, g, g);
-          const float er = nzr ? kCertSafety * __fmaf_rn(kRcpMul, ratio, __fmaf_rn(gg, rhs[r] + Eb[r], Eb[r]) * inv)
-                               : 0.0f;
-          unc = unc || (el && nzr && (!(g <= 0.5f) || !(er < 1.0e30f)));
-          elig |= el ? 1u << r : 0u;
-          lo[r] = el ? fmaxf(ratio - er, 0.0f) : 3.0e38f;  // exact ratios of eligible rows are >= 0
-          hi[r] = el ? ratio + er : 3.0e38f;
-          thlo = fminf(thlo, lo[r]);
-          thhi = fminf(thhi, hi[r]);
-        }
-        if (elig == 0) {
-          code = 2;
-          break;
-        }
-        // a row can tie with the minimum only if its interval reaches the
-        // largest possible tie limit theta + 1e-12 max(theta, 1)
-        const float l0 = __fmaf_rn(kTolTieLo, fmaxf(thlo, 1.0f), thlo);
-        const float l1 = __fmaf_rn(kTolTieHi, fmaxf(thhi, 1.0f), thhi);
-        const float limlo = __fmaf_rn(-4.0f * kU32, fabsf(l0), l0);
-        const float limhi = __fmaf_rn(4.0f * kU32, fabsf(l1), l1);
-        unsigned poss = 0, tied = 0;
-#pragma unroll
-        for (int r = 0; r < M; ++r) {
-          poss |= (((elig >> r) & 1u) && lo[r] <= limhi) ? 1u << r : 0u;
-          tied |= (hi[r] <= limlo) ? 1u << r : 0u;
-        }
-        if (__popc(poss) == 1)
-          tied = poss;
-        else
-          unc = unc || (poss & ~tied) != 0;
-        tied &= poss;
-        int leave = 0, lbas = INT_MAX;
-#pragma unroll
-        for (int r = 0; r < M; ++r)
-          if (((tied >> r) & 1u) && basis[r] < lbas) {
-            leave = r;
-            lbas = basis[r];
-          }
-        float piv = a[0], pe = ea[0], prhs_raw = rhs[0], pebr = Eb[0];
-#pragma unroll
-        for (int r = 1; r < M; ++r) {
-          piv = (leave == r) ? a[r] : piv;
-          pe = (leave == r) ? ea[r] : pe;
-          prhs_raw = (leave == r) ? rhs[r] : prhs_raw;
-          pebr = (leave == r) ? Eb[r] : pebr;
-        }
-        const float P = rcp_approx(piv);
-        const float rho = pe * P;  // relative bound of the pivot; the bounds below take rho <= 1/2
-        unc = unc || !(rho <= 0.5f);
-        const float rr = __fmaf_rn(2.0f * rho, rho, rho);  // rho / (1 - rho) <= rho (1 + 2 rho)
-        if (unc) break;
-        // pivot on (leave, q)
-        float prow[8], Ep[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          float v = T[0][k], e = E[0][k];
-#pragma unroll
-          for (int r = 1; r < M; ++r) {
-            v = (leave == r) ? T[r][k] : v;
-            e = (leave == r) ? E[r][k] : e;
-          }
-          const float pr = v * P, eP = e * P;
-          prow[k] = (k == q) ? 1.0f : pr;
-          Ep[k] = (k == q) ? 0.0f : __fmaf_rn(kRcpMul, fabsf(pr), __fmaf_rn(rr, fabsf(pr) + eP, eP));
-        }
-        const float prhs = prhs_raw * P, ebP = pebr * P;
-        const float Ebp = __fmaf_rn(kRcpMul, fabsf(prhs), __fmaf_rn(rr, fabsf(prhs) + ebP, ebP));
-#pragma unroll
-        for (int r = 0; r < M; ++r) {
-          const bool lr = (leave == r);
-          const float ar = lr ? -1.0f : a[r];
-          const float ear = lr ? 0.0f : ea[r];
-          const float aar = fabsf(ar) + ear;
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            // column q of the other rows becomes an exact 0 (its bound stays, conservatively)
-            const float tn = __fmaf_rn(-ar, prow[k], lr ? 0.0f : T[r][k]);
-            const float en = __fmaf_rn(kU32, fabsf(tn), __fmaf_rn(aar, Ep[k], __fmaf_rn(ear, fabsf(prow[k]), E[r][k])));
-            T[r][k] = tn;
-            E[r][k] = lr ? Ep[k] : en;
-          }
-          const float rn = __fmaf_rn(-ar, prhs, lr ? 0.0f : rhs[r]);
-          const float ebn = __fmaf_rn(kU32, fabsf(rn), __fmaf_rn(aar, Ebp, __fmaf_rn(ear, fabsf(prhs), Eb[r])));
-          rhs[r] = rn;
-          Eb[r] = lr ? Ebp : ebn;
-        }
-        float dq = d[0], edq = Ed[0];
-#pragma unroll
-        for (int k = 1; k < 8; ++k) {
-          dq = (q == k) ? d[k] : dq;
-          edq = (q == k) ? Ed[k] : edq;
-        }
-        const float adq = fabsf(dq) + edq;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          d[k] = __fmaf_rn(-dq, prow[k], d[k]);
-          Ed[k] = __fmaf_rn(kU32, fabsf(d[k]), __fmaf_rn(adq, Ep[k], __fmaf_rn(edq, fabsf(prow[k]), Ed[k])));
-        }
-        if (lbas >= M)
-          basic &= ~(1u << (lbas - M));
-        else
-          --n_art;
-        basic |= 1u << q;
-#pragma unroll
-        for (int r = 0; r < M; ++r) basis[r] = (leave == r) ? M + q : basis[r];
-        ++it;
-      }
+      lp_pivots32<M>(xs, es, basis, it, code, unc);
     }
     // the lanes leave the pivot loop at different counts: join them so that
     // the FP64 solve below runs once per warp
