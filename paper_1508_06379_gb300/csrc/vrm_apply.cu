@@ -32,6 +32,27 @@ __device__ __forceinline__ float mul_acc<float>(double a, double b) {
 __device__ __forceinline__ double add_acc(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float add_acc(float a, float b) { return __fadd_rn(a, b); }
 
+// Batcher odd-even merge sort of 8 source indices with their terms.
+template <typename Acc>
+__device__ __forceinline__ void cx_terms(int* k, Acc* v, int p, int q) {
+  const bool sw = k[q] < k[p];
+  const int k0 = sw ? k[q] : k[p], k1 = sw ? k[p] : k[q];
+  const Acc v0 = sw ? v[q] : v[p], v1 = sw ? v[p] : v[q];
+  k[p] = k0;
+  k[q] = k1;
+  v[p] = v0;
+  v[q] = v1;
+}
+template <typename Acc>
+__device__ __forceinline__ void sort8_terms(int* k, Acc* v) {
+  cx_terms(k, v, 0, 1); cx_terms(k, v, 2, 3); cx_terms(k, v, 4, 5); cx_terms(k, v, 6, 7);
+  cx_terms(k, v, 0, 2); cx_terms(k, v, 1, 3); cx_terms(k, v, 4, 6); cx_terms(k, v, 5, 7);
+  cx_terms(k, v, 1, 2); cx_terms(k, v, 5, 6);
+  cx_terms(k, v, 0, 4); cx_terms(k, v, 1, 5); cx_terms(k, v, 2, 6); cx_terms(k, v, 3, 7);
+  cx_terms(k, v, 2, 4); cx_terms(k, v, 3, 5);
+  cx_terms(k, v, 1, 2); cx_terms(k, v, 3, 4); cx_terms(k, v, 5, 6);
+}
+
 // W: stencil width (8 for n = 1, 12 for n = 2); slot numbers fit 4 bits.
 template <typename Acc, int W>
 __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __restrict__ n_dev, int n_gamma,
@@ -78,11 +99,41 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
         slot_hi |= (unsigned long long)slot << (4 * (t - 16));
     }
     // FP64 (or fp32) pass over the matches only, in ascending i (rows may
-    // be in visiting order: the next match is the remaining one of smallest
-    // index), the self term before the first i > j
+    // be in visiting order), the self term before the first i > j
     Acc acc = Acc(0);
     bool self_done = !self_src;
-    for (unsigned rest = match; rest;) {
+    unsigned rest = match;
+    if (__popc(match) <= 8) {
+      // up to 8 matches (nearly all targets): their terms are loaded at once
+      // (the loads of one target overlap instead of queueing), then sorted
+      // by source index with the terms as payload and added in that order
+      int mi[8];
+      Acc term[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        mi[k] = INT_MAX;
+        term[k] = Acc(0);
+        if (rest) {
+          const int t = __ffs(rest) - 1;
+          rest &= rest - 1;
+          const int i = row[t];
+          const int slot = (int)(((t < 16 ? slot_lo >> (4 * t) : slot_hi >> (4 * (t - 16)))) & 15ull);
+          mi[k] = i;
+          term[k] = mul_acc<Acc>(f[(size_t)i * W + slot], gamma[i]);
+        }
+      }
+      sort8_terms(mi, term);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (mi[k] == INT_MAX) break;
+        if (!self_done && mi[k] > j) {
+          acc = add_acc(acc, selfv);
+          self_done = true;
+        }
+        acc = add_acc(acc, term[k]);
+      }
+    }
+    for (; rest;) {
       int tb = 0, ib = INT_MAX;
       for (unsigned r2 = rest; r2; r2 &= r2 - 1) {
         const int t = __ffs(r2) - 1;
