@@ -1063,26 +1063,41 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
         a[r] = __shfl_sync(kAll, T[r], q);
         amine = (lane == r) ? a[r] : amine;
       }
-      // ratio test, row r on lane r: basic values <= kTolSnap are zeros,
-      // ratios by a Newton reciprocal (relative error ~2^-45, far inside the
-      // tie window); theta = the smallest ratio (non-negative: bit order)
+      // ratio test, row r on lane r: basic values <= kTolSnap are zeros.
+      // As in k_lp_small, the ratios are screened in binary32 (operands
+      // rounded from their bit patterns, relative error < 1e-6): the rows
+      // within 1e-5 of the smallest binary32 ratio are the only ones that
+      // can lie in the FP64 tie window, so FP64 ratios (Newton reciprocal,
+      // relative error ~2^-45) are taken only when two of them differ and
+      // are not exact zeros, and only on those rows
       const bool elig = lane < M && gt_pos(amine, kTolPivot);
-      const double num = gt_pos(rhs, kTolSnap) ? rhs : 0.0;
-      const double ratio = elig ? __dmul_rn(num, rcp_newton<1>(amine)) : 1e308;
-      unsigned long long rb = elig ? (unsigned long long)dbits(ratio) : ~0ull;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long ob = __shfl_xor_sync(kAll, rb, o);
-        rb = ob < rb ? ob : rb;
-      }
-      if (rb == ~0ull) {
+      const bool nzr = gt_pos(rhs, kTolSnap);
+      const float r32 = !elig ? 3.0e38f : nzr ? __fmul_rn(f32_of(rhs), __frcp_rn(f32_of(amine))) : 0.0f;
+      const unsigned eligm = __ballot_sync(kAll, elig);
+      if (!eligm) {
         code = 2;
         break;
       }
-      const double theta = __longlong_as_double((long long)rb);
-      const double lim = __fma_rn(kTolTie, gt_pos(theta, 1.0) ? theta : 1.0, theta);
+      const float m32 = __uint_as_float(__reduce_min_sync(kAll, __float_as_uint(r32)));
+      const float marg = __fmaf_rn(1e-5f, fmaxf(m32, 1.0f), m32);
+      const bool contr = elig && r32 <= marg;
+      unsigned cont = __ballot_sync(kAll, contr);
+      const bool allzero = __ballot_sync(kAll, contr && r32 != 0.0f) == 0u;
+      if (__popc(cont) > 1 && !allzero) {
+        const double num = nzr ? rhs : 0.0;
+        const double ratio = contr ? __dmul_rn(num, rcp_newton<1>(amine)) : 1e308;
+        unsigned long long rb = contr ? (unsigned long long)dbits(ratio) : ~0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long ob = __shfl_xor_sync(kAll, rb, o);
+          rb = ob < rb ? ob : rb;
+        }
+        const double theta = __longlong_as_double((long long)rb);
+        const double lim = __fma_rn(kTolTie, gt_pos(theta, 1.0) ? theta : 1.0, theta);
+        cont = __ballot_sync(kAll, contr && !lt_nonneg(lim, ratio));
+      }
       // leaving row: the lowest basic variable among the tied rows
-      const int key = (elig && !lt_nonneg(lim, ratio)) ? bas : INT_MAX;
+      const int key = ((cont >> lane) & 1u) ? bas : INT_MAX;
       const int lbas = __reduce_min_sync(kAll, key);
       const int leave = __ffs(__ballot_sync(kAll, key == lbas)) - 1;
       const double piv = __shfl_sync(kAll, amine, leave);
