@@ -1488,7 +1488,11 @@ cudaError_t lp_small(const Consts& c, const double* x, const double* y, const in
     k_lp_small32<5, 8><<<blocks, tb, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list,
                                              retry_list, ds, nu_dt, dt_dev, nu);
     note_launch();
-    k_lp_small<5, 8><<<blocks, tb, 0, s>>>(c, x, y, retry_list, &ds->n_retry, small, cols, f, fii, status,
+    // the re-run list is a few percent of the LPs: one-warp blocks spread it
+    // over every SM instead of over the first few hundred blocks
+    int rblocks = (int)(((long)cap + 31) / 32);
+    if (rblocks > 32 * sm_count()) rblocks = 32 * sm_count();
+    k_lp_small<5, 8><<<rblocks, 32, 0, s>>>(c, x, y, retry_list, &ds->n_retry, small, cols, f, fii, status,
                                            fail_list, ds, nu_dt, dt_dev, nu);
     note_launch();
   }
