@@ -25,6 +25,10 @@
 // pivot row/column selections are register selects on the integer pipes.
 // The rare full-neighbourhood retry runs one particle per warp, one tableau
 // column per lane (K <= 32), with the pivot column broadcast by shuffles.
+// For n = 1 the default kernel, k_lp_small32, pivots in binary32 with
+// certified decisions and keeps FP64 for the column offsets and the final
+// basis solve (see the section before it); k_lp_small re-runs the particles
+// it hands back, and serves n = 2 and the FP64-pivot schedule.
 #include <climits>
 
 #include "vrm_internal.cuh"
