@@ -1131,9 +1131,9 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
     // basic solution of the final basis by the oracle's LU sequence, row r of
     // B on lane r: column k is e_v for an artificial v = basis[k] < m, else
     // the Vandermonde column of the basic structural
-    double fv = 0.0, wsum = 0.0;
+    double fv = 0.0, wsum = 0.0, rmax = 0.0;
     if (code == 0) {
-      double A[M];
+      double A[M], B0[M];
       int bk[M];
 #pragma unroll
       for (int k = 0; k < M; ++k) {
@@ -1141,6 +1141,7 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
         const int src = bk[k] >= M ? bk[k] - M : 0;
         const double bx = __shfl_sync(kAll, cxi, src), be = __shfl_sync(kAll, ceta, src);
         A[k] = bk[k] < M ? (bk[k] == lane ? 1.0 : 0.0) : vrow(lane, bx, be);
+        B0[k] = A[k];
       }
       double z = lane < M ? b_of(lane) : 0.0;
       double rcpd[M];
@@ -1162,20 +1163,27 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
         xB[r] = __shfl_sync(kAll, __dmul_rn(acc, rcpd[r]), r);
       }
       if (sing) code = 2;
+      // residual V f - b of the snapped structural weights, row r on lane r:
+      // sum over the basic structurals of B[r][k] f_k (the basis matrix kept
+      // before its LU), then the largest |row| over the row lanes
+      double acc = lane < M ? dneg(b_of(lane)) : 0.0;
 #pragma unroll
       for (int k = 0; k < M; ++k) {
-        if (bk[k] < M) wsum = __dadd_rn(wsum, xB[k]);
-        else if (bk[k] == M + lane) fv = gt_pos(xB[k], kTolSnap) ? xB[k] : 0.0;
+        if (bk[k] < M) {
+          wsum = __dadd_rn(wsum, xB[k]);
+        } else {
+          const double vk = gt_pos(xB[k], kTolSnap) ? xB[k] : 0.0;
+          if (bk[k] == M + lane) fv = vk;
+          acc = __fma_rn(B0[k], vk, acc);
+        }
       }
-    }
-    double rmax = 0.0;
+      unsigned long long eb = lane < M ? ((unsigned long long)dbits(acc) & 0x7FFFFFFFFFFFFFFFull) : 0ull;
 #pragma unroll
-    for (int r = 0; r < M; ++r) {
-      double p = __dmul_rn(v[r], fv);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) p = __dadd_rn(p, __shfl_xor_sync(kAll, p, o));
-      const double e = fabs(__dsub_rn(p, b_of(r)));
-      rmax = abs_gt(e, rmax) ? e : rmax;
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long ob = __shfl_xor_sync(kAll, eb, o);
+        eb = ob > eb ? ob : eb;
+      }
+      rmax = __longlong_as_double((long long)eb);
     }
     const bool feasible = code == 0 && !gt_pos(wsum, kTolPhase1) && !gt_pos(rmax, kTolResid);
     int* crow = cols + (size_t)i * W;
