@@ -583,8 +583,8 @@ cudaError_t enqueue_front(vrm_ctx* ctx, double* x, double* y, int cap, const dou
                           s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
                           st)) != cudaSuccess)
     return e;
-  if ((e = search_masks_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, cap, n_dev, diffused,
-                            s.mask, st)) != cudaSuccess)
+  if ((e = search_masks_list_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.cell_key,
+                                 s.cell_rank, s.dlist, s.counters + 0, cap, s.mask, st)) != cudaSuccess)
     return e;
   if ((e = open_list(s.dlist, s.counters + 0, cap, s.mask, s.rb.keep_flag, s.pos, s.rb.open, s.counters + 1,
                      s.scan_tmp, st)) != cudaSuccess)

@@ -248,6 +248,10 @@ cudaError_t search_all_dev(const Consts& c, const Grid* g, const int* cell_start
                            const float2* sorted_loc, const int* sorted_idx, int n_bound, const int* n_dev,
                            int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small, DevStats* ds,
                            cudaStream_t s, bool sorted = true);
+cudaError_t search_masks_list_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
+                                  const float2* sorted_loc, const int* sorted_idx, const int* cell_key,
+                                  const int* cell_rank, const int* list, const int* list_count, int m_bound,
+                                  uint8_t* mask, cudaStream_t s);
 cudaError_t search_masks_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
                              const float2* sorted_loc, const int* sorted_idx, int n_bound, const int* n_dev,
                              const uint8_t* flag, uint8_t* mask, cudaStream_t s);
