@@ -252,13 +252,7 @@ cudaError_t search_masks_list_dev(const Consts& c, const Grid* g, const int* cel
                                   const float2* sorted_loc, const int* sorted_idx, const int* cell_key,
                                   const int* cell_rank, const int* list, const int* list_count, int m_bound,
                                   uint8_t* mask, cudaStream_t s);
-cudaError_t search_masks_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
-                             const float2* sorted_loc, const int* sorted_idx, int n_bound, const int* n_dev,
-                             const uint8_t* flag, uint8_t* mask, cudaStream_t s);
 // Segment masks of the particles flagged in `flag` (n entries), in cell order.
-cudaError_t search_masks(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
-                         const float2* sorted_loc, const int* sorted_idx, int n, const uint8_t* flag, uint8_t* mask,
-                         cudaStream_t s);
 
 // vrm_insert.cu
 // Cell grid of the insertion proposals of one round.

@@ -215,61 +215,11 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
   }
 }
 
-// Segment mask only, for the particles with flag[i] set (insertion rounds).
-// Threads run over the particles in cell order and skip unflagged ones.
-__global__ void __launch_bounds__(kBlock) k_search_masks(Consts c, const Grid* __restrict__ gp,
-                                                         const int* __restrict__ cell_start,
-                                                         const double2* __restrict__ sxy,
-                                                         const float2* __restrict__ sloc,
-                                                         const int* __restrict__ sidx, int n,
-                                                         const int* __restrict__ n_dev,
-                                                         const uint8_t* __restrict__ flag,
-                                                         uint8_t* __restrict__ mask) {
-  if (n_dev) n = *n_dev;
-  const Grid g = *gp;
-  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
-    const int i = sidx[p];
-    if (!flag[i]) continue;
-    const double2 pi = sxy[p];
-    const float2 li = sloc[p];
-    const int cx = grid_cell_x(g, pi.x), cy = grid_cell_y(g, pi.y);
-    unsigned mk = 0;
-    for (int by = cy - 1; by <= cy + 1; ++by) {
-      if (by < 0 || by >= g.ny) continue;
-      const float dvb = (float)(by - cy) - li.y;
-      for (int bx = cx - 1; bx <= cx + 1; ++bx) {
-        if (bx < 0 || bx >= g.nx) continue;
-        const float dub = (float)(bx - cx) - li.x;
-        const int cell = by * g.nx + bx;
-        const int q0 = cell_start[cell], q1 = cell_start[cell + 1];
-        for (int q = q0; q < q1; ++q) {
-          const float2 lj = sloc[q];
-          const float du = dub + lj.x, dv = dvb + lj.y;
-          const float d2f = __fmaf_rn(du, du, dv * dv);
-          if (d2f < g.lo_out || d2f > g.hi_out) continue;
-          int s = -1;
-          if (d2f > g.lo_in && d2f < g.hi_in) s = segment_or_ambiguous(du, dv, g.seg_eps);
-          if (s < 0) {
-            const int j = sidx[q];
-            if (j == i) continue;
-            const double2 pj = sxy[q];
-            const double dx = __dsub_rn(pj.x, pi.x), dy = __dsub_rn(pj.y, pi.y);
-            const double d2 = dist2(dx, dy);
-            if (d2 < c.lo2 || d2 > c.hi2) continue;
-            s = segment_of(dx, dy);
-          }
-          mk |= 1u << s;
-        }
-      }
-    }
-    mask[i] = (uint8_t)mk;
-  }
-}
-
 // Segment masks of the listed particles (the diffused list, in index order:
 // lattice order keeps a warp's particles neighbours), each located in the
-// sorted arrays through its cell key and rank.  The same tests as
-// k_search_masks, without lanes idling on unlisted particles.
+// sorted arrays through its cell key and rank: FP32 distances on the
+// cell-local coordinates, the FP64 definition only for the pairs within the
+// band of an annulus bound or a segment line.
 __global__ void __launch_bounds__(kBlock) k_search_masks_list(Consts c, const Grid* __restrict__ gp,
                                                               const int* __restrict__ cell_start,
                                                               const double2* __restrict__ sxy,
@@ -361,23 +311,6 @@ cudaError_t search_all(const Consts& c, const Grid* g, const int* cell_start, co
                        uint8_t* seg_mask, int* small, DevStats* ds, cudaStream_t s) {
   return search_all_dev(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n, nullptr, nbr_count, nbr_idx,
                         seg_mask, small, ds, s, true);
-}
-
-cudaError_t search_masks_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
-                             const float2* sorted_loc, const int* sorted_idx, int n_bound, const int* n_dev,
-                             const uint8_t* flag, uint8_t* mask, cudaStream_t s) {
-  if (n_bound <= 0) return cudaSuccess;
-  int blocks = (n_bound + kBlock - 1) / kBlock;
-  k_search_masks<<<blocks, kBlock, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n_bound, n_dev, flag,
-                                           mask);
-  note_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t search_masks(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
-                         const float2* sorted_loc, const int* sorted_idx, int n, const uint8_t* flag, uint8_t* mask,
-                         cudaStream_t s) {
-  return search_masks_dev(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n, nullptr, flag, mask, s);
 }
 
 }  // namespace vrm
