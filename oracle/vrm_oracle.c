@@ -37,7 +37,7 @@ typedef unsigned __int128 u128;
 #define ORC_TOL_TIE 1e-12     /* ratio ties: within tol * max(1, min ratio) */
 #define ORC_TOL_PHASE1 1e-10  /* feasible iff phase-I objective <= tol */
 #define ORC_TOL_SNAP 1e-11    /* basic values <= tol are degenerate zeros */
-#define ORC_TOL_RESID 1e-10   /* accepted iff max |V f - b| <= tol */
+#define ORC_TOL_RESID 1e-12   /* accepted iff max |V f - b| <= tol */
 
 int orc_num_threads(void) {
 #ifdef _OPENMP
@@ -588,7 +588,7 @@ static void lu_solve_transposed(int m, const double* LU, const int* piv, const d
  * V: m x K row-major.  f: K outputs: basic values above 1e-11, others 0
  * (degenerate basics come out at rounding level, of either sign; they are
  * zeros of the vertex and are snapped to 0 so that f >= 0 holds exactly).
- * Returns 0 feasible (phase-I objective <= 1e-10 and max |V f - b| <= 1e-10),
+ * Returns 0 feasible (phase-I objective <= 1e-10 and max |V f - b| <= 1e-12,
  * 1 infeasible, 2 pivot cap or singular basis.  *npiv = pivots taken,
  * *resid = max |V f - b|.
  */
@@ -914,7 +914,7 @@ long orc_step(double* x, double* y, long n, long capacity, const double* gamma_i
 }
 
 /* ------------------------------------------------------------------------ */
-/* Particle removal (the outlook of Sec. 7): a particle that has come too    */
+/* Particle removal (the outlook of Sec. 6.2): a particle that has come too    */
 /* close to another is redistributed to its neighbours by an approximation  */
 /* of the identity operator, then removed.                                   */
 /* ------------------------------------------------------------------------ */

@@ -475,7 +475,6 @@ void fill_consts(const vrm_params& p, Consts& c) {
   // their products, at most max(1, R^2) (offsets within R, up to rounding);
   // max|B| max|x| <= 37 keeps the LU backward error below 0.5e-10 (see
   // lp_finish in vrm_lp.cu)
-  c.lp_xlim = 37.0 / std::max(1.0, p.R * p.R * 1.001);
   volatile double hh = h * h;  // keep the documented rounding order
   volatile double hhh = hh * h;
   volatile double hp = p.order == 2 ? hhh * h : hhh;  // h^{n+2}

@@ -163,8 +163,9 @@ __global__ void k_rounds_init(StepState* st, const int* __restrict__ n_open_src,
   st->n_needed = 0;
   st->open_segments = 0;
   st->n_cur = st->n;
+  // with max_rounds = 0 no round runs and the open list stays as it is: its
+  // empty segments are the ones reported
   const int go = st->n_open > 0 && st->max_rounds > 0;
-  if (!go) st->n_open = 0;  // nothing to do: every round is a no-op
   if (graph) cudaGraphSetConditional(h, go);
 }
 

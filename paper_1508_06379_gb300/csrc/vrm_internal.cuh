@@ -26,7 +26,6 @@ constexpr int kBlock = 256;
 // Constants every kernel may need, passed by value.
 struct Consts {
   double h, inv_h, lo2, hi2, Rh, c_bound, nu_over_h2;
-  double lp_xlim;  // largest basic value for which the LU solve alone bounds an LP's residual below 1e-10
   float lo2f, hi2f;
   double ins_dx[8], ins_dy[8];  // insertion offsets 1.5h (cos, sin)((s+1/2) pi/4)
   int k_cap;      // neighbour row stride

@@ -16,7 +16,8 @@
 //             tie, the tie goes to the basic variable of lowest index
 //             (artificials 0..m-1 before structurals m..);
 //   at most 64 pivots; feasible iff the phase-I objective <= 1e-10 and
-//   max |V f - b| <= 1e-10; basic values <= 1e-11 are zeros.
+//   max |V f - b| <= 1e-12 (the moment conditions met to 1e-12 per
+//   particle); basic values <= 1e-11 are zeros.
 //
 // GB300 has about 1/60 of its FP32 rate in FP64, and every FP64 instruction
 // of a warp costs the same whether its lanes are busy or not.  The small
@@ -40,7 +41,7 @@ constexpr double kTolPivot = 1e-9;
 constexpr double kTolTie = 1e-12;
 constexpr double kTolPhase1 = 1e-10;
 constexpr double kTolSnap = 1e-11;
-constexpr double kTolResid = 1e-10;
+constexpr double kTolResid = 1e-12;
 constexpr int kPivotCap = 64;
 
 // FP64 comparisons on the integer pipes: for non-NaN doubles the signed
@@ -152,14 +153,48 @@ __device__ __forceinline__ void vcol_id(double xi, double eta, double* v) {
 __device__ __forceinline__ double b_id(int r) { return r == 0 ? 1.0 : 0.0; }
 
 
+// Upper bound in binary32 of |a| for a double a with |a| < 2^127, from the
+// high word of its bit pattern (three integer ops: the sign cleared, the
+// exponent rebiased with the 20 high mantissa bits moved into place, and one
+// unit of the 20th mantissa bit added, which covers the bits dropped);
+// values below the smallest normal binary32 number (zeros included) give
+// about that number.
+__device__ __forceinline__ float f32_up_abs(double a) {
+  unsigned hi = (unsigned)__double2hiint(a) & 0x7FFFFFFFu;
+  hi = hi > 0x38100000u ? hi : 0x38100000u;
+  return __uint_as_float((hi << 3) + 0x40000008u);
+}
+
+// Residual certificate of a basis solve.  The computed x of the LU solve
+// below satisfies (B + dB) x = b with |dB| <= 2 gamma_3m |L||U| (Higham,
+// Accuracy and Stability of Numerical Algorithms, Thm. 9.4; the factor 2
+// covers the multipliers and quotients taken through reciprocals, two
+// roundings each), so |B x - b| <= 2 gamma_3m s with s = max_r (|L||U||x|)_r.
+// Any FP64 evaluation of the residual sum over at most 8 columns (the
+// oracle's) adds at most gamma_8 (|B||x|)_r <= gamma_8 s (1 + 2 gamma_3m) and
+// one rounding.  s <= cert_s<M>() keeps the sum of these under 1e-12 / 1.2.
+// Partial pivoting gives |L| <= 1 + 4u, so s <= (1 + 4u) sum_c (|U||x|)_c,
+// the quantity basis_solve evaluates (the factor 1.2 covers 1 + 4u and the
+// binary32 rounding of the evaluation).
+__host__ __device__ constexpr double gamma_n(int n) { return n * 0x1p-53 / (1.0 - n * 0x1p-53); }
+template <int M>
+__host__ __device__ constexpr float cert_s() {
+  return (float)(1e-12 / (1.2 * (2.0 * gamma_n(3 * M) + gamma_n(8) * (1.0 + 2.0 * gamma_n(3 * M)))));
+}
+
 // Basic solution of the final basis, by the same LU sequence as the oracle's
 // basis solves (partial pivoting on the first largest |pivot|, full row
 // swaps, multipliers A[r][k] * (1/A[k][k]), products and differences rounded
 // separately), so that equal bases give bit-identical weights.  Column k of
 // B is the unit vector e_v for an artificial v = basis[k] < m, else the
 // Vandermonde column of (bxi[k], beta[k]).  Returns false if B is singular.
+// With cert non-null, *cert = sum over the rows of |U||z| in binary32 from
+// upper bounds of |U| and |z| (an upper bound of max_r (|L||U||z|)_r up to
+// the factor 1 + 4u and binary32 rounding); +inf if some |z| >= 256, where
+// the bounds of the conversion no longer hold and no stencil is that large.
 template <int M, bool ID = false>
-__device__ __forceinline__ bool basis_solve(const int* basis, const double* bxi, const double* beta, double* z) {
+__device__ __forceinline__ bool basis_solve(const int* basis, const double* bxi, const double* beta, double* z,
+                                            float* cert = nullptr) {
   double A[M][M];
 #pragma unroll
   for (int k = 0; k < M; ++k) {
@@ -222,7 +257,84 @@ __device__ __forceinline__ bool basis_solve(const int* basis, const double* bxi,
     for (int c = r + 1; c < M; ++c) z[r] = __dsub_rn(z[r], __dmul_rn(A[r][c], z[c]));
     z[r] = __dmul_rn(z[r], rcp[r]);
   }
+  if (cert) {
+    // sum_r (|U||z|)_r = sum_c |z_c| (sum_{r <= c} |U_rc|)
+    unsigned zhi = 0;
+    float acc = 0.0f;
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      const unsigned h = (unsigned)__double2hiint(z[c]) & 0x7FFFFFFFu;
+      zhi = h > zhi ? h : zhi;
+      float col = 0.0f;
+#pragma unroll
+      for (int r = 0; r <= c; ++r) col += f32_up_abs(A[r][c]);
+      acc = __fmaf_rn(col, f32_up_abs(z[c]), acc);
+    }
+    *cert = zhi < 0x40700000u ? acc : INFINITY;
+  }
   return true;
+}
+
+// Sorts M (key, payload) entries by ascending key: odd-even transposition
+// (M rounds of neighbour compare-exchanges), selects only.
+template <int M, int NP>
+__device__ __forceinline__ void sort_by_key(int (&key)[M], double (&pay)[NP][M]) {
+#pragma unroll
+  for (int t = 0; t < M; ++t)
+#pragma unroll
+    for (int a = t & 1; a + 1 < M; a += 2) {
+      const bool sw = key[a + 1] < key[a];
+      const int k0 = sw ? key[a + 1] : key[a], k1 = sw ? key[a] : key[a + 1];
+      key[a] = k0;
+      key[a + 1] = k1;
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const double p0 = sw ? pay[q][a + 1] : pay[q][a], p1 = sw ? pay[q][a] : pay[q][a + 1];
+        pay[q][a] = p0;
+        pay[q][a + 1] = p1;
+      }
+    }
+}
+
+// max_r |sum_j V_rj f_j - b_r| evaluated as the oracle evaluates it: the
+// terms in ascending column order, each product and sum rounded separately,
+// then the difference with b_r.  Columns outside the basis carry f = 0 and
+// leave the sum unchanged, so only the basic columns are summed: entry r is
+// basis variable basis[r] (structural column basis[r] - M, offsets bxi[r],
+// beta[r], snapped value v[r]; artificials carry v = 0).
+template <int M, bool ID = false>
+__device__ __forceinline__ double resid_in_column_order(const int (&basis)[M], const double (&bxi)[M],
+                                                        const double (&beta)[M], const double (&v)[M]) {
+  int key[M];
+  double pay[3][M];
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+    key[r] = basis[r];
+    pay[0][r] = bxi[r];
+    pay[1][r] = beta[r];
+    pay[2][r] = v[r];
+  }
+  sort_by_key<M, 3>(key, pay);
+  double acc[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) acc[q] = 0.0;
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+    double col[M];
+    if constexpr (ID)
+      vcol_id(pay[0][r], pay[1][r], col);
+    else
+      vcol<M>(pay[0][r], pay[1][r], col);
+#pragma unroll
+    for (int q = 0; q < M; ++q) acc[q] = __dadd_rn(acc[q], __dmul_rn(col[q], pay[2][r]));
+  }
+  double rmax = 0.0;
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    const double e = __dsub_rn(acc[q], ID ? b_id(q) : b_of(q));
+    rmax = abs_gt(e, rmax) ? fabs(e) : rmax;
+  }
+  return rmax;
 }
 
 struct WarpStats {
@@ -326,53 +438,29 @@ __device__ __forceinline__ void lp_finish(const Consts& c, int i, int code, cons
   double wsum = 0.0, rmax = 0.0;
   if (code == 0) {
     double xB[M];
-    if (!basis_solve<M>(basis, bxi, beta, xB)) code = 2;
-    // Residual certificate.  When every basic variable is structural (the
+    float cert = INFINITY;
+    if (!basis_solve<M>(basis, bxi, beta, xB, &cert)) code = 2;
+    // Residual certificate: when every basic variable is structural (the
     // phase-I sum is then exactly 0) and none is snapped, the residual
-    // V f - b is the backward error of the LU solve: with partial pivoting
-    // (|L| <= 1, growth <= 2^(m-1) = 16) it is at most
-    // gamma_15 (5 * 16 max|B|) 5 max|x| = 400 gamma_15 max|B| max|x|,
-    // doubled for the multipliers and quotients taken through reciprocals
-    // (two roundings each), plus the residual's own rounding: below
-    // 1.4e-12 max|B| max|x|, so max|x| <= c.lp_xlim keeps it under
-    // 0.5e-10, and any FP64 evaluation of it (the oracle's) passes the
-    // 1e-10 test.  Then the residual is not computed.
+    // V f - b is that of the basis solve, and cert <= cert_s<M>() proves it
+    // (and the oracle's FP64 evaluation of it) below 1e-12 without
+    // computing it.  Otherwise the residual is evaluated as the oracle does.
     bool all_struct = true, snapped = false;
-    unsigned long long xmax = 0;
 #pragma unroll
     for (int r = 0; r < M; ++r) {
       all_struct = all_struct && basis[r] >= M;
       snapped = snapped || !gt_pos(xB[r], kTolSnap);
-      const unsigned long long b = (unsigned long long)dbits(xB[r]) & 0x7FFFFFFFFFFFFFFFull;
-      xmax = b > xmax ? b : xmax;
     }
-    const bool certified = M == 5 && all_struct && !snapped && xmax < (unsigned long long)dbits(c.lp_xlim);
-    if (certified) {
+    const bool certified = all_struct && !snapped && cert <= cert_s<M>();
+    double v[M];
 #pragma unroll
-      for (int r = 0; r < M; ++r)
+    for (int r = 0; r < M; ++r) {
+      v[r] = (basis[r] >= M && gt_pos(xB[r], kTolSnap)) ? xB[r] : 0.0;
+      if (basis[r] < M) wsum = __dadd_rn(wsum, xB[r]);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == M + k) ? xB[r] : fv[k];
-    } else {
-      double acc[M];
-#pragma unroll
-      for (int r = 0; r < M; ++r) acc[r] = dneg(b_of(r));
-#pragma unroll
-      for (int r = 0; r < M; ++r) {
-        if (basis[r] < M) {
-          wsum = __dadd_rn(wsum, xB[r]);
-        } else {
-          const double v = gt_pos(xB[r], kTolSnap) ? xB[r] : 0.0;
-#pragma unroll
-          for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == M + k) ? v : fv[k];
-          double col[M];
-          vcol<M>(bxi[r], beta[r], col);
-#pragma unroll
-          for (int q = 0; q < M; ++q) acc[q] = __fma_rn(col[q], v, acc[q]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < M; ++r) rmax = abs_gt(acc[r], rmax) ? fabs(acc[r]) : rmax;
+      for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == M + k) ? v[r] : fv[k];
     }
+    if (code == 0 && !certified) rmax = resid_in_column_order<M>(basis, bxi, beta, v);
   }
   const bool feasible = code == 0 && !gt_pos(wsum, kTolPhase1) && !gt_pos(rmax, kTolResid);
   tl.maxpiv = it > tl.maxpiv ? it : tl.maxpiv;
@@ -1163,20 +1251,31 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
         xB[r] = __shfl_sync(kAll, __dmul_rn(acc, rcpd[r]), r);
       }
       if (sing) code = 2;
-      // residual V f - b of the snapped structural weights, row r on lane r:
-      // sum over the basic structurals of B[r][k] f_k (the basis matrix kept
-      // before its LU), then the largest |row| over the row lanes
-      double acc = lane < M ? dneg(b_of(lane)) : 0.0;
+      // residual V f - b of the snapped structural weights, row r on lane r,
+      // evaluated as the oracle does: the terms B[r][k] f_k (the basis matrix
+      // kept before its LU) in ascending column order, products and sums
+      // rounded separately, then the difference with b_r; the largest |row|
+      // over the row lanes
+      int key[M];
+      double pay[2][M];
 #pragma unroll
       for (int k = 0; k < M; ++k) {
+        double vk = 0.0;
         if (bk[k] < M) {
           wsum = __dadd_rn(wsum, xB[k]);
         } else {
-          const double vk = gt_pos(xB[k], kTolSnap) ? xB[k] : 0.0;
+          vk = gt_pos(xB[k], kTolSnap) ? xB[k] : 0.0;
           if (bk[k] == M + lane) fv = vk;
-          acc = __fma_rn(B0[k], vk, acc);
         }
+        key[k] = bk[k];
+        pay[0][k] = B0[k];
+        pay[1][k] = vk;
       }
+      sort_by_key<M, 2>(key, pay);
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < M; ++k) acc = __dadd_rn(acc, __dmul_rn(pay[0][k], pay[1][k]));
+      acc = __dsub_rn(acc, lane < M ? b_of(lane) : 0.0);
       unsigned long long eb = lane < M ? ((unsigned long long)dbits(acc) & 0x7FFFFFFFFFFFFFFFull) : 0ull;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -1245,7 +1344,7 @@ __global__ void __launch_bounds__(128) k_lp_full(Consts c, const double* __restr
 }
 
 // Identity weights of the removal candidates (particle removal, the outlook
-// of Sec. 7): the phase-I simplex of k_lp_small with rows (0,0) (1,0) (0,1)
+// of Sec. 6.2): the phase-I simplex of k_lp_small with rows (0,0) (1,0) (0,1)
 // of r_ij / h and b = (1, 0, 0), i.e. sum g = 1 and sum g r = 0 with g >= 0,
 // on the closest kept particle (close[j] == 0) of every 45-degree segment of
 // the candidate's annulus row (ties to the smaller index), columns ordered by
@@ -1424,25 +1523,15 @@ __global__ void __launch_bounds__(128) k_lp_identity(Consts c, const double* __r
         beta[r] = ev;
       }
       if (!basis_solve<M, true>(basis, bxi, beta, xB)) code = 2;
-      double acc[M];
-#pragma unroll
-      for (int r = 0; r < M; ++r) acc[r] = dneg(b_id(r));
+      double v[M];
 #pragma unroll
       for (int r = 0; r < M; ++r) {
-        if (basis[r] < M) {
-          wsum = __dadd_rn(wsum, xB[r]);
-        } else {
-          const double v = gt_pos(xB[r], kTolSnap) ? xB[r] : 0.0;
+        v[r] = (basis[r] >= M && gt_pos(xB[r], kTolSnap)) ? xB[r] : 0.0;
+        if (basis[r] < M) wsum = __dadd_rn(wsum, xB[r]);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == M + k) ? v : fv[k];
-          double col[M];
-          vcol_id(bxi[r], beta[r], col);
-#pragma unroll
-          for (int qq = 0; qq < M; ++qq) acc[qq] = __fma_rn(col[qq], v, acc[qq]);
-        }
+        for (int k = 0; k < 8; ++k) fv[k] = (basis[r] == M + k) ? v[r] : fv[k];
       }
-#pragma unroll
-      for (int r = 0; r < M; ++r) rmax = abs_gt(acc[r], rmax) ? fabs(acc[r]) : rmax;
+      if (code == 0) rmax = resid_in_column_order<M, true>(basis, bxi, beta, v);
     }
     const bool feasible = code == 0 && !gt_pos(wsum, kTolPhase1) && !gt_pos(rmax, kTolResid);
     int* crow = cols4 + (size_t)i * 4;

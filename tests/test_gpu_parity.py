@@ -166,6 +166,38 @@ def weights_equal(w_g, w_o, n):
     assert np.array_equal(fii_g, w_o["fii"])
 
 
+def moment_residuals(x, y, sel, cols, f, h):
+    """max_r |sum_j V_r(xi_ij) f~_ij - b_r| of the stencils of particles sel,
+    in FP64 from the positions: xi = (x_j - x_i)/h, rows (1,0) (0,1) (2,0)
+    (1,1) (0,2) of Eq. momcondmv, b = (0, 0, 2, 0, 2)."""
+    i = np.asarray(sel)[:, None]
+    ok = cols >= 0
+    j = np.where(ok, cols, 0)
+    xi = (x[j] - x[i]) / h
+    eta = (y[j] - y[i]) / h
+    w = np.where(ok, f, 0.0)
+    rows = (xi, eta, xi * xi, xi * eta, eta * eta)
+    b = (0.0, 0.0, 2.0, 0.0, 2.0)
+    return np.max(np.stack([np.abs((r * w).sum(1) - br) for r, br in zip(rows, b)]), axis=0)
+
+
+def check_stencils_valid(x, y, w_g, n, h):
+    """Every stencil the LP produced (small or full neighbourhood) has f~ >= 0
+    off the diagonal and meets the moment conditions to 1e-12 per particle;
+    zero stencils are all zero."""
+    st = w_g["status"].cpu().numpy()[:n]
+    cols = w_g["cols"].cpu().numpy()[: n * W].reshape(n, W)
+    f = w_g["f"].cpu().numpy()[: n * W].reshape(n, W)
+    sel = np.nonzero((st == 1) | (st == 2))[0]
+    assert np.all(f[sel] >= 0.0)
+    if len(sel):
+        res = moment_residuals(x, y, sel, cols[sel], f[sel], h)
+        worst = int(np.argmax(res))
+        assert res[worst] <= 1e-12, ("moment residual", int(sel[worst]), float(res[worst]))
+    none = st == 3
+    assert not f[none].any() and np.all(cols[none] < 0)
+
+
 @pytest.mark.parametrize("case", CLOUDS, ids=IDS)
 def test_weights_match_oracle(lib, orc, case):
     name, x, y, g, h = case
@@ -179,6 +211,51 @@ def test_weights_match_oracle(lib, orc, case):
     st = w_g["stats"]
     assert st["small_ok"] == int(np.sum(p["w"]["status"] == 1))
     assert st["full_ok"] == int(np.sum(p["w"]["status"] == 2))
+    check_stencils_valid(X, Y, w_g, n, h)
+
+
+# A uniform scatter without insertion rounds (h = 0.04): many diffused
+# particles have empty segments, so the small-neighbourhood LP is infeasible
+# for about a third of them.  The retry on the whole neighbourhood (Sec. 4.3)
+# then solves some (423 with the oracle) and the rest keep a zero stencil
+# (625); with the retry switched off all of them (1048) keep a zero stencil.
+SPARSE = vrm_inputs.uniform_scatter(3000, half_width=1.0, seed=2)
+
+
+@pytest.mark.parametrize("fallback", [True, False], ids=["retry", "no_retry"])
+def test_full_neighbourhood_retry_and_zero_stencils(lib, orc, fallback):
+    x, y, g = SPARSE
+    h, nu = 0.04, 1e-3
+    p = orc.pipeline(x, y, g, h, nu, max_rounds=0, fallback=fallback)
+    X, Y, D, nb = p["x"], p["y"], p["diffused"], p["nb"]
+    n = len(X)
+    counts = np.bincount(p["w"]["status"], minlength=4)
+    assert counts[3] > 100
+    assert (counts[2] > 100) if fallback else (counts[2] == 0)
+    ctx = lib.VRM(h=h, nu=nu, max_rounds=0, fallback=fallback)
+    # the weights stage through vrm_solve_weights
+    nbt = dict(count=cu(nb["count"]), idx=cu(nb["idx"].reshape(-1)), small=cu(nb["small"].reshape(-1)))
+    w_g = ctx.solve_weights(cu(X), cu(Y), n, cu(D), nbt)
+    weights_equal(w_g, p["w"], n)
+    st = w_g["stats"]
+    assert (st["small_ok"], st["full_ok"], st["no_stencil"]) == (counts[1], counts[2], counts[3])
+    check_stencils_valid(X, Y, w_g, n, h)
+    # the whole step through vrm_step
+    dt = (0.5 * h) ** 2 / (4 * nu) / 8
+    x2, y2, g2, st_o = orc.step(x, y, g, h, nu, dt, max_rounds=0, fallback=fallback)
+    assert (st_o["full_ok"], st_o["no_stencil"]) == (counts[2], counts[3])
+    xb = torch.zeros(n + 64, dtype=torch.float64, device="cuda")
+    yb = torch.zeros(n + 64, dtype=torch.float64, device="cuda")
+    xb[:n] = cu(x)
+    yb[:n] = cu(y)
+    go = torch.zeros(n + 64, dtype=torch.float64, device="cuda")
+    n2, st = ctx.step(xb, yb, n, cu(g), go, dt)
+    assert n2 == len(x2) == n
+    for k in ("n_diffused", "n_inserted", "small_ok", "full_ok", "no_stencil", "rounds", "open_segments"):
+        assert st[k] == st_o[k], (k, st[k], st_o[k])
+    assert np.array_equal(go.cpu().numpy()[:n2], g2)
+    # a zero stencil sends nothing, so circulation is still conserved
+    assert abs(g2.sum() - g.sum()) <= 1e-12 * np.abs(g).sum()
 
 
 def dgamma_scale(n, gamma, diffused, w, nu_over_h2):
@@ -351,6 +428,20 @@ def test_full_size_mixture_step(lib, orc):
     scale = np.abs(g2) + np.abs(g).max() * 1e-30
     assert np.all(np.abs(got - g2) <= 1e-12 * (nu / h ** 2) * dt * 16 * np.abs(g).max() + 4 * np.spacing(scale))
     assert len(mismatch) == 0, (len(mismatch), mismatch[:5])
+    # the same cloud stage by stage through the library calls: every LP
+    # stencil meets the moment conditions to 1e-12 (checked in FP64 from the
+    # positions) and the outcome counts are the step's
+    xb2 = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    yb2 = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    xb2[:n] = cu(x)
+    yb2[:n] = cu(y)
+    n3, diff, _ = ctx.insert_reduce(xb2, yb2, n, cu(g))
+    assert n3 == n2
+    nb = ctx.build_neighbourhoods(xb2, yb2, n3)
+    w_g = ctx.solve_weights(xb2, yb2, n3, diff, nb)
+    sw = w_g["stats"]
+    assert (sw["small_ok"], sw["full_ok"], sw["no_stencil"]) == (st_o["small_ok"], st_o["full_ok"], st_o["no_stencil"])
+    check_stencils_valid(x2, y2, w_g, n3, h)
 
 
 def test_graph_and_eager_steps_agree(lib, orc, monkeypatch):
@@ -411,3 +502,26 @@ def test_mixed_precision_step(lib, orc, case):
     # the fp32 accumulation is visible (not silently FP64) where anything diffuses
     if st_o["n_diffused"] > 0:
         assert not np.array_equal(got, g2)
+
+
+@pytest.mark.parametrize("eps,accepted", [(-2e-12, False), (-5e-12, False), (-8e-12, True)])
+def test_snapped_vertex_residual_bar(lib, orc, eps, accepted):
+    # particle 0 with the five neighbours (1,0) (-1,0) (eps,1) (0,-1)
+    # (0.7,0.9) h: the only solution has the weight -eps/0.63 on the last
+    # one; below the snap threshold 1e-11 it is set to zero and the moment
+    # residual (about 0.9 of it) is above 1e-12, so both the small and the
+    # full-neighbourhood LP reject it and the stencil is zero
+    h = 1.0
+    x = np.array([0.0, 1.0, -1.0, eps, 0.0, 0.7])
+    y = np.array([0.0, 0.0, 0.0, 1.0, -1.0, 0.9])
+    n = len(x)
+    D = np.zeros(n, np.uint8)
+    D[0] = 1
+    nb = orc.neighbours(x, y, h, k_cap=32)
+    w_o = orc.solve_weights(x, y, D, nb, h)
+    assert w_o["status"][0] == (1 if accepted else 3)
+    ctx = lib.VRM(h=h, nu=1.0)
+    nbt = dict(count=cu(nb["count"]), idx=cu(nb["idx"].reshape(-1)), small=cu(nb["small"].reshape(-1)))
+    w_g = ctx.solve_weights(cu(x), cu(y), n, cu(D), nbt)
+    weights_equal(w_g, w_o, n)
+    check_stencils_valid(x, y, w_g, n, h)

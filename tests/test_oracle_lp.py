@@ -135,3 +135,39 @@ def test_degenerate_inputs(orc):
     xi, eta = ring(rng, 3)
     st, f, _, _ = orc.phase1(textbook_vandermonde(xi, eta), B5)
     assert st == 1
+
+
+# Four axis neighbours at distance 1 meet every moment condition with
+# weights 1 (the five-point stencil).  Moving the one on +eta by eps < 0
+# along xi breaks the (1,1) row, and the fifth column (0.7, 0.9) takes the
+# weight -eps/0.63 to restore it: the unique solution on these five columns.
+# For eps = -2e-12 and -5e-12 that weight (3.2e-12, 7.9e-12) is below the
+# snap threshold 1e-11, so the vertex comes out with it set to zero and a
+# moment residual of 0.9 * 3.2e-12 and 0.9 * 7.9e-12: above 1e-12, the LP is
+# rejected (the moment conditions must hold to 1e-12 per particle).  For
+# eps = -8e-12 the weight 1.27e-11 is kept and the residual is at rounding
+# level.
+SNAP_CASES = [(-2e-12, 1), (-5e-12, 1), (-8e-12, 0), (-2e-11, 0)]
+
+
+def snap_columns(eps):
+    return np.array([1.0, -1.0, eps, 0.0, 0.7]), np.array([0.0, 0.0, 1.0, -1.0, 0.9])
+
+
+@pytest.mark.parametrize("eps,verdict", SNAP_CASES)
+def test_residual_bar_is_1e12_after_snapping(orc, eps, verdict):
+    xi, eta = snap_columns(eps)
+    V = textbook_vandermonde(xi, eta)
+    exact = np.linalg.solve(V, B5)
+    assert np.all(exact > 0)
+    assert abs(exact[4] - (-eps / 0.63)) <= 1e-3 * abs(eps)
+    st, f, npiv, res = orc.phase1(V, B5)
+    assert st == verdict, (st, res)
+    if verdict == 0:
+        np.testing.assert_allclose(f, exact, rtol=1e-9)
+        assert res <= 1e-15
+    else:
+        # the residual the snapped vertex would leave
+        snapped = np.where(exact > 1e-11, exact, 0.0)
+        assert np.max(np.abs(V @ snapped - B5)) > 1e-12
+        assert not f.any()
