@@ -2,15 +2,15 @@
 // vrm_build_neighbourhoods for callers that must not allocate memory.
 //
 // Some callers cannot call cudaMalloc (or any allocating routine) at the point
-// where they need neighbourhoods: code that runs while a CUDA stream is being
-// captured into a graph (an allocation there breaks or serialises the
-// capture), real-time loops whose latency budget has no room for allocator
-// calls or their implicit synchronisation, and applications that hand all
-// device memory to their own pool up front and forbid allocations afterwards.
-// This entry point needs no context and allocates nothing: its scratch (cell
-// grid, sorted copies of the cloud, scan workspace) lives in one file-scope
-// device array of fixed size, which every GPU that loads this library holds
-// until the process exits.  The caller still passes the inputs and outputs.
+// where they need neighbourhoods: applications that hand all device memory to
+// their own pool up front and forbid allocations afterwards (a host program
+// that loads this library as a plug-in and owns every buffer), and real-time
+// loops whose latency budget has no room for allocator calls, which can take
+// milliseconds and synchronise the device.  This entry point needs no context
+// and allocates nothing: its scratch (cell grid, sorted copies of the cloud,
+// scan workspace) lives in one file-scope device array of fixed size, which
+// every GPU that loads this library holds until the process exits.  The
+// caller still passes the inputs and outputs.
 #include <cstring>
 #include <mutex>
 

@@ -1,13 +1,15 @@
 """vrm_build_neighbourhoods_noalloc against vrm_build_neighbourhoods.
 
-The no-allocation entry point serves callers that cannot allocate when they
-need neighbourhoods (inside a stream capture, in latency-bound loops, with
-all memory in their own pool).  It keeps its scratch in one fixed device
-array shared by every call, so this test makes two calls in a row on
-different clouds, and a third on the first cloud again, and checks each
-against the context-based entry point bit for bit (the outputs are indices
-and masks).  The file is collected last so that a failure here leaves every
-other test already run.
+The no-allocation entry point serves callers that cannot allocate device
+memory when they need neighbourhoods (programs that own all device memory in
+their own pool, real-time loops with no room for allocator calls).  It keeps
+its scratch in one fixed device array shared by every call, so this test makes
+calls in a row on different clouds (and the first cloud again) and checks each
+against the context-based entry point bit for bit (the outputs are indices and
+masks): among them a cloud of exactly the largest size the array holds, and a
+wide sparse cloud whose grid needs more cells than the array has, so that the
+cell size is doubled.  The file is collected last so that a failure here
+leaves every other test already run.
 """
 import numpy as np
 import pytest
@@ -38,6 +40,15 @@ def test_noalloc_matches_context_entry_point_twice(vrm):
     clouds = [vrm_inputs.random_cloud(20000, h=0.01, jitter=0.3, seed=1)[:2] + (0.01,),
               vrm_inputs.uniform_scatter(5000, half_width=1.0, seed=3)[:2] + (0.03,)]
     clouds.append(clouds[0])
+    # exactly VRM_NOALLOC_MAX_N particles (a 256 x 256 jittered lattice)
+    xm, ym = vrm_inputs.random_cloud(vrm.NOALLOC_MAX_N, h=0.01, jitter=0.3, seed=4)[:2]
+    assert len(xm) == vrm.NOALLOC_MAX_N
+    clouds.append((xm, ym, 0.01))
+    # 20,000 particles scattered over [-1, 1]^2 with h = 0.0025: cells of
+    # side R h = 0.005 would need 401 x 401 > 2 * 65536 + 1024 cells
+    xs, ys = vrm_inputs.uniform_scatter(20000, half_width=1.0, seed=5)[:2]
+    assert (np.floor(2.0 / (2 * 0.0025 * (1 + 1e-6))) + 1) ** 2 > 2 * vrm.NOALLOC_MAX_N + 1024
+    clouds.append((xs, ys, 0.0025))
     for x, y, h in clouds:
         n = len(x)
         xt = torch.from_numpy(x).cuda()
