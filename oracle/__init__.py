@@ -294,7 +294,7 @@ def one_minus_exp_neg(a):
 
 
 def lamb_oseen_velocity(x, y, gamma, nu, t, x0=0.0, y0=0.0):
-    """Azimuthal velocity of the Lamb-Oseen vortex (Sec. 6):
+    """Azimuthal velocity of the Lamb-Oseen vortex (Sec. 5):
     u_theta = Gamma/(2 pi r) (1 - exp(-r^2/(4 nu t))), as
     (u, v) = (-(y - y0), x - x0) * k with k = Gamma/(2 pi r^2) * one_minus_exp_neg(r^2/(4 nu t));
     products and sums rounded separately, k = 0 at r = 0."""
@@ -367,7 +367,7 @@ def rk3_step(x, y, gamma, h, nu, t, dt, vel=None, r=0.5, R=2.0, c_diff=1.0, orde
 
 
 def biot_savart(xs, ys, gamma, xt, yt, eps, block=2048):
-    """Smoothed Biot-Savart velocity at the targets (Sec. 6, Eq. smoothkernel):
+    """Smoothed Biot-Savart velocity at the targets (Sec. 5, Eq. smoothkernel):
     u_h(x) = sum_j Gamma_j K_eps(x - x_j),
     K_eps(x) = (-y, x) / (2 pi |x|^2) (1 - exp(-|x/eps|^2)),  K_eps(0) = 0;
     direct sum in FP64 (1 - exp(-q) as -expm1(-q)), targets in blocks."""
@@ -391,7 +391,7 @@ def biot_savart(xs, ys, gamma, xt, yt, eps, block=2048):
 
 
 def remove_close(x, y, gamma, h, r=0.5, R=2.0):
-    """Particle removal (outlook of Sec. 7): returns (x', y', gamma', removed
+    """Particle removal (outlook of Sec. 6.2): returns (x', y', gamma', removed
     flags, number of candidates, stencils dict(cols, w) [n x 4], close flags)."""
     x, y, g = _f64(x), _f64(y), _f64(gamma)
     n = len(x)

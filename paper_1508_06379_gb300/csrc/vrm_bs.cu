@@ -1,4 +1,4 @@
-// Smoothed Biot-Savart velocity by direct summation (Sec. 6, Eq.
+// Smoothed Biot-Savart velocity by direct summation (Sec. 5, Eq.
 // smoothkernel): u_h(x) = sum_j Gamma_j K_eps(x - x_j),
 //   K_eps(x) = (-y, x) / (2 pi |x|^2) (1 - exp(-|x/eps|^2)),
 // written as K_eps(x) = (-y, x) phi(q) / (2 pi eps^2), q = |x|^2/eps^2,

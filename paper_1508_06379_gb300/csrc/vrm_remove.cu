@@ -1,4 +1,4 @@
-// Particle removal (the outlook of Sec. 7): where particles have come closer
+// Particle removal (the outlook of Sec. 6.2): where particles have come closer
 // than r h to one another, the one with the smaller key (|Gamma|, index) of
 // such a pair is redistributed to its kept neighbours by non-negative
 // weights that reproduce the identity's moments of order 0 and 1 (sum g = 1,

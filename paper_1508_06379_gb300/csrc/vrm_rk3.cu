@@ -1,5 +1,5 @@
 // Stage update of the SSP-RK3 (Shu-Osher) step with an analytic velocity
-// (the viscous Lamb-Oseen run of Sec. 6 with advection): positions follow
+// (the viscous Lamb-Oseen run of Sec. 5 with advection): positions follow
 // dx/dt = u(x, t), circulations dGamma/dt = L(x) Gamma with the operator of
 // the current stage.
 //

@@ -40,6 +40,24 @@ def quantised(theta):
     return out
 
 
+def term_scale(theta, cache, dY):
+    """Per gradient entry, the sum of the magnitudes of the products that
+    make it up: the backward pass of the oracle's network with every factor
+    (output gradient, GELU derivative, weight, activation) replaced by its
+    absolute value."""
+    layers = omlp.unflatten(theta)
+    grads = [None] * len(layers)
+    g = np.abs(dY)
+    for l in range(len(layers) - 1, -1, -1):
+        a, z = cache[l]
+        if l < len(layers) - 1:
+            g = g * np.abs(omlp.gelu_grad(z))
+        W, _ = layers[l]
+        grads[l] = (g.T @ np.abs(a), g.sum(axis=0))
+        g = g @ np.abs(W)
+    return omlp.flatten(grads)
+
+
 def bf16_rows(X):
     return torch.from_numpy(X.astype(np.float32)).to(torch.bfloat16).cuda()
 
@@ -90,6 +108,14 @@ def test_gradients_match_oracle(lib, B, rows):
         rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
         cos = float(a @ b / max(np.linalg.norm(a) * np.linalg.norm(b), 1e-30))
         assert rel <= 2e-2 and cos >= 0.999, (k, rel, cos)
+    # element by element: each gradient entry is a sum of products (rows x
+    # backpropagated terms); its error may be a bf16-sized fraction of the
+    # sum of those products' magnitudes, not more
+    sc = term_scale(thq, cache, dY)
+    for k, (a, b, s) in enumerate(zip(blocks(g), blocks(go), blocks(sc))):
+        excess = np.abs(a - b) - (2e-2 * s + 1e-30)
+        worst = int(np.argmax(excess))
+        assert excess[worst] <= 0, (k, worst, a[worst], b[worst], s[worst])
     # the padded input columns of W1 receive no gradient (they are not parameters)
     assert np.all(np.isfinite(g))
 

@@ -1,4 +1,4 @@
-"""GPU parity of particle removal (the outlook of Sec. 7) against the FP64
+"""GPU parity of particle removal (the outlook of Sec. 6.2) against the FP64
 oracle, through the C ABI: the removed set, the kept positions and the
 redistributed circulations bit-exact (the identity weights come from the
 same phase-I rules and the oracle's LU sequence; the gather adds the removed

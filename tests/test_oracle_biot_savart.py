@@ -1,4 +1,4 @@
-"""Pins of the oracle's smoothed Biot-Savart velocity (Sec. 6, Eq.
+"""Pins of the oracle's smoothed Biot-Savart velocity (Sec. 5, Eq.
 smoothkernel): the closed form of one blob, the point-vortex far field,
 superposition and antisymmetry, zero self-induced velocity, and the
 Lamb-Oseen velocity recovered from a particle sample (L2 error falling with

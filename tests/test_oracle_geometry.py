@@ -112,7 +112,7 @@ def test_empty_and_single(orc):
 
 
 def test_insertion_single_particle_geometry(orc):
-    # Sec. 6 starts from one Dirac: all 8 segments are empty, so the 8 points
+    # Sec. 5 starts from one Dirac: all 8 segments are empty, so the 8 points
     # at radius 1.5h on the segment centre lines are inserted (Sec. 4.2).
     h = 0.1
     x2, y2, rounds, open_ = orc.insert(np.array([0.3]), np.array([-0.2]), np.array([1], np.uint8), h)

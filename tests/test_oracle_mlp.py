@@ -1,7 +1,7 @@
 """Pins of the learned-proposal oracle (oracle/mlp.py) against what the
 mathematics fixes: closed forms, finite differences, library routines
 (torch's bfloat16 rounding and AdamW, numpy's least squares) and the paper's
-single-particle example (Sec. 6: eight inserted neighbours at 1.5h)."""
+single-particle example (Sec. 5: eight inserted neighbours at 1.5h)."""
 import math
 
 import numpy as np
@@ -161,7 +161,7 @@ def test_projection_least_change():
 
 
 def test_projection_single_particle_example():
-    # Sec. 6: a lone particle gets 8 inserted neighbours at 1.5h on the segment
+    # Sec. 5: a lone particle gets 8 inserted neighbours at 1.5h on the segment
     # centre lines; every stencil meeting the moment conditions has
     # sum f~ = 4 / 1.5^2 = 16/9 (rows (2,0) + (0,2) with |xi|^2 = 2.25)
     ang = (np.arange(8) + 0.5) * math.pi / 4

@@ -8,7 +8,7 @@
   operator, sum |x|^2 dGamma = 4 nu sum_{i in D} Gamma_i.
 * Thm. stability: ||Gamma^{n+1}||_1 <= ||Gamma^n||_1 when
   nu dt <= -1/f_ii for all i.
-* Sec. 6: single Dirac start (golden file) and second-order convergence of the
+* Sec. 5: single Dirac start (golden file) and second-order convergence of the
   heat-equation Lamb-Oseen run against the closed form.
 """
 import json
@@ -123,7 +123,7 @@ def test_stability_l1_nonincreasing(orc):
 
 
 def test_single_dirac_golden(orc):
-    # Sec. 6: the Lamb-Oseen run starts from one Dirac; see golden file
+    # Sec. 5: the Lamb-Oseen run starts from one Dirac; see golden file
     gold = json.load(open(os.path.join(GOLDEN, "single_particle.json")))
     h, nu, G = gold["h"], gold["nu"], gold["gamma"]
     p = operator(orc, np.array([0.0]), np.array([0.0]), np.array([G]), h, nu=nu)
@@ -152,9 +152,9 @@ def weak_error(x, y, g, gamma, nu, t, centres, sigma):
 
 def test_lamb_oseen_heat_convergence(orc):
     # Heat-equation Lamb-Oseen run with Euler and dt = (1/8)(r h)^2/(4 nu)
-    # (Sec. 6.1) on lattices with binary-exact coordinates (h = 2^-k), so that
+    # (Sec. 5.1) on lattices with binary-exact coordinates (h = 2^-k), so that
     # the particle locations are symmetric as in the paper's second-order
-    # observation (Sec. 6.1); the weak error against the closed form falls
+    # observation (Sec. 5.1); the weak error against the closed form falls
     # like h^2.
     gamma, nu, t0, t1 = 1.0, 1e-3, 1.0, 1.125
     centres = [(0.0, 0.0), (0.03, 0.0), (0.05, 0.04), (-0.08, 0.02), (0.0, -0.1)]

@@ -1,4 +1,4 @@
-"""Pins of the oracle's particle removal (the outlook of Sec. 7: a particle
+"""Pins of the oracle's particle removal (the outlook of Sec. 6.2: a particle
 that came too close to another is redistributed to its neighbours by an
 approximation of the identity operator and removed).
 

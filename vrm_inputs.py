@@ -6,7 +6,7 @@ arithmetic and is shared by the tests, the benchmark and the oracle checks.
 
 Workloads (the paper has no dataset; every cloud here is synthetic):
 
-* ``lamb_oseen_lattice``: the Lamb-Oseen vortex of Sec. 6,
+* ``lamb_oseen_lattice``: the Lamb-Oseen vortex of Sec. 5,
   omega(t, x) = Gamma/(4 pi nu t) exp(-|x|^2/(4 nu t)), sampled on a uniform
   lattice k h - 1 (k = 0..2/h) with Gamma_i = omega(t0, x_i) h^2 (midpoint
   quadrature), optionally keeping |omega| > eps only.
@@ -30,7 +30,7 @@ def lamb_oseen_omega(x, y, gamma=1.0, nu=1e-3, t=1.0):
 
 
 def lamb_oseen_velocity(x, y, gamma=1.0, nu=1e-3, t=1.0):
-    """Azimuthal velocity of the Lamb-Oseen vortex (Sec. 6)."""
+    """Azimuthal velocity of the Lamb-Oseen vortex (Sec. 5)."""
     r2 = x * x + y * y
     with np.errstate(invalid="ignore", divide="ignore"):
         s = gamma / (2.0 * math.pi * r2) * (1.0 - np.exp(-r2 / (4.0 * nu * t)))
