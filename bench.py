@@ -35,9 +35,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "particles/s per VRM diffusion step on 1 GB300"
+METRIC = "particles/s per VRM diffusion step on 1 GB300; learned vs plain LP at equal error"
 UNIT = "particles/s"
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07  # 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz (x1000 -> GFLOP/s)
+# derived FP64 peak, shown beside the measured one: 152 SMs x 2 FP64 FMA
+# lanes/clk x 2 flop x 2.07 GHz (GFLOP/s)
+FP64_PEAK_DERIVED_GFLOPS = 152 * 2 * 2 * 2.07
 
 
 def parse():
@@ -60,6 +62,8 @@ def parse():
     ap.add_argument("--learned-side", type=int, default=2001,
                     help="lattice side of the learned workload's cloud (2001: the 4M-particle cloud)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="default workload: skip the learned-vs-LP comparison block")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
                     help="mixed: the application accumulates in fp32 (dGamma within 1e-5 of the term scale)")
@@ -246,6 +250,9 @@ def run_ours(args):
         flush.zero_()
         ctx.step(xb, yb, n, gi, go, dt)
     torch.cuda.synchronize()
+    # the FP64/FP32 FMA rate of this GPU (k_fma_probe): the LP's roofline
+    # denominator, measured in this run
+    peaks = {"fp64_tflops": vrm.fma_peak(True) / 1e12, "fp32_tflops": vrm.fma_peak(False) / 1e12}
     gpu_id = None
     try:
         gpu_id = str(torch.cuda.get_device_properties(local).uuid)
@@ -330,8 +337,12 @@ def run_ours(args):
 
     mean_stage = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage_ms.items()}
     dom = max(mean_stage, key=mean_stage.get)
-    roofline = (roofline_for(dom, mean_stage[dom], stats, n, desc["order"], ctx.get_schedule()["lp_fp64_pivots"])
-                if mean_stage[dom] > 0 else None)
+    roofline = (roofline_for(dom, mean_stage[dom], stats, n, desc["order"], ctx.get_schedule()["lp_fp64_pivots"],
+                             peaks) if mean_stage[dom] > 0 else None)
+    learned = None
+    if args.workload == "mixture_1m" and not args.no_learned and world == 1:
+        learned = learned_vs_lp(args, ctx, xb, yb, n, gi, go, h, nu, dt, total_ms / args.steps, parts / args.steps,
+                                flush, stream)
     if rank != 0:
         if dist:
             dist.barrier()
@@ -358,12 +369,119 @@ def run_ours(args):
                "small_ok": int(stats["small_ok"]), "full_ok": int(stats["full_ok"]),
                "no_stencil": int(stats["no_stencil"]), "small_rechecked": int(stats["lp_small_rechecked"])},
         "cpu_baseline": cpu,
+        "peaks_measured": {k: round(v, 4) for k, v in peaks.items()},
     }
+    if learned is not None:
+        line["learned_vs_lp"] = learned
     print(json.dumps(line))
     sys.stdout.flush()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def max_moment_residual(x, y, w, n, order=1):
+    """Largest max_r |sum_j V_r(xi_ij) f~_ij - b_r| over the stencils of one
+    weights call (small, full and learned), in FP64 from the positions, and
+    the smallest off-diagonal weight."""
+    import numpy as np
+    W = w["cols"].numel() // max(n, 1)
+    st = w["status"][:n].cpu().numpy()
+    cols = w["cols"][: n * W].view(n, W).cpu().numpy()
+    f = w["f"][: n * W].view(n, W).cpu().numpy()
+    sel = np.nonzero((st == 1) | (st == 2) | (st == 4))[0]
+    xs, ys = x[:n].cpu().numpy(), y[:n].cpu().numpy()
+    worst, fmin = 0.0, 0.0
+    for a in range(0, len(sel), 1 << 18):
+        s_ = sel[a:a + (1 << 18)]
+        c = cols[s_]
+        ok = c >= 0
+        j = np.where(ok, c, 0)
+        h = w["h"]
+        xi = (xs[j] - xs[s_, None]) / h
+        eta = (ys[j] - ys[s_, None]) / h
+        ww = np.where(ok, f[s_], 0.0)
+        rows = [(xi, 0.0), (eta, 0.0), (xi * xi, 2.0), (xi * eta, 0.0), (eta * eta, 2.0)]
+        for r, b in rows:
+            worst = max(worst, float(np.max(np.abs((r * ww).sum(1) - b))))
+        fmin = min(fmin, float(np.min(ww)))
+    return worst, fmin, int(len(sel))
+
+
+def learned_vs_lp(args, ctx_lp, xb, yb, n, gi, go, h, nu, dt, lp_ms, lp_parts, flush, stream):
+    """The second half of the metric on the same cloud and run: a network
+    trained here on LP solutions (seeded jittered clouds, the learned_4m
+    recipe), the step with learned stencils against the step with the LP
+    alone (particles/s), acceptance, the largest moment residual and the
+    smallest weight of every stencil of both, and the weak error of both on
+    the heat-equation Lamb-Oseen run against the closed form."""
+    import torch
+
+    import paper_1508_06379_gb300 as vrm
+    from paper_1508_06379_gb300 import learn
+    t0 = time.time()
+    X, T, N = learn.make_dataset(args.train_rows)
+    t_data = time.time() - t0
+    t0 = time.time()
+    net, losses = learn.train(X, T, N, epochs=args.train_epochs, batch=4096, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    del X, T
+    ctx = vrm.VRM(h=h, nu=nu)
+    ctx.set_mlp(net)
+    ctx.set_timing(True)
+    go2 = torch.zeros_like(go)
+    for _ in range(args.warmup):
+        flush.zero_()
+        ctx.step(xb, yb, n, gi, go2, dt)
+    ms, parts, stage = 0.0, 0, {}
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n2, st = ctx.step(xb, yb, n, gi, go2, dt)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        parts += n2
+        for k, v in ctx.stage_times().items():
+            stage.setdefault(k, []).append(v)
+    learned_value = parts / (ms * 1e-3)
+    lp_value = lp_parts / (lp_ms * 1e-3)
+    # every stencil of both paths on this cloud: residual and sign
+    cap = xb.numel()
+    res = {}
+    for name, c in (("lp", ctx_lp), ("learned", ctx)):
+        x2 = torch.zeros(cap, dtype=torch.float64, device=xb.device)
+        y2 = torch.zeros(cap, dtype=torch.float64, device=xb.device)
+        x2[:n] = xb[:n]
+        y2[:n] = yb[:n]
+        n3, diff, _ = c.insert_reduce(x2, y2, n, gi)
+        nb = c.build_neighbourhoods(x2, y2, n3)
+        w = c.solve_weights(x2, y2, n3, diff, nb)
+        w["h"] = h
+        rmax, fmin, m = max_moment_residual(x2, y2, w, n3)
+        res[name] = {"max_moment_residual": rmax, "min_weight": fmin, "stencils": m,
+                     "learned": int(w["stats"]["learned_ok"]), "lp_small": int(w["stats"]["small_ok"]),
+                     "lp_full": int(w["stats"]["full_ok"]), "none": int(w["stats"]["no_stencil"])}
+    lo = lamb_oseen_weak_errors(vrm, net)
+    return {
+        "what": "the same cloud and run: stencils proposed by the trained network (FP64 support solve, accepted "
+                "when every weight >= 0 and the moment residual <= 1e-12; LP otherwise) against the LP alone",
+        "learned": {"value": learned_value, "unit": UNIT, "ms_per_step": ms / args.steps,
+                    "stage_ms": {k: round(sum(v) / len(v), 4) for k, v in stage.items()},
+                    "acceptance": st["learned_ok"] / max(1, st["n_diffused"]),
+                    "supports_screened_per_particle": st["learned_screens"] / max(1, st["n_diffused"]),
+                    **res["learned"]},
+        "lp": {"value": lp_value, "unit": UNIT, "ms_per_step": lp_ms, **res["lp"]},
+        "speedup_learned_over_lp": learned_value / lp_value,
+        "lamb_oseen_weak_error": {"lp": lo["lp"]["weak_error"], "learned": lo["learned"]["weak_error"],
+                                  "learned_fraction": lo["learned"]["learned_fraction"], "h": lo["h"],
+                                  "steps": lo["lp"]["steps"]},
+        "training": {"rows": int(N), "epochs": args.train_epochs, "data_s": round(t_data, 2),
+                     "train_s": round(t_train, 2), "loss_first_last": [losses[0][1], losses[-1][1]]},
+    }
 
 
 def traffic_for(kernel):
@@ -382,7 +500,7 @@ def traffic_for(kernel):
         return None
 
 
-def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1):
+def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1, peaks=None):
     m = 9 if order == 2 else 5
     if stage in ("lp_small", "lp_full"):
         if stage == "lp_small" and order == 1 and not lp_fp64_pivots:
@@ -397,11 +515,15 @@ def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1):
         if stage == "lp_small" and order == 1 and not lp_fp64_pivots:
             kern = "k_lp_small32"
         ach = flops / (ms * 1e-3) / 1e12
-        peak = FP64_PEAK_GFLOPS / 1000.0
+        if peaks and peaks.get("fp64_tflops"):
+            peak = peaks["fp64_tflops"]
+            src = ("of measured: FP64 FMA rate of k_fma_probe in this run (%.3f TFLOP/s; derived 152 SMs x 2 FMA "
+                   "lanes/clk x 2 flop x 2.07 GHz = %.3f)" % (peak, FP64_PEAK_DERIVED_GFLOPS / 1000.0))
+        else:
+            peak = FP64_PEAK_DERIVED_GFLOPS / 1000.0
+            src = "derived: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz"
         return {"kernel": kern, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": traffic_for(kern) if order == 1 else None,
-                "peak_source": "FP64: 152 SMs x 2 FMA lanes/clk x 2 flop x 2.07 GHz (derived; measured FMA loop "
-                               "1.198 TFLOP/s)"}
+                "frac": ach / peak, "traffic": traffic_for(kern) if order == 1 else None, "peak_source": src}
     hbm = None
     try:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
@@ -461,9 +583,14 @@ def run_reference(args):
     value = parts / t
     sample = "each step: one oracle step on the centred window holding %.0f%% of the workload (%d particles in)" % (
         100 * frac, len(x))
+    cfg = dict(desc)
+    if frac < 1.0:
+        cfg["workload"] = ("centred window holding %.0f%% of the workload (%d particles) of: %s"
+                           % (100 * frac, len(x), desc["workload"]))
+        cfg["n"] = int(len(x))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": desc,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -867,7 +994,7 @@ def run_viscous(args):
     err = max(abs(np.sum(G * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2 * 0.03 ** 2))) -
                   gamma * 0.03 ** 2 / s2 * np.exp(-(cx * cx + cy * cy) / (2 * s2))) / gamma
               for cx, cy in [(0.0, 0.0), (0.03, 0.0), (0.05, 0.04), (-0.08, 0.02), (0.0, -0.1)])
-    # e_u (Sec. 6): L2 error of the smoothed particle velocity (eps = 3h,
+    # e_u (Sec. 5): L2 error of the smoothed particle velocity (eps = 3h,
     # direct sum) against the Lamb-Oseen velocity, midpoint rule on a
     # 200 x 200 grid over A = [-1.5, 1.5]^2
     gq = -1.5 + (np.arange(200) + 0.5) * 0.015
@@ -927,7 +1054,7 @@ def removal_workload():
 
 
 def run_removal(args):
-    """Particle removal (outlook of Sec. 7) on a crowded 1.1M cloud: input
+    """Particle removal (outlook of Sec. 6.2) on a crowded 1.1M cloud: input
     particles per second of whole passes, and the oracle's pass on the host
     cores for context."""
     import torch

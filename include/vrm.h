@@ -425,7 +425,7 @@ vrm_status vrm_learned_targets(const int32_t* list, int32_t m, const int32_t* sl
 /*
  * One SSP-RK3 (Shu-Osher) step of the viscous particle method: positions
  * move with an analytic velocity, circulations follow the diffusion operator
- * (the heat part of Sec. 3; the velocity of Sec. 6's Lamb-Oseen test case
+ * (the heat part of Sec. 3; the velocity of Sec. 5's Lamb-Oseen test case
  * stands in for the Biot-Savart law).  Growth control and insertion run once,
  * on the step's initial cloud; neighbourhoods and weights (LP, or the learned
  * proposal with vrm_set_mlp) are rebuilt at each of the three stages:
@@ -449,7 +449,7 @@ typedef struct vrm_velocity {
 } vrm_velocity;
 
 /*
- * Smoothed Biot-Savart velocity by direct summation (Sec. 6, Eq.
+ * Smoothed Biot-Savart velocity by direct summation (Sec. 5, Eq.
  * smoothkernel): u_h(x) = sum_j Gamma_j K_eps(x - x_j) with
  * K_eps(x) = (-y, x)/(2 pi |x|^2) (1 - exp(-|x/eps|^2)), K_eps(0) = 0, at the m
  * targets (xt, yt) from the n sources (xs, ys, gamma); all device pointers,
@@ -478,7 +478,21 @@ vrm_status vrm_stage_times(vrm_ctx* ctx, float* ms);
 int64_t vrm_launch_count(void);
 
 /*
- * Particle removal (the outlook of Sec. 7): where particles have come closer
+ * Peak FMA probe (no paper counterpart: the roofline denominator of the LP
+ * kernels, which are bound by FP64 and binary32 arithmetic).  Enqueues one
+ * kernel of `blocks` blocks of 256 threads, each thread running 8
+ * independent chains of fused multiply-adds for iters x 16 steps, in FP64
+ * (fp64 != 0) or FP32.  sink: device buffer of blocks + 1 elements of that
+ * type (written, contents meaningless).  *flops = the floating-point
+ * operations the launch performs (2 per FMA); the caller times the launch
+ * on `stream` (divide *flops by the duration).  VRM_ERR_ARG for
+ * non-positive sizes or null pointers.
+ */
+vrm_status vrm_fma_probe(int32_t fp64, int32_t blocks, int32_t iters, void* sink, double* flops,
+                         cudaStream_t stream);
+
+/*
+ * Particle removal (the outlook of Sec. 6.2): where particles have come closer
  * than r h to one another (inside the inner bound of Eq. neighbourhood),
  * redistribute one of each such pair to its neighbours by an approximation
  * of the identity operator and remove it.
@@ -510,12 +524,13 @@ vrm_status vrm_remove_close(vrm_ctx* ctx, const double* x, const double* y, cons
 
 /*
  * The neighbourhood search of vrm_build_neighbourhoods (same outputs, bit for
- * bit) for callers that cannot allocate memory when they need it: code that
- * runs while a stream is being captured into a CUDA graph (an allocation
- * there breaks or serialises the capture), real-time loops with no room for
- * allocator latency, and applications whose memory is all handed to their
- * own pool beforehand.  The paper has no counterpart; it is a service of this
- * library.
+ * bit) for callers that cannot allocate device memory when they need
+ * neighbourhoods: applications that hand all device memory to their own pool
+ * at start-up and forbid allocations afterwards (for instance a host program
+ * that loads this library as a plug-in and owns every buffer), and real-time
+ * loops whose latency budget has no room for cudaMalloc/cudaFree, which can
+ * take milliseconds and synchronise the device.  The paper has no
+ * counterpart; it is a service of this library.
  *
  * It takes the parameters instead of a context and calls no cudaMalloc,
  * cudaFree or other allocating routine.  Its scratch is one fixed device
@@ -525,10 +540,14 @@ vrm_status vrm_remove_close(vrm_ctx* ctx, const double* x, const double* y, cons
  * The first call on a device looks the array's device address up
  * (cudaGetSymbolAddress, once per device, with that device current); make
  * that first call before any stream capture.  Every call shares the array
- * and overwrites what the previous call left there, so calls whose work
- * overlaps on the GPU (two streams, or two host threads) race: serialise
- * them.  Arguments, outputs, errors and the optional max_count are as for
- * vrm_build_neighbourhoods; only r, R, h and k_cap of *p are used.
+ * and overwrites what the previous call left there (the counters it needs
+ * at zero are cleared on the stream at the start of each call), so calls
+ * whose work overlaps on the GPU (two streams, or two host threads) race:
+ * serialise them.  Arguments, outputs and errors are as for
+ * vrm_build_neighbourhoods; only r, R, h and k_cap of *p are used.  With
+ * max_count non-NULL the call copies two small records to the host and waits
+ * for the stream (it also then reports NaN/Inf input and rows wider than
+ * k_cap); with max_count NULL it only enqueues work on the stream.
  */
 vrm_status vrm_build_neighbourhoods_noalloc(const vrm_params* p, const double* x, const double* y, int32_t n,
                                             int32_t* nbr_count, int32_t* nbr_idx, uint8_t* seg_mask, int32_t* small,

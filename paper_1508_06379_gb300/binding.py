@@ -110,6 +110,7 @@ SIGNATURES = {
     "vrm_set_timing": (ctypes.c_int, [P, I32]),
     "vrm_stage_times": (ctypes.c_int, [P, P]),
     "vrm_launch_count": (ctypes.c_int64, []),
+    "vrm_fma_probe": (ctypes.c_int, [I32, I32, I32, P, P, P]),
     "vrm_build_neighbourhoods_noalloc": (ctypes.c_int, [P, P, P, I32, P, P, P, P, P, P]),
     "vrm_batch_create": (ctypes.c_int, [P, I32, P]),
     "vrm_batch_destroy": (None, [P]),
@@ -166,6 +167,31 @@ def _lib_handle():
 def launch_count():
     """Kernels the library has launched in this process."""
     return int(_lib_handle().vrm_launch_count())
+
+
+def fma_peak(fp64=True, blocks=None, iters=None, reps=3):
+    """Peak FMA rate of this GPU in flop/s (best of `reps` launches of
+    vrm_fma_probe, timed with CUDA events on the current stream)."""
+    lib = _lib_handle()
+    dev = torch.cuda.current_device()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = blocks or 8 * sms
+    iters = iters or (200 if fp64 else 12800)
+    sink = torch.empty(blocks + 1, dtype=torch.float64 if fp64 else torch.float32, device="cuda")
+    fl = ctypes.c_double()
+    best = 0.0
+    for _ in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = lib.vrm_fma_probe(int(bool(fp64)), int(blocks), int(iters), ctypes.c_void_p(sink.data_ptr()),
+                               ctypes.byref(fl), _stream())
+        e1.record()
+        if st != VRM_OK:
+            raise VRMError(st, "vrm_fma_probe")
+        e1.synchronize()
+        best = max(best, fl.value / (e0.elapsed_time(e1) * 1e-3))
+    return best
 
 
 def build_neighbourhoods_noalloc(x, y, n, h, r=0.5, R=2.0, k_cap=32, out=None, max_count=True):
