@@ -58,6 +58,9 @@ struct vrm::Scratch {
   int* retry_list = nullptr;  // small LPs re-run in FP64
   uint8_t *seg_mask = nullptr, *status = nullptr;
   double *f = nullptr, *fii = nullptr;
+  // the stencils transposed per target (the application's lists)
+  int *tcount = nullptr, *tsrc = nullptr;
+  double* tw = nullptr;
   // counters and state
   DevStats* ds = nullptr;
   int* counters = nullptr;  // [0] |D|, [1] first open list length
@@ -155,7 +158,8 @@ void free_scratch(Scratch& s) {
                   s.mask, r.open, r.open_next, r.cnt, r.cpos, r.keep_flag, r.keep_pos, r.cx, r.cy, r.keep, r.apos,
                   r.cg.grid, r.cg.cell_key, r.cg.cell_rank, r.cg.cell_count, r.cg.cell_start, r.cg.sorted_idx,
                   r.cg.sorted_xy, r.cg.sorted_loc, r.cg.bbox, r.scan_tmp, s.nbr_count, s.nbr_idx, s.small, s.cols,
-                  s.fail_list, s.retry_list, s.seg_mask, s.status, s.f, s.fii, s.ds, s.counters, s.st};
+                  s.fail_list, s.retry_list, s.seg_mask, s.status, s.f, s.fii, s.tcount, s.tsrc, s.tw, s.ds,
+                  s.counters, s.st};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   void* hp[] = {s.h_ds, s.h_counters, s.h_grid, s.h_params, s.h_state};
@@ -334,10 +338,13 @@ cudaError_t enqueue_stage_weights(vrm_ctx* ctx, const double* x, const double* y
                           s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
                           st)) != cudaSuccess)
     return e;
-  // rows in visiting order (the application and the learned slots order
+  // rows of the diffused particles only (the LPs and the learned slots read
+  // no other row; the application goes through the transposed stencils), in
+  // visiting order (the learned slots and the full-neighbourhood LP order
   // their entries themselves)
-  if ((e = search_all_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, cap, n_cur, s.nbr_count,
-                          s.nbr_idx, s.seg_mask, s.small, s.ds, st, false)) != cudaSuccess)
+  if ((e = search_list_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.cell_key, s.cell_rank,
+                           s.dlist, s.counters + 0, cap, s.nbr_count, s.nbr_idx, s.seg_mask, s.small, s.ds, st)) !=
+      cudaSuccess)
     return e;
   const int* lp_list = s.dlist;
   const int* lp_count = s.counters + 0;
@@ -425,6 +432,9 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.status, n);
   VRM_ALLOC(s.f, (long)n * ctx->c.w);
   VRM_ALLOC(s.fii, n);
+  VRM_ALLOC(s.tcount, n);
+  VRM_ALLOC(s.tsrc, (long)n * k);
+  VRM_ALLOC(s.tw, (long)n * k);
   VRM_ALLOC(s.ds, 1);
   VRM_ALLOC(s.counters, 8);
   VRM_ALLOC(s.st, 1);
@@ -604,10 +614,13 @@ cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const doub
                           s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
                           st)) != cudaSuccess)
     return e;
-  // rows in visiting order (the application and the learned slots order
+  // rows of the diffused particles only (the LPs and the learned slots read
+  // no other row; the application goes through the transposed stencils), in
+  // visiting order (the learned slots and the full-neighbourhood LP order
   // their entries themselves)
-  if ((e = search_all_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, cap, n_cur, s.nbr_count,
-                          s.nbr_idx, s.seg_mask, s.small, s.ds, st, false)) != cudaSuccess)
+  if ((e = search_list_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.cell_key, s.cell_rank,
+                           s.dlist, s.counters + 0, cap, s.nbr_count, s.nbr_idx, s.seg_mask, s.small, s.ds, st)) !=
+      cudaSuccess)
     return e;
   if ((e = mark(ctx, VRM_STAGE_LP_SMALL, st)) != cudaSuccess) return e;
   const int* lp_list = s.dlist;
@@ -627,8 +640,9 @@ cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const doub
                    s.ds, 0.0, st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
     return e;
   if ((e = mark(ctx, VRM_STAGE_APPLY, st)) != cudaSuccess) return e;
-  if ((e = apply_gather_dev(c, cap, n_cur, cap, &s.st->n, gamma_in, s.diffused, s.nbr_count, s.nbr_idx, s.cols, s.f,
-                            s.fii, s.sorted_idx, nullptr, gamma_out, 0.0, &s.st->dt, st)) != cudaSuccess)
+  if ((e = apply_transposed_dev(c, cap, n_cur, cap, &s.st->n, gamma_in, s.diffused, s.dlist, s.counters + 0, s.cols,
+                                s.f, s.fii, s.tcount, s.tsrc, s.tw, s.ds, nullptr, gamma_out, 0.0, &s.st->dt, st)) !=
+      cudaSuccess)
     return e;
   if ((e = mark(ctx, VRM_STAGE_COUNT, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(s.h_ds, s.ds, sizeof(DevStats), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
@@ -1093,9 +1107,9 @@ vrm_status vrm_rk3_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t c
     const double* px = move ? Xs[k] : x;
     const double* py = move ? Ys[k] : y;
     VRM_CUDA(enqueue_stage_weights(ctx, px, py, capacity, stream));
-    VRM_CUDA(apply_gather_dev(ctx->c, capacity, n_cur, k == 0 ? n : capacity, k == 0 ? nullptr : n_cur, Gs[k],
-                              s.diffused, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii, s.sorted_idx, ctx->rk_dg,
-                              nullptr, 0.0, nullptr, stream));
+    VRM_CUDA(apply_transposed_dev(ctx->c, capacity, n_cur, k == 0 ? n : capacity, k == 0 ? nullptr : n_cur, Gs[k],
+                                  s.diffused, s.dlist, s.counters + 0, s.cols, s.f, s.fii, s.tcount, s.tsrc, s.tw,
+                                  s.ds, ctx->rk_dg, nullptr, 0.0, nullptr, stream));
     const double *us = nullptr, *vs = nullptr;
     if (V.kind == VRM_VEL_BIOT_SAVART) {
       // the stage's own velocity at every stage particle; in the first stage

@@ -158,6 +158,150 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same application through the transpose of the stencils (the step's
+// form).  k_transpose turns every stencil entry (i -> j, f~_ij) of the
+// diffused particles into an entry of target j's list (source i, weight),
+// at most ts per target (the in-degree of j is at most the size of its
+// annulus row, so ts = k_cap suffices whenever the rows fit); the slot
+// counter is an integer atomic, so each list holds the right entries in an
+// order that varies.  k_apply_t then sorts each target's few entries by
+// source index and adds the terms in that order with the self term at
+// i = j, exactly the sum of k_apply: no neighbour rows and no search of the
+// sources' stencils, and a target's entries are contiguous.
+// ---------------------------------------------------------------------------
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_transpose(const int* __restrict__ list, const int* __restrict__ list_count,
+                                                      const int* __restrict__ cols, const double* __restrict__ f,
+                                                      int* __restrict__ tcount, int* __restrict__ tsrc,
+                                                      double* __restrict__ tw, int ts, DevStats* __restrict__ ds) {
+  const int m = *list_count;
+  int widest = 0;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) {
+    const int i = list[t];
+    const int4* cr = reinterpret_cast<const int4*>(cols + (size_t)i * W);
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) {
+      const int4 a = cr[q];
+      const int js[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = js[u];
+        if (j < 0) continue;
+        const int slot = atomicAdd(&tcount[j], 1);
+        if (slot < ts) {
+          tsrc[(size_t)j * ts + slot] = i;
+          tw[(size_t)j * ts + slot] = f[(size_t)i * W + 4 * q + u];
+        } else {
+          widest = slot + 1 > widest ? slot + 1 : widest;
+        }
+      }
+    }
+  }
+  // a list longer than ts (only where some row is wider than k_cap) makes
+  // the step report a capacity error through the widest-row statistic
+  if (widest) atomicMax(&ds->max_count, widest);
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(kBlock) k_apply_t(Consts c, int n, const int* __restrict__ n_dev, int n_gamma,
+                                                    const int* __restrict__ n_gamma_dev,
+                                                    const double* __restrict__ gamma,
+                                                    const uint8_t* __restrict__ diffused,
+                                                    const int* __restrict__ tcount, const int* __restrict__ tsrc,
+                                                    const double* __restrict__ tw, int ts,
+                                                    const double* __restrict__ fii, double* __restrict__ dgamma,
+                                                    double* __restrict__ gamma_out, double dt,
+                                                    const double* __restrict__ dt_dev) {
+  if (n_dev) n = *n_dev;
+  if (n_gamma_dev) n_gamma = *n_gamma_dev;
+  if (dt_dev) dt = *dt_dev;
+  for (long jj = (long)blockIdx.x * blockDim.x + threadIdx.x; jj < n; jj += (long)gridDim.x * blockDim.x) {
+    const int j = (int)jj;
+    const int cnt0 = tcount[j];
+    const int cnt = cnt0 < ts ? cnt0 : ts;
+    const bool self_src = j < n_gamma && diffused[j];
+    const double gj = j < n_gamma ? gamma[j] : 0.0;
+    const Acc selfv = self_src ? mul_acc<Acc>(fii[j], gj) : Acc(0);
+    const int* src = tsrc + (size_t)j * ts;
+    const double* wt = tw + (size_t)j * ts;
+    Acc acc = Acc(0);
+    bool self_done = !self_src;
+    if (cnt <= 8) {
+      // nearly all targets: every term loaded at once, sorted by source
+      int mi[8];
+      Acc term[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        mi[k] = INT_MAX;
+        term[k] = Acc(0);
+        if (k < cnt) {
+          const int i = src[k];
+          mi[k] = i;
+          term[k] = mul_acc<Acc>(wt[k], gamma[i]);
+        }
+      }
+      sort8_terms(mi, term);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (mi[k] == INT_MAX) break;
+        if (!self_done && mi[k] > j) {
+          acc = add_acc(acc, selfv);
+          self_done = true;
+        }
+        acc = add_acc(acc, term[k]);
+      }
+    } else {
+      // long lists: the smallest source not yet added, one at a time
+      int last = -1;
+      for (int r = 0; r < cnt; ++r) {
+        int ib = INT_MAX, kb = 0;
+        for (int k = 0; k < cnt; ++k) {
+          const int i = src[k];
+          if (i > last && i < ib) {
+            ib = i;
+            kb = k;
+          }
+        }
+        last = ib;
+        if (!self_done && ib > j) {
+          acc = add_acc(acc, selfv);
+          self_done = true;
+        }
+        acc = add_acc(acc, mul_acc<Acc>(wt[kb], gamma[ib]));
+      }
+    }
+    if (!self_done) acc = add_acc(acc, selfv);
+    const double dg = __dmul_rn(c.nu_over_h2, (double)acc);
+    if (dgamma) dgamma[j] = dg;
+    if (gamma_out) gamma_out[j] = __fma_rn(dt, dg, gj);
+  }
+}
+
+cudaError_t apply_transposed_dev(const Consts& c, int n_bound, const int* n_dev, int n_gamma, const int* n_gamma_dev,
+                                 const double* gamma, const uint8_t* diffused, const int* list, const int* list_count,
+                                 const int* cols, const double* f, const double* fii, int* tcount, int* tsrc,
+                                 double* tw, DevStats* ds, double* dgamma, double* gamma_out, double dt,
+                                 const double* dt_dev, cudaStream_t s) {
+  if (n_bound <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(tcount, 0, sizeof(int) * (size_t)n_bound, s);
+  if (e != cudaSuccess) return e;
+  const int ts = c.k_cap;
+  const int blocks = (int)(((long)n_bound + kBlock - 1) / kBlock);
+  if (c.order == 2)
+    k_transpose<12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, tcount, tsrc, tw, ts, ds);
+  else
+    k_transpose<8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, tcount, tsrc, tw, ts, ds);
+  note_launch();
+  const int tb = c.apply_block;
+  const int ab = (int)(((long)n_bound + tb - 1) / tb);
+  auto kern = c.precision == VRM_PREC_MIXED ? k_apply_t<float> : k_apply_t<double>;
+  kern<<<ab, tb, 0, s>>>(c, n_bound, n_dev, n_gamma, n_gamma_dev, gamma, diffused, tcount, tsrc, tw, ts, fii, dgamma,
+                         gamma_out, dt, dt_dev);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t apply_gather_dev(const Consts& c, int n_bound, const int* n_dev, int n_gamma, const int* n_gamma_dev,
                              const double* gamma, const uint8_t* diffused, const int* nbr_count, const int* nbr_idx,
                              const int* cols, const double* f, const double* fii, const int* order, double* dgamma,

@@ -247,6 +247,13 @@ cudaError_t search_all_dev(const Consts& c, const Grid* g, const int* cell_start
                            const float2* sorted_loc, const int* sorted_idx, int n_bound, const int* n_dev,
                            int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small, DevStats* ds,
                            cudaStream_t s, bool sorted = true);
+// Rows, masks and small neighbourhoods of the listed particles only (rows in
+// visiting order, padded to whole 32-byte sectors).
+cudaError_t search_list_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
+                            const float2* sorted_loc, const int* sorted_idx, const int* cell_key,
+                            const int* cell_rank, const int* list, const int* list_count, int m_bound,
+                            int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small, DevStats* ds,
+                            cudaStream_t s);
 cudaError_t search_masks_list_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
                                   const float2* sorted_loc, const int* sorted_idx, const int* cell_key,
                                   const int* cell_rank, const int* list, const int* list_count, int m_bound,
@@ -314,6 +321,14 @@ cudaError_t lp_clear(int n, int w, const uint8_t* diffused, int* cols, double* f
 cudaError_t apply_gather(const Consts& c, int n, int n_gamma, const double* gamma, const uint8_t* diffused,
                          const int* nbr_count, const int* nbr_idx, const int* cols, const double* f, const double* fii,
                          const int* order, double* dgamma, double* gamma_out, double dt, cudaStream_t s);
+// The step's application: the stencils of the listed (diffused) particles
+// transposed into per-target lists (tcount[n_bound], tsrc and tw of
+// n_bound x k_cap), then the same sums as apply_gather.
+cudaError_t apply_transposed_dev(const Consts& c, int n_bound, const int* n_dev, int n_gamma, const int* n_gamma_dev,
+                                 const double* gamma, const uint8_t* diffused, const int* list, const int* list_count,
+                                 const int* cols, const double* f, const double* fii, int* tcount, int* tsrc,
+                                 double* tw, DevStats* ds, double* dgamma, double* gamma_out, double dt,
+                                 const double* dt_dev, cudaStream_t s);
 cudaError_t apply_gather_dev(const Consts& c, int n_bound, const int* n_dev, int n_gamma, const int* n_gamma_dev,
                              const double* gamma, const uint8_t* diffused, const int* nbr_count, const int* nbr_idx,
                              const int* cols, const double* f, const double* fii, const int* order, double* dgamma,

@@ -41,7 +41,13 @@ __device__ __forceinline__ int exact_member(const Consts& c, const double2& pi, 
 // distance and its particle, and a flag `amb` set when another member of
 // the segment lies within 2 bands of it (then the FP32 order may differ from
 // the FP64 order, and a second pass decides that segment exactly).
-template <int KCAP, bool SORTED>
+//
+// LIST = true: only the particles of `list` (list_count of them; the step's
+// diffused set, the only particles whose rows the step reads), each located
+// in the sorted arrays through its cell key and rank; threads follow the
+// list's order.  Rows are then padded with -1 to the end of their last
+// 32-byte sector, so that the sector is written whole.
+template <int KCAP, bool SORTED, bool LIST = false>
 __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __restrict__ gp,
                                                        const int* __restrict__ cell_start,
                                                        const double2* __restrict__ sxy,
@@ -50,7 +56,10 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
                                                        const int* __restrict__ n_dev,
                                                        int* __restrict__ nbr_count, int* __restrict__ nbr_idx,
                                                        uint8_t* __restrict__ seg_mask, int* __restrict__ small,
-                                                       DevStats* __restrict__ ds) {
+                                                       DevStats* __restrict__ ds,
+                                                       const int* __restrict__ list = nullptr,
+                                                       const int* __restrict__ cell_key = nullptr,
+                                                       const int* __restrict__ cell_rank = nullptr) {
   if (n_dev) n = *n_dev;
   const Grid g = *gp;
   const int k_cap = c.row_cap < KCAP ? c.row_cap : KCAP;  // entries kept
@@ -63,11 +72,25 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
   __shared__ float s_bf[8][kBlock];
   __shared__ int s_bj[8][kBlock];
   const int tx = threadIdx.x;
-  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (long)gridDim.x * blockDim.x) {
-    const int i = sidx[p];
+  for (long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x; t0 < n; t0 += (long)gridDim.x * blockDim.x) {
+    int i, cx, cy;
+    long p;
+    if (LIST) {
+      i = list[t0];
+      const int key = cell_key[i];
+      p = cell_start[key] + cell_rank[i];
+      cy = key / g.nx;
+      cx = key - cy * g.nx;
+    } else {
+      p = t0;
+      i = sidx[p];
+    }
     const double2 pi = sxy[p];
     const float2 li = sloc[p];
-    const int cx = grid_cell_x(g, pi.x), cy = grid_cell_y(g, pi.y);
+    if (!LIST) {
+      cx = grid_cell_x(g, pi.x);
+      cy = grid_cell_y(g, pi.y);
+    }
     int list[KCAP];
     int cnt = 0;
 #pragma unroll
@@ -198,6 +221,10 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
     const int m = cnt < k_cap ? cnt : k_cap;
     int* row = nbr_idx + (size_t)i * stride;
     for (int t = 0; t < m; ++t) row[t] = list[t];
+    if (LIST) {
+      const int pad = ((m + 7) & ~7) < (int)stride ? ((m + 7) & ~7) : (int)stride;
+      for (int t = m; t < pad; ++t) row[t] = -1;
+    }
     seg_mask[i] = (uint8_t)mask;
     int4* sm = reinterpret_cast<int4*>(small + (size_t)i * 8);
     sm[0] = make_int4(bj[0], bj[1], bj[2], bj[3]);
@@ -301,6 +328,29 @@ cudaError_t search_all_dev(const Consts& c, const Grid* g, const int* cell_start
   } else {
     if (sorted) VRM_SEARCH_LAUNCH(VRM_KCAP_MAX, true); else VRM_SEARCH_LAUNCH(VRM_KCAP_MAX, false);
   }
+#undef VRM_SEARCH_LAUNCH
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t search_list_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
+                            const float2* sorted_loc, const int* sorted_idx, const int* cell_key,
+                            const int* cell_rank, const int* list, const int* list_count, int m_bound,
+                            int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small, DevStats* ds,
+                            cudaStream_t s) {
+  if (m_bound <= 0) return cudaSuccess;
+  const int tb = c.search_block;
+  const int blocks = (int)(((long)m_bound + tb - 1) / tb);
+#define VRM_SEARCH_LAUNCH(K)                                                                                       \
+  k_search_all<K, false, true><<<blocks, tb, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, m_bound, \
+                                                     list_count, nbr_count, nbr_idx, seg_mask, small, ds, list,     \
+                                                     cell_key, cell_rank)
+  if (c.row_cap <= 16)
+    VRM_SEARCH_LAUNCH(16);
+  else if (c.row_cap <= 24)
+    VRM_SEARCH_LAUNCH(24);
+  else
+    VRM_SEARCH_LAUNCH(VRM_KCAP_MAX);
 #undef VRM_SEARCH_LAUNCH
   note_launch();
   return cudaGetLastError();
