@@ -160,47 +160,67 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
 
 // ---------------------------------------------------------------------------
 // The same application through the transpose of the stencils (the step's
-// form).  k_transpose turns every stencil entry (i -> j, f~_ij) of the
-// diffused particles into an entry of target j's list (source i, weight),
-// at most ts per target (the in-degree of j is at most the size of its
-// annulus row, so ts = k_cap suffices whenever the rows fit); the slot
-// counter is an integer atomic, so each list holds the right entries in an
-// order that varies.  k_apply_t then sorts each target's few entries by
-// source index and adds the terms in that order with the self term at
-// i = j, exactly the sum of k_apply: no neighbour rows and no search of the
-// sources' stencils, and a target's entries are contiguous.
+// form), as a compact CSR by target.  k_t_claim gives every stencil entry
+// (i -> j, f~_ij) of the diffused particles a place in target j's list:
+// an integer atomic counter per target returns the place (the counts are
+// exact, the order of a list varies), kept per entry; an exclusive scan of
+// the counts gives the lists' offsets; k_t_fill writes each entry (source,
+// weight) as one 16-byte record at offset + place, so that the lists lie
+// back to back and every sector of the array is written whole.  k_apply_t
+// sorts a target's few records by source index and adds the terms in that
+// order with the self term at i = j: exactly the sum of k_apply, with no
+// neighbour rows and no search of the sources' stencils.
 // ---------------------------------------------------------------------------
+struct TEntry {
+  int i, pad;
+  double w;
+};
+
 template <int W>
-__global__ void __launch_bounds__(kBlock) k_transpose(const int* __restrict__ list, const int* __restrict__ list_count,
-                                                      const int* __restrict__ cols, const double* __restrict__ f,
-                                                      int* __restrict__ tcount, int* __restrict__ tsrc,
-                                                      double* __restrict__ tw, int ts, DevStats* __restrict__ ds) {
+__global__ void __launch_bounds__(kBlock) k_t_claim(const int* __restrict__ list, const int* __restrict__ list_count,
+                                                    const int* __restrict__ cols, int* __restrict__ tcount,
+                                                    uint8_t* __restrict__ tplace) {
   const int m = *list_count;
-  int widest = 0;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) {
     const int i = list[t];
     const int4* cr = reinterpret_cast<const int4*>(cols + (size_t)i * W);
+    int js[W];
 #pragma unroll
     for (int q = 0; q < W / 4; ++q) {
       const int4 a = cr[q];
-      const int js[4] = {a.x, a.y, a.z, a.w};
+      js[4 * q] = a.x;
+      js[4 * q + 1] = a.y;
+      js[4 * q + 2] = a.z;
+      js[4 * q + 3] = a.w;
+    }
+    // every request first (their round trips overlap), then the places
+    int place[W];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = js[u];
-        if (j < 0) continue;
-        const int slot = atomicAdd(&tcount[j], 1);
-        if (slot < ts) {
-          tsrc[(size_t)j * ts + slot] = i;
-          tw[(size_t)j * ts + slot] = f[(size_t)i * W + 4 * q + u];
-        } else {
-          widest = slot + 1 > widest ? slot + 1 : widest;
-        }
-      }
+    for (int u = 0; u < W; ++u) place[u] = js[u] >= 0 ? atomicAdd(&tcount[js[u]], 1) : 0;
+    // a list holds at most k_cap <= 32 entries whenever the rows fit
+#pragma unroll
+    for (int u = 0; u < W; ++u) tplace[(size_t)i * W + u] = (uint8_t)(place[u] < 255 ? place[u] : 255);
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_t_fill(const int* __restrict__ list, const int* __restrict__ list_count,
+                                                   const int* __restrict__ cols, const double* __restrict__ f,
+                                                   const uint8_t* __restrict__ tplace, const int* __restrict__ toff,
+                                                   TEntry* __restrict__ tent) {
+  const int m = *list_count;
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) {
+    const int i = list[t];
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      const int j = cols[(size_t)i * W + u];
+      if (j < 0) continue;
+      const int pos = toff[j] + tplace[(size_t)i * W + u];
+      const double w = f[(size_t)i * W + u];
+      reinterpret_cast<int4*>(tent)[pos] =
+          make_int4(i, 0, __double2loint(w), __double2hiint(w));
     }
   }
-  // a list longer than ts (only where some row is wider than k_cap) makes
-  // the step report a capacity error through the widest-row statistic
-  if (widest) atomicMax(&ds->max_count, widest);
 }
 
 template <typename Acc>
@@ -208,23 +228,23 @@ __global__ void __launch_bounds__(kBlock) k_apply_t(Consts c, int n, const int* 
                                                     const int* __restrict__ n_gamma_dev,
                                                     const double* __restrict__ gamma,
                                                     const uint8_t* __restrict__ diffused,
-                                                    const int* __restrict__ tcount, const int* __restrict__ tsrc,
-                                                    const double* __restrict__ tw, int ts,
-                                                    const double* __restrict__ fii, double* __restrict__ dgamma,
-                                                    double* __restrict__ gamma_out, double dt,
-                                                    const double* __restrict__ dt_dev) {
+                                                    const int* __restrict__ tcount, const int* __restrict__ toff,
+                                                    const TEntry* __restrict__ tent, const double* __restrict__ fii,
+                                                    double* __restrict__ dgamma, double* __restrict__ gamma_out,
+                                                    double dt, const double* __restrict__ dt_dev,
+                                                    DevStats* __restrict__ ds) {
   if (n_dev) n = *n_dev;
   if (n_gamma_dev) n_gamma = *n_gamma_dev;
   if (dt_dev) dt = *dt_dev;
+  int widest = 0;
   for (long jj = (long)blockIdx.x * blockDim.x + threadIdx.x; jj < n; jj += (long)gridDim.x * blockDim.x) {
     const int j = (int)jj;
-    const int cnt0 = tcount[j];
-    const int cnt = cnt0 < ts ? cnt0 : ts;
+    const int cnt = tcount[j];
+    widest = cnt > widest ? cnt : widest;
     const bool self_src = j < n_gamma && diffused[j];
     const double gj = j < n_gamma ? gamma[j] : 0.0;
     const Acc selfv = self_src ? mul_acc<Acc>(fii[j], gj) : Acc(0);
-    const int* src = tsrc + (size_t)j * ts;
-    const double* wt = tw + (size_t)j * ts;
+    const int4* rec = reinterpret_cast<const int4*>(tent) + toff[j];
     Acc acc = Acc(0);
     bool self_done = !self_src;
     if (cnt <= 8) {
@@ -236,9 +256,9 @@ __global__ void __launch_bounds__(kBlock) k_apply_t(Consts c, int n, const int* 
         mi[k] = INT_MAX;
         term[k] = Acc(0);
         if (k < cnt) {
-          const int i = src[k];
-          mi[k] = i;
-          term[k] = mul_acc<Acc>(wt[k], gamma[i]);
+          const int4 r = rec[k];
+          mi[k] = r.x;
+          term[k] = mul_acc<Acc>(__hiloint2double(r.w, r.z), gamma[r.x]);
         }
       }
       sort8_terms(mi, term);
@@ -257,7 +277,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_t(Consts c, int n, const int* 
       for (int r = 0; r < cnt; ++r) {
         int ib = INT_MAX, kb = 0;
         for (int k = 0; k < cnt; ++k) {
-          const int i = src[k];
+          const int i = rec[k].x;
           if (i > last && i < ib) {
             ib = i;
             kb = k;
@@ -268,7 +288,8 @@ __global__ void __launch_bounds__(kBlock) k_apply_t(Consts c, int n, const int* 
           acc = add_acc(acc, selfv);
           self_done = true;
         }
-        acc = add_acc(acc, mul_acc<Acc>(wt[kb], gamma[ib]));
+        const int4 rk = rec[kb];
+        acc = add_acc(acc, mul_acc<Acc>(__hiloint2double(rk.w, rk.z), gamma[ib]));
       }
     }
     if (!self_done) acc = add_acc(acc, selfv);
@@ -276,28 +297,39 @@ __global__ void __launch_bounds__(kBlock) k_apply_t(Consts c, int n, const int* 
     if (dgamma) dgamma[j] = dg;
     if (gamma_out) gamma_out[j] = __fma_rn(dt, dg, gj);
   }
+  // a list longer than k_cap (only where some row is wider than k_cap, which
+  // the rows of the diffused particles report themselves) makes the step
+  // report a capacity error through the widest-row statistic
+  widest = (int)__reduce_max_sync(0xffffffffu, (unsigned)widest);
+  if ((threadIdx.x & 31) == 0 && widest > c.k_cap) atomicMax(&ds->max_count, widest);
 }
 
 cudaError_t apply_transposed_dev(const Consts& c, int n_bound, const int* n_dev, int n_gamma, const int* n_gamma_dev,
                                  const double* gamma, const uint8_t* diffused, const int* list, const int* list_count,
-                                 const int* cols, const double* f, const double* fii, int* tcount, int* tsrc,
-                                 double* tw, DevStats* ds, double* dgamma, double* gamma_out, double dt,
-                                 const double* dt_dev, cudaStream_t s) {
+                                 const int* cols, const double* f, const double* fii, int* tcount, int* toff,
+                                 uint8_t* tplace, void* tent, int* scan_tmp, DevStats* ds, double* dgamma,
+                                 double* gamma_out, double dt, const double* dt_dev, cudaStream_t s) {
   if (n_bound <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(tcount, 0, sizeof(int) * (size_t)n_bound, s);
   if (e != cudaSuccess) return e;
-  const int ts = c.k_cap;
   const int blocks = (int)(((long)n_bound + kBlock - 1) / kBlock);
   if (c.order == 2)
-    k_transpose<12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, tcount, tsrc, tw, ts, ds);
+    k_t_claim<12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, tcount, tplace);
   else
-    k_transpose<8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, tcount, tsrc, tw, ts, ds);
+    k_t_claim<8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, tcount, tplace);
+  note_launch();
+  if ((e = scan_exclusive_i32_dev(tcount, toff, n_bound, n_dev, scan_tmp, s)) != cudaSuccess) return e;
+  TEntry* te = static_cast<TEntry*>(tent);
+  if (c.order == 2)
+    k_t_fill<12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, tplace, toff, te);
+  else
+    k_t_fill<8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, tplace, toff, te);
   note_launch();
   const int tb = c.apply_block;
   const int ab = (int)(((long)n_bound + tb - 1) / tb);
   auto kern = c.precision == VRM_PREC_MIXED ? k_apply_t<float> : k_apply_t<double>;
-  kern<<<ab, tb, 0, s>>>(c, n_bound, n_dev, n_gamma, n_gamma_dev, gamma, diffused, tcount, tsrc, tw, ts, fii, dgamma,
-                         gamma_out, dt, dt_dev);
+  kern<<<ab, tb, 0, s>>>(c, n_bound, n_dev, n_gamma, n_gamma_dev, gamma, diffused, tcount, toff, te, fii, dgamma,
+                         gamma_out, dt, dt_dev, ds);
   note_launch();
   return cudaGetLastError();
 }
