@@ -532,11 +532,16 @@ def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1, peaks=None):
         hbm, src = 6800.0, "of fallback"
     n_out = stats["n_out"]
     if stage == "search":
-        nbytes = n_out * 100.0
+        # the step searches the diffused particles: row, count, mask and
+        # small neighbourhood out, position in (about 100 B each)
+        nbytes = stats["n_diffused"] * 100.0
         kern = "k_search_all"
     elif stage == "apply":
-        nbytes = n_out * 69.0 + stats["n_diffused"] * 49.0
-        kern = "k_apply"
+        # Gamma in and out per target, (index, weight, source Gamma) per
+        # stencil entry (at most 5 per diffused particle for n = 1) and the
+        # diagonal
+        nbytes = n_out * 16.0 + stats["n_diffused"] * 6 * 20.0
+        kern = "k_apply_t"
     else:
         nbytes = n_out * 24.0
         kern = stage

@@ -164,12 +164,16 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
 // (i -> j, f~_ij) of the diffused particles a place in target j's list:
 // an integer atomic counter per target returns the place (the counts are
 // exact, the order of a list varies), kept per entry; an exclusive scan of
-// the counts gives the lists' offsets; k_t_fill writes each entry (source,
-// weight) as one 16-byte record at offset + place, so that the lists lie
-// back to back and every sector of the array is written whole.  k_apply_t
-// sorts a target's few records by source index and adds the terms in that
-// order with the self term at i = j: exactly the sum of k_apply, with no
-// neighbour rows and no search of the sources' stencils.
+// the counts gives the lists' offsets; k_t_fill writes each entry as one
+// 16-byte record (source, term f~_ij Gamma_i, the product rounded as the
+// gather rounds it) at offset + place, so that the lists lie back to back
+// and every sector of the array is written whole.  k_apply_t sorts a
+// target's few records by source index and adds the terms in that order
+// with the self term at i = j: exactly the sum of k_apply, with no
+// neighbour rows and no search of the sources' stencils.  The products are
+// taken in k_t_fill (a thread per source, its entries in lockstep, the FP64
+// pipe otherwise idle) and not in k_apply_t, whose lanes carry lists of
+// uneven length: there every FP64 instruction costs the warp's longest list.
 // ---------------------------------------------------------------------------
 struct TEntry {
   int i, pad;
@@ -203,22 +207,24 @@ __global__ void __launch_bounds__(kBlock) k_t_claim(const int* __restrict__ list
   }
 }
 
-template <int W>
+template <typename Acc, int W>
 __global__ void __launch_bounds__(kBlock) k_t_fill(const int* __restrict__ list, const int* __restrict__ list_count,
                                                    const int* __restrict__ cols, const double* __restrict__ f,
-                                                   const uint8_t* __restrict__ tplace, const int* __restrict__ toff,
-                                                   TEntry* __restrict__ tent) {
+                                                   const double* __restrict__ gamma, const uint8_t* __restrict__ tplace,
+                                                   const int* __restrict__ toff, TEntry* __restrict__ tent) {
   const int m = *list_count;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) {
     const int i = list[t];
+    const double gi = gamma[i];
 #pragma unroll
     for (int u = 0; u < W; ++u) {
       const int j = cols[(size_t)i * W + u];
       if (j < 0) continue;
       const int pos = toff[j] + tplace[(size_t)i * W + u];
-      const double w = f[(size_t)i * W + u];
-      reinterpret_cast<int4*>(tent)[pos] =
-          make_int4(i, 0, __double2loint(w), __double2hiint(w));
+      // the term f~_ij Gamma_i as the gather forms it (exact in a double
+      // for the fp32 product of the mixed precision)
+      const double term = (double)mul_acc<Acc>(f[(size_t)i * W + u], gi);
+      reinterpret_cast<int4*>(tent)[pos] = make_int4(i, 0, __double2loint(term), __double2hiint(term));
     }
   }
 }
@@ -258,7 +264,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_t(Consts c, int n, const int* 
         if (k < cnt) {
           const int4 r = rec[k];
           mi[k] = r.x;
-          term[k] = mul_acc<Acc>(__hiloint2double(r.w, r.z), gamma[r.x]);
+          term[k] = (Acc)__hiloint2double(r.w, r.z);
         }
       }
       sort8_terms(mi, term);
@@ -289,7 +295,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_t(Consts c, int n, const int* 
           self_done = true;
         }
         const int4 rk = rec[kb];
-        acc = add_acc(acc, mul_acc<Acc>(__hiloint2double(rk.w, rk.z), gamma[ib]));
+        acc = add_acc(acc, (Acc)__hiloint2double(rk.w, rk.z));
       }
     }
     if (!self_done) acc = add_acc(acc, selfv);
@@ -320,10 +326,18 @@ cudaError_t apply_transposed_dev(const Consts& c, int n_bound, const int* n_dev,
   note_launch();
   if ((e = scan_exclusive_i32_dev(tcount, toff, n_bound, n_dev, scan_tmp, s)) != cudaSuccess) return e;
   TEntry* te = static_cast<TEntry*>(tent);
-  if (c.order == 2)
-    k_t_fill<12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, tplace, toff, te);
-  else
-    k_t_fill<8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, tplace, toff, te);
+  const bool mixed = c.precision == VRM_PREC_MIXED;
+  if (c.order == 2) {
+    if (mixed)
+      k_t_fill<float, 12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, gamma, tplace, toff, te);
+    else
+      k_t_fill<double, 12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, gamma, tplace, toff, te);
+  } else {
+    if (mixed)
+      k_t_fill<float, 8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, gamma, tplace, toff, te);
+    else
+      k_t_fill<double, 8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, gamma, tplace, toff, te);
+  }
   note_launch();
   const int tb = c.apply_block;
   const int ab = (int)(((long)n_bound + tb - 1) / tb);

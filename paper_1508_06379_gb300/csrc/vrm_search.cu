@@ -19,7 +19,9 @@
 // order inside a step (SORTED = false: the application orders the few
 // matches itself, and a sorted insertion per member was a third of the
 // kernel); a row that overflows keeps the row_cap smallest indices either
-// way.  The closest particle of every segment is tracked in shared memory
+// way, except in the step's form over the diffused list (LIST), which
+// writes members straight to the row and cuts it at row_cap: the step
+// then repeats with whole rows or reports the capacity error.  The closest particle of every segment is tracked in shared memory
 // with ties to the smaller index.
 #include "vrm_internal.cuh"
 
@@ -91,7 +93,12 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
       cx = grid_cell_x(g, pi.x);
       cy = grid_cell_y(g, pi.y);
     }
-    int list[KCAP];
+    // LIST: members go straight to the row in visiting order (a row longer
+    // than row_cap is cut; the step then repeats with whole rows or reports
+    // the capacity error, so no smallest-index rule is needed); otherwise
+    // they are collected in a per-thread buffer first
+    int list[LIST ? 1 : KCAP];
+    int* const row_out = nbr_idx + (size_t)i * stride;
     int cnt = 0;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -140,7 +147,9 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
             s_bf[s][tx] = d2f;
             s_bj[s][tx] = j;
           }
-          if (SORTED || cnt >= k_cap) {
+          if (LIST) {
+            if (cnt < k_cap) row_out[cnt] = j;
+          } else if (SORTED || cnt >= k_cap) {
             if (!SORTED && cnt == k_cap) {
               // the row overflows (rare): order the entries kept so far, so
               // that it keeps the k_cap smallest indices like a sorted row
@@ -220,7 +229,8 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
     nbr_count[i] = cnt;
     const int m = cnt < k_cap ? cnt : k_cap;
     int* row = nbr_idx + (size_t)i * stride;
-    for (int t = 0; t < m; ++t) row[t] = list[t];
+    if (!LIST)
+      for (int t = 0; t < m; ++t) row[t] = list[t];
     if (LIST) {
       const int pad = ((m + 7) & ~7) < (int)stride ? ((m + 7) & ~7) : (int)stride;
       for (int t = m; t < pad; ++t) row[t] = -1;
