@@ -13,7 +13,8 @@
 // one byte at a time: each pass histograms the exact q-sums of the particles
 // whose key matches the bytes chosen so far; the last block of the pass to
 // finish scans the 256 buckets in parallel and picks the first byte at which
-// the running sum crosses the remaining budget.  Particles with key == T are
+// the running sum crosses the remaining budget.  Passes 3 to 7 run in one
+// single-block launch over the list of pass 2's matches.  Particles with key == T are
 // tied; the first k_tie of them by index stay out, found with a scan of the
 // tie flags.
 #include "vrm_internal.cuh"
@@ -295,6 +296,121 @@ __global__ void __launch_bounds__(256) k_reduce_pass(const double* __restrict__ 
   if (!done) choose_digit(st, c_bound, pass);
 }
 
+// Passes 3 to 7 in one block: they read only the short list of pass 2 (the
+// particles matching the two chosen bytes), so one block of 1024 threads
+// histograms each byte in shared memory and its first 256 threads choose the
+// byte (the same inclusive scan and rule as choose_digit), five passes in
+// one launch instead of five launches of mostly idle blocks.
+__global__ void __launch_bounds__(1024) k_reduce_tail(const double* __restrict__ g, ReduceState* __restrict__ st,
+                                                      const int* __restrict__ sub) {
+  __shared__ unsigned long long h[256][4];
+  __shared__ unsigned long long s_lo[256], s_hi[256];
+  __shared__ int s_sel;
+  const int b = threadIdx.x;
+  const int n = st->n_sub;
+  const int E = exponent_of_key(st->amax_bits);
+  for (int pass = 3; pass < 8; ++pass) {
+    if (st->done) return;  // uniform: written by thread 255 before the last barrier
+    for (int k = b; k < 256; k += blockDim.x) h[k][0] = h[k][1] = h[k][2] = h[k][3] = 0;
+    __syncthreads();
+    const unsigned long long prefix = st->prefix;
+    const int shift = 56 - 8 * pass;
+    const int lane = b & 31;
+    // whole warps step through the list; lanes holding the same byte merge
+    // their limb sums first (a list of equal keys would otherwise serialise
+    // on one shared address)
+    for (int base = b & ~31; base < n; base += blockDim.x) {
+      const int t = base + lane;
+      bool pending = false;
+      int d = 0;
+      unsigned long long lim[3] = {0, 0, 0};
+      if (t < n) {
+        const unsigned long long key = (unsigned long long)__double_as_longlong(g[sub[t]]) & 0x7FFFFFFFFFFFFFFFull;
+        if ((key >> (shift + 8)) == prefix) {
+          pending = true;
+          d = (int)((key >> shift) & 0xFF);
+          const u128 q = q_of_key(key, E);
+          lim[0] = (unsigned long long)(q & 0xFFFFFFFFull);
+          lim[1] = (unsigned long long)((q >> 32) & 0xFFFFFFFFull);
+          lim[2] = (unsigned long long)(q >> 64);
+        }
+      }
+      unsigned todo = __ballot_sync(0xffffffffu, pending);
+      while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int dl = __shfl_sync(0xffffffffu, d, leader);
+        const bool mine = pending && d == dl;
+        const unsigned peers = __ballot_sync(0xffffffffu, mine);
+        // 16-bit halves of the 32-bit limbs: sums of 32 lanes stay below 2^21
+        unsigned long long sum[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const unsigned lo = mine ? (unsigned)(lim[k] & 0xFFFFu) : 0u;
+          const unsigned hi = mine ? (unsigned)(lim[k] >> 16) : 0u;
+          sum[k] = (unsigned long long)__reduce_add_sync(0xffffffffu, lo) +
+                   ((unsigned long long)__reduce_add_sync(0xffffffffu, hi) << 16);
+        }
+        if (lane == leader) {
+          if (sum[0]) atomicAdd(&h[dl][0], sum[0]);
+          if (sum[1]) atomicAdd(&h[dl][1], sum[1]);
+          if (sum[2]) atomicAdd(&h[dl][2], sum[2]);
+          atomicAdd(&h[dl][3], (unsigned long long)__popc(peers));
+        }
+        if (mine) pending = false;
+        todo &= ~peers;
+      }
+    }
+    __syncthreads();
+    // inclusive scan of the 128-bit bucket sums over the first 256 threads
+    u128 v = 0, acc = 0;
+    if (b < 256) {
+      v = (u128)h[b][0] + ((u128)h[b][1] << 32) + ((u128)h[b][2] << 64);
+      acc = v;
+      s_lo[b] = (unsigned long long)acc;
+      s_hi[b] = (unsigned long long)(acc >> 64);
+    }
+    if (b == 0) s_sel = 255;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+      u128 add = 0;
+      if (b < 256 && b >= o) add = ((u128)s_hi[b - o] << 64) | (u128)s_lo[b - o];
+      __syncthreads();
+      if (b < 256) {
+        acc += add;
+        s_lo[b] = (unsigned long long)acc;
+        s_hi[b] = (unsigned long long)(acc >> 64);
+      }
+      __syncthreads();
+    }
+    const u128 tau = ((u128)st->tau_hi << 64) | (u128)st->tau_lo;
+    const u128 excl = acc - v;
+    if (b < 256 && acc > tau && excl <= tau) atomicMin(&s_sel, b);
+    __syncthreads();
+    if (b == s_sel) {
+      const u128 rem = tau - excl;
+      st->prefix = (prefix << 8) | (unsigned long long)b;
+      st->tau_lo = (unsigned long long)rem;
+      st->tau_hi = (unsigned long long)(rem >> 64);
+      if (pass == 7) {
+        // all particles with key == T have the same q_T > 0; the first k_tie
+        // by index fit: k_tie = max k <= count with k q_T <= rem (bisection)
+        const unsigned long long T = st->prefix;
+        const u128 qT = q_of_key(T, E);
+        unsigned long long lo = 0, hi = h[b][3];
+        while (lo < hi) {
+          const unsigned long long mid = (lo + hi + 1) / 2;
+          if ((u128)mid * qT <= rem) lo = mid;
+          else hi = mid - 1;
+        }
+        st->T = T;
+        st->k_tie = (int)lo;
+        st->done = 1;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void k_reduce_prepare(ReduceState* st, double c_bound) {
   if (st->amax_bits == 0 || !(c_bound < 1.0)) {
     // no circulation, or a bound of at least ||Gamma||_1: nothing diffuses
@@ -338,11 +454,11 @@ cudaError_t reduce_select_dev(const double* gamma, int n_bound, const int* n_dev
   k_reduce_init<<<1, 256, 0, s>>>(st); note_launch();
   k_absmax<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, ds); note_launch();
   k_reduce_prepare<<<1, 1, 0, s>>>(st, c_bound); note_launch();
-  for (int pass = 0; pass < 8; ++pass) {
-    // the later passes read the short list of pass 2 (kept in tie_rank, free until the tie scan)
-    const int pb = pass >= 3 ? (pblocks < sm_count() ? pblocks : sm_count()) : pblocks;
-    k_reduce_pass<<<pb, 256, 0, s>>>(gamma, n_bound, n_dev, st, c_bound, pass, tie_rank); note_launch();
+  for (int pass = 0; pass < 3; ++pass) {
+    // pass 2 lists its matches in tie_rank (free until the tie scan)
+    k_reduce_pass<<<pblocks, 256, 0, s>>>(gamma, n_bound, n_dev, st, c_bound, pass, tie_rank); note_launch();
   }
+  k_reduce_tail<<<1, 1024, 0, s>>>(gamma, st, tie_rank); note_launch();
   k_reduce_mark<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, diffused, tie_flag); note_launch();
   cudaError_t e = scan_exclusive_u8_dev(tie_flag, tie_rank, n_bound, n_dev, scan_tmp, s);
   if (e != cudaSuccess) return e;
