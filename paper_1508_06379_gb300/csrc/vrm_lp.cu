@@ -1014,6 +1014,131 @@ __global__ void __launch_bounds__(128, 3) k_lp_small32(Consts c, const double* _
   if (lane == 0 && n_retry) atomicAdd(&ds->lp_small_retries, (unsigned long long)n_retry);
 }
 
+// ---------------------------------------------------------------------------
+// The same LPs with the work split by warps: per block, kLpPivotWarps warps
+// take the columns and the certified binary32 pivots of 32 LPs each, and
+// kLpFinishWarps warps take the FP64 part (basis offsets, LU solve,
+// certificate, stencil) of the LPs the pivot warps finished in the round
+// before, handed over in shared memory (double-buffered, one block barrier
+// per round).  The FP64 pipe, the bottleneck of the LP, then works on one
+// batch while the binary32 and integer pipes work on the next, instead of
+// every warp alternating between the two phases; the finish warps also run
+// the FP64 solve with their lanes together.  Results are those of
+// k_lp_small32 bit for bit (the same device functions in the same order).
+// ---------------------------------------------------------------------------
+constexpr int kLpPivotWarps = 4;
+constexpr int kLpFinishWarps = 2;
+constexpr int kLpBatch = 32 * kLpPivotWarps;
+constexpr int kLpWsThreads = 32 * (kLpPivotWarps + kLpFinishWarps);
+
+template <int M, int W>
+__global__ void __launch_bounds__(kLpWsThreads, 2) k_lp_small32_ws(
+    Consts c, const double* __restrict__ x, const double* __restrict__ y, const int* __restrict__ list,
+    const int* __restrict__ list_count, const int* __restrict__ small, int* __restrict__ cols,
+    double* __restrict__ f, double* __restrict__ fii, uint8_t* __restrict__ status, int* __restrict__ fail_list,
+    int* __restrict__ retry_list, DevStats* __restrict__ ds, double nu_dt, const double* __restrict__ dt_dev,
+    double nu) {
+  static_assert(M == 5, "certified binary32 pivoting is written for the n = 1 rows");
+  if (dt_dev) nu_dt = nu * *dt_dev;
+  const int m = *list_count;
+  const double inv_h2 = 1.0 / (c.h * c.h);
+  const float inv_h32 = f32_of(c.inv_h);
+  LpTally tl;
+  int n_retry = 0;
+  const unsigned lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const bool pivot_warp = warp < kLpPivotWarps;
+  // hand-over of a batch: particle, basis (4 bits per row) | pivots << 20 |
+  // code << 27 | 1 << 30 (valid), and the sorted column indices
+  __shared__ int s_i[2][kLpBatch];
+  __shared__ int s_meta[2][kLpBatch];
+  __shared__ int s_cj[2][8][kLpBatch];
+  const long nchunks = ((long)m + kLpBatch - 1) / kLpBatch;
+  for (long r = 0;; ++r) {
+    const long chunk = (long)blockIdx.x + r * gridDim.x;  // pivoted in this round
+    const long prev = chunk - gridDim.x;                   // finished in this round
+    if (prev >= nchunks) break;
+    const int buf = (int)(r & 1);
+    if (pivot_warp) {
+      if (chunk < nchunks) {
+        const int slot = warp * 32 + (int)lane;
+        const long t = chunk * kLpBatch + slot;
+        const bool active = t < m;
+        int i = 0, it = 0, code = 0;
+        int basis[M];
+        bool unc = false;
+#pragma unroll
+        for (int q = 0; q < M; ++q) basis[q] = q;
+        if (active) {
+          i = list[t];
+          float xs[8], es[8];
+          int cj[8];
+          lp_columns32(x, y, small, i, x[i], y[i], inv_h32, cj, xs, es, unc);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) s_cj[buf][k][slot] = cj[k];
+          lp_pivots32<M>(xs, es, basis, it, code, unc);
+        }
+        int meta = 0;
+        if (active && !unc) {
+          meta = (1 << 30) | (code << 27) | (it << 20);
+#pragma unroll
+          for (int q = 0; q < M; ++q) meta |= basis[q] << (4 * q);
+        }
+        s_i[buf][slot] = i;
+        s_meta[buf][slot] = meta;
+        // warp-aggregated append to the FP64 retry list
+        const bool retry = active && unc;
+        const unsigned rb = __ballot_sync(0xffffffffu, retry);
+        if (rb) {
+          const int lead = __ffs(rb) - 1;
+          int slot0 = 0;
+          if ((int)lane == lead) slot0 = atomicAdd(&ds->n_retry, __popc(rb));
+          slot0 = __shfl_sync(0xffffffffu, slot0, lead);
+          if (retry) retry_list[slot0 + __popc(rb & ((1u << lane) - 1u))] = i;
+          n_retry += (lane == 0) ? __popc(rb) : 0;
+        }
+      }
+    } else if (r > 0) {
+      const int pb = buf ^ 1;
+#pragma unroll 1
+      for (int k = 0; k < kLpBatch / (32 * kLpFinishWarps); ++k) {
+        const int slot = (warp - kLpPivotWarps) * 32 + (int)lane + k * 32 * kLpFinishWarps;
+        const int meta = s_meta[pb][slot];
+        if (meta & (1 << 30)) {
+          const int i = s_i[pb][slot];
+          int basis[M];
+#pragma unroll
+          for (int q = 0; q < M; ++q) basis[q] = (meta >> (4 * q)) & 15;
+          const int it = (meta >> 20) & 127, code = (meta >> 27) & 3;
+          int cj[8];
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) cj[kk] = s_cj[pb][kk][slot];
+          // FP64 offsets of the basic columns, computed as lp_columns computes them
+          const double xi0 = x[i], yi0 = y[i];
+          double bxi[M], beta[M];
+#pragma unroll
+          for (int q = 0; q < M; ++q) {
+            int j = INT_MAX;
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) j = (basis[q] == M + kk) ? cj[kk] : j;
+            bxi[q] = 0.0;
+            beta[q] = 0.0;
+            if (j != INT_MAX) {
+              bxi[q] = __dmul_rn(__dsub_rn(x[j], xi0), c.inv_h);
+              beta[q] = __dmul_rn(__dsub_rn(y[j], yi0), c.inv_h);
+            }
+          }
+          lp_finish<M, W>(c, i, code, basis, it, cj, bxi, beta, cols, f, fii, status, fail_list, ds, nu_dt, inv_h2,
+                          tl);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  flush_stats(ds, tl.ok, tl.none, tl.maxpiv, tl.ratio, false, tl.solved, tl.pivots);
+  if (lane == 0 && n_retry) atomicAdd(&ds->lp_small_retries, (unsigned long long)n_retry);
+}
+
 // Monomial of Vandermonde row r at (xi, eta), rounded exactly as vcol<M>
 // rounds it: rows 0, 1 are xi, eta; 2, 3, 4 are xi xi, xi eta, eta eta; 5 to
 // 8 are (xi xi) xi, (xi xi) eta, xi (eta eta), (eta eta) eta.
@@ -1571,7 +1696,9 @@ cudaError_t lp_small(const Consts& c, const double* x, const double* y, const in
                      int cap, const int* small, int* cols, double* f, double* fii, uint8_t* status, int* fail_list,
                      int* retry_list, DevStats* ds, double nu_dt, cudaStream_t s, const double* dt_dev, double nu) {
   if (cap <= 0) return cudaSuccess;
-  const int tb = c.lp_block;
+  // lp_block = kLpWsThreads selects the warp-specialised binary32 LP; the
+  // other LP kernels then run with 128 threads per block
+  const int tb = c.lp_block == kLpWsThreads ? 128 : c.lp_block;
   int blocks = (int)(((long)cap + tb - 1) / tb);
   if (blocks > c.lp_blocks_per_sm * sm_count()) blocks = c.lp_blocks_per_sm * sm_count();
   if (c.order == 2) {
@@ -1586,8 +1713,15 @@ cudaError_t lp_small(const Consts& c, const double* x, const double* y, const in
     // certified binary32 pivots, then the uncertain particles in FP64
     cudaError_t e = cudaMemsetAsync(&ds->n_retry, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_lp_small32<5, 8><<<blocks, tb, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list,
-                                             retry_list, ds, nu_dt, dt_dev, nu);
+    if (c.lp_block == kLpWsThreads) {
+      // warp-specialised form: two resident blocks per SM
+      k_lp_small32_ws<5, 8><<<2 * sm_count(), kLpWsThreads, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii,
+                                                                  status, fail_list, retry_list, ds, nu_dt, dt_dev,
+                                                                  nu);
+    } else {
+      k_lp_small32<5, 8><<<blocks, tb, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list,
+                                               retry_list, ds, nu_dt, dt_dev, nu);
+    }
     note_launch();
     // the re-run list is a few percent of the LPs: one-warp blocks spread it
     // over every SM instead of over the first few hundred blocks
