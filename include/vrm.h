@@ -260,6 +260,23 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
                     double* gamma_out, double dt, int32_t* n_out, vrm_stats* stats, cudaStream_t stream);
 
 /*
+ * vrm_step in two halves, so that a caller can keep the GPU busy with a
+ * stream of steps (no runtime counterpart in the paper).  vrm_step_begin
+ * enqueues the step on the stream and returns at once (the first step on a
+ * new set of buffers, or after the capacity grew, builds the context's
+ * scratch and captured step first, and synchronises then); vrm_step_end
+ * waits for it and returns n_out and the statistics, repeating the step with
+ * whole rows if the schedule's row_cap cut one (as vrm_step does).
+ * Arguments as vrm_step.  Between the two calls the context and its buffers
+ * belong to the pending step: no other call on the context (VRM_ERR_ARG for
+ * a second vrm_step_begin or a vrm_step), and no change of its inputs.  Two
+ * contexts let a caller enqueue step k + 1 before waiting for step k.
+ */
+vrm_status vrm_step_begin(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capacity, const double* gamma_in,
+                          double* gamma_out, double dt, cudaStream_t stream);
+vrm_status vrm_step_end(vrm_ctx* ctx, int32_t* n_out, vrm_stats* stats);
+
+/*
  * Batched steps: many independent clouds (each with its own spacing h and
  * step dt) advanced by one call.  The clouds' steps are captured once as
  * parallel branches of one CUDA graph (per-cloud insertion loops included)

@@ -107,6 +107,8 @@ SIGNATURES = {
     "vrm_solve_weights": (ctypes.c_int, [P, P, P, I32, P, P, P, P, P, P, P, P, P, P]),
     "vrm_apply": (ctypes.c_int, [P, I32, I32, P, P, P, P, P, P, P, P, P]),
     "vrm_step": (ctypes.c_int, [P, P, P, I32, I32, P, P, ctypes.c_double, P, P, P]),
+    "vrm_step_begin": (ctypes.c_int, [P, P, P, I32, I32, P, P, ctypes.c_double, P]),
+    "vrm_step_end": (ctypes.c_int, [P, P, P]),
     "vrm_set_timing": (ctypes.c_int, [P, I32]),
     "vrm_stage_times": (ctypes.c_int, [P, P]),
     "vrm_launch_count": (ctypes.c_int64, []),
@@ -459,6 +461,22 @@ class VRM:
                                _ptr(gamma_out, torch.float64, "gamma_out", cap), float(dt), ctypes.byref(n_out),
                                ctypes.byref(s) if stats else None, _stream())
         self._check(st, "vrm_step")
+        return n_out.value, s.as_dict()
+
+    def step_begin(self, x, y, n, gamma_in, gamma_out, dt):
+        """vrm_step_begin: enqueues the step and returns (step_end waits)."""
+        cap = x.numel()
+        st = self.lib.vrm_step_begin(self.ctx, _ptr(x, torch.float64, "x", n), _ptr(y, torch.float64, "y", cap),
+                                     int(n), int(cap), _ptr(gamma_in, torch.float64, "gamma_in", n),
+                                     _ptr(gamma_out, torch.float64, "gamma_out", cap), float(dt), _stream())
+        self._check(st, "vrm_step_begin")
+
+    def step_end(self, stats=True):
+        """vrm_step_end: waits for the pending step; returns (n_out, stats)."""
+        n_out = ctypes.c_int32(0)
+        s = Stats()
+        st = self.lib.vrm_step_end(self.ctx, ctypes.byref(n_out), ctypes.byref(s) if stats else None)
+        self._check(st, "vrm_step_end")
         return n_out.value, s.as_dict()
 
 

@@ -113,6 +113,16 @@ struct vrm_ctx {
   uint8_t *rm_close = nullptr, *rm_removed = nullptr, *rm_keep = nullptr;
   int *rm_clist = nullptr, *rm_klist = nullptr, *rm_cols4 = nullptr;
   double *rm_w4 = nullptr, *rm_gnew = nullptr;
+  // a step enqueued by vrm_step_begin and not yet waited for by vrm_step_end
+  struct Pending {
+    int active = 0, launched = 0;
+    double *x = nullptr, *y = nullptr;
+    const double* gi = nullptr;
+    double* go = nullptr;
+    int n = 0, cap = 0;
+    cudaStream_t stream = nullptr;
+  } pending;
+  cudaEvent_t step_done = nullptr;
 };
 
 // What a batch graph was captured for: per cloud the buffers, capacity and
@@ -845,6 +855,10 @@ vrm_status vrm_create(const vrm_params* p, vrm_ctx** out) {
 
 void vrm_destroy(vrm_ctx* ctx) {
   if (!ctx) return;
+  if (ctx->step_done) {
+    cudaEventSynchronize(ctx->step_done);
+    cudaEventDestroy(ctx->step_done);
+  }
   drop_graph(ctx);
   free_scratch(ctx->s);
   free_learned(ctx->L);
@@ -1245,63 +1259,106 @@ vrm_status vrm_apply(vrm_ctx* ctx, int32_t n, int32_t n_gamma, const double* gam
   return VRM_OK;
 }
 
-vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capacity, const double* gamma_in,
-                    double* gamma_out, double dt, int32_t* n_out, vrm_stats* stats, cudaStream_t stream) {
-  if (!ctx || !n_out || n < 0 || capacity < n || !std::isfinite(dt)) return VRM_ERR_ARG;
+// Enqueues one attempt of the step (the captured graph, or the kernels one
+// by one when graphs are off) on the stream.
+static vrm_status step_launch(vrm_ctx* ctx, bool* launched) {
+  Scratch& s = ctx->s;
+  const vrm_ctx::Pending& P = ctx->pending;
+  if (ctx->timing)
+    for (int k = 0; k < VRM_STAGE_COUNT; ++k) ctx->stage_done[k] = 0;
+  *launched = false;
+  if (ctx->use_graph) {
+    const StepGraph& G = ctx->graph;
+    const bool hit = G.exec && G.x == P.x && G.y == P.y && G.gi == P.gi && G.go == P.go && G.cap == P.cap &&
+                     G.timing == ctx->timing;
+    if (!hit && !capture_step(ctx, P.x, P.y, P.cap, P.gi, P.go)) ctx->use_graph = 0;
+    if (ctx->use_graph) {
+      // the captured event nodes record every stage boundary
+      if (ctx->timing)
+        for (int k = 0; k < VRM_STAGE_COUNT; ++k) ctx->stage_done[k] = 1;
+      VRM_CUDA(cudaGraphLaunch(ctx->graph.exec, P.stream));
+      *launched = true;
+    }
+  }
+  if (!*launched) {
+    vrm_status r = run_step_eager(ctx, P.x, P.y, P.cap, P.gi, P.go, s.diffused, true, P.stream);
+    if (r != VRM_OK) return r;
+  }
+  VRM_CUDA(cudaEventRecord(ctx->step_done, P.stream));
+  return VRM_OK;
+}
+
+vrm_status vrm_step_begin(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capacity, const double* gamma_in,
+                          double* gamma_out, double dt, cudaStream_t stream) {
+  if (!ctx || n < 0 || capacity < n || !std::isfinite(dt)) return VRM_ERR_ARG;
+  if (ctx->pending.active) return VRM_ERR_ARG;
   if (bad_ptr(x, n) || bad_ptr(y, n) || bad_ptr(gamma_in, n) || bad_ptr(gamma_out, capacity)) return VRM_ERR_ARG;
   if (n > 0 && gamma_out < gamma_in + n && gamma_in < gamma_out + capacity) return VRM_ERR_ARG;
-  vrm_stats local;
-  vrm_stats* st = stats ? stats : &local;
-  memset(st, 0, sizeof(*st));
+  vrm_ctx::Pending& P = ctx->pending;
+  P = vrm_ctx::Pending{};
+  P.x = x;
+  P.y = y;
+  P.gi = gamma_in;
+  P.go = gamma_out;
+  P.n = n;
+  P.cap = capacity;
+  P.stream = stream;
   if (n == 0) {
-    *n_out = 0;
+    P.active = 1;
     return VRM_OK;
   }
   Scratch& s = ctx->s;
   VRM_CUDA(ensure_scratch(ctx, capacity, stream));
   VRM_CUDA(ensure_learned(ctx, capacity, stream));
-  // the pinned parameter block is read by the step's head copy: wait for any
-  // earlier step on this stream before rewriting it
-  VRM_CUDA(cudaStreamSynchronize(stream));
-  StepState P;
-  memset(&P, 0, sizeof(P));
-  P.n = n;
-  P.capacity = capacity;
-  P.dt = dt;
-  P.max_rounds = ctx->p.max_rounds;
-  *s.h_params = P;
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    if (ctx->timing)
-      for (int k = 0; k < VRM_STAGE_COUNT; ++k) ctx->stage_done[k] = 0;
-    bool launched = false;
-    if (ctx->use_graph) {
-      const StepGraph& G = ctx->graph;
-      const bool hit = G.exec && G.x == x && G.y == y && G.gi == gamma_in && G.go == gamma_out &&
-                       G.cap == capacity && G.timing == ctx->timing;
-      if (!hit && !capture_step(ctx, x, y, capacity, gamma_in, gamma_out)) ctx->use_graph = 0;
-      if (ctx->use_graph) {
-        // the captured event nodes record every stage boundary
-        if (ctx->timing)
-          for (int k = 0; k < VRM_STAGE_COUNT; ++k) ctx->stage_done[k] = 1;
-        VRM_CUDA(cudaGraphLaunch(ctx->graph.exec, stream));
-        launched = true;
-      }
-    }
-    if (!launched) {
-      vrm_status r = run_step_eager(ctx, x, y, capacity, gamma_in, gamma_out, s.diffused, true, stream);
-      if (r != VRM_OK) return r;
-    }
-    VRM_CUDA(cudaStreamSynchronize(stream));
-    if (launched) add_launches(ctx->graph.kernels_outer + ctx->graph.kernels_body * s.h_state->round);
+  if (!ctx->step_done) VRM_CUDA(cudaEventCreateWithFlags(&ctx->step_done, cudaEventDisableTiming));
+  // the pinned parameter block is read by the step's head copy; the last
+  // step of this context has ended (vrm_step_end waited for it), so it is
+  // free to rewrite
+  StepState S;
+  memset(&S, 0, sizeof(S));
+  S.n = n;
+  S.capacity = capacity;
+  S.dt = dt;
+  S.max_rounds = ctx->p.max_rounds;
+  *s.h_params = S;
+  bool launched = false;
+  vrm_status r = step_launch(ctx, &launched);
+  if (r != VRM_OK) return r;
+  P.launched = launched;
+  P.active = 1;
+  return VRM_OK;
+}
+
+vrm_status vrm_step_end(vrm_ctx* ctx, int32_t* n_out, vrm_stats* stats) {
+  if (!ctx || !n_out || !ctx->pending.active) return VRM_ERR_ARG;
+  vrm_ctx::Pending& P = ctx->pending;
+  P.active = 0;
+  vrm_stats local;
+  vrm_stats* st = stats ? stats : &local;
+  memset(st, 0, sizeof(*st));
+  if (P.n == 0) {
+    *n_out = 0;
+    return VRM_OK;
+  }
+  Scratch& s = ctx->s;
+  const int n = P.n;
+  VRM_CUDA(cudaEventSynchronize(ctx->step_done));
+  for (int attempt = 0;; ++attempt) {
+    if (P.launched) add_launches(ctx->graph.kernels_outer + ctx->graph.kernels_body * s.h_state->round);
     // rows cut by a row_cap below k_cap: the step is repeated with whole rows
     // (it reads only [0, n) of x, y and gamma_in, so the repeat is exact)
     const bool cut = !s.h_grid->nonfinite && !s.h_ds->nonfinite && !s.h_state->overflow &&
                      s.h_ds->max_count > ctx->c.row_cap && ctx->c.row_cap < ctx->p.k_cap;
-    if (!cut) break;
+    if (!cut || attempt > 0) break;
     ctx->c.row_cap = ctx->p.k_cap;
     drop_graph(ctx);
+    bool launched = false;
+    vrm_status r = step_launch(ctx, &launched);
+    if (r != VRM_OK) return r;
+    P.launched = launched;
+    VRM_CUDA(cudaEventSynchronize(ctx->step_done));
   }
-  if (ctx->mlp && vrm_mlp_error(ctx->mlp, stream) != VRM_OK) return VRM_ERR_CUDA;
+  if (ctx->mlp && vrm_mlp_error(ctx->mlp, P.stream) != VRM_OK) return VRM_ERR_CUDA;
   if (s.h_grid->nonfinite || s.h_ds->nonfinite) return VRM_ERR_ARG;
   fill_front_stats(ctx, n, st);
   st->small_ok = s.h_ds->small_ok;
@@ -1325,6 +1382,18 @@ vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capac
   *n_out = s.h_state->n_cur;
   if (s.h_ds->max_count > ctx->p.k_cap) return VRM_ERR_CAPACITY;
   return VRM_OK;
+}
+
+vrm_status vrm_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t capacity, const double* gamma_in,
+                    double* gamma_out, double dt, int32_t* n_out, vrm_stats* stats, cudaStream_t stream) {
+  if (!ctx || !n_out) return VRM_ERR_ARG;
+  if (ctx->pending.active) return VRM_ERR_ARG;
+  // the head copy of an earlier step on this stream may still read the
+  // pinned parameter block: wait for the stream before rewriting it
+  if (n > 0) VRM_CUDA(cudaStreamSynchronize(stream));
+  vrm_status r = vrm_step_begin(ctx, x, y, n, capacity, gamma_in, gamma_out, dt, stream);
+  if (r != VRM_OK) return r;
+  return vrm_step_end(ctx, n_out, stats);
 }
 
 vrm_status vrm_batch_create(const vrm_params* p, int32_t max_clouds, vrm_batch** out) {

@@ -525,3 +525,41 @@ def test_snapped_vertex_residual_bar(lib, orc, eps, accepted):
     w_g = ctx.solve_weights(cu(x), cu(y), n, cu(D), nbt)
     weights_equal(w_g, w_o, n)
     check_stencils_valid(x, y, w_g, n, h)
+
+
+def test_step_begin_end_pipeline(lib, orc):
+    # vrm_step_begin / vrm_step_end on two contexts: step k + 1 is enqueued
+    # before step k is waited for; every step equals vrm_step's and the
+    # oracle's, and a second begin on a context with a pending step is refused
+    x, y, g = vrm_inputs.random_cloud(20000, h=0.01, jitter=0.3, seed=1)
+    h, nu = 0.01, 1e-3
+    dt = (0.5 * h) ** 2 / (4 * nu) / 8
+    n = len(x)
+    x2, y2, g2, st_o = orc.step(x, y, g, h, nu, dt)
+    cap = 2 * n
+    sets = []
+    for _ in range(2):
+        xb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        yb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+        xb[:n] = cu(x)
+        yb[:n] = cu(y)
+        sets.append((lib.VRM(h=h, nu=nu), xb, yb, cu(g), torch.zeros(cap, dtype=torch.float64, device="cuda")))
+    c0, xb, yb, gi, go = sets[0]
+    c0.step_begin(xb, yb, n, gi, go, dt)
+    with pytest.raises(lib.VRMError) as ei:
+        c0.step_begin(xb, yb, n, gi, go, dt)
+    assert ei.value.status == lib.VRM_ERR_ARG
+    for k in range(4):
+        if k + 1 < 4:
+            c, xb1, yb1, gi1, go1 = sets[(k + 1) % 2]
+            c.step_begin(xb1, yb1, n, gi1, go1, dt * (1 + (k + 1) % 2))
+        c, xb, yb, gi, go = sets[k % 2]
+        n2, st = c.step_end()
+        assert n2 == len(x2) and st["small_ok"] == st_o["small_ok"]
+        assert np.array_equal(xb.cpu().numpy()[:n2], x2)
+        if k % 2 == 0:
+            assert np.array_equal(go.cpu().numpy()[:n2], g2)
+    # the same context goes on with plain vrm_step afterwards
+    go2 = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    n3, _ = sets[0][0].step(sets[0][1], sets[0][2], n, sets[0][3], go2, dt)
+    assert n3 == len(x2) and np.array_equal(go2.cpu().numpy()[:n3], g2)
