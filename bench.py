@@ -401,8 +401,9 @@ def run_ours(args):
 
     mean_stage = {k: (sum(v) / len(v) if v else 0.0) for k, v in stage_ms.items()}
     dom = max(mean_stage, key=mean_stage.get)
-    roofline = (roofline_for(dom, mean_stage[dom], stats, n, desc["order"], ctx.get_schedule()["lp_fp64_pivots"],
-                             peaks) if mean_stage[dom] > 0 else None)
+    sch = ctx.get_schedule()
+    roofline = (roofline_for(dom, mean_stage[dom], stats, n, desc["order"], sch["lp_fp64_pivots"], peaks,
+                             sch["lp_block"]) if mean_stage[dom] > 0 else None)
     learned = None
     if args.workload == "mixture_1m" and not args.no_learned and world == 1:
         learned = learned_vs_lp(args, ctx, xb, yb, n, gi, go, h, nu, dt, total_ms / args.steps, parts / args.steps,
@@ -571,7 +572,7 @@ def traffic_for(kernel):
         return None
 
 
-def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1, peaks=None):
+def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1, peaks=None, lp_block=128):
     m = 9 if order == 2 else 5
     if stage in ("lp_small", "lp_full"):
         if stage == "lp_small" and order == 1 and not lp_fp64_pivots:
@@ -584,7 +585,7 @@ def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1, peaks=None):
                              col_pivots=stats["lp_full_column_pivots"])
         kern = "k_lp_" + stage[3:]
         if stage == "lp_small" and order == 1 and not lp_fp64_pivots:
-            kern = "k_lp_small32"
+            kern = "k_lp_small32_ws" if lp_block == 192 else "k_lp_small32"
         ach = flops / (ms * 1e-3) / 1e12
         if peaks and peaks.get("fp64_tflops"):
             peak = peaks["fp64_tflops"]
