@@ -74,6 +74,11 @@ struct vrm::Scratch {
   StepState* h_state = nullptr;   // state after the step
 };
 
+// The particle grid's cells as the insertion rounds read them.
+inline PartCells part_cells(const Scratch& s) {
+  return PartCells{s.cell_key, s.cell_rank, s.cell_start, s.sorted_loc};
+}
+
 struct StepGraph {
   cudaGraphExec_t exec = nullptr;
   const void *x = nullptr, *y = nullptr, *gi = nullptr, *go = nullptr;
@@ -712,7 +717,8 @@ bool record_step(vrm_ctx* ctx, cudaStream_t cs, cudaStream_t body_stream, double
            cudaSuccess;
       if (ok) {
         const long long b0 = launch_count();
-        ok = round_body(ctx->c, s.st, s.grid, s.rb, cap, s.mask, x, y, handle, true, body_stream) == cudaSuccess;
+        ok = round_body(ctx->c, s.st, s.grid, part_cells(s), s.rb, cap, s.mask, x, y, handle, true, body_stream) ==
+             cudaSuccess;
         bk = launch_count() - b0;
         cudaGraph_t got = nullptr;
         const bool ended = cudaStreamEndCapture(body_stream, &got) == cudaSuccess;
@@ -779,7 +785,7 @@ vrm_status run_step_eager(vrm_ctx* ctx, double* x, double* y, int cap, const dou
     VRM_CUDA(cudaMemcpyAsync(s.h_state, s.st, sizeof(StepState), cudaMemcpyDeviceToHost, st));
     VRM_CUDA(cudaStreamSynchronize(st));
     if (s.h_state->n_open == 0) break;
-    VRM_CUDA(round_body(ctx->c, s.st, s.grid, s.rb, cap, s.mask, x, y, 0, false, st));
+    VRM_CUDA(round_body(ctx->c, s.st, s.grid, part_cells(s), s.rb, cap, s.mask, x, y, 0, false, st));
   }
   if (back) {
     VRM_CUDA(enqueue_back(ctx, x, y, cap, gamma_in, gamma_out, st));

@@ -33,15 +33,17 @@ static int blocks_for(int m) {
 __global__ void __launch_bounds__(kBlock) k_conflict(Consts c, const Grid* __restrict__ gp,
                                                      const int* __restrict__ cell_start,
                                                      const double2* __restrict__ sxy, const float2* __restrict__ sloc,
-                                                     const int* __restrict__ sidx, const int* __restrict__ n_cand_dev,
-                                                     uint8_t* __restrict__ keep) {
+                                                     const int* __restrict__ sidx, const int* __restrict__ cell_key,
+                                                     const int* __restrict__ n_cand_dev, uint8_t* __restrict__ keep) {
   const int n_cand = *n_cand_dev;
   const Grid g = *gp;
   for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n_cand; p += (long)gridDim.x * blockDim.x) {
     const int ci = sidx[p];
     const double2 pc = sxy[p];
     const float2 lc = sloc[p];
-    const int gx = grid_cell_x(g, pc.x), gy = grid_cell_y(g, pc.y);
+    // the proposal's cell as binned (integer ops, no FP64)
+    const int key = cell_key[ci];
+    const int gy = key / g.nx, gx = key - gy * g.nx;
     bool ok = true;
     for (int by = gy - 1; by <= gy + 1 && ok; ++by) {
       if (by < 0 || by >= g.ny) continue;
@@ -82,15 +84,20 @@ __global__ void __launch_bounds__(kBlock) k_mask_update(Consts c, const Grid* __
                                                         const float2* __restrict__ sloc,
                                                         const int* __restrict__ sidx, const uint8_t* __restrict__ keep,
                                                         const double* __restrict__ x, const double* __restrict__ y,
-                                                        const int* __restrict__ open, const int* __restrict__ n_open_dev,
+                                                        PartCells pcells, const int* __restrict__ open,
+                                                        const int* __restrict__ n_open_dev,
                                                         uint8_t* __restrict__ mask, uint8_t* __restrict__ keep_flag) {
   const int n_open = *n_open_dev;
   const Grid g = *gp;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x) {
     const int i = open[t];
-    const double xi = x[i], yi = y[i];
-    const int gx = grid_cell_x(g, xi), gy = grid_cell_y(g, yi);
-    const float ux = grid_local_x(g, xi, gx), uy = grid_local_y(g, yi, gy);
+    // the open particle's cell and cell-local position from the particle
+    // grid (the proposal grid has the same geometry): integer ops and one
+    // load instead of FP64 arithmetic
+    const int key = pcells.cell_key[i];
+    const float2 li = pcells.sorted_loc[pcells.cell_start[key] + pcells.cell_rank[i]];
+    const int gy = key / g.nx, gx = key - gy * g.nx;
+    const float ux = li.x, uy = li.y;
     unsigned mk = mask[i];
     for (int by = gy - 1; by <= gy + 1; ++by) {
       if (by < 0 || by >= g.ny) continue;
@@ -110,7 +117,7 @@ __global__ void __launch_bounds__(kBlock) k_mask_update(Consts c, const Grid* __
           if (d2f > g.lo_in && d2f < g.hi_in) s = segment_or_ambiguous(du, dv, g.seg_eps);
           if (s < 0) {
             const double2 o = sxy[q];
-            const double dx = __dsub_rn(o.x, xi), dy = __dsub_rn(o.y, yi);
+            const double dx = __dsub_rn(o.x, x[i]), dy = __dsub_rn(o.y, y[i]);
             const double d2 = dist2(dx, dy);
             if (d2 < c.lo2 || d2 > c.hi2) continue;
             s = segment_of(dx, dy);
@@ -256,8 +263,9 @@ cudaError_t rounds_init(StepState* st, const int* n_open_src, cudaGraphCondition
   return cudaGetLastError();
 }
 
-cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const RoundBufs& rb, int cap, uint8_t* mask,
-                       double* x, double* y, cudaGraphConditionalHandle handle, bool graph, cudaStream_t s) {
+cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const PartCells& pcells, const RoundBufs& rb,
+                       int cap, uint8_t* mask, double* x, double* y, cudaGraphConditionalHandle handle, bool graph,
+                       cudaStream_t s) {
   const int bo = blocks_for(cap);
   const long cand_cap = 8L * cap;
   const int bc = blocks_for((int)(cand_cap < 0x7FFFFFFF ? cand_cap : 0x7FFFFFFF));
@@ -272,13 +280,14 @@ cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const 
                    rb.cg.sorted_idx, rb.scan_tmp, s);
   if (e != cudaSuccess) return e;
   k_conflict<<<bc, kBlock, 0, s>>>(c, pgrid, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
-                                   rb.cg.sorted_idx, &st->n_cand, rb.keep);
+                                   rb.cg.sorted_idx, rb.cg.cell_key, &st->n_cand, rb.keep);
   note_launch();
   e = scan_exclusive_u8_dev(rb.keep, rb.apos, (int)cand_cap, &st->n_cand, rb.scan_tmp, s);
   if (e != cudaSuccess) return e;
   k_append_dev<<<bc, kBlock, 0, s>>>(rb.cx, rb.cy, rb.keep, rb.apos, st, x, y); note_launch();
   k_mask_update<<<bo, kBlock, 0, s>>>(c, pgrid, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
-                                      rb.cg.sorted_idx, rb.keep, x, y, rb.open, &st->n_open, mask, rb.keep_flag);
+                                      rb.cg.sorted_idx, rb.keep, x, y, pcells, rb.open, &st->n_open, mask,
+                                      rb.keep_flag);
   note_launch();
   e = scan_exclusive_u8_dev(rb.keep_flag, rb.keep_pos, cap, &st->n_open, rb.scan_tmp, s);
   if (e != cudaSuccess) return e;

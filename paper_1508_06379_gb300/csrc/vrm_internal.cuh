@@ -288,6 +288,15 @@ struct RoundBufs {
   CandGrid cg;         // proposal cell grid (geometry copied from the particle grid)
   int* scan_tmp;       // scan workspace for 8 cap entries
 };
+// The particle grid's per-particle cell keys and ranks and its sorted
+// cell-local coordinates (an open particle's cell and local position come
+// from there instead of FP64 arithmetic on its coordinates).
+struct PartCells {
+  const int* cell_key;
+  const int* cell_rank;
+  const int* cell_start;
+  const float2* sorted_loc;
+};
 // Round state initialisation after the open list exists; sets the loop
 // condition (handle may be 0 when not capturing).
 cudaError_t rounds_init(StepState* st, const int* n_open_src, cudaGraphConditionalHandle handle, bool graph,
@@ -295,8 +304,9 @@ cudaError_t rounds_init(StepState* st, const int* n_open_src, cudaGraphCondition
 // One insertion round on device-resident counts; a no-op once the state has
 // no open particle.  The last kernel updates the state and, in a graph, sets
 // the while-loop condition.
-cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const RoundBufs& rb, int cap, uint8_t* mask,
-                       double* x, double* y, cudaGraphConditionalHandle handle, bool graph, cudaStream_t s);
+cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const PartCells& pcells, const RoundBufs& rb,
+                       int cap, uint8_t* mask, double* x, double* y, cudaGraphConditionalHandle handle, bool graph,
+                       cudaStream_t s);
 cudaError_t rounds_finish(StepState* st, const int* open, const uint8_t* mask, int cap, cudaStream_t s);
 
 // vrm_lp.cu
