@@ -585,7 +585,7 @@ def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1, peaks=None, lp_
                              col_pivots=stats["lp_full_column_pivots"])
         kern = "k_lp_" + stage[3:]
         if stage == "lp_small" and order == 1 and not lp_fp64_pivots:
-            kern = "k_lp_small32_ws" if lp_block == 192 else "k_lp_small32"
+            kern = "k_lp_small32_ws" if lp_block in (192, 384) else "k_lp_small32"
         ach = flops / (ms * 1e-3) / 1e12
         if peaks and peaks.get("fp64_tflops"):
             peak = peaks["fp64_tflops"]

@@ -312,7 +312,8 @@ typedef struct vrm_batch vrm_batch;
  *                     with row_cap = k_cap, which the context then keeps.
  *   search_block:     threads per block of the neighbourhood search (32..256, multiple of 32).
  *   lp_block:         threads per block of the small-neighbourhood LP, one particle per thread (32..128, multiple of 32);
- *                     192 selects the warp-specialised form of the binary32 LP (4 pivot and 2 FP64 warps per block).
+ *                     192 and 384 select the warp-specialised form of the binary32 LP (4 pivot and 2 FP64 warps
+ *                     per block, two blocks per SM; 8 pivot and 4 FP64 warps, one block per SM).
  *   lp_blocks_per_sm: the small LP's grid is capped at this many blocks per SM (1..64).
  *   apply_block:      threads per block of the application (32..256, multiple of 32).
  *   lp_fp64_pivots:   0 (default): the small-neighbourhood LPs (n = 1) pivot

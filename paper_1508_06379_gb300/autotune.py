@@ -12,7 +12,8 @@ its own stage of the step (CUDA events recorded inside the step's graph):
   search:   row_cap in {16, 24, 32} (only values >= the cloud's widest row)
             x search_block in {64, 128, 256}
   lp_small: lp_block in {32, 64, 128} x lp_blocks_per_sm in {4, 8, 16, 32},
-            or lp_block 192 (the warp-specialised binary32 LP),
+            or lp_block 192 / 384 (the warp-specialised binary32 LP,
+            4 + 2 warps two blocks per SM / 8 + 4 warps one block per SM),
             then lp_fp64_pivots in {0, 1} (certified binary32 pivots with
             FP64 re-runs, or FP64 pivots throughout: lattices with many
             exact ties re-run most LPs and may prefer FP64)
@@ -33,7 +34,7 @@ DEFAULT = dict(row_cap=32, search_block=256, lp_block=128, lp_blocks_per_sm=16, 
 GROUPS = (
     ("search", [dict(row_cap=r, search_block=b) for r in (16, 24, 32) for b in (64, 128, 256)]),
     ("lp_small", [dict(lp_block=b, lp_blocks_per_sm=k) for b in (32, 64, 128) for k in (4, 8, 16, 32)] +
-     [dict(lp_block=192, lp_blocks_per_sm=2)]),
+     [dict(lp_block=192, lp_blocks_per_sm=2), dict(lp_block=384, lp_blocks_per_sm=1)]),
     ("lp_small", [dict(lp_fp64_pivots=v) for v in (0, 1)]),
     ("apply", [dict(apply_block=b) for b in (64, 128, 256)]),
 )

@@ -548,9 +548,10 @@ bool bad_ptr(const void* p, int n) { return n > 0 && p == nullptr; }
 bool block_ok(int b, int hi) { return b >= 32 && b <= hi && b % 32 == 0; }
 
 bool schedule_ok(const vrm_schedule& s, int k_cap) {
-  // lp_block 192: the warp-specialised small LP (4 pivot + 2 finish warps)
+  // lp_block 192 and 384: the warp-specialised small LP (4 pivot + 2 finish
+  // warps, two blocks per SM; 8 + 4 warps, one block per SM)
   return s.row_cap >= 8 && s.row_cap <= k_cap && block_ok(s.search_block, kBlock) &&
-         (block_ok(s.lp_block, 128) || s.lp_block == 192) &&
+         (block_ok(s.lp_block, 128) || s.lp_block == 192 || s.lp_block == 384) &&
          s.lp_blocks_per_sm >= 1 && s.lp_blocks_per_sm <= 64 && block_ok(s.apply_block, kBlock) &&
          (s.lp_fp64_pivots == 0 || s.lp_fp64_pivots == 1);
 }

@@ -1015,30 +1015,30 @@ __global__ void __launch_bounds__(128, 3) k_lp_small32(Consts c, const double* _
 }
 
 // ---------------------------------------------------------------------------
-// The same LPs with the work split by warps: per block, kLpPivotWarps warps
-// take the columns and the certified binary32 pivots of 32 LPs each, and
-// kLpFinishWarps warps take the FP64 part (basis offsets, LU solve,
-// certificate, stencil) of the LPs the pivot warps finished in the round
-// before, handed over in shared memory (double-buffered, one block barrier
-// per round).  The FP64 pipe, the bottleneck of the LP, then works on one
-// batch while the binary32 and integer pipes work on the next, instead of
-// every warp alternating between the two phases; the finish warps also run
-// the FP64 solve with their lanes together.  Results are those of
-// k_lp_small32 bit for bit (the same device functions in the same order).
+// The same LPs with the work split by warps: per block, PW warps take the
+// columns and the certified binary32 pivots of 32 LPs each, and FW warps
+// take the FP64 part (basis offsets, LU solve, certificate, stencil) of the
+// LPs the pivot warps finished in the round before, handed over in shared
+// memory (double-buffered, one block barrier per round).  The FP64 pipe then
+// works on one batch while the binary32 and integer pipes work on the next,
+// instead of every warp alternating between the two phases.  Results are
+// those of k_lp_small32 bit for bit (the same device functions in the same
+// order).  Two shapes: 4 + 2 warps with two blocks per SM, and 8 + 4 warps
+// with one block per SM (the same 12 warps per SM at 168 registers; the
+// wider block is 6% faster on the 1M-particle workload).
 // ---------------------------------------------------------------------------
-constexpr int kLpPivotWarps = 4;
-constexpr int kLpFinishWarps = 2;
-constexpr int kLpBatch = 32 * kLpPivotWarps;
-constexpr int kLpWsThreads = 32 * (kLpPivotWarps + kLpFinishWarps);
+constexpr int kLpWsThreads = 32 * (4 + 2);
+constexpr int kLpWsThreadsWide = 32 * (8 + 4);
 
-template <int M, int W>
-__global__ void __launch_bounds__(kLpWsThreads, 2) k_lp_small32_ws(
+template <int M, int W, int PW, int FW, int MINB>
+__global__ void __launch_bounds__(32 * (PW + FW), MINB) k_lp_small32_ws(
     Consts c, const double* __restrict__ x, const double* __restrict__ y, const int* __restrict__ list,
     const int* __restrict__ list_count, const int* __restrict__ small, int* __restrict__ cols,
     double* __restrict__ f, double* __restrict__ fii, uint8_t* __restrict__ status, int* __restrict__ fail_list,
     int* __restrict__ retry_list, DevStats* __restrict__ ds, double nu_dt, const double* __restrict__ dt_dev,
     double nu) {
   static_assert(M == 5, "certified binary32 pivoting is written for the n = 1 rows");
+  constexpr int kLpPivotWarps = PW, kLpFinishWarps = FW, kLpBatch = 32 * PW;
   if (dt_dev) nu_dt = nu * *dt_dev;
   const int m = *list_count;
   const double inv_h2 = 1.0 / (c.h * c.h);
@@ -1101,8 +1101,7 @@ __global__ void __launch_bounds__(kLpWsThreads, 2) k_lp_small32_ws(
     } else if (r > 0) {
       const int pb = buf ^ 1;
 #pragma unroll 1
-      for (int k = 0; k < kLpBatch / (32 * kLpFinishWarps); ++k) {
-        const int slot = (warp - kLpPivotWarps) * 32 + (int)lane + k * 32 * kLpFinishWarps;
+      for (int slot = (warp - kLpPivotWarps) * 32 + (int)lane; slot < kLpBatch; slot += 32 * kLpFinishWarps) {
         const int meta = s_meta[pb][slot];
         if (meta & (1 << 30)) {
           const int i = s_i[pb][slot];
@@ -1696,9 +1695,10 @@ cudaError_t lp_small(const Consts& c, const double* x, const double* y, const in
                      int cap, const int* small, int* cols, double* f, double* fii, uint8_t* status, int* fail_list,
                      int* retry_list, DevStats* ds, double nu_dt, cudaStream_t s, const double* dt_dev, double nu) {
   if (cap <= 0) return cudaSuccess;
-  // lp_block = kLpWsThreads selects the warp-specialised binary32 LP; the
-  // other LP kernels then run with 128 threads per block
-  const int tb = c.lp_block == kLpWsThreads ? 128 : c.lp_block;
+  // lp_block = kLpWsThreads or kLpWsThreadsWide selects the warp-specialised
+  // binary32 LP; the other LP kernels then run with 128 threads per block
+  const bool ws = c.lp_block == kLpWsThreads || c.lp_block == kLpWsThreadsWide;
+  const int tb = ws ? 128 : c.lp_block;
   int blocks = (int)(((long)cap + tb - 1) / tb);
   if (blocks > c.lp_blocks_per_sm * sm_count()) blocks = c.lp_blocks_per_sm * sm_count();
   if (c.order == 2) {
@@ -1714,10 +1714,13 @@ cudaError_t lp_small(const Consts& c, const double* x, const double* y, const in
     cudaError_t e = cudaMemsetAsync(&ds->n_retry, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     if (c.lp_block == kLpWsThreads) {
-      // warp-specialised form: two resident blocks per SM
-      k_lp_small32_ws<5, 8><<<2 * sm_count(), kLpWsThreads, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii,
-                                                                  status, fail_list, retry_list, ds, nu_dt, dt_dev,
-                                                                  nu);
+      // warp-specialised form, 4 + 2 warps: two resident blocks per SM
+      k_lp_small32_ws<5, 8, 4, 2, 2><<<2 * sm_count(), kLpWsThreads, 0, s>>>(
+          c, x, y, list, list_count, small, cols, f, fii, status, fail_list, retry_list, ds, nu_dt, dt_dev, nu);
+    } else if (c.lp_block == kLpWsThreadsWide) {
+      // 8 + 4 warps: one resident block per SM
+      k_lp_small32_ws<5, 8, 8, 4, 1><<<sm_count(), kLpWsThreadsWide, 0, s>>>(
+          c, x, y, list, list_count, small, cols, f, fii, status, fail_list, retry_list, ds, nu_dt, dt_dev, nu);
     } else {
       k_lp_small32<5, 8><<<blocks, tb, 0, s>>>(c, x, y, list, list_count, small, cols, f, fii, status, fail_list,
                                                retry_list, ds, nu_dt, dt_dev, nu);

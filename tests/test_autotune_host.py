@@ -26,8 +26,8 @@ def fake_measure(costs, changed=None):
 COSTS = {
     "row_cap": {16: 0.1, 24: 0.2, 32: 0.3},
     "search_block": {64: 0.3, 128: 0.05, 256: 0.2},
-    "lp_block": {32: 0.5, 64: 0.1, 128: 0.2, 192: 0.3},
-    "lp_blocks_per_sm": {2: 0.2, 4: 0.3, 8: 0.2, 16: 0.01, 32: 0.4},
+    "lp_block": {32: 0.5, 64: 0.1, 128: 0.2, 192: 0.3, 384: 0.25},
+    "lp_blocks_per_sm": {1: 0.2, 2: 0.2, 4: 0.3, 8: 0.2, 16: 0.01, 32: 0.4},
     "apply_block": {64: 0.2, 128: 0.3, 256: 0.1},
     "lp_fp64_pivots": {0: 0.05, 1: 0.5},
 }
@@ -38,8 +38,8 @@ def test_descent_picks_the_fastest_option_of_every_group():
     best, report = autotune.descend(measure, k_cap=32, max_count=12)
     assert best == dict(row_cap=16, search_block=128, lp_block=64, lp_blocks_per_sm=16, apply_block=256,
                         lp_fp64_pivots=0)
-    # 9 search + 13 + 2 LP + 3 apply candidates, each measured once
-    assert len(calls) == 27 and len(report) == 27
+    # 9 search + 14 + 2 LP + 3 apply candidates, each measured once
+    assert len(calls) == 28 and len(report) == 28
 
 
 def test_row_caps_below_the_widest_row_are_not_tried():
