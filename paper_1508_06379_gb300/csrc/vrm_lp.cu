@@ -1030,6 +1030,14 @@ __global__ void __launch_bounds__(128, 3) k_lp_small32(Consts c, const double* _
 constexpr int kLpWsThreads = 32 * (4 + 2);
 constexpr int kLpWsThreadsWide = 32 * (8 + 4);
 
+// Block barrier of the warp-specialised LP (named barrier 1 over every
+// thread of the block): the two roles run their own loops with the same
+// number of rounds and meet here once per round.
+template <int NT>
+__device__ __forceinline__ void ws_barrier() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
+
 template <int M, int W, int PW, int FW, int MINB>
 __global__ void __launch_bounds__(32 * (PW + FW), MINB) k_lp_small32_ws(
     Consts c, const double* __restrict__ x, const double* __restrict__ y, const int* __restrict__ list,
@@ -1038,7 +1046,7 @@ __global__ void __launch_bounds__(32 * (PW + FW), MINB) k_lp_small32_ws(
     int* __restrict__ retry_list, DevStats* __restrict__ ds, double nu_dt, const double* __restrict__ dt_dev,
     double nu) {
   static_assert(M == 5, "certified binary32 pivoting is written for the n = 1 rows");
-  constexpr int kLpPivotWarps = PW, kLpFinishWarps = FW, kLpBatch = 32 * PW;
+  constexpr int kLpPivotWarps = PW, kLpFinishWarps = FW, kLpBatch = 32 * PW, kThreads = 32 * (PW + FW);
   if (dt_dev) nu_dt = nu * *dt_dev;
   const int m = *list_count;
   const double inv_h2 = 1.0 / (c.h * c.h);
@@ -1054,12 +1062,13 @@ __global__ void __launch_bounds__(32 * (PW + FW), MINB) k_lp_small32_ws(
   __shared__ int s_meta[2][kLpBatch];
   __shared__ int s_cj[2][8][kLpBatch];
   const long nchunks = ((long)m + kLpBatch - 1) / kLpBatch;
-  for (long r = 0;; ++r) {
-    const long chunk = (long)blockIdx.x + r * gridDim.x;  // pivoted in this round
-    const long prev = chunk - gridDim.x;                   // finished in this round
-    if (prev >= nchunks) break;
-    const int buf = (int)(r & 1);
-    if (pivot_warp) {
+  // round r pivots chunk blockIdx.x + r gridDim.x and finishes the chunk of
+  // round r - 1; the last round only finishes
+  if (pivot_warp) {
+    for (long r = 0;; ++r) {
+      const long chunk = (long)blockIdx.x + r * gridDim.x;
+      if (chunk - gridDim.x >= nchunks) break;
+      const int buf = (int)(r & 1);
       if (chunk < nchunks) {
         const int slot = warp * 32 + (int)lane;
         const long t = chunk * kLpBatch + slot;
@@ -1098,41 +1107,48 @@ __global__ void __launch_bounds__(32 * (PW + FW), MINB) k_lp_small32_ws(
           n_retry += (lane == 0) ? __popc(rb) : 0;
         }
       }
-    } else if (r > 0) {
-      const int pb = buf ^ 1;
+      ws_barrier<kThreads>();
+    }
+  } else {
+    for (long r = 0;; ++r) {
+      const long chunk = (long)blockIdx.x + r * gridDim.x;
+      if (chunk - gridDim.x >= nchunks) break;
+      const int pb = (int)(r & 1) ^ 1;
+      if (r > 0) {
 #pragma unroll 1
-      for (int slot = (warp - kLpPivotWarps) * 32 + (int)lane; slot < kLpBatch; slot += 32 * kLpFinishWarps) {
-        const int meta = s_meta[pb][slot];
-        if (meta & (1 << 30)) {
-          const int i = s_i[pb][slot];
-          int basis[M];
+        for (int slot = (warp - kLpPivotWarps) * 32 + (int)lane; slot < kLpBatch; slot += 32 * kLpFinishWarps) {
+          const int meta = s_meta[pb][slot];
+          if (meta & (1 << 30)) {
+            const int i = s_i[pb][slot];
+            int basis[M];
 #pragma unroll
-          for (int q = 0; q < M; ++q) basis[q] = (meta >> (4 * q)) & 15;
-          const int it = (meta >> 20) & 127, code = (meta >> 27) & 3;
-          int cj[8];
+            for (int q = 0; q < M; ++q) basis[q] = (meta >> (4 * q)) & 15;
+            const int it = (meta >> 20) & 127, code = (meta >> 27) & 3;
+            int cj[8];
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) cj[kk] = s_cj[pb][kk][slot];
-          // FP64 offsets of the basic columns, computed as lp_columns computes them
-          const double xi0 = x[i], yi0 = y[i];
-          double bxi[M], beta[M];
+            for (int kk = 0; kk < 8; ++kk) cj[kk] = s_cj[pb][kk][slot];
+            // FP64 offsets of the basic columns, computed as lp_columns computes them
+            const double xi0 = x[i], yi0 = y[i];
+            double bxi[M], beta[M];
 #pragma unroll
-          for (int q = 0; q < M; ++q) {
-            int j = INT_MAX;
+            for (int q = 0; q < M; ++q) {
+              int j = INT_MAX;
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) j = (basis[q] == M + kk) ? cj[kk] : j;
-            bxi[q] = 0.0;
-            beta[q] = 0.0;
-            if (j != INT_MAX) {
-              bxi[q] = __dmul_rn(__dsub_rn(x[j], xi0), c.inv_h);
-              beta[q] = __dmul_rn(__dsub_rn(y[j], yi0), c.inv_h);
+              for (int kk = 0; kk < 8; ++kk) j = (basis[q] == M + kk) ? cj[kk] : j;
+              bxi[q] = 0.0;
+              beta[q] = 0.0;
+              if (j != INT_MAX) {
+                bxi[q] = __dmul_rn(__dsub_rn(x[j], xi0), c.inv_h);
+                beta[q] = __dmul_rn(__dsub_rn(y[j], yi0), c.inv_h);
+              }
             }
+            lp_finish<M, W>(c, i, code, basis, it, cj, bxi, beta, cols, f, fii, status, fail_list, ds, nu_dt,
+                            inv_h2, tl);
           }
-          lp_finish<M, W>(c, i, code, basis, it, cj, bxi, beta, cols, f, fii, status, fail_list, ds, nu_dt, inv_h2,
-                          tl);
         }
       }
+      ws_barrier<kThreads>();
     }
-    __syncthreads();
   }
   flush_stats(ds, tl.ok, tl.none, tl.maxpiv, tl.ratio, false, tl.solved, tl.pivots);
   if (lane == 0 && n_retry) atomicAdd(&ds->lp_small_retries, (unsigned long long)n_retry);
