@@ -27,9 +27,42 @@ static int blocks_for(int m) {
   return b < 8 * sm_count() ? b : 8 * sm_count();
 }
 
-// keep[c] = 1 unless a proposal of smaller index lies closer than r h.
-// Pairs clearly apart (or clearly too close) are decided in FP32 on the
-// cell-local coordinates, the rest by the FP64 distance.
+// Proposal at sorted position p: 1 unless a proposal of smaller index lies
+// closer than r h.  Pairs clearly apart (or clearly too close) are decided in
+// FP32 on the cell-local coordinates, the rest by the FP64 distance.
+__device__ __forceinline__ bool conflict_keep(const Consts& c, const Grid& g, const int* __restrict__ cell_start,
+                                              const double2* __restrict__ sxy, const float2* __restrict__ sloc,
+                                              const int* __restrict__ sidx, int ci, int key, long p) {
+  const double2 pc = sxy[p];
+  const float2 lc = sloc[p];
+  const int gy = key / g.nx, gx = key - gy * g.nx;
+  for (int by = gy - 1; by <= gy + 1; ++by) {
+    if (by < 0 || by >= g.ny) continue;
+    const float dvb = (float)(by - gy) - lc.y;
+    for (int bx = gx - 1; bx <= gx + 1; ++bx) {
+      if (bx < 0 || bx >= g.nx) continue;
+      const float dub = (float)(bx - gx) - lc.x;
+      const int cell = by * g.nx + bx;
+      const int q0 = cell_start[cell], q1 = cell_start[cell + 1];
+      for (int q = q0; q < q1; ++q) {
+        const float2 lo = sloc[q];
+        const float du = dub + lo.x, dv = dvb + lo.y;
+        const float d2f = __fmaf_rn(du, du, dv * dv);
+        if (d2f > g.lo_in) continue;
+        if (sidx[q] >= ci) continue;
+        bool close = d2f < g.lo_out;
+        if (!close) {
+          const double2 o = sxy[q];
+          close = dist2(__dsub_rn(pc.x, o.x), __dsub_rn(pc.y, o.y)) < c.lo2;
+        }
+        if (close) return false;
+      }
+    }
+  }
+  return true;
+}
+
+// keep[c] = conflict_keep of every proposal.
 __global__ void __launch_bounds__(kBlock) k_conflict(Consts c, const Grid* __restrict__ gp,
                                                      const int* __restrict__ cell_start,
                                                      const double2* __restrict__ sxy, const float2* __restrict__ sloc,
@@ -39,45 +72,59 @@ __global__ void __launch_bounds__(kBlock) k_conflict(Consts c, const Grid* __res
   const Grid g = *gp;
   for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n_cand; p += (long)gridDim.x * blockDim.x) {
     const int ci = sidx[p];
-    const double2 pc = sxy[p];
-    const float2 lc = sloc[p];
     // the proposal's cell as binned (integer ops, no FP64)
-    const int key = cell_key[ci];
-    const int gy = key / g.nx, gx = key - gy * g.nx;
-    bool ok = true;
-    for (int by = gy - 1; by <= gy + 1 && ok; ++by) {
-      if (by < 0 || by >= g.ny) continue;
-      const float dvb = (float)(by - gy) - lc.y;
-      for (int bx = gx - 1; bx <= gx + 1 && ok; ++bx) {
-        if (bx < 0 || bx >= g.nx) continue;
-        const float dub = (float)(bx - gx) - lc.x;
-        const int cell = by * g.nx + bx;
-        const int q0 = cell_start[cell], q1 = cell_start[cell + 1];
-        for (int q = q0; q < q1; ++q) {
-          const float2 lo = sloc[q];
-          const float du = dub + lo.x, dv = dvb + lo.y;
-          const float d2f = __fmaf_rn(du, du, dv * dv);
-          if (d2f > g.lo_in) continue;
-          if (sidx[q] >= ci) continue;
-          bool close = d2f < g.lo_out;
-          if (!close) {
-            const double2 o = sxy[q];
-            close = dist2(__dsub_rn(pc.x, o.x), __dsub_rn(pc.y, o.y)) < c.lo2;
-          }
-          if (close) {
-            ok = false;
-            break;
-          }
-        }
-      }
-    }
-    keep[ci] = ok;
+    keep[ci] = conflict_keep(c, g, cell_start, sxy, sloc, sidx, ci, cell_key[ci], p);
   }
 }
 
-// Segment bits of the accepted proposals in the annulus of every open
-// particle; keep_flag[t] = 1 if the mask is still not full.  FP32 filter on
-// cell-local coordinates as in the neighbour search.
+// Segment bits of the accepted proposals in the annulus of open particle i,
+// ORed into mask[i]; returns true if the mask is still not full.  FP32
+// filter on cell-local coordinates as in the neighbour search.  The open
+// particle's cell and cell-local position come from the particle grid (the
+// proposal grid has the same geometry): integer ops and one load instead of
+// FP64 arithmetic.
+__device__ __forceinline__ bool mask_update_one(const Consts& c, const Grid& g, const int* __restrict__ cell_start,
+                                                const double2* __restrict__ sxy, const float2* __restrict__ sloc,
+                                                const int* __restrict__ sidx, const uint8_t* __restrict__ keep,
+                                                const double* __restrict__ x, const double* __restrict__ y,
+                                                const PartCells& pcells, int i, uint8_t* __restrict__ mask) {
+  const int key = pcells.cell_key[i];
+  const float2 li = pcells.sorted_loc[pcells.cell_start[key] + pcells.cell_rank[i]];
+  const int gy = key / g.nx, gx = key - gy * g.nx;
+  const float ux = li.x, uy = li.y;
+  unsigned mk = mask[i];
+  for (int by = gy - 1; by <= gy + 1; ++by) {
+    if (by < 0 || by >= g.ny) continue;
+    const float dvb = (float)(by - gy) - uy;
+    for (int bx = gx - 1; bx <= gx + 1; ++bx) {
+      if (bx < 0 || bx >= g.nx) continue;
+      const float dub = (float)(bx - gx) - ux;
+      const int cell = by * g.nx + bx;
+      const int q0 = cell_start[cell], q1 = cell_start[cell + 1];
+      for (int q = q0; q < q1; ++q) {
+        const float2 lo = sloc[q];
+        const float du = dub + lo.x, dv = dvb + lo.y;
+        const float d2f = __fmaf_rn(du, du, dv * dv);
+        if (d2f < g.lo_out || d2f > g.hi_out) continue;
+        if (!keep[sidx[q]]) continue;
+        int s = -1;
+        if (d2f > g.lo_in && d2f < g.hi_in) s = segment_or_ambiguous(du, dv, g.seg_eps);
+        if (s < 0) {
+          const double2 o = sxy[q];
+          const double dx = __dsub_rn(o.x, x[i]), dy = __dsub_rn(o.y, y[i]);
+          const double d2 = dist2(dx, dy);
+          if (d2 < c.lo2 || d2 > c.hi2) continue;
+          s = segment_of(dx, dy);
+        }
+        mk |= 1u << s;
+      }
+    }
+  }
+  mask[i] = (uint8_t)mk;
+  return mk != 0xFFu;
+}
+
+// mask_update_one for every open particle; keep_flag[t] = still open.
 __global__ void __launch_bounds__(kBlock) k_mask_update(Consts c, const Grid* __restrict__ gp,
                                                         const int* __restrict__ cell_start,
                                                         const double2* __restrict__ sxy,
@@ -89,46 +136,8 @@ __global__ void __launch_bounds__(kBlock) k_mask_update(Consts c, const Grid* __
                                                         uint8_t* __restrict__ mask, uint8_t* __restrict__ keep_flag) {
   const int n_open = *n_open_dev;
   const Grid g = *gp;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x) {
-    const int i = open[t];
-    // the open particle's cell and cell-local position from the particle
-    // grid (the proposal grid has the same geometry): integer ops and one
-    // load instead of FP64 arithmetic
-    const int key = pcells.cell_key[i];
-    const float2 li = pcells.sorted_loc[pcells.cell_start[key] + pcells.cell_rank[i]];
-    const int gy = key / g.nx, gx = key - gy * g.nx;
-    const float ux = li.x, uy = li.y;
-    unsigned mk = mask[i];
-    for (int by = gy - 1; by <= gy + 1; ++by) {
-      if (by < 0 || by >= g.ny) continue;
-      const float dvb = (float)(by - gy) - uy;
-      for (int bx = gx - 1; bx <= gx + 1; ++bx) {
-        if (bx < 0 || bx >= g.nx) continue;
-        const float dub = (float)(bx - gx) - ux;
-        const int cell = by * g.nx + bx;
-        const int q0 = cell_start[cell], q1 = cell_start[cell + 1];
-        for (int q = q0; q < q1; ++q) {
-          const float2 lo = sloc[q];
-          const float du = dub + lo.x, dv = dvb + lo.y;
-          const float d2f = __fmaf_rn(du, du, dv * dv);
-          if (d2f < g.lo_out || d2f > g.hi_out) continue;
-          if (!keep[sidx[q]]) continue;
-          int s = -1;
-          if (d2f > g.lo_in && d2f < g.hi_in) s = segment_or_ambiguous(du, dv, g.seg_eps);
-          if (s < 0) {
-            const double2 o = sxy[q];
-            const double dx = __dsub_rn(o.x, x[i]), dy = __dsub_rn(o.y, y[i]);
-            const double d2 = dist2(dx, dy);
-            if (d2 < c.lo2 || d2 > c.hi2) continue;
-            s = segment_of(dx, dy);
-          }
-          mk |= 1u << s;
-        }
-      }
-    }
-    mask[i] = (uint8_t)mk;
-    keep_flag[t] = mk != 0xFFu;
-  }
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x)
+    keep_flag[t] = mask_update_one(c, g, cell_start, sxy, sloc, sidx, keep, x, y, pcells, open[t], mask);
 }
 
 // out[k] = list[t] for the k-th flagged t (order kept); *count = total.
@@ -183,6 +192,20 @@ __global__ void k_cand_count_dev(const int* __restrict__ open, const StepState* 
     cnt[t] = __popc((~(unsigned)mask[open[t]]) & 0xFFu);
 }
 
+// The proposals of open particle i (its empty segments, ascending) from
+// list position pos on.
+__device__ __forceinline__ void emit_one(const Consts& c, int i, unsigned empty, const double* __restrict__ x,
+                                         const double* __restrict__ y, int pos, double* __restrict__ cx,
+                                         double* __restrict__ cy) {
+  const double xi = x[i], yi = y[i];
+  for (int s = 0; s < 8; ++s)
+    if ((empty >> s) & 1u) {
+      cx[pos] = __dadd_rn(xi, c.ins_dx[s]);
+      cy[pos] = __dadd_rn(yi, c.ins_dy[s]);
+      ++pos;
+    }
+}
+
 __global__ void k_cand_emit_dev(Consts c, const int* __restrict__ open, const StepState* __restrict__ st,
                                 const uint8_t* __restrict__ mask, const int* __restrict__ cpos,
                                 const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ cx,
@@ -190,15 +213,7 @@ __global__ void k_cand_emit_dev(Consts c, const int* __restrict__ open, const St
   const int n_open = st->n_open;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x) {
     const int i = open[t];
-    const unsigned empty = (~(unsigned)mask[i]) & 0xFFu;
-    const double xi = x[i], yi = y[i];
-    int pos = cpos[t];
-    for (int s = 0; s < 8; ++s)
-      if ((empty >> s) & 1u) {
-        cx[pos] = __dadd_rn(xi, c.ins_dx[s]);
-        cy[pos] = __dadd_rn(yi, c.ins_dy[s]);
-        ++pos;
-      }
+    emit_one(c, i, (~(unsigned)mask[i]) & 0xFFu, x, y, cpos[t], cx, cy);
   }
 }
 
