@@ -630,9 +630,10 @@ cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const doub
   cudaError_t e;
   if ((e = rounds_finish(s.st, s.rb.open, s.mask, cap, st)) != cudaSuccess) return e;
   if ((e = mark(ctx, VRM_STAGE_SEARCH, st)) != cudaSuccess) return e;
-  if ((e = grid_build_dev(x, y, cap, n_cur, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank,
-                          s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
-                          st)) != cudaSuccess)
+  // the grid of the given particles (enqueue_front) extended by the inserted
+  // ones, with its geometry kept
+  if ((e = grid_extend_dev(x, y, cap, &s.st->n, n_cur, s.ncell_cap, s.grid, s.cell_key, s.cell_rank, s.cell_count,
+                           s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.scan_tmp, st)) != cudaSuccess)
     return e;
   // rows of the diffused particles only (the LPs and the learned slots read
   // no other row; the application goes through the transposed stencils), in

@@ -422,6 +422,36 @@ cudaError_t grid_bin_dev(const double* x, const double* y, int n_bound, const in
   return cudaGetLastError();
 }
 
+// Particles [*n0_dev, *n1_dev) binned onto the counts of a grid that holds
+// [0, *n0_dev) already (their ranks follow the ones there).
+__global__ void k_bin_range(const double* __restrict__ x, const double* __restrict__ y,
+                            const int* __restrict__ n0_dev, const int* __restrict__ n1_dev,
+                            const Grid* __restrict__ gp, int* __restrict__ cell_key, int* __restrict__ cell_rank,
+                            int* __restrict__ cell_count) {
+  const int n0 = *n0_dev, n1 = *n1_dev;
+  const Grid g = *gp;
+  for (long i = n0 + (long)blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += (long)gridDim.x * blockDim.x) {
+    const int key = grid_cell_y(g, y[i]) * g.nx + grid_cell_x(g, x[i]);
+    cell_key[i] = key;
+    cell_rank[i] = atomicAdd(&cell_count[key], 1);
+  }
+}
+
+cudaError_t grid_extend_dev(const double* x, const double* y, int n_bound, const int* n0_dev, const int* n1_dev,
+                            int ncell_cap, const Grid* g, int* cell_key, int* cell_rank, int* cell_count,
+                            int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx, int* scan_tmp,
+                            cudaStream_t s) {
+  const int* ncell_dev = reinterpret_cast<const int*>(reinterpret_cast<const char*>(g) + offsetof(Grid, ncell));
+  const int b = stream_grid(n_bound, 8);
+  k_bin_range<<<b, kBlock, 0, s>>>(x, y, n0_dev, n1_dev, g, cell_key, cell_rank, cell_count); note_launch();
+  cudaError_t e = scan_exclusive_i32_dev(cell_count, cell_start, ncell_cap, ncell_dev, scan_tmp, s);
+  if (e != cudaSuccess) return e;
+  k_scatter<<<b, kBlock, 0, s>>>(x, y, n_bound, n1_dev, g, cell_key, cell_rank, cell_start, sorted_xy, sorted_loc,
+                                 sorted_idx);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t grid_build(const double* x, const double* y, int n, double Rh, double lo2, double hi2, int ncell_cap,
                        Grid* g, int* cell_key, int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy,
                        float2* sorted_loc, int* sorted_idx, unsigned long long* bbox_tmp, int* scan_tmp,

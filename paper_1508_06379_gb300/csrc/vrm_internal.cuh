@@ -215,6 +215,15 @@ cudaError_t grid_build_dev(const double* x, const double* y, int n_bound, const 
 cudaError_t grid_bin_dev(const double* x, const double* y, int n_bound, const int* n_dev, int ncell_cap, const Grid* g,
                          int* cell_key, int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy,
                          float2* sorted_loc, int* sorted_idx, int* scan_tmp, cudaStream_t s);
+// Grid g, built over [0, *n0_dev), extended to [0, *n1_dev) with the same
+// geometry: the new particles are binned onto the existing counts (points
+// outside the grid clamp into its edge cells; cells are >= R h, so the 3 x 3
+// scans stay complete), then the counts are scanned and every particle is
+// scattered again.  cell_count must still hold the counts of [0, *n0_dev).
+cudaError_t grid_extend_dev(const double* x, const double* y, int n_bound, const int* n0_dev, const int* n1_dev,
+                            int ncell_cap, const Grid* g, int* cell_key, int* cell_rank, int* cell_count,
+                            int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx, int* scan_tmp,
+                            cudaStream_t s);
 // Exclusive scan of n ints into out[0..n] (out[n] = total).
 cudaError_t scan_exclusive_i32(const int* in, int* out, int n, int* tmp, cudaStream_t s);
 // Scans and compaction with the count in device memory (*n_dev <= n_bound).
