@@ -171,7 +171,7 @@ void free_scratch(Scratch& s) {
   RoundBufs& r = s.rb;
   void* ptrs[] = {s.grid, s.cell_key, s.cell_rank, s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc,
                   s.sorted_idx, s.bbox, s.scan_tmp, s.pos, s.rstate, s.tie_flag, s.tie_rank, s.diffused, s.dlist,
-                  s.mask, r.open, r.open_next, r.cnt, r.cpos, r.keep_flag, r.keep_pos, r.cx, r.cy, r.keep, r.apos,
+                  s.mask, r.open, r.act0, r.act1, r.cnt, r.cpos, r.keep_flag, r.cx, r.cy, r.keep, r.apos,
                   r.cg.grid, r.cg.cell_key, r.cg.cell_rank, r.cg.cell_count, r.cg.cell_start, r.cg.sorted_idx,
                   r.cg.sorted_xy, r.cg.sorted_loc, r.cg.bbox, r.scan_tmp, s.nbr_count, s.nbr_idx, s.small, s.cols,
                   s.fail_list, s.retry_list, s.seg_mask, s.status, s.f, s.fii, s.tcount, s.toff, s.tplace, s.tent, s.ds,
@@ -418,11 +418,11 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.dlist, n);
   VRM_ALLOC(s.mask, n);
   VRM_ALLOC(r.open, n);
-  VRM_ALLOC(r.open_next, n);
+  VRM_ALLOC(r.act0, n);
+  VRM_ALLOC(r.act1, n);
   VRM_ALLOC(r.cnt, n);
   VRM_ALLOC(r.cpos, (long)n + 1);
   VRM_ALLOC(r.keep_flag, n);
-  VRM_ALLOC(r.keep_pos, (long)n + 1);
   VRM_ALLOC(r.cx, n8);
   VRM_ALLOC(r.cy, n8);
   VRM_ALLOC(r.keep, n8);
@@ -456,6 +456,8 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.counters, 8);
   VRM_ALLOC(s.st, 1);
 #undef VRM_ALLOC
+  // the proposal cells start empty; every insertion round leaves them empty
+  if (e == cudaSuccess) e = cudaMemsetAsync(r.cg.cell_count, 0, sizeof(int) * (size_t)ncell, st);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_ds, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_counters, sizeof(int) * 8);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_grid, sizeof(Grid));
@@ -628,7 +630,7 @@ cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const doub
   const Consts& c = ctx->c;
   const int* n_cur = &s.st->n_cur;
   cudaError_t e;
-  if ((e = rounds_finish(s.st, s.rb.open, s.mask, cap, st)) != cudaSuccess) return e;
+  if ((e = rounds_finish(s.st, s.rb, cap, st)) != cudaSuccess) return e;
   if ((e = mark(ctx, VRM_STAGE_SEARCH, st)) != cudaSuccess) return e;
   // the grid of the given particles (enqueue_front) extended by the inserted
   // ones, with its geometry kept
@@ -698,7 +700,7 @@ bool record_step(vrm_ctx* ctx, cudaStream_t cs, cudaStream_t body_stream, double
     ok = cudaStreamGetCaptureInfo(cs, &status, nullptr, &cg, nullptr, nullptr, nullptr) == cudaSuccess;
     ok = ok && cudaGraphConditionalHandleCreate(&handle, cg, 0, cudaGraphCondAssignDefault) == cudaSuccess;
   }
-  ok = ok && rounds_init(s.st, s.counters + 1, handle, true, cs) == cudaSuccess;
+  ok = ok && rounds_init(s.st, s.counters + 1, s.rb, s.mask, cap, handle, true, cs) == cudaSuccess;
   if (ok) {
     cudaStreamCaptureStatus status;
     cudaGraph_t cg = nullptr;
@@ -782,7 +784,7 @@ vrm_status run_step_eager(vrm_ctx* ctx, double* x, double* y, int cap, const dou
   Scratch& s = ctx->s;
   VRM_CUDA(enqueue_head(ctx, st));
   VRM_CUDA(enqueue_front(ctx, x, y, cap, gamma_in, diffused, st));
-  VRM_CUDA(rounds_init(s.st, s.counters + 1, 0, false, st));
+  VRM_CUDA(rounds_init(s.st, s.counters + 1, s.rb, s.mask, cap, 0, false, st));
   for (int r = 0; r < ctx->p.max_rounds; ++r) {
     VRM_CUDA(cudaMemcpyAsync(s.h_state, s.st, sizeof(StepState), cudaMemcpyDeviceToHost, st));
     VRM_CUDA(cudaStreamSynchronize(st));
@@ -792,7 +794,7 @@ vrm_status run_step_eager(vrm_ctx* ctx, double* x, double* y, int cap, const dou
   if (back) {
     VRM_CUDA(enqueue_back(ctx, x, y, cap, gamma_in, gamma_out, st));
   } else {
-    VRM_CUDA(rounds_finish(s.st, s.rb.open, s.mask, cap, st));
+    VRM_CUDA(rounds_finish(s.st, s.rb, cap, st));
   }
   return VRM_OK;
 }

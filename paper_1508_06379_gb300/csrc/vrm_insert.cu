@@ -9,12 +9,12 @@
 //
 // One round works on explicit lists:
 //   1. the proposals are written in key order (open particles ascending,
-//      segments ascending), so a proposal's list index is its key rank;
-//   2. the proposals get their own cell grid (cell side >= R h);
-//   3. conflict test: each proposal scans the 3 x 3 cells around it for a
+//      segments ascending), so a proposal's list index is its key rank, and
+//      binned into their own cell grid (cell side >= R h);
+//   2. conflict test: each proposal scans the 3 x 3 cells around it for a
 //      proposal of smaller list index within r h;
-//   4. the accepted ones are appended in list order;
-//   5. every open particle ORs into its segment mask the accepted proposals
+//   3. the accepted ones are appended in list order;
+//   4. every open particle ORs into its segment mask the accepted proposals
 //      of its annulus, found in the same 3 x 3 cells.
 // All threads of a warp do the same kind of work on nearby proposals, and
 // every distance is the FP64 definition, so the result is the oracle's.
@@ -124,22 +124,6 @@ __device__ __forceinline__ bool mask_update_one(const Consts& c, const Grid& g, 
   return mk != 0xFFu;
 }
 
-// mask_update_one for every open particle; keep_flag[t] = still open.
-__global__ void __launch_bounds__(kBlock) k_mask_update(Consts c, const Grid* __restrict__ gp,
-                                                        const int* __restrict__ cell_start,
-                                                        const double2* __restrict__ sxy,
-                                                        const float2* __restrict__ sloc,
-                                                        const int* __restrict__ sidx, const uint8_t* __restrict__ keep,
-                                                        const double* __restrict__ x, const double* __restrict__ y,
-                                                        PartCells pcells, const int* __restrict__ open,
-                                                        const int* __restrict__ n_open_dev,
-                                                        uint8_t* __restrict__ mask, uint8_t* __restrict__ keep_flag) {
-  const int n_open = *n_open_dev;
-  const Grid g = *gp;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x)
-    keep_flag[t] = mask_update_one(c, g, cell_start, sxy, sloc, sidx, keep, x, y, pcells, open[t], mask);
-}
-
 // out[k] = list[t] for the k-th flagged t (order kept); *count = total.
 __global__ void k_compact_list(const int* __restrict__ list, const uint8_t* __restrict__ flag,
                                const int* __restrict__ pos, int m, const int* __restrict__ m_dev,
@@ -169,15 +153,33 @@ cudaError_t open_list(const int* dlist, const int* dcount, int cap, const uint8_
 }
 
 // ---- device-resident rounds (no host round trips; graph-capturable) ----------
+//
+// Every round works on the open list of the first round (open[0 .. n_list),
+// ascending): cnt[t] is the number of empty segments of open particle t while
+// it is open and 0 once its mask is full, so the proposals of all open
+// particles, numbered by the exclusive scan of cnt, come out in key order
+// without compacting the list between rounds.  The positions t still open
+// are also kept unordered in act0 / act1 (even / odd rounds; appended with
+// warp-aggregated atomics), so that the per-particle work of a round visits
+// only them.  Per round: scan of cnt, proposals written and binned
+// (k_emit_bin), scan of the cell counts, scatter into cell order
+// (k_cand_scatter, which also empties the cells again for the next round),
+// conflict test, scan of the accepted flags, and k_round_update: append,
+// mask update, next counts and active positions, and the round's end.
 
 __global__ void k_rounds_init(StepState* st, const int* __restrict__ n_open_src, cudaGraphConditionalHandle h,
                               int graph) {
   st->n_open = *n_open_src;
+  st->n_list = st->n_open;
   st->round = 0;
   st->rounds_appended = 0;
   st->overflow = 0;
   st->n_needed = 0;
   st->open_segments = 0;
+  st->n_next = 0;
+  st->n_act[0] = st->n_open;
+  st->n_act[1] = 0;
+  st->blocks_done = 0;
   st->n_cur = st->n;
   // with max_rounds = 0 no round runs and the open list stays as it is: its
   // empty segments are the ones reported
@@ -185,96 +187,214 @@ __global__ void k_rounds_init(StepState* st, const int* __restrict__ n_open_src,
   if (graph) cudaGraphSetConditional(h, go);
 }
 
-__global__ void k_cand_count_dev(const int* __restrict__ open, const StepState* __restrict__ st,
-                                 const uint8_t* __restrict__ mask, int* __restrict__ cnt) {
-  const int n_open = st->n_open;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x)
-    cnt[t] = __popc((~(unsigned)mask[open[t]]) & 0xFFu);
-}
-
-// The proposals of open particle i (its empty segments, ascending) from
-// list position pos on.
-__device__ __forceinline__ void emit_one(const Consts& c, int i, unsigned empty, const double* __restrict__ x,
-                                         const double* __restrict__ y, int pos, double* __restrict__ cx,
-                                         double* __restrict__ cy) {
-  const double xi = x[i], yi = y[i];
-  for (int s = 0; s < 8; ++s)
-    if ((empty >> s) & 1u) {
-      cx[pos] = __dadd_rn(xi, c.ins_dx[s]);
-      cy[pos] = __dadd_rn(yi, c.ins_dy[s]);
-      ++pos;
-    }
-}
-
-__global__ void k_cand_emit_dev(Consts c, const int* __restrict__ open, const StepState* __restrict__ st,
-                                const uint8_t* __restrict__ mask, const int* __restrict__ cpos,
-                                const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ cx,
-                                double* __restrict__ cy) {
-  const int n_open = st->n_open;
+// cnt[t] of the first round; every position is active.
+__global__ void k_cand_count_dev(const int* __restrict__ open, const int* __restrict__ n_open_src,
+                                 const uint8_t* __restrict__ mask, int* __restrict__ cnt, int* __restrict__ act0) {
+  const int n_open = *n_open_src;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x) {
-    const int i = open[t];
-    emit_one(c, i, (~(unsigned)mask[i]) & 0xFFu, x, y, cpos[t], cx, cy);
+    cnt[t] = __popc((~(unsigned)mask[open[t]]) & 0xFFu);
+    act0[t] = (int)t;
   }
 }
 
-// Appends the accepted proposals.  Every block checks the capacity itself
-// (accepted count apos[n_cand]); block 0 records the count and, when the
-// cloud would outgrow its buffers, the overflow flag (then the round appends
-// nothing and the loop stops).
+// Proposals of every open particle written at their key rank and binned on
+// the particle grid's geometry (cells >= R h; points outside it clamp into
+// the edge cells, which keeps 3 x 3 scans complete).  Each warp takes 32
+// active positions and spreads their proposals over its lanes, so that the
+// FP64 position and cell arithmetic runs on full warps.  The cell counts are
+// 0 on entry.
+__global__ void k_emit_bin(Consts c, const int* __restrict__ open, const StepState* __restrict__ st,
+                           const int* __restrict__ act0, const int* __restrict__ act1,
+                           const uint8_t* __restrict__ mask, const int* __restrict__ cpos,
+                           const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ cx,
+                           double* __restrict__ cy, const Grid* __restrict__ gp, int* __restrict__ cell_key,
+                           int* __restrict__ cell_rank, int* __restrict__ cell_count) {
+  const int par = st->round & 1;
+  const int* act = par ? act1 : act0;
+  const int n_act = st->n_act[par];
+  const Grid g = *gp;
+  const int lane = threadIdx.x & 31;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_act; base += stride) {
+    const long k = base + lane;
+    int i = 0, pos0 = 0;
+    unsigned empty = 0;
+    double xi = 0.0, yi = 0.0;
+    if (k < n_act) {
+      const int t = act[k];
+      i = open[t];
+      empty = (~(unsigned)mask[i]) & 0xFFu;
+      pos0 = cpos[t];
+      xi = x[i];
+      yi = y[i];
+    }
+    // inclusive prefix of the proposal counts over the warp
+    const int cntl = __popc(empty);
+    int incl = cntl;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int q0 = 0; q0 < total; q0 += 32) {
+      const int q = q0 + lane;
+      // owner: the first lane whose inclusive prefix exceeds q
+      int owner = 0;
+#pragma unroll
+      for (int l = 0; l < 32; ++l) {
+        const int il = __shfl_sync(0xffffffffu, incl, l);
+        owner += (il <= q) ? 1 : 0;
+      }
+      owner = owner < 31 ? owner : 31;
+      const unsigned emp_o = __shfl_sync(0xffffffffu, empty, owner);
+      const int excl_o = __shfl_sync(0xffffffffu, incl - cntl, owner);
+      const int pos_o = __shfl_sync(0xffffffffu, pos0, owner);
+      const double xo = __shfl_sync(0xffffffffu, xi, owner), yo = __shfl_sync(0xffffffffu, yi, owner);
+      if (q < total) {
+        const int r = q - excl_o;  // the owner's r-th empty segment (from 0), ascending
+        int sg = 0, seen = 0;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const bool e = (emp_o >> b) & 1u;
+          sg = (e && seen == r) ? b : sg;
+          seen += e;
+        }
+        const int pos = pos_o + r;
+        const double xp = __dadd_rn(xo, c.ins_dx[sg]), yp = __dadd_rn(yo, c.ins_dy[sg]);
+        cx[pos] = xp;
+        cy[pos] = yp;
+        const int key = grid_cell_y(g, yp) * g.nx + grid_cell_x(g, xp);
+        cell_key[pos] = key;
+        cell_rank[pos] = atomicAdd(&cell_count[key], 1);
+      }
+    }
+  }
+}
+
+// Proposals into cell order (sorted_xy, sorted_loc, sorted_idx), and their
+// cells' counts set back to 0.
+__global__ void k_cand_scatter(const double* __restrict__ cx, const double* __restrict__ cy,
+                               const StepState* __restrict__ st, const Grid* __restrict__ gp,
+                               const int* __restrict__ cell_key, const int* __restrict__ cell_rank,
+                               const int* __restrict__ cell_start, int* __restrict__ cell_count,
+                               double2* __restrict__ sorted_xy, float2* __restrict__ sorted_loc,
+                               int* __restrict__ sorted_idx) {
+  const int n_cand = st->n_cand;
+  const Grid g = *gp;
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n_cand; p += (long)gridDim.x * blockDim.x) {
+    const int key = cell_key[p];
+    const int q = cell_start[key] + cell_rank[p];
+    const double xp = cx[p], yp = cy[p];
+    sorted_xy[q] = make_double2(xp, yp);
+    sorted_loc[q] = make_float2(grid_local_x(g, xp, key % g.nx), grid_local_y(g, yp, key / g.nx));
+    sorted_idx[q] = (int)p;
+    cell_count[key] = 0;
+  }
+}
+
+// Appends the accepted proposals in key order, unless the cloud would
+// outgrow its buffers (then nothing is appended; k_round_update sets the
+// overflow flag and the loop stops).
 __global__ void k_append_dev(const double* __restrict__ cx, const double* __restrict__ cy,
                              const uint8_t* __restrict__ keep, const int* __restrict__ apos,
-                             StepState* __restrict__ st, double* __restrict__ x, double* __restrict__ y) {
+                             const StepState* __restrict__ st, double* __restrict__ x, double* __restrict__ y) {
+  const int n_cand = st->n_cand, n_cur = st->n_cur;
+  if ((long)n_cur + apos[n_cand] > st->capacity) return;
+  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n_cand; p += (long)gridDim.x * blockDim.x)
+    if (keep[p]) {
+      x[n_cur + apos[p]] = cx[p];
+      y[n_cur + apos[p]] = cy[p];
+    }
+}
+
+// The end of a round: every open particle's mask ORed with the accepted
+// proposals of its annulus (positions [0, n_cur) of x, y, untouched by the
+// append), its count for the next round set (0 once the mask is full) and,
+// if still open, its position appended to the next active list; the last
+// block to finish records the round's counters and the loop condition.
+__global__ void __launch_bounds__(kBlock) k_round_update(
+    Consts c, const Grid* __restrict__ gp, const int* __restrict__ cell_start, const double2* __restrict__ sxy,
+    const float2* __restrict__ sloc, const int* __restrict__ sidx, const uint8_t* __restrict__ keep,
+    const int* __restrict__ apos, const int* __restrict__ open, int* __restrict__ cnt, int* __restrict__ act0,
+    int* __restrict__ act1, PartCells pcells, StepState* __restrict__ st, const double* __restrict__ x,
+    const double* __restrict__ y, uint8_t* __restrict__ mask, cudaGraphConditionalHandle h, int graph) {
   const int n_cand = st->n_cand, n_cur = st->n_cur;
   const int a = apos[n_cand];
   const bool over = (long)n_cur + a > st->capacity;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->accepted = a;
-    if (over) {
-      st->overflow = 1;
-      st->n_needed = n_cur + a;
+  const Grid g = *gp;
+  const long stride = (long)gridDim.x * blockDim.x;
+  // whole warps step through the active list so that the ones still open
+  // are appended to the next list with one atomic per warp
+  const int par = st->round & 1;
+  const int* act = par ? act1 : act0;
+  int* act_next = par ? act0 : act1;
+  const int n_act = st->n_act[par];
+  const int lane = threadIdx.x & 31;
+  for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_act; base += stride) {
+    const long k = base + lane;
+    bool still = false;
+    int t = 0;
+    if (k < n_act) {
+      t = act[k];
+      const int i = open[t];
+      still = mask_update_one(c, g, cell_start, sxy, sloc, sidx, keep, x, y, pcells, i, mask);
+      cnt[t] = still ? __popc((~(unsigned)mask[i]) & 0xFFu) : 0;
+    }
+    const unsigned sb = __ballot_sync(0xffffffffu, still);
+    if (sb) {
+      const int lead = __ffs(sb) - 1;
+      int slot0 = 0;
+      if (lane == lead) slot0 = atomicAdd(&st->n_act[par ^ 1], __popc(sb));
+      slot0 = __shfl_sync(0xffffffffu, slot0, lead);
+      if (still) act_next[slot0 + __popc(sb & ((1u << lane) - 1u))] = t;
     }
   }
-  if (over) return;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_cand; t += (long)gridDim.x * blockDim.x)
-    if (keep[t]) {
-      x[n_cur + apos[t]] = cx[t];
-      y[n_cur + apos[t]] = cy[t];
-    }
-}
-
-__global__ void k_copy_list(const int* __restrict__ src, int* __restrict__ dst, const StepState* __restrict__ st) {
-  const int m = st->n_next;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) dst[t] = src[t];
-}
-
-__global__ void k_round_end(StepState* st, cudaGraphConditionalHandle h, int graph) {
+  // the last block to finish ends the round (no shared memory in this
+  // kernel: a shared flag would take L1 capacity from its lookups)
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  __threadfence();
+  if (atomicAdd(&st->blocks_done, 1u) != gridDim.x - 1) return;
+  __threadfence();
+  const int n_next = *(volatile int*)&st->n_act[par ^ 1];
+  st->n_act[par] = 0;  // the list this round read becomes the next round's output
+  st->n_next = n_next;
+  st->blocks_done = 0;
+  st->accepted = a;
+  if (over) {
+    st->overflow = 1;
+    st->n_needed = n_cur + a;
+  }
   if (st->n_open > 0) {
-    if (!st->overflow) {
-      st->n_cur += st->accepted;
-      if (st->accepted > 0) st->rounds_appended += 1;
+    if (!over) {
+      st->n_cur = n_cur + a;
+      if (a > 0) st->rounds_appended += 1;
     }
     st->round += 1;
-    st->n_open = st->overflow ? 0 : st->n_next;
+    st->n_open = over ? 0 : n_next;
   }
-  // rounds stop at max_rounds with the open list kept for the statistics
-  const int go = !st->overflow && st->n_open > 0 && st->round < st->max_rounds;
+  // rounds stop at max_rounds with the open particles kept for the statistics
+  const int go = !over && st->n_open > 0 && st->round < st->max_rounds;
   if (graph) cudaGraphSetConditional(h, go);
 }
 
-// Empty segments left (only when max_rounds ended the loop with open particles).
-__global__ void k_rounds_finish(StepState* st, const int* __restrict__ open, const uint8_t* __restrict__ mask) {
-  const int n_open = (st->overflow || st->round < st->max_rounds) ? 0 : st->n_open;
+// Empty segments left (only when max_rounds ended the loop with open
+// particles): the sum of the counts.
+__global__ void k_rounds_finish(StepState* st, const int* __restrict__ cnt) {
+  const int n_list = (st->overflow || st->round < st->max_rounds || st->n_open == 0) ? 0 : st->n_list;
   int s = 0;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x)
-    s += __popc((~(unsigned)mask[open[t]]) & 0xFFu);
+  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_list; t += (long)gridDim.x * blockDim.x)
+    s += cnt[t];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(&st->open_segments, s);
 }
 
-cudaError_t rounds_init(StepState* st, const int* n_open_src, cudaGraphConditionalHandle handle, bool graph,
-                        cudaStream_t s) {
+cudaError_t rounds_init(StepState* st, const int* n_open_src, const RoundBufs& rb, const uint8_t* mask, int cap,
+                        cudaGraphConditionalHandle handle, bool graph, cudaStream_t s) {
   k_rounds_init<<<1, 1, 0, s>>>(st, n_open_src, handle, graph ? 1 : 0); note_launch();
+  k_cand_count_dev<<<blocks_for(cap), kBlock, 0, s>>>(rb.open, n_open_src, mask, rb.cnt, rb.act0); note_launch();
   return cudaGetLastError();
 }
 
@@ -284,38 +404,33 @@ cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const 
   const int bo = blocks_for(cap);
   const long cand_cap = 8L * cap;
   const int bc = blocks_for((int)(cand_cap < 0x7FFFFFFF ? cand_cap : 0x7FFFFFFF));
-  k_cand_count_dev<<<bo, kBlock, 0, s>>>(rb.open, st, mask, rb.cnt); note_launch();
-  cudaError_t e = scan_exclusive_i32_dev(rb.cnt, rb.cpos, cap, &st->n_open, rb.scan_tmp, s, &st->n_cand);
+  const CandGrid& cg = rb.cg;
+  const int* ncell_dev = reinterpret_cast<const int*>(reinterpret_cast<const char*>(pgrid) + offsetof(Grid, ncell));
+  cudaError_t e = scan_exclusive_i32_dev(rb.cnt, rb.cpos, cap, &st->n_list, rb.scan_tmp, s, &st->n_cand);
   if (e != cudaSuccess) return e;
-  k_cand_emit_dev<<<bo, kBlock, 0, s>>>(c, rb.open, st, mask, rb.cpos, x, y, rb.cx, rb.cy); note_launch();
-  // proposals binned on the particle grid's geometry (cells >= R h; points
-  // outside it clamp into the edge cells, which keeps 3 x 3 scans complete)
-  e = grid_bin_dev(rb.cx, rb.cy, (int)cand_cap, &st->n_cand, rb.ncell_cap, pgrid, rb.cg.cell_key,
-                   rb.cg.cell_rank, rb.cg.cell_count, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
-                   rb.cg.sorted_idx, rb.scan_tmp, s);
+  k_emit_bin<<<bc, kBlock, 0, s>>>(c, rb.open, st, rb.act0, rb.act1, mask, rb.cpos, x, y, rb.cx, rb.cy, pgrid,
+                                   cg.cell_key, cg.cell_rank, cg.cell_count);
+  note_launch();
+  e = scan_exclusive_i32_dev(cg.cell_count, cg.cell_start, rb.ncell_cap, ncell_dev, rb.scan_tmp, s);
   if (e != cudaSuccess) return e;
-  k_conflict<<<bc, kBlock, 0, s>>>(c, pgrid, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
-                                   rb.cg.sorted_idx, rb.cg.cell_key, &st->n_cand, rb.keep);
+  k_cand_scatter<<<bc, kBlock, 0, s>>>(rb.cx, rb.cy, st, pgrid, cg.cell_key, cg.cell_rank, cg.cell_start,
+                                       cg.cell_count, cg.sorted_xy, cg.sorted_loc, cg.sorted_idx);
+  note_launch();
+  k_conflict<<<bc, kBlock, 0, s>>>(c, pgrid, cg.cell_start, cg.sorted_xy, cg.sorted_loc, cg.sorted_idx, cg.cell_key,
+                                   &st->n_cand, rb.keep);
   note_launch();
   e = scan_exclusive_u8_dev(rb.keep, rb.apos, (int)cand_cap, &st->n_cand, rb.scan_tmp, s);
   if (e != cudaSuccess) return e;
   k_append_dev<<<bc, kBlock, 0, s>>>(rb.cx, rb.cy, rb.keep, rb.apos, st, x, y); note_launch();
-  k_mask_update<<<bo, kBlock, 0, s>>>(c, pgrid, rb.cg.cell_start, rb.cg.sorted_xy, rb.cg.sorted_loc,
-                                      rb.cg.sorted_idx, rb.keep, x, y, pcells, rb.open, &st->n_open, mask,
-                                      rb.keep_flag);
+  k_round_update<<<bo, kBlock, 0, s>>>(c, pgrid, cg.cell_start, cg.sorted_xy, cg.sorted_loc, cg.sorted_idx, rb.keep,
+                                       rb.apos, rb.open, rb.cnt, rb.act0, rb.act1, pcells, st, x, y, mask, handle,
+                                       graph ? 1 : 0);
   note_launch();
-  e = scan_exclusive_u8_dev(rb.keep_flag, rb.keep_pos, cap, &st->n_open, rb.scan_tmp, s);
-  if (e != cudaSuccess) return e;
-  k_compact_list<<<bo, kBlock, 0, s>>>(rb.open, rb.keep_flag, rb.keep_pos, cap, &st->n_open, rb.open_next,
-                                       &st->n_next);
-  note_launch();
-  k_copy_list<<<bo, kBlock, 0, s>>>(rb.open_next, rb.open, st); note_launch();
-  k_round_end<<<1, 1, 0, s>>>(st, handle, graph ? 1 : 0); note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t rounds_finish(StepState* st, const int* open, const uint8_t* mask, int cap, cudaStream_t s) {
-  k_rounds_finish<<<blocks_for(cap), kBlock, 0, s>>>(st, open, mask); note_launch();
+cudaError_t rounds_finish(StepState* st, const RoundBufs& rb, int cap, cudaStream_t s) {
+  k_rounds_finish<<<blocks_for(cap), kBlock, 0, s>>>(st, rb.cnt); note_launch();
   return cudaGetLastError();
 }
 

@@ -124,6 +124,9 @@ struct StepState {
   int n_needed;        // particles that would have been needed then
   int open_segments;   // empty segments left when max_rounds is reached
   int max_rounds;
+  int n_list;          // length of the first round's open list (every round works on it)
+  int n_act[2];        // lengths of RoundBufs::act0 / act1
+  unsigned blocks_done;  // blocks of the round's last kernel that have finished
 };
 
 struct Scratch;  // defined in vrm_api.cu
@@ -286,10 +289,10 @@ cudaError_t open_list(const int* dlist, const int* dcount, int cap, const uint8_
 // Buffers of the device-resident insertion rounds (proposal capacity 8 n).
 struct RoundBufs {
   int* open;           // open list (cap)
-  int* open_next;      // compacted next open list (cap)
+  int* act0;           // open-list positions still open in the round, unordered (cap):
+  int* act1;           // act0 for even rounds, act1 for odd ones
   int *cnt, *cpos;     // proposals per open particle and their offsets (cap, cap+1)
   uint8_t *keep_flag;  // open particle still open (cap)
-  int* keep_pos;       // (cap+1)
   double *cx, *cy;     // proposals (8 cap)
   uint8_t* keep;       // proposal accepted (8 cap)
   int* apos;           // offsets of accepted proposals (8 cap + 1)
@@ -306,17 +309,19 @@ struct PartCells {
   const int* cell_start;
   const float2* sorted_loc;
 };
-// Round state initialisation after the open list exists; sets the loop
-// condition (handle may be 0 when not capturing).
-cudaError_t rounds_init(StepState* st, const int* n_open_src, cudaGraphConditionalHandle handle, bool graph,
-                        cudaStream_t s);
+// Round state initialisation after the open list exists (rb.open, *n_open_src
+// entries): the counts of the first round's proposals (rb.cnt); sets the
+// loop condition (handle may be 0 when not capturing).  rb.cg.cell_count
+// must be all 0 (it is after allocation and after every round).
+cudaError_t rounds_init(StepState* st, const int* n_open_src, const RoundBufs& rb, const uint8_t* mask, int cap,
+                        cudaGraphConditionalHandle handle, bool graph, cudaStream_t s);
 // One insertion round on device-resident counts; a no-op once the state has
 // no open particle.  The last kernel updates the state and, in a graph, sets
 // the while-loop condition.
 cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const PartCells& pcells, const RoundBufs& rb,
                        int cap, uint8_t* mask, double* x, double* y, cudaGraphConditionalHandle handle, bool graph,
                        cudaStream_t s);
-cudaError_t rounds_finish(StepState* st, const int* open, const uint8_t* mask, int cap, cudaStream_t s);
+cudaError_t rounds_finish(StepState* st, const RoundBufs& rb, int cap, cudaStream_t s);
 
 // vrm_lp.cu
 // nu_dt = nu * dt for the stability statistic; with dt_dev it is nu * *dt_dev.
