@@ -99,57 +99,9 @@ __global__ void k_tile_sums(const T* __restrict__ in, int n, const int* __restri
   }
 }
 
-// Single block: exclusive scan of the tile sums in place; tile_sums[ntiles]
-// receives the grand total.
-__global__ void k_scan_tile_sums(int* __restrict__ tile_sums, int n, const int* __restrict__ n_dev) {
-  if (n_dev) n = *n_dev;
-  const int ntiles = (n + kScanTile - 1) / kScanTile;
-  __shared__ int total;
-  int carry = 0;
-  for (int base = 0; base < ntiles; base += kScanThreads) {
-    int i = base + threadIdx.x;
-    int v = i < ntiles ? tile_sums[i] : 0;
-    int ex = block_exclusive_scan(v, &total);
-    if (i < ntiles) tile_sums[i] = ex + carry;
-    carry += total;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) tile_sums[ntiles] = carry;
-}
-
-template <typename T>
-__global__ void k_tile_scan(const T* __restrict__ in, int n, const int* __restrict__ n_dev,
-                            const int* __restrict__ tile_sums, int* __restrict__ out, int* __restrict__ total_out) {
-  if (n_dev) n = *n_dev;
-  const int ntiles = (n + kScanTile - 1) / kScanTile;
-  __shared__ int total;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    long base = (long)t * kScanTile + (long)threadIdx.x * kScanItems;
-    int v[kScanItems];
-    int s = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      v[k] = load_count(in, base + k, n);
-      s += v[k];
-    }
-    int ex = block_exclusive_scan(s, &total) + tile_sums[t];
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      if (base + k < n) out[base + k] = ex;
-      ex += v[k];
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    out[n] = tile_sums[ntiles];
-    if (total_out) *total_out = tile_sums[ntiles];
-  }
-}
-
-// Tile scan that forms the tile's exclusive prefix itself: the block sums
-// the totals of the tiles before it (tile_sums from k_tile_sums; at most
-// kFusedScanTiles of them, at most 16 KB read from L2), which saves the
-// single-block scan of the tile sums and its launch.  out[n] = the total.
-constexpr int kFusedScanTiles = 4096;
+// Tile scan that forms each tile's exclusive prefix itself from the tile
+// totals of k_tile_sums (no separate scan of the tile sums and no launch
+// for it).  out[n] = the total.
 template <typename T>
 __global__ void k_tile_scan_fused(const T* __restrict__ in, int n, const int* __restrict__ n_dev,
                                   const int* __restrict__ tile_sums, int* __restrict__ out,
@@ -161,11 +113,15 @@ __global__ void k_tile_scan_fused(const T* __restrict__ in, int n, const int* __
     out[0] = 0;
     if (total_out) *total_out = 0;
   }
+  // a block's tiles ascend, so the prefix of tile t is carried forward from
+  // the block's previous tile: every block reads the tile sums once in all
+  int pre = 0, upto = 0;  // pre = sum of tile_sums[0 .. upto)
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     int part = 0;
-    for (int k = threadIdx.x; k < t; k += kScanThreads) part += tile_sums[k];
+    for (int k = upto + threadIdx.x; k < t; k += kScanThreads) part += tile_sums[k];
     block_exclusive_scan(part, &total);
-    const int pre = total;
+    pre += total;
+    upto = t;
     long base = (long)t * kScanTile + (long)threadIdx.x * kScanItems;
     int v[kScanItems];
     int s = 0;
@@ -204,12 +160,7 @@ static cudaError_t scan_impl(const T* in, int* out, int n, const int* n_dev, int
   }
   const int g = scan_grid(n);
   k_tile_sums<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp); note_launch();
-  if ((n + kScanTile - 1) / kScanTile <= kFusedScanTiles) {
-    k_tile_scan_fused<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp, out, total_out); note_launch();
-  } else {
-    k_scan_tile_sums<<<1, kScanThreads, 0, s>>>(tmp, n, n_dev); note_launch();
-    k_tile_scan<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp, out, total_out); note_launch();
-  }
+  k_tile_scan_fused<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp, out, total_out); note_launch();
   return cudaGetLastError();
 }
 
