@@ -456,6 +456,8 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.counters, 8);
   VRM_ALLOC(s.st, 1);
 #undef VRM_ALLOC
+  // the growth control's pass counter starts at 0 (every pass leaves it so)
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.rstate, 0, sizeof(ReduceState), st);
   // the proposal cells start empty; every insertion round leaves them empty
   if (e == cudaSuccess) e = cudaMemsetAsync(r.cg.cell_count, 0, sizeof(int) * (size_t)ncell, st);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_ds, sizeof(DevStats));

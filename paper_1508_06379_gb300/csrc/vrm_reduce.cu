@@ -61,25 +61,15 @@ __device__ __forceinline__ u128 limbs_value(const unsigned long long* h) {
   return (u128)__ldcg(h) + ((u128)__ldcg(h + 1) << 32) + ((u128)__ldcg(h + 2) << 64);
 }
 
-__global__ void k_reduce_init(ReduceState* st) {
-  int t = threadIdx.x;
-  for (int b = t; b < 256; b += blockDim.x) st->hist[b][0] = st->hist[b][1] = st->hist[b][2] = st->hist[b][3] = 0;
-  if (t == 0) {
-    st->amax_bits = 0;
-    st->E = 0;
-    st->done = 0;
-    st->prefix = 0;
-    st->tau_lo = st->tau_hi = 0;
-    st->T = 0;
-    st->k_tie = 0;
-    st->all_out = 0;
-    st->blocks_done = 0;
-    st->n_sub = 0;
-  }
-}
 
+// max |Gamma| (Inf/NaN flagged in ds->nonfinite) and the selection state
+// set up for pass 0: each block leaves its maximum in the histogram memory,
+// and the last block to finish takes the maximum, clears the histograms and
+// the state, and marks the selection done when nothing can diffuse (no
+// circulation, or a bound of at least ||Gamma||_1).  st->blocks_done is 0
+// on entry (after allocation and after every pass).
 __global__ void k_absmax(const double* __restrict__ g, int n, const int* __restrict__ n_dev, ReduceState* __restrict__ st,
-                         DevStats* ds) {
+                         DevStats* ds, double c_bound) {
   if (n_dev) n = *n_dev;
   unsigned long long m = 0;
   int bad = 0;
@@ -97,22 +87,57 @@ __global__ void k_absmax(const double* __restrict__ g, int n, const int* __restr
     m = t > m ? t : m;
   }
   bad = __any_sync(0xffffffffu, bad);
-  // one atomic per block (per-warp atomics on one address serialise at L2)
   __shared__ unsigned long long w_m[32];
   __shared__ int w_bad[32];
+  __shared__ bool last;
   const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   if ((threadIdx.x & 31) == 0) {
     w_m[warp] = m;
     w_bad[warp] = bad;
   }
   __syncthreads();
+  unsigned long long* const part = &st->hist[0][0];  // 1024 slots >= gridDim.x
   if (threadIdx.x == 0) {
     for (int w = 1; w < nw; ++w) {
       m = w_m[w] > m ? w_m[w] : m;
       bad |= w_bad[w];
     }
-    if (m) atomicMax(&st->amax_bits, m);
+    part[blockIdx.x] = m;
     if (bad) atomicOr(&ds->nonfinite, 1);
+    __threadfence();
+    last = atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  unsigned long long amax = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    const unsigned long long v = ((volatile unsigned long long*)part)[b];
+    amax = v > amax ? v : amax;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long t = __shfl_xor_sync(0xffffffffu, amax, o);
+    amax = t > amax ? t : amax;
+  }
+  if ((threadIdx.x & 31) == 0) w_m[warp] = amax;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < nw; ++w) amax = w_m[w] > amax ? w_m[w] : amax;
+  __syncthreads();  // every part[] read before it is cleared
+  for (int b = threadIdx.x; b < 256 * 4; b += blockDim.x) part[b] = 0;
+  if (threadIdx.x == 0) {
+    st->amax_bits = amax;
+    st->E = 0;
+    st->prefix = 0;
+    st->tau_lo = st->tau_hi = 0;
+    st->T = 0;
+    st->k_tie = 0;
+    st->n_sub = 0;
+    const int none = amax == 0 || !(c_bound < 1.0);
+    st->all_out = none;
+    st->done = none;
+    st->blocks_done = 0;
   }
 }
 
@@ -411,13 +436,6 @@ __global__ void __launch_bounds__(1024) k_reduce_tail(const double* __restrict__
   }
 }
 
-__global__ void k_reduce_prepare(ReduceState* st, double c_bound) {
-  if (st->amax_bits == 0 || !(c_bound < 1.0)) {
-    // no circulation, or a bound of at least ||Gamma||_1: nothing diffuses
-    st->all_out = 1;
-    st->done = 1;
-  }
-}
 
 __global__ void k_reduce_mark(const double* __restrict__ g, int n, const int* __restrict__ n_dev,
                               const ReduceState* __restrict__ st, uint8_t* __restrict__ diffused,
@@ -451,9 +469,7 @@ cudaError_t reduce_select_dev(const double* gamma, int n_bound, const int* n_dev
                               cudaStream_t s) {
   int blocks = n_bound > 0 ? (n_bound + kBlock - 1) / kBlock : 1;
   int pblocks = blocks < 2 * sm_count() ? blocks : 2 * sm_count();
-  k_reduce_init<<<1, 256, 0, s>>>(st); note_launch();
-  k_absmax<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, ds); note_launch();
-  k_reduce_prepare<<<1, 1, 0, s>>>(st, c_bound); note_launch();
+  k_absmax<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, ds, c_bound); note_launch();
   for (int pass = 0; pass < 3; ++pass) {
     // pass 2 lists its matches in tie_rank (free until the tie scan)
     k_reduce_pass<<<pblocks, 256, 0, s>>>(gamma, n_bound, n_dev, st, c_bound, pass, tie_rank); note_launch();
