@@ -171,7 +171,8 @@ void free_scratch(Scratch& s) {
   RoundBufs& r = s.rb;
   void* ptrs[] = {s.grid, s.cell_key, s.cell_rank, s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc,
                   s.sorted_idx, s.bbox, s.scan_tmp, s.pos, s.rstate, s.tie_flag, s.tie_rank, s.diffused, s.dlist,
-                  s.mask, r.open, r.act0, r.act1, r.cnt, r.cpos, r.keep_flag, r.cx, r.cy, r.keep, r.apos,
+                  s.mask, r.open, r.act0, r.act1, r.cnt, r.cpos, r.cnt_ts, r.cell_ts, r.keep_ts, r.keep_flag, r.cx,
+                  r.cy, r.keep, r.apos,
                   r.cg.grid, r.cg.cell_key, r.cg.cell_rank, r.cg.cell_count, r.cg.cell_start, r.cg.sorted_idx,
                   r.cg.sorted_xy, r.cg.sorted_loc, r.cg.bbox, r.scan_tmp, s.nbr_count, s.nbr_idx, s.small, s.cols,
                   s.fail_list, s.retry_list, s.seg_mask, s.status, s.f, s.fii, s.tcount, s.toff, s.tplace, s.tent, s.ds,
@@ -422,6 +423,9 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(r.act1, n);
   VRM_ALLOC(r.cnt, n);
   VRM_ALLOC(r.cpos, (long)n + 1);
+  VRM_ALLOC(r.cnt_ts, (long)n / kScanTile + 2);
+  VRM_ALLOC(r.cell_ts, ncell / kScanTile + 2);
+  VRM_ALLOC(r.keep_ts, n8 / kScanTile + 2);
   VRM_ALLOC(r.keep_flag, n);
   VRM_ALLOC(r.cx, n8);
   VRM_ALLOC(r.cy, n8);
@@ -458,8 +462,10 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
 #undef VRM_ALLOC
   // the growth control's pass counter starts at 0 (every pass leaves it so)
   if (e == cudaSuccess) e = cudaMemsetAsync(s.rstate, 0, sizeof(ReduceState), st);
-  // the proposal cells start empty; every insertion round leaves them empty
+  // the proposal cells (and their tile sums) start empty; every insertion
+  // round leaves them empty
   if (e == cudaSuccess) e = cudaMemsetAsync(r.cg.cell_count, 0, sizeof(int) * (size_t)ncell, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(r.cell_ts, 0, sizeof(int) * (size_t)(ncell / kScanTile + 2), st);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_ds, sizeof(DevStats));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_counters, sizeof(int) * 8);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&s.h_grid, sizeof(Grid));

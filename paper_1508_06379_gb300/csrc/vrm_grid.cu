@@ -42,7 +42,7 @@ int persistent_blocks(int block_threads, int per_sm) {
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 4;
-constexpr int kScanTile = kScanThreads * kScanItems;
+static_assert(kScanThreads * kScanItems == kScanTile, "scan tile");
 
 size_t scan_tmp_ints(int n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 2; }
 
@@ -161,6 +161,20 @@ static cudaError_t scan_impl(const T* in, int* out, int n, const int* n_dev, int
   const int g = scan_grid(n);
   k_tile_sums<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp); note_launch();
   k_tile_scan_fused<T><<<g, kScanThreads, 0, s>>>(in, n, n_dev, tmp, out, total_out); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t scan_presummed_i32_dev(const int* in, int* out, int n_bound, const int* n_dev, const int* tile_sums,
+                                   cudaStream_t s, int* total_out) {
+  k_tile_scan_fused<int><<<scan_grid(n_bound), kScanThreads, 0, s>>>(in, n_bound, n_dev, tile_sums, out, total_out);
+  note_launch();
+  return cudaGetLastError();
+}
+cudaError_t scan_presummed_u8_dev(const uint8_t* in, int* out, int n_bound, const int* n_dev, const int* tile_sums,
+                                  cudaStream_t s) {
+  k_tile_scan_fused<uint8_t><<<scan_grid(n_bound), kScanThreads, 0, s>>>(in, n_bound, n_dev, tile_sums, out,
+                                                                          nullptr);
+  note_launch();
   return cudaGetLastError();
 }
 

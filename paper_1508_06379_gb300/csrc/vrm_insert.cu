@@ -62,18 +62,29 @@ __device__ __forceinline__ bool conflict_keep(const Consts& c, const Grid& g, co
   return true;
 }
 
-// keep[c] = conflict_keep of every proposal.
+// keep[c] = conflict_keep of every proposal, and the tile sums of keep
+// (keep_ts, 0 on entry) for the scan that numbers the accepted ones.
 __global__ void __launch_bounds__(kBlock) k_conflict(Consts c, const Grid* __restrict__ gp,
                                                      const int* __restrict__ cell_start,
                                                      const double2* __restrict__ sxy, const float2* __restrict__ sloc,
                                                      const int* __restrict__ sidx, const int* __restrict__ cell_key,
-                                                     const int* __restrict__ n_cand_dev, uint8_t* __restrict__ keep) {
+                                                     const int* __restrict__ n_cand_dev, uint8_t* __restrict__ keep,
+                                                     int* __restrict__ keep_ts) {
   const int n_cand = *n_cand_dev;
   const Grid g = *gp;
-  for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n_cand; p += (long)gridDim.x * blockDim.x) {
-    const int ci = sidx[p];
-    // the proposal's cell as binned (integer ops, no FP64)
-    keep[ci] = conflict_keep(c, g, cell_start, sxy, sloc, sidx, ci, cell_key[ci], p);
+  const int lane = threadIdx.x & 31;
+  for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_cand;
+       base += (long)gridDim.x * blockDim.x) {
+    const long p = base + lane;
+    int ci = -1;
+    bool ok = false;
+    if (p < n_cand) {
+      ci = sidx[p];
+      // the proposal's cell as binned (integer ops, no FP64)
+      ok = conflict_keep(c, g, cell_start, sxy, sloc, sidx, ci, cell_key[ci], p);
+      keep[ci] = ok;
+    }
+    tile_sum_add(keep_ts, ok ? ci : -1, 1);
   }
 }
 
@@ -187,13 +198,37 @@ __global__ void k_rounds_init(StepState* st, const int* __restrict__ n_open_src,
   if (graph) cudaGraphSetConditional(h, go);
 }
 
-// cnt[t] of the first round; every position is active.
-__global__ void k_cand_count_dev(const int* __restrict__ open, const int* __restrict__ n_open_src,
-                                 const uint8_t* __restrict__ mask, int* __restrict__ cnt, int* __restrict__ act0) {
+// cnt[t] of the first round (every position active) and its tile sums:
+// each block takes whole scan tiles.
+__global__ void __launch_bounds__(kBlock) k_cand_count_dev(const int* __restrict__ open,
+                                                           const int* __restrict__ n_open_src,
+                                                           const uint8_t* __restrict__ mask, int* __restrict__ cnt,
+                                                           int* __restrict__ act0, int* __restrict__ cnt_ts) {
+  static_assert(kScanTile % kBlock == 0, "a tile is whole block passes");
+  __shared__ int s_w[kBlock / 32];
   const int n_open = *n_open_src;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < n_open; t += (long)gridDim.x * blockDim.x) {
-    cnt[t] = __popc((~(unsigned)mask[open[t]]) & 0xFFu);
-    act0[t] = (int)t;
+  const int ntiles = (n_open + kScanTile - 1) / kScanTile;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanTile / kBlock; ++k) {
+      const long t = (long)tile * kScanTile + k * kBlock + threadIdx.x;
+      if (t < n_open) {
+        const int ct = __popc((~(unsigned)mask[open[t]]) & 0xFFu);
+        cnt[t] = ct;
+        act0[t] = (int)t;
+        sum += ct;
+      }
+    }
+    sum = __reduce_add_sync(0xffffffffu, sum);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < kBlock / 32; ++w) tot += s_w[w];
+      cnt_ts[tile] = tot;
+    }
+    __syncthreads();
   }
 }
 
@@ -208,7 +243,7 @@ __global__ void k_emit_bin(Consts c, const int* __restrict__ open, const StepSta
                            const uint8_t* __restrict__ mask, const int* __restrict__ cpos,
                            const double* __restrict__ x, const double* __restrict__ y, double* __restrict__ cx,
                            double* __restrict__ cy, const Grid* __restrict__ gp, int* __restrict__ cell_key,
-                           int* __restrict__ cell_rank, int* __restrict__ cell_count) {
+                           int* __restrict__ cell_rank, int* __restrict__ cell_count, int* __restrict__ cell_ts) {
   const int par = st->round & 1;
   const int* act = par ? act1 : act0;
   const int n_act = st->n_act[par];
@@ -251,6 +286,7 @@ __global__ void k_emit_bin(Consts c, const int* __restrict__ open, const StepSta
       const int excl_o = __shfl_sync(0xffffffffu, incl - cntl, owner);
       const int pos_o = __shfl_sync(0xffffffffu, pos0, owner);
       const double xo = __shfl_sync(0xffffffffu, xi, owner), yo = __shfl_sync(0xffffffffu, yi, owner);
+      int key = -1;
       if (q < total) {
         const int r = q - excl_o;  // the owner's r-th empty segment (from 0), ascending
         int sg = 0, seen = 0;
@@ -264,24 +300,30 @@ __global__ void k_emit_bin(Consts c, const int* __restrict__ open, const StepSta
         const double xp = __dadd_rn(xo, c.ins_dx[sg]), yp = __dadd_rn(yo, c.ins_dy[sg]);
         cx[pos] = xp;
         cy[pos] = yp;
-        const int key = grid_cell_y(g, yp) * g.nx + grid_cell_x(g, xp);
+        key = grid_cell_y(g, yp) * g.nx + grid_cell_x(g, xp);
         cell_key[pos] = key;
         cell_rank[pos] = atomicAdd(&cell_count[key], 1);
       }
+      tile_sum_add(cell_ts, key, 1);
     }
   }
 }
 
 // Proposals into cell order (sorted_xy, sorted_loc, sorted_idx), and their
-// cells' counts set back to 0.
+// cells' counts set back to 0; block 0 clears the cell tile sums (read by
+// the scan before) and the tile sums of keep (for the conflict test after).
 __global__ void k_cand_scatter(const double* __restrict__ cx, const double* __restrict__ cy,
                                const StepState* __restrict__ st, const Grid* __restrict__ gp,
                                const int* __restrict__ cell_key, const int* __restrict__ cell_rank,
                                const int* __restrict__ cell_start, int* __restrict__ cell_count,
                                double2* __restrict__ sorted_xy, float2* __restrict__ sorted_loc,
-                               int* __restrict__ sorted_idx) {
+                               int* __restrict__ sorted_idx, int* __restrict__ cell_ts, int* __restrict__ keep_ts) {
   const int n_cand = st->n_cand;
   const Grid g = *gp;
+  if (blockIdx.x == 0) {
+    for (int k = threadIdx.x; k <= g.ncell / kScanTile; k += blockDim.x) cell_ts[k] = 0;
+    for (int k = threadIdx.x; k <= n_cand / kScanTile; k += blockDim.x) keep_ts[k] = 0;
+  }
   for (long p = (long)blockIdx.x * blockDim.x + threadIdx.x; p < n_cand; p += (long)gridDim.x * blockDim.x) {
     const int key = cell_key[p];
     const int q = cell_start[key] + cell_rank[p];
@@ -316,8 +358,8 @@ __global__ void k_append_dev(const double* __restrict__ cx, const double* __rest
 __global__ void __launch_bounds__(kBlock) k_round_update(
     Consts c, const Grid* __restrict__ gp, const int* __restrict__ cell_start, const double2* __restrict__ sxy,
     const float2* __restrict__ sloc, const int* __restrict__ sidx, const uint8_t* __restrict__ keep,
-    const int* __restrict__ apos, const int* __restrict__ open, int* __restrict__ cnt, int* __restrict__ act0,
-    int* __restrict__ act1, PartCells pcells, StepState* __restrict__ st, const double* __restrict__ x,
+    const int* __restrict__ apos, const int* __restrict__ open, int* __restrict__ cnt, int* __restrict__ cnt_ts,
+    int* __restrict__ act0, int* __restrict__ act1, PartCells pcells, StepState* __restrict__ st, const double* __restrict__ x,
     const double* __restrict__ y, uint8_t* __restrict__ mask, cudaGraphConditionalHandle h, int graph) {
   const int n_cand = st->n_cand, n_cur = st->n_cur;
   const int a = apos[n_cand];
@@ -334,13 +376,16 @@ __global__ void __launch_bounds__(kBlock) k_round_update(
   for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n_act; base += stride) {
     const long k = base + lane;
     bool still = false;
-    int t = 0;
+    int t = 0, dc = 0;
     if (k < n_act) {
       t = act[k];
       const int i = open[t];
       still = mask_update_one(c, g, cell_start, sxy, sloc, sidx, keep, x, y, pcells, i, mask);
-      cnt[t] = still ? __popc((~(unsigned)mask[i]) & 0xFFu) : 0;
+      const int cn = still ? __popc((~(unsigned)mask[i]) & 0xFFu) : 0;
+      dc = cn - cnt[t];
+      cnt[t] = cn;
     }
+    tile_sum_add(cnt_ts, dc ? t : -1, dc);
     const unsigned sb = __ballot_sync(0xffffffffu, still);
     if (sb) {
       const int lead = __ffs(sb) - 1;
@@ -394,7 +439,10 @@ __global__ void k_rounds_finish(StepState* st, const int* __restrict__ cnt) {
 cudaError_t rounds_init(StepState* st, const int* n_open_src, const RoundBufs& rb, const uint8_t* mask, int cap,
                         cudaGraphConditionalHandle handle, bool graph, cudaStream_t s) {
   k_rounds_init<<<1, 1, 0, s>>>(st, n_open_src, handle, graph ? 1 : 0); note_launch();
-  k_cand_count_dev<<<blocks_for(cap), kBlock, 0, s>>>(rb.open, n_open_src, mask, rb.cnt, rb.act0); note_launch();
+  const int tiles = (cap + kScanTile - 1) / kScanTile;
+  k_cand_count_dev<<<tiles < 4 * sm_count() ? tiles : 4 * sm_count(), kBlock, 0, s>>>(rb.open, n_open_src, mask, rb.cnt,
+                                                                                    rb.act0, rb.cnt_ts);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -406,25 +454,29 @@ cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const 
   const int bc = blocks_for((int)(cand_cap < 0x7FFFFFFF ? cand_cap : 0x7FFFFFFF));
   const CandGrid& cg = rb.cg;
   const int* ncell_dev = reinterpret_cast<const int*>(reinterpret_cast<const char*>(pgrid) + offsetof(Grid, ncell));
-  cudaError_t e = scan_exclusive_i32_dev(rb.cnt, rb.cpos, cap, &st->n_list, rb.scan_tmp, s, &st->n_cand);
+  // the three scans of a round get their tile sums from the kernels that
+  // write their inputs (k_cand_count_dev / k_round_update, k_emit_bin,
+  // k_conflict)
+  cudaError_t e = scan_presummed_i32_dev(rb.cnt, rb.cpos, cap, &st->n_list, rb.cnt_ts, s, &st->n_cand);
   if (e != cudaSuccess) return e;
   k_emit_bin<<<bc, kBlock, 0, s>>>(c, rb.open, st, rb.act0, rb.act1, mask, rb.cpos, x, y, rb.cx, rb.cy, pgrid,
-                                   cg.cell_key, cg.cell_rank, cg.cell_count);
+                                   cg.cell_key, cg.cell_rank, cg.cell_count, rb.cell_ts);
   note_launch();
-  e = scan_exclusive_i32_dev(cg.cell_count, cg.cell_start, rb.ncell_cap, ncell_dev, rb.scan_tmp, s);
+  e = scan_presummed_i32_dev(cg.cell_count, cg.cell_start, rb.ncell_cap, ncell_dev, rb.cell_ts, s);
   if (e != cudaSuccess) return e;
   k_cand_scatter<<<bc, kBlock, 0, s>>>(rb.cx, rb.cy, st, pgrid, cg.cell_key, cg.cell_rank, cg.cell_start,
-                                       cg.cell_count, cg.sorted_xy, cg.sorted_loc, cg.sorted_idx);
+                                       cg.cell_count, cg.sorted_xy, cg.sorted_loc, cg.sorted_idx, rb.cell_ts,
+                                       rb.keep_ts);
   note_launch();
   k_conflict<<<bc, kBlock, 0, s>>>(c, pgrid, cg.cell_start, cg.sorted_xy, cg.sorted_loc, cg.sorted_idx, cg.cell_key,
-                                   &st->n_cand, rb.keep);
+                                   &st->n_cand, rb.keep, rb.keep_ts);
   note_launch();
-  e = scan_exclusive_u8_dev(rb.keep, rb.apos, (int)cand_cap, &st->n_cand, rb.scan_tmp, s);
+  e = scan_presummed_u8_dev(rb.keep, rb.apos, (int)cand_cap, &st->n_cand, rb.keep_ts, s);
   if (e != cudaSuccess) return e;
   k_append_dev<<<bc, kBlock, 0, s>>>(rb.cx, rb.cy, rb.keep, rb.apos, st, x, y); note_launch();
   k_round_update<<<bo, kBlock, 0, s>>>(c, pgrid, cg.cell_start, cg.sorted_xy, cg.sorted_loc, cg.sorted_idx, rb.keep,
-                                       rb.apos, rb.open, rb.cnt, rb.act0, rb.act1, pcells, st, x, y, mask, handle,
-                                       graph ? 1 : 0);
+                                       rb.apos, rb.open, rb.cnt, rb.cnt_ts, rb.act0, rb.act1, pcells, st, x, y, mask,
+                                       handle, graph ? 1 : 0);
   note_launch();
   return cudaGetLastError();
 }

@@ -227,6 +227,27 @@ cudaError_t grid_extend_dev(const double* x, const double* y, int n_bound, const
                             int ncell_cap, const Grid* g, int* cell_key, int* cell_rank, int* cell_count,
                             int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx, int* scan_tmp,
                             cudaStream_t s);
+// Scans work on tiles of kScanTile elements.  A kernel that produces the
+// input can accumulate the tiles' sums itself (tile_sum_add); the scan then
+// skips its first pass (scan_presummed_*).
+constexpr int kScanTileLog = 10;
+constexpr int kScanTile = 1 << kScanTileLog;
+// tsum[idx >> kScanTileLog] += v with one atomic per distinct tile of the
+// warp.  Every lane of the warp must call it; a lane without a value passes
+// idx < 0 or v = 0.
+__device__ __forceinline__ void tile_sum_add(int* tsum, long idx, int v) {
+  const int tile = (idx >= 0 && v != 0) ? (int)(idx >> kScanTileLog) : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, tile);
+  const int sum = __reduce_add_sync(peers, v);
+  if (tile >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&tsum[tile], sum);
+}
+// Exclusive scan of *n_dev (<= n_bound) ints or bytes whose tile sums are
+// already in tile_sums (ceil(n / kScanTile) of them): out[0..n], out[n] =
+// total (also written to total_out when given).  One launch.
+cudaError_t scan_presummed_i32_dev(const int* in, int* out, int n_bound, const int* n_dev, const int* tile_sums,
+                                   cudaStream_t s, int* total_out = nullptr);
+cudaError_t scan_presummed_u8_dev(const uint8_t* in, int* out, int n_bound, const int* n_dev, const int* tile_sums,
+                                  cudaStream_t s);
 // Exclusive scan of n ints into out[0..n] (out[n] = total).
 cudaError_t scan_exclusive_i32(const int* in, int* out, int n, int* tmp, cudaStream_t s);
 // Scans and compaction with the count in device memory (*n_dev <= n_bound).
@@ -292,6 +313,9 @@ struct RoundBufs {
   int* act0;           // open-list positions still open in the round, unordered (cap):
   int* act1;           // act0 for even rounds, act1 for odd ones
   int *cnt, *cpos;     // proposals per open particle and their offsets (cap, cap+1)
+  int* cnt_ts;         // tile sums of cnt (kept up to date by the round kernels)
+  int* cell_ts;        // tile sums of the proposal cell counts (0 between rounds)
+  int* keep_ts;        // tile sums of keep (0 before each conflict test)
   uint8_t *keep_flag;  // open particle still open (cap)
   double *cx, *cy;     // proposals (8 cap)
   uint8_t* keep;       // proposal accepted (8 cap)
