@@ -48,6 +48,9 @@ struct vrm::Scratch {
   ReduceState* rstate = nullptr;
   uint8_t* tie_flag = nullptr;
   int* tie_rank = nullptr;
+  // tile sums of the scans whose inputs the kernels before them accumulate:
+  // the diffused flags, the tie flags, the particle grid's cell counts
+  int *dflag_ts = nullptr, *tie_ts = nullptr, *cell_ts = nullptr;
   uint8_t* diffused = nullptr;
   int* dlist = nullptr;
   // insertion: masks and the round buffers (proposals up to 8 per open particle)
@@ -170,7 +173,8 @@ void drop_graph(vrm_ctx* ctx) {
 void free_scratch(Scratch& s) {
   RoundBufs& r = s.rb;
   void* ptrs[] = {s.grid, s.cell_key, s.cell_rank, s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc,
-                  s.sorted_idx, s.bbox, s.scan_tmp, s.pos, s.rstate, s.tie_flag, s.tie_rank, s.diffused, s.dlist,
+                  s.sorted_idx, s.bbox, s.scan_tmp, s.pos, s.rstate, s.tie_flag, s.tie_rank, s.dflag_ts, s.tie_ts,
+                  s.cell_ts, s.diffused, s.dlist,
                   s.mask, r.open, r.act0, r.act1, r.cnt, r.cpos, r.cnt_ts, r.cell_ts, r.keep_ts, r.keep_flag, r.cx,
                   r.cy, r.keep, r.apos,
                   r.cg.grid, r.cg.cell_key, r.cg.cell_rank, r.cg.cell_count, r.cg.cell_start, r.cg.sorted_idx,
@@ -353,7 +357,7 @@ cudaError_t enqueue_stage_weights(vrm_ctx* ctx, const double* x, const double* y
   if ((e = cudaMemsetAsync(&s.ds->n_fail, 0, sizeof(int), st)) != cudaSuccess) return e;
   if ((e = grid_build_dev(x, y, cap, n_cur, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank,
                           s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
-                          st)) != cudaSuccess)
+                          st, s.cell_ts)) != cudaSuccess)
     return e;
   // rows of the diffused particles only (the LPs and the learned slots read
   // no other row; the application goes through the transposed stencils), in
@@ -415,6 +419,9 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.rstate, 1);
   VRM_ALLOC(s.tie_flag, n);
   VRM_ALLOC(s.tie_rank, (long)n + 1);
+  VRM_ALLOC(s.dflag_ts, (long)n / kScanTile + 2);
+  VRM_ALLOC(s.tie_ts, (long)n / kScanTile + 2);
+  VRM_ALLOC(s.cell_ts, ncell / kScanTile + 2);
   VRM_ALLOC(s.diffused, n);
   VRM_ALLOC(s.dlist, n);
   VRM_ALLOC(s.mask, n);
@@ -597,11 +604,6 @@ cudaError_t mark(vrm_ctx* ctx, int k, cudaStream_t st) {
   return cudaEventRecord(ctx->ev[k], st);
 }
 
-__global__ void k_clear_tail(uint8_t* __restrict__ a, const StepState* __restrict__ st, int cap) {
-  const int n = st->n;
-  for (long i = (long)n + blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (long)gridDim.x * blockDim.x) a[i] = 0;
-}
-
 // Growth control, grid of the given cloud, segment masks, first open list
 // (the rounds follow).  n is read from s.st->n.
 cudaError_t enqueue_front(vrm_ctx* ctx, double* x, double* y, int cap, const double* gamma, uint8_t* diffused,
@@ -612,21 +614,21 @@ cudaError_t enqueue_front(vrm_ctx* ctx, double* x, double* y, int cap, const dou
   cudaError_t e;
   if ((e = mark(ctx, VRM_STAGE_REDUCE, st)) != cudaSuccess) return e;
   if ((e = reduce_select_dev(gamma, cap, n_dev, c.c_bound, diffused, s.rstate, s.tie_flag, s.tie_rank, s.scan_tmp,
-                             s.ds, st)) != cudaSuccess)
+                             s.ds, st, s.dflag_ts, s.tie_ts)) != cudaSuccess)
     return e;
-  k_clear_tail<<<4 * sm_count(), kBlock, 0, st>>>(diffused, s.st, cap); note_launch();
-  if ((e = compact_flags_dev(diffused, cap, n_dev, s.dlist, s.counters + 0, s.pos, s.scan_tmp, st)) != cudaSuccess)
+  if ((e = compact_flags_dev(diffused, cap, n_dev, s.dlist, s.counters + 0, s.pos, s.scan_tmp, st, s.dflag_ts)) !=
+      cudaSuccess)
     return e;
   if ((e = mark(ctx, VRM_STAGE_GRID, st)) != cudaSuccess) return e;
   if ((e = grid_build_dev(x, y, cap, n_dev, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank,
                           s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
-                          st)) != cudaSuccess)
+                          st, s.cell_ts)) != cudaSuccess)
     return e;
   if ((e = search_masks_list_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.cell_key,
                                  s.cell_rank, s.dlist, s.counters + 0, cap, s.mask, st)) != cudaSuccess)
     return e;
   if ((e = open_list(s.dlist, s.counters + 0, cap, s.mask, s.rb.keep_flag, s.pos, s.rb.open, s.counters + 1,
-                     s.scan_tmp, st)) != cudaSuccess)
+                     s.rb.keep_ts, st)) != cudaSuccess)
     return e;
   return mark(ctx, VRM_STAGE_INSERT, st);
 }
@@ -643,7 +645,8 @@ cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const doub
   // the grid of the given particles (enqueue_front) extended by the inserted
   // ones, with its geometry kept
   if ((e = grid_extend_dev(x, y, cap, &s.st->n, n_cur, s.ncell_cap, s.grid, s.cell_key, s.cell_rank, s.cell_count,
-                           s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.scan_tmp, st)) != cudaSuccess)
+                           s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.scan_tmp, st, s.cell_ts)) !=
+      cudaSuccess)
     return e;
   // rows of the diffused particles only (the LPs and the learned slots read
   // no other row; the application goes through the transposed stencils), in

@@ -315,16 +315,33 @@ __global__ void k_grid_finalize(const unsigned long long* __restrict__ bb, int n
   *g = G;
 }
 
+// Keys and ranks of particles [n0, n1); with cell_ts the scan's tile sums
+// of the cell counts are accumulated too.  Whole warps step through the
+// particles (tile_sum_add needs every lane).
+__device__ __forceinline__ void bin_range(const double* __restrict__ x, const double* __restrict__ y, long n0,
+                                          long n1, const Grid& g, int* __restrict__ cell_key,
+                                          int* __restrict__ cell_rank, int* __restrict__ cell_count,
+                                          int* __restrict__ cell_ts) {
+  const int lane = threadIdx.x & 31;
+  for (long base = n0 + (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n1;
+       base += (long)gridDim.x * blockDim.x) {
+    const long i = base + lane;
+    int key = -1;
+    if (i < n1) {
+      key = grid_cell_y(g, y[i]) * g.nx + grid_cell_x(g, x[i]);
+      cell_key[i] = key;
+      cell_rank[i] = atomicAdd(&cell_count[key], 1);
+    }
+    if (cell_ts) tile_sum_add(cell_ts, key, 1);
+  }
+}
+
 __global__ void k_bin(const double* __restrict__ x, const double* __restrict__ y, int n, const int* __restrict__ n_dev,
                       const Grid* __restrict__ gp, int* __restrict__ cell_key, int* __restrict__ cell_rank,
-                      int* __restrict__ cell_count) {
+                      int* __restrict__ cell_count, int* __restrict__ cell_ts) {
   if (n_dev) n = *n_dev;
   const Grid g = *gp;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    int key = grid_cell_y(g, y[i]) * g.nx + grid_cell_x(g, x[i]);
-    cell_key[i] = key;
-    cell_rank[i] = atomicAdd(&cell_count[key], 1);
-  }
+  bin_range(x, y, 0, n, g, cell_key, cell_rank, cell_count, cell_ts);
 }
 
 __global__ void k_scatter(const double* __restrict__ x, const double* __restrict__ y, int n,
@@ -353,33 +370,37 @@ static int stream_grid(int n_bound, int per_sm) {
 cudaError_t grid_build_dev(const double* x, const double* y, int n_bound, const int* n_dev, double Rh, double lo2,
                            double hi2, int ncell_cap, Grid* g, int* cell_key, int* cell_rank, int* cell_count,
                            int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx,
-                           unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s) {
+                           unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s, int* cell_ts) {
   k_bbox_init<<<1, 1, 0, s>>>(bbox_tmp); note_launch();
   k_bbox<<<stream_grid(n_bound, 4), kBlock, 0, s>>>(x, y, n_bound, n_dev, bbox_tmp); note_launch();
   k_grid_finalize<<<1, 1, 0, s>>>(bbox_tmp, n_bound, n_dev, Rh, lo2, hi2, ncell_cap, g); note_launch();
   return grid_bin_dev(x, y, n_bound, n_dev, ncell_cap, g, cell_key, cell_rank, cell_count, cell_start, sorted_xy,
-                      sorted_loc, sorted_idx, scan_tmp, s);
+                      sorted_loc, sorted_idx, scan_tmp, s, cell_ts);
 }
 
 // Zeroes the counts of the grid's own cells (g->ncell of them, at most the
-// capacity the buffers were sized for).
-__global__ void k_zero_cells(const Grid* __restrict__ g, int* __restrict__ cell_count) {
+// capacity the buffers were sized for) and, when given, their tile sums.
+__global__ void k_zero_cells(const Grid* __restrict__ g, int* __restrict__ cell_count, int* __restrict__ cell_ts) {
   const int m = g->ncell;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x)
     cell_count[t] = 0;
+  if (cell_ts)
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t <= m / kScanTile; t += (long)gridDim.x * blockDim.x)
+      cell_ts[t] = 0;
 }
 
 cudaError_t grid_bin_dev(const double* x, const double* y, int n_bound, const int* n_dev, int ncell_cap, const Grid* g,
                          int* cell_key, int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy,
-                         float2* sorted_loc, int* sorted_idx, int* scan_tmp, cudaStream_t s) {
+                         float2* sorted_loc, int* sorted_idx, int* scan_tmp, cudaStream_t s, int* cell_ts) {
   // only the grid's own cells (g->ncell, known on the device) are counted
   // and scanned, not the whole capacity: a cloud of spacing h has about
   // (extent / 2h)^2 cells, far fewer than the capacity's 2 per particle
   const int* ncell_dev = reinterpret_cast<const int*>(reinterpret_cast<const char*>(g) + offsetof(Grid, ncell));
-  k_zero_cells<<<stream_grid(ncell_cap, 4), kBlock, 0, s>>>(g, cell_count); note_launch();
+  k_zero_cells<<<stream_grid(ncell_cap, 4), kBlock, 0, s>>>(g, cell_count, cell_ts); note_launch();
   const int b = stream_grid(n_bound, 8);
-  k_bin<<<b, kBlock, 0, s>>>(x, y, n_bound, n_dev, g, cell_key, cell_rank, cell_count); note_launch();
-  cudaError_t e = scan_exclusive_i32_dev(cell_count, cell_start, ncell_cap, ncell_dev, scan_tmp, s);
+  k_bin<<<b, kBlock, 0, s>>>(x, y, n_bound, n_dev, g, cell_key, cell_rank, cell_count, cell_ts); note_launch();
+  cudaError_t e = cell_ts ? scan_presummed_i32_dev(cell_count, cell_start, ncell_cap, ncell_dev, cell_ts, s)
+                          : scan_exclusive_i32_dev(cell_count, cell_start, ncell_cap, ncell_dev, scan_tmp, s);
   if (e != cudaSuccess) return e;
   k_scatter<<<b, kBlock, 0, s>>>(x, y, n_bound, n_dev, g, cell_key, cell_rank, cell_start, sorted_xy, sorted_loc,
                                  sorted_idx);
@@ -392,24 +413,20 @@ cudaError_t grid_bin_dev(const double* x, const double* y, int n_bound, const in
 __global__ void k_bin_range(const double* __restrict__ x, const double* __restrict__ y,
                             const int* __restrict__ n0_dev, const int* __restrict__ n1_dev,
                             const Grid* __restrict__ gp, int* __restrict__ cell_key, int* __restrict__ cell_rank,
-                            int* __restrict__ cell_count) {
-  const int n0 = *n0_dev, n1 = *n1_dev;
+                            int* __restrict__ cell_count, int* __restrict__ cell_ts) {
   const Grid g = *gp;
-  for (long i = n0 + (long)blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += (long)gridDim.x * blockDim.x) {
-    const int key = grid_cell_y(g, y[i]) * g.nx + grid_cell_x(g, x[i]);
-    cell_key[i] = key;
-    cell_rank[i] = atomicAdd(&cell_count[key], 1);
-  }
+  bin_range(x, y, *n0_dev, *n1_dev, g, cell_key, cell_rank, cell_count, cell_ts);
 }
 
 cudaError_t grid_extend_dev(const double* x, const double* y, int n_bound, const int* n0_dev, const int* n1_dev,
                             int ncell_cap, const Grid* g, int* cell_key, int* cell_rank, int* cell_count,
                             int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx, int* scan_tmp,
-                            cudaStream_t s) {
+                            cudaStream_t s, int* cell_ts) {
   const int* ncell_dev = reinterpret_cast<const int*>(reinterpret_cast<const char*>(g) + offsetof(Grid, ncell));
   const int b = stream_grid(n_bound, 8);
-  k_bin_range<<<b, kBlock, 0, s>>>(x, y, n0_dev, n1_dev, g, cell_key, cell_rank, cell_count); note_launch();
-  cudaError_t e = scan_exclusive_i32_dev(cell_count, cell_start, ncell_cap, ncell_dev, scan_tmp, s);
+  k_bin_range<<<b, kBlock, 0, s>>>(x, y, n0_dev, n1_dev, g, cell_key, cell_rank, cell_count, cell_ts); note_launch();
+  cudaError_t e = cell_ts ? scan_presummed_i32_dev(cell_count, cell_start, ncell_cap, ncell_dev, cell_ts, s)
+                          : scan_exclusive_i32_dev(cell_count, cell_start, ncell_cap, ncell_dev, scan_tmp, s);
   if (e != cudaSuccess) return e;
   k_scatter<<<b, kBlock, 0, s>>>(x, y, n_bound, n1_dev, g, cell_key, cell_rank, cell_start, sorted_xy, sorted_loc,
                                  sorted_idx);
@@ -435,8 +452,9 @@ __global__ void k_compact_dev(const uint8_t* __restrict__ flags, int n, const in
 }
 
 cudaError_t compact_flags_dev(const uint8_t* flags, int n_bound, const int* n_dev, int* list, int* count, int* pos,
-                              int* tmp, cudaStream_t s) {
-  cudaError_t e = scan_exclusive_u8_dev(flags, pos, n_bound, n_dev, tmp, s);
+                              int* tmp, cudaStream_t s, const int* flag_ts) {
+  cudaError_t e = flag_ts ? scan_presummed_u8_dev(flags, pos, n_bound, n_dev, flag_ts, s)
+                          : scan_exclusive_u8_dev(flags, pos, n_bound, n_dev, tmp, s);
   if (e != cudaSuccess) return e;
   k_compact_dev<<<stream_grid(n_bound, 8), kBlock, 0, s>>>(flags, n_bound, n_dev, pos, list, count); note_launch();
   return cudaGetLastError();

@@ -145,21 +145,47 @@ __global__ void k_compact_list(const int* __restrict__ list, const uint8_t* __re
   if (blockIdx.x == 0 && threadIdx.x == 0) *count = pos[m];
 }
 
-// Open list of round 1: diffused particles whose mask is not full.
-__global__ void k_open_flags(const int* __restrict__ list, const int* __restrict__ list_count,
-                             const uint8_t* __restrict__ mask, uint8_t* __restrict__ flag, int cap) {
+// Open list of round 1: diffused particles whose mask is not full.  Each
+// block takes whole scan tiles of the diffused list and writes their sums.
+__global__ void __launch_bounds__(kBlock) k_open_flags(const int* __restrict__ list,
+                                                       const int* __restrict__ list_count,
+                                                       const uint8_t* __restrict__ mask, uint8_t* __restrict__ flag,
+                                                       int* __restrict__ flag_ts) {
+  static_assert(kScanTile % kBlock == 0, "a tile is whole block passes");
+  __shared__ int s_w[kBlock / 32];
   const int m = *list_count;
-  for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < cap; t += (long)gridDim.x * blockDim.x)
-    flag[t] = t < m ? (mask[list[t]] != 0xFFu) : 0;
+  const int ntiles = (m + kScanTile - 1) / kScanTile;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanTile / kBlock; ++k) {
+      const long t = (long)tile * kScanTile + k * kBlock + threadIdx.x;
+      if (t < m) {
+        const uint8_t f = mask[list[t]] != 0xFFu;
+        flag[t] = f;
+        sum += f;
+      }
+    }
+    sum = __reduce_add_sync(0xffffffffu, sum);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int tot = 0;
+      for (int w = 0; w < kBlock / 32; ++w) tot += s_w[w];
+      flag_ts[tile] = tot;
+    }
+    __syncthreads();
+  }
 }
 
 cudaError_t open_list(const int* dlist, const int* dcount, int cap, const uint8_t* mask, uint8_t* flag, int* pos,
-                      int* open, int* n_open, int* scan_tmp, cudaStream_t s) {
-  int b = blocks_for(cap);
-  k_open_flags<<<b, kBlock, 0, s>>>(dlist, dcount, mask, flag, cap); note_launch();
-  cudaError_t e = scan_exclusive_u8(flag, pos, cap, scan_tmp, s);
+                      int* open, int* n_open, int* flag_ts, cudaStream_t s) {
+  const int tiles = (cap + kScanTile - 1) / kScanTile;
+  k_open_flags<<<tiles < 4 * sm_count() ? tiles : 4 * sm_count(), kBlock, 0, s>>>(dlist, dcount, mask, flag, flag_ts);
+  note_launch();
+  cudaError_t e = scan_presummed_u8_dev(flag, pos, cap, dcount, flag_ts, s);
   if (e != cudaSuccess) return e;
-  k_compact_list<<<b, kBlock, 0, s>>>(dlist, flag, pos, cap, nullptr, open, n_open); note_launch();
+  k_compact_list<<<blocks_for(cap), kBlock, 0, s>>>(dlist, flag, pos, cap, dcount, open, n_open); note_launch();
   return cudaGetLastError();
 }
 

@@ -214,10 +214,13 @@ cudaError_t grid_build(const double* x, const double* y, int n, double Rh, doubl
 cudaError_t grid_build_dev(const double* x, const double* y, int n_bound, const int* n_dev, double Rh, double lo2,
                            double hi2, int ncell_cap, Grid* g, int* cell_key, int* cell_rank, int* cell_count,
                            int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx,
-                           unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s);
+                           unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s, int* cell_ts = nullptr);
+// cell_ts (optional, ncell_cap / kScanTile + 2 ints): the binning kernel
+// accumulates the tile sums of the cell counts there, and the scan of the
+// counts is one launch.
 cudaError_t grid_bin_dev(const double* x, const double* y, int n_bound, const int* n_dev, int ncell_cap, const Grid* g,
                          int* cell_key, int* cell_rank, int* cell_count, int* cell_start, double2* sorted_xy,
-                         float2* sorted_loc, int* sorted_idx, int* scan_tmp, cudaStream_t s);
+                         float2* sorted_loc, int* sorted_idx, int* scan_tmp, cudaStream_t s, int* cell_ts = nullptr);
 // Grid g, built over [0, *n0_dev), extended to [0, *n1_dev) with the same
 // geometry: the new particles are binned onto the existing counts (points
 // outside the grid clamp into its edge cells; cells are >= R h, so the 3 x 3
@@ -226,7 +229,7 @@ cudaError_t grid_bin_dev(const double* x, const double* y, int n_bound, const in
 cudaError_t grid_extend_dev(const double* x, const double* y, int n_bound, const int* n0_dev, const int* n1_dev,
                             int ncell_cap, const Grid* g, int* cell_key, int* cell_rank, int* cell_count,
                             int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx, int* scan_tmp,
-                            cudaStream_t s);
+                            cudaStream_t s, int* cell_ts = nullptr);
 // Scans work on tiles of kScanTile elements.  A kernel that produces the
 // input can accumulate the tiles' sums itself (tile_sum_add); the scan then
 // skips its first pass (scan_presummed_*).
@@ -256,8 +259,10 @@ cudaError_t scan_exclusive_i32_dev(const int* in, int* out, int n_bound, const i
                                    int* total_out = nullptr);
 cudaError_t scan_exclusive_u8_dev(const uint8_t* in, int* out, int n_bound, const int* n_dev, int* tmp,
                                   cudaStream_t s);
+// flag_ts (optional): the flags' tile sums, already accumulated by their
+// producer (the scan is then one launch).
 cudaError_t compact_flags_dev(const uint8_t* flags, int n_bound, const int* n_dev, int* list, int* count, int* pos,
-                              int* tmp, cudaStream_t s);
+                              int* tmp, cudaStream_t s, const int* flag_ts = nullptr);
 // Exclusive scan of n bytes (0/1) into out[0..n].
 cudaError_t scan_exclusive_u8(const uint8_t* in, int* out, int n, int* tmp, cudaStream_t s);
 // list[k] = the k-th index with flag set (ascending); count written to *count
@@ -266,11 +271,12 @@ cudaError_t compact_flags(const uint8_t* flags, int n, int* list, int* count, in
 size_t scan_tmp_ints(int n);
 
 // vrm_reduce.cu
-cudaError_t reduce_select(const double* gamma, int n, double c_bound, uint8_t* diffused, ReduceState* st,
-                          uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds, cudaStream_t s);
+// Growth control over *n_dev (<= n_bound) particles: diffused[i] for i < n,
+// 0 on [n, n_bound).  dflag_ts and tie_ts (n_bound / kScanTile + 2 ints
+// each) receive the tile sums of diffused and of the tie flags.
 cudaError_t reduce_select_dev(const double* gamma, int n_bound, const int* n_dev, double c_bound, uint8_t* diffused,
                               ReduceState* st, uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds,
-                              cudaStream_t s);
+                              cudaStream_t s, int* dflag_ts, int* tie_ts);
 
 // vrm_search.cu
 cudaError_t search_all(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
@@ -305,7 +311,7 @@ struct CandGrid {
 // Open list of round 1: the diffused particles (dlist, ascending) whose
 // segment mask is not full; open[] ascending, *n_open on the device.
 cudaError_t open_list(const int* dlist, const int* dcount, int cap, const uint8_t* mask, uint8_t* flag, int* pos,
-                      int* open, int* n_open, int* scan_tmp, cudaStream_t s);
+                      int* open, int* n_open, int* flag_ts, cudaStream_t s);
 
 // Buffers of the device-resident insertion rounds (proposal capacity 8 n).
 struct RoundBufs {

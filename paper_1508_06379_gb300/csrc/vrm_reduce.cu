@@ -437,36 +437,84 @@ __global__ void __launch_bounds__(1024) k_reduce_tail(const double* __restrict__
 }
 
 
-__global__ void k_reduce_mark(const double* __restrict__ g, int n, const int* __restrict__ n_dev,
-                              const ReduceState* __restrict__ st, uint8_t* __restrict__ diffused,
-                              uint8_t* __restrict__ tie_flag) {
-  if (n_dev) n = *n_dev;
+// diffused[i] = key > T, tie_flag[i] = key == T for i < n (both 0 when
+// every particle stays out), diffused[i] = 0 for n <= i < n_bound; each block
+// takes whole scan tiles and writes their sums of both flags (the tie scan
+// and the diffused list's scan then skip their first pass).
+__global__ void __launch_bounds__(kBlock) k_reduce_mark(const double* __restrict__ g, int n_bound,
+                                                        const int* __restrict__ n_dev,
+                                                        const ReduceState* __restrict__ st,
+                                                        uint8_t* __restrict__ diffused, uint8_t* __restrict__ tie_flag,
+                                                        int* __restrict__ dflag_ts, int* __restrict__ tie_ts) {
+  static_assert(kScanTile % kBlock == 0, "a tile is whole block passes");
+  __shared__ int s_d[kBlock / 32], s_t[kBlock / 32];
+  const int n = n_dev ? *n_dev : n_bound;
   const int all_out = st->all_out;
   const unsigned long long T = st->T;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const unsigned long long key = (unsigned long long)__double_as_longlong(g[i]) & 0x7FFFFFFFFFFFFFFFull;
-    uint8_t d = 0, t = 0;
-    if (!all_out) {
-      d = key > T;
-      t = key == T;
+  const int ntiles = (n_bound + kScanTile - 1) / kScanTile;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int sd = 0, stie = 0;
+#pragma unroll
+    for (int k = 0; k < kScanTile / kBlock; ++k) {
+      const long i = (long)tile * kScanTile + k * kBlock + threadIdx.x;
+      if (i < n) {
+        const unsigned long long key = (unsigned long long)__double_as_longlong(g[i]) & 0x7FFFFFFFFFFFFFFFull;
+        uint8_t d = 0, t = 0;
+        if (!all_out) {
+          d = key > T;
+          t = key == T;
+        }
+        diffused[i] = d;
+        tie_flag[i] = t;
+        sd += d;
+        stie += t;
+      } else if (i < n_bound) {
+        diffused[i] = 0;
+      }
     }
-    diffused[i] = d;
-    tie_flag[i] = t;
+    sd = __reduce_add_sync(0xffffffffu, sd);
+    stie = __reduce_add_sync(0xffffffffu, stie);
+    if ((threadIdx.x & 31) == 0) {
+      s_d[threadIdx.x >> 5] = sd;
+      s_t[threadIdx.x >> 5] = stie;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int a = 0, b = 0;
+      for (int w = 0; w < kBlock / 32; ++w) {
+        a += s_d[w];
+        b += s_t[w];
+      }
+      dflag_ts[tile] = a;
+      tie_ts[tile] = b;
+    }
+    __syncthreads();
   }
 }
 
+// The ties that diffuse (rank >= k_tie), added to the diffused flags and
+// their tile sums.
 __global__ void k_reduce_ties(int n, const int* __restrict__ n_dev, const ReduceState* __restrict__ st,
                               const uint8_t* __restrict__ tie_flag, const int* __restrict__ tie_rank,
-                              uint8_t* __restrict__ diffused) {
+                              uint8_t* __restrict__ diffused, int* __restrict__ dflag_ts) {
   if (n_dev) n = *n_dev;
   const int k_tie = st->k_tie;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    if (tie_flag[i] && tie_rank[i] >= k_tie) diffused[i] = 1;
+  const int lane = threadIdx.x & 31;
+  for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+       base += (long)gridDim.x * blockDim.x) {
+    const long i = base + lane;
+    bool up = false;
+    if (i < n && tie_flag[i] && tie_rank[i] >= k_tie) {
+      diffused[i] = 1;
+      up = true;
+    }
+    tile_sum_add(dflag_ts, up ? i : -1, 1);
+  }
 }
 
 cudaError_t reduce_select_dev(const double* gamma, int n_bound, const int* n_dev, double c_bound, uint8_t* diffused,
                               ReduceState* st, uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds,
-                              cudaStream_t s) {
+                              cudaStream_t s, int* dflag_ts, int* tie_ts) {
   int blocks = n_bound > 0 ? (n_bound + kBlock - 1) / kBlock : 1;
   int pblocks = blocks < 2 * sm_count() ? blocks : 2 * sm_count();
   k_absmax<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, ds, c_bound); note_launch();
@@ -475,16 +523,13 @@ cudaError_t reduce_select_dev(const double* gamma, int n_bound, const int* n_dev
     k_reduce_pass<<<pblocks, 256, 0, s>>>(gamma, n_bound, n_dev, st, c_bound, pass, tie_rank); note_launch();
   }
   k_reduce_tail<<<1, 1024, 0, s>>>(gamma, st, tie_rank); note_launch();
-  k_reduce_mark<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, diffused, tie_flag); note_launch();
-  cudaError_t e = scan_exclusive_u8_dev(tie_flag, tie_rank, n_bound, n_dev, scan_tmp, s);
+  k_reduce_mark<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, diffused, tie_flag, dflag_ts, tie_ts);
+  note_launch();
+  cudaError_t e = scan_presummed_u8_dev(tie_flag, tie_rank, n_bound, n_dev, tie_ts, s);
   if (e != cudaSuccess) return e;
-  k_reduce_ties<<<pblocks, kBlock, 0, s>>>(n_bound, n_dev, st, tie_flag, tie_rank, diffused); note_launch();
+  k_reduce_ties<<<pblocks, kBlock, 0, s>>>(n_bound, n_dev, st, tie_flag, tie_rank, diffused, dflag_ts);
+  note_launch();
   return cudaGetLastError();
-}
-
-cudaError_t reduce_select(const double* gamma, int n, double c_bound, uint8_t* diffused, ReduceState* st,
-                          uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds, cudaStream_t s) {
-  return reduce_select_dev(gamma, n, nullptr, c_bound, diffused, st, tie_flag, tie_rank, scan_tmp, ds, s);
 }
 
 }  // namespace vrm
