@@ -357,15 +357,18 @@ cudaError_t enqueue_stage_weights(vrm_ctx* ctx, const double* x, const double* y
   if ((e = cudaMemsetAsync(&s.ds->n_fail, 0, sizeof(int), st)) != cudaSuccess) return e;
   if ((e = grid_build_dev(x, y, cap, n_cur, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank,
                           s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
-                          st, s.cell_ts)) != cudaSuccess)
+                          st, s.cell_ts, true)) != cudaSuccess)
     return e;
-  // rows of the diffused particles only (the LPs and the learned slots read
-  // no other row; the application goes through the transposed stencils), in
-  // visiting order (the learned slots and the full-neighbourhood LP order
-  // their entries themselves)
+  // counts, masks and small neighbourhoods of the diffused particles (the
+  // LPs read no other particle's); their rows only where the learned slots
+  // read them (the full-neighbourhood LP's few particles get theirs below;
+  // the application goes through the transposed stencils), in visiting order
+  // (the learned slots and the full-neighbourhood LP order their entries
+  // themselves)
+  const bool rows = ctx->mlp != nullptr;
   if ((e = search_list_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.cell_key, s.cell_rank,
-                           s.dlist, s.counters + 0, cap, s.nbr_count, s.nbr_idx, s.seg_mask, s.small, s.ds, st)) !=
-      cudaSuccess)
+                           s.dlist, s.counters + 0, cap, s.nbr_count, s.nbr_idx, s.seg_mask, s.small, s.ds, st,
+                           rows)) != cudaSuccess)
     return e;
   const int* lp_list = s.dlist;
   const int* lp_count = s.counters + 0;
@@ -378,6 +381,10 @@ cudaError_t enqueue_stage_weights(vrm_ctx* ctx, const double* x, const double* y
   }
   if ((e = lp_small(c, x, y, lp_list, lp_count, cap, s.small, s.cols, s.f, s.fii, s.status, s.fail_list, s.retry_list, s.ds,
                     0.0, st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
+    return e;
+  if (!rows && (e = search_list_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.cell_key,
+                                    s.cell_rank, s.fail_list, &s.ds->n_fail, std::min(cap, 32 * sm_count()),
+                                    s.nbr_count, s.nbr_idx, s.seg_mask, s.small, s.ds, st, true)) != cudaSuccess)
     return e;
   return lp_full(c, x, y, s.fail_list, &s.ds->n_fail, cap, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii, s.status,
                  s.ds, 0.0, st, &s.st->dt, ctx->p.nu);
@@ -467,6 +474,8 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.counters, 8);
   VRM_ALLOC(s.st, 1);
 #undef VRM_ALLOC
+  // the bounding box starts at its initial values (every grid build leaves it so)
+  if (e == cudaSuccess) e = grid_bbox_reset(s.bbox, st);
   // the growth control's pass counter starts at 0 (every pass leaves it so)
   if (e == cudaSuccess) e = cudaMemsetAsync(s.rstate, 0, sizeof(ReduceState), st);
   // the proposal cells (and their tile sums) start empty; every insertion
@@ -622,7 +631,7 @@ cudaError_t enqueue_front(vrm_ctx* ctx, double* x, double* y, int cap, const dou
   if ((e = mark(ctx, VRM_STAGE_GRID, st)) != cudaSuccess) return e;
   if ((e = grid_build_dev(x, y, cap, n_dev, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank,
                           s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
-                          st, s.cell_ts)) != cudaSuccess)
+                          st, s.cell_ts, true)) != cudaSuccess)
     return e;
   if ((e = search_masks_list_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.cell_key,
                                  s.cell_rank, s.dlist, s.counters + 0, cap, s.mask, st)) != cudaSuccess)
@@ -648,13 +657,16 @@ cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const doub
                            s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.scan_tmp, st, s.cell_ts)) !=
       cudaSuccess)
     return e;
-  // rows of the diffused particles only (the LPs and the learned slots read
-  // no other row; the application goes through the transposed stencils), in
-  // visiting order (the learned slots and the full-neighbourhood LP order
-  // their entries themselves)
+  // counts, masks and small neighbourhoods of the diffused particles (the
+  // LPs read no other particle's); their rows only where the learned slots
+  // read them (the full-neighbourhood LP's few particles get theirs below;
+  // the application goes through the transposed stencils), in visiting order
+  // (the learned slots and the full-neighbourhood LP order their entries
+  // themselves)
+  const bool rows = ctx->mlp != nullptr;
   if ((e = search_list_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.cell_key, s.cell_rank,
-                           s.dlist, s.counters + 0, cap, s.nbr_count, s.nbr_idx, s.seg_mask, s.small, s.ds, st)) !=
-      cudaSuccess)
+                           s.dlist, s.counters + 0, cap, s.nbr_count, s.nbr_idx, s.seg_mask, s.small, s.ds, st,
+                           rows)) != cudaSuccess)
     return e;
   if ((e = mark(ctx, VRM_STAGE_LP_SMALL, st)) != cudaSuccess) return e;
   const int* lp_list = s.dlist;
@@ -670,6 +682,10 @@ cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const doub
                     0.0, st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
     return e;
   if ((e = mark(ctx, VRM_STAGE_LP_FULL, st)) != cudaSuccess) return e;
+  if (!rows && (e = search_list_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.cell_key,
+                                    s.cell_rank, s.fail_list, &s.ds->n_fail, std::min(cap, 32 * sm_count()),
+                                    s.nbr_count, s.nbr_idx, s.seg_mask, s.small, s.ds, st, true)) != cudaSuccess)
+    return e;
   if ((e = lp_full(c, x, y, s.fail_list, &s.ds->n_fail, cap, s.nbr_count, s.nbr_idx, s.cols, s.f, s.fii, s.status,
                    s.ds, 0.0, st, &s.st->dt, ctx->p.nu)) != cudaSuccess)
     return e;

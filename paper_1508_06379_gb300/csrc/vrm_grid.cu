@@ -278,7 +278,9 @@ __global__ void k_bbox(const double* __restrict__ x, const double* __restrict__ 
   }
 }
 
-__global__ void k_grid_finalize(const unsigned long long* __restrict__ bb, int n, const int* __restrict__ n_dev,
+// Also puts the bounding-box accumulators back to their initial values once
+// read, so that the next grid build may skip k_bbox_init.
+__global__ void k_grid_finalize(unsigned long long* __restrict__ bb, int n, const int* __restrict__ n_dev,
                                 double Rh, double lo2, double hi2, int ncell_cap, Grid* __restrict__ g) {
   if (n_dev) n = *n_dev;
   Grid G;
@@ -313,6 +315,11 @@ __global__ void k_grid_finalize(const unsigned long long* __restrict__ bb, int n
   G.hi_out = hi2c + kBand;
   G.seg_eps = kSegEps;
   *g = G;
+  bb[0] = ~0ull;
+  bb[1] = 0ull;
+  bb[2] = ~0ull;
+  bb[3] = 0ull;
+  bb[4] = 0ull;
 }
 
 // Keys and ranks of particles [n0, n1); with cell_ts the scan's tile sums
@@ -370,8 +377,12 @@ static int stream_grid(int n_bound, int per_sm) {
 cudaError_t grid_build_dev(const double* x, const double* y, int n_bound, const int* n_dev, double Rh, double lo2,
                            double hi2, int ncell_cap, Grid* g, int* cell_key, int* cell_rank, int* cell_count,
                            int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx,
-                           unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s, int* cell_ts) {
-  k_bbox_init<<<1, 1, 0, s>>>(bbox_tmp); note_launch();
+                           unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s, int* cell_ts,
+                           bool bbox_ready) {
+  if (!bbox_ready) {
+    k_bbox_init<<<1, 1, 0, s>>>(bbox_tmp);
+    note_launch();
+  }
   k_bbox<<<stream_grid(n_bound, 4), kBlock, 0, s>>>(x, y, n_bound, n_dev, bbox_tmp); note_launch();
   k_grid_finalize<<<1, 1, 0, s>>>(bbox_tmp, n_bound, n_dev, Rh, lo2, hi2, ncell_cap, g); note_launch();
   return grid_bin_dev(x, y, n_bound, n_dev, ncell_cap, g, cell_key, cell_rank, cell_count, cell_start, sorted_xy,
@@ -430,6 +441,12 @@ cudaError_t grid_extend_dev(const double* x, const double* y, int n_bound, const
   if (e != cudaSuccess) return e;
   k_scatter<<<b, kBlock, 0, s>>>(x, y, n_bound, n1_dev, g, cell_key, cell_rank, cell_start, sorted_xy, sorted_loc,
                                  sorted_idx);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t grid_bbox_reset(unsigned long long* bbox_tmp, cudaStream_t s) {
+  k_bbox_init<<<1, 1, 0, s>>>(bbox_tmp);
   note_launch();
   return cudaGetLastError();
 }

@@ -214,7 +214,11 @@ cudaError_t grid_build(const double* x, const double* y, int n, double Rh, doubl
 cudaError_t grid_build_dev(const double* x, const double* y, int n_bound, const int* n_dev, double Rh, double lo2,
                            double hi2, int ncell_cap, Grid* g, int* cell_key, int* cell_rank, int* cell_count,
                            int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx,
-                           unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s, int* cell_ts = nullptr);
+                           unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s, int* cell_ts = nullptr,
+                           bool bbox_ready = false);
+// Sets the bounding-box accumulators to their initial values (every grid
+// build leaves them so; a build with bbox_ready = true relies on it).
+cudaError_t grid_bbox_reset(unsigned long long* bbox_tmp, cudaStream_t s);
 // cell_ts (optional, ncell_cap / kScanTile + 2 ints): the binning kernel
 // accumulates the tile sums of the cell counts there, and the scan of the
 // counts is one launch.
@@ -287,12 +291,13 @@ cudaError_t search_all_dev(const Consts& c, const Grid* g, const int* cell_start
                            int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small, DevStats* ds,
                            cudaStream_t s, bool sorted = true);
 // Rows, masks and small neighbourhoods of the listed particles only (rows in
-// visiting order, padded to whole 32-byte sectors).
+// visiting order, padded to whole 32-byte sectors); rows = false leaves the
+// rows unwritten (counts, masks and small neighbourhoods still are).
 cudaError_t search_list_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
                             const float2* sorted_loc, const int* sorted_idx, const int* cell_key,
                             const int* cell_rank, const int* list, const int* list_count, int m_bound,
                             int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small, DevStats* ds,
-                            cudaStream_t s);
+                            cudaStream_t s, bool rows = true);
 cudaError_t search_masks_list_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
                                   const float2* sorted_loc, const int* sorted_idx, const int* cell_key,
                                   const int* cell_rank, const int* list, const int* list_count, int m_bound,

@@ -49,7 +49,9 @@ __device__ __forceinline__ int exact_member(const Consts& c, const double2& pi, 
 // in the sorted arrays through its cell key and rank; threads follow the
 // list's order.  Rows are then padded with -1 to the end of their last
 // 32-byte sector, so that the sector is written whole.
-template <int KCAP, bool SORTED, bool LIST = false>
+// ROWS = false (list form only): the rows are not written (the count, mask
+// and small neighbourhood are).
+template <int KCAP, bool SORTED, bool LIST = false, bool ROWS = true>
 __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __restrict__ gp,
                                                        const int* __restrict__ cell_start,
                                                        const double2* __restrict__ sxy,
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
             s_bj[s][tx] = j;
           }
           if (LIST) {
-            if (cnt < k_cap) row_out[cnt] = j;
+            if (ROWS && cnt < k_cap) row_out[cnt] = j;
           } else if (SORTED || cnt >= k_cap) {
             if (!SORTED && cnt == k_cap) {
               // the row overflows (rare): order the entries kept so far, so
@@ -231,7 +233,7 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
     int* row = nbr_idx + (size_t)i * stride;
     if (!LIST)
       for (int t = 0; t < m; ++t) row[t] = list[t];
-    if (LIST) {
+    if (LIST && ROWS) {
       const int pad = ((m + 7) & ~7) < (int)stride ? ((m + 7) & ~7) : (int)stride;
       for (int t = m; t < pad; ++t) row[t] = -1;
     }
@@ -347,20 +349,22 @@ cudaError_t search_list_dev(const Consts& c, const Grid* g, const int* cell_star
                             const float2* sorted_loc, const int* sorted_idx, const int* cell_key,
                             const int* cell_rank, const int* list, const int* list_count, int m_bound,
                             int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small, DevStats* ds,
-                            cudaStream_t s) {
+                            cudaStream_t s, bool rows) {
   if (m_bound <= 0) return cudaSuccess;
   const int tb = c.search_block;
   const int blocks = (int)(((long)m_bound + tb - 1) / tb);
-#define VRM_SEARCH_LAUNCH(K)                                                                                       \
-  k_search_all<K, false, true><<<blocks, tb, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, m_bound, \
-                                                     list_count, nbr_count, nbr_idx, seg_mask, small, ds, list,     \
-                                                     cell_key, cell_rank)
-  if (c.row_cap <= 16)
-    VRM_SEARCH_LAUNCH(16);
+#define VRM_SEARCH_LAUNCH(K, R)                                                                                    \
+  k_search_all<K, false, true, R><<<blocks, tb, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx,       \
+                                                        m_bound, list_count, nbr_count, nbr_idx, seg_mask, small, \
+                                                        ds, list, cell_key, cell_rank)
+  if (!rows)
+    VRM_SEARCH_LAUNCH(VRM_KCAP_MAX, false);  // rows not written: the cap only bounds the count
+  else if (c.row_cap <= 16)
+    VRM_SEARCH_LAUNCH(16, true);
   else if (c.row_cap <= 24)
-    VRM_SEARCH_LAUNCH(24);
+    VRM_SEARCH_LAUNCH(24, true);
   else
-    VRM_SEARCH_LAUNCH(VRM_KCAP_MAX);
+    VRM_SEARCH_LAUNCH(VRM_KCAP_MAX, true);
 #undef VRM_SEARCH_LAUNCH
   note_launch();
   return cudaGetLastError();
