@@ -810,17 +810,25 @@ __device__ __forceinline__ void lp_pivots32(const float (&xs)[8], const float (&
       a[r] = v;
       ea[r] = e;
     }
-    // eligible rows, zero basic values, ratios with bounds
-    unsigned elig = 0;
+    // eligible rows, zero basic values, ratios with bounds.  A row whose
+    // eligibility is uncertain (pivot element within its bound of the
+    // tolerance, mostly exact zeros) but whose basic value is certainly
+    // positive would, if eligible, have a ratio of at least
+    // (rhs - Eb) / (a + Ea): when that is above every possible tie limit,
+    // the row can neither be the minimum nor tie with it, and the leaving
+    // row is the same either way
+    unsigned elig = 0, amb = 0;
     float lo[M], hi[M], thlo = 3.0e38f, thhi = 3.0e38f;
 #pragma unroll
     for (int r = 0; r < M; ++r) {
       const float mg = kCertSafety * ea[r];
       const bool el = a[r] > kTolPivotHi + mg;
-      unc = unc || (!el && !(a[r] < kTolPivotLo - mg));
+      const bool am = !el && !(a[r] < kTolPivotLo - mg);
       const float mb = kCertSafety * Eb[r];
       const bool nzr = rhs[r] > kTolSnapHi + mb;
+      unc = unc || (am && !nzr);
       unc = unc || (el && !nzr && !(rhs[r] < kTolSnapLo - mb));
+      amb |= am ? 1u << r : 0u;
       const float inv = rcp_approx(a[r]);
       const float ratio = nzr ? rhs[r] * inv : 0.0f;
       // relative bound of the pivot element; for g <= 1/2,
@@ -837,6 +845,8 @@ __device__ __forceinline__ void lp_pivots32(const float (&xs)[8], const float (&
       thhi = fminf(thhi, hi[r]);
     }
     if (elig == 0) {
+      // an uncertain row decides between no eligible row and a pivot
+      unc = unc || amb != 0;
       code = 2;
       break;
     }
@@ -851,6 +861,17 @@ __device__ __forceinline__ void lp_pivots32(const float (&xs)[8], const float (&
     for (int r = 0; r < M; ++r) {
       poss |= (((elig >> r) & 1u) && lo[r] <= limhi) ? 1u << r : 0u;
       tied |= (hi[r] <= limlo) ? 1u << r : 0u;
+    }
+    if (amb != 0) {
+      // (rhs - mb) / (a + mg) > limhi without a division: a + mg is at least
+      // the pivot tolerance for these rows, and the factor covers the
+      // roundings of the difference, the sum and the product (< 4 u)
+#pragma unroll
+      for (int r = 0; r < M; ++r) {
+        const float num = __fsub_rn(rhs[r], kCertSafety * Eb[r]);
+        const float lim = __fmul_rn(limhi, __fadd_rn(a[r], kCertSafety * ea[r]));
+        unc = unc || (((amb >> r) & 1u) && !(__fmul_rn(num, 1.0f - 8.0f * kU32) > lim));
+      }
     }
     if (__popc(poss) == 1)
       tied = poss;
