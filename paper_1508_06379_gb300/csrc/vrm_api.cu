@@ -176,7 +176,7 @@ void free_scratch(Scratch& s) {
                   s.sorted_idx, s.bbox, s.scan_tmp, s.pos, s.rstate, s.tie_flag, s.tie_rank, s.dflag_ts, s.tie_ts,
                   s.cell_ts, s.diffused, s.dlist,
                   s.mask, r.open, r.act0, r.act1, r.cnt, r.cpos, r.cnt_ts, r.cell_ts, r.keep_ts, r.keep_flag, r.cx,
-                  r.cy, r.keep, r.apos,
+                  r.cy, r.keep, r.keep_s, r.apos,
                   r.cg.grid, r.cg.cell_key, r.cg.cell_rank, r.cg.cell_count, r.cg.cell_start, r.cg.sorted_idx,
                   r.cg.sorted_xy, r.cg.sorted_loc, r.cg.bbox, r.scan_tmp, s.nbr_count, s.nbr_idx, s.small, s.cols,
                   s.fail_list, s.retry_list, s.seg_mask, s.status, s.f, s.fii, s.tcount, s.toff, s.tplace, s.tent, s.ds,
@@ -444,6 +444,7 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(r.cx, n8);
   VRM_ALLOC(r.cy, n8);
   VRM_ALLOC(r.keep, n8);
+  VRM_ALLOC(r.keep_s, n8);
   VRM_ALLOC(r.apos, n8 + 1);
   VRM_ALLOC(r.cg.grid, 1);
   VRM_ALLOC(r.cg.cell_key, n8);

@@ -62,14 +62,16 @@ __device__ __forceinline__ bool conflict_keep(const Consts& c, const Grid& g, co
   return true;
 }
 
-// keep[c] = conflict_keep of every proposal, and the tile sums of keep
-// (keep_ts, 0 on entry) for the scan that numbers the accepted ones.
+// keep[c] = conflict_keep of every proposal, the same flag by sorted
+// position (keep_s, for the mask update, which visits the proposals in cell
+// order), and the tile sums of keep (keep_ts, 0 on entry) for the scan that
+// numbers the accepted ones.
 __global__ void __launch_bounds__(kBlock) k_conflict(Consts c, const Grid* __restrict__ gp,
                                                      const int* __restrict__ cell_start,
                                                      const double2* __restrict__ sxy, const float2* __restrict__ sloc,
                                                      const int* __restrict__ sidx, const int* __restrict__ cell_key,
                                                      const int* __restrict__ n_cand_dev, uint8_t* __restrict__ keep,
-                                                     int* __restrict__ keep_ts) {
+                                                     uint8_t* __restrict__ keep_s, int* __restrict__ keep_ts) {
   const int n_cand = *n_cand_dev;
   const Grid g = *gp;
   const int lane = threadIdx.x & 31;
@@ -83,6 +85,7 @@ __global__ void __launch_bounds__(kBlock) k_conflict(Consts c, const Grid* __res
       // the proposal's cell as binned (integer ops, no FP64)
       ok = conflict_keep(c, g, cell_start, sxy, sloc, sidx, ci, cell_key[ci], p);
       keep[ci] = ok;
+      keep_s[p] = ok;
     }
     tile_sum_add(keep_ts, ok ? ci : -1, 1);
   }
@@ -96,9 +99,9 @@ __global__ void __launch_bounds__(kBlock) k_conflict(Consts c, const Grid* __res
 // FP64 arithmetic.
 __device__ __forceinline__ bool mask_update_one(const Consts& c, const Grid& g, const int* __restrict__ cell_start,
                                                 const double2* __restrict__ sxy, const float2* __restrict__ sloc,
-                                                const int* __restrict__ sidx, const uint8_t* __restrict__ keep,
-                                                const double* __restrict__ x, const double* __restrict__ y,
-                                                const PartCells& pcells, int i, uint8_t* __restrict__ mask) {
+                                                const uint8_t* __restrict__ keep_s, const double* __restrict__ x,
+                                                const double* __restrict__ y, const PartCells& pcells, int i,
+                                                uint8_t* __restrict__ mask) {
   const int key = pcells.cell_key[i];
   const float2 li = pcells.sorted_loc[pcells.cell_start[key] + pcells.cell_rank[i]];
   const int gy = key / g.nx, gx = key - gy * g.nx;
@@ -117,7 +120,7 @@ __device__ __forceinline__ bool mask_update_one(const Consts& c, const Grid& g, 
         const float du = dub + lo.x, dv = dvb + lo.y;
         const float d2f = __fmaf_rn(du, du, dv * dv);
         if (d2f < g.lo_out || d2f > g.hi_out) continue;
-        if (!keep[sidx[q]]) continue;
+        if (!keep_s[q]) continue;
         int s = -1;
         if (d2f > g.lo_in && d2f < g.hi_in) s = segment_or_ambiguous(du, dv, g.seg_eps);
         if (s < 0) {
@@ -383,8 +386,8 @@ __global__ void k_append_dev(const double* __restrict__ cx, const double* __rest
 // block to finish records the round's counters and the loop condition.
 __global__ void __launch_bounds__(kBlock) k_round_update(
     Consts c, const Grid* __restrict__ gp, const int* __restrict__ cell_start, const double2* __restrict__ sxy,
-    const float2* __restrict__ sloc, const int* __restrict__ sidx, const uint8_t* __restrict__ keep,
-    const int* __restrict__ apos, const int* __restrict__ open, int* __restrict__ cnt, int* __restrict__ cnt_ts,
+    const float2* __restrict__ sloc, const uint8_t* __restrict__ keep_s, const int* __restrict__ apos,
+    const int* __restrict__ open, int* __restrict__ cnt, int* __restrict__ cnt_ts,
     int* __restrict__ act0, int* __restrict__ act1, PartCells pcells, StepState* __restrict__ st, const double* __restrict__ x,
     const double* __restrict__ y, uint8_t* __restrict__ mask, cudaGraphConditionalHandle h, int graph) {
   const int n_cand = st->n_cand, n_cur = st->n_cur;
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(kBlock) k_round_update(
     if (k < n_act) {
       t = act[k];
       const int i = open[t];
-      still = mask_update_one(c, g, cell_start, sxy, sloc, sidx, keep, x, y, pcells, i, mask);
+      still = mask_update_one(c, g, cell_start, sxy, sloc, keep_s, x, y, pcells, i, mask);
       const int cn = still ? __popc((~(unsigned)mask[i]) & 0xFFu) : 0;
       dc = cn - cnt[t];
       cnt[t] = cn;
@@ -495,13 +498,13 @@ cudaError_t round_body(const Consts& c, StepState* st, const Grid* pgrid, const 
                                        rb.keep_ts);
   note_launch();
   k_conflict<<<bc, kBlock, 0, s>>>(c, pgrid, cg.cell_start, cg.sorted_xy, cg.sorted_loc, cg.sorted_idx, cg.cell_key,
-                                   &st->n_cand, rb.keep, rb.keep_ts);
+                                   &st->n_cand, rb.keep, rb.keep_s, rb.keep_ts);
   note_launch();
   e = scan_presummed_u8_dev(rb.keep, rb.apos, (int)cand_cap, &st->n_cand, rb.keep_ts, s);
   if (e != cudaSuccess) return e;
   k_append_dev<<<bc, kBlock, 0, s>>>(rb.cx, rb.cy, rb.keep, rb.apos, st, x, y); note_launch();
-  k_round_update<<<bo, kBlock, 0, s>>>(c, pgrid, cg.cell_start, cg.sorted_xy, cg.sorted_loc, cg.sorted_idx, rb.keep,
-                                       rb.apos, rb.open, rb.cnt, rb.cnt_ts, rb.act0, rb.act1, pcells, st, x, y, mask,
+  k_round_update<<<bo, kBlock, 0, s>>>(c, pgrid, cg.cell_start, cg.sorted_xy, cg.sorted_loc, rb.keep_s, rb.apos,
+                                       rb.open, rb.cnt, rb.cnt_ts, rb.act0, rb.act1, pcells, st, x, y, mask,
                                        handle, graph ? 1 : 0);
   note_launch();
   return cudaGetLastError();

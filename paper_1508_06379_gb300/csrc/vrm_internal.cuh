@@ -330,6 +330,7 @@ struct RoundBufs {
   uint8_t *keep_flag;  // open particle still open (cap)
   double *cx, *cy;     // proposals (8 cap)
   uint8_t* keep;       // proposal accepted (8 cap)
+  uint8_t* keep_s;     // the same flags by position in the proposal grid's cell order (8 cap)
   int* apos;           // offsets of accepted proposals (8 cap + 1)
   int ncell_cap;       // cells of the proposal grid
   CandGrid cg;         // proposal cell grid (geometry copied from the particle grid)

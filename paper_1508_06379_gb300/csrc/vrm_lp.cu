@@ -501,6 +501,64 @@ __device__ __forceinline__ void lp_finish(const Consts& c, int i, int code, cons
   }
 }
 
+// Leaving row of an FP64 pivot whose entering column is a (the ratio test;
+// one function for the FP64 kernels, so that they decide alike): basic
+// values <= kTolSnap are zeros.  The ratios are screened in binary32
+// (operands rounded from their bit patterns: relative error < 1e-6, no FP64
+// instruction); the rows within 1e-5 of the smallest binary32 ratio are the
+// only ones that can lie in the FP64 tie window (1e-12), so the leaving row
+// is decided without FP64 unless two of them differ and are not exact zeros,
+// and then in FP64 (Newton reciprocal, relative error ~2^-45) on those rows.
+// Returns false when no row is eligible; else the leaving row and its basic
+// variable.
+template <int M>
+__device__ __forceinline__ bool lp_leave(const double (&a)[M], const double (&rhs)[M], const int (&basis)[M],
+                                         int& leave, int& lbas) {
+  bool elig[M], any = false;
+  float r32[M], m32 = 3.0e38f;
+#pragma unroll
+  for (int r = 0; r < M; ++r) {
+    elig[r] = gt_pos(a[r], kTolPivot);
+    const bool nz = gt_pos(rhs[r], kTolSnap);
+    r32[r] = !elig[r] ? 3.0e38f : nz ? __fmul_rn(f32_of(rhs[r]), __frcp_rn(f32_of(a[r]))) : 0.0f;
+    any = any || elig[r];
+    m32 = fminf(m32, r32[r]);
+  }
+  leave = -1;
+  lbas = INT_MAX;
+  if (!any) return false;
+  const float marg = __fmaf_rn(1e-5f, fmaxf(m32, 1.0f), m32);
+  unsigned cont = 0;
+  bool allzero = true;
+#pragma unroll
+  for (int r = 0; r < M; ++r)
+    if (elig[r] && r32[r] <= marg) {
+      cont |= 1u << r;
+      allzero = allzero && r32[r] == 0.0f;
+    }
+  if (__popc(cont) > 1 && !allzero) {
+    double ratio[M], theta = 1e308;
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+      const double num = gt_pos(rhs[r], kTolSnap) ? rhs[r] : 0.0;
+      ratio[r] = ((cont >> r) & 1u) ? __dmul_rn(num, rcp_newton<1>(a[r])) : 1e308;
+      theta = lt_nonneg(ratio[r], theta) ? ratio[r] : theta;
+    }
+    const double lim = __fma_rn(kTolTie, gt_pos(theta, 1.0) ? theta : 1.0, theta);
+#pragma unroll
+    for (int r = 0; r < M; ++r)
+      if (((cont >> r) & 1u) && lt_nonneg(lim, ratio[r])) cont &= ~(1u << r);
+  }
+  // the tied rows: the one with the lowest basic variable leaves
+#pragma unroll
+  for (int r = 0; r < M; ++r)
+    if (((cont >> r) & 1u) && basis[r] < lbas) {
+      leave = r;
+      lbas = basis[r];
+    }
+  return true;
+}
+
 template <int M, int W>
 __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __restrict__ x,
                                                   const double* __restrict__ y, const int* __restrict__ list,
@@ -566,57 +624,11 @@ __global__ void __launch_bounds__(128) k_lp_small(Consts c, const double* __rest
           for (int k = 1; k < 8; ++k) v = (q == k) ? T[r][k] : v;
           a[r] = v;
         }
-        // ratio test: basic values <= kTolSnap are zeros.  The ratios are
-        // screened in binary32 (operands rounded from their bit patterns:
-        // relative error < 1e-6, no FP64 instruction); the rows within 1e-5
-        // of the smallest binary32 ratio are the only ones that can lie in
-        // the FP64 tie window (1e-12), so the leaving row is decided without
-        // FP64 unless two of them differ and are not exact zeros, and then
-        // in FP64 (Newton reciprocal, relative error ~2^-45) on those rows
-        bool elig[M], any = false;
-        float r32[M], m32 = 3.0e38f;
-#pragma unroll
-        for (int r = 0; r < M; ++r) {
-          elig[r] = gt_pos(a[r], kTolPivot);
-          const bool nz = gt_pos(rhs[r], kTolSnap);
-          r32[r] = !elig[r] ? 3.0e38f : nz ? __fmul_rn(f32_of(rhs[r]), __frcp_rn(f32_of(a[r]))) : 0.0f;
-          any = any || elig[r];
-          m32 = fminf(m32, r32[r]);
-        }
-        if (!any) {
+        int leave, lbas;
+        if (!lp_leave<M>(a, rhs, basis, leave, lbas)) {
           code = 2;
           break;
         }
-        const float marg = __fmaf_rn(1e-5f, fmaxf(m32, 1.0f), m32);
-        unsigned cont = 0;
-        bool allzero = true;
-#pragma unroll
-        for (int r = 0; r < M; ++r)
-          if (elig[r] && r32[r] <= marg) {
-            cont |= 1u << r;
-            allzero = allzero && r32[r] == 0.0f;
-          }
-        if (__popc(cont) > 1 && !allzero) {
-          double ratio[M], theta = 1e308;
-#pragma unroll
-          for (int r = 0; r < M; ++r) {
-            const double num = gt_pos(rhs[r], kTolSnap) ? rhs[r] : 0.0;
-            ratio[r] = ((cont >> r) & 1u) ? __dmul_rn(num, rcp_newton<1>(a[r])) : 1e308;
-            theta = lt_nonneg(ratio[r], theta) ? ratio[r] : theta;
-          }
-          const double lim = __fma_rn(kTolTie, gt_pos(theta, 1.0) ? theta : 1.0, theta);
-#pragma unroll
-          for (int r = 0; r < M; ++r)
-            if (((cont >> r) & 1u) && lt_nonneg(lim, ratio[r])) cont &= ~(1u << r);
-        }
-        // the tied rows: the one with the lowest basic variable leaves
-        int leave = -1, lbas = INT_MAX;
-#pragma unroll
-        for (int r = 0; r < M; ++r)
-          if (((cont >> r) & 1u) && basis[r] < lbas) {
-            leave = r;
-            lbas = basis[r];
-          }
         double piv = a[0], prhs_raw = rhs[0];
 #pragma unroll
         for (int r = 1; r < M; ++r) {
