@@ -403,7 +403,8 @@ def run_ours(args):
     dom = max(mean_stage, key=mean_stage.get)
     sch = ctx.get_schedule()
     roofline = (roofline_for(dom, mean_stage[dom], stats, n, desc["order"], sch["lp_fp64_pivots"], peaks,
-                             sch["lp_block"]) if mean_stage[dom] > 0 else None)
+                             sch["lp_block"], rows=bool(getattr(args, "learned", False)))
+                if mean_stage[dom] > 0 else None)
     learned = None
     if args.workload == "mixture_1m" and not args.no_learned and world == 1:
         learned = learned_vs_lp(args, ctx, xb, yb, n, gi, go, h, nu, dt, total_ms / args.steps, parts / args.steps,
@@ -572,7 +573,7 @@ def traffic_for(kernel):
         return None
 
 
-def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1, peaks=None, lp_block=128):
+def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1, peaks=None, lp_block=128, rows=False):
     m = 9 if order == 2 else 5
     if stage in ("lp_small", "lp_full"):
         if stage == "lp_small" and order == 1 and not lp_fp64_pivots:
@@ -604,9 +605,11 @@ def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1, peaks=None, lp_
         hbm, src = 6800.0, "of fallback"
     n_out = stats["n_out"]
     if stage == "search":
-        # the step searches the diffused particles: row, count, mask and
-        # small neighbourhood out, position in (about 100 B each)
-        nbytes = stats["n_diffused"] * 100.0
+        # the step searches the diffused particles: cell key, rank and
+        # cell-local position in (16 B), count, mask and small neighbourhood
+        # out (37 B); the neighbour row (about 47 B more) only where the
+        # learned path reads it
+        nbytes = stats["n_diffused"] * (100.0 if rows else 53.0)
         kern = "k_search_all"
     elif stage == "apply":
         # Gamma in and out per target, (index, weight, source Gamma) per

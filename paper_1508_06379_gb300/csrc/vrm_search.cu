@@ -72,9 +72,13 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
   int local_max = 0;
   // closest member of every segment so far (FP32 squared distance, index),
   // one column per thread: read and written with a dynamic segment index
-  // (conflict-free: the row stride is a multiple of 32 words)
-  __shared__ float s_bf[8][kBlock];
-  __shared__ int s_bj[8][kBlock];
+  // (conflict-free: the row stride, the block size, is a multiple of 32
+  // words).  Sized by the launch (8 + 8 words per thread), so that a small
+  // block leaves the rest of the SM's shared memory to L1.
+  extern __shared__ int s_search[];
+  const int nb = blockDim.x;
+  float* const s_bf = reinterpret_cast<float*>(s_search);
+  int* const s_bj = s_search + 8 * nb;
   const int tx = threadIdx.x;
   for (long t0 = (long)blockIdx.x * blockDim.x + threadIdx.x; t0 < n; t0 += (long)gridDim.x * blockDim.x) {
     int i, cx, cy;
@@ -104,8 +108,8 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
     int cnt = 0;
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-      s_bf[t][tx] = 3e38f;
-      s_bj[t][tx] = -1;
+      s_bf[t * nb + tx] = 3e38f;
+      s_bj[t * nb + tx] = -1;
     }
     unsigned mask = 0, amb = 0;
     for (int by = cy - 1; by <= cy + 1; ++by) {
@@ -139,15 +143,15 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
             if (s < 0) continue;
           }
           mask |= 1u << s;
-          const float cb = s_bf[s][tx];
-          const int cjb = s_bj[s][tx];
+          const float cb = s_bf[s * nb + tx];
+          const int cjb = s_bj[s * nb + tx];
           const bool take = cjb < 0 || d2f < cb || (d2f == cb && j < cjb);
           // conservative: the displaced or the new member is close to the best
           const bool close = cjb >= 0 && fabsf(d2f - cb) <= tie;
           if (close) amb |= 1u << s;
           if (take) {
-            s_bf[s][tx] = d2f;
-            s_bj[s][tx] = j;
+            s_bf[s * nb + tx] = d2f;
+            s_bj[s * nb + tx] = j;
           }
           if (LIST) {
             if (ROWS && cnt < k_cap) row_out[cnt] = j;
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(kBlock) k_search_all(Consts c, const Grid* __r
     }
     int bj[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) bj[t] = s_bj[t][tx];
+    for (int t = 0; t < 8; ++t) bj[t] = s_bj[t * nb + tx];
     if (amb) {
       // exact FP64 order (ties to the smaller index) for the flagged segments
       double bd[8];
@@ -323,6 +327,10 @@ cudaError_t search_masks_list_dev(const Consts& c, const Grid* g, const int* cel
   return cudaGetLastError();
 }
 
+// Dynamic shared memory of k_search_all: a segment's best distance and
+// index per thread, eight segments.
+static size_t search_smem(int tb) { return (size_t)tb * 8 * (sizeof(float) + sizeof(int)); }
+
 cudaError_t search_all_dev(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,
                            const float2* sorted_loc, const int* sorted_idx, int n_bound, const int* n_dev,
                            int* nbr_count, int* nbr_idx, uint8_t* seg_mask, int* small, DevStats* ds,
@@ -331,8 +339,8 @@ cudaError_t search_all_dev(const Consts& c, const Grid* g, const int* cell_start
   const int tb = c.search_block;
   const int blocks = (int)(((long)n_bound + tb - 1) / tb);
 #define VRM_SEARCH_LAUNCH(K, S)                                                                                     \
-  k_search_all<K, S><<<blocks, tb, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, n_bound, n_dev,    \
-                                           nbr_count, nbr_idx, seg_mask, small, ds)
+  k_search_all<K, S><<<blocks, tb, search_smem(tb), s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx,      \
+                                                         n_bound, n_dev, nbr_count, nbr_idx, seg_mask, small, ds)
   if (c.row_cap <= 16) {
     if (sorted) VRM_SEARCH_LAUNCH(16, true); else VRM_SEARCH_LAUNCH(16, false);
   } else if (c.row_cap <= 24) {
@@ -354,9 +362,9 @@ cudaError_t search_list_dev(const Consts& c, const Grid* g, const int* cell_star
   const int tb = c.search_block;
   const int blocks = (int)(((long)m_bound + tb - 1) / tb);
 #define VRM_SEARCH_LAUNCH(K, R)                                                                                    \
-  k_search_all<K, false, true, R><<<blocks, tb, 0, s>>>(c, g, cell_start, sorted_xy, sorted_loc, sorted_idx,       \
-                                                        m_bound, list_count, nbr_count, nbr_idx, seg_mask, small, \
-                                                        ds, list, cell_key, cell_rank)
+  k_search_all<K, false, true, R><<<blocks, tb, search_smem(tb), s>>>(                                            \
+      c, g, cell_start, sorted_xy, sorted_loc, sorted_idx, m_bound, list_count, nbr_count, nbr_idx, seg_mask, small, \
+      ds, list, cell_key, cell_rank)
   if (!rows)
     VRM_SEARCH_LAUNCH(VRM_KCAP_MAX, false);  // rows not written: the cap only bounds the count
   else if (c.row_cap <= 16)
