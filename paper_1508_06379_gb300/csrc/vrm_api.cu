@@ -63,7 +63,6 @@ struct vrm::Scratch {
   double *f = nullptr, *fii = nullptr;
   // the stencils transposed per target (the application's lists, a CSR)
   int *tcount = nullptr, *toff = nullptr;
-  uint8_t* tplace = nullptr;
   double2* tent = nullptr;
   // counters and state
   DevStats* ds = nullptr;
@@ -179,7 +178,7 @@ void free_scratch(Scratch& s) {
                   r.cy, r.keep, r.keep_s, r.apos,
                   r.cg.grid, r.cg.cell_key, r.cg.cell_rank, r.cg.cell_count, r.cg.cell_start, r.cg.sorted_idx,
                   r.cg.sorted_xy, r.cg.sorted_loc, r.cg.bbox, r.scan_tmp, s.nbr_count, s.nbr_idx, s.small, s.cols,
-                  s.fail_list, s.retry_list, s.seg_mask, s.status, s.f, s.fii, s.tcount, s.toff, s.tplace, s.tent, s.ds,
+                  s.fail_list, s.retry_list, s.seg_mask, s.status, s.f, s.fii, s.tcount, s.toff, s.tent, s.ds,
                   s.counters, s.st};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -469,7 +468,6 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   VRM_ALLOC(s.fii, n);
   VRM_ALLOC(s.tcount, n);
   VRM_ALLOC(s.toff, (long)n + 1);
-  VRM_ALLOC(s.tplace, (long)n * ctx->c.w);
   VRM_ALLOC(s.tent, (long)n * ctx->c.w);
   VRM_ALLOC(s.ds, 1);
   VRM_ALLOC(s.counters, 8);
@@ -479,6 +477,9 @@ cudaError_t ensure_scratch(vrm_ctx* ctx, int cap, cudaStream_t st) {
   if (e == cudaSuccess) e = grid_bbox_reset(s.bbox, st);
   // the growth control's pass counter starts at 0 (every pass leaves it so)
   if (e == cudaSuccess) e = cudaMemsetAsync(s.rstate, 0, sizeof(ReduceState), st);
+  // the application's per-target counters start at 0 (every application
+  // leaves them so)
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.tcount, 0, sizeof(int) * (size_t)n, st);
   // the proposal cells (and their tile sums) start empty; every insertion
   // round leaves them empty
   if (e == cudaSuccess) e = cudaMemsetAsync(r.cg.cell_count, 0, sizeof(int) * (size_t)ncell, st);
@@ -692,7 +693,7 @@ cudaError_t enqueue_back(vrm_ctx* ctx, double* x, double* y, int cap, const doub
     return e;
   if ((e = mark(ctx, VRM_STAGE_APPLY, st)) != cudaSuccess) return e;
   if ((e = apply_transposed_dev(c, cap, n_cur, cap, &s.st->n, gamma_in, s.diffused, s.dlist, s.counters + 0, s.cols,
-                                s.f, s.fii, s.tcount, s.toff, s.tplace, s.tent, s.scan_tmp, s.ds, nullptr, gamma_out,
+                                s.f, s.fii, s.tcount, s.toff, s.tent, s.scan_tmp, s.ds, nullptr, gamma_out,
                                 0.0, &s.st->dt, st)) != cudaSuccess)
     return e;
   if ((e = mark(ctx, VRM_STAGE_COUNT, st)) != cudaSuccess) return e;
@@ -1165,7 +1166,7 @@ vrm_status vrm_rk3_step(vrm_ctx* ctx, double* x, double* y, int32_t n, int32_t c
     VRM_CUDA(enqueue_stage_weights(ctx, px, py, capacity, stream));
     VRM_CUDA(apply_transposed_dev(ctx->c, capacity, n_cur, k == 0 ? n : capacity, k == 0 ? nullptr : n_cur, Gs[k],
                                   s.diffused, s.dlist, s.counters + 0, s.cols, s.f, s.fii, s.tcount, s.toff,
-                                  s.tplace, s.tent, s.scan_tmp, s.ds, ctx->rk_dg, nullptr, 0.0, nullptr, stream));
+                                  s.tent, s.scan_tmp, s.ds, ctx->rk_dg, nullptr, 0.0, nullptr, stream));
     const double *us = nullptr, *vs = nullptr;
     if (V.kind == VRM_VEL_BIOT_SAVART) {
       // the stage's own velocity at every stage particle; in the first stage

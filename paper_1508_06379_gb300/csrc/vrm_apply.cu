@@ -160,14 +160,17 @@ __global__ void __launch_bounds__(kBlock) k_apply(Consts c, int n, const int* __
 
 // ---------------------------------------------------------------------------
 // The same application through the transpose of the stencils (the step's
-// form), as a compact CSR by target.  k_t_claim gives every stencil entry
-// (i -> j, f~_ij) of the diffused particles a place in target j's list:
-// an integer atomic counter per target returns the place (the counts are
-// exact, the order of a list varies), kept per entry; an exclusive scan of
-// the counts gives the lists' offsets; k_t_fill writes each entry as one
-// 16-byte record (source, term f~_ij Gamma_i, the product rounded as the
-// gather rounds it) at offset + place, so that the lists lie back to back
-// and every sector of the array is written whole.  k_apply_t sorts a
+// form), as a compact CSR by target.  k_t_count adds every stencil entry
+// (i -> j, f~_ij) of the diffused particles to target j's integer counter
+// (atomics whose results nobody waits for); an exclusive scan of the counts
+// gives the lists' offsets; k_t_fill takes each entry's place in j's list
+// from an integer atomic on j's offset (the counts are exact, the order of a
+// list varies; the offset ends at the list's end) and writes the entry as
+// one 16-byte record (source, term f~_ij Gamma_i, the product rounded as the
+// gather rounds it), so that the lists lie back to back and every sector of
+// the array is written whole.  k_apply_t sets each counter back to 0 once it
+// has read it, so that the counters are clear for the next application
+// without a memset (they start at 0 when allocated).  k_apply_t sorts a
 // target's few records by source index and adds the terms in that order
 // with the self term at i = j: exactly the sum of k_apply, with no
 // neighbour rows and no search of the sources' stencils.  The products are
@@ -181,9 +184,8 @@ struct TEntry {
 };
 
 template <int W>
-__global__ void __launch_bounds__(kBlock) k_t_claim(const int* __restrict__ list, const int* __restrict__ list_count,
-                                                    const int* __restrict__ cols, int* __restrict__ tcount,
-                                                    uint8_t* __restrict__ tplace) {
+__global__ void __launch_bounds__(kBlock) k_t_count(const int* __restrict__ list, const int* __restrict__ list_count,
+                                                    const int* __restrict__ cols, int* __restrict__ tcount) {
   const int m = *list_count;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) {
     const int i = list[t];
@@ -197,21 +199,17 @@ __global__ void __launch_bounds__(kBlock) k_t_claim(const int* __restrict__ list
       js[4 * q + 2] = a.z;
       js[4 * q + 3] = a.w;
     }
-    // every request first (their round trips overlap), then the places
-    int place[W];
 #pragma unroll
-    for (int u = 0; u < W; ++u) place[u] = js[u] >= 0 ? atomicAdd(&tcount[js[u]], 1) : 0;
-    // a list holds at most k_cap <= 32 entries whenever the rows fit
-#pragma unroll
-    for (int u = 0; u < W; ++u) tplace[(size_t)i * W + u] = (uint8_t)(place[u] < 255 ? place[u] : 255);
+    for (int u = 0; u < W; ++u)
+      if (js[u] >= 0) atomicAdd(&tcount[js[u]], 1);
   }
 }
 
 template <typename Acc, int W>
 __global__ void __launch_bounds__(kBlock) k_t_fill(const int* __restrict__ list, const int* __restrict__ list_count,
                                                    const int* __restrict__ cols, const double* __restrict__ f,
-                                                   const double* __restrict__ gamma, const uint8_t* __restrict__ tplace,
-                                                   const int* __restrict__ toff, TEntry* __restrict__ tent) {
+                                                   const double* __restrict__ gamma, int* __restrict__ toff,
+                                                   TEntry* __restrict__ tent) {
   const int m = *list_count;
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) {
     const int i = list[t];
@@ -220,7 +218,7 @@ __global__ void __launch_bounds__(kBlock) k_t_fill(const int* __restrict__ list,
     for (int u = 0; u < W; ++u) {
       const int j = cols[(size_t)i * W + u];
       if (j < 0) continue;
-      const int pos = toff[j] + tplace[(size_t)i * W + u];
+      const int pos = atomicAdd(&toff[j], 1);
       // the term f~_ij Gamma_i as the gather forms it (exact in a double
       // for the fp32 product of the mixed precision)
       const double term = (double)mul_acc<Acc>(f[(size_t)i * W + u], gi);
@@ -234,7 +232,7 @@ __global__ void __launch_bounds__(kBlock) k_apply_t(Consts c, int n, const int* 
                                                     const int* __restrict__ n_gamma_dev,
                                                     const double* __restrict__ gamma,
                                                     const uint8_t* __restrict__ diffused,
-                                                    const int* __restrict__ tcount, const int* __restrict__ toff,
+                                                    int* __restrict__ tcount, const int* __restrict__ toff,
                                                     const TEntry* __restrict__ tent, const double* __restrict__ fii,
                                                     double* __restrict__ dgamma, double* __restrict__ gamma_out,
                                                     double dt, const double* __restrict__ dt_dev,
@@ -246,11 +244,13 @@ __global__ void __launch_bounds__(kBlock) k_apply_t(Consts c, int n, const int* 
   for (long jj = (long)blockIdx.x * blockDim.x + threadIdx.x; jj < n; jj += (long)gridDim.x * blockDim.x) {
     const int j = (int)jj;
     const int cnt = tcount[j];
+    if (cnt) tcount[j] = 0;  // clear for the next application
     widest = cnt > widest ? cnt : widest;
     const bool self_src = j < n_gamma && diffused[j];
     const double gj = j < n_gamma ? gamma[j] : 0.0;
     const Acc selfv = self_src ? mul_acc<Acc>(fii[j], gj) : Acc(0);
-    const int4* rec = reinterpret_cast<const int4*>(tent) + toff[j];
+    // k_t_fill moved the offset to the end of the list
+    const int4* rec = reinterpret_cast<const int4*>(tent) + (toff[j] - cnt);
     Acc acc = Acc(0);
     bool self_done = !self_src;
     if (cnt <= 8) {
@@ -313,30 +313,29 @@ __global__ void __launch_bounds__(kBlock) k_apply_t(Consts c, int n, const int* 
 cudaError_t apply_transposed_dev(const Consts& c, int n_bound, const int* n_dev, int n_gamma, const int* n_gamma_dev,
                                  const double* gamma, const uint8_t* diffused, const int* list, const int* list_count,
                                  const int* cols, const double* f, const double* fii, int* tcount, int* toff,
-                                 uint8_t* tplace, void* tent, int* scan_tmp, DevStats* ds, double* dgamma,
-                                 double* gamma_out, double dt, const double* dt_dev, cudaStream_t s) {
+                                 void* tent, int* scan_tmp, DevStats* ds, double* dgamma, double* gamma_out, double dt,
+                                 const double* dt_dev, cudaStream_t s) {
   if (n_bound <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(tcount, 0, sizeof(int) * (size_t)n_bound, s);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   const int blocks = (int)(((long)n_bound + kBlock - 1) / kBlock);
   if (c.order == 2)
-    k_t_claim<12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, tcount, tplace);
+    k_t_count<12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, tcount);
   else
-    k_t_claim<8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, tcount, tplace);
+    k_t_count<8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, tcount);
   note_launch();
   if ((e = scan_exclusive_i32_dev(tcount, toff, n_bound, n_dev, scan_tmp, s)) != cudaSuccess) return e;
   TEntry* te = static_cast<TEntry*>(tent);
   const bool mixed = c.precision == VRM_PREC_MIXED;
   if (c.order == 2) {
     if (mixed)
-      k_t_fill<float, 12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, gamma, tplace, toff, te);
+      k_t_fill<float, 12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, gamma, toff, te);
     else
-      k_t_fill<double, 12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, gamma, tplace, toff, te);
+      k_t_fill<double, 12><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, gamma, toff, te);
   } else {
     if (mixed)
-      k_t_fill<float, 8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, gamma, tplace, toff, te);
+      k_t_fill<float, 8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, gamma, toff, te);
     else
-      k_t_fill<double, 8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, gamma, tplace, toff, te);
+      k_t_fill<double, 8><<<blocks, kBlock, 0, s>>>(list, list_count, cols, f, gamma, toff, te);
   }
   note_launch();
   const int tb = c.apply_block;

@@ -382,14 +382,14 @@ cudaError_t apply_gather(const Consts& c, int n, int n_gamma, const double* gamm
                          const int* nbr_count, const int* nbr_idx, const int* cols, const double* f, const double* fii,
                          const int* order, double* dgamma, double* gamma_out, double dt, cudaStream_t s);
 // The step's application: the stencils of the listed (diffused) particles
-// transposed into a CSR by target (tcount[n_bound], toff[n_bound + 1],
-// tplace[n_bound x w] bytes, tent n_bound x w records of 16 bytes), then the
-// same sums as apply_gather.
+// transposed into a CSR by target (tcount[n_bound], all 0 on entry and left
+// so; toff[n_bound + 1]; tent n_bound x w records of 16 bytes), then the same
+// sums as apply_gather.
 cudaError_t apply_transposed_dev(const Consts& c, int n_bound, const int* n_dev, int n_gamma, const int* n_gamma_dev,
                                  const double* gamma, const uint8_t* diffused, const int* list, const int* list_count,
                                  const int* cols, const double* f, const double* fii, int* tcount, int* toff,
-                                 uint8_t* tplace, void* tent, int* scan_tmp, DevStats* ds, double* dgamma,
-                                 double* gamma_out, double dt, const double* dt_dev, cudaStream_t s);
+                                 void* tent, int* scan_tmp, DevStats* ds, double* dgamma, double* gamma_out, double dt,
+                                 const double* dt_dev, cudaStream_t s);
 cudaError_t apply_gather_dev(const Consts& c, int n_bound, const int* n_dev, int n_gamma, const int* n_gamma_dev,
                              const double* gamma, const uint8_t* diffused, const int* nbr_count, const int* nbr_idx,
                              const int* cols, const double* f, const double* fii, const int* order, double* dgamma,
