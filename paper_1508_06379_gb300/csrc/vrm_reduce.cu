@@ -145,26 +145,32 @@ __global__ void k_absmax(const double* __restrict__ g, int n, const int* __restr
 // threads of the last block: inclusive scan of the 128-bit bucket sums, then
 // the first bucket whose running sum exceeds the budget.
 __device__ void choose_digit(ReduceState* st, double c_bound, int pass) {
-  __shared__ unsigned long long s_lo[256], s_hi[256];
+  __shared__ unsigned long long s_lo[8], s_hi[8];
   __shared__ int s_sel;
-  const int b = threadIdx.x;
+  const int b = threadIdx.x;  // 256 threads, one per bucket
   const u128 v = limbs_value(st->hist[b]);
   const unsigned long long cnt = __ldcg(&st->hist[b][3]);
-  // inclusive scan (Hillis-Steele over 256 entries in shared memory)
+  // inclusive scan: shuffles within each warp, then the warps' totals
   u128 acc = v;
-  s_lo[b] = (unsigned long long)acc;
-  s_hi[b] = (unsigned long long)(acc >> 64);
-  __syncthreads();
-  for (int o = 1; o < 256; o <<= 1) {
-    u128 add = 0;
-    if (b >= o) add = ((u128)s_hi[b - o] << 64) | (u128)s_lo[b - o];
-    __syncthreads();
-    acc += add;
-    s_lo[b] = (unsigned long long)acc;
-    s_hi[b] = (unsigned long long)(acc >> 64);
-    __syncthreads();
+  const int lane = b & 31, w = b >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long lo = __shfl_up_sync(0xffffffffu, (unsigned long long)acc, o);
+    const unsigned long long hi = __shfl_up_sync(0xffffffffu, (unsigned long long)(acc >> 64), o);
+    if (lane >= o) acc += ((u128)hi << 64) | (u128)lo;
   }
-  const u128 total = ((u128)s_hi[255] << 64) | (u128)s_lo[255];
+  if (lane == 31) {
+    s_lo[w] = (unsigned long long)acc;
+    s_hi[w] = (unsigned long long)(acc >> 64);
+  }
+  __syncthreads();
+  u128 total = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const u128 wk = ((u128)s_hi[k] << 64) | (u128)s_lo[k];
+    if (k < w) acc += wk;
+    total += wk;
+  }
   u128 tau;
   if (pass == 0) {
     tau = dbl_floor_to_u128(__dmul_rn(c_bound, u128_to_dbl(total)));
@@ -217,6 +223,8 @@ __device__ void choose_digit(ReduceState* st, double c_bound, int pass) {
 // binade of |Gamma|, a small fraction), and passes 3 to 7 read that list
 // only.  The sums are exact integers, so the list's order (atomic appends)
 // does not matter.
+constexpr int kReduceUnroll = 4;  // particles per lane whose loads one pass issues together
+
 __global__ void __launch_bounds__(256) k_reduce_pass(const double* __restrict__ g, int n, const int* __restrict__ n_dev,
                                                      ReduceState* __restrict__ st, double c_bound, int pass,
                                                      int* __restrict__ sub) {
@@ -236,68 +244,84 @@ __global__ void __launch_bounds__(256) k_reduce_pass(const double* __restrict__ 
     const int lane = threadIdx.x & 31;
     // whole warps step through the particles so that lanes holding the same
     // byte merge their exact limb sums before one shared atomic per byte (the
-    // leading bytes are shared by nearly all particles)
-    const long stride = (long)gridDim.x * blockDim.x;
-    for (long base = (long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-      const long i = base + lane;
-      bool pending = false;
-      int d = 0, idx = 0;
-      unsigned long long l0 = 0, l1 = 0, l2 = 0;
-      if (i < n) {
-        idx = pass >= 3 ? sub[i] : (int)i;
-        const unsigned long long key = (unsigned long long)__double_as_longlong(g[idx]) & 0x7FFFFFFFFFFFFFFFull;
-        if (pass == 0 || (key >> (shift + 8)) == prefix) {
-          pending = true;
-          d = (int)((key >> shift) & 0xFF);
-          const u128 q = q_of_key(key, E);
-          l0 = (unsigned long long)(q & 0xFFFFFFFFull);
-          l1 = (unsigned long long)((q >> 32) & 0xFFFFFFFFull);
-          l2 = (unsigned long long)(q >> 64);
-        }
-      }
-      unsigned todo = __ballot_sync(0xffffffffu, pending);
-      if (pass == 2 && todo) {
-        // list the matches for the later passes (warp-aggregated append)
-        const int lead = __ffs(todo) - 1;
-        int slot0 = 0;
-        if (lane == lead) slot0 = atomicAdd(&st->n_sub, __popc(todo));
-        slot0 = __shfl_sync(0xffffffffu, slot0, lead);
-        if (pending) sub[slot0 + __popc(todo & ((1u << lane) - 1u))] = idx;
-      }
-      if (pass > 0) {
-        // bytes after the first are spread over many values: one shared
-        // atomic per lane and limb (equal bytes in a warp serialise, rarely)
-        if (pending) {
-          if (l0) atomicAdd(&h[d][0], l0);
-          if (l1) atomicAdd(&h[d][1], l1);
-          if (l2) atomicAdd(&h[d][2], l2);
-          atomicAdd(&h[d][3], 1ull);
-        }
-        todo = 0;
-      }
-      while (todo) {
-        const int leader = __ffs(todo) - 1;
-        const int dl = __shfl_sync(0xffffffffu, d, leader);
-        const bool mine = pending && d == dl;
-        const unsigned peers = __ballot_sync(0xffffffffu, mine);
-        // 16-bit halves of the 32-bit limbs: sums of 32 lanes stay below 2^21
-        unsigned long long sum[3];
-        const unsigned long long lim[3] = {l0, l1, l2};
+    // leading bytes are shared by nearly all particles); each warp takes
+    // kReduceUnroll x 32 particles at a time, their loads issued together
+    const long stride = (long)gridDim.x * blockDim.x * kReduceUnroll;
+    for (long base = ((long)blockIdx.x * blockDim.x + (threadIdx.x & ~31)) * kReduceUnroll; base < n;
+         base += stride) {
+      int idxs[kReduceUnroll];
+      unsigned long long keys[kReduceUnroll];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const unsigned lo = mine ? (unsigned)(lim[k] & 0xFFFFu) : 0u;
-          const unsigned hi = mine ? (unsigned)(lim[k] >> 16) : 0u;
-          sum[k] = (unsigned long long)__reduce_add_sync(0xffffffffu, lo) +
-                   ((unsigned long long)__reduce_add_sync(0xffffffffu, hi) << 16);
+      for (int u = 0; u < kReduceUnroll; ++u) {
+        const long i = base + u * 32 + lane;
+        idxs[u] = -1;
+        keys[u] = 0;
+        if (i < n) {
+          idxs[u] = pass >= 3 ? sub[i] : (int)i;
+          keys[u] = (unsigned long long)__double_as_longlong(g[idxs[u]]) & 0x7FFFFFFFFFFFFFFFull;
         }
-        if (lane == leader) {
-          if (sum[0]) atomicAdd(&h[dl][0], sum[0]);
-          if (sum[1]) atomicAdd(&h[dl][1], sum[1]);
-          if (sum[2]) atomicAdd(&h[dl][2], sum[2]);
-          atomicAdd(&h[dl][3], (unsigned long long)__popc(peers));
+      }
+#pragma unroll
+      for (int u = 0; u < kReduceUnroll; ++u) {
+        bool pending = false;
+        int d = 0;
+        const int idx = idxs[u];
+        unsigned long long l0 = 0, l1 = 0, l2 = 0;
+        if (idx >= 0) {
+          const unsigned long long key = keys[u];
+          if (pass == 0 || (key >> (shift + 8)) == prefix) {
+            pending = true;
+            d = (int)((key >> shift) & 0xFF);
+            const u128 q = q_of_key(key, E);
+            l0 = (unsigned long long)(q & 0xFFFFFFFFull);
+            l1 = (unsigned long long)((q >> 32) & 0xFFFFFFFFull);
+            l2 = (unsigned long long)(q >> 64);
+          }
         }
-        if (mine) pending = false;
-        todo &= ~peers;
+        unsigned todo = __ballot_sync(0xffffffffu, pending);
+        if (pass == 2 && todo) {
+          // list the matches for the later passes (warp-aggregated append)
+          const int lead = __ffs(todo) - 1;
+          int slot0 = 0;
+          if (lane == lead) slot0 = atomicAdd(&st->n_sub, __popc(todo));
+          slot0 = __shfl_sync(0xffffffffu, slot0, lead);
+          if (pending) sub[slot0 + __popc(todo & ((1u << lane) - 1u))] = idx;
+        }
+        if (pass > 0) {
+          // bytes after the first are spread over many values: one shared
+          // atomic per lane and limb (equal bytes in a warp serialise, rarely)
+          if (pending) {
+            if (l0) atomicAdd(&h[d][0], l0);
+            if (l1) atomicAdd(&h[d][1], l1);
+            if (l2) atomicAdd(&h[d][2], l2);
+            atomicAdd(&h[d][3], 1ull);
+          }
+          todo = 0;
+        }
+        while (todo) {
+          const int leader = __ffs(todo) - 1;
+          const int dl = __shfl_sync(0xffffffffu, d, leader);
+          const bool mine = pending && d == dl;
+          const unsigned peers = __ballot_sync(0xffffffffu, mine);
+          // 16-bit halves of the 32-bit limbs: sums of 32 lanes stay below 2^21
+          unsigned long long sum[3];
+          const unsigned long long lim[3] = {l0, l1, l2};
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const unsigned lo = mine ? (unsigned)(lim[k] & 0xFFFFu) : 0u;
+            const unsigned hi = mine ? (unsigned)(lim[k] >> 16) : 0u;
+            sum[k] = (unsigned long long)__reduce_add_sync(0xffffffffu, lo) +
+                     ((unsigned long long)__reduce_add_sync(0xffffffffu, hi) << 16);
+          }
+          if (lane == leader) {
+            if (sum[0]) atomicAdd(&h[dl][0], sum[0]);
+            if (sum[1]) atomicAdd(&h[dl][1], sum[1]);
+            if (sum[2]) atomicAdd(&h[dl][2], sum[2]);
+            atomicAdd(&h[dl][3], (unsigned long long)__popc(peers));
+          }
+          if (mine) pending = false;
+          todo &= ~peers;
+        }
       }
     }
   }
@@ -310,10 +334,14 @@ __global__ void __launch_bounds__(256) k_reduce_pass(const double* __restrict__ 
         atomicAdd(&st->hist[b][2], h[b][2]);
         atomicAdd(&st->hist[b][3], h[b][3]);
       }
-  // last block to finish chooses the byte (histogram complete)
-  __threadfence();
+  // last block to finish chooses the byte (histogram complete): the block's
+  // atomics are ordered before its ticket by the barrier and one fence of
+  // the thread that takes the ticket (the pattern of a grid barrier)
   __syncthreads();
-  if (threadIdx.x == 0) last = atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&st->blocks_done, 1u) == gridDim.x - 1;
+  }
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -516,7 +544,7 @@ cudaError_t reduce_select_dev(const double* gamma, int n_bound, const int* n_dev
                               ReduceState* st, uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds,
                               cudaStream_t s, int* dflag_ts, int* tie_ts) {
   int blocks = n_bound > 0 ? (n_bound + kBlock - 1) / kBlock : 1;
-  int pblocks = blocks < 2 * sm_count() ? blocks : 2 * sm_count();
+  int pblocks = blocks < 4 * sm_count() ? blocks : 4 * sm_count();
   k_absmax<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, ds, c_bound); note_launch();
   for (int pass = 0; pass < 3; ++pass) {
     // pass 2 lists its matches in tie_rank (free until the tie scan)
