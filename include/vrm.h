@@ -557,8 +557,8 @@ vrm_status vrm_remove_close(vrm_ctx* ctx, const double* x, const double* y, cons
  * library holds until the process exits; it serves clouds of at most
  * VRM_NOALLOC_MAX_N particles and returns VRM_ERR_CAPACITY above that.
  * The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress, once per device, with that device current); make
- * that first call before any stream capture.  Every call shares the array
+ * (cudaGetSymbolAddress, once per device, with that device current).  Every
+ * call shares the array
  * and overwrites what the previous call left there (the counters it needs
  * at zero are cleared on the stream at the start of each call), so calls
  * whose work overlaps on the GPU (two streams, or two host threads) race:
