@@ -573,6 +573,22 @@ def traffic_for(kernel):
         return None
 
 
+def binding_for(kernel):
+    """The kernel's busiest resources from its committed ncu capture (FP64
+    pipe and issue slots as fractions of their peaks), if it was taken on the
+    current source of that kernel (else None)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        ent = json.load(open(p))[kernel]
+        src = open(os.path.join(ROOT, "paper_1508_06379_gb300", "csrc", ent["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest() != ent["source_sha256"]:
+            return None
+        return ent.get("binding")
+    except Exception:
+        return None
+
+
 def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1, peaks=None, lp_block=128, rows=False):
     m = 9 if order == 2 else 5
     if stage in ("lp_small", "lp_full"):
@@ -595,8 +611,12 @@ def roofline_for(stage, ms, stats, n, order=1, lp_fp64_pivots=1, peaks=None, lp_
         else:
             peak = FP64_PEAK_DERIVED_GFLOPS / 1000.0
             src = "derived: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2.07 GHz"
-        return {"kernel": kern, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": traffic_for(kern) if order == 1 else None, "peak_source": src}
+        out = {"kernel": kern, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+               "frac": ach / peak, "traffic": traffic_for(kern) if order == 1 else None, "peak_source": src}
+        binding = binding_for(kern) if order == 1 else None
+        if binding:
+            out["binding"] = binding
+        return out
     hbm = None
     try:
         hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]
