@@ -214,16 +214,38 @@ __global__ void __launch_bounds__(kBlock) k_t_fill(const int* __restrict__ list,
   for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (long)gridDim.x * blockDim.x) {
     const int i = list[t];
     const double gi = gamma[i];
+    // the stencil row as vectors (rows of 8 or 12 entries start on 16-byte
+    // boundaries), every place requested before any is used (their round
+    // trips overlap), then the records
+    const int4* cr = reinterpret_cast<const int4*>(cols + (size_t)i * W);
+    const double2* fr = reinterpret_cast<const double2*>(f + (size_t)i * W);
+    int js[W];
+    double fs[W];
 #pragma unroll
-    for (int u = 0; u < W; ++u) {
-      const int j = cols[(size_t)i * W + u];
-      if (j < 0) continue;
-      const int pos = atomicAdd(&toff[j], 1);
-      // the term f~_ij Gamma_i as the gather forms it (exact in a double
-      // for the fp32 product of the mixed precision)
-      const double term = (double)mul_acc<Acc>(f[(size_t)i * W + u], gi);
-      reinterpret_cast<int4*>(tent)[pos] = make_int4(i, 0, __double2loint(term), __double2hiint(term));
+    for (int q = 0; q < W / 4; ++q) {
+      const int4 a = cr[q];
+      js[4 * q] = a.x;
+      js[4 * q + 1] = a.y;
+      js[4 * q + 2] = a.z;
+      js[4 * q + 3] = a.w;
     }
+#pragma unroll
+    for (int q = 0; q < W / 2; ++q) {
+      const double2 b = fr[q];
+      fs[2 * q] = b.x;
+      fs[2 * q + 1] = b.y;
+    }
+    int pos[W];
+#pragma unroll
+    for (int u = 0; u < W; ++u) pos[u] = js[u] >= 0 ? atomicAdd(&toff[js[u]], 1) : 0;
+#pragma unroll
+    for (int u = 0; u < W; ++u)
+      if (js[u] >= 0) {
+        // the term f~_ij Gamma_i as the gather forms it (exact in a double
+        // for the fp32 product of the mixed precision)
+        const double term = (double)mul_acc<Acc>(fs[u], gi);
+        reinterpret_cast<int4*>(tent)[pos[u]] = make_int4(i, 0, __double2loint(term), __double2hiint(term));
+      }
   }
 }
 
