@@ -1063,13 +1063,42 @@ __global__ void __launch_bounds__(128, 3) k_lp_small32(Consts c, const double* _
 constexpr int kLpWsThreads = 32 * (4 + 2);
 constexpr int kLpWsThreadsWide = 32 * (8 + 4);
 
-// Block barrier of the warp-specialised LP (named barrier 1 over every
-// thread of the block): the two roles run their own loops with the same
-// number of rounds and meet here once per round.
+// Hand-over of the warp-specialised LP: kWsSlots buffers, and per buffer two
+// named barriers over every thread of the block.  FULL (1 + slot): the pivot
+// warps arrive once they have written the batch, the FP64 warps wait there
+// before reading it; EMPTY (1 + kWsSlots + slot): the FP64 warps arrive once
+// they have read it, the pivot warps wait there before writing the slot
+// again.  With three buffers the pivot warps may run two batches ahead, so
+// that neither role waits for the other's slowest batch.  Both roles count
+// the same rounds, and the last arrival on each EMPTY barrier that no later
+// round waits for is left out, so every barrier generation completes.
+constexpr int kWsSlots = 3;
+// (immediate barrier numbers, so that the block reserves barriers 1 to 6
+// only; the switch is uniform over the warp)
+#define VRM_WS_BAR(op, id) asm volatile("bar." op " " #id ", %0;" ::"n"(NT) : "memory")
 template <int NT>
-__device__ __forceinline__ void ws_barrier() {
-  asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+__device__ __forceinline__ void ws_arrive(int id) {
+  switch (id) {
+    case 1: VRM_WS_BAR("arrive", 1); break;
+    case 2: VRM_WS_BAR("arrive", 2); break;
+    case 3: VRM_WS_BAR("arrive", 3); break;
+    case 4: VRM_WS_BAR("arrive", 4); break;
+    case 5: VRM_WS_BAR("arrive", 5); break;
+    default: VRM_WS_BAR("arrive", 6); break;
+  }
 }
+template <int NT>
+__device__ __forceinline__ void ws_sync(int id) {
+  switch (id) {
+    case 1: VRM_WS_BAR("sync", 1); break;
+    case 2: VRM_WS_BAR("sync", 2); break;
+    case 3: VRM_WS_BAR("sync", 3); break;
+    case 4: VRM_WS_BAR("sync", 4); break;
+    case 5: VRM_WS_BAR("sync", 5); break;
+    default: VRM_WS_BAR("sync", 6); break;
+  }
+}
+#undef VRM_WS_BAR
 
 template <int M, int W, int PW, int FW, int MINB>
 __global__ void __launch_bounds__(32 * (PW + FW), MINB) k_lp_small32_ws(
@@ -1091,18 +1120,20 @@ __global__ void __launch_bounds__(32 * (PW + FW), MINB) k_lp_small32_ws(
   const bool pivot_warp = warp < kLpPivotWarps;
   // hand-over of a batch: particle, basis (4 bits per row) | pivots << 20 |
   // code << 27 | 1 << 30 (valid), and the sorted column indices
-  __shared__ int s_i[2][kLpBatch];
-  __shared__ int s_meta[2][kLpBatch];
-  __shared__ int s_cj[2][8][kLpBatch];
+  __shared__ int s_i[kWsSlots][kLpBatch];
+  __shared__ int s_meta[kWsSlots][kLpBatch];
+  __shared__ int s_cj[kWsSlots][8][kLpBatch];
   const long nchunks = ((long)m + kLpBatch - 1) / kLpBatch;
-  // round r pivots chunk blockIdx.x + r gridDim.x and finishes the chunk of
-  // round r - 1; the last round only finishes
+  // the block's batches: chunks blockIdx.x + r gridDim.x, r < rounds; the
+  // pivot warps take batch r into slot r mod kWsSlots, the FP64 warps finish
+  // it from there
+  const long rounds = (long)blockIdx.x < nchunks ? (nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   if (pivot_warp) {
-    for (long r = 0;; ++r) {
+    int buf = 0;
+    for (long r = 0; r < rounds; ++r) {
       const long chunk = (long)blockIdx.x + r * gridDim.x;
-      if (chunk - gridDim.x >= nchunks) break;
-      const int buf = (int)(r & 1);
-      if (chunk < nchunks) {
+      if (r >= kWsSlots) ws_sync<kThreads>(1 + kWsSlots + buf);  // batch r - kWsSlots read
+      {
         const int slot = warp * 32 + (int)lane;
         const long t = chunk * kLpBatch + slot;
         const bool active = t < m;
@@ -1140,14 +1171,14 @@ __global__ void __launch_bounds__(32 * (PW + FW), MINB) k_lp_small32_ws(
           n_retry += (lane == 0) ? __popc(rb) : 0;
         }
       }
-      ws_barrier<kThreads>();
+      ws_arrive<kThreads>(1 + buf);  // batch r written
+      buf = buf + 1 == kWsSlots ? 0 : buf + 1;
     }
   } else {
-    for (long r = 0;; ++r) {
-      const long chunk = (long)blockIdx.x + r * gridDim.x;
-      if (chunk - gridDim.x >= nchunks) break;
-      const int pb = (int)(r & 1) ^ 1;
-      if (r > 0) {
+    int pb = 0;
+    for (long d = 0; d < rounds; ++d) {
+      ws_sync<kThreads>(1 + pb);  // batch d written
+      {
 #pragma unroll 1
         for (int slot = (warp - kLpPivotWarps) * 32 + (int)lane; slot < kLpBatch; slot += 32 * kLpFinishWarps) {
           const int meta = s_meta[pb][slot];
@@ -1180,7 +1211,8 @@ __global__ void __launch_bounds__(32 * (PW + FW), MINB) k_lp_small32_ws(
           }
         }
       }
-      ws_barrier<kThreads>();
+      if (d + kWsSlots < rounds) ws_arrive<kThreads>(1 + kWsSlots + pb);  // batch d read
+      pb = pb + 1 == kWsSlots ? 0 : pb + 1;
     }
   }
   flush_stats(ds, tl.ok, tl.none, tl.maxpiv, tl.ratio, false, tl.solved, tl.pivots);
