@@ -1051,8 +1051,8 @@ __global__ void __launch_bounds__(128, 3) k_lp_small32(Consts c, const double* _
 // The same LPs with the work split by warps: per block, PW warps take the
 // columns and the certified binary32 pivots of 32 LPs each, and FW warps
 // take the FP64 part (basis offsets, LU solve, certificate, stencil) of the
-// LPs the pivot warps finished in the round before, handed over in shared
-// memory (double-buffered, one block barrier per round).  The FP64 pipe then
+// LPs the pivot warps finished before, handed over in shared memory (three
+// buffers, a full and an empty named barrier each).  The FP64 pipe then
 // works on one batch while the binary32 and integer pipes work on the next,
 // instead of every warp alternating between the two phases.  Results are
 // those of k_lp_small32 bit for bit (the same device functions in the same
