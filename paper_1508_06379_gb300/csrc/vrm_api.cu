@@ -624,8 +624,10 @@ cudaError_t enqueue_front(vrm_ctx* ctx, double* x, double* y, int cap, const dou
   const int* n_dev = &s.st->n;
   cudaError_t e;
   if ((e = mark(ctx, VRM_STAGE_REDUCE, st)) != cudaSuccess) return e;
+  // the growth control's first pass also takes the bounding box of the
+  // particles for the grid build below
   if ((e = reduce_select_dev(gamma, cap, n_dev, c.c_bound, diffused, s.rstate, s.tie_flag, s.tie_rank, s.scan_tmp,
-                             s.ds, st, s.dflag_ts, s.tie_ts)) != cudaSuccess)
+                             s.ds, st, s.dflag_ts, s.tie_ts, x, y, s.bbox)) != cudaSuccess)
     return e;
   if ((e = compact_flags_dev(diffused, cap, n_dev, s.dlist, s.counters + 0, s.pos, s.scan_tmp, st, s.dflag_ts)) !=
       cudaSuccess)
@@ -633,7 +635,7 @@ cudaError_t enqueue_front(vrm_ctx* ctx, double* x, double* y, int cap, const dou
   if ((e = mark(ctx, VRM_STAGE_GRID, st)) != cudaSuccess) return e;
   if ((e = grid_build_dev(x, y, cap, n_dev, c.Rh, c.lo2, c.hi2, s.ncell_cap, s.grid, s.cell_key, s.cell_rank,
                           s.cell_count, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.bbox, s.scan_tmp,
-                          st, s.cell_ts, true)) != cudaSuccess)
+                          st, s.cell_ts, true, true)) != cudaSuccess)
     return e;
   if ((e = search_masks_list_dev(c, s.grid, s.cell_start, s.sorted_xy, s.sorted_loc, s.sorted_idx, s.cell_key,
                                  s.cell_rank, s.dlist, s.counters + 0, cap, s.mask, st)) != cudaSuccess)

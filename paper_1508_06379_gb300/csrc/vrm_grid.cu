@@ -378,12 +378,14 @@ cudaError_t grid_build_dev(const double* x, const double* y, int n_bound, const 
                            double hi2, int ncell_cap, Grid* g, int* cell_key, int* cell_rank, int* cell_count,
                            int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx,
                            unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s, int* cell_ts,
-                           bool bbox_ready) {
-  if (!bbox_ready) {
-    k_bbox_init<<<1, 1, 0, s>>>(bbox_tmp);
-    note_launch();
+                           bool bbox_ready, bool bbox_done) {
+  if (!bbox_done) {
+    if (!bbox_ready) {
+      k_bbox_init<<<1, 1, 0, s>>>(bbox_tmp);
+      note_launch();
+    }
+    k_bbox<<<stream_grid(n_bound, 4), kBlock, 0, s>>>(x, y, n_bound, n_dev, bbox_tmp); note_launch();
   }
-  k_bbox<<<stream_grid(n_bound, 4), kBlock, 0, s>>>(x, y, n_bound, n_dev, bbox_tmp); note_launch();
   k_grid_finalize<<<1, 1, 0, s>>>(bbox_tmp, n_bound, n_dev, Rh, lo2, hi2, ncell_cap, g); note_launch();
   return grid_bin_dev(x, y, n_bound, n_dev, ncell_cap, g, cell_key, cell_rank, cell_count, cell_start, sorted_xy,
                       sorted_loc, sorted_idx, scan_tmp, s, cell_ts);

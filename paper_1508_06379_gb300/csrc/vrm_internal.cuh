@@ -215,9 +215,11 @@ cudaError_t grid_build_dev(const double* x, const double* y, int n_bound, const 
                            double hi2, int ncell_cap, Grid* g, int* cell_key, int* cell_rank, int* cell_count,
                            int* cell_start, double2* sorted_xy, float2* sorted_loc, int* sorted_idx,
                            unsigned long long* bbox_tmp, int* scan_tmp, cudaStream_t s, int* cell_ts = nullptr,
-                           bool bbox_ready = false);
+                           bool bbox_ready = false, bool bbox_done = false);
 // Sets the bounding-box accumulators to their initial values (every grid
-// build leaves them so; a build with bbox_ready = true relies on it).
+// build leaves them so; a build with bbox_ready = true relies on it).  A
+// build with bbox_done = true finds the box of its particles already
+// accumulated (reduce_select_dev with x, y and bbox) and skips k_bbox.
 cudaError_t grid_bbox_reset(unsigned long long* bbox_tmp, cudaStream_t s);
 // cell_ts (optional, ncell_cap / kScanTile + 2 ints): the binning kernel
 // accumulates the tile sums of the cell counts there, and the scan of the
@@ -278,9 +280,13 @@ size_t scan_tmp_ints(int n);
 // Growth control over *n_dev (<= n_bound) particles: diffused[i] for i < n,
 // 0 on [n, n_bound).  dflag_ts and tie_ts (n_bound / kScanTile + 2 ints
 // each) receive the tile sums of diffused and of the tie flags.
+// With x, y and bbox given, the first pass over Gamma also accumulates the
+// bounding box of the same particles into bbox, as k_bbox does (for a grid
+// build with bbox_done = true).
 cudaError_t reduce_select_dev(const double* gamma, int n_bound, const int* n_dev, double c_bound, uint8_t* diffused,
                               ReduceState* st, uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds,
-                              cudaStream_t s, int* dflag_ts, int* tie_ts);
+                              cudaStream_t s, int* dflag_ts, int* tie_ts, const double* x = nullptr,
+                              const double* y = nullptr, unsigned long long* bbox = nullptr);
 
 // vrm_search.cu
 cudaError_t search_all(const Consts& c, const Grid* g, const int* cell_start, const double2* sorted_xy,

@@ -69,12 +69,29 @@ __device__ __forceinline__ u128 limbs_value(const unsigned long long* h) {
 // circulation, or a bound of at least ||Gamma||_1).  st->blocks_done is 0
 // on entry (after allocation and after every pass).
 __global__ void k_absmax(const double* __restrict__ g, int n, const int* __restrict__ n_dev, ReduceState* __restrict__ st,
-                         DevStats* ds, double c_bound) {
+                         DevStats* ds, double c_bound, const double* __restrict__ x, const double* __restrict__ y,
+                         unsigned long long* __restrict__ bb) {
   if (n_dev) n = *n_dev;
   unsigned long long m = 0;
   int bad = 0;
+  // with bb: the bounding box of the same particles, as k_bbox takes it
+  // (ordered bit patterns; a NaN or Inf position flagged)
+  unsigned long long mnx = ~0ull, mxx = 0, mny = ~0ull, mxy = 0;
+  int badxy = 0;
   for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(g[i]) & 0x7FFFFFFFFFFFFFFFull;
+    if (bb) {
+      const double a = x[i], c = y[i];
+      if (!isfinite(a) || !isfinite(c)) {
+        badxy = 1;
+      } else {
+        const unsigned long long oa = ordered_bits(a), oc = ordered_bits(c);
+        mnx = oa < mnx ? oa : mnx;
+        mxx = oa > mxx ? oa : mxx;
+        mny = oc < mny ? oc : mny;
+        mxy = oc > mxy ? oc : mxy;
+      }
+    }
     if (b >= 0x7FF0000000000000ull) {  // Inf or NaN
       bad = 1;
       continue;
@@ -87,6 +104,47 @@ __global__ void k_absmax(const double* __restrict__ g, int n, const int* __restr
     m = t > m ? t : m;
   }
   bad = __any_sync(0xffffffffu, bad);
+  if (bb) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long t;
+      t = __shfl_xor_sync(0xffffffffu, mnx, o);
+      mnx = t < mnx ? t : mnx;
+      t = __shfl_xor_sync(0xffffffffu, mxx, o);
+      mxx = t > mxx ? t : mxx;
+      t = __shfl_xor_sync(0xffffffffu, mny, o);
+      mny = t < mny ? t : mny;
+      t = __shfl_xor_sync(0xffffffffu, mxy, o);
+      mxy = t > mxy ? t : mxy;
+    }
+    badxy = __any_sync(0xffffffffu, badxy);
+    // one atomic per block and quantity
+    __shared__ unsigned long long w_bb[4][32];
+    __shared__ int w_badxy[32];
+    const int wb = threadIdx.x >> 5, nwb = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      w_bb[0][wb] = mnx;
+      w_bb[1][wb] = mxx;
+      w_bb[2][wb] = mny;
+      w_bb[3][wb] = mxy;
+      w_badxy[wb] = badxy;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < nwb; ++w) {
+        mnx = w_bb[0][w] < mnx ? w_bb[0][w] : mnx;
+        mxx = w_bb[1][w] > mxx ? w_bb[1][w] : mxx;
+        mny = w_bb[2][w] < mny ? w_bb[2][w] : mny;
+        mxy = w_bb[3][w] > mxy ? w_bb[3][w] : mxy;
+        badxy |= w_badxy[w];
+      }
+      if (mnx != ~0ull) atomicMin(&bb[0], mnx);
+      if (mxx) atomicMax(&bb[1], mxx);
+      if (mny != ~0ull) atomicMin(&bb[2], mny);
+      if (mxy) atomicMax(&bb[3], mxy);
+      if (badxy) atomicOr(&bb[4], 1ull);
+    }
+  }
   __shared__ unsigned long long w_m[32];
   __shared__ int w_bad[32];
   __shared__ bool last;
@@ -542,10 +600,11 @@ __global__ void k_reduce_ties(int n, const int* __restrict__ n_dev, const Reduce
 
 cudaError_t reduce_select_dev(const double* gamma, int n_bound, const int* n_dev, double c_bound, uint8_t* diffused,
                               ReduceState* st, uint8_t* tie_flag, int* tie_rank, int* scan_tmp, DevStats* ds,
-                              cudaStream_t s, int* dflag_ts, int* tie_ts) {
+                              cudaStream_t s, int* dflag_ts, int* tie_ts, const double* x, const double* y,
+                              unsigned long long* bbox) {
   int blocks = n_bound > 0 ? (n_bound + kBlock - 1) / kBlock : 1;
   int pblocks = blocks < 4 * sm_count() ? blocks : 4 * sm_count();
-  k_absmax<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, ds, c_bound); note_launch();
+  k_absmax<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, ds, c_bound, x, y, bbox); note_launch();
   for (int pass = 0; pass < 3; ++pass) {
     // pass 2 lists its matches in tie_rank (free until the tie scan)
     k_reduce_pass<<<pblocks, 256, 0, s>>>(gamma, n_bound, n_dev, st, c_bound, pass, tie_rank); note_launch();
