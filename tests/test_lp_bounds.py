@@ -14,7 +14,11 @@ to binary32), replay the same pivots in exact rational arithmetic
 * every binary32 entry lies within its bound of the exact value (the factor
   1.0001 covers the emulated fma's double rounding, at most 2^-53 on top of
   the binary32 rounding the bound accounts for);
-* every certified decision is the exact decision.
+* every certified decision is the exact decision;
+* a row whose eligibility is uncertain is passed over only where, were it
+  eligible, its exact ratio would lie above the exact tie limit (so that the
+  leaving row is the same either way); binary-exact lattice columns, whose
+  exact zeros carry running bounds, exercise that rule.
 """
 from fractions import Fraction
 
@@ -26,6 +30,9 @@ RCP_MUL = f32(3.01) * U
 INIT = f32(1.0)  # scale of the initial conversion bounds (1 in the kernel)
 TP_HI, TP_LO = f32(1.0000001e-9), f32(0.99999994e-9)
 TS_HI, TS_LO = f32(1.0000001e-11), f32(0.99999994e-11)
+TT_HI = f32(1.0000001e-12)
+SAFE = f32(1.25)
+STATS = {"uncertain_rows_passed": 0, "uncertain_rows_eligible": 0}
 M, K = 5, 8
 B = [0, 0, 2, 0, 2]
 
@@ -54,6 +61,30 @@ def columns(rng, R=2.0, r=0.5):
     inv_h32 = f32(inv_h)
     xs = [f32(f32(dx[k]) * inv_h32) for k in range(8)]
     es = [f32(f32(dy[k]) * inv_h32) for k in range(8)]
+    return xi64, eta64, xs, es
+
+
+def lattice_columns(rng, R=2.0, r=0.5):
+    """Eight offsets on the integer lattice of a binary-exact spacing
+    h = 1/64 (one per 45-degree segment where the annulus has one), sorted by
+    distance: the offsets, their products and many tableau entries are exact
+    in binary32, and exact zeros appear after the first pivots."""
+    pts = [(a, b) for a in range(-2, 3) for b in range(-2, 3) if r * r <= a * a + b * b <= R * R]
+    segs = {}
+    for a, b in pts:
+        s_ = int(np.floor(np.arctan2(b, a) / (np.pi / 4))) % 8
+        segs.setdefault(s_, []).append((a, b))
+    chosen = [segs[k][rng.integers(len(segs[k]))] for k in sorted(segs)]
+    while len(chosen) < 8:
+        chosen.append(pts[rng.integers(len(pts))])
+    h = 1.0 / 64
+    dx = np.array([a * h for a, b in chosen])
+    dy = np.array([b * h for a, b in chosen])
+    order = np.argsort(dx * dx + dy * dy, kind="stable")
+    dx, dy = dx[order], dy[order]
+    xi64, eta64 = dx / h, dy / h
+    xs = [f32(f32(dx[k]) * f32(1 / h)) for k in range(8)]
+    es = [f32(f32(dy[k]) * f32(1 / h)) for k in range(8)]
     return xi64, eta64, xs, es
 
 
@@ -118,20 +149,56 @@ def run(xi64, eta64, xs, es, check):
                 check(dx_[k] >= Fraction(-1, 10 ** 9))
         a = [T[r][q] for r in range(M)]
         ea = [E[r][q] for r in range(M)]
-        elig = []
+        elig, amb = [], []
         for r in range(M):
-            mg = f32(1.25) * ea[r]
+            mg = SAFE * ea[r]
+            mb = SAFE * Eb[r]
+            nzr = rhs[r] > TS_HI + mb
             if a[r] > TP_HI + mg:
                 elig.append(r)
-                mb = f32(1.25) * Eb[r]
-                if not (rhs[r] > TS_HI + mb or rhs[r] < TS_LO - mb):
+                if not (nzr or rhs[r] < TS_LO - mb):
                     return it
             elif not a[r] < TP_LO - mg:
-                return it
+                # eligibility uncertain: the LP goes on only if the basic
+                # value is certainly positive (and the ratio bound below holds)
+                if not nzr:
+                    return it
+                amb.append(r)
         for r in range(M):
-            check((Tx[r][q] > Fraction(1, 10 ** 9)) == (r in elig))
+            if r not in amb:
+                check((Tx[r][q] > Fraction(1, 10 ** 9)) == (r in elig))
         if not elig:
             return it
+        if amb:
+            # the largest possible tie limit from the binary32 ratio intervals
+            # of the certainly eligible rows, as the kernel bounds it
+            thhi = f32(3.0e38)
+            for r in elig:
+                nz = rhs[r] > TS_HI + SAFE * Eb[r]
+                inv = f32(f32(1) / a[r])
+                ratio = f32(rhs[r] * inv) if nz else f32(0)
+                g = f32(ea[r] * inv)
+                gg = fma32(f32(2) * g, g, g)
+                if nz and not g <= 0.5:
+                    return it
+                er = f32(SAFE * fma32(RCP_MUL, ratio, f32(fma32(gg, f32(rhs[r] + Eb[r]), Eb[r]) * inv))) if nz else f32(0)
+                thhi = min(thhi, f32(ratio + er))
+            l1 = fma32(TT_HI, max(thhi, f32(1)), thhi)
+            limhi = fma32(f32(4) * U, abs(l1), l1)
+            exact_elig = [r for r in elig]
+            best = min((rx[r] if rx[r] > Fraction(1, 10 ** 11) else Fraction(0)) / Tx[r][q] for r in exact_elig)
+            lim_exact = best + Fraction(1, 10 ** 12) * max(best, 1)
+            for r in amb:
+                num = f32(rhs[r] - SAFE * Eb[r])
+                lim = f32(limhi * f32(a[r] + SAFE * ea[r]))
+                if not f32(num * f32(1 - 8 * U)) > lim:
+                    return it
+                STATS["uncertain_rows_passed"] += 1
+                # were it eligible, its ratio could neither be the minimum
+                # nor tie with it
+                if Tx[r][q] > Fraction(1, 10 ** 9):
+                    STATS["uncertain_rows_eligible"] += 1
+                    check(rx[r] / Tx[r][q] > lim_exact)
         # the kernel's tie certification is exercised by the GPU parity tests;
         # here the exact minimum ratio row (unique in these samples) is taken
         # when the binary32 ratios separate it
@@ -216,6 +283,28 @@ def test_running_bounds_hold_and_certified_decisions_are_exact():
         pivots += run(xi64, eta64, xs, es, check)
     assert not fails, len(fails)
     assert pivots >= 150  # most samples pivot through phase I under certification
+
+
+def test_uncertain_rows_passed_over_are_never_the_leaving_row():
+    rng = np.random.default_rng(1508)
+    fails = []
+
+    def check(ok):
+        if not ok:
+            fails.append(1)
+
+    STATS.update(uncertain_rows_passed=0, uncertain_rows_eligible=0)
+    for _ in range(300):
+        run(*lattice_columns(rng), check)
+    # jittered neighbourhoods also give uncertain rows that are in fact
+    # eligible (pivot elements just above 1e-9 under large bounds), where the
+    # exact comparison with the tie limit has teeth
+    rng = np.random.default_rng(5)
+    for _ in range(600):
+        run(*columns(rng), check)
+    assert not fails, len(fails)
+    assert STATS["uncertain_rows_passed"] > 0  # the rule is exercised
+    assert STATS["uncertain_rows_eligible"] > 0
 
 
 def test_a_planted_underestimate_is_caught():
