@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(256) k_reduce_pass(const double* __restrict__ 
 __global__ void __launch_bounds__(1024) k_reduce_tail(const double* __restrict__ g, ReduceState* __restrict__ st,
                                                       const int* __restrict__ sub) {
   __shared__ unsigned long long h[256][4];
-  __shared__ unsigned long long s_lo[256], s_hi[256];
+  __shared__ unsigned long long s_lo[8], s_hi[8];
   __shared__ int s_sel;
   const int b = threadIdx.x;
   const int n = st->n_sub;
@@ -473,26 +473,26 @@ __global__ void __launch_bounds__(1024) k_reduce_tail(const double* __restrict__
     }
     __syncthreads();
     // inclusive scan of the 128-bit bucket sums over the first 256 threads
+    // (warps 0..7): shuffles within each warp, then the warps' totals
     u128 v = 0, acc = 0;
     if (b < 256) {
       v = (u128)h[b][0] + ((u128)h[b][1] << 32) + ((u128)h[b][2] << 64);
       acc = v;
-      s_lo[b] = (unsigned long long)acc;
-      s_hi[b] = (unsigned long long)(acc >> 64);
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long lo = __shfl_up_sync(0xffffffffu, (unsigned long long)acc, o);
+        const unsigned long long hi = __shfl_up_sync(0xffffffffu, (unsigned long long)(acc >> 64), o);
+        if (lane >= o) acc += ((u128)hi << 64) | (u128)lo;
+      }
+      if (lane == 31) {
+        s_lo[b >> 5] = (unsigned long long)acc;
+        s_hi[b >> 5] = (unsigned long long)(acc >> 64);
+      }
     }
     if (b == 0) s_sel = 255;
     __syncthreads();
-    for (int o = 1; o < 256; o <<= 1) {
-      u128 add = 0;
-      if (b < 256 && b >= o) add = ((u128)s_hi[b - o] << 64) | (u128)s_lo[b - o];
-      __syncthreads();
-      if (b < 256) {
-        acc += add;
-        s_lo[b] = (unsigned long long)acc;
-        s_hi[b] = (unsigned long long)(acc >> 64);
-      }
-      __syncthreads();
-    }
+    if (b < 256)
+      for (int k = 0; k < (b >> 5); ++k) acc += ((u128)s_hi[k] << 64) | (u128)s_lo[k];
     const u128 tau = ((u128)st->tau_hi << 64) | (u128)st->tau_lo;
     const u128 excl = acc - v;
     if (b < 256 && acc > tau && excl <= tau) atomicMin(&s_sel, b);
