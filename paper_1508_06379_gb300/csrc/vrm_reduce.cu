@@ -604,6 +604,8 @@ cudaError_t reduce_select_dev(const double* gamma, int n_bound, const int* n_dev
                               unsigned long long* bbox) {
   int blocks = n_bound > 0 ? (n_bound + kBlock - 1) / kBlock : 1;
   int pblocks = blocks < 4 * sm_count() ? blocks : 4 * sm_count();
+  // k_absmax keeps one partial maximum per block in the 1024 slots of hist
+  if (pblocks > 1024) pblocks = 1024;
   k_absmax<<<pblocks, kBlock, 0, s>>>(gamma, n_bound, n_dev, st, ds, c_bound, x, y, bbox); note_launch();
   for (int pass = 0; pass < 3; ++pass) {
     // pass 2 lists its matches in tie_rank (free until the tie scan)
