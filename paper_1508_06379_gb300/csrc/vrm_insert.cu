@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kBlock) k_open_flags(const int* __restrict__ l
 cudaError_t open_list(const int* dlist, const int* dcount, int cap, const uint8_t* mask, uint8_t* flag, int* pos,
                       int* open, int* n_open, int* flag_ts, cudaStream_t s) {
   const int tiles = (cap + kScanTile - 1) / kScanTile;
-  k_open_flags<<<tiles < 4 * sm_count() ? tiles : 4 * sm_count(), kBlock, 0, s>>>(dlist, dcount, mask, flag, flag_ts);
+  k_open_flags<<<tiles < 8 * sm_count() ? tiles : 8 * sm_count(), kBlock, 0, s>>>(dlist, dcount, mask, flag, flag_ts);
   note_launch();
   cudaError_t e = scan_presummed_u8_dev(flag, pos, cap, dcount, flag_ts, s);
   if (e != cudaSuccess) return e;
@@ -469,7 +469,7 @@ cudaError_t rounds_init(StepState* st, const int* n_open_src, const RoundBufs& r
                         cudaGraphConditionalHandle handle, bool graph, cudaStream_t s) {
   k_rounds_init<<<1, 1, 0, s>>>(st, n_open_src, handle, graph ? 1 : 0); note_launch();
   const int tiles = (cap + kScanTile - 1) / kScanTile;
-  k_cand_count_dev<<<tiles < 4 * sm_count() ? tiles : 4 * sm_count(), kBlock, 0, s>>>(rb.open, n_open_src, mask, rb.cnt,
+  k_cand_count_dev<<<tiles < 8 * sm_count() ? tiles : 8 * sm_count(), kBlock, 0, s>>>(rb.open, n_open_src, mask, rb.cnt,
                                                                                     rb.act0, rb.cnt_ts);
   note_launch();
   return cudaGetLastError();
